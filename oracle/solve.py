@@ -1,0 +1,89 @@
+"""Whole-solve drivers (oracle) with the same inputs and outputs as the C ABI.
+
+A solve takes the density rho and a potential field phi that carries the
+initial guess on unknown nodes and Dirichlet data on boundary/ghost nodes.
+The right-hand side of Eq. 1 / Eq. 2 is f = 4 pi G rho.  With the multipole
+boundary (Sec. 2.2) the boundary values are first replaced by the truncated
+outer expansion of the moments of rho.  Iterations stop when
+||f - A phi||_2 <= tol * ||f - A phi0||_2, phi0 being phi with zero unknowns,
+checked after every SOR step, CG/BiCGSTAB iteration or V-cycle; reaching
+max_iter without that is "not converged" (Sec. 2.1: a warning, not an error).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import multigrid, multipole
+from .grid import CartGrid
+from .operators import norm2, reference_norm, residual
+from .smoothers import sweep
+from .spherical import SphericalOperator, bicgstab_solve
+
+
+@dataclass
+class SolveInfo:
+    iterations: int
+    converged: bool
+    rel_residual: float
+    rho_conv: float
+    history: list = field(default_factory=list)
+    moments: np.ndarray | None = None
+
+
+def sor_solve(phi, f, grid: CartGrid, omega: float, tol: float, max_iter: int):
+    ref = reference_norm(phi, f, grid)
+    if ref == 0.0:
+        ref = 1.0
+    hist = [norm2(residual(phi, f, grid), grid) / ref]
+    if hist[-1] <= tol:
+        return 0, True, hist
+    for it in range(1, max_iter + 1):
+        sweep(phi, f, grid, omega)
+        hist.append(norm2(residual(phi, f, grid), grid) / ref)
+        if hist[-1] <= tol:
+            return it, True, hist
+    return max_iter, False, hist
+
+
+def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: str, tol: float,
+                    max_iter: int = 10000, G: float = 1.0, bc: str = "dirichlet", lmax: int = 4,
+                    origin=None, omega: float = 1.0, nu1: int = 2, nu2: int = 2,
+                    inner: int = 1) -> SolveInfo:
+    """method in {"sor", "cg", "mg", "ir"}; phi is updated in place."""
+    f = 4.0 * math.pi * G * rho
+    q = None
+    if bc == "multipole":
+        if origin is None:
+            origin = tuple(0.5 * (grid.lo[a] + grid.hi[a]) for a in range(3))
+        q = multipole.moments_cartesian(rho, grid, origin, lmax)
+        multipole.apply_cartesian_bc(phi, grid, q, origin, lmax, G)
+    if method == "sor":
+        it, conv, hist = sor_solve(phi, f, grid, omega, tol, max_iter)
+    elif method == "cg":
+        res = multigrid.cg_on_grid(phi, f, grid, tol, max_iter)
+        it, conv, hist = res.iterations, res.converged, res.history
+    elif method == "mg":
+        it, conv, hist = multigrid.mg_solve(phi, f, grid, tol, max_iter, nu1, nu2)
+    elif method == "ir":
+        it, conv, hist = multigrid.ir_solve(phi, f, grid, tol, max_iter, nu1, nu2, inner)
+    else:
+        raise ValueError(method)
+    return SolveInfo(it, conv, hist[-1], multigrid.convergence_factor(hist), hist, q)
+
+
+def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
+                    max_iter: int = 20000, G: float = 1.0, bc: str = "multipole",
+                    lmax: int = 6) -> SolveInfo:
+    """Right-Jacobi BiCGSTAB on the spherical grid; phi in the ghosted layout."""
+    op = SphericalOperator(r, th, ph)
+    f = 4.0 * math.pi * G * rho
+    q = None
+    if bc == "multipole":
+        q = multipole.moments_spherical(rho, r, th, ph, lmax)
+        phi[1:-1, 1:-1, -1] = multipole.spherical_outer_ghost(q, r, th, ph, lmax, G)
+    res = bicgstab_solve(phi, f, op, tol, max_iter)
+    return SolveInfo(res.iterations, res.converged, res.history[-1],
+                     multigrid.convergence_factor(res.history), res.history, q)

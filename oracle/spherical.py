@@ -1,0 +1,115 @@
+"""Spherical-grid Laplacian and BiCGSTAB solve (oracle).
+
+Eq. 2 discretised by direct finite differences in flux form on nodes
+r_i (any increasing radii, here logarithmic), theta_j = (j+1/2) pi / Ntheta,
+phi_k = 2 pi k / Nphi:
+
+  (1/r_i^2) [ r_{i+1/2}^2 (P_{i+1}-P_i)/(r_{i+1}-r_i)
+              - r_{i-1/2}^2 (P_i-P_{i-1})/(r_i-r_{i-1}) ] / ((r_{i+1}-r_{i-1})/2)
++ 1/(r_i^2 sin(t_j) dt^2) [ sin(t_{j+1/2}) (P_{j+1}-P_j) - sin(t_{j-1/2}) (P_j-P_{j-1}) ]
++ (P_{k+1} - 2 P_k + P_{k-1}) / (r_i^2 sin^2(t_j) dp^2)
+
+with r_{i+-1/2} the arithmetic midpoints and sin(t_{-1/2}) = sin(t_{Nt-1/2}) = 0
+at the poles (Sec. 2.2: angular boundaries follow the coordinate symmetries;
+phi is periodic).  The operator is not symmetric, hence BiCGSTAB (Sec. 2.1.2).
+Inner boundary: Neumann by a mirror ghost P_{-1} = P_1 at r_{-1} = 2 r_0 - r_1.
+Outer boundary: Dirichlet ghost at r_N (multipole potential or given data).
+
+Layout: (Nphi+2, Ntheta+2, Nr+2), r fastest, node (i,j,k) at [k+1, j+1, i+1].
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import krylov
+from .multipole import radial_extended
+
+
+class SphericalOperator:
+    def __init__(self, r, th, ph):
+        self.r = np.asarray(r, dtype=np.float64)
+        self.th = np.asarray(th, dtype=np.float64)
+        self.ph = np.asarray(ph, dtype=np.float64)
+        self.nr, self.nt, self.np_ = self.r.size, self.th.size, self.ph.size
+        self.re = radial_extended(self.r)
+        self.dth = math.pi / self.nt
+        self.dph = 2.0 * math.pi / self.np_
+        j = np.arange(self.nt + 1)
+        sf = np.sin(j * math.pi / self.nt)           # sin(theta_{j-1/2}) for j=0..Nt
+        sf[0] = 0.0
+        sf[-1] = 0.0
+        self.sin_face = sf
+        self.sin_c = np.sin(self.th)
+
+    @property
+    def shape(self):
+        return (self.np_ + 2, self.nt + 2, self.nr + 2)
+
+    def fill_ghosts(self, P: np.ndarray) -> None:
+        """Inner mirror and periodic phi ghosts (outer ghost untouched)."""
+        P[:, :, 0] = P[:, :, 2]
+        P[0, :, :] = P[self.np_, :, :]
+        P[self.np_ + 1, :, :] = P[1, :, :]
+
+    def apply(self, P: np.ndarray) -> np.ndarray:
+        """L P on the unknown nodes, shape (Nphi, Ntheta, Nr)."""
+        P = P.copy()
+        self.fill_ghosts(P)
+        re = self.re
+        ri = re[1:-1]
+        rp = 0.5 * (re[2:] + re[1:-1])       # r_{i+1/2}
+        rm = 0.5 * (re[1:-1] + re[:-2])      # r_{i-1/2}
+        C = P[1:-1, 1:-1, 1:-1]
+        rad = (rp ** 2 * (P[1:-1, 1:-1, 2:] - C) / (re[2:] - ri)
+               - rm ** 2 * (C - P[1:-1, 1:-1, :-2]) / (ri - re[:-2])) / (0.5 * (re[2:] - re[:-2]))
+        rad = rad / ri ** 2
+        sp = self.sin_face[1:][None, :, None]
+        sm = self.sin_face[:-1][None, :, None]
+        sc = self.sin_c[None, :, None]
+        th = (sp * (P[1:-1, 2:, 1:-1] - C) - sm * (C - P[1:-1, :-2, 1:-1])) / (
+            ri[None, None, :] ** 2 * sc * self.dth ** 2)
+        ph = (P[2:, 1:-1, 1:-1] - 2.0 * C + P[:-2, 1:-1, 1:-1]) / (
+            ri[None, None, :] ** 2 * sc ** 2 * self.dph ** 2)
+        return rad + th + ph
+
+    def diagonal(self) -> np.ndarray:
+        re = self.re
+        ri = re[1:-1]
+        rp = 0.5 * (re[2:] + re[1:-1])
+        rm = 0.5 * (re[1:-1] + re[:-2])
+        drad = -(rp ** 2 / (re[2:] - ri) + rm ** 2 / (ri - re[:-2])) / (0.5 * (re[2:] - re[:-2])) / ri ** 2
+        sp = self.sin_face[1:][None, :, None]
+        sm = self.sin_face[:-1][None, :, None]
+        sc = self.sin_c[None, :, None]
+        dth = -(sp + sm) / (ri[None, None, :] ** 2 * sc * self.dth ** 2)
+        dph = -2.0 / (ri[None, None, :] ** 2 * sc ** 2 * self.dph ** 2)
+        d = drad[None, None, :] + dth + dph
+        return np.broadcast_to(d, (self.np_, self.nt, self.nr)).copy()
+
+
+def bicgstab_solve(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator, tol: float,
+                   max_iter: int):
+    """Solve L P = f (f on the ghosted layout) with right-Jacobi BiCGSTAB.
+
+    The outer ghost of Pfield is Dirichlet data; unknown nodes hold the
+    initial guess and receive the solution."""
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    shp = Pfield[U].shape
+
+    def apply_hom(v):
+        full = np.zeros(op.shape)
+        full[U] = v.reshape(shp)
+        return op.apply(full).ravel()
+
+    bdry = np.zeros(op.shape)
+    bdry[:, :, -1] = Pfield[:, :, -1]
+    b = (f[U] - op.apply(bdry)).ravel()
+    ref = float(np.sqrt(b @ b))
+    if ref == 0.0:
+        ref = 1.0
+    inv_diag = (1.0 / op.diagonal()).ravel()
+    res = krylov.bicgstab(apply_hom, inv_diag, b, Pfield[U].ravel().copy(), tol, max_iter, ref)
+    Pfield[U] = res.x.reshape(shp)
+    return res

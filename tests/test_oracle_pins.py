@@ -1,0 +1,536 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Every test here checks the oracle against something other than itself:
+closed-form potentials, convergence orders under refinement, a dense direct
+solve of an independently assembled matrix, textbook identities of the
+transfer operators, brute-force sequential sweeps, library special functions,
+the addition theorem, and the step counts printed in Table 3.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov, multigrid, multipole as MP, smoothers as SM, solve as S
+from oracle import spherical as SP, transfer as TR
+from oracle.grid import cart_grid, hierarchy
+from oracle.operators import laplacian, residual
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("order,expect,tol", [(2, 4.0, 0.3), (4, 16.0, 2.0)])
+def test_manufactured_convergence_order(order, expect, tol):
+    """sin(pi x) sin(pi y) sin(pi z): max error ratio under N -> 2N is 2^order."""
+    errs = []
+    for n in (16, 32, 64):
+        rho, phi, exact = W.manufactured_sine(n, order)
+        g = cart_grid(n, order)
+        info = S.solve_cartesian(rho, phi, g, "mg", 1e-12)
+        assert info.converged
+        errs.append(np.max(np.abs(phi[g.interior] - exact[g.interior])))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    for r in ratios:
+        assert abs(r - expect) < tol, ratios
+
+
+def _lap1d(n, h, order):
+    """1-D second-derivative matrix on interior nodes 1..n-1, zero boundary."""
+    m = n - 1
+    w = {2: [(-1, 1.0), (0, -2.0), (1, 1.0)],
+         4: [(-2, -1 / 12), (-1, 16 / 12), (0, -30 / 12), (1, 16 / 12), (2, -1 / 12)]}[order]
+    D = np.zeros((m, m))
+    for i in range(m):
+        for d, c in w:
+            j = i + d
+            if 0 <= j < m:
+                D[i, j] += c / h ** 2
+    return D
+
+
+def _dense_matrix(n, order):
+    h = 1.0 / n
+    D = _lap1d(n, h, order)
+    I = np.eye(n - 1)
+    return (np.kron(I, np.kron(I, D)) + np.kron(I, np.kron(D, I)) + np.kron(D, np.kron(I, I)))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("method", ["cg", "mg", "sor", "ir"])
+def test_dense_direct_solve(order, method):
+    """8^3 intervals, zero boundary, random rho: iterative solutions agree with
+    numpy.linalg.solve on a Kronecker-sum matrix assembled independently."""
+    n = 8 if method != "mg" else 16        # MG needs one coarsening (>= 16)
+    g = cart_grid(n, order)
+    gen = W.rng(11)
+    rho = np.zeros(g.shape)
+    rho[g.interior] = gen.standard_normal(rho[g.interior].shape)
+    A = _dense_matrix(n, order)
+    x = np.linalg.solve(A, (4 * math.pi * rho[g.interior]).ravel())
+    phi = g.zeros()
+    kw = {"omega": 1.5} if method == "sor" else {}
+    info = S.solve_cartesian(rho, phi, g, method, 1e-13, max_iter=20000, **kw)
+    assert info.converged
+    got = phi[g.interior].ravel()
+    assert np.max(np.abs(got - x)) / np.max(np.abs(x)) < 1e-11
+
+
+def test_operator_matches_dense_matrix():
+    for order in (2, 4):
+        n = 8
+        g = cart_grid(n, order)
+        v = g.zeros()
+        v[g.interior] = W.rng(3).standard_normal(v[g.interior].shape)
+        A = _dense_matrix(n, order)
+        got = laplacian(v, g)[g.interior].ravel()
+        np.testing.assert_allclose(got, A @ v[g.interior].ravel(), rtol=1e-13, atol=1e-9)
+
+
+def test_uniform_sphere_closed_form():
+    """Config with rho = 1 in a sphere of radius 0.25: error vs the textbook
+    potential <= 2e-2 at N = 32 and decreasing under refinement."""
+    errs = []
+    for n in (16, 32):
+        rho, phi, exact = W.uniform_sphere(n)
+        g = cart_grid(n)
+        S.solve_cartesian(rho, phi, g, "mg", 1e-10)
+        I = g.interior
+        errs.append(np.max(np.abs(phi[I] - exact[I])) / np.max(np.abs(exact[I])))
+    assert errs[1] <= 2e-2
+    assert errs[1] < errs[0]
+
+
+def _phi_smooth_sphere(X, Y, Z, c, a, m, G=1.0):
+    """Sec. 3.1 closed form (reading (x - x_p)^2 for the garbled (x - x_p^2))."""
+    rp = m / (32 * math.pi * a ** 3 / 105)
+    d = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+    w = d / a
+    inside = 4 * math.pi * G * rp * a ** 2 * (-1 / 6 + w ** 2 / 6 - w ** 4 / 10 + w ** 6 / 42)
+    return np.where(d < a, inside, -G * m / np.maximum(d, 1e-300))
+
+
+def test_smooth_sphere_closed_form_is_a_poisson_solution():
+    """The printed potential satisfies Eq. 1 for the printed density (checked by
+    centred differences of the closed form) and is continuous at d = a."""
+    c, a, m = (0.1, -0.05, 0.02), 0.3, 1.5
+    h = 1e-3
+    pts = np.array([[0.1, -0.05, 0.1], [0.25, 0.0, 0.0], [0.5, 0.4, -0.3], [0.1, 0.1, 0.05]])
+    for p in pts:
+        lap = 0.0
+        for ax in range(3):
+            e = np.zeros(3)
+            e[ax] = h
+            f = lambda q: _phi_smooth_sphere(*q, c, a, m)
+            lap += (f(p + e) - 2 * f(p) + f(p - e)) / h ** 2
+        d = np.linalg.norm(p - np.array(c))
+        rho = m / (32 * math.pi * a ** 3 / 105) * (1 - (d / a) ** 2) ** 2 if d < a else 0.0
+        assert abs(lap - 4 * math.pi * rho) < 1e-4 * max(1.0, 4 * math.pi * rho)
+    inner = _phi_smooth_sphere(np.array(c[0] + a - 1e-12), np.array(c[1]), np.array(c[2]), c, a, m)
+    assert abs(inner + m / a) < 1e-9
+
+
+def test_smooth_sphere_second_order():
+    """Dirichlet data from the closed form, one resolved sphere: error ~ h^2."""
+    c, a, m = (0.0, 0.0, 0.0), 0.6, 1.0
+    errs = []
+    for n in (16, 32, 64):
+        g = cart_grid(n, 2, (-1, -1, -1), (1, 1, 1))
+        x, y, z = g.coords(0), g.coords(1), g.coords(2)
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        exact = _phi_smooth_sphere(X, Y, Z, c, a, m)
+        rho = W.smooth_sphere_density(n, 2, [c], [a], [m])
+        phi = exact.copy()
+        phi[g.interior] = 0.0
+        S.solve_cartesian(rho, phi, g, "mg", 1e-12)
+        errs.append(np.max(np.abs(phi - exact)))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+# ------------------------------------------------------------------ smoothers
+
+def _bruteforce_sweep(phi, f, n, order, omega):
+    """Sequential per-colour lexicographic sweep, one node at a time."""
+    w = {2: {1: 1.0}, 4: {1: 16 / 12, 2: -1 / 12}}[order]
+    w0 = {2: -2.0, 4: -30 / 12}[order]
+    h2 = (1.0 / n) ** 2
+    g = order // 2
+    ncol = {2: 2, 4: 3}[order]
+    for c in range(ncol):
+        for k in range(1, n):
+            for j in range(1, n):
+                for i in range(1, n):
+                    if (i + j + k) % ncol != c:
+                        continue
+                    K, J, Ii = k + g - 1, j + g - 1, i + g - 1
+                    off = 0.0
+                    for d, wd in w.items():
+                        off += wd * (phi[K, J, Ii + d] + phi[K, J, Ii - d] + phi[K, J + d, Ii]
+                                     + phi[K, J - d, Ii] + phi[K + d, J, Ii] + phi[K - d, J, Ii])
+                    diag = 3 * w0
+                    gs = (f[K, J, Ii] * h2 - off) / diag
+                    phi[K, J, Ii] += omega * (gs - phi[K, J, Ii])
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_sweep_equals_sequential_gauss_seidel(order):
+    n = 6
+    g = cart_grid(n, order)
+    gen = W.rng(5)
+    phi = gen.standard_normal(g.shape)
+    f = gen.standard_normal(g.shape)
+    a = phi.copy()
+    b = phi.copy()
+    SM.sweep(a, f, g, 1.3)
+    _bruteforce_sweep(b, f, n, order, 1.3)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+def test_two_colours_are_not_enough_for_radius_two():
+    """Sec. 2.1.1: with two colours, independence holds only for radius one:
+    a 2-colour sweep of the 13-point stencil depends on node order."""
+    n = 6
+    g = cart_grid(n, 4)
+    gen = W.rng(6)
+    phi = gen.standard_normal(g.shape)
+    f = gen.standard_normal(g.shape)
+    vec = phi.copy()
+    SM.sweep(vec, f, g, 1.0, ncol=2)
+    seq = phi.copy()
+    # sequential 2-colour sweep in lexicographic order
+    w = {1: 16 / 12, 2: -1 / 12}
+    for c in range(2):
+        for k in range(1, n):
+            for j in range(1, n):
+                for i in range(1, n):
+                    if (i + j + k) % 2 != c:
+                        continue
+                    K, J, I = k + 1, j + 1, i + 1
+                    off = sum(wd * (seq[K, J, I + d] + seq[K, J, I - d] + seq[K, J + d, I]
+                                    + seq[K, J - d, I] + seq[K + d, J, I] + seq[K - d, J, I])
+                              for d, wd in w.items())
+                    seq[K, J, I] = (f[K, J, I] / n ** 2 - off) / (-3 * 30 / 12)
+    assert np.max(np.abs(vec - seq)) > 1e-6
+
+
+def test_omega_formulas():
+    """Eqs. 3-5: uniform cube gives rJ = cos(pi/N), omega_opt = 2/(1+sin(pi/N));
+    omega_opt,a approaches omega_opt as N grows."""
+    for n in (16, 32, 64, 512):
+        g = cart_grid(n)
+        rj = SM.rjac_uniform(g)
+        assert abs(rj - math.cos(math.pi / n)) < 1e-15
+        assert abs(SM.omega_opt(rj) - 2 / (1 + math.sin(math.pi / n))) < 1e-12
+    d32 = abs(SM.omega_opt_a(32) - SM.omega_opt(math.cos(math.pi / 32)))
+    d512 = abs(SM.omega_opt_a(512) - SM.omega_opt(math.cos(math.pi / 512)))
+    assert d512 < d32 / 100
+    # anisotropic spacing weights the cosines by h^-2
+    g = cart_grid((16, 32, 64), lo=(0, 0, 0), hi=(1, 1, 1))
+    num = sum(math.cos(math.pi / g.n[a]) / g.h[a] ** 2 for a in range(3))
+    assert abs(SM.rjac_uniform(g) - num / sum(1 / g.h[a] ** 2 for a in range(3))) < 1e-15
+
+
+def test_sor_optimal_omega_beats_gauss_seidel():
+    rho, phi, _ = W.uniform_sphere(16)
+    g = cart_grid(16)
+    it_gs = S.solve_cartesian(rho, phi.copy(), g, "sor", 1e-8, omega=1.0).iterations
+    w = SM.omega_opt(SM.rjac_uniform(g))
+    it_sor = S.solve_cartesian(rho, phi.copy(), g, "sor", 1e-8, omega=w).iterations
+    assert it_sor < it_gs / 3
+
+
+# ------------------------------------------------------------------- transfer
+
+def test_restriction_prolongation_adjoint_and_constants():
+    fine = cart_grid(16)
+    coarse = fine.coarsen()
+    gen = W.rng(7)
+    u = fine.zeros()
+    u[fine.interior] = gen.standard_normal(u[fine.interior].shape)
+    v = coarse.zeros()
+    v[coarse.interior] = gen.standard_normal(v[coarse.interior].shape)
+    lhs = 8.0 * np.sum(TR.restrict(u, fine, coarse) * v)
+    rhs = np.sum(u * TR.prolong(v, coarse, fine))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    one = fine.zeros()
+    one[fine.interior] = 1.0
+    np.testing.assert_allclose(TR.restrict(one, fine, coarse)[coarse.interior], 1.0, rtol=1e-15)
+    c1 = coarse.zeros()
+    c1[coarse.interior] = 1.0
+    pc = TR.prolong(c1, coarse, fine)
+    # away from the boundary (where coarse boundary values are zero) P keeps constants
+    np.testing.assert_allclose(pc[2:-2, 2:-2, 2:-2], 1.0, rtol=1e-15)
+
+
+def test_full_weighting_of_quadratic():
+    """1-D full weighting maps x^2 to x^2 + h^2/2 per axis."""
+    fine = cart_grid(16)
+    coarse = fine.coarsen()
+    x = fine.coords(0)
+    u = np.broadcast_to(x[None, None, :] ** 2, fine.shape).copy()
+    rc = TR.restrict(u, fine, coarse)[coarse.interior]
+    xc = coarse.coords(0)[coarse.interior[2]]
+    h = fine.h[0]
+    np.testing.assert_allclose(rc, np.broadcast_to(xc ** 2 + h ** 2 / 2, rc.shape), rtol=1e-13)
+
+
+def test_prolongation_is_trilinear():
+    fine = cart_grid(16)
+    coarse = fine.coarsen()
+    xc, yc, zc = coarse.coords(0), coarse.coords(1), coarse.coords(2)
+    lin = lambda X, Y, Z: 1.0 + 2 * X - 3 * Y + 0.5 * Z + X * Y * Z
+    Zc, Yc, Xc = np.meshgrid(zc, yc, xc, indexing="ij")
+    vc = coarse.zeros()
+    vc[coarse.interior] = lin(Xc, Yc, Zc)[coarse.interior]
+    pf = TR.prolong(vc, coarse, fine)
+    Zf, Yf, Xf = np.meshgrid(fine.coords(2), fine.coords(1), fine.coords(0), indexing="ij")
+    # trilinear interpolation reproduces multilinear functions exactly inside the
+    # region spanned by interior coarse nodes (fine nodes 2..N-2)
+    sl = (slice(2, -2), slice(2, -2), slice(2, -2))
+    np.testing.assert_allclose(pf[sl], lin(Xf, Yf, Zf)[sl], rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------------------------------ multigrid
+
+def test_mg_grid_independent_convergence():
+    """Sec. 2.1.3: MG convergence does not depend on the grid spacing; the
+    V-cycle count to 1e-6 stays within 3-7 (Sec. 4) and flat in N."""
+    counts, rhos = [], []
+    for n in (32, 64):
+        rho = W.gaussian_blobs(n, seed=2)
+        g = cart_grid(n)
+        phi = g.zeros()
+        info = S.solve_cartesian(rho, phi, g, "mg", 1e-6, bc="multipole", lmax=4)
+        counts.append(info.iterations)
+        rhos.append(info.rho_conv)
+    assert all(3 <= c <= 7 for c in counts), counts
+    assert abs(counts[0] - counts[1]) <= 1
+    assert abs(rhos[0] - rhos[1]) < 0.25 * max(rhos)
+
+
+def test_ir_reproduces_mg():
+    """One V-cycle on the error equation per refinement step is the MG
+    iteration itself (linear stationary iteration), in float64."""
+    rho = W.gaussian_blobs(32, seed=2)
+    g = cart_grid(32)
+    a, b = g.zeros(), g.zeros()
+    ia = S.solve_cartesian(rho, a, g, "mg", 1e-10, bc="multipole")
+    ib = S.solve_cartesian(rho, b, g, "ir", 1e-10, bc="multipole")
+    assert ia.iterations == ib.iterations
+    assert np.max(np.abs(a - b)) / np.max(np.abs(a)) < 1e-12
+
+
+def test_hierarchy_levels():
+    assert [l.n[0] for l in hierarchy(cart_grid(256))] == [256, 128, 64, 32, 16, 8]
+    assert [l.n[0] for l in hierarchy(cart_grid(96))] == [96, 48, 24, 12]
+    assert [l.n[0] for l in hierarchy(cart_grid(512))][-1] == 8
+
+
+# ------------------------------------------------------------------ Table 3
+
+def _two_sphere(n):
+    cfg = json.load(open(os.path.join(GOLDEN, "two_sphere_setup.json")))
+    g = cart_grid(n, 2, (-1, -1, -1), (1, 1, 1))
+    rho = W.smooth_sphere_density(n, 2, cfg["centres"], cfg["radii"], cfg["masses"])
+    return g, rho
+
+
+@pytest.mark.parametrize("method,slack", [("CG2", 0.05), ("SOR", 0.12)])
+def test_table3_step_counts(method, slack):
+    """Steps to the residual reductions of Table 3 at N = 64 (cold start,
+    multipole boundary, SOR with omega_opt,a of Eq. 5)."""
+    tab = json.load(open(os.path.join(GOLDEN, "table3_steps.json")))
+    n = 64
+    g, rho = _two_sphere(n)
+    for row in tab["rows"]:
+        if row["method"] != method or row["N"] != n:
+            continue
+        phi = g.zeros()
+        if method == "CG2":
+            info = S.solve_cartesian(rho, phi, g, "cg", row["reduction"], bc="multipole",
+                                     lmax=4, origin=(0, 0, 0))
+        else:
+            info = S.solve_cartesian(rho, phi, g, "sor", row["reduction"], bc="multipole",
+                                     lmax=4, origin=(0, 0, 0), omega=SM.omega_opt_a(n))
+        assert abs(info.iterations - row["steps"]) <= slack * row["steps"], (row, info.iterations)
+
+
+# ------------------------------------------------------------------ multipole
+
+def test_multipole_matches_addition_theorem():
+    """Eq. outer_multipole + Eq. outer_expansion equal the Legendre form
+    -G sum rho dV sum_l r'^l/r^(l+1) P_l(cos gamma) (numpy's Legendre series)."""
+    n = 12
+    g = cart_grid(n)
+    rho = W.gaussian_blobs(n, seed=4, nblobs=3)
+    for lmax in (0, 3, 8):
+        q = MP.moments_cartesian(rho, g, (0.5, 0.5, 0.5), lmax)
+        pts = [(0.5, 0.1, -0.2), (-0.5, -0.5, 0.5), (0.3, -0.5, 0.45), (0.0, 0.0, 0.6)]
+        direct = MP.direct_legendre_potential(rho, g, (0.5, 0.5, 0.5), lmax, 1.0, pts)
+        pp = np.array(pts)
+        exp = MP.potential_points(q, pp[:, 0], pp[:, 1], pp[:, 2], lmax, 1.0)
+        np.testing.assert_allclose(exp, direct, rtol=1e-13)
+
+
+def test_monopole_is_total_mass_and_odd_moments_vanish():
+    n = 16
+    g = cart_grid(n)
+    rho = W.gaussian_blobs(n, blobs=[W.Blob((0.5, 0.5, 0.5), 0.1, 1.0)])
+    q = MP.moments_cartesian(rho, g, (0.5, 0.5, 0.5), 6)
+    assert abs(q[0] - rho[g.interior].sum() / n ** 3) < 1e-15
+    for l in (1, 3, 5):
+        for m in range(-l, l + 1):
+            assert abs(q[MP.idx(l, m)]) < 1e-16
+    # an off-centre blob has a dipole along its offset
+    rho2 = W.gaussian_blobs(n, blobs=[W.Blob((0.5, 0.5, 0.7), 0.05, 1.0)])
+    q2 = MP.moments_cartesian(rho2, g, (0.5, 0.5, 0.5), 1)
+    assert q2[MP.idx(1, 0)] > 0 and abs(q2[MP.idx(1, 1)]) < 1e-15 and abs(q2[MP.idx(1, -1)]) < 1e-15
+    np.testing.assert_allclose(q2[MP.idx(1, 0)] / q2[0], 0.2, rtol=1e-4)
+
+
+def test_real_harmonics_against_scipy_and_orthonormality():
+    sp = pytest.importorskip("scipy.special")
+    lmax = 6
+    gen = W.rng(9)
+    th = gen.uniform(0, math.pi, 40)
+    ph = gen.uniform(-math.pi, math.pi, 40)
+    Y = MP.real_sph_harm(lmax, th, ph)
+    if hasattr(sp, "sph_harm_y"):
+        for l in range(lmax + 1):
+            for m in range(0, l + 1):
+                c = sp.sph_harm_y(l, m, th, ph)          # complex, Condon-Shortley phase
+                cs = (-1) ** m
+                if m == 0:
+                    np.testing.assert_allclose(Y[MP.idx(l, 0)], c.real, atol=1e-13)
+                else:
+                    np.testing.assert_allclose(Y[MP.idx(l, m)], cs * math.sqrt(2) * c.real, atol=1e-13)
+                    np.testing.assert_allclose(Y[MP.idx(l, -m)], cs * math.sqrt(2) * c.imag, atol=1e-13)
+    # orthonormality by Gauss-Legendre x trapezoid quadrature (exact for these degrees)
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    phs = np.arange(32) * 2 * math.pi / 32
+    T, Pp = np.meshgrid(np.arccos(xg), phs, indexing="ij")
+    W2 = wg[:, None] * (2 * math.pi / 32)
+    Yq = MP.real_sph_harm(lmax, T, Pp)
+    G = np.array([[np.sum(a * b * W2) for b in Yq] for a in Yq])
+    np.testing.assert_allclose(G, np.eye(len(Yq)), atol=1e-12)
+
+
+def test_multipole_boundary_converges_to_green_sum():
+    """Paper's two-sphere setup: the truncated expansion approaches the direct
+    Green's sum -G sum rho dV / |x - x'| on the faces as l_max grows."""
+    cfg = json.load(open(os.path.join(GOLDEN, "two_sphere_setup.json")))
+    n = 32
+    g = cart_grid(n, 2, (-1, -1, -1), (1, 1, 1))
+    rho = W.smooth_sphere_density(n, 2, cfg["centres"], cfg["radii"], cfg["masses"])
+    I = g.interior
+    Z, Y, X = np.meshgrid(g.coords(2), g.coords(1), g.coords(0), indexing="ij")
+    src = np.stack([X[I], Y[I], Z[I]], -1).reshape(-1, 3)
+    w = (rho[I] * g.h[0] ** 3).ravel()
+    keep = w > 0
+    src, w = src[keep], w[keep]
+    pts = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0], [0.0, 0.0, -1.0], [1.0, 1.0, 1.0], [0.3, -1.0, 0.2]])
+    green = np.array([-np.sum(w / np.linalg.norm(src - p, axis=1)) for p in pts])
+    errs = []
+    for lmax in (0, 2, 4, 8):
+        q = MP.moments_cartesian(rho, g, (0, 0, 0), lmax)
+        v = MP.potential_points(q, pts[:, 0], pts[:, 1], pts[:, 2], lmax, 1.0)
+        errs.append(np.max(np.abs(v - green) / np.abs(green)))
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    # truncation bound ~ (r'_max / r_min)^(lmax+1) with r'_max = 0.48, r_min = 1
+    assert errs[3] < 0.48 ** 9
+    assert errs[3] < errs[1] / 10
+
+
+# ------------------------------------------------------------------ spherical
+
+def _sph_exact(rr, rin, rout):
+    return 4 * math.pi * (np.log(rr / rout) + rin / rr - rin / rout) - 4 * math.pi * (rout - rin) / rout
+
+
+def test_spherical_radial_closed_form_second_order():
+    """rho = r^-2 on r_in < r < r_out with Neumann at r_in: Gauss's law gives
+    Phi = 4 pi [ln(r/r_out) + r_in/r - r_in/r_out] - 4 pi (r_out - r_in)/r_out."""
+    errs = []
+    for nr in (32, 64, 128):
+        r, th, ph = W.spherical_coords(nr, 4, 8, 0.01, 1.0)
+        rho = W.spherical_density(r, th, ph, with_angles=False)
+        op = SP.SphericalOperator(r, th, ph)
+        phi = np.zeros(op.shape)
+        phi[:, :, -1] = -4 * math.pi * (r[-1] - r[0]) / MP.radial_extended(r)[-1]
+        res = SP.bicgstab_solve(phi, 4 * math.pi * rho, op, 1e-12, 5000)
+        assert res.converged
+        ex = _sph_exact(r, r[0], r[-1])
+        errs.append(np.max(np.abs(phi[1:-1, 1:-1, 1:-1] - ex[None, None, :])) / np.max(np.abs(ex)))
+    assert 3.5 < errs[0] / errs[1] < 4.6 and 3.5 < errs[1] / errs[2] < 4.6, errs
+
+
+def test_spherical_operator_annihilates_harmonics():
+    """x^2 - y^2 and 2z^2 - x^2 - y^2 are harmonic: the truncation error of the
+    discrete operator on them falls as h^2."""
+    vals = []
+    for n in (16, 32, 64):
+        r, th, ph = W.spherical_coords(n, n, 2 * n, 0.5, 1.5)
+        op = SP.SphericalOperator(r, th, ph)
+        re = MP.radial_extended(r)
+        P = np.zeros(op.shape)
+        R, T, F = re[None, None, :], th[None, :, None], ph[:, None, None]
+        P[1:-1, 1:-1, :] = (R * np.sin(T)) ** 2 * np.cos(2 * F) + R ** 2 * (3 * np.cos(T) ** 2 - 1)
+        vals.append(np.max(np.abs(op.apply(P)[:, :, 1:])))
+    assert 3.5 < vals[0] / vals[1] < 4.5 and 3.5 < vals[1] / vals[2] < 4.5, vals
+
+
+def test_bicgstab_matches_dense_solve():
+    r, th, ph = W.spherical_coords(6, 6, 8, 0.1, 1.0)
+    op = SP.SphericalOperator(r, th, ph)
+    nunk = 6 * 6 * 8
+    A = np.zeros((nunk, nunk))
+    for c in range(nunk):
+        e = np.zeros(op.shape)
+        e[1:-1, 1:-1, 1:-1].flat[c] = 1.0
+        A[:, c] = op.apply(e).ravel()
+    assert np.max(np.abs(A - A.T)) > 1e-3          # not symmetric (hence BiCGSTAB)
+    rho = W.spherical_density(r, th, ph)
+    phi = np.zeros(op.shape)
+    phi[:, :, -1] = -1.0
+    f = 4 * math.pi * rho
+    bd = np.zeros(op.shape)
+    bd[:, :, -1] = -1.0
+    b = f[1:-1, 1:-1, 1:-1].ravel() - op.apply(bd).ravel()
+    x = np.linalg.solve(A, b)
+    res = SP.bicgstab_solve(phi, f, op, 1e-13, 2000)
+    assert res.converged
+    np.testing.assert_allclose(phi[1:-1, 1:-1, 1:-1].ravel(), x, rtol=1e-10)
+
+
+def test_spherical_multipole_monopole_is_mass():
+    """rho = r^-2: q_00 = sum_i dr_i * 2 pi sum_j sin(theta_j) dtheta exactly, and
+    the midpoint spacings telescope to (r_{N-1} + r_N - r_0 - r_{-1}) / 2; the
+    angular midpoint sum tends to 4 pi.  Higher moments vanish by symmetry."""
+    r, th, ph = W.spherical_coords(64, 16, 32, 0.01, 1.0)
+    rho = W.spherical_density(r, th, ph, with_angles=False)
+    q = MP.moments_spherical(rho, r, th, ph, 2)
+    re = MP.radial_extended(r)
+    radial = 0.5 * (re[-1] + re[-2] - re[1] - re[0])
+    angular = 2 * math.pi * np.sum(np.sin(th)) * math.pi / th.size
+    assert abs(q[0] - radial * angular) < 1e-13 * q[0]
+    assert abs(angular - 4 * math.pi) < 4 * math.pi * (math.pi / 16) ** 2 / 8
+    others = [q[MP.idx(l, m)] for l in (1, 2) for m in range(-l, l + 1) if (l, m) != (2, 0)]
+    assert np.max(np.abs(others)) < 1e-12 * q[0]
+    # q_20 is the midpoint-rule error of int P_2(cos t) sin t dt = 0: O(dtheta^2)
+    r2, th2, ph2 = W.spherical_coords(64, 32, 32, 0.01, 1.0)
+    q2 = MP.moments_spherical(W.spherical_density(r2, th2, ph2, with_angles=False), r2, th2, ph2, 2)
+    assert 3.8 < q[MP.idx(2, 0)] / q2[MP.idx(2, 0)] < 4.2
+
+
+# ------------------------------------------------------------------ inputs
+
+def test_lognormal_generator_statistics():
+    rho = W.lognormal_field(32, order=4, seed=3)
+    core = rho[1:-2, 1:-2, 1:-2]                 # the periodic 32^3 block
+    assert abs(np.std(np.log(core)) - 1.0) < 1e-12
+    assert abs(np.mean(np.log(core)) + 0.5) < 1e-12
+    np.testing.assert_array_equal(rho[1], rho[-2])   # node N repeats node 0

@@ -1,0 +1,259 @@
+"""Seeded synthetic inputs for the Poisson solvers.
+
+This module only produces input data: node coordinates, densities, boundary
+potentials of textbook closed forms and request streams.  It holds none of the
+solver arithmetic, so both the CUDA path and the FP64 CPU oracle may use it.
+
+Conventions (shared by every consumer):
+
+* Cartesian "N^3" means N intervals per axis on [lo, hi]^3, nodes 0..N,
+  (N-1)^3 interior unknowns (vertex-centred grids, Sec. 2.1.3).  A field is a
+  C-ordered array of shape (nz+2g-1, ny+2g-1, nx+2g-1), x fastest, where g is
+  the stencil radius (1 for the 7-point, 2 for the 13-point Laplacian); node
+  index i sits at array index i+g-1.
+* Spherical grids (Eq. 2) store (Nphi+2, Ntheta+2, Nr+2) with r fastest; node
+  (i, j, k) sits at array index (k+1, j+1, i+1); the ghost layers hold the
+  inner mirror, the pole slots, the periodic copies and the outer boundary.
+* Random numbers come from numpy's PCG64 with fixed seeds.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "cart_shape", "cart_coords", "uniform_sphere", "gaussian_blobs",
+    "gaussian_blob_params", "lognormal_field", "manufactured_sine",
+    "smooth_sphere_density", "spherical_coords", "spherical_density",
+    "ServingRequest", "serving_stream", "rng",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def cart_shape(n, order: int):
+    """Array shape (z, y, x) of a Cartesian field with n=(nx,ny,nz) intervals."""
+    g = order // 2
+    nx, ny, nz = (n, n, n) if np.isscalar(n) else n
+    return (nz + 2 * g - 1, ny + 2 * g - 1, nx + 2 * g - 1)
+
+
+def cart_coords(n, order: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Node coordinates (x, y, z) as 1-D arrays covering the whole array,
+    ghost layers included."""
+    g = order // 2
+    nn = (n, n, n) if np.isscalar(n) else tuple(n)
+    out = []
+    for a in range(3):
+        h = (hi[a] - lo[a]) / nn[a]
+        idx = np.arange(-(g - 1), nn[a] + g, dtype=np.float64)
+        out.append(lo[a] + idx * h)
+    return tuple(out)
+
+
+def _mesh(n, order, lo, hi):
+    x, y, z = cart_coords(n, order, lo, hi)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def uniform_sphere(n: int, order: int = 2, radius: float = 0.25, rho0: float = 1.0,
+                   G: float = 1.0, centre=(0.5, 0.5, 0.5)):
+    """Uniform sphere of density rho0 in the unit box.
+
+    Returns (rho, phi0, phi_exact): phi0 is zero on interior nodes and carries
+    the closed-form potential on the boundary (and ghost) nodes, so it serves
+    both as a cold-start guess and as Dirichlet data.  The closed form is the
+    textbook potential of a uniform ball: 2 pi G rho0 (r^2/3 - a^2) inside,
+    -G M / r outside, M = 4 pi rho0 a^3 / 3.
+    """
+    X, Y, Z = _mesh(n, order, (0, 0, 0), (1, 1, 1))
+    r = np.sqrt((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2)
+    rho = np.where(r < radius, rho0, 0.0)
+    mass = 4.0 * math.pi * rho0 * radius ** 3 / 3.0
+    with np.errstate(divide="ignore"):
+        outside = -G * mass / np.maximum(r, 1e-300)
+    phi_exact = np.where(r < radius, 2.0 * math.pi * G * rho0 * (r * r / 3.0 - radius ** 2), outside)
+    phi0 = phi_exact.copy()
+    g = order // 2
+    phi0[g:-g, g:-g, g:-g] = 0.0
+    return rho, phi0, phi_exact
+
+
+@dataclass
+class Blob:
+    centre: tuple
+    sigma: float
+    amp: float
+
+
+def gaussian_blob_params(seed: int, nblobs: int = 8):
+    """Blob parameters drawn per blob in the order centre (3), sigma, amplitude:
+    centres U[0.2,0.8]^3, sigma U[0.02,0.08], amplitude U[0.5,2]."""
+    g = rng(seed)
+    blobs = []
+    for _ in range(nblobs):
+        c = tuple(g.uniform(0.2, 0.8, size=3))
+        s = float(g.uniform(0.02, 0.08))
+        a = float(g.uniform(0.5, 2.0))
+        blobs.append(Blob(c, s, a))
+    return blobs
+
+
+def gaussian_blobs(n: int, order: int = 2, seed: int = 2, nblobs: int = 8, blobs=None,
+                   shift=(0.0, 0.0, 0.0)):
+    """Sum of isotropic Gaussians A exp(-|x-c|^2/(2 sigma^2)) sampled on the
+    nodes of the unit box; `shift` translates every centre."""
+    if blobs is None:
+        blobs = gaussian_blob_params(seed, nblobs)
+    x, y, z = cart_coords(n, order)
+    rho = np.zeros((z.size, y.size, x.size))
+    for b in blobs:
+        cx, cy, cz = (b.centre[a] + shift[a] for a in range(3))
+        w = -0.5 / (b.sigma * b.sigma)
+        ex = np.exp(w * (x - cx) ** 2)
+        ey = np.exp(w * (y - cy) ** 2)
+        ez = np.exp(w * (z - cz) ** 2)
+        rho += b.amp * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    return rho
+
+
+def lognormal_field(n: int, order: int = 4, seed: int = 3, slope: float = -11.0 / 3.0):
+    """Lognormal turbulent-like density: a Gaussian random field g with 3-D
+    power spectrum P(k) ~ |k|^slope (k=0 zeroed) on the periodic N^3 lattice,
+    standardised to unit variance, then rho = exp(g - 1/2) so that
+    sigma(ln rho) = 1 and <rho> ~ 1.  Node N repeats node 0."""
+    g = rng(seed)
+    white = g.standard_normal((n, n, n))
+    wk = np.fft.rfftn(white)
+    kz = np.fft.fftfreq(n)[:, None, None]
+    ky = np.fft.fftfreq(n)[None, :, None]
+    kx = np.fft.rfftfreq(n)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    amp = k2 ** (slope / 4.0)          # sqrt(P(k)) with P ~ k^slope
+    amp[0, 0, 0] = 0.0
+    field_ = np.fft.irfftn(wk * amp, s=(n, n, n))
+    field_ -= field_.mean()
+    field_ /= field_.std()
+    rho_p = np.exp(field_ - 0.5)
+    gh = order // 2
+    idx = (np.arange(-(gh - 1), n + gh) % n)
+    return rho_p[np.ix_(idx, idx, idx)]
+
+
+def manufactured_sine(n: int, order: int, G: float = 1.0):
+    """Phi = sin(pi x) sin(pi y) sin(pi z) on [0,1]^3 with its density
+    rho = -3 pi^2 Phi / (4 pi G).  Returns (rho, phi0, phi_exact); phi0 has the
+    exact values on boundary and ghost nodes and zero inside."""
+    X, Y, Z = _mesh(n, order, (0, 0, 0), (1, 1, 1))
+    phi = np.sin(math.pi * X) * np.sin(math.pi * Y) * np.sin(math.pi * Z)
+    rho = -3.0 * math.pi ** 2 * phi / (4.0 * math.pi * G)
+    phi0 = phi.copy()
+    g = order // 2
+    phi0[g:-g, g:-g, g:-g] = 0.0
+    return rho, phi0, phi
+
+
+def smooth_sphere_density(n, order, centres, radii, masses, lo=(-1, -1, -1), hi=(1, 1, 1)):
+    """The (1-w^2)^2 spheres of Sec. 3.1: rho_p (1 - (d/a_p)^2)^2 inside d < a_p,
+    rho_p = M_p / (32 pi a_p^3 / 105)."""
+    X, Y, Z = _mesh(n, order, lo, hi)
+    rho = np.zeros_like(X)
+    for c, a, m in zip(centres, radii, masses):
+        rp = m / (32.0 * math.pi * a ** 3 / 105.0)
+        d = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
+        w2 = (d / a) ** 2
+        rho += np.where(d < a, rp * (1.0 - w2) ** 2, 0.0)
+    return rho
+
+
+def spherical_coords(nr: int = 256, nth: int = 128, nph: int = 256, r_in: float = 0.01,
+                     r_out: float = 1.0):
+    """Node coordinates of the spherical grid: r log-spaced from r_in to r_out
+    (nr nodes), theta_j = (j+1/2) pi / nth, phi_k = 2 pi k / nph."""
+    i = np.arange(nr, dtype=np.float64)
+    r = r_in * (r_out / r_in) ** (i / (nr - 1))
+    r[0], r[-1] = r_in, r_out
+    th = (np.arange(nth) + 0.5) * math.pi / nth
+    ph = 2.0 * math.pi * np.arange(nph) / nph
+    return r, th, ph
+
+
+def spherical_density(r, th, ph, with_angles: bool = True):
+    """rho = r^-2 (1 + 0.1 cos 2 phi)(1 + 0.2 cos^2 theta) on the node grid,
+    returned in the (Nphi+2, Ntheta+2, Nr+2) ghosted layout (ghosts zero)."""
+    rho = np.zeros((ph.size + 2, th.size + 2, r.size + 2))
+    fr = r ** -2.0
+    if with_angles:
+        fth = 1.0 + 0.2 * np.cos(th) ** 2
+        fph = 1.0 + 0.1 * np.cos(2.0 * ph)
+    else:
+        fth = np.ones_like(th)
+        fph = np.ones_like(ph)
+    rho[1:-1, 1:-1, 1:-1] = fph[:, None, None] * fth[None, :, None] * fr[None, None, :]
+    return rho
+
+
+@dataclass
+class ServingRequest:
+    rid: int
+    arrival_s: float
+    n: int
+    tol: float
+    blobs: list
+    seq_id: int = -1          # >= 0: member of a warm-started sequence
+    seq_step: int = 0
+    shift: tuple = field(default=(0.0, 0.0, 0.0))
+
+
+def serving_stream(n_requests: int = 2000, rate_hz: float = 200.0, seed: int = 5,
+                   sizes=(32, 64, 96, 128, 192, 256), seq_fraction: float = 0.3,
+                   seq_len: int = 10, step_shift: float = 0.01):
+    """Request stream: Poisson arrivals (exponential gaps of mean 1/rate),
+    cube sizes uniform over `sizes`, 1-16 Gaussian blobs, tolerance 1e-6 or
+    1e-10 with probability 1/2.  A fraction `seq_fraction` of the requests
+    belongs to sequences of `seq_len` steps whose blobs translate by
+    `step_shift` per step along a fixed seeded direction."""
+    g = rng(seed)
+    gaps = g.exponential(1.0 / rate_hz, size=n_requests)
+    t = np.cumsum(gaps)
+    n_seq_req = int(round(seq_fraction * n_requests)) // seq_len * seq_len
+    n_seq = n_seq_req // seq_len
+    # sequence members are interleaved through the stream at seeded slots
+    slots = np.sort(g.choice(n_requests, size=n_seq_req, replace=False))
+    seq_of_slot = np.repeat(np.arange(n_seq), seq_len)
+    g.shuffle(seq_of_slot)
+    seq_params = []
+    for s in range(n_seq):
+        nsz = int(g.choice(sizes))
+        nb = int(g.integers(1, 17))
+        blobs = [Blob(tuple(g.uniform(0.3, 0.7, size=3)), float(g.uniform(0.02, 0.08)),
+                      float(g.uniform(0.5, 2.0))) for _ in range(nb)]
+        d = g.standard_normal(3)
+        d /= np.linalg.norm(d)
+        tol = 1e-6 if g.uniform() < 0.5 else 1e-10
+        seq_params.append((nsz, blobs, tuple(d), tol))
+    slot_to_seq = dict(zip(slots.tolist(), seq_of_slot.tolist()))
+    step_count = [0] * n_seq
+    out = []
+    for rid in range(n_requests):
+        if rid in slot_to_seq:
+            s = slot_to_seq[rid]
+            nsz, blobs, d, tol = seq_params[s]
+            k = step_count[s]
+            step_count[s] += 1
+            shift = tuple(step_shift * k * d[a] for a in range(3))
+            out.append(ServingRequest(rid, float(t[rid]), nsz, tol, blobs, s, k, shift))
+        else:
+            nsz = int(g.choice(sizes))
+            nb = int(g.integers(1, 17))
+            blobs = [Blob(tuple(g.uniform(0.2, 0.8, size=3)), float(g.uniform(0.02, 0.08)),
+                          float(g.uniform(0.5, 2.0))) for _ in range(nb)]
+            tol = 1e-6 if g.uniform() < 0.5 else 1e-10
+            out.append(ServingRequest(rid, float(t[rid]), nsz, tol, blobs))
+    return out
