@@ -1,0 +1,213 @@
+/*
+ * poisson.h -- C ABI of the GB300 (sm_103a) library for matrix-free iterative
+ * solution of the Poisson equation for the gravitational potential,
+ *
+ *     laplacian(Phi) = 4 pi G rho                      (Eq. 1 Cartesian, Eq. 2 spherical)
+ *
+ * after "Iterative Poisson Solvers for Self-gravity with the GPU Code Astaroth"
+ * (arXiv 2605.03563).  Solvers: multicolour SOR / Gauss-Seidel (Sec. 2.1.1),
+ * CG and Jacobi-preconditioned BiCGSTAB (Sec. 2.1.2), geometric multigrid
+ * V-cycles (Sec. 2.1.3); open boundary by multipole expansion (Sec. 2.2,
+ * Eqs. outer_expansion and outer_multipole).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers named *_dev are device pointers (cudaMalloc or torch tensors on the
+ * current device); pointers named *_host are host pointers.  The caller owns
+ * every buffer it passes; the library owns what a handle allocates and frees
+ * it in poisson_destroy.  `stream` is a cudaStream_t (NULL = the handle's own
+ * stream for solves, the legacy default stream for the op-level calls).
+ *
+ * Cartesian fields: contiguous, x fastest, extents (n[a] + 2g - 1) per axis,
+ * where g = stencil_order / 2 is the stencil radius; node i of axis a (node 0
+ * and node n[a] are the boundary, 1..n[a]-1 the unknowns) sits at array index
+ * i + g - 1.  The non-interior layers of phi carry Dirichlet data (given, or
+ * written by the multipole boundary).  "N^3" means N intervals per axis.
+ *
+ * Spherical fields: extents (Nr+2, Ntheta+2, Nphi+2) with r fastest; node
+ * (i,j,k) sits at array index (i+1, j+1, k+1); array index 0 / Nr+1 along r
+ * are the inner mirror ghost and the outer Dirichlet ghost.
+ *
+ * Errors: every call returns a ps_status; nothing is thrown and nothing
+ * aborts.  poisson_last_error() returns a thread-local message describing the
+ * last failure.  Argument errors are detected before any GPU work.
+ */
+#ifndef POISSON_GB300_H
+#define POISSON_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PS_OK = 0,
+  PS_ERR_INVALID_ARG = 1,   /* bad shape, order, method, l_max, pointer ... */
+  PS_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  PS_ERR_OOM = 3,           /* device allocation failed */
+  PS_ERR_CUDA = 4,          /* a CUDA runtime call failed (message has the text) */
+  PS_NOT_CONVERGED = 5,     /* max_iter reached; phi and info are valid (Sec. 2.1) */
+  PS_DIVERGED = 6,          /* residual became NaN/Inf or grew 1e3-fold */
+  PS_ERR_TIMEOUT = 7        /* a bounded device wait ran out */
+} ps_status;
+
+typedef enum { PS_GRID_CART_UNIFORM = 0, PS_GRID_SPHERICAL = 1 } ps_grid_kind;
+
+/* Cartesian: n = intervals per axis, lo/hi = box corners (uniform spacing
+ * h[a] = (hi[a]-lo[a])/n[a]).  Spherical: n = node counts (Nr, Ntheta, Nphi);
+ * lo/hi are ignored (the coordinates come from poisson_create's coords). */
+typedef struct {
+  int32_t kind;
+  int32_t n[3];
+  double lo[3];
+  double hi[3];
+} ps_grid;
+
+typedef enum { PS_BC_DIRICHLET_GIVEN = 0, PS_BC_MULTIPOLE = 1 } ps_outer_bc;
+typedef enum { PS_INNER_NONE = 0, PS_INNER_NEUMANN = 1 } ps_inner_bc;
+
+/* origin: expansion centre of the multipole boundary (Cartesian; Sec. 2.2
+ * recommends keeping it near the centre of mass); the spherical grid always
+ * expands about r = 0.  G: gravitational constant of Eq. 1. */
+typedef struct {
+  int32_t outer;
+  int32_t inner;
+  double origin[3];
+  double G;
+} ps_bc;
+
+typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3 } ps_method;
+
+/* PS_FP64: every kernel computes and stores in FP64.
+ * PS_MIXED_FP32: FP64 iterative refinement (outer residual, correction, norms,
+ *   multipole moments and coarsest solve in FP64) around FP32 inner solves.
+ * PS_MIXED_BF16: as PS_MIXED_FP32, with the finest inner level stored in BF16. */
+typedef enum { PS_FP64 = 0, PS_MIXED_FP32 = 1, PS_MIXED_BF16 = 2 } ps_precision;
+
+typedef struct {
+  int32_t method;        /* ps_method */
+  int32_t prec;          /* ps_precision */
+  double omega;          /* SOR weight (Sec. 2.1.1); MG smoothing uses 1 */
+  int32_t nu1, nu2;      /* V(nu1,nu2) pre-/post-smoothing sweeps */
+  int32_t max_iter;      /* SOR steps / CG or BiCGSTAB iterations / V-cycles / IR steps */
+  int32_t inner_cycles;  /* mixed modes: V-cycles (or Krylov iterations) per IR step */
+  void* stream;          /* cudaStream_t or NULL */
+} ps_solve_opts;
+
+typedef struct {
+  int32_t iterations;        /* steps taken (V-cycles, Krylov iterations, SOR steps, IR steps) */
+  int32_t status;            /* ps_status of the solve */
+  double rel_residual;       /* ||f - A phi||_2 / ||f - A phi0||_2, phi0 = boundary data only */
+  double rho_conv;           /* Eq. rho: (||r_m|| / ||r_0||)^(1/m) */
+  double t_mp_ms;            /* multipole boundary time (moments + faces) */
+  double t_iter_ms;          /* iteration time */
+  int64_t inner_cycles;      /* mixed modes: total inner V-cycles / Krylov iterations */
+  int64_t coarse_iterations; /* MG: total CG iterations on the coarsest level */
+  double moments[81];        /* first min((l_max+1)^2, 81) multipole moments q_lm, index l*l+l+m */
+} ps_info;
+
+typedef struct ps_ctx* ps_handle;
+
+/* ------------------------------------------------------------------ solves */
+
+/* Build a solver for one grid.  Validates everything, builds the multigrid
+ * level list (halving while every axis has an even interval count >= 16,
+ * Sec. 2.1.3), allocates the device hierarchy and workspace, uploads the
+ * 1-D coordinate tables and the multipole coefficient tables.
+ *   grid           Cartesian or spherical description (see ps_grid)
+ *   coords_host    NULL for Cartesian; spherical: three host arrays r[Nr],
+ *                  theta[Ntheta], phi[Nphi] of node coordinates (r increasing,
+ *                  theta_j = (j+1/2) pi / Ntheta, phi_k = 2 pi k / Nphi)
+ *   stencil_order  2 (7-point) or 4 (13-point, Cartesian only)
+ *   bc             boundary description (NULL = Dirichlet data given, G = 1)
+ *   l_max          multipole order, 0..16 (ignored for given Dirichlet data)
+ *   out            receives the handle
+ * Returns PS_ERR_INVALID_ARG before allocating if anything is inconsistent. */
+ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3],
+                         int stencil_order, const ps_bc* bc, int l_max, ps_handle* out);
+
+/* Solve laplacian(phi) = 4 pi G rho to ||f - A phi|| <= tol * ||f - A phi0||.
+ *   rho_dev   density on the field layout (FP64, read only)
+ *   phi_dev   FP64 field: in = initial guess (unknowns) + Dirichlet data
+ *             (boundary/ghost layers), out = solution (and, with the
+ *             multipole boundary, the boundary values it used)
+ *   opts      method, precision, smoothing, limits and stream (NULL = MG,
+ *             FP64, V(2,2), max_iter 100)
+ *   info      filled after an internal stream synchronisation (may be NULL)
+ * Runs asynchronously on the stream except for the final synchronisation.
+ * Returns PS_NOT_CONVERGED / PS_DIVERGED with phi holding the last iterate. */
+ps_status poisson_solve(ps_handle h, const double* rho_dev, double* phi_dev, double tol,
+                        const ps_solve_opts* opts, ps_info* info);
+
+/* Solve n independent requests, each with its own handle, density, potential
+ * and tolerance, on one stream.  Results equal n separate poisson_solve calls
+ * bit for bit; infos[i] receives request i's info.  Handles must be distinct. */
+ps_status poisson_solve_batch(ps_handle* hs, const double* const* rho_dev, double* const* phi_dev,
+                              const double* tol, int n, const ps_solve_opts* opts,
+                              ps_info* infos);
+
+/* Release the handle and everything it allocated (NULL is a no-op). */
+void poisson_destroy(ps_handle h);
+
+/* Thread-local text of the last error (never NULL; "" when none). */
+const char* poisson_last_error(void);
+
+/* Device bytes poisson_create + poisson_solve would allocate for this grid and
+ * precision (used for admission control); 0 for invalid arguments. */
+size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max, int prec);
+
+/* ------------------------------------------------------------------ op-level calls
+ * Single kernels of the hot path on caller-owned buffers, for validation and
+ * benchmarking.  dtype: 0 = FP64, 1 = FP32, 2 = BF16 storage (arithmetic in
+ * FP64 for FP64 storage, FP32 otherwise).  Cartesian fields follow the layout
+ * above.  Each call is asynchronous on `stream` unless it returns a host value. */
+
+/* out = A phi on interior nodes (7-point or 13-point Laplacian, Eq. 1 with
+ * the stencils of Sec. 2.1); non-interior entries of out are left untouched. */
+ps_status ps_op_apply(const ps_grid* grid, int stencil_order, int dtype, const void* phi_dev,
+                      void* out_dev, void* stream);
+
+/* r = f - A phi on interior nodes and ||r||_2^2 (FP64, deterministic) into
+ * *norm2_host (synchronises; pass NULL to skip). */
+ps_status ps_op_residual(const ps_grid* grid, int stencil_order, int dtype, const void* phi_dev,
+                         const void* f_dev, void* r_dev, double* norm2_host, void* stream);
+
+/* One multicolour SOR step in place (Sec. 2.1.1): colours (i+j+k) mod 2 for
+ * order 2, mod 3 for order 4, ascending; phi += omega (phi_GS - phi). */
+ps_status ps_op_sweep(const ps_grid* grid, int stencil_order, int dtype, void* phi_dev,
+                      const void* f_dev, double omega, void* stream);
+
+/* Full-weighting restriction (Sec. 2.1.3) of the interior of r_fine_dev onto
+ * the interior of f_coarse_dev (grid = the fine grid; coarse = n/2). */
+ps_status ps_op_restrict(const ps_grid* fine_grid, int stencil_order, int dtype,
+                         const void* r_fine_dev, void* f_coarse_dev, void* stream);
+
+/* phi_fine += P e_coarse with P = 8 R^T (trilinear, Sec. 2.1.3); coarse
+ * boundary values are treated as zero (grid = the fine grid). */
+ps_status ps_op_prolong(const ps_grid* fine_grid, int stencil_order, int dtype,
+                        const void* e_coarse_dev, void* phi_fine_dev, void* stream);
+
+/* Multipole moments q_lm (Eq. outer_multipole) of rho over the interior nodes
+ * about `origin`, (l_max+1)^2 doubles into q_host (synchronises). */
+ps_status ps_op_multipole_moments(const ps_grid* grid, int stencil_order, const double* rho_dev,
+                                  const double origin[3], int l_max, double* q_host,
+                                  void* stream);
+
+/* Eq. outer_expansion written on every non-interior node of phi_dev. */
+ps_status ps_op_multipole_boundary(const ps_grid* grid, int stencil_order, const double* q_host,
+                                   const double origin[3], int l_max, double G, double* phi_dev,
+                                   void* stream);
+
+/* Spherical operator (Eq. 2 in flux form) applied to phi_dev (ghosted layout):
+ * out = L phi on every unknown node, using phi's outer ghost as given, the
+ * inner mirror ghost and periodic phi (ghost slots of phi are read, not
+ * written).  Uses the coordinates of handle h (spherical). */
+ps_status ps_op_spherical_apply(ps_handle h, const double* phi_dev, double* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POISSON_GB300_H */

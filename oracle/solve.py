@@ -76,7 +76,7 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
 
 def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
                     max_iter: int = 20000, G: float = 1.0, bc: str = "multipole",
-                    lmax: int = 6) -> SolveInfo:
+                    lmax: int = 6, exact_dots: bool = False) -> SolveInfo:
     """Right-Jacobi BiCGSTAB on the spherical grid; phi in the ghosted layout."""
     op = SphericalOperator(r, th, ph)
     f = 4.0 * math.pi * G * rho
@@ -84,6 +84,8 @@ def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
     if bc == "multipole":
         q = multipole.moments_spherical(rho, r, th, ph, lmax)
         phi[1:-1, 1:-1, -1] = multipole.spherical_outer_ghost(q, r, th, ph, lmax, G)
-    res = bicgstab_solve(phi, f, op, tol, max_iter)
+    from . import krylov
+    res = bicgstab_solve(phi, f, op, tol, max_iter,
+                         dot=krylov.exact_dot if exact_dots else krylov.numpy_dot)
     return SolveInfo(res.iterations, res.converged, res.history[-1],
                      multigrid.convergence_factor(res.history), res.history, q)

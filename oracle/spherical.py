@@ -90,7 +90,7 @@ class SphericalOperator:
 
 
 def bicgstab_solve(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator, tol: float,
-                   max_iter: int):
+                   max_iter: int, dot=krylov.numpy_dot):
     """Solve L P = f (f on the ghosted layout) with right-Jacobi BiCGSTAB.
 
     The outer ghost of Pfield is Dirichlet data; unknown nodes hold the
@@ -110,6 +110,7 @@ def bicgstab_solve(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator, tol
     if ref == 0.0:
         ref = 1.0
     inv_diag = (1.0 / op.diagonal()).ravel()
-    res = krylov.bicgstab(apply_hom, inv_diag, b, Pfield[U].ravel().copy(), tol, max_iter, ref)
+    res = krylov.bicgstab(apply_hom, inv_diag, b, Pfield[U].ravel().copy(), tol, max_iter, ref,
+                          dot=dot)
     Pfield[U] = res.x.reshape(shp)
     return res

@@ -1,0 +1,189 @@
+"""GB300-native iterative Poisson solvers for self-gravity (arXiv 2605.03563).
+
+Python face of libpoisson.so: tensors (torch, on the current CUDA device)
+are passed to the C ABI by pointer together with torch's current stream.
+Nothing here computes; every step of every solve runs in the CUDA library.
+
+    from paper_2605_03563_gb300 import CartesianSolver
+    s = CartesianSolver(256, bc="multipole", lmax=4)
+    info = s.solve(rho, phi, tol=1e-10, method="mg")
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+from . import capi
+from .capi import lib, check
+
+__all__ = ["CartesianSolver", "SphericalSolver", "SolveInfo", "ops", "capi", "workspace_bytes"]
+
+METHODS = {"sor": capi.PS_SOR, "cg": capi.PS_CG, "mg": capi.PS_MG, "bicgstab": capi.PS_BICGSTAB}
+PRECISIONS = {"fp64": capi.PS_FP64, "mixed_fp32": capi.PS_MIXED_FP32, "mixed_bf16": capi.PS_MIXED_BF16}
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iterations: int
+    rel_residual: float
+    rho_conv: float
+    t_mp_ms: float
+    t_iter_ms: float
+    inner_cycles: int
+    coarse_iterations: int
+    moments: list = field(default_factory=list)
+
+    @property
+    def converged(self) -> bool:
+        return self.status == capi.PS_OK
+
+    @staticmethod
+    def from_c(info: capi.PsInfo, nmom: int) -> "SolveInfo":
+        return SolveInfo(info.status, info.iterations, info.rel_residual, info.rho_conv,
+                         info.t_mp_ms, info.t_iter_ms, info.inner_cycles, info.coarse_iterations,
+                         list(info.moments[:nmom]))
+
+
+def _ptr(t, dtype_name="float64"):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if str(t.dtype).replace("torch.", "") != dtype_name:
+        raise ValueError(f"tensor dtype must be {dtype_name}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def workspace_bytes(n, order=2, lmax=4, prec="fp64", lo=(0, 0, 0), hi=(1, 1, 1)) -> int:
+    g = capi.make_grid(n, lo, hi)
+    return int(lib().poisson_workspace_bytes(C.byref(g), order, lmax, PRECISIONS[prec]))
+
+
+class _Handle:
+    def __init__(self):
+        self._h = C.c_void_p()
+
+    def close(self):
+        if self._h:
+            lib().poisson_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _solve(self, rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
+               stream, nmom):
+        opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
+                                int(nu2), int(max_iter), int(inner_cycles), _stream(stream))
+        info = capi.PsInfo()
+        st = lib().poisson_solve(self._h, _ptr(rho), _ptr(phi), float(tol), C.byref(opts),
+                                 C.byref(info))
+        check(st, "poisson_solve", allow=(capi.PS_OK, capi.PS_NOT_CONVERGED, capi.PS_DIVERGED))
+        return SolveInfo.from_c(info, nmom)
+
+
+class CartesianSolver(_Handle):
+    """Uniform Cartesian grid with n intervals per axis on [lo, hi]^3.
+
+    Fields are float64 tensors of shape (nz+2g-1, ny+2g-1, nx+2g-1), g = order/2.
+    bc = "dirichlet" (phi carries the boundary data) or "multipole" (Sec. 2.2)."""
+
+    def __init__(self, n, order=2, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc="dirichlet",
+                 lmax=4, origin=None, G=1.0):
+        super().__init__()
+        self.n = (n, n, n) if isinstance(n, int) else tuple(n)
+        self.order, self.lmax = order, lmax
+        if origin is None:
+            origin = tuple(0.5 * (lo[a] + hi[a]) for a in range(3))
+        grid = capi.make_grid(self.n, lo, hi)
+        b = capi.PsBC(capi.PS_BC_MULTIPOLE if bc == "multipole" else capi.PS_BC_DIRICHLET_GIVEN,
+                      capi.PS_INNER_NONE, (C.c_double * 3)(*origin), float(G))
+        self.multipole = bc == "multipole"
+        check(lib().poisson_create(C.byref(grid), None, order, C.byref(b), lmax, C.byref(self._h)),
+              "poisson_create")
+
+    @property
+    def shape(self):
+        g = self.order // 2
+        nx, ny, nz = self.n
+        return (nz + 2 * g - 1, ny + 2 * g - 1, nx + 2 * g - 1)
+
+    def solve(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
+              max_iter=100, inner_cycles=1, stream=None) -> SolveInfo:
+        nmom = (self.lmax + 1) ** 2 if self.multipole else 0
+        return self._solve(rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
+                           stream, min(nmom, 81))
+
+
+class SphericalSolver(_Handle):
+    """Spherical grid with node coordinates r (increasing), theta_j = (j+1/2) pi/Nt,
+    phi_k = 2 pi k/Np; Neumann inner boundary, multipole or given outer boundary.
+    Fields are float64 tensors of shape (Np+2, Nt+2, Nr+2) (r fastest)."""
+
+    def __init__(self, r, theta, phi, bc="multipole", lmax=6, G=1.0):
+        super().__init__()
+        import numpy as np
+        self._coords = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (r, theta, phi)]
+        self.n = tuple(a.size for a in self._coords)
+        self.lmax = lmax
+        grid = capi.make_grid(self.n, kind=capi.PS_GRID_SPHERICAL)
+        ptrs = (C.c_void_p * 3)(*[a.ctypes.data for a in self._coords])
+        b = capi.PsBC(capi.PS_BC_MULTIPOLE if bc == "multipole" else capi.PS_BC_DIRICHLET_GIVEN,
+                      capi.PS_INNER_NEUMANN, (C.c_double * 3)(0, 0, 0), float(G))
+        self.multipole = bc == "multipole"
+        check(lib().poisson_create(C.byref(grid), C.cast(ptrs, C.POINTER(C.c_void_p)), 2,
+                                   C.byref(b), lmax, C.byref(self._h)), "poisson_create")
+
+    @property
+    def shape(self):
+        nr, nt, np_ = self.n
+        return (np_ + 2, nt + 2, nr + 2)
+
+    def solve(self, rho, phi, tol=1e-10, prec="fp64", max_iter=20000, inner_cycles=0,
+              stream=None) -> SolveInfo:
+        nmom = (self.lmax + 1) ** 2 if self.multipole else 0
+        return self._solve(rho, phi, tol, "bicgstab", prec, 1.0, 0, 0, max_iter, inner_cycles,
+                           stream, min(nmom, 81))
+
+    def apply(self, phi, out, stream=None):
+        check(lib().ps_op_spherical_apply(self._h, _ptr(phi), _ptr(out), _stream(stream)),
+              "ps_op_spherical_apply")
+
+
+def solve_batch(solvers, rhos, phis, tols, method="mg", prec="fp64", nu1=2, nu2=2, max_iter=100,
+                inner_cycles=1, stream=None):
+    """poisson_solve_batch over distinct CartesianSolver handles."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
+    rp = (C.c_void_p * n)(*[_ptr(r).value for r in rhos])
+    pp = (C.c_void_p * n)(*[_ptr(p).value for p in phis])
+    tl = (C.c_double * n)(*[float(t) for t in tols])
+    opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], 1.0, nu1, nu2, max_iter,
+                            inner_cycles, _stream(stream))
+    infos = (capi.PsInfo * n)()
+    st = lib().poisson_solve_batch(hs, rp, pp, tl, n, C.byref(opts), infos)
+    check(st, "poisson_solve_batch", allow=(capi.PS_OK, capi.PS_NOT_CONVERGED, capi.PS_DIVERGED))
+    return [SolveInfo.from_c(infos[i], min(81, (s.lmax + 1) ** 2 if s.multipole else 0))
+            for i, s in enumerate(solvers)]
+
+
+from . import ops  # noqa: E402

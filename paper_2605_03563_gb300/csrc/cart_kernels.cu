@@ -1,0 +1,851 @@
+// Cartesian stencil kernels of the GB300 Poisson library.
+//
+// Operators (Eq. 1 on a vertex-centred uniform grid, Sec. 2.1):
+//   order 2: 7-point   sum_a (phi_{+1} - 2 phi + phi_{-1}) / h_a^2
+//   order 4: 13-point  sum_a (-phi_{+2} + 16 phi_{+1} - 30 phi + 16 phi_{-1} - phi_{-2}) / (12 h_a^2)
+// Every kernel works in the scaled Gauss-Seidel form: with d = -(diagonal) the
+// GS value is  phi_GS = sum_a c1_a (phi_{+-1}) + c2_a (phi_{+-2}) + fs,  fs = -f/d,
+// and delta = phi_GS - phi = -(f - A phi)/d.  This needs the fewest FP64
+// instructions per node (6 for an isotropic 7-point GS update), which matters
+// because the GB300 FP64 pipe issues ~0.6 T instructions/s while HBM delivers
+// ~6.6 TB/s: FP64 sweeps are bound by FP64 issue, FP32/BF16 sweeps by HBM.
+//
+// Launch geometry of the point kernels: 32 x 8 threads per block over (x, y)
+// and a z-chunk of ZCH nodes per thread.
+#include <cstdio>
+
+#include "cart_kernels.cuh"
+
+namespace ps {
+
+static constexpr int BX = 32, BY = 8, ZCH = 16;
+
+template <typename C>
+Coef<C> make_coef(const Dims& d, const double h[3], int order) {
+  (void)d;
+  Coef<C> cf;
+  double w0 = order == 2 ? -2.0 : -30.0 / 12.0;
+  double w1 = order == 2 ? 1.0 : 16.0 / 12.0;
+  double w2 = order == 2 ? 0.0 : -1.0 / 12.0;
+  double ih2[3], sum = 0.0;
+  for (int a = 0; a < 3; a++) { ih2[a] = 1.0 / (h[a] * h[a]); sum += ih2[a]; }
+  double dd = -w0 * sum;
+  for (int a = 0; a < 3; a++) {
+    cf.c1[a] = (C)(w1 * ih2[a] / dd);
+    cf.c2[a] = (C)(w2 * ih2[a] / dd);
+  }
+  cf.d = dd;
+  cf.inv_d = 1.0 / dd;
+  return cf;
+}
+template Coef<double> make_coef<double>(const Dims&, const double*, int);
+template Coef<float> make_coef<float>(const Dims&, const double*, int);
+
+static inline bool is_iso(const double h[3]) { return h[0] == h[1] && h[1] == h[2]; }
+
+int cart_partials_count(const Dims& d) {
+  int gx = (d.ni() + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY, gz = (d.nk() + ZCH - 1) / ZCH;
+  return gx * gy * gz;
+}
+
+static inline dim3 point_grid(const Dims& d) {
+  return dim3((d.ni() + BX - 1) / BX, (d.nj() + BY - 1) / BY, (d.nk() + ZCH - 1) / ZCH);
+}
+
+// ------------------------------------------------------------------ stencil core
+// phi_GS without the diagonal: sum of weighted neighbours plus fs.
+template <int G, bool ISO, typename T, typename C>
+__device__ __forceinline__ C gs_value(const T* __restrict__ phi, long long p, long long sy,
+                                      long long sz, const Coef<C>& cf, C fs) {
+  using S = St<T>;
+  C ax = S::ld(phi + p + 1) + S::ld(phi + p - 1);
+  C ay = S::ld(phi + p + sy) + S::ld(phi + p - sy);
+  C az = S::ld(phi + p + sz) + S::ld(phi + p - sz);
+  C v;
+  if (ISO) {
+    v = fma((ax + ay) + az, cf.c1[0], fs);
+  } else {
+    v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], fs)));
+  }
+  if (G == 2) {
+    C bx = S::ld(phi + p + 2) + S::ld(phi + p - 2);
+    C by = S::ld(phi + p + 2 * sy) + S::ld(phi + p - 2 * sy);
+    C bz = S::ld(phi + p + 2 * sz) + S::ld(phi + p - 2 * sz);
+    if (ISO) {
+      v = fma((bx + by) + bz, cf.c2[0], v);
+    } else {
+      v = fma(bx, cf.c2[0], fma(by, cf.c2[1], fma(bz, cf.c2[2], v)));
+    }
+  }
+  return v;
+}
+
+// Same with every interior neighbour read as zero (reference norm only).
+template <int G, typename T, typename C>
+__device__ C gs_value_zero_interior(const T* __restrict__ phi, const Dims& d, int i, int j, int k,
+                                    const Coef<C>& cf, C fs) {
+  using S = St<T>;
+  auto val = [&](int ii, int jj, int kk) -> C {
+    bool inside = ii >= G && ii < G + d.ni() && jj >= G && jj < G + d.nj() && kk >= G &&
+                  kk < G + d.nk();
+    return inside ? (C)0 : S::ld(phi + d.at(ii, jj, kk));
+  };
+  C v = fs;
+  for (int o = 1; o <= G; o++) {
+    C ax = val(i + o, j, k) + val(i - o, j, k);
+    C ay = val(i, j + o, k) + val(i, j - o, k);
+    C az = val(i, j, k + o) + val(i, j, k - o);
+    const C* c = o == 1 ? cf.c1 : cf.c2;
+    v += ax * c[0] + ay * c[1] + az * c[2];
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_dt(void* out, int dt, long long p, double v) {
+  if (dt == DT_F64) ((double*)out)[p] = v;
+  else if (dt == DT_F32) ((float*)out)[p] = (float)v;
+  else ((__nv_bfloat16*)out)[p] = __float2bfloat16_rn((float)v);
+}
+
+// Block reduction of {sum, max} into partials[2*block], partials[2*block+1].
+__device__ __forceinline__ void block_sum_max(double s, double m, double* partials) {
+  __shared__ double sh[64];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+  s = warp_sum(s);
+  m = warp_max(m);
+  if (lane == 0) { sh[warp] = s; sh[32 + warp] = m; }
+  __syncthreads();
+  if (warp == 0) {
+    double a = lane < nw ? sh[lane] : 0.0;
+    double b = lane < nw ? sh[32 + lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_max(b);
+    if (lane == 0) {
+      int bid = block_linear_id();
+      partials[2 * bid] = a;
+      partials[2 * bid + 1] = b;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ delta pass
+template <int G, bool ISO, typename TI>
+__global__ void __launch_bounds__(BX* BY)
+    k_delta(Dims d, Coef<typename St<TI>::C> cf, const TI* __restrict__ phi,
+            const TI* __restrict__ fs, int dout, void* __restrict__ out, double out_scale,
+            const DevState* __restrict__ st, int zero_interior, double* __restrict__ partials) {
+  using C = typename St<TI>::C;
+  using S = St<TI>;
+  const int i = blockIdx.x * BX + threadIdx.x + G;
+  const int j = blockIdx.y * BY + threadIdx.y + G;
+  const int k0 = blockIdx.z * ZCH + G;
+  const int k1 = min(k0 + ZCH, G + d.nk());
+  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  double s2 = 0.0, mx = 0.0;
+  double oscale = out_scale;
+  if (st != nullptr) oscale = st->scale_next;
+  if (i < G + d.ni() && j < G + d.nj()) {
+    for (int k = k0; k < k1; k++) {
+      const long long p = d.at(i, j, k);
+      C dl;
+      if (zero_interior) {
+        dl = gs_value_zero_interior<G>(phi, d, i, j, k, cf, S::ld(fs + p));
+      } else {
+        dl = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p)) - S::ld(phi + p);
+      }
+      double dd = (double)dl;
+      s2 = fma(dd, dd, s2);
+      mx = fmax(mx, fabs(dd));
+      if (out != nullptr) store_dt<C>(out, dout, p, dd * oscale);
+    }
+  }
+  if (partials != nullptr) block_sum_max(s2, mx, partials);
+}
+
+template <int G, bool ISO, typename TI>
+static cudaError_t delta_t(const Dims& d, const double h[3], int order, const void* phi,
+                           const void* fs, int dout, void* out, double out_scale,
+                           const DevState* st, bool zi, double* partials, cudaStream_t s) {
+  using C = typename St<TI>::C;
+  Coef<C> cf = make_coef<C>(d, h, order);
+  k_delta<G, ISO, TI><<<point_grid(d), dim3(BX, BY), 0, s>>>(
+      d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+template <typename TI>
+static cudaError_t delta_dispatch(const Dims& d, int order, const double h[3], const void* phi,
+                                  const void* fs, int dout, void* out, double out_scale,
+                                  const DevState* st, bool zi, double* partials, cudaStream_t s) {
+  bool iso = is_iso(h);
+  if (order == 2) {
+    return iso ? delta_t<1, true, TI>(d, h, order, phi, fs, dout, out, out_scale, st, zi, partials, s)
+               : delta_t<1, false, TI>(d, h, order, phi, fs, dout, out, out_scale, st, zi, partials, s);
+  }
+  return iso ? delta_t<2, true, TI>(d, h, order, phi, fs, dout, out, out_scale, st, zi, partials, s)
+             : delta_t<2, false, TI>(d, h, order, phi, fs, dout, out, out_scale, st, zi, partials, s);
+}
+
+cudaError_t launch_delta_st(const Dims& d, int order, const double h[3], int din, const void* phi,
+                            const void* fs, int dout, void* out, const DevState* st,
+                            double* partials, cudaStream_t s) {
+  if (din == DT_F64) return delta_dispatch<double>(d, order, h, phi, fs, dout, out, 1.0, st, false, partials, s);
+  if (din == DT_F32) return delta_dispatch<float>(d, order, h, phi, fs, dout, out, 1.0, st, false, partials, s);
+  return delta_dispatch<__nv_bfloat16>(d, order, h, phi, fs, dout, out, 1.0, st, false, partials, s);
+}
+
+cudaError_t launch_delta(const Dims& d, int order, const double h[3], int din, const void* phi,
+                         const void* fs, int dout, void* out, double out_scale, bool zero_interior,
+                         double* partials, LaunchCfg* cfg, cudaStream_t s) {
+  if (cfg) cfg->nblocks = cart_partials_count(d);
+  if (din == DT_F64)
+    return delta_dispatch<double>(d, order, h, phi, fs, dout, out, out_scale, nullptr, zero_interior, partials, s);
+  if (din == DT_F32)
+    return delta_dispatch<float>(d, order, h, phi, fs, dout, out, out_scale, nullptr, zero_interior, partials, s);
+  return delta_dispatch<__nv_bfloat16>(d, order, h, phi, fs, dout, out, out_scale, nullptr, zero_interior, partials, s);
+}
+
+// ------------------------------------------------------------------ sweep (one colour)
+// Nodes of colour c: (i+j+k) mod NCOL == c (global node indices).  Thread t of a
+// row handles node i = i0 + NCOL t, i0 the first interior node of the colour.
+template <int G, bool ISO, typename T, bool OM1>
+__global__ void __launch_bounds__(BX* BY)
+    k_sweep(Dims d, Coef<typename St<T>::C> cf, T* __restrict__ phi, const T* __restrict__ fs,
+            int colour, typename St<T>::C omega, const DevState* __restrict__ st) {
+  using C = typename St<T>::C;
+  using S = St<T>;
+  constexpr int NCOL = G == 1 ? 2 : 3;
+  if (st != nullptr && st->done) return;
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn = blockIdx.y * BY + threadIdx.y + 1;
+  if (jn > d.nj()) return;
+  const int kn0 = blockIdx.z * ZCH + 1;
+  const int kn1 = min(kn0 + ZCH, d.nk() + 1);
+  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  for (int kn = kn0; kn < kn1; kn++) {
+    int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;
+    int in = 1 + r0 + NCOL * t;
+    if (in > d.ni()) continue;
+    const long long p = d.at(in + G - 1, jn + G - 1, kn + G - 1);
+    C gs = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p));
+    if (OM1) {
+      S::st(phi + p, gs);
+    } else {
+      C old = S::ld(phi + p);
+      S::st(phi + p, fma(omega, gs - old, old));
+    }
+  }
+}
+
+template <int G, bool ISO, typename T>
+static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* phi, const void* fs,
+                           int colour, double omega, const DevState* st, cudaStream_t s) {
+  using C = typename St<T>::C;
+  constexpr int NCOL = G == 1 ? 2 : 3;
+  Coef<C> cf = make_coef<C>(d, h, order);
+  int per_row = (d.ni() + NCOL - 1) / NCOL;
+  dim3 grid((per_row + BX - 1) / BX, (d.nj() + BY - 1) / BY, (d.nk() + ZCH - 1) / ZCH);
+  if (omega == 1.0)
+    k_sweep<G, ISO, T, true><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st);
+  else
+    k_sweep<G, ISO, T, false><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t sweep_dispatch(const Dims& d, int order, const double h[3], void* phi,
+                                  const void* fs, int colour, double omega, const DevState* st,
+                                  cudaStream_t s) {
+  bool iso = is_iso(h);
+  if (order == 2)
+    return iso ? sweep_t<1, true, T>(d, h, order, phi, fs, colour, omega, st, s)
+               : sweep_t<1, false, T>(d, h, order, phi, fs, colour, omega, st, s);
+  return iso ? sweep_t<2, true, T>(d, h, order, phi, fs, colour, omega, st, s)
+             : sweep_t<2, false, T>(d, h, order, phi, fs, colour, omega, st, s);
+}
+
+cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int dt, void* phi,
+                                const void* fs, int colour, double omega, const DevState* st,
+                                cudaStream_t s) {
+  if (dt == DT_F64) return sweep_dispatch<double>(d, order, h, phi, fs, colour, omega, st, s);
+  if (dt == DT_F32) return sweep_dispatch<float>(d, order, h, phi, fs, colour, omega, st, s);
+  return sweep_dispatch<__nv_bfloat16>(d, order, h, phi, fs, colour, omega, st, s);
+}
+
+// ------------------------------------------------------------------ restriction
+// Full weighting (Sec. 2.1.3): coarse node I <- sum_{d in {-1,0,1}^3} w w w delta(2I+d),
+// w = (1,2,1)/4, times `factor` (4 maps a fine scaled residual to the coarse
+// scaled right-hand side because d_coarse = d_fine / 4).
+template <typename TF, typename TC>
+__global__ void __launch_bounds__(BX* BY)
+    k_restrict(Dims fd, Dims cd, const TF* __restrict__ df, TC* __restrict__ fsc, double factor) {
+  using CF = typename St<TF>::C;
+  using CC = typename St<TC>::C;
+  const int I = blockIdx.x * BX + threadIdx.x + 1;
+  const int J = blockIdx.y * BY + threadIdx.y + 1;
+  if (I > cd.ni() || J > cd.nj()) return;
+  const int K0 = blockIdx.z * ZCH + 1;
+  const int K1 = min(K0 + ZCH, cd.nk() + 1);
+  const int g = fd.g;
+  const long long sy = fd.ex, sz = (long long)fd.ex * fd.ey;
+  const CF sc = (CF)(factor / 64.0);
+  for (int K = K0; K < K1; K++) {
+    const long long c = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
+    CF plane[3];
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++) {
+      CF rows[3];
+#pragma unroll
+      for (int dy = -1; dy <= 1; dy++) {
+        const long long q = c + dz * sz + dy * sy;
+        rows[dy + 1] = (St<TF>::ld(df + q - 1) + St<TF>::ld(df + q + 1)) + (CF)2 * St<TF>::ld(df + q);
+      }
+      plane[dz + 1] = (rows[0] + rows[2]) + (CF)2 * rows[1];
+    }
+    CF acc = (plane[0] + plane[2]) + (CF)2 * plane[1];
+    St<TC>::st(fsc + cd.at(I + g - 1, J + g - 1, K + g - 1), (CC)(acc * sc));
+  }
+}
+
+template <typename TF, typename TC>
+static cudaError_t restrict_t(const Dims& fine, const void* df, void* fsc, double factor,
+                              cudaStream_t s) {
+  Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2, fine.g);
+  dim3 grid((cd.ni() + BX - 1) / BX, (cd.nj() + BY - 1) / BY, (cd.nk() + ZCH - 1) / ZCH);
+  k_restrict<TF, TC><<<grid, dim3(BX, BY), 0, s>>>(fine, cd, (const TF*)df, (TC*)fsc, factor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const Dims& fine, int dt_f, const void* delta_f, int dt_c, void* fs_c,
+                            double factor, cudaStream_t s) {
+  if (dt_c == DT_F64) {
+    if (dt_f == DT_F64) return restrict_t<double, double>(fine, delta_f, fs_c, factor, s);
+    if (dt_f == DT_F32) return restrict_t<float, double>(fine, delta_f, fs_c, factor, s);
+    return restrict_t<__nv_bfloat16, double>(fine, delta_f, fs_c, factor, s);
+  }
+  if (dt_c == DT_F32) {
+    if (dt_f == DT_F64) return restrict_t<double, float>(fine, delta_f, fs_c, factor, s);
+    if (dt_f == DT_F32) return restrict_t<float, float>(fine, delta_f, fs_c, factor, s);
+    return restrict_t<__nv_bfloat16, float>(fine, delta_f, fs_c, factor, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ prolongation
+// phi_fine += P e_coarse, P = 8 R^T: a fine node at an even index along an axis
+// takes the coincident coarse node, an odd one the mean of the two neighbours.
+template <typename TC, typename TF>
+__global__ void __launch_bounds__(BX* BY)
+    k_prolong(Dims fd, Dims cd, const TC* __restrict__ ec, TF* __restrict__ phif) {
+  using CF = typename St<TF>::C;
+  const int in = blockIdx.x * BX + threadIdx.x + 1;
+  const int jn = blockIdx.y * BY + threadIdx.y + 1;
+  if (in > fd.ni() || jn > fd.nj()) return;
+  const int kn0 = blockIdx.z * ZCH + 1;
+  const int kn1 = min(kn0 + ZCH, fd.nk() + 1);
+  const int g = fd.g;
+  const int oi = in & 1, oj = jn & 1;
+  const int I0 = in >> 1, J0 = jn >> 1;
+  for (int kn = kn0; kn < kn1; kn++) {
+    const int ok = kn & 1, K0 = kn >> 1;
+    CF s = 0;
+    for (int a = 0; a <= ok; a++)
+      for (int b = 0; b <= oj; b++) {
+        const long long row = cd.at(I0 + g - 1, J0 + b + g - 1, K0 + a + g - 1);
+        CF v = (CF)St<TC>::ld(ec + row);
+        if (oi) v += (CF)St<TC>::ld(ec + row + 1);
+        s += v;
+      }
+    const int nodd = oi + oj + ok;
+    const CF scale = nodd == 0 ? (CF)1 : nodd == 1 ? (CF)0.5 : nodd == 2 ? (CF)0.25 : (CF)0.125;
+    const long long p = fd.at(in + g - 1, jn + g - 1, kn + g - 1);
+    St<TF>::st(phif + p, fma(s, scale, St<TF>::ld(phif + p)));
+  }
+}
+
+template <typename TC, typename TF>
+static cudaError_t prolong_t(const Dims& fine, const void* ec, void* phif, cudaStream_t s) {
+  Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2, fine.g);
+  k_prolong<TC, TF><<<point_grid(fine), dim3(BX, BY), 0, s>>>(fine, cd, (const TC*)ec, (TF*)phif);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const Dims& fine, int dt_c, const void* e_c, int dt_f, void* phi_f,
+                           cudaStream_t s) {
+  if (dt_c == DT_F64) {
+    if (dt_f == DT_F64) return prolong_t<double, double>(fine, e_c, phi_f, s);
+    if (dt_f == DT_F32) return prolong_t<double, float>(fine, e_c, phi_f, s);
+    return prolong_t<double, __nv_bfloat16>(fine, e_c, phi_f, s);
+  }
+  if (dt_c == DT_F32) {
+    if (dt_f == DT_F64) return prolong_t<float, double>(fine, e_c, phi_f, s);
+    if (dt_f == DT_F32) return prolong_t<float, float>(fine, e_c, phi_f, s);
+    return prolong_t<float, __nv_bfloat16>(fine, e_c, phi_f, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ elementwise
+template <typename T>
+__global__ void __launch_bounds__(BX* BY)
+    k_scale_rhs(Dims d, double factor, const double* __restrict__ rho, T* __restrict__ fs) {
+  const int g = d.g;
+  const int i = blockIdx.x * BX + threadIdx.x + g;
+  const int j = blockIdx.y * BY + threadIdx.y + g;
+  if (i >= g + d.ni() || j >= g + d.nj()) return;
+  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  for (int k = k0; k < k1; k++) {
+    const long long p = d.at(i, j, k);
+    St<T>::st(fs + p, (typename St<T>::C)(factor * rho[p]));
+  }
+}
+
+cudaError_t launch_scale_rhs(const Dims& d, double factor, const double* rho, int dt, void* fs,
+                             cudaStream_t s) {
+  if (dt == DT_F64) k_scale_rhs<double><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, rho, (double*)fs);
+  else if (dt == DT_F32) k_scale_rhs<float><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, rho, (float*)fs);
+  else k_scale_rhs<__nv_bfloat16><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, rho, (__nv_bfloat16*)fs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY)
+    k_scale_any(Dims d, double factor, const T* __restrict__ f, T* __restrict__ fs) {
+  const int g = d.g;
+  const int i = blockIdx.x * BX + threadIdx.x + g;
+  const int j = blockIdx.y * BY + threadIdx.y + g;
+  if (i >= g + d.ni() || j >= g + d.nj()) return;
+  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  for (int k = k0; k < k1; k++) {
+    const long long p = d.at(i, j, k);
+    St<T>::st(fs + p, (typename St<T>::C)(factor * (double)St<T>::ld(f + p)));
+  }
+}
+
+cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,
+                                 cudaStream_t s) {
+  if (dt == DT_F64) k_scale_any<double><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, (const double*)f, (double*)fs);
+  else if (dt == DT_F32) k_scale_any<float><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, (const float*)f, (float*)fs);
+  else k_scale_any<__nv_bfloat16><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, (const __nv_bfloat16*)f, (__nv_bfloat16*)fs);
+  return cudaGetLastError();
+}
+
+template <typename TE>
+__global__ void __launch_bounds__(BX* BY)
+    k_correct(Dims d, const TE* __restrict__ e, double inv_scale, double* __restrict__ phi,
+              const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  double isc = inv_scale;
+  if (st != nullptr) isc = 1.0 / st->scale_cur;
+  const int g = d.g;
+  const int i = blockIdx.x * BX + threadIdx.x + g;
+  const int j = blockIdx.y * BY + threadIdx.y + g;
+  if (i >= g + d.ni() || j >= g + d.nj()) return;
+  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  for (int k = k0; k < k1; k++) {
+    const long long p = d.at(i, j, k);
+    phi[p] = fma((double)St<TE>::ld(e + p), isc, phi[p]);
+  }
+}
+
+cudaError_t launch_correct(const Dims& d, int dt_e, const void* e, double inv_scale, double* phi,
+                           const DevState* st, cudaStream_t s) {
+  if (dt_e == DT_F64) k_correct<double><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, (const double*)e, inv_scale, phi, st);
+  else if (dt_e == DT_F32) k_correct<float><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, (const float*)e, inv_scale, phi, st);
+  else k_correct<__nv_bfloat16><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, (const __nv_bfloat16*)e, inv_scale, phi, st);
+  return cudaGetLastError();
+}
+
+// out = A phi = d * (phi_GS(fs=0) - phi) * (-1) ... written directly:
+// A phi = d * (sum c phi_nb - phi)
+template <int G, bool ISO, typename T>
+__global__ void __launch_bounds__(BX* BY)
+    k_apply(Dims d, Coef<typename St<T>::C> cf, const T* __restrict__ phi, T* __restrict__ out) {
+  using C = typename St<T>::C;
+  const int i = blockIdx.x * BX + threadIdx.x + G;
+  const int j = blockIdx.y * BY + threadIdx.y + G;
+  if (i >= G + d.ni() || j >= G + d.nj()) return;
+  const int k0 = blockIdx.z * ZCH + G, k1 = min(k0 + ZCH, G + d.nk());
+  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const C dd = (C)cf.d;
+  for (int k = k0; k < k1; k++) {
+    const long long p = d.at(i, j, k);
+    C v = gs_value<G, ISO>(phi, p, sy, sz, cf, (C)0) - St<T>::ld(phi + p);
+    St<T>::st(out + p, v * dd);
+  }
+}
+
+template <typename T>
+static cudaError_t apply_dispatch(const Dims& d, int order, const double h[3], const void* phi,
+                                  void* out, cudaStream_t s) {
+  using C = typename St<T>::C;
+  Coef<C> cf = make_coef<C>(d, h, order);
+  bool iso = is_iso(h);
+  dim3 grid = point_grid(d), blk(BX, BY);
+  if (order == 2) {
+    if (iso) k_apply<1, true, T><<<grid, blk, 0, s>>>(d, cf, (const T*)phi, (T*)out);
+    else k_apply<1, false, T><<<grid, blk, 0, s>>>(d, cf, (const T*)phi, (T*)out);
+  } else {
+    if (iso) k_apply<2, true, T><<<grid, blk, 0, s>>>(d, cf, (const T*)phi, (T*)out);
+    else k_apply<2, false, T><<<grid, blk, 0, s>>>(d, cf, (const T*)phi, (T*)out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const Dims& d, int order, const double h[3], int dt, const void* phi,
+                         void* out, cudaStream_t s) {
+  if (dt == DT_F64) return apply_dispatch<double>(d, order, h, phi, out, s);
+  if (dt == DT_F32) return apply_dispatch<float>(d, order, h, phi, out, s);
+  return apply_dispatch<__nv_bfloat16>(d, order, h, phi, out, s);
+}
+
+// ------------------------------------------------------------------ coarsest-level CG
+// One CTA solves -A e = d * fs (zero boundary, e0 = 0) by CG (Sec. 2.1.3: the
+// coarsest level is solved with CG) until ||r|| <= tol ||r0|| or max_iter
+// iterations, entirely in shared memory (x, p, r, q on the full ghosted layout).
+template <int G, bool ISO, typename TF, typename TE>
+__global__ void __launch_bounds__(1024)
+    k_coarse_cg(Dims d, Coef<double> cf, const TF* __restrict__ fs, TE* __restrict__ e,
+                double tol, int max_iter, DevState* __restrict__ st) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double bc;
+  const long long n = d.size();
+  double* x = sm;
+  double* p = x + n;
+  double* r = p + n;
+  double* q = r + n;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int nint = ni * nj * nk;
+  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  for (long long u = tid; u < 4 * n; u += nthr) sm[u] = 0.0;
+  __syncthreads();
+  auto pos = [&](int u) -> long long {
+    int i = u % ni, t = u / ni;
+    int j = t % nj, k = t / nj;
+    return d.at(i + G, j + G, k + G);
+  };
+  auto bsum = [&](double v) -> double {
+    double a[1] = {v};
+    block_sum<1>(a, red);
+    if (tid == 0) bc = a[0];
+    __syncthreads();
+    double out = bc;
+    __syncthreads();
+    return out;
+  };
+  double loc = 0.0;
+  for (int u = tid; u < nint; u += nthr) {
+    long long c = pos(u);
+    double b = cf.d * (double)St<TF>::ld(fs + c);
+    r[c] = b;
+    p[c] = b;
+    loc = fma(b, b, loc);
+  }
+  double rr = bsum(loc);
+  const double ref = sqrt(rr);
+  int it = 0;
+  if (ref > 0.0) {
+    while (it < max_iter) {
+      loc = 0.0;
+      for (int u = tid; u < nint; u += nthr) {
+        long long c = pos(u);
+        double v = cf.d * (p[c] - gs_value<G, ISO>(p, c, sy, sz, cf, 0.0));
+        q[c] = v;
+        loc = fma(p[c], v, loc);
+      }
+      double pq = bsum(loc);
+      double alpha = rr / pq;
+      loc = 0.0;
+      for (int u = tid; u < nint; u += nthr) {
+        long long c = pos(u);
+        x[c] = fma(alpha, p[c], x[c]);
+        double rv = fma(-alpha, q[c], r[c]);
+        r[c] = rv;
+        loc = fma(rv, rv, loc);
+      }
+      double rrn = bsum(loc);
+      it++;
+      if (sqrt(rrn) <= tol * ref) break;
+      double beta = rrn / rr;
+      for (int u = tid; u < nint; u += nthr) {
+        long long c = pos(u);
+        p[c] = fma(beta, p[c], r[c]);
+      }
+      rr = rrn;
+      __syncthreads();
+    }
+  }
+  for (int u = tid; u < nint; u += nthr) {
+    long long c = pos(u);
+    St<TE>::st(e + c, (typename St<TE>::C)x[c]);
+  }
+  if (tid == 0 && st != nullptr) {
+    st->coarse_iter_last = it;
+    st->coarse_iter_total += it;
+  }
+}
+
+size_t coarse_cg_smem_bytes(const Dims& d) { return 4 * (size_t)d.size() * sizeof(double); }
+
+template <int G, bool ISO, typename TF, typename TE>
+static cudaError_t coarse_t(const Dims& d, const double h[3], int order, const void* fs, void* e,
+                            double tol, int max_iter, DevState* st, cudaStream_t s) {
+  Coef<double> cf = make_coef<double>(d, h, order);
+  size_t smem = coarse_cg_smem_bytes(d);
+  auto kern = k_coarse_cg<G, ISO, TF, TE>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<1, 1024, smem, s>>>(d, cf, (const TF*)fs, (TE*)e, tol, max_iter, st);
+  return cudaGetLastError();
+}
+
+template <typename TF, typename TE>
+static cudaError_t coarse_dispatch(const Dims& d, int order, const double h[3], const void* fs,
+                                   void* e, double tol, int max_iter, DevState* st, cudaStream_t s) {
+  bool iso = is_iso(h);
+  if (order == 2)
+    return iso ? coarse_t<1, true, TF, TE>(d, h, order, fs, e, tol, max_iter, st, s)
+               : coarse_t<1, false, TF, TE>(d, h, order, fs, e, tol, max_iter, st, s);
+  return iso ? coarse_t<2, true, TF, TE>(d, h, order, fs, e, tol, max_iter, st, s)
+             : coarse_t<2, false, TF, TE>(d, h, order, fs, e, tol, max_iter, st, s);
+}
+
+cudaError_t launch_coarse_cg(const Dims& d, int order, const double h[3], int dt_fs,
+                             const void* fs, int dt_e, void* e, double tol, int max_iter,
+                             DevState* st, cudaStream_t s) {
+  if (dt_fs == DT_F64 && dt_e == DT_F64) return coarse_dispatch<double, double>(d, order, h, fs, e, tol, max_iter, st, s);
+  if (dt_fs == DT_F32 && dt_e == DT_F32) return coarse_dispatch<float, float>(d, order, h, fs, e, tol, max_iter, st, s);
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ norm finisher
+__global__ void k_finish_norm(const double* __restrict__ partials, int nblocks, double dscale,
+                              int mode, DevState* __restrict__ st) {
+  __shared__ double red[64];
+  double s = 0.0, m = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    s += partials[2 * b];
+    m = fmax(m, partials[2 * b + 1]);
+  }
+  double a[1] = {s};
+  block_sum<1>(a, red);
+  // max over the block
+  m = warp_max(m);
+  __shared__ double mx[32];
+  if ((threadIdx.x & 31) == 0) mx[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x + 31) / 32; w++) m = fmax(m, mx[w]);
+  m = fmax(m, mx[0]);
+  const double S = a[0];
+  const double rr = dscale * dscale * S;
+  if (mode == 0) {
+    double ref = sqrt(rr);
+    st->ref = ref > 0.0 ? ref : 1.0;
+    st->amax = m;
+    st->scale_next = m > 0.0 ? exp2(-rint(log2(m))) : 1.0;
+    return;
+  }
+  if (st->done && mode == 2) return;
+  st->rr = rr;
+  st->amax = m;
+  const double rel = sqrt(rr) / st->ref;
+  st->rel = rel;
+  // IR: the scale of the next stored inner right-hand side (power of two)
+  st->scale_cur = st->scale_next;
+  st->scale_next = m > 0.0 ? exp2(-rint(log2(m))) : 1.0;
+  if (mode == 1) {
+    st->iter = 0;
+    st->rel0 = rel;
+    st->done = rel <= st->tol ? DONE_CONVERGED : (st->max_iter <= 0 ? DONE_MAXITER : DONE_NO);
+    if (!isfinite(rel)) st->done = DONE_DIVERGED;
+    return;
+  }
+  st->iter += 1;
+  if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
+  else if (rel <= st->tol) st->done = DONE_CONVERGED;
+  else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+}
+
+cudaError_t launch_finish_norm(const double* partials, int nblocks, double dscale, int mode,
+                               DevState* st, cudaStream_t s) {
+  k_finish_norm<<<1, 256, 0, s>>>(partials, nblocks, dscale, mode, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ CG kernels (FP64)
+// The SPD system is -A x = -(f - A b) (Sec. 2.1.2 needs A SPD): its residual
+// is r_spd = -(f - A phi) = d * delta.
+template <int G, bool ISO>
+__global__ void __launch_bounds__(BX* BY)
+    k_cg_init(Dims d, Coef<double> cf, const double* __restrict__ phi, const double* __restrict__ fs,
+              double* __restrict__ r, double* __restrict__ p, double* __restrict__ partials) {
+  const int i = blockIdx.x * BX + threadIdx.x + G;
+  const int j = blockIdx.y * BY + threadIdx.y + G;
+  const int k0 = blockIdx.z * ZCH + G, k1 = min(k0 + ZCH, G + d.nk());
+  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  double s2 = 0.0;
+  if (i < G + d.ni() && j < G + d.nj()) {
+    for (int k = k0; k < k1; k++) {
+      const long long c = d.at(i, j, k);
+      double v = cf.d * (gs_value<G, ISO>(phi, c, sy, sz, cf, fs[c]) - phi[c]);
+      r[c] = v;
+      p[c] = v;
+      s2 = fma(v, v, s2);
+    }
+  }
+  block_sum_max(s2, 0.0, partials);
+}
+
+template <int G, bool ISO>
+__global__ void __launch_bounds__(BX* BY)
+    k_cg_apply(Dims d, Coef<double> cf, const double* __restrict__ p, double* __restrict__ q,
+               double* __restrict__ partials, const DevState* __restrict__ st) {
+  if (st->done) return;
+  const int i = blockIdx.x * BX + threadIdx.x + G;
+  const int j = blockIdx.y * BY + threadIdx.y + G;
+  const int k0 = blockIdx.z * ZCH + G, k1 = min(k0 + ZCH, G + d.nk());
+  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  double s2 = 0.0;
+  if (i < G + d.ni() && j < G + d.nj()) {
+    for (int k = k0; k < k1; k++) {
+      const long long c = d.at(i, j, k);
+      double pc = p[c];
+      double v = cf.d * (pc - gs_value<G, ISO>(p, c, sy, sz, cf, 0.0));
+      q[c] = v;
+      s2 = fma(pc, v, s2);
+    }
+  }
+  block_sum_max(s2, 0.0, partials);
+}
+
+__global__ void __launch_bounds__(BX* BY)
+    k_cg_update(Dims d, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                const double* __restrict__ q, double* __restrict__ partials,
+                const DevState* __restrict__ st) {
+  if (st->done) return;
+  const int g = d.g;
+  const double alpha = st->alpha;
+  const int i = blockIdx.x * BX + threadIdx.x + g;
+  const int j = blockIdx.y * BY + threadIdx.y + g;
+  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  double s2 = 0.0;
+  if (i < g + d.ni() && j < g + d.nj()) {
+    for (int k = k0; k < k1; k++) {
+      const long long c = d.at(i, j, k);
+      // x solves -A x = ..., i.e. the potential itself: phi += alpha p
+      x[c] = fma(alpha, p[c], x[c]);
+      double rv = fma(-alpha, q[c], r[c]);
+      r[c] = rv;
+      s2 = fma(rv, rv, s2);
+    }
+  }
+  block_sum_max(s2, 0.0, partials);
+}
+
+__global__ void __launch_bounds__(BX* BY)
+    k_cg_pupdate(Dims d, const double* __restrict__ r, double* __restrict__ p,
+                 const DevState* __restrict__ st) {
+  if (st->done) return;
+  const int g = d.g;
+  const double beta = st->beta;
+  const int i = blockIdx.x * BX + threadIdx.x + g;
+  const int j = blockIdx.y * BY + threadIdx.y + g;
+  if (i >= g + d.ni() || j >= g + d.nj()) return;
+  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  for (int k = k0; k < k1; k++) {
+    const long long c = d.at(i, j, k);
+    p[c] = fma(beta, p[c], r[c]);
+  }
+}
+
+// which 0: alpha = rr / (p.q) ; which 1: convergence check, beta ; which 2: init
+__global__ void k_cg_scalar(const double* __restrict__ partials, int nblocks, int which,
+                            DevState* __restrict__ st) {
+  __shared__ double red[32];
+  if (which != 2 && st->done) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[2 * b];
+  double a[1] = {s};
+  block_sum<1>(a, red);
+  if (threadIdx.x != 0) return;
+  const double S = a[0];
+  if (which == 0) {
+    st->pq = S;
+    st->alpha = st->rho / S;
+  } else if (which == 1) {
+    st->iter += 1;
+    st->rr = S;
+    double rel = sqrt(S) / st->ref;
+    st->rel = rel;
+    st->beta = S / st->rho;
+    st->rho = S;
+    if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
+    else if (rel <= st->tol) st->done = DONE_CONVERGED;
+    else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+  } else {
+    st->rho = S;
+    st->rr = S;
+    st->iter = 0;
+    double rel = sqrt(S) / st->ref;
+    st->rel = rel;
+    st->rel0 = rel;
+    st->done = rel <= st->tol ? DONE_CONVERGED : (st->max_iter <= 0 ? DONE_MAXITER : DONE_NO);
+  }
+}
+
+cudaError_t launch_cg_init(const Dims& d, int order, const double h[3], const double* phi,
+                           const double* fs, double* r, double* p, double* partials,
+                           LaunchCfg* cfg, cudaStream_t s) {
+  Coef<double> cf = make_coef<double>(d, h, order);
+  if (cfg) cfg->nblocks = cart_partials_count(d);
+  bool iso = is_iso(h);
+  dim3 grid = point_grid(d), blk(BX, BY);
+  if (order == 2) {
+    if (iso) k_cg_init<1, true><<<grid, blk, 0, s>>>(d, cf, phi, fs, r, p, partials);
+    else k_cg_init<1, false><<<grid, blk, 0, s>>>(d, cf, phi, fs, r, p, partials);
+  } else {
+    if (iso) k_cg_init<2, true><<<grid, blk, 0, s>>>(d, cf, phi, fs, r, p, partials);
+    else k_cg_init<2, false><<<grid, blk, 0, s>>>(d, cf, phi, fs, r, p, partials);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_apply(const Dims& d, int order, const double h[3], const double* p,
+                            double* q, double* partials, const DevState* st, cudaStream_t s) {
+  Coef<double> cf = make_coef<double>(d, h, order);
+  bool iso = is_iso(h);
+  dim3 grid = point_grid(d), blk(BX, BY);
+  if (order == 2) {
+    if (iso) k_cg_apply<1, true><<<grid, blk, 0, s>>>(d, cf, p, q, partials, st);
+    else k_cg_apply<1, false><<<grid, blk, 0, s>>>(d, cf, p, q, partials, st);
+  } else {
+    if (iso) k_cg_apply<2, true><<<grid, blk, 0, s>>>(d, cf, p, q, partials, st);
+    else k_cg_apply<2, false><<<grid, blk, 0, s>>>(d, cf, p, q, partials, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(const Dims& d, double* x, double* r, const double* p, const double* q,
+                             double* partials, const DevState* st, cudaStream_t s) {
+  k_cg_update<<<point_grid(d), dim3(BX, BY), 0, s>>>(d, x, r, p, q, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pupdate(const Dims& d, const double* r, double* p, const DevState* st,
+                              cudaStream_t s) {
+  k_cg_pupdate<<<point_grid(d), dim3(BX, BY), 0, s>>>(d, r, p, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_scalar(const double* partials, int nblocks, int which, DevState* st,
+                             cudaStream_t s) {
+  k_cg_scalar<<<1, 256, 0, s>>>(partials, nblocks, which, st);
+  return cudaGetLastError();
+}
+
+}  // namespace ps

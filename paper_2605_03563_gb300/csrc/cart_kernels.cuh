@@ -1,0 +1,94 @@
+// Host-side launchers of the Cartesian stencil kernels (cart_kernels.cu).
+#pragma once
+#include "ps_common.cuh"
+
+namespace ps {
+
+enum DType { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+
+template <typename C>
+Coef<C> make_coef(const Dims& d, const double h[3], int order);
+
+// Which reduction a delta pass produces.
+enum { RED_NONE = 0, RED_SUM2 = 1, RED_SUM2_MAX = 2 };
+
+struct LaunchCfg {
+  int nblocks;   // number of reduction partials the launch writes
+};
+
+// delta = phi_GS - phi on interior nodes (scaled residual, r = -d delta).
+//   phi/fs: storage dtype `din`; out (optional): storage dtype `dout`, scaled by out_scale.
+//   zero_interior: treat interior phi as zero (reference norm).
+//   partials (optional): per block {sum delta^2, max |delta|}.
+// Returns the number of blocks (partials written) via cfg.
+cudaError_t launch_delta(const Dims& d, int order, const double h[3], int din, const void* phi,
+                         const void* fs, int dout, void* out, double out_scale, bool zero_interior,
+                         double* partials, LaunchCfg* cfg, cudaStream_t s);
+
+// As launch_delta, storing delta * st->scale_next (iterative refinement).
+cudaError_t launch_delta_st(const Dims& d, int order, const double h[3], int din, const void* phi,
+                            const void* fs, int dout, void* out, const DevState* st,
+                            double* partials, cudaStream_t s);
+
+// One colour pass of the multicolour GS/SOR sweep (skipped once st->done, if st given).
+cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int dt, void* phi,
+                                const void* fs, int colour, double omega, const DevState* st,
+                                cudaStream_t s);
+
+// fs = factor * f on interior nodes, both of storage dt
+cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,
+                                 cudaStream_t s);
+
+// fs_coarse = 4 * R(delta_fine)  (scaled coarse right-hand side)
+cudaError_t launch_restrict(const Dims& fine, int dt_f, const void* delta_f, int dt_c,
+                            void* fs_c, double factor, cudaStream_t s);
+
+// phi_fine += P e_coarse
+cudaError_t launch_prolong(const Dims& fine, int dt_c, const void* e_c, int dt_f, void* phi_f,
+                           cudaStream_t s);
+
+// fs = -(4 pi G / d) rho on interior nodes (rho FP64)
+cudaError_t launch_scale_rhs(const Dims& d, double factor, const double* rho, int dt, void* fs,
+                             cudaStream_t s);
+
+// phi64 += e * inv_scale on interior nodes
+cudaError_t launch_correct(const Dims& d, int dt_e, const void* e, double inv_scale, double* phi,
+                           const DevState* st, cudaStream_t s);
+
+// out = A phi (unscaled) on interior nodes, storage dt
+cudaError_t launch_apply(const Dims& d, int order, const double h[3], int dt, const void* phi,
+                         void* out, cudaStream_t s);
+
+// Single-CTA CG on the coarsest level: solves -A e = d * fs (zero boundary).
+cudaError_t launch_coarse_cg(const Dims& d, int order, const double h[3], int dt_fs,
+                             const void* fs, int dt_e, void* e, double tol, int max_iter,
+                             DevState* st, cudaStream_t s);
+size_t coarse_cg_smem_bytes(const Dims& d);
+
+// Sum the per-block partials of a delta pass into the state and decide
+// convergence.  mode: 0 = record reference norm, 1 = record initial residual,
+// 2 = iteration check (iter += 1), 3 = IR outer check (also sets the scale).
+cudaError_t launch_finish_norm(const double* partials, int nblocks, double dscale, int mode,
+                               DevState* st, cudaStream_t s);
+
+// ---------------------------------------------------------------- CG (FP64)
+// r = d * delta(phi)  (SPD residual), p = r, partials of r.r
+cudaError_t launch_cg_init(const Dims& d, int order, const double h[3], const double* phi,
+                           const double* fs, double* r, double* p, double* partials,
+                           LaunchCfg* cfg, cudaStream_t s);
+// q = -A p, partials of p.q
+cudaError_t launch_cg_apply(const Dims& d, int order, const double h[3], const double* p,
+                            double* q, double* partials, const DevState* st, cudaStream_t s);
+// x += alpha p; r -= alpha q; partials of r.r
+cudaError_t launch_cg_update(const Dims& d, double* x, double* r, const double* p, const double* q,
+                             double* partials, const DevState* st, cudaStream_t s);
+// p = r + beta p
+cudaError_t launch_cg_pupdate(const Dims& d, const double* r, double* p, const DevState* st,
+                              cudaStream_t s);
+// scalar steps: which = 0: alpha = rho/pq ; which = 1: convergence + beta
+cudaError_t launch_cg_scalar(const double* partials, int nblocks, int which, DevState* st,
+                             cudaStream_t s);
+
+int cart_partials_count(const Dims& d);
+
+}  // namespace ps

@@ -1,0 +1,53 @@
+// Multipole open boundary (Sec. 2.2): moments (Eq. outer_multipole) and the
+// truncated outer expansion (Eq. outer_expansion) on boundary nodes.
+#pragma once
+#include <vector>
+
+#include "ps_common.cuh"
+
+namespace ps {
+
+// Regular solid harmonics in Schmidt (Racah) normalisation,
+//   R_lm(x) = sqrt(4 pi / (2l+1)) r^l Y_lm(x),
+// so that q_lm = sum rho dV R_lm(x') and Phi(x) = -G sum q_lm R_lm(x) / r^(2l+1).
+// Host tables shared by the Cartesian and spherical kernels.
+struct MultipoleTables {
+  int lmax = -1;
+  // Cartesian: R_lm as a sparse polynomial sum_k val[k] x^a y^b z^c with
+  // mono[k] = (a*(L+1) + b)*(L+1) + c, terms of (l,m) in [off[lm], off[lm+1]).
+  std::vector<int> off, mono;
+  std::vector<double> val;
+  // recurrence constants for direct evaluation: rec_a[l*(L+1)+m] = (2l-1)/(l-m),
+  // rec_b = (l+m-1)/(l-m) for l >= m+2; nrm[l*(L+1)+m] = sqrt(2 (l-m)!/(l+m)!) (m>0), 1 (m=0);
+  // dfac[m] = (2m-1)!!
+  std::vector<double> rec_a, rec_b, nrm, dfac;
+};
+
+void build_multipole_tables(int lmax, MultipoleTables* t);
+
+struct CartMultipoleDev {
+  int lmax = -1;
+  double* rowmom = nullptr;    // [nk*nj*(L+1)]
+  double* planemom = nullptr;  // [nk*(L+1)*(L+2)/2]
+  double* q = nullptr;         // [(L+1)^2]
+  int* off = nullptr;
+  int* mono = nullptr;
+  double* val = nullptr;
+  double* consts = nullptr;    // rec_a | rec_b | nrm | dfac
+  size_t bytes = 0;
+};
+
+cudaError_t cart_multipole_alloc(const Dims& d, int lmax, const MultipoleTables& t,
+                                 CartMultipoleDev* m);
+void cart_multipole_free(CartMultipoleDev* m);
+
+// q (device) <- moments of rho over interior nodes about origin (weights h^3).
+cudaError_t launch_cart_moments(const Dims& d, const double lo[3], const double h[3],
+                                const double origin[3], const double* rho, CartMultipoleDev* m,
+                                cudaStream_t s);
+// phi <- -G sum q R / r^(2l+1) on every non-interior node.
+cudaError_t launch_cart_faces(const Dims& d, const double lo[3], const double h[3],
+                              const double origin[3], double G, const double* q,
+                              const CartMultipoleDev* m, double* phi, cudaStream_t s);
+
+}  // namespace ps

@@ -1,0 +1,148 @@
+// Common device/host helpers of the GB300 Poisson library.
+//
+// Storage types: double, float, __nv_bfloat16.  Arithmetic type: double for
+// double storage, float otherwise.  Reductions always accumulate in double and
+// are deterministic: a fixed xor-shuffle tree per warp, a fixed tree per block,
+// per-block partials summed in block order by a single-block finisher.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/poisson.h"
+
+namespace ps {
+
+// ------------------------------------------------------------ storage traits
+template <typename T> struct St;
+template <> struct St<double> {
+  using C = double;
+  static __device__ __forceinline__ double ld(const double* p) { return *p; }
+  static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <> struct St<float> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct St<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------------------ Cartesian level geometry
+// Array extents (ex,ey,ez) = n + 2g - 1 per axis, x fastest; node index i sits at
+// array index i + g - 1; interior unknowns occupy array indices [g, n + g - 2].
+struct Dims {
+  int nx, ny, nz;   // intervals
+  int g;            // stencil radius (ghost width)
+  int ex, ey, ez;   // array extents
+  __host__ __device__ long long size() const { return (long long)ex * ey * ez; }
+  __host__ __device__ long long at(int i, int j, int k) const {
+    return ((long long)k * ey + j) * ex + i;
+  }
+  __host__ __device__ int ni() const { return nx - 1; }   // interior counts
+  __host__ __device__ int nj() const { return ny - 1; }
+  __host__ __device__ int nk() const { return nz - 1; }
+};
+
+inline Dims make_dims(int nx, int ny, int nz, int g) {
+  Dims d;
+  d.nx = nx; d.ny = ny; d.nz = nz; d.g = g;
+  d.ex = nx + 2 * g - 1; d.ey = ny + 2 * g - 1; d.ez = nz + 2 * g - 1;
+  return d;
+}
+
+// Scaled stencil coefficients.  With d = -(diagonal of A) > 0 the Gauss-Seidel
+// value of a node is  phi_GS = sum_a c1[a](phi_{+1}+phi_{-1}) + c2[a](phi_{+2}+phi_{-2}) + fs
+// where fs = -f/d is the scaled right-hand side; delta = phi_GS - phi and the
+// residual is r = f - A phi = -d * delta.
+template <typename C> struct Coef {
+  C c1[3];
+  C c2[3];
+  double d;          // -(diagonal), kept in double for norms
+  double inv_d;
+};
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of NV values per thread, result valid in thread 0.
+// `sh` must hold 32 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; q++) v[q] = warp_sum(v[q]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) sh[q * 32 + warp] = v[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      double x = lane < nw ? sh[q * 32 + lane] : 0.0;
+      v[q] = warp_sum(x);
+    }
+  }
+}
+
+__device__ __forceinline__ int block_linear_id() {
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+// ------------------------------------------------------------ device solver state
+// One per solve; lives in device memory, copied to pinned host memory for
+// progress checks.  Kernels of an iteration body skip their work once done != 0.
+struct DevState {
+  double ref;         // reference norm (denominator of the relative residual)
+  double rr;          // latest squared residual norm (unscaled)
+  double rel;         // latest relative residual
+  double rel0;        // initial relative residual
+  double tol;
+  double amax;        // max |delta| of the latest residual pass
+  double scale_cur;   // IR: power-of-two scale of the inner RHS being solved
+  double scale_next;  // IR: scale the next stored inner RHS will use
+  // Krylov scalars
+  double alpha, beta, omega, rho, rho_new, pq, ts, tt, ss;
+  int iter;
+  int max_iter;
+  int done;           // 1 converged, 2 not converged (max_iter), 3 diverged
+  int coarse_iter_last;
+  int early;          // BiCGSTAB: converged at the s check of this iteration
+  long long coarse_iter_total;
+  long long inner_cycles;
+};
+
+enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
+
+}  // namespace ps
+
+#define PS_CUDA_TRY(expr)                                                     \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) {                                                  \
+      ps::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr,               \
+                    cudaGetErrorString(_e));                                  \
+      return PS_ERR_CUDA;                                                     \
+    }                                                                         \
+  } while (0)
+
+namespace ps {
+void set_error(const char* fmt, ...);
+}

@@ -1,0 +1,82 @@
+// Spherical-grid operator, BiCGSTAB kernels and multipole (Eq. 2, Sec. 2.1.2, Sec. 2.2).
+#pragma once
+#include <vector>
+
+#include "multipole.cuh"
+#include "ps_common.cuh"
+
+namespace ps {
+
+// Ghosted layout (Nr+2, Ntheta+2, Nphi+2), r fastest; node (i,j,k) at
+// ((k+1)*(nt+2) + (j+1))*(nr+2) + (i+1).
+struct SphDims {
+  int nr, nt, np;
+  __host__ __device__ long long sy() const { return nr + 2; }
+  __host__ __device__ long long sz() const { return (long long)(nr + 2) * (nt + 2); }
+  __host__ __device__ long long size() const { return sz() * (np + 2); }
+  __host__ __device__ long long at(int i, int j, int k) const {
+    return ((long long)(k + 1) * (nt + 2) + (j + 1)) * (nr + 2) + (i + 1);
+  }
+};
+
+// 1-D coefficient tables of the flux-form operator (device, FP64):
+//   rad_p[i], rad_m[i], inv_r2[i]  (Nr), th_p[j], th_m[j], ph[j] (Ntheta),
+//   inv_diag[j*Nr+i] (Nr*Ntheta).
+struct SphTables {
+  double *rad_p = nullptr, *rad_m = nullptr, *inv_r2 = nullptr;
+  double *th_p = nullptr, *th_m = nullptr, *ph = nullptr;
+  double* inv_diag = nullptr;
+  float *rad_pf = nullptr, *rad_mf = nullptr, *inv_r2f = nullptr;   // FP32 copies
+  float *th_pf = nullptr, *th_mf = nullptr, *phf = nullptr, *inv_diagf = nullptr;
+  // multipole tables
+  int lmax = -1;
+  double* cosT = nullptr;   // [(L+1) * Nphi]
+  double* sinT = nullptr;
+  double* Pn = nullptr;     // [(L+1)^2 (m>=0 packed as l*(L+1)+m) * Ntheta]
+  double* Rw = nullptr;     // [(L+1) * Nr]: r_i^(l+2) dr_i dtheta dphi
+  double* sinth = nullptr;  // [Ntheta]
+  double* Fc = nullptr;     // [(L+1) * Ntheta * Nr]
+  double* Fs = nullptr;
+  double* q = nullptr;      // [(L+1)^2]
+  double r_ghost = 0.0;     // outer ghost radius
+  size_t bytes = 0;
+};
+
+cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th, const double* ph,
+                             int lmax, SphTables* t);
+void sph_tables_free(SphTables* t);
+
+// out = L phi on unknown nodes (phi's outer ghost as given, mirror + periodic by index)
+cudaError_t launch_sph_apply(const SphDims& d, const SphTables& t, const double* phi, double* out,
+                             cudaStream_t s);
+
+// ---- BiCGSTAB (storage T = double or float; dots in FP64)
+// mode 0: ref norm of b = f - L(boundary only); mode 1: r = f - L x, rhat = p = r.
+// f = fscale * rho (FP64 rho) when rho != nullptr, else f = fin (storage T).
+cudaError_t launch_bicg_resid(const SphDims& d, const SphTables& t, int dt, int mode,
+                              const double* rho, double fscale, const void* fin, const void* x,
+                              void* r, void* rhat, void* p, void* phat, double* partials, int* nblk,
+                              cudaStream_t s);
+cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, void* x, void* r,
+                             const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
+                             void* tv, double* partials, DevState* st, cudaStream_t s);
+// scalar finisher for the reference / initial residual (mode 0/1)
+cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
+                              cudaStream_t s);
+
+// x += e / st->scale_cur (FP64 x; e FP32 or FP64) on unknown nodes
+cudaError_t launch_sph_correct(const SphDims& d, int dt_e, const void* e, double* x,
+                               const DevState* st, cudaStream_t s);
+// IR outer residual: out = (f - L x) * st->scale_next (FP32), partials {sum r^2, max |r|}
+cudaError_t launch_sph_outer_resid(const SphDims& d, const SphTables& t, const double* rho,
+                                   double fscale, const double* x, float* out, const DevState* st,
+                                   double* partials, int* nblk, cudaStream_t s);
+
+// multipole: q <- moments of rho (unknown nodes, dV = r^2 sin t dr dt dp);
+// outer ghost of phi <- expansion at r_ghost
+cudaError_t launch_sph_moments(const SphDims& d, const SphTables& t, const double* rho,
+                               cudaStream_t s);
+cudaError_t launch_sph_face(const SphDims& d, const SphTables& t, double G, double* phi,
+                            cudaStream_t s);
+
+}  // namespace ps

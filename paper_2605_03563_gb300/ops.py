@@ -1,0 +1,77 @@
+"""Op-level entry points of the C ABI (single hot-path kernels on caller buffers).
+
+dtype of the tensors selects the kernel instantiation: float64, float32 or
+bfloat16 storage.  Grids are Cartesian with n intervals per axis.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import capi
+from .capi import check, lib
+
+_DT = {"float64": capi.DT_F64, "float32": capi.DT_F32, "bfloat16": capi.DT_BF16}
+
+
+def _dt(t):
+    return _DT[str(t.dtype).replace("torch.", "")]
+
+
+def _p(t):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("contiguous CUDA tensor required")
+    return C.c_void_p(t.data_ptr())
+
+
+def _s(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def apply(n, order, phi, out, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    g = capi.make_grid(n, lo, hi)
+    check(lib().ps_op_apply(C.byref(g), order, _dt(phi), _p(phi), _p(out), _s(stream)), "ps_op_apply")
+
+
+def residual(n, order, phi, f, r, lo=(0, 0, 0), hi=(1, 1, 1), stream=None) -> float:
+    g = capi.make_grid(n, lo, hi)
+    nrm = C.c_double()
+    check(lib().ps_op_residual(C.byref(g), order, _dt(phi), _p(phi), _p(f), _p(r), C.byref(nrm),
+                               _s(stream)), "ps_op_residual")
+    return nrm.value
+
+
+def sweep(n, order, phi, f, omega=1.0, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    g = capi.make_grid(n, lo, hi)
+    check(lib().ps_op_sweep(C.byref(g), order, _dt(phi), _p(phi), _p(f), float(omega), _s(stream)),
+          "ps_op_sweep")
+
+
+def restrict(n, order, r_fine, f_coarse, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    g = capi.make_grid(n, lo, hi)
+    check(lib().ps_op_restrict(C.byref(g), order, _dt(r_fine), _p(r_fine), _p(f_coarse), _s(stream)),
+          "ps_op_restrict")
+
+
+def prolong(n, order, e_coarse, phi_fine, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    g = capi.make_grid(n, lo, hi)
+    check(lib().ps_op_prolong(C.byref(g), order, _dt(phi_fine), _p(e_coarse), _p(phi_fine), _s(stream)),
+          "ps_op_prolong")
+
+
+def multipole_moments(n, order, rho, origin, lmax, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    g = capi.make_grid(n, lo, hi)
+    q = (C.c_double * ((lmax + 1) ** 2))()
+    o = (C.c_double * 3)(*origin)
+    check(lib().ps_op_multipole_moments(C.byref(g), order, _p(rho), o, lmax, q, _s(stream)),
+          "ps_op_multipole_moments")
+    return list(q)
+
+
+def multipole_boundary(n, order, q, origin, lmax, G, phi, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    g = capi.make_grid(n, lo, hi)
+    qq = (C.c_double * len(q))(*q)
+    o = (C.c_double * 3)(*origin)
+    check(lib().ps_op_multipole_boundary(C.byref(g), order, qq, o, lmax, float(G), _p(phi), _s(stream)),
+          "ps_op_multipole_boundary")

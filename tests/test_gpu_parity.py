@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 results within 1e-10 of the oracle relative to max |phi|
+(operator-level results within 1e-12 of the operator's scale), identical
+iteration counts in FP64 mode; mixed FP32/BF16 modes within 1e-7.
+Grids are chosen so tiles are ragged: interior extents that are not multiples
+of the 32 x 8 x 16 thread tile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multipole as OM, smoothers as OSM, solve as OS, transfer as OT
+from oracle import spherical as OSP
+from oracle.grid import cart_grid
+from oracle.operators import laplacian, residual
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_03563_gb300 as P
+    P.capi.lib()
+    return P
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dtype=dtype)
+
+
+def host(t):
+    return t.to(torch.float64).cpu().numpy()
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+RAGGED = [((34, 20, 18), 2), ((34, 20, 18), 4), ((16, 16, 16), 2)]
+
+
+def _grid(n, order, box=(1.0, 1.0, 1.0)):
+    return cart_grid(n, order, (0, 0, 0), box)
+
+
+# ------------------------------------------------------------------ op level
+@pytest.mark.parametrize("n,order", RAGGED)
+@pytest.mark.parametrize("box", [(1.0, 1.0, 1.0), (1.0, 0.7, 1.3)])
+def test_apply_and_residual_fp64(pkg, n, order, box):
+    g = _grid(n, order, box)
+    gen = W.rng(1)
+    phi = gen.standard_normal(g.shape)
+    f = gen.standard_normal(g.shape)
+    scale = np.max(np.abs(phi)) * sum(4.0 / h ** 2 for h in g.h)
+    out = dev(np.zeros(g.shape))
+    pkg.ops.apply(n, order, dev(phi), out, hi=box)
+    ref = laplacian(phi, g)
+    assert np.max(np.abs(host(out)[g.interior] - ref[g.interior])) <= 1e-13 * scale
+    r = dev(np.zeros(g.shape))
+    nrm2 = pkg.ops.residual(n, order, dev(phi), dev(f), r, hi=box)
+    rref = residual(phi, f, g)
+    assert np.max(np.abs(host(r)[g.interior] - rref[g.interior])) <= 1e-13 * scale
+    assert abs(nrm2 - np.sum(rref[g.interior] ** 2)) <= 1e-12 * np.sum(rref[g.interior] ** 2)
+
+
+@pytest.mark.parametrize("n,order", RAGGED)
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 2e-6), (torch.bfloat16, 2e-2)])
+def test_apply_low_precision(pkg, n, order, dtype, tol):
+    g = _grid(n, order)
+    phi = W.rng(2).standard_normal(g.shape)
+    phi_t = dev(phi, dtype)
+    phi_r = host(phi_t)                   # the values the kernel actually sees
+    out = torch.zeros(g.shape, device="cuda:0", dtype=dtype)
+    pkg.ops.apply(n, order, phi_t, out)
+    ref = laplacian(phi_r, g)
+    scale = np.max(np.abs(phi_r)) * sum(4.0 / h ** 2 for h in g.h)
+    assert np.max(np.abs(host(out)[g.interior] - ref[g.interior])) <= tol * scale
+
+
+@pytest.mark.parametrize("n,order", RAGGED)
+@pytest.mark.parametrize("omega", [1.0, 1.8])
+def test_sweep_fp64(pkg, n, order, omega):
+    g = _grid(n, order)
+    gen = W.rng(3)
+    phi = gen.standard_normal(g.shape)
+    f = gen.standard_normal(g.shape) * 100
+    a = dev(phi)
+    pkg.ops.sweep(n, order, a, dev(f), omega)
+    b = phi.copy()
+    OSM.sweep(b, f, g, omega)
+    assert rel_err(host(a), b) <= 1e-13
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-5), (torch.bfloat16, 3e-2)])
+def test_sweep_low_precision(pkg, dtype, tol):
+    n, order = (34, 20, 18), 2
+    g = _grid(n, order)
+    gen = W.rng(4)
+    phi_t = dev(gen.standard_normal(g.shape), dtype)
+    f_t = dev(gen.standard_normal(g.shape), dtype)
+    phi_r, f_r = host(phi_t), host(f_t)
+    pkg.ops.sweep(n, order, phi_t, f_t, 1.0)
+    b = phi_r.copy()
+    OSM.sweep(b, f_r, g, 1.0)
+    assert np.max(np.abs(host(phi_t) - b)) <= tol * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("n,order", [((34, 20, 18), 2), ((34, 20, 18), 4), ((64, 32, 48), 2)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_restrict_and_prolong(pkg, n, order, dtype):
+    fine = _grid(n, order)
+    coarse = fine.coarsen()
+    gen = W.rng(5)
+    u = fine.zeros()
+    u[fine.interior] = gen.standard_normal(u[fine.interior].shape)
+    fc = torch.zeros(coarse.shape, device="cuda:0", dtype=dtype)
+    pkg.ops.restrict(n, order, dev(u, dtype), fc)
+    ref = OT.restrict(host(dev(u, dtype)), fine, coarse)
+    tol = 1e-15 if dtype == torch.float64 else 1e-6
+    assert np.max(np.abs(host(fc) - ref)) <= tol * np.max(np.abs(ref)) * 4
+    v = coarse.zeros()
+    v[coarse.interior] = gen.standard_normal(v[coarse.interior].shape)
+    base = gen.standard_normal(fine.shape)
+    pf = dev(base, dtype)
+    base_r = host(pf)
+    pkg.ops.prolong(n, order, dev(v, dtype), pf)
+    refp = base_r + OT.prolong(host(dev(v, dtype)), coarse, fine)
+    assert np.max(np.abs(host(pf) - refp)) <= tol * 8 * np.max(np.abs(refp))
+
+
+@pytest.mark.parametrize("lmax", [0, 1, 4, 8, 12])
+@pytest.mark.parametrize("n,order", [((34, 20, 18), 2), ((24, 24, 24), 4)])
+def test_multipole_moments_and_boundary(pkg, lmax, n, order):
+    g = _grid(n, order)
+    rho = np.abs(W.rng(8).standard_normal(g.shape))
+    origin = (0.45, 0.55, 0.5)
+    q = np.array(pkg.ops.multipole_moments(n, order, dev(rho), origin, lmax))
+    qo = OM.moments_cartesian(rho, g, origin, lmax)
+    assert np.max(np.abs(q - qo)) <= 1e-12 * np.max(np.abs(qo))
+    phi = dev(np.zeros(g.shape))
+    pkg.ops.multipole_boundary(n, order, list(qo), origin, lmax, 1.3, phi)
+    ref = g.zeros()
+    OM.apply_cartesian_bc(ref, g, qo, origin, lmax, 1.3)
+    got = host(phi)
+    m = OM.boundary_mask(g)
+    assert rel_err(got[m], ref[m]) <= 1e-12
+    assert np.all(got[~m] == 0.0)
+
+
+# ------------------------------------------------------------------ whole solves (FP64)
+def _solve_pair(pkg, n, order, rho, phi0, method, tol, bc="dirichlet", lmax=4, omega=1.0,
+                max_iter=10000, box=(1.0, 1.0, 1.0), prec="fp64", nu=(2, 2)):
+    g = _grid(n, order, box)
+    phi_o = phi0.copy()
+    info_o = OS.solve_cartesian(rho, phi_o, g, {"mg": "mg", "cg": "cg", "sor": "sor"}[method], tol,
+                                max_iter=max_iter, bc=bc, lmax=lmax, omega=omega, nu1=nu[0], nu2=nu[1])
+    phi_t = dev(phi0)
+    with pkg.CartesianSolver(n, order, hi=box, bc=bc, lmax=lmax) as s:
+        info = s.solve(dev(rho), phi_t, tol=tol, method=method, prec=prec, omega=omega,
+                       max_iter=max_iter, nu1=nu[0], nu2=nu[1])
+    return info, info_o, host(phi_t), phi_o
+
+
+def test_config1_sor_and_cg_match_oracle(pkg):
+    """32^3 uniform sphere, Dirichlet data from the closed form: red-black SOR
+    (omega = 1.8) and CG to 1e-10 (the small FP64 configuration)."""
+    rho, phi0, exact = W.uniform_sphere(32)
+    for method, omega in (("sor", 1.8), ("cg", 1.0)):
+        info, info_o, got, ref = _solve_pair(pkg, 32, 2, rho, phi0, method, 1e-10, omega=omega)
+        assert info.converged and info_o.converged
+        assert info.iterations == info_o.iterations, (method, info.iterations, info_o.iterations)
+        assert rel_err(got, ref) <= FP64_TOL
+        assert abs(info.rel_residual - info_o.rel_residual) <= 1e-3 * info_o.rel_residual
+        g = cart_grid(32)
+        assert rel_err(got[g.interior], exact[g.interior]) <= 2e-2
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_mg_multipole_fp64_matches_oracle(pkg, n):
+    rho = W.gaussian_blobs(n, seed=2)
+    info, info_o, got, ref = _solve_pair(pkg, n, 2, rho, np.zeros(W.cart_shape(n, 2)), "mg", 1e-10,
+                                         bc="multipole", lmax=4)
+    assert info.converged and info.iterations == info_o.iterations
+    assert rel_err(got, ref) <= FP64_TOL
+    np.testing.assert_allclose(info.moments, info_o.moments, rtol=0, atol=1e-12 * abs(info_o.moments[0]))
+    assert info.coarse_iterations > 0
+
+
+def test_mg_anisotropic_noncubic_fp64(pkg):
+    n = (32, 64, 48)
+    rho = np.abs(W.rng(12).standard_normal(W.cart_shape(n, 2)))
+    info, info_o, got, ref = _solve_pair(pkg, n, 2, rho, np.zeros(W.cart_shape(n, 2)), "mg", 1e-10,
+                                         box=(1.0, 1.0, 1.0))
+    assert info.iterations == info_o.iterations
+    assert rel_err(got, ref) <= FP64_TOL
+
+
+def test_mg_13point_fp64(pkg):
+    rho, phi0, exact = W.manufactured_sine(32, 4)
+    info, info_o, got, ref = _solve_pair(pkg, 32, 4, rho, phi0, "mg", 1e-10)
+    assert info.iterations == info_o.iterations
+    assert rel_err(got, ref) <= FP64_TOL
+
+
+def test_sor_13point_three_colours(pkg):
+    rho, phi0, _ = W.manufactured_sine(16, 4)
+    info, info_o, got, ref = _solve_pair(pkg, 16, 4, rho, phi0, "sor", 1e-10, omega=1.5)
+    assert info.iterations == info_o.iterations
+    assert rel_err(got, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("prec", ["mixed_fp32", "mixed_bf16"])
+@pytest.mark.parametrize("order", [2, 4])
+def test_mixed_precision_ir_within_1e7(pkg, prec, order):
+    n = 64
+    rho = W.gaussian_blobs(n, order=order, seed=2)
+    g = cart_grid(n, order)
+    phi_o = g.zeros()
+    info_o = OS.solve_cartesian(rho, phi_o, g, "mg", 1e-10, bc="multipole", lmax=4)
+    phi_t = dev(np.zeros(g.shape))
+    with pkg.CartesianSolver(n, order, bc="multipole", lmax=4) as s:
+        info = s.solve(dev(rho), phi_t, tol=1e-10, method="mg", prec=prec, max_iter=60)
+    assert info.converged, info
+    assert info.rel_residual <= 1e-10
+    assert rel_err(host(phi_t), phi_o) <= MIXED_TOL
+
+
+def test_not_converged_status_and_partial_result(pkg):
+    rho = W.gaussian_blobs(32, seed=2)
+    phi_t = dev(np.zeros(W.cart_shape(32, 2)))
+    with pkg.CartesianSolver(32, bc="multipole") as s:
+        info = s.solve(dev(rho), phi_t, tol=1e-14, method="mg", max_iter=2)
+    assert info.status == pkg.capi.PS_NOT_CONVERGED
+    assert info.iterations == 2 and info.rel_residual > 1e-14
+    assert np.isfinite(host(phi_t)).all()
+
+
+def test_batch_equals_separate_solves(pkg):
+    sizes = [32, 64, 32]
+    solvers = [pkg.CartesianSolver(n, bc="multipole") for n in sizes]
+    rhos = [dev(W.gaussian_blobs(n, seed=20 + i)) for i, n in enumerate(sizes)]
+    phis = [torch.zeros_like(r) for r in rhos]
+    infos = pkg.solve_batch(solvers, rhos, phis, [1e-10, 1e-6, 1e-8])
+    for i, n in enumerate(sizes):
+        p = torch.zeros_like(rhos[i])
+        one = solvers[i].solve(rhos[i], p, tol=[1e-10, 1e-6, 1e-8][i])
+        assert one.iterations == infos[i].iterations
+        assert torch.equal(p, phis[i])
+    for s in solvers:
+        s.close()
+
+
+# ------------------------------------------------------------------ spherical
+def _sph_problem(nr=32, nt=16, np_=32):
+    r, th, ph = W.spherical_coords(nr, nt, np_, 0.01, 1.0)
+    rho = W.spherical_density(r, th, ph)
+    return r, th, ph, rho
+
+
+def test_spherical_operator_matches_oracle(pkg):
+    r, th, ph, _ = _sph_problem(20, 12, 24)
+    op = OSP.SphericalOperator(r, th, ph)
+    P = W.rng(13).standard_normal(op.shape)
+    out = dev(np.zeros(op.shape))
+    with pkg.SphericalSolver(r, th, ph, bc="dirichlet") as s:
+        s.apply(dev(P), out)
+    ref = op.apply(P)
+    got = host(out)[1:-1, 1:-1, 1:-1]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_spherical_bicgstab_matches_oracle(pkg, prec):
+    """BiCGSTAB's iteration count on the graded log grid is set by rounding
+    (the oracle itself needs 179 to 186 iterations depending on how its dot
+    products are summed), so the FP64 count must lie inside the oracle's own
+    spread over two valid summation orders, widened by 3% + 2; phi must agree
+    to 1e-10."""
+    r, th, ph, rho = _sph_problem()
+    phi_o = np.zeros(rho.shape)
+    info_o = OS.solve_spherical(rho, phi_o, r, th, ph, 1e-10, lmax=6)
+    info_x = OS.solve_spherical(rho, np.zeros(rho.shape), r, th, ph, 1e-10, lmax=6, exact_dots=True)
+    lo_it = min(info_o.iterations, info_x.iterations)
+    hi_it = max(info_o.iterations, info_x.iterations)
+    phi_t = dev(np.zeros(rho.shape))
+    with pkg.SphericalSolver(r, th, ph, bc="multipole", lmax=6) as s:
+        info = s.solve(dev(rho), phi_t, tol=1e-10, prec=prec, max_iter=5000)
+    assert info.converged, info
+    got = host(phi_t)
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    np.testing.assert_allclose(got[1:-1, 1:-1, -1], phi_o[1:-1, 1:-1, -1], rtol=1e-12)
+    if prec == "fp64":
+        assert 0.97 * lo_it - 2 <= info.iterations <= 1.03 * hi_it + 2, (info.iterations, lo_it, hi_it)
+        assert rel_err(got[U], phi_o[U]) <= FP64_TOL
+    else:
+        assert rel_err(got[U], phi_o[U]) <= MIXED_TOL
