@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark: 256^3 multigrid solve with the multipole open boundary on GB300.
+
+Workload (one "step" = one whole solve, cold start, to relative residual 1e-10):
+256 intervals per axis on the unit cube (255^3 unknowns), FP64, 7-point
+Laplacian, V(2,2) cycles with red-black Gauss-Seidel, full weighting, trilinear
+prolongation, CG on the 8^3 coarsest level, multipole boundary with l_max = 4;
+density = 8 isotropic Gaussians (centres U[0.2,0.8]^3, sigma U[0.02,0.08],
+amplitude U[0.5,2], seed 2).  Inputs are synthetic and larger than L2
+(rho and phi are 136 MB each in FP64).
+
+value = fine-grid unknown updates per second over the whole solve:
+(N-1)^3 x V-cycles / solve time, in GLUPS.  The same solve is also timed in the
+mixed FP32 and mixed BF16 refinement modes (FP64 outer residual) for the
+FP64-vs-mixed part of the metric.
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+Multi-GPU: independent replicas, one per rank (the solve does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+LMAX = 4
+TOL = 1e-10
+SEED = 2
+WORKLOAD = ("256^3 uniform Cartesian, FP64, 7-point Laplacian, MG V(2,2) red-black GS, full "
+            "weighting, trilinear prolongation, CG-solved 8^3 coarsest level, multipole l_max=4, "
+            "8 Gaussian blobs seed 2, cold start to rel. residual 1e-10")
+FP64_PIPE_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 (FMA = 2 flops) = 625 G FP64 instr/s
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception as e:  # no nvidia-smi: report nothing rather than guess
+            log("clock sampling unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import workloads as W
+    from oracle import multigrid as OMG, multipole as OM
+    from oracle.grid import cart_grid, hierarchy
+    # each step is one FP64 V(2,2) cycle of the same 256^3 workload (the oracle needs
+    # ~10 s per cycle); for long runs the sample shrinks to the 128^3 grid
+    n = N if (args.steps + args.warmup) <= 16 else 128
+    g = cart_grid(n)
+    rho = W.gaussian_blobs(n, seed=SEED)
+    phi = g.zeros()
+    q = OM.moments_cartesian(rho, g, (0.5, 0.5, 0.5), LMAX)
+    OM.apply_cartesian_bc(phi, g, q, (0.5, 0.5, 0.5), LMAX, 1.0)
+    f = 4 * math.pi * rho
+    levels = hierarchy(g)
+    for _ in range(args.warmup):
+        OMG.vcycle(levels, 0, phi, f, 2, 2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        OMG.vcycle(levels, 0, phi, f, 2, 2)
+    dt = time.perf_counter() - t0
+    value = (n - 1) ** 3 * args.steps / dt / 1e9
+    sample = f"{args.steps} FP64 V(2,2) cycles of the {n}^3 workload (oracle/multigrid.vcycle, numpy)"
+    line = {"impl": "reference", "metric": "GLUPS (fine-grid unknown updates/s over the whole solve)",
+            "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_n": n},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample():
+    """The oracle on the host: one FP64 V(2,2) cycle of the same 256^3 workload."""
+    import workloads as W
+    from oracle import multigrid as OMG
+    from oracle.grid import cart_grid, hierarchy
+    g = cart_grid(N)
+    rho = W.gaussian_blobs(N, seed=SEED)
+    phi = g.zeros()
+    f = 4 * math.pi * rho
+    levels = hierarchy(g)
+    t0 = time.perf_counter()
+    OMG.vcycle(levels, 0, phi, f, 2, 2)
+    dt = time.perf_counter() - t0
+    return {"value": (N - 1) ** 3 / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 V(2,2) cycle of the 256^3 workload on the host ({dt:.1f} s, "
+                      "numpy, single thread)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2605_03563_gb300 as P
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    rho_h = torch.from_numpy(W.gaussian_blobs(N, seed=SEED)).pin_memory()
+    rho = rho_h.to(dev)
+    phi = torch.zeros_like(rho)
+    stream = torch.cuda.current_stream()
+    solver = P.CartesianSolver(N, bc="multipole", lmax=LMAX)
+
+    def one(prec="fp64", out=None):
+        out = phi if out is None else out
+        out.zero_()
+        return solver.solve(rho, out, tol=TOL, method="mg", prec=prec, max_iter=100)
+
+    for _ in range(args.warmup):
+        info = one()
+    assert info.converged, info
+
+    # ---- timed FP64 region
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id)
+    solver.profile(True)
+    infos, ev = [], [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        infos.append(one())
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    prof = solver.profile_read()
+    solver.profile(False)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cycles = [i.iterations for i in infos]
+    assert all(i.converged for i in infos), infos[-1]
+    unknowns = (N - 1) ** 3
+    value = world * unknowns * sum(cycles) / (total_ms / 1e3) / 1e9
+    launches = sum(i.kernel_launches for i in infos)
+    phi64 = phi.clone()
+
+    # ---- end to end through the public API with host buffers
+    phi_zero_h = torch.zeros_like(rho_h).pin_memory()
+    phi_out_h = torch.empty_like(rho_h).pin_memory()
+    rho_d = torch.empty_like(rho)
+    phi_d = torch.empty_like(rho)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_cycles = 0
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        rho_d.copy_(rho_h, non_blocking=True)
+        phi_d.copy_(phi_zero_h, non_blocking=True)
+        inf = solver.solve(rho_d, phi_d, tol=TOL, method="mg", max_iter=100)
+        e2e_cycles += inf.iterations
+        phi_out_h.copy_(phi_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = world * unknowns * e2e_cycles / (e2e_ms / 1e3) / 1e9
+    nbytes = rho_h.numel() * 8
+
+    # ---- mixed precision variants (same workload, same tolerance)
+    mixed = {}
+    if not args.no_mixed:
+        for prec in ("mixed_fp32", "mixed_bf16"):
+            out = torch.zeros_like(rho)
+            for _ in range(2):
+                one(prec, out)
+            times, its, inner = [], [], []
+            for _ in range(max(3, args.steps // 2)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                inf = one(prec, out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+                its.append(inf.iterations)
+                inner.append(inf.inner_cycles)
+            err = float((out - phi64).abs().max() / phi64.abs().max())
+            t_med = statistics.median(times)
+            mixed[prec] = {"time_to_1e-10_ms": t_med, "ir_steps": its[-1], "inner_vcycles": inner[-1],
+                           "rel_residual": inf.rel_residual, "max_rel_diff_vs_fp64_gpu": err,
+                           "speedup_vs_fp64": statistics.median(step_ms) / t_med,
+                           "converged": inf.converged}
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    avg_s = dom["avg_ms"] / 1e3
+    gbs = dom["bytes_per_launch"] / avg_s / 1e9
+    gops = dom["ops_per_launch"] / avg_s / 1e9
+    if dom["fp64"]:
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
+                "unit": "Gop/s (FP64 pipe instructions, FMA = 1)", "frac": gops / FP64_PIPE_PEAK_GOPS,
+                "traffic": None, "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": gbs / peaks["hbm_gbs"],
+                "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                "ops_per_launch": dom["ops_per_launch"], "avg_launch_ms": dom["avg_ms"],
+                "peak_source": "nominal FP64 rate 1.25 TFLOP/s / 2 (FMA); hbm peak " + peak_src}
+    else:
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                "algorithmic_bytes_per_launch": dom["bytes_per_launch"], "avg_launch_ms": dom["avg_ms"],
+                "peak_source": peak_src}
+    kernels = {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 5),
+                   "share_of_profiled": round(v["total_ms"] / sum(x["total_ms"] for x in prof.values()), 4),
+                   "GB/s": round(v["bytes_per_launch"] / (v["avg_ms"] / 1e3) / 1e9, 1) if v["avg_ms"] > 0 else None,
+                   "Gop/s": round(v["ops_per_launch"] / (v["avg_ms"] / 1e3) / 1e9, 1) if v["avg_ms"] > 0 else None}
+               for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_sample()
+
+    solver.close()
+    if rank == 0:
+        sorted_ms = sorted(step_ms)
+        p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
+        line = {
+            "metric": "GLUPS (fine-grid unknown updates/s over the whole solve) + time-to-1e-10",
+            "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_intervals": N, "unknowns": unknowns, "l_max": LMAX,
+                       "tol": TOL, "v_cycles_per_solve": cycles[0],
+                       "l2": "inputs larger than L2 (rho, phi, scaled RHS: 136 MB each)",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_1e-10_ms": {"p50": statistics.median(step_ms), "p99": p99,
+                                 "mean": total_ms / args.steps},
+            "s_t_glups": unknowns / (statistics.median(step_ms) / 1e3) / 1e9,
+            "t_mp_ms": infos[-1].t_mp_ms, "rel_residual": infos[-1].rel_residual,
+            "rho_conv": infos[-1].rho_conv,
+            "mixed": mixed,
+            "roofline": roof,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 2 * nbytes,
+                    "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -105,6 +105,7 @@ typedef struct {
   double t_iter_ms;          /* iteration time */
   int64_t inner_cycles;      /* mixed modes: total inner V-cycles / Krylov iterations */
   int64_t coarse_iterations; /* MG: total CG iterations on the coarsest level */
+  int64_t kernel_launches;   /* CUDA kernels this solve launched */
   double moments[81];        /* first min((l_max+1)^2, 81) multipole moments q_lm, index l*l+l+m */
 } ps_info;
 
@@ -157,6 +158,33 @@ const char* poisson_last_error(void);
 /* Device bytes poisson_create + poisson_solve would allocate for this grid and
  * precision (used for admission control); 0 for invalid arguments. */
 size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max, int prec);
+
+/* ------------------------------------------------------------------ kernel timing
+ * Opt-in timing of the hot kernels of a handle's solves with CUDA events
+ * recorded on the solve stream around each launch (finest-level sweeps,
+ * residual/restriction/prolongation passes, convergence norms, coarsest
+ * solve, multipole moments and boundary values).  Each record carries the
+ * algorithmic bytes (minimal HBM traffic of the operation) and FP64/FP32
+ * arithmetic operations of one launch.  No paper counterpart: measurement
+ * support for the roofline figures. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double bytes_per_launch;   /* algorithmic bytes of one launch */
+  double ops_per_launch;     /* arithmetic instructions of one launch (FMA = 1) */
+  int32_t fp64;              /* 1 when the arithmetic runs on the FP64 pipe */
+  int32_t pad;
+} ps_kernel_stat;
+
+/* enable != 0 starts recording (events are created lazily; at most 16384
+ * launches are recorded between reads); 0 stops. */
+ps_status poisson_profile_enable(ps_handle h, int enable);
+
+/* Synchronises the handle's stream, folds the recorded launches into per-kernel
+ * totals, writes up to max entries and returns how many kernels were seen
+ * (negative on error).  Recorded launches are cleared. */
+int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max);
 
 /* ------------------------------------------------------------------ op-level calls
  * Single kernels of the hot path on caller-owned buffers, for validation and

@@ -32,6 +32,7 @@ class SolveInfo:
     t_iter_ms: float
     inner_cycles: int
     coarse_iterations: int
+    kernel_launches: int
     moments: list = field(default_factory=list)
 
     @property
@@ -42,7 +43,7 @@ class SolveInfo:
     def from_c(info: capi.PsInfo, nmom: int) -> "SolveInfo":
         return SolveInfo(info.status, info.iterations, info.rel_residual, info.rho_conv,
                          info.t_mp_ms, info.t_iter_ms, info.inner_cycles, info.coarse_iterations,
-                         list(info.moments[:nmom]))
+                         info.kernel_launches, list(info.moments[:nmom]))
 
 
 def _ptr(t, dtype_name="float64"):
@@ -83,6 +84,25 @@ class _Handle:
             self.close()
         except Exception:
             pass
+
+    def profile(self, enable=True):
+        """Record CUDA-event timings of the hot kernels of this handle's solves."""
+        check(lib().poisson_profile_enable(self._h, 1 if enable else 0), "poisson_profile_enable")
+
+    def profile_read(self):
+        """Per-kernel {launches, total_ms, avg_ms, bytes_per_launch, ops_per_launch, fp64}."""
+        buf = (capi.PsKernelStat * 32)()
+        k = lib().poisson_profile_read(self._h, buf, 32)
+        if k < 0:
+            raise capi.PoissonError(capi.PS_ERR_CUDA, "poisson_profile_read")
+        out = {}
+        for i in range(min(k, 32)):
+            e = buf[i]
+            out[e.name.decode()] = dict(launches=e.launches, total_ms=e.total_ms,
+                                        avg_ms=e.total_ms / max(e.launches, 1),
+                                        bytes_per_launch=e.bytes_per_launch,
+                                        ops_per_launch=e.ops_per_launch, fp64=bool(e.fp64))
+        return out
 
     def __enter__(self):
         return self

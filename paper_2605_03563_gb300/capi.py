@@ -43,7 +43,13 @@ class PsInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("rel_residual", C.c_double),
                 ("rho_conv", C.c_double), ("t_mp_ms", C.c_double), ("t_iter_ms", C.c_double),
                 ("inner_cycles", C.c_int64), ("coarse_iterations", C.c_int64),
-                ("moments", C.c_double * 81)]
+                ("kernel_launches", C.c_int64), ("moments", C.c_double * 81)]
+
+
+class PsKernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("bytes_per_launch", C.c_double), ("ops_per_launch", C.c_double),
+                ("fp64", C.c_int32), ("pad", C.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -58,6 +64,8 @@ SIGNATURES = {
     "poisson_destroy": (None, [C.c_void_p]),
     "poisson_last_error": (C.c_char_p, []),
     "poisson_workspace_bytes": (C.c_size_t, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_int]),
+    "poisson_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "poisson_profile_read": (C.c_int, [C.c_void_p, C.POINTER(PsKernelStat), C.c_int]),
     "ps_op_apply": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_op_residual": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),

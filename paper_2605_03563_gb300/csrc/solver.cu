@@ -63,6 +63,23 @@ static const double COARSE_TOL = 1e-12;
 
 using namespace ps;
 
+// Kernel classes of the opt-in profiler.
+enum ProfClass {
+  PC_SWEEP0 = 0, PC_DELTA0, PC_RESTRICT0, PC_PROLONG0, PC_NORM0, PC_COARSE, PC_MOMENTS, PC_FACES,
+  PC_SWEEP_C, PC_CORRECT0, PC_KRYLOV, PC_COUNT
+};
+static const char* kProfNames[PC_COUNT] = {
+  "sweep_colour_finest", "residual_finest", "restrict_finest", "prolong_finest", "norm_finest",
+  "coarse_cg", "multipole_moments", "multipole_boundary", "sweep_colour_coarse", "ir_correct",
+  "krylov_vector"};
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes, ops;
+  int fp64;
+};
+
 struct ps_ctx {
   ps_grid grid{};
   int order = 2;
@@ -95,6 +112,12 @@ struct ps_ctx {
   float* ir_rhs = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   size_t bytes = 0;
+  // profiler
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> ev_pool;
+  int prof_open = -1;
+  long long nlaunch = 0;   // kernels launched by the current solve
 };
 
 namespace {
@@ -107,6 +130,32 @@ ps_status fail(ps_status s, const char* fmt, ...) {
   va_end(ap);
   g_err = buf;
   return s;
+}
+
+// Profiler: begin/end pair around one launch on stream s.
+void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStream_t s) {
+  if (!h->prof || h->recs.size() >= 16384) return;
+  ProfRec r;
+  r.cls = cls;
+  r.bytes = bytes;
+  r.ops = ops;
+  r.fp64 = fp64;
+  for (cudaEvent_t* e : {&r.a, &r.b}) {
+    if (!h->ev_pool.empty()) {
+      *e = h->ev_pool.back();
+      h->ev_pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      return;
+    }
+  }
+  cudaEventRecord(r.a, s);
+  h->recs.push_back(r);
+  h->prof_open = (int)h->recs.size() - 1;
+}
+void prof_end(ps_ctx* h, cudaStream_t s) {
+  if (h->prof_open < 0) return;
+  cudaEventRecord(h->recs[h->prof_open].b, s);
+  h->prof_open = -1;
 }
 
 #define TRY(expr)                                                                      \
@@ -198,27 +247,82 @@ void free_hier(Hier* H) {
   H->built = false;
 }
 
+// Algorithmic work of the finest-level passes (per launch), for the profiler.
+struct Work {
+  double n;       // interior unknowns
+  double S, St;   // storage bytes of phi/fs and of the delta buffer
+  int G;
+  bool fp64;
+};
+Work work_of(const Level& L, int order) {
+  Work w;
+  w.n = (double)L.d.ni() * L.d.nj() * L.d.nk();
+  w.S = (double)dt_size(L.dt);
+  w.St = (double)dt_size(L.dt_tmp);
+  w.G = order / 2;
+  w.fp64 = L.dt == DT_F64;
+  return w;
+}
+
+cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState* st, cudaStream_t s) {
+  const int ncol = h->order == 2 ? 2 : 3;
+  const Work w = work_of(L, h->order);
+  cudaError_t e;
+  for (int c = 0; c < ncol; c++) {
+    // one colour pass reads phi everywhere, fs and phi on its colour, writes phi on its colour
+    prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, w.n * w.S * (1.0 + 2.0 / ncol),
+               w.n / ncol * (6.0 * w.G + (omega != 1.0 ? 2.0 : 0.0)), w.fp64, s);
+    e = (h->nlaunch += 1, launch_sweep_colour(L.d, h->order, L.h, L.dt, L.phi, L.fs, c, omega, st, s));
+    prof_end(h, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) {
   Level& L = H.lv[l];
-  const int ncol = h->order == 2 ? 2 : 3;
   cudaError_t e;
   if (l == h->nlev - 1) {
     const int nunk = L.d.ni() * L.d.nj() * L.d.nk();
-    return launch_coarse_cg(L.d, h->order, L.h, L.dt, L.fs, L.dt, L.phi, COARSE_TOL, nunk, h->st, s);
+    prof_begin(h, PC_COARSE, 0.0, 0.0, 1, s);
+    e = (h->nlaunch += 1, launch_coarse_cg(L.d, h->order, L.h, L.dt, L.fs, L.dt, L.phi, COARSE_TOL, nunk, h->st, s));
+    prof_end(h, s);
+    return e;
   }
+  const Work w = work_of(L, h->order);
   for (int it = 0; it < nu1; it++)
-    for (int c = 0; c < ncol; c++)
-      if ((e = launch_sweep_colour(L.d, h->order, L.h, L.dt, L.phi, L.fs, c, 1.0, nullptr, s)) != cudaSuccess) return e;
-  if ((e = launch_delta(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, 1.0, false, nullptr, nullptr, s)) != cudaSuccess) return e;
+    if ((e = sweep_level(h, L, l, 1.0, nullptr, s)) != cudaSuccess) return e;
+  if (l == 0) prof_begin(h, PC_DELTA0, w.n * (2.0 * w.S + w.St), w.n * (6.0 * w.G + 1.0), w.fp64, s);
+  e = (h->nlaunch += 1, launch_delta(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, 1.0, false, nullptr, nullptr, s));
+  if (l == 0) prof_end(h, s);
+  if (e != cudaSuccess) return e;
   Level& Cl = H.lv[l + 1];
-  if ((e = launch_restrict(L.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s)) != cudaSuccess) return e;
+  if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * 4.5, w.St == 8.0, s);
+  e = (h->nlaunch += 1, launch_restrict(L.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s));
+  if (l == 0) prof_end(h, s);
+  if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(Cl.phi, 0, (size_t)Cl.d.size() * dt_size(Cl.dt), s)) != cudaSuccess) return e;
   if ((e = vcycle(h, H, l + 1, nu1, nu2, s)) != cudaSuccess) return e;
-  if ((e = launch_prolong(L.d, Cl.dt, Cl.phi, L.dt, L.phi, s)) != cudaSuccess) return e;
+  if (l == 0) prof_begin(h, PC_PROLONG0, w.n * 2.0 * w.S + w.n / 8.0 * dt_size(Cl.dt), w.n * 4.0, w.fp64, s);
+  e = (h->nlaunch += 1, launch_prolong(L.d, Cl.dt, Cl.phi, L.dt, L.phi, s));
+  if (l == 0) prof_end(h, s);
+  if (e != cudaSuccess) return e;
   for (int it = 0; it < nu2; it++)
-    for (int c = 0; c < ncol; c++)
-      if ((e = launch_sweep_colour(L.d, h->order, L.h, L.dt, L.phi, L.fs, c, 1.0, nullptr, s)) != cudaSuccess) return e;
+    if ((e = sweep_level(h, L, l, 1.0, nullptr, s)) != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+// Convergence pass on the finest FP64 level (optionally storing the IR inner RHS).
+cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cudaStream_t s) {
+  const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+  const int G = h->order / 2;
+  const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
+  prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (6.0 * G + 3.0), 1, s);
+  cudaError_t e = out ? launch_delta_st(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, dout, out, h->st, h->partials, s)
+                      : launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, false, h->partials, nullptr, s);
+  prof_end(h, s);
+  if (e != cudaSuccess) return e;
+  return (h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), dd, mode, h->st, s));
 }
 
 ps_status read_state(ps_ctx* h, cudaStream_t s) {
@@ -256,19 +360,28 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
   // multipole boundary
   TRY(cudaEventRecord(h->ev[0], s));
   if (h->bc.outer == PS_BC_MULTIPOLE) {
-    TRY(launch_cart_moments(h->d0, h->grid.lo, h->h0, h->bc.origin, rho, &h->mp, s));
-    TRY(launch_cart_faces(h->d0, h->grid.lo, h->h0, h->bc.origin, h->bc.G, h->mp.q, &h->mp, phi, s));
+    const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+    const double nf = (double)h->d0.size() - n;
+    const double W = h->lmax + 1.0;
+    prof_begin(h, PC_MOMENTS, n * 8.0, n * 2.0 * W, 1, s);
+    cudaError_t e = (h->nlaunch += 3, launch_cart_moments(h->d0, h->grid.lo, h->h0, h->bc.origin, rho, &h->mp, s));
+    prof_end(h, s);
+    TRY(e);
+    prof_begin(h, PC_FACES, nf * 8.0, nf * 4.0 * W * W, 1, s);
+    e = (h->nlaunch += 1, launch_cart_faces(h->d0, h->grid.lo, h->h0, h->bc.origin, h->bc.G, h->mp.q, &h->mp, phi, s));
+    prof_end(h, s);
+    TRY(e);
   }
   TRY(cudaEventRecord(h->ev[1], s));
   Coef<double> cf = make_coef<double>(h->d0, h->h0, h->order);
   const double fscale = -4.0 * M_PI * h->bc.G * cf.inv_d;
   *fscale_out = fscale;
-  TRY(launch_scale_rhs(h->d0, fscale, rho, DT_F64, h->fs64, s));
+  TRY((h->nlaunch += 1, launch_scale_rhs(h->d0, fscale, rho, DT_F64, h->fs64, s)));
   ps_status st = reset_state(h, h->st, h->hst, tol, max_iter, s);
   if (st != PS_OK) return st;
   // reference norm ||f - A phi0||, phi0 = boundary data only
-  TRY(launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, true, h->partials, nullptr, s));
-  TRY(launch_finish_norm(h->partials, cart_partials_count(h->d0), cf.d, 0, h->st, s));
+  TRY((h->nlaunch += 1, launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, true, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), cf.d, 0, h->st, s)));
   return PS_OK;
 }
 
@@ -277,15 +390,11 @@ ps_status cart_mg64(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t
   if (r != PS_OK) return r;
   Hier& H = h->h64;
   H.lv[0].phi = phi;
-  const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
-  const int nb = cart_partials_count(h->d0);
-  TRY(launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, false, h->partials, nullptr, s));
-  TRY(launch_finish_norm(h->partials, nb, dd, 1, h->st, s));
+  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
   if ((r = read_state(h, s)) != PS_OK) return r;
   while (h->hst->done == DONE_NO) {
     TRY(vcycle(h, H, 0, o->nu1, o->nu2, s));
-    TRY(launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, false, h->partials, nullptr, s));
-    TRY(launch_finish_norm(h->partials, nb, dd, 2, h->st, s));
+    TRY(norm_pass(h, phi, 2, DT_F64, nullptr, s));
     if ((r = read_state(h, s)) != PS_OK) return r;
   }
   return PS_OK;
@@ -297,20 +406,22 @@ ps_status cart_ir(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s
   if (r != PS_OK) return r;
   Hier& H = h->hmx[p];
   Level& L0 = H.lv[0];
-  const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
-  const int nb = cart_partials_count(h->d0);
   const int inner = std::max(1, o->inner_cycles);
-  TRY(launch_delta_st(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, L0.dt, L0.fs, h->st, h->partials, s));
-  TRY(launch_finish_norm(h->partials, nb, dd, 1, h->st, s));
+  TRY(norm_pass(h, phi, 1, L0.dt, L0.fs, s));
   if ((r = read_state(h, s)) != PS_OK) return r;
   long long cycles = 0;
   while (h->hst->done == DONE_NO) {
     TRY(cudaMemsetAsync(L0.phi, 0, (size_t)L0.d.size() * dt_size(L0.dt), s));
     for (int c = 0; c < inner; c++) TRY(vcycle(h, H, 0, o->nu1, o->nu2, s));
     cycles += inner;
-    TRY(launch_correct(h->d0, L0.dt, L0.phi, 1.0, phi, h->st, s));
-    TRY(launch_delta_st(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, L0.dt, L0.fs, h->st, h->partials, s));
-    TRY(launch_finish_norm(h->partials, nb, dd, 2, h->st, s));
+    {
+      const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+      prof_begin(h, PC_CORRECT0, n * (16.0 + dt_size(L0.dt)), n * 2.0, 1, s);
+      cudaError_t e = (h->nlaunch += 1, launch_correct(h->d0, L0.dt, L0.phi, 1.0, phi, h->st, s));
+      prof_end(h, s);
+      TRY(e);
+    }
+    TRY(norm_pass(h, phi, 2, L0.dt, L0.fs, s));
     if ((r = read_state(h, s)) != PS_OK) return r;
   }
   h->hst->inner_cycles = cycles;
@@ -318,19 +429,18 @@ ps_status cart_ir(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s
 }
 
 ps_status cart_sor(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s) {
-  const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
-  const int nb = cart_partials_count(h->d0);
-  const int ncol = h->order == 2 ? 2 : 3;
   ps_status r;
-  TRY(launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, false, h->partials, nullptr, s));
-  TRY(launch_finish_norm(h->partials, nb, dd, 1, h->st, s));
+  Level L0;
+  L0.d = h->d0;
+  for (int a = 0; a < 3; a++) L0.h[a] = h->h0[a];
+  L0.phi = phi;
+  L0.fs = h->fs64;
+  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
   if ((r = read_state(h, s)) != PS_OK) return r;
   while (h->hst->done == DONE_NO) {
     for (int q = 0; q < KRYLOV_CHUNK; q++) {
-      for (int c = 0; c < ncol; c++)
-        TRY(launch_sweep_colour(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, c, o->omega, h->st, s));
-      TRY(launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, false, h->partials, nullptr, s));
-      TRY(launch_finish_norm(h->partials, nb, dd, 2, h->st, s));
+      TRY(sweep_level(h, L0, 0, o->omega, h->st, s));
+      TRY(norm_pass(h, phi, 2, DT_F64, nullptr, s));
     }
     if ((r = read_state(h, s)) != PS_OK) return r;
   }
@@ -347,16 +457,16 @@ ps_status cart_cg(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s
     if ((r = alloc_zero((void**)&h->cg_q, n * 8, &h->bytes)) != PS_OK) return r;
   }
   const int nb = cart_partials_count(h->d0);
-  TRY(launch_cg_init(h->d0, h->order, h->h0, phi, h->fs64, h->cg_r, h->cg_p, h->partials, nullptr, s));
-  TRY(launch_cg_scalar(h->partials, nb, 2, h->st, s));
+  TRY((h->nlaunch += 1, launch_cg_init(h->d0, h->order, h->h0, phi, h->fs64, h->cg_r, h->cg_p, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 2, h->st, s)));
   if ((r = read_state(h, s)) != PS_OK) return r;
   while (h->hst->done == DONE_NO) {
     for (int q = 0; q < KRYLOV_CHUNK; q++) {
-      TRY(launch_cg_apply(h->d0, h->order, h->h0, h->cg_p, h->cg_q, h->partials, h->st, s));
-      TRY(launch_cg_scalar(h->partials, nb, 0, h->st, s));
-      TRY(launch_cg_update(h->d0, phi, h->cg_r, h->cg_p, h->cg_q, h->partials, h->st, s));
-      TRY(launch_cg_scalar(h->partials, nb, 1, h->st, s));
-      TRY(launch_cg_pupdate(h->d0, h->cg_r, h->cg_p, h->st, s));
+      TRY((h->nlaunch += 1, launch_cg_apply(h->d0, h->order, h->h0, h->cg_p, h->cg_q, h->partials, h->st, s)));
+      TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 0, h->st, s)));
+      TRY((h->nlaunch += 1, launch_cg_update(h->d0, phi, h->cg_r, h->cg_p, h->cg_q, h->partials, h->st, s)));
+      TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 1, h->st, s)));
+      TRY((h->nlaunch += 1, launch_cg_pupdate(h->d0, h->cg_r, h->cg_p, h->st, s)));
     }
     if ((r = read_state(h, s)) != PS_OK) return r;
   }
@@ -383,15 +493,15 @@ ps_status sph_bicg(ps_ctx* h, int dt, const double* rho, double fscale, const vo
   if (r != PS_OK) return r;
   int nb = 0;
   void** v = h->sv;
-  TRY(launch_bicg_resid(h->sd, h->stab, dt, 0, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s));
-  TRY(launch_bicg_start(h->partials, nb, 0, st, s));
-  TRY(launch_bicg_resid(h->sd, h->stab, dt, 1, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s));
-  TRY(launch_bicg_start(h->partials, nb, 1, st, s));
+  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 0, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, st, s)));
+  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 1, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 1, st, s)));
   TRY(cudaMemcpyAsync(hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
   while (hst->done == DONE_NO) {
     for (int q = 0; q < KRYLOV_CHUNK; q++)
-      TRY(launch_bicg_iter(h->sd, h->stab, dt, x, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->partials, st, s));
+      TRY((h->nlaunch += 9, launch_bicg_iter(h->sd, h->stab, dt, x, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->partials, st, s)));
     TRY(cudaMemcpyAsync(hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
   }
@@ -403,8 +513,8 @@ ps_status sph_solve(ps_ctx* h, const double* rho, double* phi, double tol, const
   ps_status r;
   TRY(cudaEventRecord(h->ev[0], s));
   if (h->bc.outer == PS_BC_MULTIPOLE) {
-    TRY(launch_sph_moments(h->sd, h->stab, rho, s));
-    TRY(launch_sph_face(h->sd, h->stab, h->bc.G, phi, s));
+    TRY((h->nlaunch += 2, launch_sph_moments(h->sd, h->stab, rho, s)));
+    TRY((h->nlaunch += 1, launch_sph_face(h->sd, h->stab, h->bc.G, phi, s)));
   }
   TRY(cudaEventRecord(h->ev[1], s));
   const double fscale = 4.0 * M_PI * h->bc.G;
@@ -424,10 +534,10 @@ ps_status sph_solve(ps_ctx* h, const double* rho, double* phi, double tol, const
   if ((r = reset_state(h, h->st, h->hst, tol, o->max_iter, s)) != PS_OK) return r;
   int nb = 0;
   // reference norm ||f - L(boundary)|| (FP64 kernel, no vector output)
-  TRY(launch_bicg_resid(h->sd, h->stab, DT_F64, 0, rho, fscale, nullptr, phi, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s));
-  TRY(launch_bicg_start(h->partials, nb, 0, h->st, s));
-  TRY(launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s));
-  TRY(launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s));
+  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, DT_F64, 0, rho, fscale, nullptr, phi, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, h->st, s)));
+  TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
   if ((r = read_state(h, s)) != PS_OK) return r;
   const double inner_tol = 1e-4;
   const int inner_max = o->inner_cycles > 0 ? o->inner_cycles : 400;
@@ -436,9 +546,9 @@ ps_status sph_solve(ps_ctx* h, const double* rho, double* phi, double tol, const
     TRY(cudaMemsetAsync(e, 0, n * 4, s));
     if ((r = sph_bicg(h, DT_F32, nullptr, 1.0, h->ir_rhs, e, h->st2, h->hst2, inner_tol, inner_max, s)) != PS_OK) return r;
     inner_total += h->hst2->iter;
-    TRY(launch_sph_correct(h->sd, DT_F32, e, phi, h->st, s));
-    TRY(launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s));
-    TRY(launch_finish_norm(h->partials, nb, 1.0, 2, h->st, s));
+    TRY((h->nlaunch += 1, launch_sph_correct(h->sd, DT_F32, e, phi, h->st, s)));
+    TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
+    TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, s)));
     if ((r = read_state(h, s)) != PS_OK) return r;
   }
   h->hst->inner_cycles = inner_total;
@@ -454,6 +564,7 @@ void fill_info(ps_ctx* h, ps_info* info, ps_status st) {
   info->rho_conv = (d.iter > 0 && d.rel0 > 0.0) ? std::pow(d.rel / d.rel0, 1.0 / d.iter) : 0.0;
   info->inner_cycles = d.inner_cycles;
   info->coarse_iterations = d.coarse_iter_total;
+  info->kernel_launches = h->nlaunch;
   info->status = st;
   float a = 0.f, b = 0.f;
   if (cudaEventElapsedTime(&a, h->ev[0], h->ev[1]) == cudaSuccess) info->t_mp_ms = a;
@@ -635,6 +746,11 @@ void poisson_destroy(ps_handle h) {
   if (h->hst2) cudaFreeHost(h->hst2);
   for (auto& ev : h->ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto ev : h->ev_pool) cudaEventDestroy(ev);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -657,6 +773,7 @@ ps_status poisson_solve(ps_handle h, const double* rho_dev, double* phi_dev, dou
   if (o.prec < PS_FP64 || o.prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", o.prec);
   cudaStream_t s = o.stream ? (cudaStream_t)o.stream : h->stream;
   ps_status r = PS_OK;
+  h->nlaunch = 0;
   if (h->sph) {
     if (o.method != PS_BICGSTAB) return fail(PS_ERR_UNSUPPORTED, "spherical grids are solved by BiCGSTAB (method %d)", o.method);
     if (o.prec == PS_MIXED_BF16) return fail(PS_ERR_UNSUPPORTED, "BF16 storage is a multigrid option");
@@ -706,6 +823,55 @@ ps_status poisson_solve_batch(ps_handle* hs, const double* const* rho, double* c
     if (s != PS_OK && worst == PS_OK) worst = s;
   }
   return worst;
+}
+
+ps_status poisson_profile_enable(ps_handle h, int enable) {
+  if (!h) return fail(PS_ERR_INVALID_ARG, "NULL handle");
+  h->prof = enable != 0;
+  return PS_OK;
+}
+
+int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
+  if (!h || (max > 0 && !out)) {
+    fail(PS_ERR_INVALID_ARG, "bad profile_read arguments");
+    return -1;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    fail(PS_ERR_CUDA, "profile_read: synchronisation failed");
+    return -1;
+  }
+  struct Acc { int64_t n = 0; double ms = 0, bytes = 0, ops = 0; int fp64 = 0; };
+  std::vector<Acc> acc(PC_COUNT);
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      Acc& a = acc[r.cls];
+      a.n++;
+      a.ms += ms;
+      a.bytes = r.bytes;
+      a.ops = r.ops;
+      a.fp64 = r.fp64;
+    }
+    h->ev_pool.push_back(r.a);
+    h->ev_pool.push_back(r.b);
+  }
+  h->recs.clear();
+  int k = 0;
+  for (int c = 0; c < PC_COUNT; c++) {
+    if (acc[c].n == 0) continue;
+    if (k < max) {
+      ps_kernel_stat& o = out[k];
+      memset(&o, 0, sizeof(o));
+      snprintf(o.name, sizeof(o.name), "%s", kProfNames[c]);
+      o.launches = acc[c].n;
+      o.total_ms = acc[c].ms;
+      o.bytes_per_launch = acc[c].bytes;
+      o.ops_per_launch = acc[c].ops;
+      o.fp64 = acc[c].fp64;
+    }
+    k++;
+  }
+  return k;
 }
 
 // ---------------------------------------------------------------------- op-level calls

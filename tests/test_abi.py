@@ -40,7 +40,7 @@ def test_struct_layouts_match_the_header():
     assert C.sizeof(capi.PsGrid) == 16 + 48
     assert C.sizeof(capi.PsBC) == 8 + 24 + 8
     assert C.sizeof(capi.PsSolveOpts) == 8 + 8 + 16 + 8
-    assert C.sizeof(capi.PsInfo) == 8 + 32 + 16 + 81 * 8
+    assert C.sizeof(capi.PsInfo) == 8 + 32 + 24 + 81 * 8
 
 
 def test_invalid_arguments_rejected_before_gpu_work(lib):
