@@ -202,6 +202,25 @@ ps_status ps_op_apply(const ps_grid* grid, int stencil_order, int dtype, const v
 ps_status ps_op_residual(const ps_grid* grid, int stencil_order, int dtype, const void* phi_dev,
                          const void* f_dev, void* r_dev, double* norm2_host, void* stream);
 
+/* Allocation-free variant of ps_op_residual for FP64 fields (the paper has no
+ * counterpart; this is an integration aid).  For callers that must not
+ * allocate device memory -- code whose device memory is owned by an external
+ * pool or arena, latency-critical loops where an allocation may stall or
+ * fail, hosts with a no-allocation policy.  It computes the same r = f - A phi
+ * on interior nodes and ||r||_2^2 (into *norm2_host unless NULL, which
+ * synchronises the stream) but calls no cudaMalloc/cudaFree: its scratch
+ * (per-block partial sums) is one fixed 256 KB array in device global memory
+ * that every device loading the library keeps until exit.
+ *   - Grids whose launch needs more than 32768 thread blocks (beyond about
+ *     512^3 intervals) are rejected with PS_ERR_INVALID_ARG before GPU work.
+ *   - All calls on a device share that array: calls whose kernels can
+ *     overlap on the GPU race on it and must be serialised by the caller.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make it before any stream capture. */
+ps_status ps_op_residual_noalloc(const ps_grid* grid, int stencil_order, const double* phi_dev,
+                                 const double* f_dev, double* r_dev, double* norm2_host,
+                                 void* stream);
+
 /* One multicolour SOR step in place (Sec. 2.1.1): colours (i+j+k) mod 2 for
  * order 2, mod 3 for order 4, ascending; phi += omega (phi_GS - phi). */
 ps_status ps_op_sweep(const ps_grid* grid, int stencil_order, int dtype, void* phi_dev,

@@ -69,6 +69,8 @@ SIGNATURES = {
     "ps_op_apply": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_op_residual": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "ps_op_residual_noalloc": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "ps_op_sweep": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                               C.c_double, C.c_void_p]),
     "ps_op_restrict": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
