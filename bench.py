@@ -219,7 +219,6 @@ def main():
     except Exception:
         gpu_id = None
     clocks = ClockSampler(gpu_id)
-    solver.profile(True)
     infos, ev = [], [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier()
     torch.cuda.synchronize()
@@ -231,8 +230,6 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    prof = solver.profile_read()
-    solver.profile(False)
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[args.steps])
     if dist is not None:
@@ -245,6 +242,21 @@ def main():
     value = world * unknowns * sum(cycles) / (total_ms / 1e3) / 1e9
     launches = sum(i.kernel_launches for i in infos)
     phi64 = phi.clone()
+
+    # ---- per-kernel durations: the same solves again with CUDA events recorded
+    # on the solve stream around each hot kernel (event records cannot live
+    # inside the captured loop graphs, so this region launches kernels directly)
+    solver.profile(True)
+    prof_steps = max(3, args.steps // 2)
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pa.record(stream)
+    for _ in range(prof_steps):
+        one()
+    pb.record(stream)
+    torch.cuda.synchronize()
+    prof_region_ms = pa.elapsed_time(pb) / prof_steps
+    prof = solver.profile_read()
+    solver.profile(False)
 
     # ---- end to end through the public API with host buffers
     phi_zero_h = torch.zeros_like(rho_h).pin_memory()
@@ -342,6 +354,7 @@ def main():
             "mixed": mixed,
             "roofline": roof,
             "kernels": kernels,
+            "profiled_region_ms_per_step": prof_region_ms,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 2 * nbytes,
                     "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms / args.steps},

@@ -15,8 +15,8 @@
  * Pointers named *_dev are device pointers (cudaMalloc or torch tensors on the
  * current device); pointers named *_host are host pointers.  The caller owns
  * every buffer it passes; the library owns what a handle allocates and frees
- * it in poisson_destroy.  `stream` is a cudaStream_t (NULL = the handle's own
- * stream for solves, the legacy default stream for the op-level calls).
+ * it in poisson_destroy.  `stream` is a cudaStream_t; NULL is CUDA's default
+ * stream, so work is ordered after what the caller enqueued there.
  *
  * Cartesian fields: contiguous, x fastest, extents (n[a] + 2g - 1) per axis,
  * where g = stencil_order / 2 is the stencil radius; node i of axis a (node 0
@@ -93,7 +93,7 @@ typedef struct {
   int32_t nu1, nu2;      /* V(nu1,nu2) pre-/post-smoothing sweeps */
   int32_t max_iter;      /* SOR steps / CG or BiCGSTAB iterations / V-cycles / IR steps */
   int32_t inner_cycles;  /* mixed modes: V-cycles (or Krylov iterations) per IR step */
-  void* stream;          /* cudaStream_t or NULL */
+  void* stream;          /* cudaStream_t; NULL = CUDA's default stream */
 } ps_solve_opts;
 
 typedef struct {
@@ -142,9 +142,31 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
 ps_status poisson_solve(ps_handle h, const double* rho_dev, double* phi_dev, double tol,
                         const ps_solve_opts* opts, ps_info* info);
 
+/* Asynchronous, steppable form of poisson_solve (continuous batching).  The
+ * solve's state stays on the device between calls; its work runs on the
+ * handle's own stream, ordered after what opts->stream held at begin, and
+ * opts->stream waits for the copy-back enqueued by end.  One solve in flight
+ * per handle; phi_dev and rho_dev must stay valid until end.
+ *   begin  validates, enqueues the multipole boundary, right-hand side,
+ *          reference and initial residual (no host synchronisation)
+ *   step   enqueues up to max_iterations more iterations (one CUDA-graph
+ *          launch whose device-side while loop stops at convergence)
+ *   poll   waits for the handle's stream and reports *done (converged, not
+ *          converged or diverged); info (may be NULL) gets the progress
+ *   end    copies the iterate to phi_dev, waits, fills info and returns the
+ *          solve's status exactly as poisson_solve does.
+ * poisson_solve = begin, poll, (step, poll)*, end. */
+ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_dev, double tol,
+                              const ps_solve_opts* opts);
+ps_status poisson_solve_step(ps_handle h, int max_iterations);
+ps_status poisson_solve_poll(ps_handle h, int* done, ps_info* info);
+ps_status poisson_solve_end(ps_handle h, ps_info* info);
+
 /* Solve n independent requests, each with its own handle, density, potential
- * and tolerance, on one stream.  Results equal n separate poisson_solve calls
- * bit for bit; infos[i] receives request i's info.  Handles must be distinct. */
+ * and tolerance.  Each request runs on its handle's stream, so the kernels of
+ * different requests overlap on the GPU.  Results equal n separate
+ * poisson_solve calls bit for bit; infos[i] receives request i's info.
+ * Handles must be distinct. */
 ps_status poisson_solve_batch(ps_handle* hs, const double* const* rho_dev, double* const* phi_dev,
                               const double* tol, int n, const ps_solve_opts* opts,
                               ps_info* infos);

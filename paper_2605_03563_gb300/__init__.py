@@ -110,6 +110,36 @@ class _Handle:
     def __exit__(self, *exc):
         self.close()
 
+    # ---- asynchronous, steppable solves (continuous batching)
+    def begin(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
+              max_iter=100, inner_cycles=1, stream=None):
+        """Start a solve whose state stays on the device; rho/phi must stay alive until end()."""
+        self._opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
+                                      int(nu2), int(max_iter), int(inner_cycles), _stream(stream))
+        self._keep = (rho, phi)
+        check(lib().poisson_solve_begin(self._h, _ptr(rho), _ptr(phi), float(tol),
+                                        C.byref(self._opts)), "poisson_solve_begin")
+
+    def step(self, max_iterations=1):
+        """Enqueue up to max_iterations more iterations (no host synchronisation)."""
+        check(lib().poisson_solve_step(self._h, int(max_iterations)), "poisson_solve_step")
+
+    def poll(self):
+        """Wait for this solve's stream; returns (done, SolveInfo so far)."""
+        done = C.c_int()
+        info = capi.PsInfo()
+        check(lib().poisson_solve_poll(self._h, C.byref(done), C.byref(info)), "poisson_solve_poll")
+        return bool(done.value), SolveInfo.from_c(info, 0)
+
+    def end(self):
+        """Copy the iterate back to phi and return the final SolveInfo."""
+        info = capi.PsInfo()
+        st = lib().poisson_solve_end(self._h, C.byref(info))
+        check(st, "poisson_solve_end", allow=(capi.PS_OK, capi.PS_NOT_CONVERGED, capi.PS_DIVERGED))
+        self._keep = None
+        nmom = (self.lmax + 1) ** 2 if getattr(self, "multipole", False) else 0
+        return SolveInfo.from_c(info, min(nmom, 81))
+
     def _solve(self, rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
                stream, nmom):
         opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),

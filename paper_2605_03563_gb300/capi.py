@@ -61,6 +61,11 @@ SIGNATURES = {
     "poisson_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p), C.POINTER(C.c_double), C.c_int,
                                       C.POINTER(PsSolveOpts), C.POINTER(PsInfo)]),
+    "poisson_solve_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                      C.POINTER(PsSolveOpts)]),
+    "poisson_solve_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "poisson_solve_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(PsInfo)]),
+    "poisson_solve_end": (C.c_int, [C.c_void_p, C.POINTER(PsInfo)]),
     "poisson_destroy": (None, [C.c_void_p]),
     "poisson_last_error": (C.c_char_p, []),
     "poisson_workspace_bytes": (C.c_size_t, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_int]),

@@ -12,6 +12,7 @@
 //
 // Launch geometry of the point kernels: 32 x 8 threads per block over (x, y)
 // and a z-chunk of ZCH nodes per thread.
+#include <algorithm>
 #include <cstdio>
 
 #include "cart_kernels.cuh"
@@ -131,7 +132,8 @@ __device__ __forceinline__ void block_sum_max(double s, double m, double* partia
 }
 
 // ------------------------------------------------------------------ delta pass
-template <int G, bool ISO, typename TI>
+// RED: 0 no reduction, 1 sum of delta^2, 2 sum of delta^2 and max |delta|.
+template <int G, bool ISO, typename TI, int RED>
 __global__ void __launch_bounds__(BX* BY)
     k_delta(Dims d, Coef<typename St<TI>::C> cf, const TI* __restrict__ phi,
             const TI* __restrict__ fs, int dout, void* __restrict__ out, double out_scale,
@@ -144,6 +146,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int k1 = min(k0 + ZCH, G + d.nk());
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
   double s2 = 0.0, mx = 0.0;
+  float s2f = 0.0f, mxf = 0.0f;
   double oscale = out_scale;
   if (st != nullptr) oscale = st->scale_next;
   if (i < G + d.ni() && j < G + d.nj()) {
@@ -156,12 +159,27 @@ __global__ void __launch_bounds__(BX* BY)
         dl = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p)) - S::ld(phi + p);
       }
       double dd = (double)dl;
-      s2 = fma(dd, dd, s2);
-      mx = fmax(mx, fabs(dd));
+      if (RED == 2 && dout != DT_F64) {
+        // refinement pass: the stored inner right-hand side is FP32/BF16, so the
+        // sum of squares and the max run on the FP32 pipe over the scaled value
+        // (O(1) by the choice of the power-of-two scale; exact to undo)
+        const float v = (float)(dd * oscale);
+        s2f = fmaf(v, v, s2f);
+        mxf = fmaxf(mxf, fabsf(v));
+        if (dout == DT_F32) ((float*)out)[p] = v;
+        else ((__nv_bfloat16*)out)[p] = __float2bfloat16_rn(v);
+        continue;
+      }
+      if (RED >= 1) s2 = fma(dd, dd, s2);
+      if (RED == 2) mx = fmax(mx, fabs(dd));
       if (out != nullptr) store_dt<C>(out, dout, p, dd * oscale);
     }
   }
-  if (partials != nullptr) block_sum_max(s2, mx, partials);
+  if (RED == 2 && dout != DT_F64) {
+    s2 += (double)s2f / (oscale * oscale);
+    mx = fmax(mx, (double)mxf / oscale);
+  }
+  if (RED >= 1) block_sum_max(s2, mx, partials);
 }
 
 template <int G, bool ISO, typename TI>
@@ -170,8 +188,16 @@ static cudaError_t delta_t(const Dims& d, const double h[3], int order, const vo
                            const DevState* st, bool zi, double* partials, cudaStream_t s) {
   using C = typename St<TI>::C;
   Coef<C> cf = make_coef<C>(d, h, order);
-  k_delta<G, ISO, TI><<<point_grid(d), dim3(BX, BY), 0, s>>>(
-      d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
+  // the refinement path needs max |delta| for its scale; plain norms need the sum only
+  if (partials == nullptr)
+    k_delta<G, ISO, TI, 0><<<point_grid(d), dim3(BX, BY), 0, s>>>(
+        d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
+  else if (st != nullptr || zi)
+    k_delta<G, ISO, TI, 2><<<point_grid(d), dim3(BX, BY), 0, s>>>(
+        d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
+  else
+    k_delta<G, ISO, TI, 1><<<point_grid(d), dim3(BX, BY), 0, s>>>(
+        d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
   return cudaGetLastError();
 }
 
@@ -504,102 +530,130 @@ cudaError_t launch_apply(const Dims& d, int order, const double h[3], int dt, co
 // ------------------------------------------------------------------ coarsest-level CG
 // One CTA solves -A e = d * fs (zero boundary, e0 = 0) by CG (Sec. 2.1.3: the
 // coarsest level is solved with CG) until ||r|| <= tol ||r0|| or max_iter
-// iterations, entirely in shared memory (x, p, r, q on the full ghosted layout).
-template <int G, bool ISO, typename TF, typename TE>
+// iterations.  Each thread owns up to PPT unknowns and keeps their x, r, q in
+// registers; only the search direction p lives in shared memory (on the full
+// ghosted layout, zero boundary), because the stencil reads neighbours.  Every
+// block reduction is one warp shuffle tree, one barrier, and a shuffle tree
+// over the per-warp values that every warp evaluates identically.
+__device__ __forceinline__ double block_allreduce(double v, double* buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) buf[warp] = v;
+  __syncthreads();
+  double t = lane < nw ? buf[lane] : 0.0;
+  return warp_sum(t);
+}
+
+template <int G, bool ISO, typename TF, typename TE, int PPT>
 __global__ void __launch_bounds__(1024)
     k_coarse_cg(Dims d, Coef<double> cf, const TF* __restrict__ fs, TE* __restrict__ e,
                 double tol, int max_iter, DevState* __restrict__ st) {
-  extern __shared__ double sm[];
-  __shared__ double red[32];
-  __shared__ double bc;
-  const long long n = d.size();
-  double* x = sm;
-  double* p = x + n;
-  double* r = p + n;
-  double* q = r + n;
+  extern __shared__ double p[];
+  __shared__ double red[2][32];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int ni = d.ni(), nj = d.nj(), nk = d.nk();
   const int nint = ni * nj * nk;
+  const long long n = d.size();
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
-  for (long long u = tid; u < 4 * n; u += nthr) sm[u] = 0.0;
-  __syncthreads();
-  auto pos = [&](int u) -> long long {
-    int i = u % ni, t = u / ni;
-    int j = t % nj, k = t / nj;
-    return d.at(i + G, j + G, k + G);
-  };
-  auto bsum = [&](double v) -> double {
-    double a[1] = {v};
-    block_sum<1>(a, red);
-    if (tid == 0) bc = a[0];
-    __syncthreads();
-    double out = bc;
-    __syncthreads();
-    return out;
-  };
-  double loc = 0.0;
-  for (int u = tid; u < nint; u += nthr) {
-    long long c = pos(u);
-    double b = cf.d * (double)St<TF>::ld(fs + c);
-    r[c] = b;
-    p[c] = b;
-    loc = fma(b, b, loc);
+  for (long long u = tid; u < n; u += nthr) p[u] = 0.0;
+  long long c[PPT];
+  double x[PPT], r[PPT], q[PPT];
+  bool own[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    const int u = tid + k * nthr;
+    own[k] = u < nint;
+    const int uu = own[k] ? u : 0;
+    const int i = uu % ni, t = uu / ni;
+    c[k] = d.at(i + G, t % nj + G, t / nj + G);
+    x[k] = 0.0;
+    r[k] = 0.0;
+    q[k] = 0.0;
   }
-  double rr = bsum(loc);
+  __syncthreads();
+  double loc = 0.0;
+#pragma unroll
+  for (int k = 0; k < PPT; k++) {
+    if (own[k]) {
+      const double b = cf.d * (double)St<TF>::ld(fs + c[k]);
+      r[k] = b;
+      p[c[k]] = b;
+      loc = fma(b, b, loc);
+    }
+  }
+  double rr = block_allreduce(loc, red[0]);
   const double ref = sqrt(rr);
   int it = 0;
   if (ref > 0.0) {
     while (it < max_iter) {
+      __syncthreads();   // p complete
       loc = 0.0;
-      for (int u = tid; u < nint; u += nthr) {
-        long long c = pos(u);
-        double v = cf.d * (p[c] - gs_value<G, ISO>(p, c, sy, sz, cf, 0.0));
-        q[c] = v;
-        loc = fma(p[c], v, loc);
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        if (own[k]) {
+          const double pc = p[c[k]];
+          q[k] = cf.d * (pc - gs_value<G, ISO>(p, c[k], sy, sz, cf, 0.0));
+          loc = fma(pc, q[k], loc);
+        }
       }
-      double pq = bsum(loc);
-      double alpha = rr / pq;
+      const double pq = block_allreduce(loc, red[1]);
+      const double alpha = rr / pq;
       loc = 0.0;
-      for (int u = tid; u < nint; u += nthr) {
-        long long c = pos(u);
-        x[c] = fma(alpha, p[c], x[c]);
-        double rv = fma(-alpha, q[c], r[c]);
-        r[c] = rv;
-        loc = fma(rv, rv, loc);
+#pragma unroll
+      for (int k = 0; k < PPT; k++) {
+        if (own[k]) {
+          x[k] = fma(alpha, p[c[k]], x[k]);
+          r[k] = fma(-alpha, q[k], r[k]);
+          loc = fma(r[k], r[k], loc);
+        }
       }
-      double rrn = bsum(loc);
+      const double rrn = block_allreduce(loc, red[0]);
       it++;
       if (sqrt(rrn) <= tol * ref) break;
-      double beta = rrn / rr;
-      for (int u = tid; u < nint; u += nthr) {
-        long long c = pos(u);
-        p[c] = fma(beta, p[c], r[c]);
-      }
+      const double beta = rrn / rr;
+      // every thread has passed the stencil reads (barrier inside the reductions)
+#pragma unroll
+      for (int k = 0; k < PPT; k++)
+        if (own[k]) p[c[k]] = fma(beta, p[c[k]], r[k]);
       rr = rrn;
-      __syncthreads();
     }
   }
-  for (int u = tid; u < nint; u += nthr) {
-    long long c = pos(u);
-    St<TE>::st(e + c, (typename St<TE>::C)x[c]);
-  }
+#pragma unroll
+  for (int k = 0; k < PPT; k++)
+    if (own[k]) St<TE>::st(e + c[k], (typename St<TE>::C)x[k]);
   if (tid == 0 && st != nullptr) {
     st->coarse_iter_last = it;
     st->coarse_iter_total += it;
   }
 }
 
-size_t coarse_cg_smem_bytes(const Dims& d) { return 4 * (size_t)d.size() * sizeof(double); }
+size_t coarse_cg_smem_bytes(const Dims& d) { return (size_t)d.size() * sizeof(double); }
 
 template <int G, bool ISO, typename TF, typename TE>
 static cudaError_t coarse_t(const Dims& d, const double h[3], int order, const void* fs, void* e,
                             double tol, int max_iter, DevState* st, cudaStream_t s) {
   Coef<double> cf = make_coef<double>(d, h, order);
-  size_t smem = coarse_cg_smem_bytes(d);
-  auto kern = k_coarse_cg<G, ISO, TF, TE>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  kern<<<1, 1024, smem, s>>>(d, cf, (const TF*)fs, (TE*)e, tol, max_iter, st);
+  const size_t smem = coarse_cg_smem_bytes(d);
+  const int nint = d.ni() * d.nj() * d.nk();
+  int ppt = 1;
+  while (ppt < 8 && (nint + ppt - 1) / ppt > 1024) ppt *= 2;
+  if ((nint + ppt - 1) / ppt > 1024) return cudaErrorInvalidValue;
+  const int nthr = std::max(32, (((nint + ppt - 1) / ppt) + 31) / 32 * 32);
+  cudaError_t err;
+#define PS_COARSE_LAUNCH(P)                                                                   \
+  {                                                                                           \
+    auto kern = k_coarse_cg<G, ISO, TF, TE, P>;                                               \
+    if (smem > 48 * 1024 &&                                                                   \
+        (err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                    (int)smem)) != cudaSuccess)                               \
+      return err;                                                                             \
+    kern<<<1, nthr, smem, s>>>(d, cf, (const TF*)fs, (TE*)e, tol, max_iter, st);              \
+  }
+  if (ppt == 1) PS_COARSE_LAUNCH(1)
+  else if (ppt == 2) PS_COARSE_LAUNCH(2)
+  else if (ppt == 4) PS_COARSE_LAUNCH(4)
+  else PS_COARSE_LAUNCH(8)
+#undef PS_COARSE_LAUNCH
   return cudaGetLastError();
 }
 
@@ -623,8 +677,53 @@ cudaError_t launch_coarse_cg(const Dims& d, int order, const double h[3], int dt
 }
 
 // ------------------------------------------------------------------ norm finisher
+// Set the enclosing graph's while-condition (chunk > 0 marks a graph body):
+// continue while not done and below the iteration budget of this step, so
+// every graph launch ends after a bounded number of iterations.
+__device__ __forceinline__ void set_loop(const DevState* st, unsigned long long cond, int chunk) {
+  if (chunk > 0) {
+    const unsigned int more = (st->done == DONE_NO && st->iter < st->chunk_end) ? 1u : 0u;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, more);
+  }
+}
+
+__global__ void k_set_budget(DevState* st, int k) { st->chunk_end = st->iter + k; }
+
+__global__ void k_init_state(DevState* st, double tol, int max_iter) {
+  DevState z;
+  memset(&z, 0, sizeof(z));
+  z.tol = tol;
+  z.max_iter = max_iter;
+  z.scale_cur = 1.0;
+  z.scale_next = 1.0;
+  z.ref = 1.0;
+  *st = z;
+}
+
+cudaError_t launch_init_state(DevState* st, double tol, int max_iter, cudaStream_t s) {
+  k_init_state<<<1, 1, 0, s>>>(st, tol, max_iter);
+  return cudaGetLastError();
+}
+
+// First node of a loop graph: open the while loop only if there is work left.
+__global__ void k_loop_gate(const DevState* st, unsigned long long cond) {
+  const unsigned int go = (st->done == DONE_NO && st->iter < st->chunk_end) ? 1u : 0u;
+  cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);
+}
+
+cudaError_t launch_loop_gate(const DevState* st, unsigned long long cond, cudaStream_t s) {
+  k_loop_gate<<<1, 1, 0, s>>>(st, cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_budget(DevState* st, int k, cudaStream_t s) {
+  k_set_budget<<<1, 1, 0, s>>>(st, k);
+  return cudaGetLastError();
+}
+
 __global__ void k_finish_norm(const double* __restrict__ partials, int nblocks, double dscale,
-                              int mode, DevState* __restrict__ st) {
+                              int mode, DevState* __restrict__ st, unsigned long long cond,
+                              int chunk) {
   __shared__ double red[64];
   double s = 0.0, m = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -650,7 +749,10 @@ __global__ void k_finish_norm(const double* __restrict__ partials, int nblocks, 
     st->scale_next = m > 0.0 ? exp2(-rint(log2(m))) : 1.0;
     return;
   }
-  if (st->done && mode == 2) return;
+  if (st->done && mode == 2) {
+    set_loop(st, cond, chunk);
+    return;
+  }
   st->rr = rr;
   st->amax = m;
   const double rel = sqrt(rr) / st->ref;
@@ -669,11 +771,12 @@ __global__ void k_finish_norm(const double* __restrict__ partials, int nblocks, 
   if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
   else if (rel <= st->tol) st->done = DONE_CONVERGED;
   else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+  set_loop(st, cond, chunk);
 }
 
 cudaError_t launch_finish_norm(const double* partials, int nblocks, double dscale, int mode,
-                               DevState* st, cudaStream_t s) {
-  k_finish_norm<<<1, 256, 0, s>>>(partials, nblocks, dscale, mode, st);
+                               DevState* st, cudaStream_t s, unsigned long long cond, int chunk) {
+  k_finish_norm<<<1, 1024, 0, s>>>(partials, nblocks, dscale, mode, st, cond, chunk);
   return cudaGetLastError();
 }
 
@@ -765,9 +868,12 @@ __global__ void __launch_bounds__(BX* BY)
 
 // which 0: alpha = rr / (p.q) ; which 1: convergence check, beta ; which 2: init
 __global__ void k_cg_scalar(const double* __restrict__ partials, int nblocks, int which,
-                            DevState* __restrict__ st) {
+                            DevState* __restrict__ st, unsigned long long cond, int chunk) {
   __shared__ double red[32];
-  if (which != 2 && st->done) return;
+  if (which != 2 && st->done) {
+    if (which == 1 && threadIdx.x == 0) set_loop(st, cond, chunk);
+    return;
+  }
   double s = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[2 * b];
   double a[1] = {s};
@@ -787,6 +893,7 @@ __global__ void k_cg_scalar(const double* __restrict__ partials, int nblocks, in
     if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
     else if (rel <= st->tol) st->done = DONE_CONVERGED;
     else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+    set_loop(st, cond, chunk);
   } else {
     st->rho = S;
     st->rr = S;
@@ -843,8 +950,8 @@ cudaError_t launch_cg_pupdate(const Dims& d, const double* r, double* p, const D
 }
 
 cudaError_t launch_cg_scalar(const double* partials, int nblocks, int which, DevState* st,
-                             cudaStream_t s) {
-  k_cg_scalar<<<1, 256, 0, s>>>(partials, nblocks, which, st);
+                             cudaStream_t s, unsigned long long cond, int chunk) {
+  k_cg_scalar<<<1, 1024, 0, s>>>(partials, nblocks, which, st, cond, chunk);
   return cudaGetLastError();
 }
 

@@ -68,8 +68,11 @@ size_t coarse_cg_smem_bytes(const Dims& d);
 // Sum the per-block partials of a delta pass into the state and decide
 // convergence.  mode: 0 = record reference norm, 1 = record initial residual,
 // 2 = iteration check (iter += 1), 3 = IR outer check (also sets the scale).
+// cond/chunk: when chunk > 0 the kernel runs inside a CUDA-graph while loop and
+// sets its condition (continue while not done and iter % chunk != 0).
 cudaError_t launch_finish_norm(const double* partials, int nblocks, double dscale, int mode,
-                               DevState* st, cudaStream_t s);
+                               DevState* st, cudaStream_t s, unsigned long long cond = 0,
+                               int chunk = 0);
 
 // ---------------------------------------------------------------- CG (FP64)
 // r = d * delta(phi)  (SPD residual), p = r, partials of r.r
@@ -87,8 +90,15 @@ cudaError_t launch_cg_pupdate(const Dims& d, const double* r, double* p, const D
                               cudaStream_t s);
 // scalar steps: which = 0: alpha = rho/pq ; which = 1: convergence + beta
 cudaError_t launch_cg_scalar(const double* partials, int nblocks, int which, DevState* st,
-                             cudaStream_t s);
+                             cudaStream_t s, unsigned long long cond = 0, int chunk = 0);
 
 int cart_partials_count(const Dims& d);
+
+// st->chunk_end = st->iter + k: iteration budget of the next loop-graph launch
+cudaError_t launch_set_budget(DevState* st, int k, cudaStream_t s);
+// reset a solve's state on the device (no host round trip)
+cudaError_t launch_init_state(DevState* st, double tol, int max_iter, cudaStream_t s);
+// first node of a loop graph: sets the while condition from the state
+cudaError_t launch_loop_gate(const DevState* st, unsigned long long cond, cudaStream_t s);
 
 }  // namespace ps

@@ -138,34 +138,58 @@ void build_multipole_tables(int L, MultipoleTables* t) {
 }
 
 // ------------------------------------------------------------------ moment kernels
+// Pass 1: x-row moments.  One warp per row (4 rows per warp, 8 warps per block);
+// the powers x_i^a (a <= L) of the block's rows come from a shared table when
+// it fits (one FP64 FMA per node and power), else from a running product.
+constexpr int ROWS_PER_BLOCK = 32;
+
+template <int L, bool TABLE>
 __global__ void __launch_bounds__(256)
-    k_mp_rows(Dims d, double x0, double hx, double dV, int L, const double* __restrict__ rho,
+    k_mp_rows(Dims d, double x0, double hx, double dV, const double* __restrict__ rho,
               double* __restrict__ rowmom) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int u = blockIdx.x * 8 + warp;            // row id = k * nj + j (interior)
-  const int nrows = d.nj() * d.nk();
-  if (u >= nrows) return;
-  const int j = u % d.nj(), k = u / d.nj();
-  const int g = d.g;
-  double s[MAXL + 1];
+  extern __shared__ double X[];   // [(L+1) * ni] when TABLE
+  const int ni = d.ni();
+  if (TABLE) {
+    for (int t = threadIdx.x; t < ni; t += blockDim.x) {
+      const double x = fma((double)(t + 1), hx, x0);
+      double p = 1.0;
 #pragma unroll
-  for (int a = 0; a <= MAXL; a++) s[a] = 0.0;
-  const long long row = d.at(g, j + g, k + g);
-  for (int i = lane; i < d.ni(); i += 32) {
-    const double x = fma((double)(i + 1), hx, x0);   // node i+1 relative to the origin
-    double p = rho[row + i] * dV;
-#pragma unroll
-    for (int a = 0; a <= MAXL; a++) {
-      if (a <= L) {
-        s[a] += p;
+      for (int a = 0; a <= L; a++) {
+        X[a * ni + t] = p;
         p *= x;
       }
     }
+    __syncthreads();
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrows = d.nj() * d.nk();
+  const int g = d.g;
+  for (int q = 0; q < ROWS_PER_BLOCK / 8; q++) {
+    const int u = blockIdx.x * ROWS_PER_BLOCK + q * 8 + warp;   // row id = k * nj + j
+    if (u >= nrows) break;
+    const int j = u % d.nj(), k = u / d.nj();
+    const long long row = d.at(g, j + g, k + g);
+    double s[L + 1];
 #pragma unroll
-  for (int a = 0; a <= MAXL; a++) {
-    if (a <= L) {
-      double v = warp_sum(s[a]);
+    for (int a = 0; a <= L; a++) s[a] = 0.0;
+    for (int i = lane; i < ni; i += 32) {
+      const double w = rho[row + i] * dV;
+      if (TABLE) {
+#pragma unroll
+        for (int a = 0; a <= L; a++) s[a] = fma(w, X[a * ni + i], s[a]);
+      } else {
+        const double x = fma((double)(i + 1), hx, x0);
+        double p = w;
+#pragma unroll
+        for (int a = 0; a <= L; a++) {
+          s[a] += p;
+          p *= x;
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a <= L; a++) {
+      const double v = warp_sum(s[a]);
       if (lane == 0) rowmom[(long long)u * (L + 1) + a] = v;
     }
   }
@@ -176,45 +200,62 @@ __device__ __forceinline__ int pair_index(int a, int b, int L) {
   return a * (L + 1) - a * (a - 1) / 2 + b;
 }
 
-__global__ void k_mp_planes(Dims d, double y0, double hy, int L, const double* __restrict__ rowmom,
-                            double* __restrict__ planemom) {
-  const int k = blockIdx.x;
+// Pass 2: y-moments within each plane.  One block per plane; warp w handles
+// pairs w, w+8, ...; lanes stride over the rows; y^b from a shared table.
+__global__ void __launch_bounds__(256)
+    k_mp_planes(Dims d, double y0, double hy, int L, const double* __restrict__ rowmom,
+                double* __restrict__ planemom) {
+  extern __shared__ double Y[];   // [(L+1) * nj]
+  const int nj = d.nj(), k = blockIdx.x;
+  for (int t = threadIdx.x; t < nj; t += blockDim.x) {
+    const double y = fma((double)(t + 1), hy, y0);
+    double p = 1.0;
+    for (int b = 0; b <= L; b++) {
+      Y[b * nj + t] = p;
+      p *= y;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int P2 = (L + 1) * (L + 2) / 2;
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    // decode pair t -> (a, b)
+  for (int t = warp; t < P2; t += 8) {
     int a = 0, rem = t;
     while (rem > L - a) { rem -= L - a + 1; a++; }
     const int b = rem;
     double acc = 0.0;
-    for (int j = 0; j < d.nj(); j++) {
-      const double y = fma((double)(j + 1), hy, y0);
-      double yb = 1.0;
-      for (int e = 0; e < b; e++) yb *= y;
-      acc = fma(rowmom[((long long)k * d.nj() + j) * (L + 1) + a], yb, acc);
-    }
-    planemom[(long long)k * P2 + pair_index(a, b, L)] = acc;
+    for (int j = lane; j < nj; j += 32)
+      acc = fma(rowmom[((long long)k * nj + j) * (L + 1) + a], Y[b * nj + j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) planemom[(long long)k * P2 + pair_index(a, b, L)] = acc;
   }
 }
 
-__global__ void k_mp_final(Dims d, double z0, double hz, int L, const double* __restrict__ planemom,
-                           const int* __restrict__ off, const int* __restrict__ mono,
-                           const double* __restrict__ val, double* __restrict__ q) {
+// Pass 3: z-moments across planes (warp per monomial, lanes over planes),
+// then the sparse map from monomials to q_lm.
+__global__ void __launch_bounds__(1024)
+    k_mp_final(Dims d, double z0, double hz, int L, const double* __restrict__ planemom,
+               const int* __restrict__ off, const int* __restrict__ mono,
+               const double* __restrict__ val, double* __restrict__ q) {
   extern __shared__ double M[];   // (L+1)^3
   const int W = L + 1;
   const int P2 = W * (W + 1) / 2;
-  for (int t = threadIdx.x; t < W * W * W; t += blockDim.x) {
+  const int nk = d.nk();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < W * W * W; t += blockDim.x) M[t] = 0.0;
+  __syncthreads();
+  for (int t = warp; t < W * W * W; t += nw) {
     const int c = t % W, b = (t / W) % W, a = t / (W * W);
+    if (a + b + c > L) continue;
+    const int pi = pair_index(a, b, L);
     double acc = 0.0;
-    if (a + b + c <= L) {
-      const int pi = pair_index(a, b, L);
-      for (int k = 0; k < d.nk(); k++) {
-        const double z = fma((double)(k + 1), hz, z0);
-        double zc = 1.0;
-        for (int e = 0; e < c; e++) zc *= z;
-        acc = fma(planemom[(long long)k * P2 + pi], zc, acc);
-      }
+    for (int k = lane; k < nk; k += 32) {
+      const double z = fma((double)(k + 1), hz, z0);
+      double zc = 1.0;
+      for (int e = 0; e < c; e++) zc *= z;
+      acc = fma(planemom[(long long)k * P2 + pi], zc, acc);
     }
-    M[t] = acc;
+    acc = warp_sum(acc);
+    if (lane == 0) M[t] = acc;
   }
   __syncthreads();
   for (int lm = threadIdx.x; lm < W * W; lm += blockDim.x) {
@@ -349,15 +390,47 @@ void cart_multipole_free(CartMultipoleDev* m) {
   *m = CartMultipoleDev();
 }
 
+template <int L>
+static void rows_launch(const Dims& d, double x0, double hx, double dV, const double* rho,
+                        double* rowmom, cudaStream_t s) {
+  const int nrows = d.nj() * d.nk();
+  const unsigned blocks = (nrows + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
+  const size_t table = (size_t)(L + 1) * d.ni() * sizeof(double);
+  if (table <= 48 * 1024)
+    k_mp_rows<L, true><<<blocks, 256, table, s>>>(d, x0, hx, dV, rho, rowmom);
+  else
+    k_mp_rows<L, false><<<blocks, 256, 0, s>>>(d, x0, hx, dV, rho, rowmom);
+}
+
 cudaError_t launch_cart_moments(const Dims& d, const double lo[3], const double h[3],
                                 const double origin[3], const double* rho, CartMultipoleDev* m,
                                 cudaStream_t s) {
   const int L = m->lmax;
   if (L < 0 || L > MAXL) return cudaErrorInvalidValue;
+  if ((size_t)(L + 1) * d.nj() * sizeof(double) > 48 * 1024) return cudaErrorInvalidValue;
   const double dV = h[0] * h[1] * h[2];
-  const int nrows = d.nj() * d.nk();
-  k_mp_rows<<<(nrows + 7) / 8, 256, 0, s>>>(d, lo[0] - origin[0], h[0], dV, L, rho, m->rowmom);
-  k_mp_planes<<<d.nk(), 160, 0, s>>>(d, lo[1] - origin[1], h[1], L, m->rowmom, m->planemom);
+  const double x0 = lo[0] - origin[0];
+  switch (L) {
+    case 0: rows_launch<0>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 1: rows_launch<1>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 2: rows_launch<2>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 3: rows_launch<3>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 4: rows_launch<4>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 5: rows_launch<5>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 6: rows_launch<6>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 7: rows_launch<7>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 8: rows_launch<8>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 9: rows_launch<9>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 10: rows_launch<10>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 11: rows_launch<11>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 12: rows_launch<12>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 13: rows_launch<13>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 14: rows_launch<14>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    case 15: rows_launch<15>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    default: rows_launch<16>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+  }
+  const size_t ytab = (size_t)(L + 1) * d.nj() * sizeof(double);
+  k_mp_planes<<<d.nk(), 256, ytab, s>>>(d, lo[1] - origin[1], h[1], L, m->rowmom, m->planemom);
   const int W = L + 1;
   size_t smem = (size_t)W * W * W * sizeof(double);
   k_mp_final<<<1, 1024, smem, s>>>(d, lo[2] - origin[2], h[2], L, m->planemom, m->off, m->mono,

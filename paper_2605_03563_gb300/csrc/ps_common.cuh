@@ -124,6 +124,7 @@ struct DevState {
   int max_iter;
   int done;           // 1 converged, 2 not converged (max_iter), 3 diverged
   int coarse_iter_last;
+  int chunk_end;      // a captured loop continues while iter < chunk_end (set per step)
   int early;          // BiCGSTAB: converged at the s check of this iteration
   long long coarse_iter_total;
   long long inner_cycles;

@@ -17,6 +17,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -57,7 +59,10 @@ struct Hier {
 };
 
 static const int KRYLOV_CHUNK = 16;
-static const double COARSE_TOL = 1e-12;
+// Coarsest-level CG tolerance: Sec. 2.1.3 -- a relative accuracy of about the
+// V-cycle convergence factor (~0.075 here) keeps the asymptotic rate; 1e-2 stays
+// an order of magnitude below it.
+static const double COARSE_TOL = 1e-2;
 
 }  // namespace ps
 
@@ -72,6 +77,33 @@ static const char* kProfNames[PC_COUNT] = {
   "sweep_colour_finest", "residual_finest", "restrict_finest", "prolong_finest", "norm_finest",
   "coarse_cg", "multipole_moments", "multipole_boundary", "sweep_colour_coarse", "ir_correct",
   "krylov_vector"};
+
+// One iteration of a solve, enqueued on a stream; cond/chunk are set when it is
+// being captured into a loop graph.
+using Body = std::function<cudaError_t(unsigned long long, int, cudaStream_t)>;
+
+// The solve in flight on a handle (begin .. end).
+struct Active {
+  bool on = false;
+  ps_solve_opts o{};
+  double tol = 0.0;
+  const double* rho = nullptr;
+  double* phi_user = nullptr;
+  cudaStream_t caller = nullptr;
+  std::string key;
+  Body body;
+  int chunk = 32, plain_chunk = 1;
+  bool host_driven = false, plain_steps = false;
+  long long body_kernels = 0, inner_total = 0;
+  int inner_per_iter = 0, inner_max = 400;
+  double sph_fscale = 0.0;
+};
+
+// A captured iteration body inside a CUDA-graph while loop.
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long body_kernels = 0;
+};
 
 struct ProfRec {
   int cls;
@@ -118,6 +150,14 @@ struct ps_ctx {
   std::vector<cudaEvent_t> ev_pool;
   int prof_open = -1;
   long long nlaunch = 0;   // kernels launched by the current solve
+  // captured loop bodies (keyed by method and parameters) and their capture stream
+  std::map<std::string, LoopGraph> graphs;
+  cudaStream_t cap = nullptr;
+  double* phi0 = nullptr;  // internal finest-level potential (Cartesian) / unknowns (spherical)
+  float* ir_e = nullptr;   // spherical refinement: inner correction
+  Active act;
+  DevState* st_active = nullptr;   // the state the loop gate reads (= st)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -313,7 +353,8 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
 }
 
 // Convergence pass on the finest FP64 level (optionally storing the IR inner RHS).
-cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cudaStream_t s) {
+cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cudaStream_t s,
+                      unsigned long long cond = 0, int chunk = 0) {
   const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
   const int G = h->order / 2;
   const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
@@ -322,25 +363,11 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
                       : launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, false, h->partials, nullptr, s);
   prof_end(h, s);
   if (e != cudaSuccess) return e;
-  return (h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), dd, mode, h->st, s));
+  return (h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), dd, mode, h->st, s, cond, chunk));
 }
 
 ps_status read_state(ps_ctx* h, cudaStream_t s) {
   TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  TRY(cudaStreamSynchronize(s));
-  return PS_OK;
-}
-
-ps_status reset_state(ps_ctx* h, DevState* dst, DevState* hst, double tol, int max_iter,
-                      cudaStream_t s) {
-  TRY(cudaStreamSynchronize(s));
-  memset(hst, 0, sizeof(DevState));
-  hst->tol = tol;
-  hst->max_iter = max_iter;
-  hst->scale_cur = 1.0;
-  hst->scale_next = 1.0;
-  hst->ref = 1.0;
-  TRY(cudaMemcpyAsync(dst, hst, sizeof(DevState), cudaMemcpyHostToDevice, s));
   TRY(cudaStreamSynchronize(s));
   return PS_OK;
 }
@@ -355,15 +382,16 @@ ps_status ensure_partials(ps_ctx* h, int nblk) {
 }
 
 // ------------------------------------------------------------------ Cartesian solves
+// Multipole boundary (t_mp), scaled right-hand side, state reset and reference
+// norm, all enqueued on s without a host round trip.
 ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, int max_iter,
-                       cudaStream_t s, double* fscale_out) {
-  // multipole boundary
+                       cudaStream_t s) {
   TRY(cudaEventRecord(h->ev[0], s));
   if (h->bc.outer == PS_BC_MULTIPOLE) {
     const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
     const double nf = (double)h->d0.size() - n;
     const double W = h->lmax + 1.0;
-    prof_begin(h, PC_MOMENTS, n * 8.0, n * 2.0 * W, 1, s);
+    prof_begin(h, PC_MOMENTS, n * 8.0, n * W, 1, s);
     cudaError_t e = (h->nlaunch += 3, launch_cart_moments(h->d0, h->grid.lo, h->h0, h->bc.origin, rho, &h->mp, s));
     prof_end(h, s);
     TRY(e);
@@ -375,80 +403,90 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
   TRY(cudaEventRecord(h->ev[1], s));
   Coef<double> cf = make_coef<double>(h->d0, h->h0, h->order);
   const double fscale = -4.0 * M_PI * h->bc.G * cf.inv_d;
-  *fscale_out = fscale;
   TRY((h->nlaunch += 1, launch_scale_rhs(h->d0, fscale, rho, DT_F64, h->fs64, s)));
-  ps_status st = reset_state(h, h->st, h->hst, tol, max_iter, s);
-  if (st != PS_OK) return st;
+  TRY((h->nlaunch += 1, launch_init_state(h->st, tol, max_iter, s)));
   // reference norm ||f - A phi0||, phi0 = boundary data only
   TRY((h->nlaunch += 1, launch_delta(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, DT_F64, nullptr, 1.0, true, h->partials, nullptr, s)));
   TRY((h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), cf.d, 0, h->st, s)));
   return PS_OK;
 }
 
-ps_status cart_mg64(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s) {
+static const int MG_CHUNK = 32, KRYLOV_GRAPH_CHUNK = 64;
+
+// Each begin_* enqueues the initial residual pass and installs the iteration
+// body (one V-cycle / refinement step / SOR step / Krylov iteration) that the
+// step calls repeat.
+ps_status begin_mg64(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   ps_status r = build_hier(h, 0, &h->h64);
   if (r != PS_OK) return r;
-  Hier& H = h->h64;
-  H.lv[0].phi = phi;
+  Hier* H = &h->h64;
+  double* phi = h->phi0;
+  H->lv[0].phi = phi;
   TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
-  if ((r = read_state(h, s)) != PS_OK) return r;
-  while (h->hst->done == DONE_NO) {
-    TRY(vcycle(h, H, 0, o->nu1, o->nu2, s));
-    TRY(norm_pass(h, phi, 2, DT_F64, nullptr, s));
-    if ((r = read_state(h, s)) != PS_OK) return r;
-  }
+  const int nu1 = o->nu1, nu2 = o->nu2;
+  h->act.body = [h, H, phi, nu1, nu2](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    cudaError_t e = vcycle(h, *H, 0, nu1, nu2, q);
+    if (e != cudaSuccess) return e;
+    return norm_pass(h, phi, 2, DT_F64, nullptr, q, cond, chunk);
+  };
+  h->act.key = "mg64:" + std::to_string(nu1) + ":" + std::to_string(nu2);
+  h->act.chunk = MG_CHUNK;
+  h->act.plain_chunk = 1;
   return PS_OK;
 }
 
-ps_status cart_ir(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s) {
+ps_status begin_ir(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   const int p = o->prec == PS_MIXED_BF16 ? 1 : 0;
   ps_status r = build_hier(h, p + 1, &h->hmx[p]);
   if (r != PS_OK) return r;
-  Hier& H = h->hmx[p];
-  Level& L0 = H.lv[0];
+  Hier* H = &h->hmx[p];
+  Level* L0 = &H->lv[0];
+  double* phi = h->phi0;
   const int inner = std::max(1, o->inner_cycles);
-  TRY(norm_pass(h, phi, 1, L0.dt, L0.fs, s));
-  if ((r = read_state(h, s)) != PS_OK) return r;
-  long long cycles = 0;
-  while (h->hst->done == DONE_NO) {
-    TRY(cudaMemsetAsync(L0.phi, 0, (size_t)L0.d.size() * dt_size(L0.dt), s));
-    for (int c = 0; c < inner; c++) TRY(vcycle(h, H, 0, o->nu1, o->nu2, s));
-    cycles += inner;
-    {
-      const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
-      prof_begin(h, PC_CORRECT0, n * (16.0 + dt_size(L0.dt)), n * 2.0, 1, s);
-      cudaError_t e = (h->nlaunch += 1, launch_correct(h->d0, L0.dt, L0.phi, 1.0, phi, h->st, s));
-      prof_end(h, s);
-      TRY(e);
-    }
-    TRY(norm_pass(h, phi, 2, L0.dt, L0.fs, s));
-    if ((r = read_state(h, s)) != PS_OK) return r;
-  }
-  h->hst->inner_cycles = cycles;
+  TRY(norm_pass(h, phi, 1, L0->dt, L0->fs, s));
+  const int nu1 = o->nu1, nu2 = o->nu2;
+  h->act.body = [h, H, L0, phi, nu1, nu2, inner](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(L0->phi, 0, (size_t)L0->d.size() * dt_size(L0->dt), q);
+    for (int c = 0; c < inner && e == cudaSuccess; c++) e = vcycle(h, *H, 0, nu1, nu2, q);
+    if (e != cudaSuccess) return e;
+    const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+    prof_begin(h, PC_CORRECT0, n * (16.0 + dt_size(L0->dt)), n * 2.0, 1, q);
+    e = (h->nlaunch += 1, launch_correct(h->d0, L0->dt, L0->phi, 1.0, phi, h->st, q));
+    prof_end(h, q);
+    if (e != cudaSuccess) return e;
+    return norm_pass(h, phi, 2, L0->dt, L0->fs, q, cond, chunk);
+  };
+  h->act.key = "ir" + std::to_string(p) + ":" + std::to_string(nu1) + ":" + std::to_string(nu2) +
+               ":" + std::to_string(inner);
+  h->act.chunk = MG_CHUNK;
+  h->act.plain_chunk = 1;
+  h->act.inner_per_iter = inner;
   return PS_OK;
 }
 
-ps_status cart_sor(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s) {
-  ps_status r;
+ps_status begin_sor(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
+  double* phi = h->phi0;
+  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
   Level L0;
   L0.d = h->d0;
   for (int a = 0; a < 3; a++) L0.h[a] = h->h0[a];
   L0.phi = phi;
   L0.fs = h->fs64;
-  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
-  if ((r = read_state(h, s)) != PS_OK) return r;
-  while (h->hst->done == DONE_NO) {
-    for (int q = 0; q < KRYLOV_CHUNK; q++) {
-      TRY(sweep_level(h, L0, 0, o->omega, h->st, s));
-      TRY(norm_pass(h, phi, 2, DT_F64, nullptr, s));
-    }
-    if ((r = read_state(h, s)) != PS_OK) return r;
-  }
+  const double omega = o->omega;
+  h->act.body = [h, L0, phi, omega](unsigned long long cond, int chunk, cudaStream_t q) mutable -> cudaError_t {
+    cudaError_t e = sweep_level(h, L0, 0, omega, h->st, q);
+    if (e != cudaSuccess) return e;
+    return norm_pass(h, phi, 2, DT_F64, nullptr, q, cond, chunk);
+  };
+  char key[64];
+  snprintf(key, sizeof(key), "sor:%.17g", omega);
+  h->act.key = key;
+  h->act.chunk = KRYLOV_GRAPH_CHUNK;
+  h->act.plain_chunk = KRYLOV_CHUNK;
   return PS_OK;
 }
 
-ps_status cart_cg(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s) {
-  (void)o;
+ps_status begin_cg(ps_ctx* h, cudaStream_t s) {
   ps_status r;
   const size_t n = (size_t)h->d0.size();
   if (!h->cg_r) {
@@ -456,20 +494,25 @@ ps_status cart_cg(ps_ctx* h, double* phi, const ps_solve_opts* o, cudaStream_t s
     if ((r = alloc_zero((void**)&h->cg_p, n * 8, &h->bytes)) != PS_OK) return r;
     if ((r = alloc_zero((void**)&h->cg_q, n * 8, &h->bytes)) != PS_OK) return r;
   }
+  double* phi = h->phi0;
   const int nb = cart_partials_count(h->d0);
   TRY((h->nlaunch += 1, launch_cg_init(h->d0, h->order, h->h0, phi, h->fs64, h->cg_r, h->cg_p, h->partials, nullptr, s)));
   TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 2, h->st, s)));
-  if ((r = read_state(h, s)) != PS_OK) return r;
-  while (h->hst->done == DONE_NO) {
-    for (int q = 0; q < KRYLOV_CHUNK; q++) {
-      TRY((h->nlaunch += 1, launch_cg_apply(h->d0, h->order, h->h0, h->cg_p, h->cg_q, h->partials, h->st, s)));
-      TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 0, h->st, s)));
-      TRY((h->nlaunch += 1, launch_cg_update(h->d0, phi, h->cg_r, h->cg_p, h->cg_q, h->partials, h->st, s)));
-      TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 1, h->st, s)));
-      TRY((h->nlaunch += 1, launch_cg_pupdate(h->d0, h->cg_r, h->cg_p, h->st, s)));
-    }
-    if ((r = read_state(h, s)) != PS_OK) return r;
-  }
+  h->act.body = [h, phi, nb](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    const double nn = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+    cudaError_t e;
+    prof_begin(h, PC_KRYLOV, nn * 16.0, nn * (6.0 * (h->order / 2) + 3.0), 1, q);
+    e = (h->nlaunch += 1, launch_cg_apply(h->d0, h->order, h->h0, h->cg_p, h->cg_q, h->partials, h->st, q));
+    prof_end(h, q);
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 0, h->st, q));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_update(h->d0, phi, h->cg_r, h->cg_p, h->cg_q, h->partials, h->st, q));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 1, h->st, q, cond, chunk));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_pupdate(h->d0, h->cg_r, h->cg_p, h->st, q));
+    return e;
+  };
+  h->act.key = "cg";
+  h->act.chunk = KRYLOV_GRAPH_CHUNK;
+  h->act.plain_chunk = KRYLOV_CHUNK;
   return PS_OK;
 }
 
@@ -486,89 +529,191 @@ ps_status sph_vectors(ps_ctx* h, int dt) {
   return PS_OK;
 }
 
-// vectors: 0 r, 1 rhat, 2 p, 3 phat, 4 v, 5 s, 6 shat, 7 t
-ps_status sph_bicg(ps_ctx* h, int dt, const double* rho, double fscale, const void* fin, void* x,
-                   DevState* st, DevState* hst, double tol, int max_iter, cudaStream_t s) {
-  ps_status r = reset_state(h, st, hst, tol, max_iter, s);
-  if (r != PS_OK) return r;
+// Enqueue a BiCGSTAB start (reference and initial residual) for storage dt and
+// return its iteration body.  vectors: 0 r, 1 rhat, 2 p, 3 phat, 4 v, 5 s, 6 shat, 7 t
+ps_status bicg_start(ps_ctx* h, int dt, const double* rho, double fscale, const void* fin, void* x,
+                     DevState* st, double tol, int max_iter, cudaStream_t s, Body* body) {
   int nb = 0;
   void** v = h->sv;
+  TRY((h->nlaunch += 1, launch_init_state(st, tol, max_iter, s)));
   TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 0, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, st, s)));
   TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 1, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 1, st, s)));
-  TRY(cudaMemcpyAsync(hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  TRY(cudaStreamSynchronize(s));
-  while (hst->done == DONE_NO) {
-    for (int q = 0; q < KRYLOV_CHUNK; q++)
-      TRY((h->nlaunch += 9, launch_bicg_iter(h->sd, h->stab, dt, x, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->partials, st, s)));
-    TRY(cudaMemcpyAsync(hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    TRY(cudaStreamSynchronize(s));
-  }
+  *body = [h, dt, x, v, st](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    const double n = (double)h->sd.nr * h->sd.nt * h->sd.np;
+    const double S = dt == DT_F64 ? 8.0 : 4.0;
+    prof_begin(h, PC_KRYLOV, n * S * 16.0, n * 60.0, dt == DT_F64, q);
+    cudaError_t e = (h->nlaunch += 9, launch_bicg_iter(h->sd, h->stab, dt, x, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->partials, st, q, cond, chunk));
+    prof_end(h, q);
+    return e;
+  };
   return PS_OK;
 }
 
-ps_status sph_solve(ps_ctx* h, const double* rho, double* phi, double tol, const ps_solve_opts* o,
+ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, const ps_solve_opts* o,
                     cudaStream_t s) {
   ps_status r;
   TRY(cudaEventRecord(h->ev[0], s));
   if (h->bc.outer == PS_BC_MULTIPOLE) {
     TRY((h->nlaunch += 2, launch_sph_moments(h->sd, h->stab, rho, s)));
-    TRY((h->nlaunch += 1, launch_sph_face(h->sd, h->stab, h->bc.G, phi, s)));
+    TRY((h->nlaunch += 1, launch_sph_face(h->sd, h->stab, h->bc.G, phi_user, s)));
   }
   TRY(cudaEventRecord(h->ev[1], s));
+  double* phi = h->phi0;
+  TRY(cudaMemcpyAsync(phi, phi_user, (size_t)h->sd.size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
   const double fscale = 4.0 * M_PI * h->bc.G;
+  h->act.chunk = KRYLOV_GRAPH_CHUNK;
+  h->act.plain_chunk = KRYLOV_CHUNK;
   if (o->prec == PS_FP64) {
     if ((r = sph_vectors(h, DT_F64)) != PS_OK) return r;
-    return sph_bicg(h, DT_F64, rho, fscale, nullptr, phi, h->st, h->hst, tol, o->max_iter, s);
+    h->act.key = "bicg64";
+    return bicg_start(h, DT_F64, rho, fscale, nullptr, phi, h->st, tol, o->max_iter, s, &h->act.body);
   }
-  // FP64 iterative refinement around FP32 BiCGSTAB
+  // FP64 iterative refinement around FP32 BiCGSTAB: the outer steps are driven
+  // from the host (each step runs an inner solve to its own tolerance)
   if ((r = sph_vectors(h, DT_F32)) != PS_OK) return r;
   const size_t n = (size_t)h->sd.size();
-  if (!h->ir_rhs) {
-    if ((r = alloc_zero((void**)&h->ir_rhs, n * 4, &h->bytes)) != PS_OK) return r;
-  }
-  float* e = nullptr;
-  if ((r = alloc_zero((void**)&e, n * 4, &h->bytes)) != PS_OK) return r;
-  struct Guard { float* p; size_t n; size_t* acc; ~Guard() { cudaFree(p); *acc -= n; } } g{e, n * 4, &h->bytes};
-  if ((r = reset_state(h, h->st, h->hst, tol, o->max_iter, s)) != PS_OK) return r;
+  if (!h->ir_rhs && (r = alloc_zero((void**)&h->ir_rhs, n * 4, &h->bytes)) != PS_OK) return r;
+  if (!h->ir_e && (r = alloc_zero((void**)&h->ir_e, n * 4, &h->bytes)) != PS_OK) return r;
   int nb = 0;
-  // reference norm ||f - L(boundary)|| (FP64 kernel, no vector output)
+  TRY((h->nlaunch += 1, launch_init_state(h->st, tol, o->max_iter, s)));
   TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, DT_F64, 0, rho, fscale, nullptr, phi, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, h->st, s)));
   TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
-  if ((r = read_state(h, s)) != PS_OK) return r;
-  const double inner_tol = 1e-4;
-  const int inner_max = o->inner_cycles > 0 ? o->inner_cycles : 400;
-  long long inner_total = 0;
-  while (h->hst->done == DONE_NO) {
-    TRY(cudaMemsetAsync(e, 0, n * 4, s));
-    if ((r = sph_bicg(h, DT_F32, nullptr, 1.0, h->ir_rhs, e, h->st2, h->hst2, inner_tol, inner_max, s)) != PS_OK) return r;
-    inner_total += h->hst2->iter;
-    TRY((h->nlaunch += 1, launch_sph_correct(h->sd, DT_F32, e, phi, h->st, s)));
-    TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
-    TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, s)));
-    if ((r = read_state(h, s)) != PS_OK) return r;
-  }
-  h->hst->inner_cycles = inner_total;
+  h->act.host_driven = true;
+  h->act.sph_fscale = fscale;
+  h->act.inner_max = o->inner_cycles > 0 ? o->inner_cycles : 400;
   return PS_OK;
 }
 
-void fill_info(ps_ctx* h, ps_info* info, ps_status st) {
+// One outer refinement step of the spherical mixed solve (host driven).
+ps_status sph_ir_step(ps_ctx* h, cudaStream_t s) {
+  const size_t n = (size_t)h->sd.size();
+  float* e = h->ir_e;
+  double* phi = h->phi0;
+  TRY(cudaMemsetAsync(e, 0, n * 4, s));
+  Body inner;
+  ps_status r = bicg_start(h, DT_F32, nullptr, 1.0, h->ir_rhs, e, h->st2, 1e-4, h->act.inner_max, s, &inner);
+  if (r != PS_OK) return r;
+  TRY(cudaMemcpyAsync(h->hst2, h->st2, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  while (h->hst2->done == DONE_NO) {
+    for (int q = 0; q < KRYLOV_CHUNK; q++) TRY(inner(0ull, 0, s));
+    TRY(cudaMemcpyAsync(h->hst2, h->st2, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+  }
+  h->act.inner_total += h->hst2->iter;
+  int nb = 0;
+  TRY((h->nlaunch += 1, launch_sph_correct(h->sd, DT_F32, e, phi, h->st, s)));
+  TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, h->act.rho, h->act.sph_fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, s)));
+  return PS_OK;
+}
+
+// ------------------------------------------------------------------ stepping
+// Capture the active body into a graph: gate kernel -> while(body).  The gate
+// opens the loop only when the state has work left within the step budget;
+// the body's last scalar kernel re-evaluates the condition every iteration.
+ps_status build_loop_graph(ps_ctx* h, LoopGraph* g) {
+  cudaGraph_t graph = nullptr;
+  TRY(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault);
+  cudaGraphNode_t gate = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t eg = launch_loop_gate(h->st_active, (unsigned long long)cond, h->cap);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(h->cap, &captured);
+    if (eg != cudaSuccess) e = eg;
+  }
+  size_t nn = 1;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &gate, &nn);
+  alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+  memset(np_raw, 0, sizeof(np_raw));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, graph, &gate, nullptr, 1, &np);
+  if (e == cudaSuccess) {
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    const long long before = h->nlaunch;
+    e = cudaStreamBeginCaptureToGraph(h->cap, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t eb = h->act.body((unsigned long long)cond, 1, h->cap);
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(h->cap, &captured);
+      if (eb != cudaSuccess) e = eb;
+    }
+    g->body_kernels = h->nlaunch - before;
+    h->nlaunch = before;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g->exec = nullptr;
+    return fail(PS_ERR_CUDA, "building the %s loop graph: %s", h->act.key.c_str(), cudaGetErrorString(e));
+  }
+  return PS_OK;
+}
+
+// Enqueue up to k more iterations of the active solve on the handle's stream.
+ps_status step_active(ps_ctx* h, int k) {
+  cudaStream_t s = h->stream;
+  ps_status r;
+  if (h->act.host_driven) {   // spherical refinement: one outer step, synchronously
+    if ((r = read_state(h, s)) != PS_OK) return r;
+    if (h->hst->done != DONE_NO) return PS_OK;
+    return sph_ir_step(h, s);
+  }
+  if (h->prof) {
+    // event records cannot sit inside graph bodies: launch directly, after a
+    // state read so that no iteration runs past convergence
+    if ((r = read_state(h, s)) != PS_OK) return r;
+    const int n = std::min(k, h->act.plain_chunk);
+    for (int q = 0; q < n && h->hst->done == DONE_NO; q++) TRY(h->act.body(0ull, 0, s));
+    h->act.plain_steps = true;
+    return PS_OK;
+  }
+  LoopGraph& g = h->graphs[h->act.key];
+  if (!g.exec && (r = build_loop_graph(h, &g)) != PS_OK) return r;
+  h->act.body_kernels = g.body_kernels;
+  TRY((h->nlaunch += 2, launch_set_budget(h->st, k, s)));
+  TRY(cudaGraphLaunch(g.exec, s));
+  return PS_OK;
+}
+
+// Read the active solve's state (waits for its stream).
+ps_status poll_active(ps_ctx* h, int* done) {
+  const int it0 = h->hst->iter;
+  ps_status r = read_state(h, h->stream);
+  if (r != PS_OK) return r;
+  if (!h->act.plain_steps && !h->act.host_driven && h->hst->iter > it0)
+    h->nlaunch += h->act.body_kernels * (h->hst->iter - it0);
+  h->act.plain_steps = false;
+  *done = h->hst->done != DONE_NO;
+  return PS_OK;
+}
+
+void fill_info(ps_ctx* h, ps_info* info, ps_status st, bool final_) {
   if (!info) return;
   memset(info, 0, sizeof(*info));
   const DevState& d = *h->hst;
   info->iterations = d.iter;
   info->rel_residual = d.rel;
   info->rho_conv = (d.iter > 0 && d.rel0 > 0.0) ? std::pow(d.rel / d.rel0, 1.0 / d.iter) : 0.0;
-  info->inner_cycles = d.inner_cycles;
+  info->inner_cycles = h->act.host_driven ? h->act.inner_total : (long long)d.iter * h->act.inner_per_iter;
   info->coarse_iterations = d.coarse_iter_total;
   info->kernel_launches = h->nlaunch;
   info->status = st;
   float a = 0.f, b = 0.f;
   if (cudaEventElapsedTime(&a, h->ev[0], h->ev[1]) == cudaSuccess) info->t_mp_ms = a;
-  if (cudaEventElapsedTime(&b, h->ev[1], h->ev[2]) == cudaSuccess) info->t_iter_ms = b;
+  if (final_ && cudaEventElapsedTime(&b, h->ev[1], h->ev[2]) == cudaSuccess) info->t_iter_ms = b;
   if (h->bc.outer == PS_BC_MULTIPOLE) {
     const int nq = std::min(81, (h->lmax + 1) * (h->lmax + 1));
     const double* q = h->sph ? h->stab.q : h->mp.q;
@@ -676,14 +821,20 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(fail(PS_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+  if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(fail(PS_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
   for (auto& ev : h->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(fail(PS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
+  if ((e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(fail(PS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
   if ((e = cudaMalloc(&h->st, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "state alloc"));
   if ((e = cudaMalloc(&h->st2, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "state alloc"));
   if ((e = cudaMallocHost(&h->hst, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "pinned alloc"));
   if ((e = cudaMallocHost(&h->hst2, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "pinned alloc"));
   memset(h->hst, 0, sizeof(DevState));
   memset(h->hst2, 0, sizeof(DevState));
+  h->st_active = h->st;
   ps_status s;
   if (!h->sph) {
     const int gw = stencil_order / 2;
@@ -699,6 +850,7 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
     h->d0 = h->dims[0];
     for (int a = 0; a < 3; a++) h->h0[a] = h->hs[0][a];
     if ((s = alloc_zero((void**)&h->fs64, (size_t)h->d0.size() * 8, &h->bytes)) != PS_OK) return bail(s);
+    if ((s = alloc_zero((void**)&h->phi0, (size_t)h->d0.size() * 8, &h->bytes)) != PS_OK) return bail(s);
     if ((s = ensure_partials(h, cart_partials_count(h->d0))) != PS_OK) return bail(s);
     if (b.outer == PS_BC_MULTIPOLE) {
       build_multipole_tables(l_max, &h->mpt);
@@ -718,6 +870,7 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
                               b.outer == PS_BC_MULTIPOLE ? l_max : -1, &h->stab)) != cudaSuccess)
       return bail(fail(PS_ERR_OOM, "spherical tables: %s", cudaGetErrorString(e)));
     h->bytes += h->stab.bytes;
+    if ((s = alloc_zero((void**)&h->phi0, (size_t)h->sd.size() * 8, &h->bytes)) != PS_OK) return bail(s);
     const int nblk = ((h->sd.nr + 31) / 32) * ((h->sd.nt + 7) / 8) * h->sd.np;
     if ((s = ensure_partials(h, nblk)) != PS_OK) return bail(s);
   }
@@ -728,6 +881,12 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
 void poisson_destroy(ps_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+  cudaFree(h->phi0);
+  cudaFree(h->ir_e);
+  if (h->cap) cudaStreamDestroy(h->cap);
   free_hier(&h->h64);
   free_hier(&h->hmx[0]);
   free_hier(&h->hmx[1]);
@@ -751,13 +910,16 @@ void poisson_destroy(ps_handle h) {
     cudaEventDestroy(r.b);
   }
   for (auto ev : h->ev_pool) cudaEventDestroy(ev);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 
-ps_status poisson_solve(ps_handle h, const double* rho_dev, double* phi_dev, double tol,
-                        const ps_solve_opts* opts, ps_info* info) {
+ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_dev, double tol,
+                              const ps_solve_opts* opts) {
   if (!h) return fail(PS_ERR_INVALID_ARG, "NULL handle");
+  if (h->act.on) return fail(PS_ERR_INVALID_ARG, "a solve is already in flight on this handle");
   if (!rho_dev || !phi_dev) return fail(PS_ERR_INVALID_ARG, "rho and phi must be device pointers");
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(PS_ERR_INVALID_ARG, "tol must be finite and >= 0");
   ps_solve_opts o{};
@@ -771,56 +933,140 @@ ps_status poisson_solve(ps_handle h, const double* rho_dev, double* phi_dev, dou
   if (opts) o = *opts;
   if (o.max_iter < 0) return fail(PS_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (o.prec < PS_FP64 || o.prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", o.prec);
-  cudaStream_t s = o.stream ? (cudaStream_t)o.stream : h->stream;
-  ps_status r = PS_OK;
-  h->nlaunch = 0;
   if (h->sph) {
     if (o.method != PS_BICGSTAB) return fail(PS_ERR_UNSUPPORTED, "spherical grids are solved by BiCGSTAB (method %d)", o.method);
     if (o.prec == PS_MIXED_BF16) return fail(PS_ERR_UNSUPPORTED, "BF16 storage is a multigrid option");
-    r = sph_solve(h, rho_dev, phi_dev, tol, &o, s);
+  } else if (o.method == PS_MG) {
+    if (h->nlev < 2) return fail(PS_ERR_INVALID_ARG, "multigrid needs all interval counts even and >= 16");
+    if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1) return fail(PS_ERR_INVALID_ARG, "nu1, nu2 >= 0 with nu1 + nu2 >= 1");
+  } else if (o.method == PS_SOR) {
+    if (!(o.omega > 0.0 && o.omega < 2.0)) return fail(PS_ERR_INVALID_ARG, "SOR needs 0 < omega < 2");
+    if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "SOR runs in FP64 only");
+  } else if (o.method == PS_CG) {
+    if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "CG runs in FP64 only");
   } else {
-    if (o.method == PS_MG) {
-      if (h->nlev < 2) return fail(PS_ERR_INVALID_ARG, "multigrid needs all interval counts even and >= 16");
-      if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1) return fail(PS_ERR_INVALID_ARG, "nu1, nu2 >= 0 with nu1 + nu2 >= 1");
-    } else if (o.method == PS_SOR) {
-      if (!(o.omega > 0.0 && o.omega < 2.0)) return fail(PS_ERR_INVALID_ARG, "SOR needs 0 < omega < 2");
-      if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "SOR runs in FP64 only");
-    } else if (o.method == PS_CG) {
-      if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "CG runs in FP64 only");
-    } else {
-      return fail(PS_ERR_INVALID_ARG, "method %d is not available on Cartesian grids", o.method);
-    }
-    double fscale = 0.0;
-    if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, s, &fscale)) != PS_OK) return r;
-    if (o.method == PS_MG) r = o.prec == PS_FP64 ? cart_mg64(h, phi_dev, &o, s) : cart_ir(h, phi_dev, &o, s);
-    else if (o.method == PS_SOR) r = cart_sor(h, phi_dev, &o, s);
-    else r = cart_cg(h, phi_dev, &o, s);
+    return fail(PS_ERR_INVALID_ARG, "method %d is not available on Cartesian grids", o.method);
+  }
+  Active& a = h->act;
+  a = Active();
+  a.o = o;
+  a.tol = tol;
+  a.rho = rho_dev;
+  a.phi_user = phi_dev;
+  a.caller = (cudaStream_t)o.stream;   // NULL = CUDA's default stream
+  h->nlaunch = 0;
+  // the handle's stream starts after everything the caller enqueued so far
+  cudaStream_t s = h->stream;
+  TRY(cudaEventRecord(h->ev_in, a.caller));
+  TRY(cudaStreamWaitEvent(s, h->ev_in, 0));
+  ps_status r;
+  if (h->sph) {
+    r = begin_sph(h, rho_dev, phi_dev, tol, &o, s);
+  } else {
+    if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, s)) != PS_OK) return r;
+    // iterate on the handle's own copy of phi: captured loop graphs reference it
+    TRY(cudaMemcpyAsync(h->phi0, phi_dev, (size_t)h->d0.size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (o.method == PS_MG) r = o.prec == PS_FP64 ? begin_mg64(h, &o, s) : begin_ir(h, &o, s);
+    else if (o.method == PS_SOR) r = begin_sor(h, &o, s);
+    else r = begin_cg(h, s);
   }
   if (r != PS_OK) return r;
-  cudaError_t e = cudaEventRecord(h->ev[2], s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  h->hst->iter = 0;
+  h->hst->done = DONE_NO;
+  a.on = true;
+  return PS_OK;
+}
+
+ps_status poisson_solve_step(ps_handle h, int max_iterations) {
+  if (!h || !h->act.on) return fail(PS_ERR_INVALID_ARG, "no solve in flight");
+  if (max_iterations < 1) return fail(PS_ERR_INVALID_ARG, "max_iterations must be >= 1");
+  return step_active(h, max_iterations);
+}
+
+ps_status poisson_solve_poll(ps_handle h, int* done, ps_info* info) {
+  if (!h || !h->act.on || !done) return fail(PS_ERR_INVALID_ARG, "no solve in flight / NULL done");
+  ps_status r = poll_active(h, done);
+  if (r != PS_OK) return r;
+  if (info) fill_info(h, info, PS_OK, false);
+  return PS_OK;
+}
+
+ps_status poisson_solve_end(ps_handle h, ps_info* info) {
+  if (!h || !h->act.on) return fail(PS_ERR_INVALID_ARG, "no solve in flight");
+  Active& a = h->act;
+  cudaStream_t s = h->stream;
+  a.on = false;
+  const size_t bytes = (size_t)(h->sph ? h->sd.size() : h->d0.size()) * sizeof(double);
+  TRY(cudaEventRecord(h->ev[2], s));
+  TRY(cudaMemcpyAsync(a.phi_user, h->phi0, bytes, cudaMemcpyDeviceToDevice, s));
+  TRY(cudaEventRecord(h->ev_out, s));
+  TRY(cudaStreamWaitEvent(a.caller, h->ev_out, 0));
+  int done = 0;
+  ps_status r = poll_active(h, &done);
+  if (r != PS_OK) return r;
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(PS_ERR_CUDA, "solve: %s", cudaGetErrorString(e));
   ps_status out = PS_OK;
-  if (h->hst->done == DONE_MAXITER) out = PS_NOT_CONVERGED;
+  if (h->hst->done == DONE_MAXITER || h->hst->done == DONE_NO) out = PS_NOT_CONVERGED;
   else if (h->hst->done == DONE_DIVERGED) out = PS_DIVERGED;
   if (out == PS_NOT_CONVERGED) fail(out, "not converged: relative residual %.3e after %d iterations", h->hst->rel, h->hst->iter);
   if (out == PS_DIVERGED) fail(out, "diverged: relative residual %.3e after %d iterations", h->hst->rel, h->hst->iter);
-  fill_info(h, info, out);
+  fill_info(h, info, out, true);
   return out;
 }
 
+ps_status poisson_solve(ps_handle h, const double* rho_dev, double* phi_dev, double tol,
+                        const ps_solve_opts* opts, ps_info* info) {
+  ps_status r = poisson_solve_begin(h, rho_dev, phi_dev, tol, opts);
+  if (r != PS_OK) return r;
+  int done = 0;
+  if ((r = poll_active(h, &done)) != PS_OK) { h->act.on = false; return r; }
+  while (!done) {
+    if ((r = step_active(h, h->act.chunk)) != PS_OK || (r = poll_active(h, &done)) != PS_OK) {
+      h->act.on = false;
+      return r;
+    }
+  }
+  return poisson_solve_end(h, info);
+}
+
+// Batched solve: every request runs on its own handle's stream, so their kernels
+// overlap on the GPU; each request's kernels and reductions are exactly those
+// of a solo solve, so results equal separate poisson_solve calls bit for bit.
 ps_status poisson_solve_batch(ps_handle* hs, const double* const* rho, double* const* phi,
                               const double* tol, int n, const ps_solve_opts* opts, ps_info* infos) {
   if (n < 0 || (n > 0 && (!hs || !rho || !phi || !tol))) return fail(PS_ERR_INVALID_ARG, "bad batch arguments");
-  for (int i = 0; i < n; i++)
+  for (int i = 0; i < n; i++) {
+    if (!hs[i]) return fail(PS_ERR_INVALID_ARG, "NULL handle in batch");
     for (int j = i + 1; j < n; j++)
       if (hs[i] == hs[j]) return fail(PS_ERR_INVALID_ARG, "batch handles must be distinct");
+  }
+  ps_status r;
+  std::vector<int> done(n, 0);
+  for (int i = 0; i < n; i++)
+    if ((r = poisson_solve_begin(hs[i], rho[i], phi[i], tol[i], opts)) != PS_OK) {
+      for (int j = 0; j < i; j++) hs[j]->act.on = false;
+      return r;
+    }
+  int left = n;
+  for (int i = 0; i < n; i++) {
+    if ((r = poll_active(hs[i], &done[i])) != PS_OK) return r;
+    if (done[i]) left--;
+  }
+  while (left > 0) {
+    for (int i = 0; i < n; i++)
+      if (!done[i] && (r = step_active(hs[i], hs[i]->act.chunk)) != PS_OK) return r;
+    for (int i = 0; i < n; i++) {
+      if (done[i]) continue;
+      if ((r = poll_active(hs[i], &done[i])) != PS_OK) return r;
+      if (done[i]) left--;
+    }
+  }
   ps_status worst = PS_OK;
   for (int i = 0; i < n; i++) {
-    ps_status s = poisson_solve(hs[i], rho[i], phi[i], tol[i], opts, infos ? &infos[i] : nullptr);
-    if (s != PS_OK && s != PS_NOT_CONVERGED && s != PS_DIVERGED) return s;
-    if (s != PS_OK && worst == PS_OK) worst = s;
+    ps_status si = poisson_solve_end(hs[i], infos ? &infos[i] : nullptr);
+    if (si != PS_OK && si != PS_NOT_CONVERGED && si != PS_DIVERGED) return si;
+    if (si != PS_OK && worst == PS_OK) worst = si;
   }
   return worst;
 }

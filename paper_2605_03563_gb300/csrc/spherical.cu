@@ -201,10 +201,20 @@ __global__ void __launch_bounds__(SBX* SBY)
 }
 
 // which: 0 alpha; 1 s-norm check; 2 omega; 3 r check + beta
+__device__ __forceinline__ void bicg_set_loop(const DevState* st, unsigned long long cond, int chunk) {
+  if (chunk > 0) {
+    const unsigned int more = (st->done == DONE_NO && st->iter < st->chunk_end) ? 1u : 0u;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, more);
+  }
+}
+
 __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int which,
-                              DevState* __restrict__ st) {
+                              DevState* __restrict__ st, unsigned long long cond, int chunk) {
   __shared__ double sh[64];
-  if (st->done) return;
+  if (st->done) {
+    if (which == 3 && threadIdx.x == 0) bicg_set_loop(st, cond, chunk);
+    return;
+  }
   if ((which == 2) && st->early) return;
   if (which == 3 && st->early) {
     if (threadIdx.x == 0) {
@@ -212,6 +222,7 @@ __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int
       st->rel = sqrt(st->ss) / st->ref;
       st->done = DONE_CONVERGED;
       st->early = 0;
+      bicg_set_loop(st, cond, chunk);
     }
     return;
   }
@@ -243,6 +254,7 @@ __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int
     if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
     else if (rel <= st->tol) st->done = DONE_CONVERGED;
     else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+    bicg_set_loop(st, cond, chunk);
   }
 }
 
@@ -307,29 +319,31 @@ cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevSta
 template <typename T>
 static cudaError_t iter_t(const SphDims& d, const SphTables& t, void* x, int x_is_f64, void* r,
                           const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
-                          void* tv, double* partials, DevState* st, cudaStream_t s) {
+                          void* tv, double* partials, DevState* st, cudaStream_t s,
+                          unsigned long long cond, int chunk) {
   using C = typename St<T>::C;
   const Tab<C> tb = tab_of<C>(t);
   const dim3 g = sph_grid(d), b(SBX, SBY);
   const int nblk = g.x * g.y * g.z;
   k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)phat, (T*)v, (const T*)rhat, 0, partials, st, 0);
-  k_bicg_scalar<<<1, 256, 0, s>>>(partials, nblk, 0, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 0, st, 0ull, 0);
   k_bicg_s<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (const T*)v, (T*)sv, (T*)shat, partials, st);
-  k_bicg_scalar<<<1, 256, 0, s>>>(partials, nblk, 1, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 1, st, 0ull, 0);
   k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)shat, (T*)tv, (const T*)sv, 1, partials, st, 1);
-  k_bicg_scalar<<<1, 256, 0, s>>>(partials, nblk, 2, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 2, st, 0ull, 0);
   k_bicg_xr<T><<<g, b, 0, s>>>(d, x, x_is_f64, (T*)r, (const T*)rhat, (const T*)phat, (const T*)sv,
                                (const T*)shat, (const T*)tv, partials, st);
-  k_bicg_scalar<<<1, 256, 0, s>>>(partials, nblk, 3, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 3, st, cond, chunk);
   k_bicg_p<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (T*)p, (const T*)v, (T*)phat, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, void* x, void* r,
                              const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
-                             void* tv, double* partials, DevState* st, cudaStream_t s) {
-  if (dt == DT_F64) return iter_t<double>(d, t, x, 1, r, rhat, p, phat, v, sv, shat, tv, partials, st, s);
-  return iter_t<float>(d, t, x, 0, r, rhat, p, phat, v, sv, shat, tv, partials, st, s);
+                             void* tv, double* partials, DevState* st, cudaStream_t s,
+                             unsigned long long cond, int chunk) {
+  if (dt == DT_F64) return iter_t<double>(d, t, x, 1, r, rhat, p, phat, v, sv, shat, tv, partials, st, s, cond, chunk);
+  return iter_t<float>(d, t, x, 0, r, rhat, p, phat, v, sv, shat, tv, partials, st, s, cond, chunk);
 }
 
 // Iterative refinement: r = f - L x in FP64, stored as FP32 times st->scale_next.
@@ -394,31 +408,33 @@ cudaError_t launch_sph_correct(const SphDims& d, int dt_e, const void* e, double
 // ------------------------------------------------------------------ multipole
 // Moments (Eq. outer_multipole) factor on the spherical grid: a phi-Fourier
 // pass per (r, theta) line, then the theta-Legendre and r sums per (l, m).
+template <int L>
 __global__ void __launch_bounds__(128)
-    k_sph_fourier(SphDims d, int L, const double* __restrict__ rho, const double* __restrict__ cosT,
+    k_sph_fourier(SphDims d, const double* __restrict__ rho, const double* __restrict__ cosT,
                   const double* __restrict__ sinT, double* __restrict__ Fc, double* __restrict__ Fs) {
   const int i = blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
   if (i >= d.nr) return;
-  double ac[MAXL + 1], as[MAXL + 1];
+  double ac[L + 1], as[L + 1];
 #pragma unroll
-  for (int m = 0; m <= MAXL; m++) { ac[m] = 0.0; as[m] = 0.0; }
+  for (int m = 0; m <= L; m++) { ac[m] = 0.0; as[m] = 0.0; }
   for (int k = 0; k < d.np; k++) {
     const double v = rho[d.at(i, j, k)];
 #pragma unroll
-    for (int m = 0; m <= MAXL; m++) {
-      if (m <= L) {
-        ac[m] = fma(v, cosT[m * d.np + k], ac[m]);
-        as[m] = fma(v, sinT[m * d.np + k], as[m]);
-      }
+    for (int m = 0; m <= L; m++) {
+      ac[m] = fma(v, cosT[m * d.np + k], ac[m]);
+      as[m] = fma(v, sinT[m * d.np + k], as[m]);
     }
   }
 #pragma unroll
-  for (int m = 0; m <= MAXL; m++) {
-    if (m <= L) {
-      Fc[((long long)m * d.nt + j) * d.nr + i] = ac[m];
-      Fs[((long long)m * d.nt + j) * d.nr + i] = as[m];
-    }
+  for (int m = 0; m <= L; m++) {
+    Fc[((long long)m * d.nt + j) * d.nr + i] = ac[m];
+    Fs[((long long)m * d.nt + j) * d.nr + i] = as[m];
   }
+}
+
+template <int L>
+static void fourier_launch(const SphDims& d, const SphTables& t, const double* rho, cudaStream_t s) {
+  k_sph_fourier<L><<<dim3((d.nr + 127) / 128, d.nt), 128, 0, s>>>(d, rho, t.cosT, t.sinT, t.Fc, t.Fs);
 }
 
 __global__ void __launch_bounds__(256)
@@ -471,7 +487,25 @@ cudaError_t launch_sph_moments(const SphDims& d, const SphTables& t, const doubl
                                cudaStream_t s) {
   const int L = t.lmax;
   if (L < 0 || L > MAXL) return cudaErrorInvalidValue;
-  k_sph_fourier<<<dim3((d.nr + 127) / 128, d.nt), 128, 0, s>>>(d, L, rho, t.cosT, t.sinT, t.Fc, t.Fs);
+  switch (L) {
+    case 0: fourier_launch<0>(d, t, rho, s); break;
+    case 1: fourier_launch<1>(d, t, rho, s); break;
+    case 2: fourier_launch<2>(d, t, rho, s); break;
+    case 3: fourier_launch<3>(d, t, rho, s); break;
+    case 4: fourier_launch<4>(d, t, rho, s); break;
+    case 5: fourier_launch<5>(d, t, rho, s); break;
+    case 6: fourier_launch<6>(d, t, rho, s); break;
+    case 7: fourier_launch<7>(d, t, rho, s); break;
+    case 8: fourier_launch<8>(d, t, rho, s); break;
+    case 9: fourier_launch<9>(d, t, rho, s); break;
+    case 10: fourier_launch<10>(d, t, rho, s); break;
+    case 11: fourier_launch<11>(d, t, rho, s); break;
+    case 12: fourier_launch<12>(d, t, rho, s); break;
+    case 13: fourier_launch<13>(d, t, rho, s); break;
+    case 14: fourier_launch<14>(d, t, rho, s); break;
+    case 15: fourier_launch<15>(d, t, rho, s); break;
+    default: fourier_launch<16>(d, t, rho, s); break;
+  }
   k_sph_moments<<<(L + 1) * (L + 1), 256, 0, s>>>(d, L, t.Pn, t.sinth, t.Rw, t.Fc, t.Fs, t.q);
   return cudaGetLastError();
 }

@@ -57,9 +57,12 @@ cudaError_t launch_bicg_resid(const SphDims& d, const SphTables& t, int dt, int 
                               const double* rho, double fscale, const void* fin, const void* x,
                               void* r, void* rhat, void* p, void* phat, double* partials, int* nblk,
                               cudaStream_t s);
+// One iteration (9 kernels).  With chunk > 0 it runs inside a CUDA-graph while
+// loop whose condition the last scalar kernel sets.
 cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, void* x, void* r,
                              const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
-                             void* tv, double* partials, DevState* st, cudaStream_t s);
+                             void* tv, double* partials, DevState* st, cudaStream_t s,
+                             unsigned long long cond = 0, int chunk = 0);
 // scalar finisher for the reference / initial residual (mode 0/1)
 cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
                               cudaStream_t s);

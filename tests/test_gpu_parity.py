@@ -303,3 +303,48 @@ def test_spherical_bicgstab_matches_oracle(pkg, prec):
         assert rel_err(got[U], phi_o[U]) <= FP64_TOL
     else:
         assert rel_err(got[U], phi_o[U]) <= MIXED_TOL
+
+
+def test_solve_is_ordered_after_work_on_the_callers_stream(pkg):
+    """Inputs copied asynchronously on torch's stream (default or a side stream)
+    right before the call must be seen by the solve: same result as a solve on
+    settled inputs, bit for bit."""
+    n = 64
+    rho_h = torch.from_numpy(W.gaussian_blobs(n, seed=2)).pin_memory()
+    ref_rho = rho_h.cuda()
+    ref_phi = torch.zeros_like(ref_rho)
+    with pkg.CartesianSolver(n, bc="multipole") as s:
+        torch.cuda.synchronize()
+        base = s.solve(ref_rho, ref_phi, tol=1e-10)
+        zeros_h = torch.zeros_like(rho_h).pin_memory()
+        side = torch.cuda.Stream()
+        for stream in (torch.cuda.current_stream(), side):
+            with torch.cuda.stream(stream):
+                rho_d = torch.empty_like(ref_rho)
+                phi_d = torch.full_like(ref_phi, 7.0)
+                for _ in range(3):
+                    rho_d.copy_(rho_h, non_blocking=True)
+                    phi_d.copy_(zeros_h, non_blocking=True)
+                    info = s.solve(rho_d, phi_d, tol=1e-10)
+                    assert info.iterations == base.iterations
+                    assert torch.equal(phi_d, ref_phi)
+
+
+def test_stepwise_solve_equals_one_shot(pkg):
+    """begin / step(k) / poll / end gives the same iterate as poisson_solve."""
+    n = 64
+    rho = dev(W.gaussian_blobs(n, seed=2))
+    with pkg.CartesianSolver(n, bc="multipole") as s:
+        ref = torch.zeros_like(rho)
+        base = s.solve(rho, ref, tol=1e-10)
+        phi = torch.zeros_like(rho)
+        s.begin(rho, phi, tol=1e-10)
+        done, _ = s.poll()
+        steps = 0
+        while not done:
+            s.step(2)
+            done, prog = s.poll()
+            steps += 1
+        info = s.end()
+    assert info.iterations == base.iterations and steps == (base.iterations + 1) // 2
+    assert torch.equal(phi, ref)
