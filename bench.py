@@ -162,6 +162,61 @@ def cpu_baseline_sample():
                       "numpy, single thread)"}
 
 
+# ------------------------------------------------------------------ serving stream
+def run_serving(args, rank, world):
+    """2000 Cartesian solve requests (Poisson arrivals, mean 200/s, cubes 32..256,
+    1-16 Gaussian blobs, tolerance 1e-6 or 1e-10, 30% warm-started sequence
+    steps) served with continuous batching under an HBM budget."""
+    import torch
+    import workloads as W
+    import paper_2605_03563_gb300 as P
+    from paper_2605_03563_gb300.serving import PoissonServer, summarize
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    reqs = W.serving_stream(n_requests=args.requests, rate_hz=200.0, seed=5)
+    srv = PoissonServer(dev, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), prec=args.prec,
+                        cycles_per_step=args.cycles_per_step, max_active=args.max_active)
+    # pre-warm: a few handles per size with their loop graphs captured
+    warm_reqs = []
+    sizes = sorted({r.n for r in reqs})
+    for n in sizes:
+        for k in range(args.prewarm):
+            r = W.ServingRequest(-1 - len(warm_reqs), 0.0, n, 1e-6, W.gaussian_blob_params(99, 2))
+            warm_reqs.append(r)
+    srv.run(warm_reqs, realtime=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    t0 = time.perf_counter()
+    results, stats = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    srv.close()
+    summ = summarize(results)
+    by_tol = {}
+    for tol in (1e-6, 1e-10):
+        sub = [r for r in results if r.tol == tol]
+        if sub:
+            s2 = summarize(sub)
+            by_tol[f"{tol:g}"] = {k: s2[k] for k in ("requests", "latency_p50_ms", "latency_p99_ms")}
+    line = {"metric": "solves/s + p50/p99 latency (serving stream)", "value": summ["solves_per_s"],
+            "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "dtype": args.prec,
+            "data": "synthetic", "scaling": "weak",
+            "config": {"workload": "2000 requests, Poisson arrivals 200/s, cubes {32..256}^3, 1-16 "
+                                   "Gaussian blobs, tol 1e-6/1e-10, 30% warm-started sequences",
+                       "requests": len(reqs), "max_active": args.max_active,
+                       "cycles_per_step": args.cycles_per_step, "budget_gb": args.budget_gb},
+            "latency_p50_ms": summ["latency_p50_ms"], "latency_p99_ms": summ["latency_p99_ms"],
+            "latency_mean_ms": summ["latency_mean_ms"], "by_tol": by_tol,
+            "converged": summ["converged"], "makespan_s": summ["makespan_s"], "wall_s": wall,
+            "peak_active": stats["peak_active"], "ticks": stats["ticks"],
+            "warm_started": sum(1 for r in results if r.warm), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -171,6 +226,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="mg256", choices=["mg256", "serving"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed_fp32", "mixed_bf16"])
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--max-active", type=int, default=64)
+    ap.add_argument("--cycles-per-step", type=int, default=2)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--prewarm", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -179,6 +241,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serving":
+        return run_serving(args, rank, world)
 
     import numpy as np
     import torch

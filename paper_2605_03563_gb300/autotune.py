@@ -1,0 +1,83 @@
+"""Autotuner for the multigrid cycle shape and the refinement inner loop.
+
+For a grid size, stencil order, precision and tolerance it times whole solves
+of a seeded Gaussian-mixture density (the serving workload's recipe) for each
+candidate (nu1, nu2, inner V-cycles per refinement step) and keeps the fastest
+time to tolerance.  Results are cached in a JSON table keyed by
+"n:order:prec:tol" so servers and benchmarks can reuse them.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+DEFAULT_CANDIDATES = [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]
+TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_table.json")
+
+
+def key(n, order, prec, tol) -> str:
+    return f"{n}:{order}:{prec}:{tol:g}"
+
+
+def load(path: str = TABLE) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save(table: dict, path: str = TABLE) -> None:
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune(n: int, order: int = 2, prec: str = "fp64", tol: float = 1e-10, device=None,
+         cycles=DEFAULT_CANDIDATES, inners=None, reps: int = 3, seed: int = 2, lmax: int = 4):
+    """Time every candidate and return the best settings with all timings."""
+    import torch
+    import workloads as W
+    from . import CartesianSolver
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    if inners is None:
+        inners = (1,) if prec == "fp64" else (1, 2, 3)
+    rho = W.gaussian_blobs_device(n, W.gaussian_blob_params(seed), device, order=order)
+    phi = torch.zeros_like(rho)
+    trials = []
+    with CartesianSolver(n, order, bc="multipole", lmax=lmax) as s:
+        for (nu1, nu2) in cycles:
+            for inner in inners:
+                times = []
+                for r in range(reps + 1):
+                    phi.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    info = s.solve(rho, phi, tol=tol, method="mg", prec=prec, nu1=nu1, nu2=nu2,
+                                   inner_cycles=inner, max_iter=200)
+                    b.record()
+                    torch.cuda.synchronize()
+                    if r > 0:
+                        times.append(a.elapsed_time(b))
+                if info.converged:
+                    trials.append({"nu1": nu1, "nu2": nu2, "inner": inner,
+                                   "ms": statistics.median(times), "iterations": info.iterations})
+    best = min(trials, key=lambda t: t["ms"])
+    return dict(best, trials=trials)
+
+
+def tune_table(sizes, order=2, prec="fp64", tol=1e-10, path: str = TABLE, **kw) -> dict:
+    table = load(path)
+    for n in sizes:
+        table[key(n, order, prec, tol)] = tune(n, order, prec, tol, **kw)
+    save(table, path)
+    return table
+
+
+def lookup(table: dict, n: int, order=2, prec="fp64", tol=1e-10):
+    e = table.get(key(n, order, prec, tol))
+    if not e:
+        return {}
+    return {"nu1": e["nu1"], "nu2": e["nu2"], "inner": e["inner"]}

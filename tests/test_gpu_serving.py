@@ -1,0 +1,90 @@
+"""Continuous batching: every request's result is the same alone and in the mix.
+
+A small stream with two grid sizes, two tolerances and warm-started sequences
+is served once with up to 8 solves in flight (their kernels overlap on the
+GPU) and once strictly one at a time; each request's potential must match
+bit for bit (well inside the 1e-10 FP64 tolerance), with equal iteration
+counts.  Also: warm starts help, the HBM budget gates admission, the
+autotuner returns a converged configuration.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_03563_gb300 as P
+    P.capi.lib()
+    return P
+
+
+def _stream():
+    return W.serving_stream(n_requests=24, rate_hz=1e4, seed=7, sizes=(32, 64),
+                            seq_fraction=0.5, seq_len=4, step_shift=0.01)
+
+
+def _serve(pkg, reqs, max_active, **kw):
+    from paper_2605_03563_gb300.serving import PoissonServer
+    srv = PoissonServer(torch.device("cuda", 0), max_active=max_active, **kw)
+    try:
+        res, stats = srv.run(reqs, realtime=False, keep_results=True)
+        phis = {rid: p.clone() for rid, p in srv.final_phi.items()}
+    finally:
+        srv.close()
+    return {r.rid: r for r in res}, phis, stats
+
+
+def test_results_identical_alone_and_in_the_mix(pkg):
+    reqs = _stream()
+    mix, phi_mix, st_mix = _serve(pkg, reqs, max_active=8)
+    solo, phi_solo, st_solo = _serve(pkg, reqs, max_active=1)
+    assert st_mix["peak_active"] > 1 and st_solo["peak_active"] == 1
+    assert len(mix) == len(reqs) == len(solo)
+    for rid, r in mix.items():
+        assert r.status == 0 and solo[rid].status == 0
+        assert r.iterations == solo[rid].iterations
+        assert r.rel_residual <= r.tol
+        assert torch.equal(phi_mix[rid], phi_solo[rid]), rid
+
+
+def test_warm_starts_take_fewer_cycles(pkg):
+    reqs = _stream()
+    res, _, _ = _serve(pkg, reqs, max_active=8)
+    warm = [r.iterations for r in res.values() if r.warm]
+    first = [r.iterations for r in res.values() if r.seq_id >= 0 and r.seq_step == 0]
+    assert warm and first
+    assert np.mean(warm) < np.mean(first)
+
+
+def test_hbm_budget_gates_admission(pkg):
+    from paper_2605_03563_gb300.serving import PoissonServer
+    reqs = [r for r in _stream() if r.seq_id < 0][:6]
+    n = max(r.n for r in reqs)
+    one = PoissonServer.field_bytes(n)
+    srv = PoissonServer(torch.device("cuda", 0), hbm_budget_bytes=3 * one + pkg.workspace_bytes(n) + (n + 1) ** 3 * 8,
+                        max_active=8)
+    try:
+        res, stats = srv.run(reqs, realtime=False)
+        assert len(res) == len(reqs) and all(r.status == 0 for r in res)
+        assert stats["peak_active"] < len(reqs)
+    finally:
+        srv.close()
+    tiny = PoissonServer(torch.device("cuda", 0), hbm_budget_bytes=1024)
+    with pytest.raises(RuntimeError, match="HBM budget"):
+        tiny.run(reqs[:1], realtime=False)
+    tiny.close()
+
+
+def test_autotuner_picks_a_converged_configuration(pkg):
+    from paper_2605_03563_gb300 import autotune
+    best = autotune.tune(32, prec="mixed_fp32", tol=1e-8, reps=1, cycles=[(1, 1), (2, 2)], inners=(1, 2))
+    assert (best["nu1"], best["nu2"]) in [(1, 1), (2, 2)] and best["inner"] in (1, 2)
+    assert best["ms"] == min(t["ms"] for t in best["trials"])
+    assert len(best["trials"]) == 4

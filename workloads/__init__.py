@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "cart_shape", "cart_coords", "uniform_sphere", "gaussian_blobs",
-    "gaussian_blob_params", "lognormal_field", "manufactured_sine",
+    "gaussian_blob_params", "gaussian_blobs_device", "lognormal_field", "manufactured_sine",
     "smooth_sphere_density", "spherical_coords", "spherical_density",
     "ServingRequest", "serving_stream", "rng",
 ]
@@ -118,6 +118,24 @@ def gaussian_blobs(n: int, order: int = 2, seed: int = 2, nblobs: int = 8, blobs
         ex = np.exp(w * (x - cx) ** 2)
         ey = np.exp(w * (y - cy) ** 2)
         ez = np.exp(w * (z - cz) ** 2)
+        rho += b.amp * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    return rho
+
+
+def gaussian_blobs_device(n: int, blobs, device, order: int = 2, shift=(0.0, 0.0, 0.0)):
+    """gaussian_blobs() evaluated with torch on `device` (same separable
+    formula, float64), for request streams whose densities are made on the GPU."""
+    import torch
+    g = order // 2
+    idx = torch.arange(-(g - 1), n + g, dtype=torch.float64, device=device)
+    x = idx * (1.0 / n)
+    rho = torch.zeros((x.numel(),) * 3, dtype=torch.float64, device=device)
+    for b in blobs:
+        cx, cy, cz = (b.centre[a] + shift[a] for a in range(3))
+        w = -0.5 / (b.sigma * b.sigma)
+        ex = torch.exp(w * (x - cx) ** 2)
+        ey = torch.exp(w * (x - cy) ** 2)
+        ez = torch.exp(w * (x - cz) ** 2)
         rho += b.amp * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
     return rho
 
