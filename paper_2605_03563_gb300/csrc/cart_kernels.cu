@@ -11,7 +11,10 @@
 // ~6.6 TB/s: FP64 sweeps are bound by FP64 issue, FP32/BF16 sweeps by HBM.
 //
 // Launch geometry of the point kernels: 32 x 8 threads per block over (x, y)
-// and a z-chunk of ZCH nodes per thread.
+// and a z-chunk of nodes per thread chosen per level (zchunk_for): deep chunks
+// on the large finest levels, one node per thread on small levels so that the
+// launch still fills the 152 SMs instead of serialising memory latency along z.
+// Kernels recover the chunk from gridDim.z.
 #include <algorithm>
 #include <cstdio>
 
@@ -20,6 +23,15 @@
 namespace ps {
 
 static constexpr int BX = 32, BY = 8, ZCH = 16;
+static constexpr int kTargetBlocks = 8 * 152;
+
+static inline int zchunk_for(int gxy, int nk) {
+  long long z = (long long)gxy * nk / kTargetBlocks;
+  return (int)std::max(1LL, std::min((long long)ZCH, z));
+}
+
+// z-chunk of the current launch
+__device__ __forceinline__ int zchunk(int nk) { return (nk + gridDim.z - 1) / gridDim.z; }
 
 template <typename C>
 Coef<C> make_coef(const Dims& d, const double h[3], int order) {
@@ -44,13 +56,15 @@ template Coef<float> make_coef<float>(const Dims&, const double*, int);
 
 static inline bool is_iso(const double h[3]) { return h[0] == h[1] && h[1] == h[2]; }
 
-int cart_partials_count(const Dims& d) {
-  int gx = (d.ni() + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY, gz = (d.nk() + ZCH - 1) / ZCH;
-  return gx * gy * gz;
+static inline dim3 point_grid(const Dims& d) {
+  const int gx = (d.ni() + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY;
+  const int zc = zchunk_for(gx * gy, d.nk());
+  return dim3(gx, gy, (d.nk() + zc - 1) / zc);
 }
 
-static inline dim3 point_grid(const Dims& d) {
-  return dim3((d.ni() + BX - 1) / BX, (d.nj() + BY - 1) / BY, (d.nk() + ZCH - 1) / ZCH);
+int cart_partials_count(const Dims& d) {
+  const dim3 g = point_grid(d);
+  return g.x * g.y * g.z;
 }
 
 // ------------------------------------------------------------------ stencil core
@@ -142,8 +156,9 @@ __global__ void __launch_bounds__(BX* BY)
   using S = St<TI>;
   const int i = blockIdx.x * BX + threadIdx.x + G;
   const int j = blockIdx.y * BY + threadIdx.y + G;
-  const int k0 = blockIdx.z * ZCH + G;
-  const int k1 = min(k0 + ZCH, G + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + G;
+  const int k1 = min(k0 + zc, G + d.nk());
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
   double s2 = 0.0, mx = 0.0;
   float s2f = 0.0f, mxf = 0.0f;
@@ -158,7 +173,7 @@ __global__ void __launch_bounds__(BX* BY)
       } else {
         dl = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p)) - S::ld(phi + p);
       }
-      double dd = (double)dl;
+      const double dd = (RED >= 1 || sizeof(C) == sizeof(double)) ? (double)dl : 0.0;
       if (RED == 2 && dout != DT_F64) {
         // refinement pass: the stored inner right-hand side is FP32/BF16, so the
         // sum of squares and the max run on the FP32 pipe over the scaled value
@@ -172,7 +187,17 @@ __global__ void __launch_bounds__(BX* BY)
       }
       if (RED >= 1) s2 = fma(dd, dd, s2);
       if (RED == 2) mx = fmax(mx, fabs(dd));
-      if (out != nullptr) store_dt<C>(out, dout, p, dd * oscale);
+      if (out != nullptr) {
+        if (sizeof(C) == sizeof(float)) {
+          // FP32 arithmetic levels never touch the FP64 pipe on the store path
+          const float v = (float)dl * (float)oscale;
+          if (dout == DT_F32) ((float*)out)[p] = v;
+          else if (dout == DT_BF16) ((__nv_bfloat16*)out)[p] = __float2bfloat16_rn(v);
+          else ((double*)out)[p] = (double)v;
+        } else {
+          store_dt<C>(out, dout, p, dd * oscale);
+        }
+      }
     }
   }
   if (RED == 2 && dout != DT_F64) {
@@ -247,8 +272,9 @@ __global__ void __launch_bounds__(BX* BY)
   const int t = blockIdx.x * BX + threadIdx.x;
   const int jn = blockIdx.y * BY + threadIdx.y + 1;
   if (jn > d.nj()) return;
-  const int kn0 = blockIdx.z * ZCH + 1;
-  const int kn1 = min(kn0 + ZCH, d.nk() + 1);
+  const int zc = zchunk(d.nk());
+  const int kn0 = blockIdx.z * zc + 1;
+  const int kn1 = min(kn0 + zc, d.nk() + 1);
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
   for (int kn = kn0; kn < kn1; kn++) {
     int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;
@@ -272,7 +298,9 @@ static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* ph
   constexpr int NCOL = G == 1 ? 2 : 3;
   Coef<C> cf = make_coef<C>(d, h, order);
   int per_row = (d.ni() + NCOL - 1) / NCOL;
-  dim3 grid((per_row + BX - 1) / BX, (d.nj() + BY - 1) / BY, (d.nk() + ZCH - 1) / ZCH);
+  const int gx = (per_row + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY;
+  const int zc = zchunk_for(gx * gy, d.nk());
+  dim3 grid(gx, gy, (d.nk() + zc - 1) / zc);
   if (omega == 1.0)
     k_sweep<G, ISO, T, true><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st);
   else
@@ -312,8 +340,9 @@ __global__ void __launch_bounds__(BX* BY)
   const int I = blockIdx.x * BX + threadIdx.x + 1;
   const int J = blockIdx.y * BY + threadIdx.y + 1;
   if (I > cd.ni() || J > cd.nj()) return;
-  const int K0 = blockIdx.z * ZCH + 1;
-  const int K1 = min(K0 + ZCH, cd.nk() + 1);
+  const int zc = zchunk(cd.nk());
+  const int K0 = blockIdx.z * zc + 1;
+  const int K1 = min(K0 + zc, cd.nk() + 1);
   const int g = fd.g;
   const long long sy = fd.ex, sz = (long long)fd.ex * fd.ey;
   const CF sc = (CF)(factor / 64.0);
@@ -339,7 +368,7 @@ template <typename TF, typename TC>
 static cudaError_t restrict_t(const Dims& fine, const void* df, void* fsc, double factor,
                               cudaStream_t s) {
   Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2, fine.g);
-  dim3 grid((cd.ni() + BX - 1) / BX, (cd.nj() + BY - 1) / BY, (cd.nk() + ZCH - 1) / ZCH);
+  dim3 grid = point_grid(cd);
   k_restrict<TF, TC><<<grid, dim3(BX, BY), 0, s>>>(fine, cd, (const TF*)df, (TC*)fsc, factor);
   return cudaGetLastError();
 }
@@ -369,8 +398,9 @@ __global__ void __launch_bounds__(BX* BY)
   const int in = blockIdx.x * BX + threadIdx.x + 1;
   const int jn = blockIdx.y * BY + threadIdx.y + 1;
   if (in > fd.ni() || jn > fd.nj()) return;
-  const int kn0 = blockIdx.z * ZCH + 1;
-  const int kn1 = min(kn0 + ZCH, fd.nk() + 1);
+  const int zc = zchunk(fd.nk());
+  const int kn0 = blockIdx.z * zc + 1;
+  const int kn1 = min(kn0 + zc, fd.nk() + 1);
   const int g = fd.g;
   const int oi = in & 1, oj = jn & 1;
   const int I0 = in >> 1, J0 = jn >> 1;
@@ -421,7 +451,8 @@ __global__ void __launch_bounds__(BX* BY)
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
   if (i >= g + d.ni() || j >= g + d.nj()) return;
-  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
   for (int k = k0; k < k1; k++) {
     const long long p = d.at(i, j, k);
     St<T>::st(fs + p, (typename St<T>::C)(factor * rho[p]));
@@ -443,7 +474,8 @@ __global__ void __launch_bounds__(BX* BY)
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
   if (i >= g + d.ni() || j >= g + d.nj()) return;
-  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
   for (int k = k0; k < k1; k++) {
     const long long p = d.at(i, j, k);
     St<T>::st(fs + p, (typename St<T>::C)(factor * (double)St<T>::ld(f + p)));
@@ -469,7 +501,8 @@ __global__ void __launch_bounds__(BX* BY)
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
   if (i >= g + d.ni() || j >= g + d.nj()) return;
-  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
   for (int k = k0; k < k1; k++) {
     const long long p = d.at(i, j, k);
     phi[p] = fma((double)St<TE>::ld(e + p), isc, phi[p]);
@@ -493,7 +526,8 @@ __global__ void __launch_bounds__(BX* BY)
   const int i = blockIdx.x * BX + threadIdx.x + G;
   const int j = blockIdx.y * BY + threadIdx.y + G;
   if (i >= G + d.ni() || j >= G + d.nj()) return;
-  const int k0 = blockIdx.z * ZCH + G, k1 = min(k0 + ZCH, G + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + G, k1 = min(k0 + zc, G + d.nk());
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
   const C dd = (C)cf.d;
   for (int k = k0; k < k1; k++) {
@@ -789,7 +823,8 @@ __global__ void __launch_bounds__(BX* BY)
               double* __restrict__ r, double* __restrict__ p, double* __restrict__ partials) {
   const int i = blockIdx.x * BX + threadIdx.x + G;
   const int j = blockIdx.y * BY + threadIdx.y + G;
-  const int k0 = blockIdx.z * ZCH + G, k1 = min(k0 + ZCH, G + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + G, k1 = min(k0 + zc, G + d.nk());
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
   double s2 = 0.0;
   if (i < G + d.ni() && j < G + d.nj()) {
@@ -811,7 +846,8 @@ __global__ void __launch_bounds__(BX* BY)
   if (st->done) return;
   const int i = blockIdx.x * BX + threadIdx.x + G;
   const int j = blockIdx.y * BY + threadIdx.y + G;
-  const int k0 = blockIdx.z * ZCH + G, k1 = min(k0 + ZCH, G + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + G, k1 = min(k0 + zc, G + d.nk());
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
   double s2 = 0.0;
   if (i < G + d.ni() && j < G + d.nj()) {
@@ -835,7 +871,8 @@ __global__ void __launch_bounds__(BX* BY)
   const double alpha = st->alpha;
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
-  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
   double s2 = 0.0;
   if (i < g + d.ni() && j < g + d.nj()) {
     for (int k = k0; k < k1; k++) {
@@ -859,7 +896,8 @@ __global__ void __launch_bounds__(BX* BY)
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
   if (i >= g + d.ni() || j >= g + d.nj()) return;
-  const int k0 = blockIdx.z * ZCH + g, k1 = min(k0 + ZCH, g + d.nk());
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
   for (int k = k0; k < k1; k++) {
     const long long c = d.at(i, j, k);
     p[c] = fma(beta, p[c], r[c]);

@@ -112,6 +112,21 @@ struct ProfRec {
   int fp64;
 };
 
+// Per-kernel-class totals of timed launches.
+struct ProfAcc {
+  long long n = 0;
+  double ms = 0.0, bytes = 0.0, ops = 0.0;
+  int fp64 = 0;
+};
+
+// A captured iteration body with CUDA-event record nodes around its hot
+// kernels (a plain graph: event nodes cannot sit inside conditional bodies).
+struct ProfGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfRec> slots;
+  long long body_kernels = 0;
+};
+
 struct ps_ctx {
   ps_grid grid{};
   int order = 2;
@@ -147,6 +162,9 @@ struct ps_ctx {
   // profiler
   bool prof = false;
   std::vector<ProfRec> recs;
+  std::vector<ProfRec>* cap_slots = nullptr;   // non-null while capturing a profiling graph
+  std::map<std::string, ProfGraph> pgraphs;
+  ProfAcc acc[PC_COUNT];
   std::vector<cudaEvent_t> ev_pool;
   int prof_open = -1;
   long long nlaunch = 0;   // kernels launched by the current solve
@@ -174,7 +192,8 @@ ps_status fail(ps_status s, const char* fmt, ...) {
 
 // Profiler: begin/end pair around one launch on stream s.
 void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStream_t s) {
-  if (!h->prof || h->recs.size() >= 16384) return;
+  std::vector<ProfRec>& sink = h->cap_slots ? *h->cap_slots : h->recs;
+  if (!h->prof || sink.size() >= 16384) return;
   ProfRec r;
   r.cls = cls;
   r.bytes = bytes;
@@ -188,13 +207,17 @@ void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStre
       return;
     }
   }
-  cudaEventRecord(r.a, s);
-  h->recs.push_back(r);
-  h->prof_open = (int)h->recs.size() - 1;
+  // inside a stream capture only an external record becomes an event-record node
+  if (h->cap_slots) cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+  else cudaEventRecord(r.a, s);
+  sink.push_back(r);
+  h->prof_open = (int)sink.size() - 1;
 }
 void prof_end(ps_ctx* h, cudaStream_t s) {
   if (h->prof_open < 0) return;
-  cudaEventRecord(h->recs[h->prof_open].b, s);
+  std::vector<ProfRec>& sink = h->cap_slots ? *h->cap_slots : h->recs;
+  if (h->cap_slots) cudaEventRecordWithFlags(sink[h->prof_open].b, s, cudaEventRecordExternal);
+  else cudaEventRecord(sink[h->prof_open].b, s);
   h->prof_open = -1;
 }
 
@@ -672,11 +695,55 @@ ps_status step_active(ps_ctx* h, int k) {
     return sph_ir_step(h, s);
   }
   if (h->prof) {
-    // event records cannot sit inside graph bodies: launch directly, after a
-    // state read so that no iteration runs past convergence
+    // Event records cannot sit inside conditional graph bodies, so profiling
+    // replays one iteration per launch from a plain graph that carries event
+    // record nodes around the hot kernels, after a state read so that no
+    // iteration runs past convergence; the events are harvested after each
+    // launch (no host gaps between the kernels being timed).
     if ((r = read_state(h, s)) != PS_OK) return r;
+    ProfGraph& pg = h->pgraphs[h->act.key];
+    if (!pg.exec) {
+      while (h->ev_pool.size() < 512) {
+        cudaEvent_t ev;
+        TRY(cudaEventCreate(&ev));
+        h->ev_pool.push_back(ev);
+      }
+      const long long before = h->nlaunch;
+      TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      h->cap_slots = &pg.slots;
+      cudaError_t eb = h->act.body(0ull, 0, h->cap);
+      h->cap_slots = nullptr;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+      if (eb != cudaSuccess) e = eb;
+      pg.body_kernels = h->nlaunch - before;
+      h->nlaunch = before;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&pg.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        pg.exec = nullptr;
+        return fail(PS_ERR_CUDA, "building the profiling graph: %s", cudaGetErrorString(e));
+      }
+    }
     const int n = std::min(k, h->act.plain_chunk);
-    for (int q = 0; q < n && h->hst->done == DONE_NO; q++) TRY(h->act.body(0ull, 0, s));
+    for (int q = 0; q < n && h->hst->done == DONE_NO; q++) {
+      TRY(cudaGraphLaunch(pg.exec, s));
+      TRY(cudaStreamSynchronize(s));
+      h->nlaunch += pg.body_kernels;
+      for (auto& rec : pg.slots) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, rec.a, rec.b) != cudaSuccess) {
+          (void)cudaGetLastError();   // a slot that did not run leaves no sticky error
+          continue;
+        }
+        ProfAcc& a = h->acc[rec.cls];
+        a.n++;
+        a.ms += ms;
+        a.bytes = rec.bytes;
+        a.ops = rec.ops;
+        a.fp64 = rec.fp64;
+      }
+    }
     h->act.plain_steps = true;
     return PS_OK;
   }
@@ -884,6 +951,14 @@ void poisson_destroy(ps_handle h) {
   for (auto& kv : h->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
+  for (auto& kv : h->pgraphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& rec : kv.second.slots) {
+      cudaEventDestroy(rec.a);
+      cudaEventDestroy(rec.b);
+    }
+  }
+  h->pgraphs.clear();
   cudaFree(h->phi0);
   cudaFree(h->ir_e);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -1088,6 +1163,14 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
   }
   struct Acc { int64_t n = 0; double ms = 0, bytes = 0, ops = 0; int fp64 = 0; };
   std::vector<Acc> acc(PC_COUNT);
+  for (int c = 0; c < PC_COUNT; c++) {
+    acc[c].n = h->acc[c].n;
+    acc[c].ms = h->acc[c].ms;
+    acc[c].bytes = h->acc[c].bytes;
+    acc[c].ops = h->acc[c].ops;
+    acc[c].fp64 = h->acc[c].fp64;
+    h->acc[c] = ProfAcc();
+  }
   for (auto& r : h->recs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
