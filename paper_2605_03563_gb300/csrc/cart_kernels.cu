@@ -276,17 +276,56 @@ __global__ void __launch_bounds__(BX* BY)
   const int kn0 = blockIdx.z * zc + 1;
   const int kn1 = min(kn0 + zc, d.nk() + 1);
   const long long sy = d.ex, sz = (long long)d.ex * d.ey;
-  for (int kn = kn0; kn < kn1; kn++) {
-    int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;
-    int in = 1 + r0 + NCOL * t;
-    if (in > d.ni()) continue;
-    const long long p = d.at(in + G - 1, jn + G - 1, kn + G - 1);
-    C gs = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p));
-    if (OM1) {
-      S::st(phi + p, gs);
-    } else {
-      C old = S::ld(phi + p);
-      S::st(phi + p, fma(omega, gs - old, old));
+  auto site = [&](int kn) -> long long {
+    const int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;
+    const int in = 1 + r0 + NCOL * t;
+    return in > d.ni() ? -1 : d.at(in + G - 1, jn + G - 1, kn + G - 1);
+  };
+  if constexpr (G == 1 && sizeof(T) == sizeof(double)) {
+    // FP64 7-point: a colour point's neighbours all have the other colour and
+    // are never written in this pass, so the operands of the next z point are
+    // loaded before this point's store (two points' loads in flight).  (For
+    // FP32/BF16 storage the plain loop measured faster.)
+    struct Ops { C s6, f, c; };
+    auto load = [&](long long p) -> Ops {
+      Ops o;
+      o.s6 = ((S::ld(phi + p + 1) + S::ld(phi + p - 1)) + (S::ld(phi + p + sy) + S::ld(phi + p - sy))) +
+             (S::ld(phi + p + sz) + S::ld(phi + p - sz));
+      o.f = S::ld(fs + p);
+      o.c = OM1 ? (C)0 : S::ld(phi + p);
+      return o;
+    };
+    long long p = kn0 < kn1 ? site(kn0) : -1;
+    Ops cur{};
+    if (p >= 0) cur = load(p);
+    for (int kn = kn0; kn < kn1; kn++) {
+      const long long pn = kn + 1 < kn1 ? site(kn + 1) : -1;
+      Ops nxt{};
+      if (pn >= 0) nxt = load(pn);
+      if (p >= 0) {
+        C gs;
+        if (ISO) {
+          gs = fma(cur.s6, cf.c1[0], cur.f);
+        } else {
+          gs = gs_value<G, ISO>(phi, p, sy, sz, cf, cur.f);
+        }
+        if (OM1) S::st(phi + p, gs);
+        else S::st(phi + p, fma(omega, gs - cur.c, cur.c));
+      }
+      p = pn;
+      cur = nxt;
+    }
+  } else {
+    for (int kn = kn0; kn < kn1; kn++) {
+      const long long p = site(kn);
+      if (p < 0) continue;
+      C gs = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p));
+      if (OM1) {
+        S::st(phi + p, gs);
+      } else {
+        C old = S::ld(phi + p);
+        S::st(phi + p, fma(omega, gs - old, old));
+      }
     }
   }
 }
@@ -389,42 +428,78 @@ cudaError_t launch_restrict(const Dims& fine, int dt_f, const void* delta_f, int
 }
 
 // ------------------------------------------------------------------ prolongation
-// phi_fine += P e_coarse, P = 8 R^T: a fine node at an even index along an axis
-// takes the coincident coarse node, an odd one the mean of the two neighbours.
+// phi_fine += P e_coarse, P = 8 R^T (trilinear).  One thread per coarse cell
+// (I..I+1, J..J+1, K..K+1): it loads the cell's 8 corner values once and
+// updates the cell's fine nodes 2I+a, 2J+b, 2K+c (a,b,c in {0,1}) by separable
+// interpolation (x, then y, then z; a node midway between two coarse nodes
+// takes their mean).  Fine node 0 of an axis is the boundary and is skipped;
+// coarse boundary values are zero.  Every interior fine node belongs to exactly
+// one cell.
 template <typename TC, typename TF>
 __global__ void __launch_bounds__(BX* BY)
     k_prolong(Dims fd, Dims cd, const TC* __restrict__ ec, TF* __restrict__ phif) {
   using CF = typename St<TF>::C;
-  const int in = blockIdx.x * BX + threadIdx.x + 1;
-  const int jn = blockIdx.y * BY + threadIdx.y + 1;
-  if (in > fd.ni() || jn > fd.nj()) return;
-  const int zc = zchunk(fd.nk());
-  const int kn0 = blockIdx.z * zc + 1;
-  const int kn1 = min(kn0 + zc, fd.nk() + 1);
+  const int I = blockIdx.x * BX + threadIdx.x;   // cell index 0 .. nc-1
+  const int J = blockIdx.y * BY + threadIdx.y;
+  if (I >= cd.nx || J >= cd.ny) return;
+  const int zc = zchunk(cd.nz);
+  const int K0 = blockIdx.z * zc, K1 = min(K0 + zc, cd.nz);
   const int g = fd.g;
-  const int oi = in & 1, oj = jn & 1;
-  const int I0 = in >> 1, J0 = jn >> 1;
-  for (int kn = kn0; kn < kn1; kn++) {
-    const int ok = kn & 1, K0 = kn >> 1;
-    CF s = 0;
-    for (int a = 0; a <= ok; a++)
-      for (int b = 0; b <= oj; b++) {
-        const long long row = cd.at(I0 + g - 1, J0 + b + g - 1, K0 + a + g - 1);
-        CF v = (CF)St<TC>::ld(ec + row);
-        if (oi) v += (CF)St<TC>::ld(ec + row + 1);
-        s += v;
+  const long long csy = cd.ex, csz = (long long)cd.ex * cd.ey;
+  const long long fsy = fd.ex, fsz = (long long)fd.ex * fd.ey;
+  const CF half = (CF)0.5;
+  for (int K = K0; K < K1; K++) {
+    const long long c0 = cd.at(I + g - 1, J + g - 1, K + g - 1);
+    CF c[2][2][2];   // [z][y][x]
+#pragma unroll
+    for (int z = 0; z < 2; z++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        c[z][y][0] = (CF)St<TC>::ld(ec + c0 + z * csz + y * csy);
+        c[z][y][1] = (CF)St<TC>::ld(ec + c0 + z * csz + y * csy + 1);
       }
-    const int nodd = oi + oj + ok;
-    const CF scale = nodd == 0 ? (CF)1 : nodd == 1 ? (CF)0.5 : nodd == 2 ? (CF)0.25 : (CF)0.125;
-    const long long p = fd.at(in + g - 1, jn + g - 1, kn + g - 1);
-    St<TF>::st(phif + p, fma(s, scale, St<TF>::ld(phif + p)));
+    CF vx[2][2][2];   // [z][y][a]: x-interpolated
+#pragma unroll
+    for (int z = 0; z < 2; z++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        vx[z][y][0] = c[z][y][0];
+        vx[z][y][1] = half * (c[z][y][0] + c[z][y][1]);
+      }
+    CF vy[2][2][2];   // [z][b][a]
+#pragma unroll
+    for (int z = 0; z < 2; z++)
+#pragma unroll
+      for (int a = 0; a < 2; a++) {
+        vy[z][0][a] = vx[z][0][a];
+        vy[z][1][a] = half * (vx[z][0][a] + vx[z][1][a]);
+      }
+    const long long f0 = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++) {
+      if (cz == 0 && K == 0) continue;
+#pragma unroll
+      for (int b = 0; b < 2; b++) {
+        if (b == 0 && J == 0) continue;
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+          if (a == 0 && I == 0) continue;
+          const CF v = cz == 0 ? vy[0][b][a] : half * (vy[0][b][a] + vy[1][b][a]);
+          const long long p = f0 + cz * fsz + b * fsy + a;
+          St<TF>::st(phif + p, St<TF>::ld(phif + p) + v);
+        }
+      }
+    }
   }
 }
 
 template <typename TC, typename TF>
 static cudaError_t prolong_t(const Dims& fine, const void* ec, void* phif, cudaStream_t s) {
   Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2, fine.g);
-  k_prolong<TC, TF><<<point_grid(fine), dim3(BX, BY), 0, s>>>(fine, cd, (const TC*)ec, (TF*)phif);
+  const int gx = (cd.nx + BX - 1) / BX, gy = (cd.ny + BY - 1) / BY;
+  const int zc = zchunk_for(gx * gy, cd.nz);
+  const dim3 grid(gx, gy, (cd.nz + zc - 1) / zc);
+  k_prolong<TC, TF><<<grid, dim3(BX, BY), 0, s>>>(fine, cd, (const TC*)ec, (TF*)phif);
   return cudaGetLastError();
 }
 
