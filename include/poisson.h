@@ -81,9 +81,17 @@ typedef struct {
 typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3 } ps_method;
 
 /* PS_FP64: every kernel computes and stores in FP64.
- * PS_MIXED_FP32: FP64 iterative refinement (outer residual, correction, norms,
- *   multipole moments and coarsest solve in FP64) around FP32 inner solves.
- * PS_MIXED_BF16: as PS_MIXED_FP32, with the finest inner level stored in BF16. */
+ * PS_MIXED_FP32: Cartesian: FP64 iterative refinement (outer residual,
+ *   correction, norms, multipole moments and coarsest solve in FP64) around
+ *   FP32 inner V-cycles.  Spherical: BiCGSTAB with FP32 Krylov vectors and the
+ *   iterate, right-hand side, true residuals and dot products in FP64.  Its
+ *   convergence needs cond(A B^-1) * 2^-24 well below 1, which strongly graded
+ *   grids violate; it then ends with PS_NOT_CONVERGED.
+ * PS_MIXED_BF16: as PS_MIXED_FP32, with the finest inner level stored in BF16
+ *   (Cartesian; spherical treats it as PS_MIXED_FP32).
+ * Spherical BiCGSTAB in either precision stops on the true residual b - A x,
+ * which replaces the recursively updated one at every hundredfold drop
+ * (residual replacement). */
 typedef enum { PS_FP64 = 0, PS_MIXED_FP32 = 1, PS_MIXED_BF16 = 2 } ps_precision;
 
 typedef struct {
@@ -92,7 +100,7 @@ typedef struct {
   double omega;          /* SOR weight (Sec. 2.1.1); MG smoothing uses 1 */
   int32_t nu1, nu2;      /* V(nu1,nu2) pre-/post-smoothing sweeps */
   int32_t max_iter;      /* SOR steps / CG or BiCGSTAB iterations / V-cycles / IR steps */
-  int32_t inner_cycles;  /* mixed modes: V-cycles (or Krylov iterations) per IR step */
+  int32_t inner_cycles;  /* Cartesian mixed modes: inner V-cycles per IR step (spherical: unused) */
   void* stream;          /* cudaStream_t; NULL = CUDA's default stream */
 } ps_solve_opts;
 
@@ -103,7 +111,7 @@ typedef struct {
   double rho_conv;           /* Eq. rho: (||r_m|| / ||r_0||)^(1/m) */
   double t_mp_ms;            /* multipole boundary time (moments + faces) */
   double t_iter_ms;          /* iteration time */
-  int64_t inner_cycles;      /* mixed modes: total inner V-cycles / Krylov iterations */
+  int64_t inner_cycles;      /* Cartesian mixed: total inner V-cycles; spherical mixed: residual replacements */
   int64_t coarse_iterations; /* MG: total CG iterations on the coarsest level */
   int64_t kernel_launches;   /* CUDA kernels this solve launched */
   double moments[81];        /* first min((l_max+1)^2, 81) multipole moments q_lm, index l*l+l+m */

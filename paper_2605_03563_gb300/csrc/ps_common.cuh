@@ -125,9 +125,15 @@ struct DevState {
   int done;           // 1 converged, 2 not converged (max_iter), 3 diverged
   int coarse_iter_last;
   int chunk_end;      // a captured loop continues while iter < chunk_end (set per step)
-  int early;          // BiCGSTAB: converged at the s check of this iteration
+  int pad0_;
   long long coarse_iter_total;
-  long long inner_cycles;
+  long long inner_cycles;   // IR inner cycles; FP32 BiCGSTAB: residual replacements
+  // BiCGSTAB: breakdown restart and residual replacement
+  double rmax;        // largest recurrence residual norm since the last replacement
+  int broke;          // alpha or omega broke down in this iteration
+  int restart;        // the next direction update restarts rhat = p = r
+  int replace;        // the true residual replaces the recurrence one this iteration
+  int pad1_;
 };
 
 enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };

@@ -93,10 +93,10 @@ struct Active {
   std::string key;
   Body body;
   int chunk = 32, plain_chunk = 1;
-  bool host_driven = false, plain_steps = false;
-  long long body_kernels = 0, inner_total = 0;
-  int inner_per_iter = 0, inner_max = 400;
-  double sph_fscale = 0.0;
+  bool plain_steps = false;
+  bool count_replacements = false;   // inner_cycles reports FP32 BiCGSTAB residual replacements
+  long long body_kernels = 0;
+  int inner_per_iter = 0;
 };
 
 // A captured iteration body inside a CUDA-graph while loop.
@@ -136,8 +136,6 @@ struct ps_ctx {
   cudaStream_t stream = nullptr;
   DevState* st = nullptr;    // device
   DevState* hst = nullptr;   // pinned host mirror
-  DevState* st2 = nullptr;   // inner state (spherical refinement)
-  DevState* hst2 = nullptr;
   double* partials = nullptr;
   int npart = 0;
   // Cartesian
@@ -156,7 +154,7 @@ struct ps_ctx {
   SphTables stab;
   void* sv[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int sv_dt = -1;
-  float* ir_rhs = nullptr;
+  double* sz = nullptr;   // BiCGSTAB group-wise increments of the iterate (FP64)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   size_t bytes = 0;
   // profiler
@@ -172,7 +170,6 @@ struct ps_ctx {
   std::map<std::string, LoopGraph> graphs;
   cudaStream_t cap = nullptr;
   double* phi0 = nullptr;  // internal finest-level potential (Cartesian) / unknowns (spherical)
-  float* ir_e = nullptr;   // spherical refinement: inner correction
   Active act;
   DevState* st_active = nullptr;   // the state the loop gate reads (= st)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -542,8 +539,10 @@ ps_status begin_cg(ps_ctx* h, cudaStream_t s) {
 // ------------------------------------------------------------------ spherical solves
 ps_status sph_vectors(ps_ctx* h, int dt) {
   if (h->sv_dt == dt) return PS_OK;
-  for (auto& p : h->sv) { cudaFree(p); p = nullptr; }
   const size_t n = (size_t)h->sd.size();
+  if (h->sv_dt >= 0) h->bytes -= 8 * n * dt_size(h->sv_dt);
+  for (auto& p : h->sv) { cudaFree(p); p = nullptr; }
+  h->sv_dt = -1;
   for (int q = 0; q < 8; q++) {
     ps_status r = alloc_zero(&h->sv[q], n * dt_size(dt), &h->bytes);
     if (r != PS_OK) return r;
@@ -552,28 +551,44 @@ ps_status sph_vectors(ps_ctx* h, int dt) {
   return PS_OK;
 }
 
-// Enqueue a BiCGSTAB start (reference and initial residual) for storage dt and
-// return its iteration body.  vectors: 0 r, 1 rhat, 2 p, 3 phat, 4 v, 5 s, 6 shat, 7 t
-ps_status bicg_start(ps_ctx* h, int dt, const double* rho, double fscale, const void* fin, void* x,
-                     DevState* st, double tol, int max_iter, cudaStream_t s, Body* body) {
+// Enqueue a BiCGSTAB start (reference and initial residual) with Krylov
+// vectors of storage dt and return its iteration body.  x is the FP64 iterate.
+// vectors: 0 r, 1 rhat, 2 p, 3 phat, 4 v, 5 s, 6 shat, 7 t
+ps_status bicg_start(ps_ctx* h, int dt, const double* rho, double fscale, double* x, DevState* st,
+                     double tol, int max_iter, cudaStream_t s, Body* body) {
   int nb = 0;
   void** v = h->sv;
   TRY((h->nlaunch += 1, launch_init_state(st, tol, max_iter, s)));
-  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 0, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 0, rho, fscale, x, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, st, s)));
-  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 1, rho, fscale, fin, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 1, rho, fscale, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 1, st, s)));
-  *body = [h, dt, x, v, st](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+  if (!h->sz) {
+    ps_status r = alloc_zero((void**)&h->sz, (size_t)h->sd.size() * sizeof(double), &h->bytes);
+    if (r != PS_OK) return r;
+  }
+  TRY(cudaMemsetAsync(h->sz, 0, (size_t)h->sd.size() * sizeof(double), s));
+  double* z = h->sz;
+  *body = [h, dt, rho, fscale, x, z, v, st](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
     const double n = (double)h->sd.nr * h->sd.nt * h->sd.np;
     const double S = dt == DT_F64 ? 8.0 : 4.0;
-    prof_begin(h, PC_KRYLOV, n * S * 16.0, n * 60.0, dt == DT_F64, q);
-    cudaError_t e = (h->nlaunch += 9, launch_bicg_iter(h->sd, h->stab, dt, x, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->partials, st, q, cond, chunk));
+    // 21 vector streams of the storage type (apply 3, s 4, apply 3, x/r 6,
+    // p 5) plus the FP64 increment z read and written; replacements (a few
+    // per hundred iterations) are not counted
+    const double bytes = n * (S * 21.0 + 16.0);
+    prof_begin(h, PC_KRYLOV, bytes, n * 60.0, dt == DT_F64, q);
+    h->nlaunch += bicg_iter_kernels(dt);
+    cudaError_t e = launch_bicg_iter(h->sd, h->stab, dt, rho, fscale, x, z, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], h->partials, st, q, cond, chunk);
     prof_end(h, q);
     return e;
   };
   return PS_OK;
 }
 
+// Spherical solve: right-Jacobi BiCGSTAB stopping on true residuals.  PS_FP64
+// keeps every vector in FP64; the mixed precisions keep the Krylov vectors in
+// FP32 and the iterate, the right-hand side, the replaced residuals and every
+// dot product in FP64.
 ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, const ps_solve_opts* o,
                     cudaStream_t s) {
   ps_status r;
@@ -588,51 +603,11 @@ ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, 
   const double fscale = 4.0 * M_PI * h->bc.G;
   h->act.chunk = KRYLOV_GRAPH_CHUNK;
   h->act.plain_chunk = KRYLOV_CHUNK;
-  if (o->prec == PS_FP64) {
-    if ((r = sph_vectors(h, DT_F64)) != PS_OK) return r;
-    h->act.key = "bicg64";
-    return bicg_start(h, DT_F64, rho, fscale, nullptr, phi, h->st, tol, o->max_iter, s, &h->act.body);
-  }
-  // FP64 iterative refinement around FP32 BiCGSTAB: the outer steps are driven
-  // from the host (each step runs an inner solve to its own tolerance)
-  if ((r = sph_vectors(h, DT_F32)) != PS_OK) return r;
-  const size_t n = (size_t)h->sd.size();
-  if (!h->ir_rhs && (r = alloc_zero((void**)&h->ir_rhs, n * 4, &h->bytes)) != PS_OK) return r;
-  if (!h->ir_e && (r = alloc_zero((void**)&h->ir_e, n * 4, &h->bytes)) != PS_OK) return r;
-  int nb = 0;
-  TRY((h->nlaunch += 1, launch_init_state(h->st, tol, o->max_iter, s)));
-  TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, DT_F64, 0, rho, fscale, nullptr, phi, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
-  TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, h->st, s)));
-  TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, rho, fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
-  h->act.host_driven = true;
-  h->act.sph_fscale = fscale;
-  h->act.inner_max = o->inner_cycles > 0 ? o->inner_cycles : 400;
-  return PS_OK;
-}
-
-// One outer refinement step of the spherical mixed solve (host driven).
-ps_status sph_ir_step(ps_ctx* h, cudaStream_t s) {
-  const size_t n = (size_t)h->sd.size();
-  float* e = h->ir_e;
-  double* phi = h->phi0;
-  TRY(cudaMemsetAsync(e, 0, n * 4, s));
-  Body inner;
-  ps_status r = bicg_start(h, DT_F32, nullptr, 1.0, h->ir_rhs, e, h->st2, 1e-4, h->act.inner_max, s, &inner);
-  if (r != PS_OK) return r;
-  TRY(cudaMemcpyAsync(h->hst2, h->st2, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  TRY(cudaStreamSynchronize(s));
-  while (h->hst2->done == DONE_NO) {
-    for (int q = 0; q < KRYLOV_CHUNK; q++) TRY(inner(0ull, 0, s));
-    TRY(cudaMemcpyAsync(h->hst2, h->st2, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    TRY(cudaStreamSynchronize(s));
-  }
-  h->act.inner_total += h->hst2->iter;
-  int nb = 0;
-  TRY((h->nlaunch += 1, launch_sph_correct(h->sd, DT_F32, e, phi, h->st, s)));
-  TRY((h->nlaunch += 1, launch_sph_outer_resid(h->sd, h->stab, h->act.rho, h->act.sph_fscale, phi, h->ir_rhs, h->st, h->partials, &nb, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, s)));
-  return PS_OK;
+  const int dt = o->prec == PS_FP64 ? DT_F64 : DT_F32;
+  if ((r = sph_vectors(h, dt)) != PS_OK) return r;
+  h->act.key = dt == DT_F64 ? "bicg64" : "bicg32";
+  h->act.count_replacements = dt != DT_F64;
+  return bicg_start(h, dt, rho, fscale, phi, h->st, tol, o->max_iter, s, &h->act.body);
 }
 
 // ------------------------------------------------------------------ stepping
@@ -689,11 +664,6 @@ ps_status build_loop_graph(ps_ctx* h, LoopGraph* g) {
 ps_status step_active(ps_ctx* h, int k) {
   cudaStream_t s = h->stream;
   ps_status r;
-  if (h->act.host_driven) {   // spherical refinement: one outer step, synchronously
-    if ((r = read_state(h, s)) != PS_OK) return r;
-    if (h->hst->done != DONE_NO) return PS_OK;
-    return sph_ir_step(h, s);
-  }
   if (h->prof) {
     // Event records cannot sit inside conditional graph bodies, so profiling
     // replays one iteration per launch from a plain graph that carries event
@@ -760,7 +730,7 @@ ps_status poll_active(ps_ctx* h, int* done) {
   const int it0 = h->hst->iter;
   ps_status r = read_state(h, h->stream);
   if (r != PS_OK) return r;
-  if (!h->act.plain_steps && !h->act.host_driven && h->hst->iter > it0)
+  if (!h->act.plain_steps && h->hst->iter > it0)
     h->nlaunch += h->act.body_kernels * (h->hst->iter - it0);
   h->act.plain_steps = false;
   *done = h->hst->done != DONE_NO;
@@ -774,7 +744,7 @@ void fill_info(ps_ctx* h, ps_info* info, ps_status st, bool final_) {
   info->iterations = d.iter;
   info->rel_residual = d.rel;
   info->rho_conv = (d.iter > 0 && d.rel0 > 0.0) ? std::pow(d.rel / d.rel0, 1.0 / d.iter) : 0.0;
-  info->inner_cycles = h->act.host_driven ? h->act.inner_total : (long long)d.iter * h->act.inner_per_iter;
+  info->inner_cycles = h->act.count_replacements ? d.inner_cycles : (long long)d.iter * h->act.inner_per_iter;
   info->coarse_iterations = d.coarse_iter_total;
   info->kernel_launches = h->nlaunch;
   info->status = st;
@@ -829,7 +799,9 @@ size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max
   if (grid->kind == PS_GRID_SPHERICAL) {
     const size_t n = (size_t)(grid->n[0] + 2) * (grid->n[1] + 2) * (grid->n[2] + 2);
     const size_t vec = prec == PS_FP64 ? 8 : 4;
-    return n * (8 * vec + (prec == PS_FP64 ? 0 : 8)) + (size_t)grid->n[0] * grid->n[1] * 16;
+    // 8 Krylov vectors, the FP64 iterate and its increments, and the
+    // (r, theta) diagonal tables
+    return n * (8 * vec + 16) + (size_t)grid->n[0] * grid->n[1] * 16;
   }
   return 0;
 }
@@ -896,11 +868,8 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
       (e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming)) != cudaSuccess)
     return bail(fail(PS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)));
   if ((e = cudaMalloc(&h->st, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "state alloc"));
-  if ((e = cudaMalloc(&h->st2, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "state alloc"));
   if ((e = cudaMallocHost(&h->hst, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "pinned alloc"));
-  if ((e = cudaMallocHost(&h->hst2, sizeof(DevState))) != cudaSuccess) return bail(fail(PS_ERR_OOM, "pinned alloc"));
   memset(h->hst, 0, sizeof(DevState));
-  memset(h->hst2, 0, sizeof(DevState));
   h->st_active = h->st;
   ps_status s;
   if (!h->sph) {
@@ -960,7 +929,6 @@ void poisson_destroy(ps_handle h) {
   }
   h->pgraphs.clear();
   cudaFree(h->phi0);
-  cudaFree(h->ir_e);
   if (h->cap) cudaStreamDestroy(h->cap);
   free_hier(&h->h64);
   free_hier(&h->hmx[0]);
@@ -972,12 +940,10 @@ void poisson_destroy(ps_handle h) {
   cart_multipole_free(&h->mp);
   sph_tables_free(&h->stab);
   for (auto& p : h->sv) cudaFree(p);
-  cudaFree(h->ir_rhs);
+  cudaFree(h->sz);
   cudaFree(h->partials);
   cudaFree(h->st);
-  cudaFree(h->st2);
   if (h->hst) cudaFreeHost(h->hst);
-  if (h->hst2) cudaFreeHost(h->hst2);
   for (auto& ev : h->ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& r : h->recs) {

@@ -1,7 +1,8 @@
 // Spherical grids: variable-coefficient Laplacian (Eq. 2), right-Jacobi
 // BiCGSTAB (Sec. 2.1.2, van der Vorst's method as described by Saad, with the
-// preconditioner B^-1 = diag(A)^-1 applied to vectors, never formed), and the
-// multipole outer boundary (Sec. 2.2).
+// preconditioner B^-1 = diag(A)^-1 applied to vectors, never formed; stopping
+// on true residuals by Sleijpen and van der Vorst's residual replacement), and
+// the multipole outer boundary (Sec. 2.2).
 //
 // Operator in flux form on nodes r_i, theta_j, phi_k:
 //   L p = rad_p_i (p_{i+1} - p) - rad_m_i (p - p_{i-1})
@@ -81,49 +82,63 @@ cudaError_t launch_sph_apply(const SphDims& d, const SphTables& t, const double*
 }
 
 // ------------------------------------------------------------------ BiCGSTAB kernels
+// One iteration: v = L phat; alpha; s = r - alpha v, shat = B^-1 s; t = L shat;
+// omega; x += alpha phat + omega shat, r = s - omega t; then either the
+// recurrence residual stands, or (on a drop to REPLACE_DROP of its largest
+// value since the last replacement, a claim of convergence, a breakdown or the
+// end of the budget) r is replaced by the FP64 true residual b - L x and the
+// stopping decision is taken on it; last the direction update (or restart).
+// The iterate is updated group-wise: the increments accumulate in z (FP64) and
+// are added to x only at a replacement, so x is rounded once per replacement
+// (every rounding of x is amplified by the pole coefficients, up to ~1e11).
+// The Krylov vectors are stored as T (double or float); x, the right-hand side
+// f = fscale * rho and all dot products are FP64.
+static constexpr double REPLACE_DROP = 0.01;
+
+//   mode 0: partials {|b|^2, |b|^2} for b = f - L(boundary part of x)
+//   mode 1: r = rhat = p = f - L x, phat = B^-1 r; partials {r.r, r.r}
+//   mode 2 (only while st->replace is set): r = f - L x; partials
+//           {r.r (FP64), rhat.r}
 template <typename T>
 __global__ void __launch_bounds__(SBX* SBY)
-    k_bicg_resid(SphDims d, Tab<typename St<T>::C> tb, int mode, const double* __restrict__ rho,
-                 double fscale, const T* __restrict__ fin, const void* __restrict__ xv,
-                 int x_is_f64, T* __restrict__ r, T* __restrict__ rhat, T* __restrict__ p,
-                 T* __restrict__ phat, double* __restrict__ partials) {
-  using C = typename St<T>::C;
+    k_bicg_resid(SphDims d, Tab<double> tb, int mode, const double* __restrict__ rho, double fscale,
+                 const double* __restrict__ x, T* __restrict__ r, T* __restrict__ rhat,
+                 T* __restrict__ p, T* __restrict__ phat, double* __restrict__ partials,
+                 const DevState* __restrict__ st) {
+  if (mode == 2 && (st->done || !st->replace)) return;
   const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
   double s0 = 0.0, s1 = 0.0;
   if (i < d.nr && j < d.nt) {
     const long long c = d.at(i, j, k);
-    const C f = rho != nullptr ? (C)(fscale * rho[c]) : (C)fin[c];
-    C Lx;
-    if (mode == 0) {
-      // boundary part only: the outer ghost enters through rad_p at i = nr-1
-      C g = 0;
-      if (i == d.nr - 1)
-        g = x_is_f64 ? (C)((const double*)xv)[c + 1] : (C)((const T*)xv)[c + 1];
-      Lx = tb.rad_p[i] * g;
-    } else {
-      Lx = x_is_f64 ? sph_L<double, C>(d, tb, (const double*)xv, i, j, k, c)
-                    : sph_L<T, C>(d, tb, (const T*)xv, i, j, k, c);
-    }
-    const C rv = f - Lx;
-    s0 = (double)rv * (double)rv;
+    const double f = fscale * rho[c];
+    // mode 0: the outer ghost enters through rad_p at i = nr-1, nothing else
+    const double Lx = mode == 0 ? tb.rad_p[i] * (i == d.nr - 1 ? x[c + 1] : 0.0)
+                                : sph_L<double, double>(d, tb, x, i, j, k, c);
+    const double rv = f - Lx;
+    s0 = rv * rv;
     s1 = s0;
     if (mode == 1) {
       r[c] = (T)rv;
       rhat[c] = (T)rv;
       p[c] = (T)rv;
       phat[c] = (T)(rv * tb.inv_diag[j * d.nr + i]);
+    } else if (mode == 2) {
+      const T rs = (T)rv;
+      r[c] = rs;
+      s1 = (double)rs * (double)rhat[c];
     }
   }
   block_sum2(s0, s1, partials);
 }
 
+// dst = L src; partials {dst.w1, dst.dst (with_tt)}
 template <typename T>
 __global__ void __launch_bounds__(SBX* SBY)
     k_bicg_apply(SphDims d, Tab<typename St<T>::C> tb, const T* __restrict__ src, T* __restrict__ dst,
                  const T* __restrict__ w1, int with_tt, double* __restrict__ partials,
-                 const DevState* __restrict__ st, int skip_early) {
+                 const DevState* __restrict__ st) {
   using C = typename St<T>::C;
-  if (st->done || (skip_early && st->early)) return;
+  if (st->done) return;
   const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
   double s0 = 0.0, s1 = 0.0;
   if (i < d.nr && j < d.nt) {
@@ -137,70 +152,83 @@ __global__ void __launch_bounds__(SBX* SBY)
   block_sum2(s0, s1, partials);
 }
 
+// s = r - alpha v, shat = B^-1 s
 template <typename T>
 __global__ void __launch_bounds__(SBX* SBY)
     k_bicg_s(SphDims d, Tab<typename St<T>::C> tb, const T* __restrict__ r, const T* __restrict__ v,
-             T* __restrict__ sv, T* __restrict__ shat, double* __restrict__ partials,
-             const DevState* __restrict__ st) {
+             T* __restrict__ sv, T* __restrict__ shat, const DevState* __restrict__ st) {
   using C = typename St<T>::C;
   if (st->done) return;
   const C alpha = (C)st->alpha;
   const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
-  double s0 = 0.0;
-  if (i < d.nr && j < d.nt) {
-    const long long c = d.at(i, j, k);
-    const C s = fma(-alpha, (C)v[c], (C)r[c]);
-    sv[c] = (T)s;
-    shat[c] = (T)(s * tb.inv_diag[j * d.nr + i]);
-    s0 = (double)s * (double)s;
-  }
-  block_sum2(s0, 0.0, partials);
+  if (i >= d.nr || j >= d.nt) return;
+  const long long c = d.at(i, j, k);
+  const C s = fma(-alpha, (C)v[c], (C)r[c]);
+  sv[c] = (T)s;
+  shat[c] = (T)(s * tb.inv_diag[j * d.nr + i]);
 }
 
+// z += alpha phat + omega shat (FP64 increments since the last replacement),
+// r = s - omega t; partials {r.r, rhat.r}
 template <typename T>
 __global__ void __launch_bounds__(SBX* SBY)
-    k_bicg_xr(SphDims d, void* __restrict__ xv, int x_is_f64, T* __restrict__ r,
-              const T* __restrict__ rhat, const T* __restrict__ phat, const T* __restrict__ sv,
-              const T* __restrict__ shat, const T* __restrict__ tv, double* __restrict__ partials,
+    k_bicg_xr(SphDims d, double* __restrict__ z, T* __restrict__ r, const T* __restrict__ rhat,
+              const T* __restrict__ phat, const T* __restrict__ sv, const T* __restrict__ shat,
+              const T* __restrict__ tv, double* __restrict__ partials,
               const DevState* __restrict__ st) {
   using C = typename St<T>::C;
   if (st->done) return;
-  const int early = st->early;
   const double alpha = st->alpha, omega = st->omega;
   const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
   double s0 = 0.0, s1 = 0.0;
   if (i < d.nr && j < d.nt) {
     const long long c = d.at(i, j, k);
-    double dx = alpha * (double)phat[c];
-    if (!early) dx = fma(omega, (double)shat[c], dx);
-    if (x_is_f64) ((double*)xv)[c] += dx;
-    else ((T*)xv)[c] = (T)((C)((T*)xv)[c] + (C)dx);
-    if (!early) {
-      const C rv = fma(-(C)omega, (C)tv[c], (C)sv[c]);
-      r[c] = (T)rv;
-      s0 = (double)rv * (double)rv;
-      s1 = (double)rv * (double)rhat[c];
-    }
+    z[c] += fma(omega, (double)shat[c], alpha * (double)phat[c]);
+    const C rv = fma(-(C)omega, (C)tv[c], (C)sv[c]);
+    r[c] = (T)rv;
+    s0 = (double)rv * (double)rv;
+    s1 = (double)rv * (double)rhat[c];
   }
-  if (!early) block_sum2(s0, s1, partials);
+  block_sum2(s0, s1, partials);
 }
 
-template <typename T>
+// Group-wise update at a replacement: x += z, z = 0.
 __global__ void __launch_bounds__(SBX* SBY)
-    k_bicg_p(SphDims d, Tab<typename St<T>::C> tb, const T* __restrict__ r, T* __restrict__ p,
-             const T* __restrict__ v, T* __restrict__ phat, const DevState* __restrict__ st) {
-  using C = typename St<T>::C;
-  if (st->done) return;
-  const C beta = (C)st->beta, omega = (C)st->omega;
+    k_bicg_fold(SphDims d, double* __restrict__ x, double* __restrict__ z,
+                const DevState* __restrict__ st) {
+  if (st->done || !st->replace) return;
   const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nr || j >= d.nt) return;
   const long long c = d.at(i, j, k);
+  x[c] += z[c];
+  z[c] = 0.0;
+}
+
+// p = r + beta (p - omega v), phat = B^-1 p; on a restart rhat = p = r.
+template <typename T>
+__global__ void __launch_bounds__(SBX* SBY)
+    k_bicg_p(SphDims d, Tab<typename St<T>::C> tb, const T* __restrict__ r, T* __restrict__ rhat,
+             T* __restrict__ p, const T* __restrict__ v, T* __restrict__ phat,
+             const DevState* __restrict__ st) {
+  using C = typename St<T>::C;
+  if (st->done) return;
+  const C beta = (C)st->beta, omega = (C)st->omega;
+  const int restart = st->restart;
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nr || j >= d.nt) return;
+  const long long c = d.at(i, j, k);
+  if (restart) {
+    const T rv = r[c];
+    rhat[c] = rv;
+    p[c] = rv;
+    phat[c] = (T)((C)rv * tb.inv_diag[j * d.nr + i]);
+    return;
+  }
   const C pv = fma(beta, fma(-omega, (C)v[c], (C)p[c]), (C)r[c]);
   p[c] = (T)pv;
   phat[c] = (T)(pv * tb.inv_diag[j * d.nr + i]);
 }
 
-// which: 0 alpha; 1 s-norm check; 2 omega; 3 r check + beta
 __device__ __forceinline__ void bicg_set_loop(const DevState* st, unsigned long long cond, int chunk) {
   if (chunk > 0) {
     const unsigned int more = (st->done == DONE_NO && st->iter < st->chunk_end) ? 1u : 0u;
@@ -208,6 +236,35 @@ __device__ __forceinline__ void bicg_set_loop(const DevState* st, unsigned long 
   }
 }
 
+// Direction update from the current residual (r.r = rr, rhat.r = rho_new):
+// beta as usual, or a restart rhat = p = r after a breakdown of alpha or omega
+// or an exactly vanishing rhat.r.
+__device__ __forceinline__ void bicg_direction(DevState* st, double rr, double rho_new) {
+  if (st->broke || rho_new == 0.0) {
+    st->restart = 1;
+    st->rho = rr;
+    st->beta = 0.0;
+  } else {
+    st->beta = (rho_new / st->rho) * (st->alpha / st->omega);
+    st->rho = rho_new;
+  }
+  st->broke = 0;
+}
+
+__device__ __forceinline__ void sum_partials2(const double* __restrict__ partials, int nblk,
+                                              double* sh, double (&v)[2]) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+    a += partials[2 * q];
+    b += partials[2 * q + 1];
+  }
+  v[0] = a;
+  v[1] = b;
+  block_sum<2>(v, sh);
+}
+
+// which: 0 alpha; 2 omega; 3 recurrence residual (direction update, or a
+// replacement request that k_bicg_replace_finish completes).
 __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int which,
                               DevState* __restrict__ st, unsigned long long cond, int chunk) {
   __shared__ double sh[64];
@@ -215,59 +272,67 @@ __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int
     if (which == 3 && threadIdx.x == 0) bicg_set_loop(st, cond, chunk);
     return;
   }
-  if ((which == 2) && st->early) return;
-  if (which == 3 && st->early) {
-    if (threadIdx.x == 0) {
-      st->iter += 1;
-      st->rel = sqrt(st->ss) / st->ref;
-      st->done = DONE_CONVERGED;
-      st->early = 0;
-      bicg_set_loop(st, cond, chunk);
-    }
-    return;
-  }
-  double a = 0.0, b = 0.0;
-  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
-    a += partials[2 * q];
-    b += partials[2 * q + 1];
-  }
-  double v[2] = {a, b};
-  block_sum<2>(v, sh);
+  double v[2];
+  sum_partials2(partials, nblk, sh, v);
   if (threadIdx.x != 0) return;
   if (which == 0) {
-    st->alpha = st->rho / v[0];
-  } else if (which == 1) {
-    st->ss = v[0];
-    if (sqrt(v[0]) / st->ref <= st->tol) st->early = 1;
+    st->restart = 0;
+    const double al = st->rho / v[0];
+    st->broke = isfinite(al) ? 0 : 1;
+    st->alpha = isfinite(al) ? al : 0.0;
   } else if (which == 2) {
     st->ts = v[0];
     st->tt = v[1];
-    st->omega = v[0] / v[1];
+    const double om = v[0] / v[1];
+    if (isfinite(om) && om != 0.0) {
+      st->omega = om;
+    } else {
+      st->omega = 0.0;
+      st->broke = 1;
+    }
   } else {
     st->iter += 1;
+    const double rn = sqrt(v[0]);
+    if (!isfinite(rn) || st->broke || rn <= REPLACE_DROP * st->rmax || rn / st->ref <= st->tol ||
+        st->iter >= st->max_iter) {
+      st->replace = 1;   // k_bicg_replace_finish decides and sets the loop
+      return;
+    }
+    st->rmax = fmax(st->rmax, rn);
     st->rr = v[0];
-    const double rel = sqrt(v[0]) / st->ref;
-    st->rel = rel;
-    const double rho_new = v[1];
-    st->beta = (rho_new / st->rho) * (st->alpha / st->omega);
-    st->rho = rho_new;
-    if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
-    else if (rel <= st->tol) st->done = DONE_CONVERGED;
-    else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+    st->rel = rn / st->ref;
+    bicg_direction(st, v[0], v[1]);
     bicg_set_loop(st, cond, chunk);
   }
+}
+
+// After a residual replacement: stop on the true residual, else continue the
+// search direction from it.
+__global__ void k_bicg_replace_finish(const double* __restrict__ partials, int nblk,
+                                      DevState* __restrict__ st, unsigned long long cond, int chunk) {
+  __shared__ double sh[64];
+  if (st->done || !st->replace) return;   // the loop condition is already set
+  double v[2];
+  sum_partials2(partials, nblk, sh, v);
+  if (threadIdx.x != 0) return;
+  st->replace = 0;
+  st->inner_cycles += 1;
+  const double rn = sqrt(v[0]);
+  st->rmax = rn;
+  st->rr = v[0];
+  st->rel = rn / st->ref;
+  if (st->rel <= st->tol) st->done = DONE_CONVERGED;
+  else if (!isfinite(rn)) st->done = DONE_DIVERGED;
+  else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
+  else bicg_direction(st, v[0], v[1]);
+  bicg_set_loop(st, cond, chunk);
 }
 
 __global__ void k_bicg_start(const double* __restrict__ partials, int nblk, int mode,
                              DevState* __restrict__ st) {
   __shared__ double sh[64];
-  double a = 0.0, b = 0.0;
-  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
-    a += partials[2 * q];
-    b += partials[2 * q + 1];
-  }
-  double v[2] = {a, b};
-  block_sum<2>(v, sh);
+  double v[2];
+  sum_partials2(partials, nblk, sh, v);
   if (threadIdx.x != 0) return;
   if (mode == 0) {
     const double ref = sqrt(v[0]);
@@ -277,8 +342,11 @@ __global__ void k_bicg_start(const double* __restrict__ partials, int nblk, int 
   }
   st->rr = v[0];
   st->rho = v[1];
+  st->rmax = sqrt(v[0]);
   st->iter = 0;
-  st->early = 0;
+  st->broke = 0;
+  st->restart = 0;
+  st->replace = 0;
   const double rel = sqrt(v[0]) / st->ref;
   st->rel = rel;
   st->rel0 = rel;
@@ -286,28 +354,19 @@ __global__ void k_bicg_start(const double* __restrict__ partials, int nblk, int 
   if (!isfinite(rel)) st->done = DONE_DIVERGED;
 }
 
-template <typename T>
-static cudaError_t resid_t(const SphDims& d, const SphTables& t, int mode, const double* rho,
-                           double fscale, const void* fin, const void* x, int x_is_f64, void* r,
-                           void* rhat, void* p, void* phat, double* partials, cudaStream_t s) {
-  using C = typename St<T>::C;
-  k_bicg_resid<T><<<sph_grid(d), dim3(SBX, SBY), 0, s>>>(
-      d, tab_of<C>(t), mode, rho, fscale, (const T*)fin, x, x_is_f64, (T*)r, (T*)rhat, (T*)p,
-      (T*)phat, partials);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_bicg_resid(const SphDims& d, const SphTables& t, int dt, int mode,
-                              const double* rho, double fscale, const void* fin, const void* x,
-                              void* r, void* rhat, void* p, void* phat, double* partials, int* nblk,
+                              const double* rho, double fscale, const double* x, void* r,
+                              void* rhat, void* p, void* phat, double* partials, int* nblk,
                               cudaStream_t s) {
-  dim3 g = sph_grid(d);
+  const dim3 g = sph_grid(d), b(SBX, SBY);
   if (nblk) *nblk = g.x * g.y * g.z;
-  // x is the FP64 potential when the arithmetic is FP64 or when rho is given
-  // (outer residual); the inner FP32 solve passes FP32 vectors.
   if (dt == DT_F64)
-    return resid_t<double>(d, t, mode, rho, fscale, fin, x, 1, r, rhat, p, phat, partials, s);
-  return resid_t<float>(d, t, mode, rho, fscale, fin, x, 0, r, rhat, p, phat, partials, s);
+    k_bicg_resid<double><<<g, b, 0, s>>>(d, tab_of<double>(t), mode, rho, fscale, x, (double*)r,
+                                         (double*)rhat, (double*)p, (double*)phat, partials, nullptr);
+  else
+    k_bicg_resid<float><<<g, b, 0, s>>>(d, tab_of<double>(t), mode, rho, fscale, x, (float*)r,
+                                        (float*)rhat, (float*)p, (float*)phat, partials, nullptr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
@@ -317,93 +376,40 @@ cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevSta
 }
 
 template <typename T>
-static cudaError_t iter_t(const SphDims& d, const SphTables& t, void* x, int x_is_f64, void* r,
-                          const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
-                          void* tv, double* partials, DevState* st, cudaStream_t s,
-                          unsigned long long cond, int chunk) {
+static cudaError_t iter_t(const SphDims& d, const SphTables& t, const double* rho, double fscale,
+                          double* x, double* z, void* r, void* rhat, void* p, void* phat, void* v,
+                          void* sv, void* shat, void* tv, double* partials, DevState* st,
+                          cudaStream_t s, unsigned long long cond, int chunk) {
   using C = typename St<T>::C;
   const Tab<C> tb = tab_of<C>(t);
   const dim3 g = sph_grid(d), b(SBX, SBY);
   const int nblk = g.x * g.y * g.z;
-  k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)phat, (T*)v, (const T*)rhat, 0, partials, st, 0);
+  k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)phat, (T*)v, (const T*)rhat, 0, partials, st);
   k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 0, st, 0ull, 0);
-  k_bicg_s<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (const T*)v, (T*)sv, (T*)shat, partials, st);
-  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 1, st, 0ull, 0);
-  k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)shat, (T*)tv, (const T*)sv, 1, partials, st, 1);
+  k_bicg_s<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (const T*)v, (T*)sv, (T*)shat, st);
+  k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)shat, (T*)tv, (const T*)sv, 1, partials, st);
   k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 2, st, 0ull, 0);
-  k_bicg_xr<T><<<g, b, 0, s>>>(d, x, x_is_f64, (T*)r, (const T*)rhat, (const T*)phat, (const T*)sv,
+  k_bicg_xr<T><<<g, b, 0, s>>>(d, z, (T*)r, (const T*)rhat, (const T*)phat, (const T*)sv,
                                (const T*)shat, (const T*)tv, partials, st);
   k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 3, st, cond, chunk);
-  k_bicg_p<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (T*)p, (const T*)v, (T*)phat, st);
+  k_bicg_fold<<<g, b, 0, s>>>(d, x, z, st);
+  k_bicg_resid<T><<<g, b, 0, s>>>(d, tab_of<double>(t), 2, rho, fscale, x, (T*)r, (T*)rhat,
+                                  nullptr, nullptr, partials, st);
+  k_bicg_replace_finish<<<1, 1024, 0, s>>>(partials, nblk, st, cond, chunk);
+  k_bicg_p<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (T*)rhat, (T*)p, (const T*)v, (T*)phat, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, void* x, void* r,
-                             const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
-                             void* tv, double* partials, DevState* st, cudaStream_t s,
-                             unsigned long long cond, int chunk) {
-  if (dt == DT_F64) return iter_t<double>(d, t, x, 1, r, rhat, p, phat, v, sv, shat, tv, partials, st, s, cond, chunk);
-  return iter_t<float>(d, t, x, 0, r, rhat, p, phat, v, sv, shat, tv, partials, st, s, cond, chunk);
+cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, const double* rho,
+                             double fscale, double* x, double* z, void* r, void* rhat, void* p,
+                             void* phat, void* v, void* sv, void* shat, void* tv, double* partials,
+                             DevState* st, cudaStream_t s, unsigned long long cond, int chunk) {
+  if (dt == DT_F64)
+    return iter_t<double>(d, t, rho, fscale, x, z, r, rhat, p, phat, v, sv, shat, tv, partials, st, s, cond, chunk);
+  return iter_t<float>(d, t, rho, fscale, x, z, r, rhat, p, phat, v, sv, shat, tv, partials, st, s, cond, chunk);
 }
 
-// Iterative refinement: r = f - L x in FP64, stored as FP32 times st->scale_next.
-__global__ void __launch_bounds__(SBX* SBY)
-    k_sph_outer_resid(SphDims d, Tab<double> tb, const double* __restrict__ rho, double fscale,
-                      const double* __restrict__ x, float* __restrict__ out,
-                      const DevState* __restrict__ st, double* __restrict__ partials) {
-  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
-  const double sc = st->scale_next;
-  double s0 = 0.0, s1 = 0.0;
-  if (i < d.nr && j < d.nt) {
-    const long long c = d.at(i, j, k);
-    const double rv = fscale * rho[c] - sph_L<double, double>(d, tb, x, i, j, k, c);
-    out[c] = (float)(rv * sc);
-    s0 = rv * rv;
-    s1 = fabs(rv);
-  }
-  // second slot: sum |r| is not needed; keep max |r| for the scale
-  __shared__ double sh[64];
-  double v[1] = {s0};
-  block_sum<1>(v, sh);
-  double m = warp_max(s1);
-  __shared__ double mx[32];
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  if ((tid & 31) == 0) mx[tid >> 5] = m;
-  __syncthreads();
-  if (tid == 0) {
-    for (int w = 0; w < (int)(blockDim.x * blockDim.y + 31) / 32; w++) m = fmax(m, mx[w]);
-    const int bid = block_linear_id();
-    partials[2 * bid] = v[0];
-    partials[2 * bid + 1] = m;
-  }
-}
-
-cudaError_t launch_sph_outer_resid(const SphDims& d, const SphTables& t, const double* rho,
-                                   double fscale, const double* x, float* out, const DevState* st,
-                                   double* partials, int* nblk, cudaStream_t s) {
-  dim3 g = sph_grid(d);
-  if (nblk) *nblk = g.x * g.y * g.z;
-  k_sph_outer_resid<<<g, dim3(SBX, SBY), 0, s>>>(d, tab_of<double>(t), rho, fscale, x, out, st, partials);
-  return cudaGetLastError();
-}
-
-template <typename TE>
-__global__ void __launch_bounds__(SBX* SBY)
-    k_sph_correct(SphDims d, const TE* __restrict__ e, double inv_scale, double* __restrict__ x,
-                  const DevState* __restrict__ st) {
-  if (st != nullptr) inv_scale = 1.0 / st->scale_cur;
-  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
-  if (i >= d.nr || j >= d.nt) return;
-  const long long c = d.at(i, j, k);
-  x[c] = fma((double)e[c], inv_scale, x[c]);
-}
-
-cudaError_t launch_sph_correct(const SphDims& d, int dt_e, const void* e, double* x,
-                               const DevState* st, cudaStream_t s) {
-  if (dt_e == DT_F64) k_sph_correct<double><<<sph_grid(d), dim3(SBX, SBY), 0, s>>>(d, (const double*)e, 1.0, x, st);
-  else k_sph_correct<float><<<sph_grid(d), dim3(SBX, SBY), 0, s>>>(d, (const float*)e, 1.0, x, st);
-  return cudaGetLastError();
-}
+int bicg_iter_kernels(int) { return 11; }
 
 // ------------------------------------------------------------------ multipole
 // Moments (Eq. outer_multipole) factor on the spherical grid: a phi-Fourier

@@ -50,30 +50,31 @@ void sph_tables_free(SphTables* t);
 cudaError_t launch_sph_apply(const SphDims& d, const SphTables& t, const double* phi, double* out,
                              cudaStream_t s);
 
-// ---- BiCGSTAB (storage T = double or float; dots in FP64)
-// mode 0: ref norm of b = f - L(boundary only); mode 1: r = f - L x, rhat = p = r.
-// f = fscale * rho (FP64 rho) when rho != nullptr, else f = fin (storage T).
+// ---- BiCGSTAB (Krylov vectors stored as T = double or float; x, the
+// right-hand side f = fscale * rho and every dot product in FP64)
+// mode 0: ref norm of b = f - L(boundary part of x); mode 1: r = f - L x,
+// rhat = p = r, phat = B^-1 r (FP64 arithmetic, stored as T).
 cudaError_t launch_bicg_resid(const SphDims& d, const SphTables& t, int dt, int mode,
-                              const double* rho, double fscale, const void* fin, const void* x,
-                              void* r, void* rhat, void* p, void* phat, double* partials, int* nblk,
+                              const double* rho, double fscale, const double* x, void* r,
+                              void* rhat, void* p, void* phat, double* partials, int* nblk,
                               cudaStream_t s);
-// One iteration (9 kernels).  With chunk > 0 it runs inside a CUDA-graph while
-// loop whose condition the last scalar kernel sets.
-cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, void* x, void* r,
-                             const void* rhat, void* p, void* phat, void* v, void* sv, void* shat,
-                             void* tv, double* partials, DevState* st, cudaStream_t s,
-                             unsigned long long cond = 0, int chunk = 0);
+// One iteration (bicg_iter_kernels(dt) kernels).  The FP64 true residual
+// replaces the recurrence one whenever the latter has dropped a hundredfold
+// below its largest value since the last replacement or claims convergence,
+// and every stopping decision is taken on a replaced residual.  With chunk > 0
+// it runs inside a CUDA-graph while loop whose condition the last scalar
+// kernel sets.
+// x is the FP64 iterate, z (FP64, zero at the start) accumulates its
+// increments between replacements (group-wise update).
+cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, const double* rho,
+                             double fscale, double* x, double* z, void* r, void* rhat, void* p,
+                             void* phat, void* v, void* sv, void* shat, void* tv, double* partials,
+                             DevState* st, cudaStream_t s, unsigned long long cond = 0,
+                             int chunk = 0);
+int bicg_iter_kernels(int dt);
 // scalar finisher for the reference / initial residual (mode 0/1)
 cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
                               cudaStream_t s);
-
-// x += e / st->scale_cur (FP64 x; e FP32 or FP64) on unknown nodes
-cudaError_t launch_sph_correct(const SphDims& d, int dt_e, const void* e, double* x,
-                               const DevState* st, cudaStream_t s);
-// IR outer residual: out = (f - L x) * st->scale_next (FP32), partials {sum r^2, max |r|}
-cudaError_t launch_sph_outer_resid(const SphDims& d, const SphTables& t, const double* rho,
-                                   double fscale, const double* x, float* out, const DevState* st,
-                                   double* partials, int* nblk, cudaStream_t s);
 
 // multipole: q <- moments of rho (unknown nodes, dV = r^2 sin t dr dt dp);
 // outer ghost of phi <- expansion at r_ghost

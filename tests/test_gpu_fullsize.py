@@ -1,0 +1,124 @@
+"""Full-size checks in the configurations the benchmarks time.
+
+At 256^3 / 512^3 / 256x128x256 the oracle cannot run whole solves in seconds,
+so these tests check what it can compute one by one at full size:
+  * the oracle's own relative residual ||f - A phi||/||f - A phi0|| of the GPU
+    potential (must meet the tolerance the GPU reported reaching);
+  * multipole boundary values at sampled boundary nodes against the oracle's
+    direct addition-theorem form -G sum rho dV sum_l r'^l/r^(l+1) P_l(cos g)
+    over the full density (the GPU uses monomial moments + solid harmonics);
+  * the monopole moment against the total mass sum rho h^3;
+  * mixed-precision refinement against the FP64 GPU potential (<= 1e-7).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multipole as OM, spherical as OSP
+from oracle.grid import cart_grid
+from oracle.operators import norm2, reference_norm, residual
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_03563_gb300 as P
+    P.capi.lib()
+    return P
+
+
+def _face_points(g, k):
+    """k boundary nodes spread over the faces: (array index, coordinate) pairs."""
+    n = g.n[0]
+    gh = g.g
+    pts = []
+    picks = [(0, n // 3, 2 * n // 5), (n, n // 2, n // 7), (n // 4, 0, 3 * n // 4),
+             (2 * n // 3, n, n // 2), (n // 5, n // 6, 0), (n // 2, 3 * n // 5, n)]
+    for (i, j, kk) in picks[:k]:
+        idx = (kk + gh - 1, j + gh - 1, i + gh - 1)
+        xyz = tuple(g.lo[a] + [i, j, kk][a] * g.h[a] for a in range(3))
+        pts.append((idx, xyz))
+    return pts
+
+
+def _check_cartesian(pkg, n, order, lmax, rho, tol, mixed_prec, nfaces):
+    g = cart_grid(n, order)
+    rho_t = torch.from_numpy(rho).cuda()
+    origin = (0.5, 0.5, 0.5)
+    with pkg.CartesianSolver(n, order, bc="multipole", lmax=lmax) as s:
+        phi = torch.zeros_like(rho_t)
+        info = s.solve(rho_t, phi, tol=tol, method="mg", max_iter=60)
+        assert info.converged, info
+        phi_m = torch.zeros_like(rho_t)
+        info_m = s.solve(rho_t, phi_m, tol=tol, method="mg", prec=mixed_prec, max_iter=60,
+                         inner_cycles=2)
+        assert info_m.converged, info_m
+    ph = phi.cpu().numpy()
+    # the oracle's residual of the GPU potential
+    f = 4 * math.pi * rho
+    rel = norm2(residual(ph, f, g), g) / reference_norm(ph, f, g)
+    assert rel <= tol * (1 + 1e-6), (rel, info.rel_residual)
+    assert abs(rel - info.rel_residual) <= 1e-3 * rel
+    # monopole = total mass
+    mass = float(np.sum(rho[g.interior]) * g.h[0] * g.h[1] * g.h[2])
+    assert abs(info.moments[0] - mass) <= 1e-13 * mass
+    # boundary values against the direct Legendre form over the whole density
+    pts = _face_points(g, nfaces)
+    rel_pts = [tuple(c - o for c, o in zip(xyz, origin)) for _, xyz in pts]
+    direct = OM.direct_legendre_potential(rho, g, origin, lmax, 1.0, rel_pts)
+    for (idx, _), dv in zip(pts, direct):
+        assert abs(ph[idx] - dv) <= 1e-12 * abs(dv), (idx, ph[idx], dv)
+    # mixed precision against FP64
+    err = float((phi_m - phi).abs().max() / phi.abs().max())
+    assert err <= 1e-7, err
+    return info, info_m
+
+
+def test_config2_256_fp64_and_mixed(pkg):
+    """256^3, 7-point, V(2,2), multipole l_max=4, 8 Gaussian blobs (the timed workload)."""
+    rho = W.gaussian_blobs(256, seed=2)
+    info, info_m = _check_cartesian(pkg, 256, 2, 4, rho, 1e-10, "mixed_fp32", 6)
+    assert 5 <= info.iterations <= 12
+
+
+def test_config3_512_13point_bf16(pkg):
+    """512^3, 13-point, multipole l_max=8, lognormal density; FP64 path and the
+    BF16-finest / FP32-smoothing refinement path to 1e-10."""
+    rho = W.lognormal_field_device(512, torch.device("cuda"), order=4, seed=3).cpu().numpy()
+    _check_cartesian(pkg, 512, 4, 8, rho, 1e-10, "mixed_bf16", 1)
+
+
+def test_config4_spherical_full(pkg):
+    """256 x 128 x 256 spherical grid, r log-spaced 0.01..1, multipole l_max=6,
+    Neumann inner boundary, FP64 BiCGSTAB.  The exact solution rounded to FP64
+    already has a relative residual near 1e-9 on this grid (pole coefficients
+    up to 1e11), so the solve runs to 1e-8."""
+    tol = 1e-8
+    r, th, ph_ = W.spherical_coords(256, 128, 256, 0.01, 1.0)
+    rho = W.spherical_density(r, th, ph_)
+    rho_t = torch.from_numpy(rho).cuda()
+    with pkg.SphericalSolver(r, th, ph_, bc="multipole", lmax=6) as s:
+        phi = torch.zeros_like(rho_t)
+        info = s.solve(rho_t, phi, tol=tol, max_iter=30000)
+        assert info.converged, info
+    P = phi.cpu().numpy()
+    op = OSP.SphericalOperator(r, th, ph_)
+    f = 4 * math.pi * rho
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    res = f[U] - op.apply(P)
+    bd = np.zeros(op.shape)
+    bd[:, :, -1] = P[:, :, -1]
+    ref = np.linalg.norm(f[U] - op.apply(bd))
+    rel = np.linalg.norm(res) / ref
+    assert rel <= tol * (1 + 1e-3), rel
+    # outer boundary shell against the oracle's moments and expansion
+    q = OM.moments_spherical(rho, r, th, ph_, 6)
+    np.testing.assert_allclose(info.moments[:49], q, rtol=0, atol=1e-12 * abs(q[0]))
+    shell = OM.spherical_outer_ghost(q, r, th, ph_, 6, 1.0)
+    np.testing.assert_allclose(P[1:-1, 1:-1, -1], shell, rtol=1e-12)

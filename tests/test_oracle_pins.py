@@ -506,6 +506,43 @@ def test_bicgstab_matches_dense_solve():
     np.testing.assert_allclose(phi[1:-1, 1:-1, 1:-1].ravel(), x, rtol=1e-10)
 
 
+def test_bicgstab_restarts_through_an_exact_breakdown():
+    """A 3x3 system on which rhat.r becomes exactly zero at the first step
+    (rhat = r0 = (2,0,0), r1 = (0,-0.4,0.8)): without the restart rule the next
+    beta is 0/0 and the iterate turns NaN; with it the method restarts from r1
+    and reaches the dense solution."""
+    A = np.array([[2.0, 1.0, 0.0], [0.0, 1.0, 2.0], [-1.0, -1.0, 1.0]])
+    b = np.array([2.0, 0.0, 0.0])
+    inv = 1.0 / np.diag(A)
+    ref = float(np.linalg.norm(b))
+    plain = krylov.bicgstab(lambda x: A @ x, inv, b, np.zeros(3), 1e-13, 20, ref, restart=False)
+    assert not plain.converged and not np.all(np.isfinite(plain.x))
+    res = krylov.bicgstab(lambda x: A @ x, inv, b, np.zeros(3), 1e-13, 20, ref)
+    assert res.converged and res.iterations <= 6
+    np.testing.assert_allclose(res.x, np.linalg.solve(A, b), rtol=0, atol=1e-12)
+
+
+def test_bicgstab_stops_on_the_true_residual():
+    """On the graded log-r grid (48x24x48, r_in = 0.01) the recursively updated
+    BiCGSTAB residual drifts from b - A x: stopping on it leaves a true
+    residual of 2e-10 > 1e-10.  The returned iterate must meet the tolerance
+    on the residual recomputed from scratch with the operator."""
+    r, th, ph = W.spherical_coords(48, 24, 48, 0.01, 1.0)
+    op = SP.SphericalOperator(r, th, ph)
+    rho = W.spherical_density(r, th, ph)
+    f = 4 * math.pi * rho
+    P = np.zeros(op.shape)
+    P[:, :, -1] = -1.0
+    res = SP.bicgstab_solve(P, f, op, 1e-10, 5000)
+    assert res.converged
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    bd = np.zeros(op.shape)
+    bd[:, :, -1] = P[:, :, -1]
+    true = np.linalg.norm(f[U] - op.apply(P)) / np.linalg.norm(f[U] - op.apply(bd))
+    assert true <= 1e-10, true
+    assert res.history[-1] == pytest.approx(true, rel=1e-6)
+
+
 def test_spherical_multipole_monopole_is_mass():
     """rho = r^-2: q_00 = sum_i dr_i * 2 pi sum_j sin(theta_j) dtheta exactly, and
     the midpoint spacings telescope to (r_{N-1} + r_N - r_0 - r_{-1}) / 2; the

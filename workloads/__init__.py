@@ -25,7 +25,8 @@ import numpy as np
 
 __all__ = [
     "cart_shape", "cart_coords", "uniform_sphere", "gaussian_blobs",
-    "gaussian_blob_params", "gaussian_blobs_device", "lognormal_field", "manufactured_sine",
+    "gaussian_blob_params", "gaussian_blobs_device", "lognormal_field", "lognormal_field_device",
+    "manufactured_sine",
     "smooth_sphere_density", "spherical_coords", "spherical_density",
     "ServingRequest", "serving_stream", "rng",
 ]
@@ -162,6 +163,35 @@ def lognormal_field(n: int, order: int = 4, seed: int = 3, slope: float = -11.0 
     gh = order // 2
     idx = (np.arange(-(gh - 1), n + gh) % n)
     return rho_p[np.ix_(idx, idx, idx)]
+
+
+def lognormal_field_device(n: int, device, order: int = 4, seed: int = 3,
+                           slope: float = -11.0 / 3.0):
+    """lognormal_field() with the FFT done by torch on `device` (same seeded
+    white noise from PCG64, same spectrum and standardisation), for grids where
+    a host FFT would take minutes."""
+    import torch
+    g = rng(seed)
+    white = torch.from_numpy(g.standard_normal((n, n, n))).to(device)
+    wk = torch.fft.rfftn(white)
+    del white
+    fz = torch.fft.fftfreq(n, device=device, dtype=torch.float64)
+    fx = torch.fft.rfftfreq(n, device=device, dtype=torch.float64)
+    k2 = fx[None, None, :] ** 2 + fz[None, :, None] ** 2 + fz[:, None, None] ** 2
+    k2[0, 0, 0] = 1.0
+    amp = k2 ** (slope / 4.0)
+    amp[0, 0, 0] = 0.0
+    wk *= amp
+    del amp, k2
+    field_ = torch.fft.irfftn(wk, s=(n, n, n))
+    del wk
+    field_ -= field_.mean()
+    field_ /= field_.std(unbiased=False)
+    rho_p = torch.exp(field_ - 0.5)
+    del field_
+    gh = order // 2
+    idx = torch.arange(-(gh - 1), n + gh, device=device) % n
+    return rho_p[idx][:, idx][:, :, idx].contiguous()
 
 
 def manufactured_sine(n: int, order: int, G: float = 1.0):
