@@ -233,6 +233,9 @@ def main():
     ap.add_argument("--cycles-per-step", type=int, default=2)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--prewarm", type=int, default=4)
+    ap.add_argument("--tile-min-n", type=int, default=0,
+                    help="levels with at least this many intervals use the TMA tile kernels "
+                         "(0 = library default, -1 = never)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -269,7 +272,8 @@ def main():
     def one(prec="fp64", out=None):
         out = phi if out is None else out
         out.zero_()
-        return solver.solve(rho, out, tol=TOL, method="mg", prec=prec, max_iter=100)
+        return solver.solve(rho, out, tol=TOL, method="mg", prec=prec, max_iter=100,
+                            tile_min_n=args.tile_min_n)
 
     for _ in range(args.warmup):
         info = one()
@@ -335,7 +339,7 @@ def main():
     for _ in range(args.steps):
         rho_d.copy_(rho_h, non_blocking=True)
         phi_d.copy_(phi_zero_h, non_blocking=True)
-        inf = solver.solve(rho_d, phi_d, tol=TOL, method="mg", max_iter=100)
+        inf = solver.solve(rho_d, phi_d, tol=TOL, method="mg", max_iter=100, tile_min_n=args.tile_min_n)
         e2e_cycles += inf.iterations
         phi_out_h.copy_(phi_d, non_blocking=True)
     e1.record(stream)
@@ -371,13 +375,15 @@ def main():
             for inner in (1, 2, 3):
                 for _ in range(2):
                     out.zero_()
-                    solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=inner)
+                    solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=inner,
+                                 tile_min_n=args.tile_min_n)
                 times = []
                 for _ in range(reps):
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     out.zero_()
                     a.record(stream)
-                    inf = solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=inner)
+                    inf = solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=inner,
+                                 tile_min_n=args.tile_min_n)
                     b.record(stream)
                     torch.cuda.synchronize()
                     times.append(a.elapsed_time(b))
@@ -386,12 +392,14 @@ def main():
                                  "rel_residual": inf.rel_residual}
             best = min((t for t in trials if trials[t]["converged"]), key=lambda t: trials[t]["time_to_1e-10_ms"])
             out.zero_()
-            inf = solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=best)
+            inf = solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=best,
+                         tile_min_n=args.tile_min_n)
             err = float((out - phi64).abs().max() / phi64.abs().max())
             solver.profile(True)
             for _ in range(2):
                 out.zero_()
-                solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=best)
+                solver.solve(rho, out, tol=TOL, method="mg", prec=prec, inner_cycles=best,
+                         tile_min_n=args.tile_min_n)
             pr = solver.profile_read()
             solver.profile(False)
             t_best = trials[best]["time_to_1e-10_ms"]
@@ -436,7 +444,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_intervals": N, "unknowns": unknowns, "l_max": LMAX,
-                       "tol": TOL, "v_cycles_per_solve": cycles[0],
+                       "tol": TOL, "v_cycles_per_solve": cycles[0], "tile_min_n": args.tile_min_n,
                        "l2": "inputs larger than L2 (rho, phi, scaled RHS: 136 MB each)",
                        "parallelism": f"replicas x{world}"},
             "time_to_1e-10_ms": {"p50": statistics.median(step_ms), "p99": p99,

@@ -112,10 +112,11 @@ class _Handle:
 
     # ---- asynchronous, steppable solves (continuous batching)
     def begin(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
-              max_iter=100, inner_cycles=1, stream=None):
+              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0):
         """Start a solve whose state stays on the device; rho/phi must stay alive until end()."""
         self._opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
-                                      int(nu2), int(max_iter), int(inner_cycles), _stream(stream))
+                                      int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
+                                      int(tile_min_n))
         self._keep = (rho, phi)
         check(lib().poisson_solve_begin(self._h, _ptr(rho), _ptr(phi), float(tol),
                                         C.byref(self._opts)), "poisson_solve_begin")
@@ -141,9 +142,10 @@ class _Handle:
         return SolveInfo.from_c(info, min(nmom, 81))
 
     def _solve(self, rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-               stream, nmom):
+               stream, nmom, tile_min_n=0):
         opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
-                                int(nu2), int(max_iter), int(inner_cycles), _stream(stream))
+                                int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
+                                int(tile_min_n))
         info = capi.PsInfo()
         st = lib().poisson_solve(self._h, _ptr(rho), _ptr(phi), float(tol), C.byref(opts),
                                  C.byref(info))
@@ -178,10 +180,12 @@ class CartesianSolver(_Handle):
         return (nz + 2 * g - 1, ny + 2 * g - 1, nx + 2 * g - 1)
 
     def solve(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
-              max_iter=100, inner_cycles=1, stream=None) -> SolveInfo:
+              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0) -> SolveInfo:
+        """tile_min_n: levels with at least this many intervals per axis use the TMA tile
+        kernels (0 = library default, negative = never); results are bitwise identical."""
         nmom = (self.lmax + 1) ** 2 if self.multipole else 0
         return self._solve(rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-                           stream, min(nmom, 81))
+                           stream, min(nmom, 81), tile_min_n)
 
 
 class SphericalSolver(_Handle):
@@ -220,7 +224,7 @@ class SphericalSolver(_Handle):
 
 
 def solve_batch(solvers, rhos, phis, tols, method="mg", prec="fp64", nu1=2, nu2=2, max_iter=100,
-                inner_cycles=1, stream=None):
+                inner_cycles=1, stream=None, tile_min_n=0):
     """poisson_solve_batch over distinct CartesianSolver handles."""
     n = len(solvers)
     hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
@@ -228,7 +232,7 @@ def solve_batch(solvers, rhos, phis, tols, method="mg", prec="fp64", nu1=2, nu2=
     pp = (C.c_void_p * n)(*[_ptr(p).value for p in phis])
     tl = (C.c_double * n)(*[float(t) for t in tols])
     opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], 1.0, nu1, nu2, max_iter,
-                            inner_cycles, _stream(stream))
+                            inner_cycles, _stream(stream), int(tile_min_n))
     infos = (capi.PsInfo * n)()
     st = lib().poisson_solve_batch(hs, rp, pp, tl, n, C.byref(opts), infos)
     check(st, "poisson_solve_batch", allow=(capi.PS_OK, capi.PS_NOT_CONVERGED, capi.PS_DIVERGED))

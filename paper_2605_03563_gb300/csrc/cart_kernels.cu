@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + G;
   const int k1 = min(k0 + zc, G + d.nk());
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   double s2 = 0.0, mx = 0.0;
   float s2f = 0.0f, mxf = 0.0f;
   double oscale = out_scale;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int zc = zchunk(d.nk());
   const int kn0 = blockIdx.z * zc + 1;
   const int kn1 = min(kn0 + zc, d.nk() + 1);
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   auto site = [&](int kn) -> long long {
     const int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;
     const int in = 1 + r0 + NCOL * t;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int K0 = blockIdx.z * zc + 1;
   const int K1 = min(K0 + zc, cd.nk() + 1);
   const int g = fd.g;
-  const long long sy = fd.ex, sz = (long long)fd.ex * fd.ey;
+  const long long sy = fd.sy(), sz = fd.sz();
   const CF sc = (CF)(factor / 64.0);
   for (int K = K0; K < K1; K++) {
     const long long c = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
@@ -404,25 +404,24 @@ __global__ void __launch_bounds__(BX* BY)
 }
 
 template <typename TF, typename TC>
-static cudaError_t restrict_t(const Dims& fine, const void* df, void* fsc, double factor,
+static cudaError_t restrict_t(const Dims& fine, const Dims& cd, const void* df, void* fsc, double factor,
                               cudaStream_t s) {
-  Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2, fine.g);
   dim3 grid = point_grid(cd);
   k_restrict<TF, TC><<<grid, dim3(BX, BY), 0, s>>>(fine, cd, (const TF*)df, (TC*)fsc, factor);
   return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const Dims& fine, int dt_f, const void* delta_f, int dt_c, void* fs_c,
+cudaError_t launch_restrict(const Dims& fine, const Dims& coarse, int dt_f, const void* delta_f, int dt_c, void* fs_c,
                             double factor, cudaStream_t s) {
   if (dt_c == DT_F64) {
-    if (dt_f == DT_F64) return restrict_t<double, double>(fine, delta_f, fs_c, factor, s);
-    if (dt_f == DT_F32) return restrict_t<float, double>(fine, delta_f, fs_c, factor, s);
-    return restrict_t<__nv_bfloat16, double>(fine, delta_f, fs_c, factor, s);
+    if (dt_f == DT_F64) return restrict_t<double, double>(fine, coarse, delta_f, fs_c, factor, s);
+    if (dt_f == DT_F32) return restrict_t<float, double>(fine, coarse, delta_f, fs_c, factor, s);
+    return restrict_t<__nv_bfloat16, double>(fine, coarse, delta_f, fs_c, factor, s);
   }
   if (dt_c == DT_F32) {
-    if (dt_f == DT_F64) return restrict_t<double, float>(fine, delta_f, fs_c, factor, s);
-    if (dt_f == DT_F32) return restrict_t<float, float>(fine, delta_f, fs_c, factor, s);
-    return restrict_t<__nv_bfloat16, float>(fine, delta_f, fs_c, factor, s);
+    if (dt_f == DT_F64) return restrict_t<double, float>(fine, coarse, delta_f, fs_c, factor, s);
+    if (dt_f == DT_F32) return restrict_t<float, float>(fine, coarse, delta_f, fs_c, factor, s);
+    return restrict_t<__nv_bfloat16, float>(fine, coarse, delta_f, fs_c, factor, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -445,8 +444,8 @@ __global__ void __launch_bounds__(BX* BY)
   const int zc = zchunk(cd.nz);
   const int K0 = blockIdx.z * zc, K1 = min(K0 + zc, cd.nz);
   const int g = fd.g;
-  const long long csy = cd.ex, csz = (long long)cd.ex * cd.ey;
-  const long long fsy = fd.ex, fsz = (long long)fd.ex * fd.ey;
+  const long long csy = cd.sy(), csz = cd.sz();
+  const long long fsy = fd.sy(), fsz = fd.sz();
   const CF half = (CF)0.5;
   for (int K = K0; K < K1; K++) {
     const long long c0 = cd.at(I + g - 1, J + g - 1, K + g - 1);
@@ -494,8 +493,7 @@ __global__ void __launch_bounds__(BX* BY)
 }
 
 template <typename TC, typename TF>
-static cudaError_t prolong_t(const Dims& fine, const void* ec, void* phif, cudaStream_t s) {
-  Dims cd = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2, fine.g);
+static cudaError_t prolong_t(const Dims& fine, const Dims& cd, const void* ec, void* phif, cudaStream_t s) {
   const int gx = (cd.nx + BX - 1) / BX, gy = (cd.ny + BY - 1) / BY;
   const int zc = zchunk_for(gx * gy, cd.nz);
   const dim3 grid(gx, gy, (cd.nz + zc - 1) / zc);
@@ -503,17 +501,17 @@ static cudaError_t prolong_t(const Dims& fine, const void* ec, void* phif, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(const Dims& fine, int dt_c, const void* e_c, int dt_f, void* phi_f,
+cudaError_t launch_prolong(const Dims& fine, const Dims& coarse, int dt_c, const void* e_c, int dt_f, void* phi_f,
                            cudaStream_t s) {
   if (dt_c == DT_F64) {
-    if (dt_f == DT_F64) return prolong_t<double, double>(fine, e_c, phi_f, s);
-    if (dt_f == DT_F32) return prolong_t<double, float>(fine, e_c, phi_f, s);
-    return prolong_t<double, __nv_bfloat16>(fine, e_c, phi_f, s);
+    if (dt_f == DT_F64) return prolong_t<double, double>(fine, coarse, e_c, phi_f, s);
+    if (dt_f == DT_F32) return prolong_t<double, float>(fine, coarse, e_c, phi_f, s);
+    return prolong_t<double, __nv_bfloat16>(fine, coarse, e_c, phi_f, s);
   }
   if (dt_c == DT_F32) {
-    if (dt_f == DT_F64) return prolong_t<float, double>(fine, e_c, phi_f, s);
-    if (dt_f == DT_F32) return prolong_t<float, float>(fine, e_c, phi_f, s);
-    return prolong_t<float, __nv_bfloat16>(fine, e_c, phi_f, s);
+    if (dt_f == DT_F64) return prolong_t<float, double>(fine, coarse, e_c, phi_f, s);
+    if (dt_f == DT_F32) return prolong_t<float, float>(fine, coarse, e_c, phi_f, s);
+    return prolong_t<float, __nv_bfloat16>(fine, coarse, e_c, phi_f, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -521,24 +519,22 @@ cudaError_t launch_prolong(const Dims& fine, int dt_c, const void* e_c, int dt_f
 // ------------------------------------------------------------------ elementwise
 template <typename T>
 __global__ void __launch_bounds__(BX* BY)
-    k_scale_rhs(Dims d, double factor, const double* __restrict__ rho, T* __restrict__ fs) {
+    k_scale_rhs(Dims d, Dims du, double factor, const double* __restrict__ rho, T* __restrict__ fs) {
   const int g = d.g;
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
   if (i >= g + d.ni() || j >= g + d.nj()) return;
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
-  for (int k = k0; k < k1; k++) {
-    const long long p = d.at(i, j, k);
-    St<T>::st(fs + p, (typename St<T>::C)(factor * rho[p]));
-  }
+  for (int k = k0; k < k1; k++)
+    St<T>::st(fs + d.at(i, j, k), (typename St<T>::C)(factor * rho[du.at(i, j, k)]));
 }
 
-cudaError_t launch_scale_rhs(const Dims& d, double factor, const double* rho, int dt, void* fs,
-                             cudaStream_t s) {
-  if (dt == DT_F64) k_scale_rhs<double><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, rho, (double*)fs);
-  else if (dt == DT_F32) k_scale_rhs<float><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, rho, (float*)fs);
-  else k_scale_rhs<__nv_bfloat16><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, factor, rho, (__nv_bfloat16*)fs);
+cudaError_t launch_scale_rhs(const Dims& d, const Dims& du, double factor, const double* rho, int dt,
+                             void* fs, cudaStream_t s) {
+  if (dt == DT_F64) k_scale_rhs<double><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, du, factor, rho, (double*)fs);
+  else if (dt == DT_F32) k_scale_rhs<float><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, du, factor, rho, (float*)fs);
+  else k_scale_rhs<__nv_bfloat16><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, du, factor, rho, (__nv_bfloat16*)fs);
   return cudaGetLastError();
 }
 
@@ -603,7 +599,7 @@ __global__ void __launch_bounds__(BX* BY)
   if (i >= G + d.ni() || j >= G + d.nj()) return;
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + G, k1 = min(k0 + zc, G + d.nk());
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   const C dd = (C)cf.d;
   for (int k = k0; k < k1; k++) {
     const long long p = d.at(i, j, k);
@@ -663,7 +659,7 @@ __global__ void __launch_bounds__(1024)
   const int ni = d.ni(), nj = d.nj(), nk = d.nk();
   const int nint = ni * nj * nk;
   const long long n = d.size();
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   for (long long u = tid; u < n; u += nthr) p[u] = 0.0;
   long long c[PPT];
   double x[PPT], r[PPT], q[PPT];
@@ -862,6 +858,11 @@ __global__ void k_finish_norm(const double* __restrict__ partials, int nblocks, 
     set_loop(st, cond, chunk);
     return;
   }
+  if (st->fault) {
+    st->done = DONE_FAULT;
+    set_loop(st, cond, chunk);
+    return;
+  }
   st->rr = rr;
   st->amax = m;
   const double rel = sqrt(rr) / st->ref;
@@ -900,7 +901,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int j = blockIdx.y * BY + threadIdx.y + G;
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + G, k1 = min(k0 + zc, G + d.nk());
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   double s2 = 0.0;
   if (i < G + d.ni() && j < G + d.nj()) {
     for (int k = k0; k < k1; k++) {
@@ -923,7 +924,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int j = blockIdx.y * BY + threadIdx.y + G;
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + G, k1 = min(k0 + zc, G + d.nk());
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   double s2 = 0.0;
   if (i < G + d.ni() && j < G + d.nj()) {
     for (int k = k0; k < k1; k++) {

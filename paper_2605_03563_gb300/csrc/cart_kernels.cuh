@@ -39,17 +39,17 @@ cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int
 cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,
                                  cudaStream_t s);
 
-// fs_coarse = 4 * R(delta_fine)  (scaled coarse right-hand side)
-cudaError_t launch_restrict(const Dims& fine, int dt_f, const void* delta_f, int dt_c,
+// fs_coarse = factor * R(delta_fine)  (scaled coarse right-hand side); coarse = layout of fs_c
+cudaError_t launch_restrict(const Dims& fine, const Dims& coarse, int dt_f, const void* delta_f, int dt_c,
                             void* fs_c, double factor, cudaStream_t s);
 
-// phi_fine += P e_coarse
-cudaError_t launch_prolong(const Dims& fine, int dt_c, const void* e_c, int dt_f, void* phi_f,
+// phi_fine += P e_coarse; coarse = layout of e_c
+cudaError_t launch_prolong(const Dims& fine, const Dims& coarse, int dt_c, const void* e_c, int dt_f, void* phi_f,
                            cudaStream_t s);
 
-// fs = -(4 pi G / d) rho on interior nodes (rho FP64)
-cudaError_t launch_scale_rhs(const Dims& d, double factor, const double* rho, int dt, void* fs,
-                             cudaStream_t s);
+// fs = -(4 pi G / d) rho on interior nodes (rho FP64 in layout du, fs in layout d)
+cudaError_t launch_scale_rhs(const Dims& d, const Dims& du, double factor, const double* rho, int dt,
+                             void* fs, cudaStream_t s);
 
 // phi64 += e * inv_scale on interior nodes
 cudaError_t launch_correct(const Dims& d, int dt_e, const void* e, double inv_scale, double* phi,

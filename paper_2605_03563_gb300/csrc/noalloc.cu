@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NB_X* NB_Y)
   const int i = blockIdx.x * NB_X + threadIdx.x + G;
   const int j = blockIdx.y * NB_Y + threadIdx.y + G;
   const int k0 = blockIdx.z * NB_Z + G, k1 = min(k0 + NB_Z, G + d.nk());
-  const long long sy = d.ex, sz = (long long)d.ex * d.ey;
+  const long long sy = d.sy(), sz = d.sz();
   double s2 = 0.0;
   if (i < G + d.ni() && j < G + d.nj()) {
     for (int k = k0; k < k1; k++) {

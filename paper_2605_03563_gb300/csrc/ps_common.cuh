@@ -32,26 +32,56 @@ template <> struct St<__nv_bfloat16> {
   static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Two adjacent values stored with one vector store (p aligned to the pair), and
+// the value a store of type T keeps (rounding to BF16 where T is BF16).
+template <typename T> struct St2;
+template <> struct St2<double> {
+  static __device__ __forceinline__ void st(double* p, double a, double b) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  }
+};
+template <> struct St2<float> {
+  static __device__ __forceinline__ void st(float* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  }
+};
+template <> struct St2<__nv_bfloat16> {
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
+};
+template <typename T> __device__ __forceinline__ typename St<T>::C stored(typename St<T>::C v) { return v; }
+template <> __device__ __forceinline__ float stored<__nv_bfloat16>(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
 // ------------------------------------------------------------ Cartesian level geometry
-// Array extents (ex,ey,ez) = n + 2g - 1 per axis, x fastest; node index i sits at
+// Logical extents (ex,ey,ez) = n + 2g - 1 per axis, x fastest; node index i sits at
 // array index i + g - 1; interior unknowns occupy array indices [g, n + g - 2].
+// Rows are px >= ex elements apart: caller-owned arrays are dense (px = ex);
+// the library's own level arrays pad rows to a multiple of 32 elements so that
+// every row starts on a 16-byte boundary (TMA tensor maps need 16-byte strides).
 struct Dims {
   int nx, ny, nz;   // intervals
   int g;            // stencil radius (ghost width)
-  int ex, ey, ez;   // array extents
-  __host__ __device__ long long size() const { return (long long)ex * ey * ez; }
+  int ex, ey, ez;   // logical array extents
+  int px;           // row pitch in elements
+  __host__ __device__ long long size() const { return (long long)px * ey * ez; }
   __host__ __device__ long long at(int i, int j, int k) const {
-    return ((long long)k * ey + j) * ex + i;
+    return ((long long)k * ey + j) * px + i;
   }
+  __host__ __device__ long long sy() const { return px; }
+  __host__ __device__ long long sz() const { return (long long)px * ey; }
   __host__ __device__ int ni() const { return nx - 1; }   // interior counts
   __host__ __device__ int nj() const { return ny - 1; }
   __host__ __device__ int nk() const { return nz - 1; }
 };
 
-inline Dims make_dims(int nx, int ny, int nz, int g) {
+inline Dims make_dims(int nx, int ny, int nz, int g, int align = 1) {
   Dims d;
   d.nx = nx; d.ny = ny; d.nz = nz; d.g = g;
   d.ex = nx + 2 * g - 1; d.ey = ny + 2 * g - 1; d.ez = nz + 2 * g - 1;
+  d.px = (d.ex + align - 1) / align * align;
   return d;
 }
 
@@ -133,10 +163,10 @@ struct DevState {
   int broke;          // alpha or omega broke down in this iteration
   int restart;        // the next direction update restarts rhat = p = r
   int replace;        // the true residual replaces the recurrence one this iteration
-  int pad1_;
+  int fault;          // a tile kernel's TMA copy did not complete in time
 };
 
-enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3 };
+enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3, DONE_FAULT = 4 };
 
 }  // namespace ps
 

@@ -34,13 +34,39 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
         assert n in capi.SIGNATURES, n
 
 
-def test_struct_layouts_match_the_header():
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every field offset and struct size of the ctypes binding equals what a C
+    compiler makes of include/poisson.h."""
+    import shutil
+    import subprocess
     from paper_2605_03563_gb300 import capi
-    # int32 kind, int32 n[3], double lo[3], double hi[3]
-    assert C.sizeof(capi.PsGrid) == 16 + 48
-    assert C.sizeof(capi.PsBC) == 8 + 24 + 8
-    assert C.sizeof(capi.PsSolveOpts) == 8 + 8 + 16 + 8
-    assert C.sizeof(capi.PsInfo) == 8 + 32 + 24 + 81 * 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ps_grid": capi.PsGrid, "ps_bc": capi.PsBC, "ps_solve_opts": capi.PsSolveOpts,
+               "ps_info": capi.PsInfo, "ps_kernel_stat": capi.PsKernelStat}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "poisson.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line.strip():
+            continue
+        cname, what, val = line.split()
+        py = structs[cname]
+        got = C.sizeof(py) if what == "size" else getattr(py, what).offset
+        assert got == int(val), (cname, what, got, val)
+        seen += 1
+    assert seen == sum(len(p._fields_) + 1 for p in structs.values())
 
 
 def test_invalid_arguments_rejected_before_gpu_work(lib):
