@@ -637,29 +637,37 @@ cudaError_t launch_apply(const Dims& d, int order, const double h[3], int dt, co
 // coarsest level is solved with CG) until ||r|| <= tol ||r0|| or max_iter
 // iterations.  Each thread owns up to PPT unknowns and keeps their x, r, q in
 // registers; only the search direction p lives in shared memory (on the full
-// ghosted layout, zero boundary), because the stencil reads neighbours.  Every
-// block reduction is one warp shuffle tree, one barrier, and a shuffle tree
-// over the per-warp values that every warp evaluates identically.
-__device__ __forceinline__ double block_allreduce(double v, double* buf) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) buf[warp] = v;
-  __syncthreads();
-  double t = lane < nw ? buf[lane] : 0.0;
-  return warp_sum(t);
-}
-
-template <int G, bool ISO, typename TF, typename TE, int PPT>
-__global__ void __launch_bounds__(1024)
+// ghosted layout, zero boundary), because the stencil reads neighbours.
+// GB300's FP64 pipe is narrow, so the FP64 work that is not per unknown is done
+// once: each dot product is one per-thread partial in shared memory summed by
+// warp 0 (a strided loop, then one shuffle tree), and thread 0 alone forms
+// alpha, beta and the convergence test and hands them out through shared memory.
+// About 100 threads with several unknowns each keep the pipe busy with
+// independent work while the block's barriers stay cheap.
+template <int G, bool ISO, typename TF, typename TE, int PPT, int MAXT>
+__global__ void __launch_bounds__(MAXT)
     k_coarse_cg(Dims d, Coef<double> cf, const TF* __restrict__ fs, TE* __restrict__ e,
                 double tol, int max_iter, DevState* __restrict__ st) {
   extern __shared__ double p[];
-  __shared__ double red[2][32];
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  __shared__ double part[MAXT];
+  __shared__ double scal[2];   // alpha / beta handed out by thread 0
+  __shared__ int stop;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
   const int ni = d.ni(), nj = d.nj(), nk = d.nk();
   const int nint = ni * nj * nk;
   const long long n = d.size();
   const long long sy = d.sy(), sz = d.sz();
+  // block sum of v into lane values of warp 0 (valid in thread 0)
+  auto block_sum0 = [&](double v) -> double {
+    part[tid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (tid < 32) {
+      for (int i = lane; i < nthr; i += 32) t += part[i];
+      t = warp_sum(t);
+    }
+    return t;
+  };
   for (long long u = tid; u < n; u += nthr) p[u] = 0.0;
   long long c[PPT];
   double x[PPT], r[PPT], q[PPT];
@@ -686,42 +694,52 @@ __global__ void __launch_bounds__(1024)
       loc = fma(b, b, loc);
     }
   }
-  double rr = block_allreduce(loc, red[0]);
-  const double ref = sqrt(rr);
+  // thread 0 keeps rr, ref and the iteration count
+  double rr = block_sum0(loc);
+  double ref = 0.0;
   int it = 0;
-  if (ref > 0.0) {
-    while (it < max_iter) {
-      __syncthreads();   // p complete
-      loc = 0.0;
+  if (tid == 0) {
+    ref = sqrt(rr);
+    stop = !(ref > 0.0) || max_iter <= 0;
+  }
+  __syncthreads();
+  while (!stop) {
+    loc = 0.0;
 #pragma unroll
-      for (int k = 0; k < PPT; k++) {
-        if (own[k]) {
-          const double pc = p[c[k]];
-          q[k] = cf.d * (pc - gs_value<G, ISO>(p, c[k], sy, sz, cf, 0.0));
-          loc = fma(pc, q[k], loc);
-        }
+    for (int k = 0; k < PPT; k++) {
+      if (own[k]) {
+        const double pc = p[c[k]];
+        q[k] = cf.d * (pc - gs_value<G, ISO>(p, c[k], sy, sz, cf, 0.0));
+        loc = fma(pc, q[k], loc);
       }
-      const double pq = block_allreduce(loc, red[1]);
-      const double alpha = rr / pq;
-      loc = 0.0;
+    }
+    const double pq = block_sum0(loc);
+    if (tid == 0) scal[0] = rr / pq;
+    __syncthreads();
+    const double alpha = scal[0];
+    loc = 0.0;
 #pragma unroll
-      for (int k = 0; k < PPT; k++) {
-        if (own[k]) {
-          x[k] = fma(alpha, p[c[k]], x[k]);
-          r[k] = fma(-alpha, q[k], r[k]);
-          loc = fma(r[k], r[k], loc);
-        }
+    for (int k = 0; k < PPT; k++) {
+      if (own[k]) {
+        x[k] = fma(alpha, p[c[k]], x[k]);
+        r[k] = fma(-alpha, q[k], r[k]);
+        loc = fma(r[k], r[k], loc);
       }
-      const double rrn = block_allreduce(loc, red[0]);
+    }
+    const double rrn = block_sum0(loc);
+    if (tid == 0) {
       it++;
-      if (sqrt(rrn) <= tol * ref) break;
-      const double beta = rrn / rr;
-      // every thread has passed the stencil reads (barrier inside the reductions)
-#pragma unroll
-      for (int k = 0; k < PPT; k++)
-        if (own[k]) p[c[k]] = fma(beta, p[c[k]], r[k]);
+      stop = sqrt(rrn) <= tol * ref || it >= max_iter;
+      scal[1] = rrn / rr;
       rr = rrn;
     }
+    __syncthreads();   // every thread is past its stencil reads of p
+    if (stop) break;
+    const double beta = scal[1];
+#pragma unroll
+    for (int k = 0; k < PPT; k++)
+      if (own[k]) p[c[k]] = fma(beta, p[c[k]], r[k]);
+    __syncthreads();   // p complete
   }
 #pragma unroll
   for (int k = 0; k < PPT; k++)
@@ -741,23 +759,28 @@ static cudaError_t coarse_t(const Dims& d, const double h[3], int order, const v
   const size_t smem = coarse_cg_smem_bytes(d);
   const int nint = d.ni() * d.nj() * d.nk();
   int ppt = 1;
-  while (ppt < 8 && (nint + ppt - 1) / ppt > 1024) ppt *= 2;
-  if ((nint + ppt - 1) / ppt > 1024) return cudaErrorInvalidValue;
+  while (ppt < 16 && (nint + ppt - 1) / ppt > 128) ppt *= 2;
+  // very elongated coarsest levels (more than 16 x 256 unknowns): up to 1024 threads x 8
+  const bool wide = (nint + ppt - 1) / ppt > 256;
+  if (wide) ppt = 8;
+  if ((nint + ppt - 1) / ppt > (wide ? 1024 : 256)) return cudaErrorInvalidValue;
   const int nthr = std::max(32, (((nint + ppt - 1) / ppt) + 31) / 32 * 32);
   cudaError_t err;
-#define PS_COARSE_LAUNCH(P)                                                                   \
+#define PS_COARSE_LAUNCH(P, MT)                                                               \
   {                                                                                           \
-    auto kern = k_coarse_cg<G, ISO, TF, TE, P>;                                               \
+    auto kern = k_coarse_cg<G, ISO, TF, TE, P, MT>;                                           \
     if (smem > 48 * 1024 &&                                                                   \
         (err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                     (int)smem)) != cudaSuccess)                               \
       return err;                                                                             \
     kern<<<1, nthr, smem, s>>>(d, cf, (const TF*)fs, (TE*)e, tol, max_iter, st);              \
   }
-  if (ppt == 1) PS_COARSE_LAUNCH(1)
-  else if (ppt == 2) PS_COARSE_LAUNCH(2)
-  else if (ppt == 4) PS_COARSE_LAUNCH(4)
-  else PS_COARSE_LAUNCH(8)
+  if (wide) PS_COARSE_LAUNCH(8, 1024)
+  else if (ppt == 1) PS_COARSE_LAUNCH(1, 256)
+  else if (ppt == 2) PS_COARSE_LAUNCH(2, 256)
+  else if (ppt == 4) PS_COARSE_LAUNCH(4, 256)
+  else if (ppt == 8) PS_COARSE_LAUNCH(8, 256)
+  else PS_COARSE_LAUNCH(16, 256)
 #undef PS_COARSE_LAUNCH
   return cudaGetLastError();
 }

@@ -4,9 +4,9 @@
 // harmonics R_lm = sqrt(4 pi/(2l+1)) r^l Y_lm, which are homogeneous
 // polynomials of degree l in (x, y, z).  The GPU therefore reduces the density
 // to Cartesian monomial moments M_abc = sum rho dV x^a y^b z^c (a+b+c <= l_max)
-// in three separable passes -- x along rows, y within planes, z across planes --
-// and maps them to q_lm with a fixed sparse table built on the host.  The
-// per-node cost is l_max+1 FP64 multiply-adds and one read of rho.
+// in three separable passes -- z along columns, then y, then x -- and maps them
+// to q_lm with a fixed sparse table built on the host.  The per-node cost is
+// l_max+1 FP64 multiply-adds and one coalesced read of rho.
 //
 // Boundary values (Eq. outer_expansion): Phi = -G sum_lm q_lm R_lm(x) / r^(2l+1),
 // with R_lm evaluated per node from the recurrences
@@ -15,6 +15,7 @@
 //   (l-m) T_lm = (2l-1) z T_{l-1,m} - (l+m-1) r^2 T_{l-2,m},
 //   R_l0 = T_l0,  R_l(+-m) = sqrt(2 (l-m)!/(l+m)!) T_lm {C_m, S_m}
 // (T_lm = r^l P_l^m(cos t) / (r sin t)^m, P without the Condon-Shortley phase).
+#include <algorithm>
 #include <cmath>
 #include <map>
 
@@ -138,124 +139,133 @@ void build_multipole_tables(int L, MultipoleTables* t) {
 }
 
 // ------------------------------------------------------------------ moment kernels
-// Pass 1: x-row moments.  One warp per row (4 rows per warp, 8 warps per block);
-// the powers x_i^a (a <= L) of the block's rows come from a shared table when
-// it fits (one FP64 FMA per node and power), else from a running product.
-constexpr int ROWS_PER_BLOCK = 32;
+// Pass 1: z-moments of every (i, j) column, S_c(i, j) = sum_k rho(i, j, k) z_k^c,
+// c <= L.  One thread per column and z-chunk: a warp reads 32 consecutive x
+// nodes of a plane (coalesced), and each node costs L+1 FP64 multiply-adds with
+// the powers z_k^c taken from a shared table of the block's z-chunk.  No
+// reduction is needed inside the pass; z-chunks (for parallelism on small
+// grids) leave separate partial sums that pass 2 adds up.
+constexpr int MP_KC_MAX = 256;   // planes per z-chunk
 
-template <int L, bool TABLE>
+template <int L>
 __global__ void __launch_bounds__(256)
-    k_mp_rows(Dims d, double x0, double hx, double dV, const double* __restrict__ rho,
-              double* __restrict__ rowmom) {
-  extern __shared__ double X[];   // [(L+1) * ni] when TABLE
-  const int ni = d.ni();
-  if (TABLE) {
-    for (int t = threadIdx.x; t < ni; t += blockDim.x) {
-      const double x = fma((double)(t + 1), hx, x0);
-      double p = 1.0;
+    k_mp_cols(Dims d, double z0, double hz, int kc, const double* __restrict__ rho,
+              double* __restrict__ colmom) {
+  __shared__ double Z[MP_KC_MAX * (L + 1)];
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk(), g = d.g;
+  const int kb = blockIdx.y * kc, ke = min(kb + kc, nk);
+  for (int t = threadIdx.x; t < (ke - kb); t += blockDim.x) {
+    const double z = fma((double)(kb + t + 1), hz, z0);
+    double pw = 1.0;
 #pragma unroll
-      for (int a = 0; a <= L; a++) {
-        X[a * ni + t] = p;
-        p *= x;
-      }
-    }
-    __syncthreads();
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nrows = d.nj() * d.nk();
-  const int g = d.g;
-  for (int q = 0; q < ROWS_PER_BLOCK / 8; q++) {
-    const int u = blockIdx.x * ROWS_PER_BLOCK + q * 8 + warp;   // row id = k * nj + j
-    if (u >= nrows) break;
-    const int j = u % d.nj(), k = u / d.nj();
-    const long long row = d.at(g, j + g, k + g);
-    double s[L + 1];
-#pragma unroll
-    for (int a = 0; a <= L; a++) s[a] = 0.0;
-    for (int i = lane; i < ni; i += 32) {
-      const double w = rho[row + i] * dV;
-      if (TABLE) {
-#pragma unroll
-        for (int a = 0; a <= L; a++) s[a] = fma(w, X[a * ni + i], s[a]);
-      } else {
-        const double x = fma((double)(i + 1), hx, x0);
-        double p = w;
-#pragma unroll
-        for (int a = 0; a <= L; a++) {
-          s[a] += p;
-          p *= x;
-        }
-      }
-    }
-#pragma unroll
-    for (int a = 0; a <= L; a++) {
-      const double v = warp_sum(s[a]);
-      if (lane == 0) rowmom[(long long)u * (L + 1) + a] = v;
-    }
-  }
-}
-
-__device__ __forceinline__ int pair_index(int a, int b, int L) {
-  // pairs (a, b) with a + b <= L ordered by a, then b
-  return a * (L + 1) - a * (a - 1) / 2 + b;
-}
-
-// Pass 2: y-moments within each plane.  One block per plane; warp w handles
-// pairs w, w+8, ...; lanes stride over the rows; y^b from a shared table.
-__global__ void __launch_bounds__(256)
-    k_mp_planes(Dims d, double y0, double hy, int L, const double* __restrict__ rowmom,
-                double* __restrict__ planemom) {
-  extern __shared__ double Y[];   // [(L+1) * nj]
-  const int nj = d.nj(), k = blockIdx.x;
-  for (int t = threadIdx.x; t < nj; t += blockDim.x) {
-    const double y = fma((double)(t + 1), hy, y0);
-    double p = 1.0;
-    for (int b = 0; b <= L; b++) {
-      Y[b * nj + t] = p;
-      p *= y;
+    for (int c = 0; c <= L; c++) {
+      Z[t * (L + 1) + c] = pw;
+      pw *= z;
     }
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (col >= (long long)ni * nj) return;
+  const int i = (int)(col % ni), j = (int)(col / ni);
+  double sacc[L + 1];
+#pragma unroll
+  for (int c = 0; c <= L; c++) sacc[c] = 0.0;
+  const long long sz = d.sz();
+  const double* r = rho + d.at(i + g, j + g, kb + g);
+  for (int k = kb; k < ke; k++, r += sz) {
+    const double w = *r;
+    const double* zp = Z + (k - kb) * (L + 1);
+#pragma unroll
+    for (int c = 0; c <= L; c++) sacc[c] = fma(w, zp[c], sacc[c]);
+  }
+  const long long plane = (long long)ni * nj;
+  double* out = colmom + (long long)blockIdx.y * (L + 1) * plane + col;
+#pragma unroll
+  for (int c = 0; c <= L; c++) out[c * plane] = sacc[c];
+}
+
+__device__ __forceinline__ int pair_index(int b, int c, int L) {
+  // pairs (b, c) with b + c <= L ordered by b, then c
+  return b * (L + 1) - b * (b - 1) / 2 + c;
+}
+
+// Pass 2: y-moments of the column sums over one y-chunk of 32 rows,
+// Y_bc(i) = sum_j y_j^b S_c(i, j), summed over the z-chunks.  Block = 8 warps
+// over (x tile of 32, power c, y-chunk); lanes over x (coalesced), warps over
+// the chunk's rows; the 8 warp partials are added in warp order.
+constexpr int MP_JT = 32;   // rows per y-chunk
+
+template <int L>
+__global__ void __launch_bounds__(256)
+    k_mp_ycols(Dims d, double y0, double hy, int nchunk, const double* __restrict__ colmom,
+               double* __restrict__ ypart) {
+  __shared__ double red[8][L + 1][32];
+  const int ni = d.ni(), nj = d.nj();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int c = blockIdx.y;
+  const int nb = L - c + 1;
+  const int jb = blockIdx.z * MP_JT, je = min(jb + MP_JT, nj);
+  const long long plane = (long long)ni * nj;
+  double acc[L + 1];
+#pragma unroll
+  for (int b = 0; b <= L; b++) acc[b] = 0.0;
+  if (i < ni) {
+    for (int q = 0; q < nchunk; q++) {
+      const double* src = colmom + ((long long)q * (L + 1) + c) * plane + i;
+      for (int j = jb + w; j < je; j += 8) {
+        const double y = fma((double)(j + 1), hy, y0);
+        double pw = src[(long long)j * ni];
+#pragma unroll
+        for (int b = 0; b <= L; b++) {
+          if (b < nb) acc[b] += pw;
+          pw *= y;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b <= L; b++) red[w][b][lane] = acc[b];
+  __syncthreads();
   const int P2 = (L + 1) * (L + 2) / 2;
-  for (int t = warp; t < P2; t += 8) {
-    int a = 0, rem = t;
-    while (rem > L - a) { rem -= L - a + 1; a++; }
-    const int b = rem;
-    double acc = 0.0;
-    for (int j = lane; j < nj; j += 32)
-      acc = fma(rowmom[((long long)k * nj + j) * (L + 1) + a], Y[b * nj + j], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) planemom[(long long)k * P2 + pair_index(a, b, L)] = acc;
+  for (int t = threadIdx.x; t < nb * 32; t += blockDim.x) {
+    const int b = t >> 5, l = t & 31;
+    double sum = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < 8; ww++) sum += red[ww][b][l];
+    const int ii = blockIdx.x * 32 + l;
+    if (ii < ni) ypart[((long long)blockIdx.z * P2 + pair_index(b, c, L)) * ni + ii] = sum;
   }
 }
 
-// Pass 3: z-moments across planes (warp per monomial, lanes over planes),
-// then the sparse map from monomials to q_lm.
+// Pass 3: x-moments M_abc = dV sum_i x_i^a Y_bc(i), Y summed over the y-chunks
+// (warp per monomial, lanes over x), then the sparse map from monomials to q_lm.
 __global__ void __launch_bounds__(1024)
-    k_mp_final(Dims d, double z0, double hz, int L, const double* __restrict__ planemom,
+    k_mp_final(Dims d, double x0, double hx, double dV, int L, int njc, const double* __restrict__ ypart,
                const int* __restrict__ off, const int* __restrict__ mono,
                const double* __restrict__ val, double* __restrict__ q) {
   extern __shared__ double M[];   // (L+1)^3
   const int W = L + 1;
   const int P2 = W * (W + 1) / 2;
-  const int nk = d.nk();
+  const int ni = d.ni();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = threadIdx.x; t < W * W * W; t += blockDim.x) M[t] = 0.0;
   __syncthreads();
   for (int t = warp; t < W * W * W; t += nw) {
     const int c = t % W, b = (t / W) % W, a = t / (W * W);
     if (a + b + c > L) continue;
-    const int pi = pair_index(a, b, L);
+    const int pi = pair_index(b, c, L);
     double acc = 0.0;
-    for (int k = lane; k < nk; k += 32) {
-      const double z = fma((double)(k + 1), hz, z0);
-      double zc = 1.0;
-      for (int e = 0; e < c; e++) zc *= z;
-      acc = fma(planemom[(long long)k * P2 + pi], zc, acc);
+    for (int i = lane; i < ni; i += 32) {
+      double y = 0.0;
+      for (int jc = 0; jc < njc; jc++) y += ypart[((long long)jc * P2 + pi) * ni + i];
+      const double x = fma((double)(i + 1), hx, x0);
+      double xa = 1.0;
+      for (int e = 0; e < a; e++) xa *= x;
+      acc = fma(y, xa, acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) M[t] = acc;
+    if (lane == 0) M[t] = acc * dV;
   }
   __syncthreads();
   for (int lm = threadIdx.x; lm < W * W; lm += blockDim.x) {
@@ -349,22 +359,31 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ host launchers
+// z-chunks of pass 1: enough columns x chunks for about 152 x 1024 threads
+static int mp_chunks(const Dims& d) {
+  const long long cols = (long long)d.ni() * d.nj();
+  long long nc = (152LL * 1024 + cols - 1) / cols;
+  nc = std::max(nc, (long long)((d.nk() + MP_KC_MAX - 1) / MP_KC_MAX));
+  return (int)std::max(1LL, std::min(nc, (long long)d.nk()));
+}
+
 cudaError_t cart_multipole_alloc(const Dims& d, int lmax, const MultipoleTables& t,
                                  CartMultipoleDev* m) {
   const int W = lmax + 1;
   m->lmax = lmax;
-  size_t nrow = (size_t)d.nj() * d.nk() * W;
-  size_t nplane = (size_t)d.nk() * W * (W + 1) / 2;
+  m->nchunk = mp_chunks(d);
+  size_t ncol = (size_t)m->nchunk * W * d.ni() * d.nj();
+  size_t ny = (size_t)((d.nj() + MP_JT - 1) / MP_JT) * d.ni() * W * (W + 1) / 2;
   size_t ncons = 3 * (size_t)W * W + W;
   cudaError_t e;
-  if ((e = cudaMalloc(&m->rowmom, nrow * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&m->planemom, nplane * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->colmom, ncol * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->ymom, ny * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->q, (size_t)W * W * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->off, t.off.size() * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->mono, std::max<size_t>(1, t.mono.size()) * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->val, std::max<size_t>(1, t.val.size()) * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->consts, ncons * sizeof(double))) != cudaSuccess) return e;
-  m->bytes = (nrow + nplane + W * W + ncons + t.val.size()) * sizeof(double) +
+  m->bytes = (ncol + ny + W * W + ncons + t.val.size()) * sizeof(double) +
              (t.off.size() + t.mono.size()) * sizeof(int);
   std::vector<double> cons;
   cons.insert(cons.end(), t.rec_a.begin(), t.rec_a.end());
@@ -379,9 +398,16 @@ cudaError_t cart_multipole_alloc(const Dims& d, int lmax, const MultipoleTables&
   return cudaMemcpy(m->consts, cons.data(), cons.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
+size_t cart_multipole_bytes(const Dims& d, int lmax) {
+  const size_t W = lmax + 1;
+  return ((size_t)mp_chunks(d) * W * d.ni() * d.nj() +
+          (size_t)((d.nj() + MP_JT - 1) / MP_JT) * d.ni() * W * (W + 1) / 2 + W * W * 4 + 4096) *
+         sizeof(double);
+}
+
 void cart_multipole_free(CartMultipoleDev* m) {
-  cudaFree(m->rowmom);
-  cudaFree(m->planemom);
+  cudaFree(m->colmom);
+  cudaFree(m->ymom);
   cudaFree(m->q);
   cudaFree(m->off);
   cudaFree(m->mono);
@@ -391,49 +417,40 @@ void cart_multipole_free(CartMultipoleDev* m) {
 }
 
 template <int L>
-static void rows_launch(const Dims& d, double x0, double hx, double dV, const double* rho,
-                        double* rowmom, cudaStream_t s) {
-  const int nrows = d.nj() * d.nk();
-  const unsigned blocks = (nrows + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
-  const size_t table = (size_t)(L + 1) * d.ni() * sizeof(double);
-  if (table <= 48 * 1024)
-    k_mp_rows<L, true><<<blocks, 256, table, s>>>(d, x0, hx, dV, rho, rowmom);
-  else
-    k_mp_rows<L, false><<<blocks, 256, 0, s>>>(d, x0, hx, dV, rho, rowmom);
+static void passes12(const Dims& d, double y0, double hy, double z0, double hz, int nchunk_alloc,
+                     const double* rho, double* colmom, double* ypart, cudaStream_t s) {
+  const long long cols = (long long)d.ni() * d.nj();
+  const int kc = (d.nk() + nchunk_alloc - 1) / nchunk_alloc;
+  const int nchunk = (d.nk() + kc - 1) / kc;
+  const dim3 g1((unsigned)((cols + 255) / 256), (unsigned)nchunk);
+  k_mp_cols<L><<<g1, 256, 0, s>>>(d, z0, hz, kc, rho, colmom);
+  const dim3 g2((unsigned)((d.ni() + 31) / 32), L + 1, (unsigned)((d.nj() + MP_JT - 1) / MP_JT));
+  k_mp_ycols<L><<<g2, 256, 0, s>>>(d, y0, hy, nchunk, colmom, ypart);
 }
 
+// Moments about the origin in three separable passes (z, then y, then x).
+// Launches: 3.
 cudaError_t launch_cart_moments(const Dims& d, const double lo[3], const double h[3],
                                 const double origin[3], const double* rho, CartMultipoleDev* m,
                                 cudaStream_t s) {
   const int L = m->lmax;
   if (L < 0 || L > MAXL) return cudaErrorInvalidValue;
-  if ((size_t)(L + 1) * d.nj() * sizeof(double) > 48 * 1024) return cudaErrorInvalidValue;
+  if ((d.nk() + m->nchunk - 1) / m->nchunk > MP_KC_MAX) return cudaErrorInvalidValue;
   const double dV = h[0] * h[1] * h[2];
-  const double x0 = lo[0] - origin[0];
+  const double y0 = lo[1] - origin[1], z0 = lo[2] - origin[2];
+#define PS_MP_CASE(LL) \
+  case LL: passes12<LL>(d, y0, h[1], z0, h[2], m->nchunk, rho, m->colmom, m->ymom, s); break;
   switch (L) {
-    case 0: rows_launch<0>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 1: rows_launch<1>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 2: rows_launch<2>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 3: rows_launch<3>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 4: rows_launch<4>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 5: rows_launch<5>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 6: rows_launch<6>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 7: rows_launch<7>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 8: rows_launch<8>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 9: rows_launch<9>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 10: rows_launch<10>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 11: rows_launch<11>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 12: rows_launch<12>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 13: rows_launch<13>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 14: rows_launch<14>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    case 15: rows_launch<15>(d, x0, h[0], dV, rho, m->rowmom, s); break;
-    default: rows_launch<16>(d, x0, h[0], dV, rho, m->rowmom, s); break;
+    PS_MP_CASE(0) PS_MP_CASE(1) PS_MP_CASE(2) PS_MP_CASE(3) PS_MP_CASE(4) PS_MP_CASE(5)
+    PS_MP_CASE(6) PS_MP_CASE(7) PS_MP_CASE(8) PS_MP_CASE(9) PS_MP_CASE(10) PS_MP_CASE(11)
+    PS_MP_CASE(12) PS_MP_CASE(13) PS_MP_CASE(14) PS_MP_CASE(15)
+    default: passes12<16>(d, y0, h[1], z0, h[2], m->nchunk, rho, m->colmom, m->ymom, s); break;
   }
-  const size_t ytab = (size_t)(L + 1) * d.nj() * sizeof(double);
-  k_mp_planes<<<d.nk(), 256, ytab, s>>>(d, lo[1] - origin[1], h[1], L, m->rowmom, m->planemom);
+#undef PS_MP_CASE
   const int W = L + 1;
   size_t smem = (size_t)W * W * W * sizeof(double);
-  k_mp_final<<<1, 1024, smem, s>>>(d, lo[2] - origin[2], h[2], L, m->planemom, m->off, m->mono,
+  const int njc = (d.nj() + MP_JT - 1) / MP_JT;
+  k_mp_final<<<1, 1024, smem, s>>>(d, lo[0] - origin[0], h[0], dV, L, njc, m->ymom, m->off, m->mono,
                                    m->val, m->q);
   return cudaGetLastError();
 }

@@ -27,8 +27,9 @@ void build_multipole_tables(int lmax, MultipoleTables* t);
 
 struct CartMultipoleDev {
   int lmax = -1;
-  double* rowmom = nullptr;    // [nk*nj*(L+1)]
-  double* planemom = nullptr;  // [nk*(L+1)*(L+2)/2]
+  int nchunk = 1;              // z-chunks of the column pass
+  double* colmom = nullptr;    // [nchunk][L+1][nj][ni] column z-moments
+  double* ymom = nullptr;      // [y-chunks][(L+1)(L+2)/2][ni] y-moments of the column sums
   double* q = nullptr;         // [(L+1)^2]
   int* off = nullptr;
   int* mono = nullptr;
@@ -40,6 +41,8 @@ struct CartMultipoleDev {
 cudaError_t cart_multipole_alloc(const Dims& d, int lmax, const MultipoleTables& t,
                                  CartMultipoleDev* m);
 void cart_multipole_free(CartMultipoleDev* m);
+// device bytes cart_multipole_alloc takes for a grid (admission estimates)
+size_t cart_multipole_bytes(const Dims& d, int lmax);
 
 // q (device) <- moments of rho over interior nodes about origin (weights h^3).
 cudaError_t launch_cart_moments(const Dims& d, const double lo[3], const double h[3],

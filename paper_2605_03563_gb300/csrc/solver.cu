@@ -847,14 +847,12 @@ size_t cart_bytes(const ps_grid* g, int order, int lmax, int prec, bool multipol
     if (prec == PS_FP64) {
       b += (size_t)d.size() * 8 * (l == 0 ? (last ? 0 : 1) : (last ? 2 : 3));
     } else {
+      // phi, fs, the delta buffer and (7-point) the fused sweeps' second phi
       const size_t s = (l == 0 && prec == PS_MIXED_BF16) ? 2 : 4;
-      b += (size_t)d.size() * (2 * s + (last ? 0 : 4));
+      b += (size_t)d.size() * (2 * s + (last ? 0 : 4 + (order == 2 ? s : 0)));
     }
   }
-  if (multipole) {
-    const int W = lmax + 1;
-    b += ((size_t)d0.nj() * d0.nk() * W + (size_t)d0.nk() * W * (W + 1) / 2 + 3 * W * W + 4096) * 8;
-  }
+  if (multipole) b += cart_multipole_bytes(make_dims(g->n[0], g->n[1], g->n[2], gw), lmax);
   b += (size_t)cart_partials_count(d0) * 16 + 2 * sizeof(DevState);
   return b;
 }
