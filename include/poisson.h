@@ -105,7 +105,7 @@ typedef struct {
   int32_t tile_min_n;    /* Cartesian MG, mixed modes: FP32/BF16 inner levels (other than the
                             coarsest) with at least this many intervals on every axis run the
                             TMA-staged tile kernels (fused two-colour sweep for the 7-point
-                            operator, fused residual + restriction); 0 = library default (64),
+                            operator, fused residual + restriction); 0 = library default (16),
                             < 0 = never.  Results are bitwise the same either way.  FP64 levels
                             always use the per-colour passes. */
   int32_t reserved_;     /* set to 0 */

@@ -258,6 +258,75 @@ cudaError_t launch_delta(const Dims& d, int order, const double h[3], int din, c
   return delta_dispatch<__nv_bfloat16>(d, order, h, phi, fs, dout, out, out_scale, nullptr, zero_interior, partials, s);
 }
 
+// ------------------------------------------------------------------ delta after a sweep
+// After a complete omega = 1 colour sweep, delta = phi_GS - phi is exactly zero on
+// the last colour: its nodes were just set to phi_GS from operands that have not
+// changed since, and this kernel repeats that arithmetic.  So delta is evaluated
+// on the other colours only (one thread per node of each colour in a row, as in
+// the colour passes) and zeros are stored on the last colour.
+template <int G, bool ISO, typename T, typename TO>
+__global__ void __launch_bounds__(BX* BY)
+    k_delta_skip(Dims d, Coef<typename St<T>::C> cf, const T* __restrict__ phi,
+                 const T* __restrict__ fs, TO* __restrict__ out) {
+  using C = typename St<T>::C;
+  using S = St<T>;
+  constexpr int NCOL = G == 1 ? 2 : 3;
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn = blockIdx.y * BY + threadIdx.y + 1;
+  if (jn > d.nj()) return;
+  const int zc = zchunk(d.nk());
+  const int kn0 = blockIdx.z * zc + 1;
+  const int kn1 = min(kn0 + zc, d.nk() + 1);
+  const long long sy = d.sy(), sz = d.sz();
+  for (int kn = kn0; kn < kn1; kn++) {
+#pragma unroll
+    for (int colour = 0; colour < NCOL; colour++) {
+      const int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;
+      const int in = 1 + r0 + NCOL * t;
+      if (in > d.ni()) continue;
+      const long long p = d.at(in + G - 1, jn + G - 1, kn + G - 1);
+      if (colour == NCOL - 1) {
+        St<TO>::st(out + p, (typename St<TO>::C)0);
+      } else {
+        const C dl = gs_value<G, ISO>(phi, p, sy, sz, cf, S::ld(fs + p)) - S::ld(phi + p);
+        St<TO>::st(out + p, (typename St<TO>::C)dl);
+      }
+    }
+  }
+}
+
+template <int G, bool ISO, typename T, typename TO>
+static cudaError_t delta_skip_t(const Dims& d, const double h[3], int order, const void* phi,
+                                const void* fs, void* out, cudaStream_t s) {
+  using C = typename St<T>::C;
+  constexpr int NCOL = G == 1 ? 2 : 3;
+  Coef<C> cf = make_coef<C>(d, h, order);
+  const int per_row = (d.ni() + NCOL - 1) / NCOL;
+  const int gx = (per_row + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY;
+  const int zc = zchunk_for(gx * gy, d.nk());
+  const dim3 grid(gx, gy, (d.nk() + zc - 1) / zc);
+  k_delta_skip<G, ISO, T, TO><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (const T*)phi, (const T*)fs, (TO*)out);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TO>
+static cudaError_t delta_skip_dispatch(const Dims& d, int order, const double h[3], const void* phi,
+                                       const void* fs, void* out, cudaStream_t s) {
+  const bool iso = is_iso(h);
+  if (order == 2)
+    return iso ? delta_skip_t<1, true, T, TO>(d, h, order, phi, fs, out, s)
+               : delta_skip_t<1, false, T, TO>(d, h, order, phi, fs, out, s);
+  return iso ? delta_skip_t<2, true, T, TO>(d, h, order, phi, fs, out, s)
+             : delta_skip_t<2, false, T, TO>(d, h, order, phi, fs, out, s);
+}
+
+cudaError_t launch_delta_after_sweep(const Dims& d, int order, const double h[3], int din, const void* phi,
+                                     const void* fs, int dout, void* out, cudaStream_t s) {
+  if (din == DT_F64 && dout == DT_F64) return delta_skip_dispatch<double, double>(d, order, h, phi, fs, out, s);
+  if (din == DT_F32 && dout == DT_F32) return delta_skip_dispatch<float, float>(d, order, h, phi, fs, out, s);
+  return cudaErrorNotSupported;
+}
+
 // ------------------------------------------------------------------ sweep (one colour)
 // Nodes of colour c: (i+j+k) mod NCOL == c (global node indices).  Thread t of a
 // row handles node i = i0 + NCOL t, i0 the first interior node of the colour.

@@ -30,6 +30,13 @@ cudaError_t launch_delta_st(const Dims& d, int order, const double h[3], int din
                             const void* fs, int dout, void* out, const DevState* st,
                             double* partials, cudaStream_t s);
 
+// delta = phi_GS - phi right after a complete omega = 1 colour sweep of phi: the
+// last colour's delta is exactly zero (stored without evaluation), the other
+// colours are evaluated.  Storage pairs (din, dout): F64/F64, F32/F32.  (With
+// BF16 storage the last colour keeps its rounding error; use launch_delta.)
+cudaError_t launch_delta_after_sweep(const Dims& d, int order, const double h[3], int din, const void* phi,
+                                     const void* fs, int dout, void* out, cudaStream_t s);
+
 // One colour pass of the multicolour GS/SOR sweep (skipped once st->done, if st given).
 cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int dt, void* phi,
                                 const void* fs, int colour, double omega, const DevState* st,

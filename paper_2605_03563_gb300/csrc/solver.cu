@@ -366,7 +366,7 @@ cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState
 // adds more FP64 instructions than the HBM traffic they save is worth (measured
 // on the 256^3 level: fused restriction 0.42 ms against 0.39 ms).
 // tile_min_n < 0 disables the tile kernels.
-static const int kTileMinDefault = 64;
+static const int kTileMinDefault = 16;
 bool use_tiles(const ps_ctx* h, const Level& L, int l) {
   const int tmin = h->act.o.tile_min_n == 0 ? kTileMinDefault : h->act.o.tile_min_n;
   if (tmin < 0 || l == h->nlev - 1 || L.dt == DT_F64) return false;
@@ -413,6 +413,19 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
   if (use_tiles(h, L, l)) {
     if (l == 0) prof_begin(h, PC_RESTRICT_FUSED0, w.n * 2.0 * w.S + w.n / 8.0 * dt_size(Cl.dt), w.n * (6.0 * w.G + 3.0), w.fp64, s);
     e = (h->nlaunch += 1, launch_resid_restrict(L.d, Cl.d, h->order, L.h, L.dt, L.phi, L.fs, Cl.dt, Cl.fs, 4.0, &h->st->fault, s));
+    if (l == 0) prof_end(h, s);
+    if (e != cudaSuccess) return e;
+  } else if (nu1 >= 1 && L.dt != DT_BF16) {
+    // the pre-smoothing sweeps end with a complete omega = 1 sweep: the last
+    // colour's residual is exactly zero and is not evaluated (not for BF16
+    // storage, where it is the rounding error of the stored value)
+    const double frac = h->order == 2 ? 0.5 : 2.0 / 3.0;
+    if (l == 0) prof_begin(h, PC_DELTA0, w.n * (w.S * (1.0 + frac) + w.St), w.n * frac * (6.0 * w.G + 1.0), w.fp64, s);
+    e = (h->nlaunch += 1, launch_delta_after_sweep(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, s));
+    if (l == 0) prof_end(h, s);
+    if (e != cudaSuccess) return e;
+    if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * 4.5, w.St == 8.0, s);
+    e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
   } else {
