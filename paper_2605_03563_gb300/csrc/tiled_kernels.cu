@@ -132,16 +132,15 @@ __global__ void __launch_bounds__(32 * (TY + 2))
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = 1 + blockIdx.z * zc;
   const int z1 = min(z0 + zc, nz);     // output planes [z0, z1)
-  const int zl = z0 - 2, zh = z1 + 1;  // staged planes [zl, zh]
+  const int zl = z0 - 2, zh = z1 + 1;  // staged planes [zl, zh]; plane z sits in stage (z - zl) % NS
   if (tid == 0) {
     for (int q = 0; q < NS; q++) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
 
-  auto issue = [&](int z) {
+  auto issue = [&](int z, int q) {   // thread 0: stage q <- plane z
     if (z > zh) return;
-    const int q = (z - zl) % NS;
     mbar_expect_tx(&bar[q], Gm::PBYTES + Gm::FBYTES);
     tma_load_3d(Pst + q * PBE, &mP, x0 - XH, y0 - 2, z, &bar[q]);
     tma_load_3d(Fst + q * FBE, &mF, x0 - XH, y0 - 1, z, &bar[q]);
@@ -154,50 +153,53 @@ __global__ void __launch_bounds__(32 * (TY + 2))
     mbar_wait(&bar[wq], wph, ok);
     if (++wq == NS) { wq = 0; wph ^= 1u; }
   };
-  auto stage_of = [&](int z) { return (z - zl) % NS; };
+  auto nxt = [](int q) { return q + 1 == NS ? 0 : q + 1; };
 
   const int y = y0 - 1 + w;                        // this warp's grid row
   const bool row_out = w >= 1 && w <= TY && y >= 1 && y < ny;
   const bool row_bnd = y <= 0 || y >= ny;
   const int xa = x0 + 2 * l;
-  const int prow = (w + 1) * WP + XH - x0;         // P index of (x, y) = prow + x
-  const int frow = w * WP + XH - x0;               // F index of (x, y) = frow + x
-  const int rrow = w * RW + 1 - x0;                // R index of (x, y) = rrow + x
+  // boundary or outside in x, for the pair's even / odd column
+  const bool bnd_e = row_bnd || xa <= 0 || xa >= nx;
+  const bool bnd_o = row_bnd || xa + 1 >= nx;
+  const bool st_pair = row_out && xa >= 1 && xa + 1 < nx;
+  const bool st_a = row_out && xa >= 1 && xa < nx, st_b = row_out && xa + 1 < nx;
+  const int pbase = (w + 1) * WP + XH + 2 * l;     // P index of (xa, y)
+  const int fbase = w * WP + XH + 2 * l;           // F index of (xa, y)
+  const int rbase = w * RW + 1 + 2 * l;            // R index of (xa, y)
 
-  // red value at (c, y, z) of this warp's row; zm = old phi at (c, y, z-1)
-  // (register or staged), returns the value as stored (rounded to T)
-  auto red_at = [&](int c, int z, const T* P, const T* Pp, C zm, const T* F) -> C {
-    const int pc = prow + c;
+  // red value at column xa + par of this warp's row on plane z (stage qz, plane z+1 in
+  // stage qp), zm = old phi one plane down; returns the value as stored
+  auto red_at = [&](int par, bool zb, int qz, int qp, C zm) -> C {
+    const T* P = Pst + qz * PBE + pbase + par;
     C v;
-    if (row_bnd || z <= 0 || z >= nz || c <= 0 || c >= nx) {
-      v = S::ld(P + pc);
+    if (zb || (par ? bnd_o : bnd_e)) {
+      v = S::ld(P);
     } else {
-      const C ax = S::ld(P + pc + 1) + S::ld(P + pc - 1);
-      const C ay = S::ld(P + pc + WP) + S::ld(P + pc - WP);
-      const C az = S::ld(Pp + pc) + zm;
-      const C f = S::ld(F + frow + c);
+      const C ax = S::ld(P + 1) + S::ld(P - 1);
+      const C ay = S::ld(P + WP) + S::ld(P - WP);
+      const C az = S::ld(Pst + qp * PBE + pbase + par) + zm;
+      const C f = S::ld(Fst + qz * FBE + fbase + par);
       if (ISO) v = fma((ax + ay) + az, cf.c1[0], f);
       else v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
     }
-    return v;
+    return stored<T>(v);
   };
   // warp 0: red value of the halo column of ring row l (l < NW) on plane z
-  auto halo_red = [&](int z, T* R) {
+  auto halo_red = [&](int z, int qm, int qz, int qp, T* R) {
     if (w != 0 || l >= NW) return;
     const int yy = y0 - 1 + l;
     const int hc = ((yy + z) & 1) ? x0 - 1 : x0 + TX;
-    const T* P = Pst + stage_of(z) * PBE;
+    const T* P = Pst + qz * PBE;
     const int pc = (l + 1) * WP + XH + (hc - x0);
     C v;
     if (yy <= 0 || yy >= ny || z <= 0 || z >= nz || hc <= 0 || hc >= nx) {
       v = S::ld(P + pc);
     } else {
-      const T* Pp = Pst + stage_of(z + 1) * PBE;
-      const T* Pm = Pst + stage_of(z - 1) * PBE;
       const C ax = S::ld(P + pc + 1) + S::ld(P + pc - 1);
       const C ay = S::ld(P + pc + WP) + S::ld(P + pc - WP);
-      const C az = S::ld(Pp + pc) + S::ld(Pm + pc);
-      const C f = S::ld(Fst + stage_of(z) * FBE + l * WP + XH + (hc - x0));
+      const C az = S::ld(Pst + qp * PBE + pc) + S::ld(Pst + qm * PBE + pc);
+      const C f = S::ld(Fst + qz * FBE + l * WP + XH + (hc - x0));
       if (ISO) v = fma((ax + ay) + az, cf.c1[0], f);
       else v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
     }
@@ -205,89 +207,83 @@ __global__ void __launch_bounds__(32 * (TY + 2))
   };
 
   if (tid == 0)
-    for (int z = zl; z < zl + NS; z++) issue(z);
-  // prologue: red values of planes z0-1 and z0
-  wait_next();   // zl = z0 - 2
-  wait_next();   // z0 - 1
-  wait_next();   // z0
-  int rs = 0;    // ring slot of plane z0-1; slot of plane z is rs + (z - z0 + 1) mod 3
+    for (int q = 0; q < NS; q++) issue(zl + q, q);
+  // prologue: red values of planes z0-1 (stages 0,1,2 = planes z0-2, z0-1, z0) and z0
+  wait_next();
+  wait_next();
+  wait_next();
   C rm2, rm1, ph0, ph1;   // red(k-1), red(k); old phi one plane above the red column of planes k+1, k+2
   {
-    const int z = z0 - 1;
-    const int c = xa + ((y + z) & 1);
-    const T* P = Pst + stage_of(z) * PBE;
-    const T* Pp = Pst + stage_of(z + 1) * PBE;
-    const C zm = S::ld(Pst + stage_of(z - 1) * PBE + prow + c);
-    T* R = Rr + rs * RBE;
-    const C v = stored<T>(red_at(c, z, P, Pp, zm, Fst + stage_of(z) * FBE));
-    S::st(R + rrow + c, v);
-    rm2 = v;
-    ph0 = S::ld(Pp + prow + c);   // phi(c, z0): lower z neighbour of red(z0+1), same column
-    halo_red(z, R);
+    const int z = z0 - 1, par = (y + z) & 1;
+    const C zm = S::ld(Pst + 0 * PBE + pbase + par);
+    rm2 = red_at(par, z <= 0, 1, 2, zm);
+    S::st(Rr + 0 * RBE + rbase + par, rm2);
+    ph0 = S::ld(Pst + 2 * PBE + pbase + par);   // phi(z0) at the red column of planes z0-1, z0+1
+    halo_red(z, 0, 1, 2, Rr + 0 * RBE);
   }
-  wait_next();   // z0 + 1
+  wait_next();   // plane z0 + 1 in stage 3
   {
-    const int z = z0;
-    const int c = xa + ((y + z) & 1);
-    const T* P = Pst + stage_of(z) * PBE;
-    const T* Pp = Pst + stage_of(z + 1) * PBE;
-    const C zm = S::ld(Pst + stage_of(z - 1) * PBE + prow + c);
-    T* R = Rr + ((rs + 1) % 3) * RBE;
-    const C v = stored<T>(red_at(c, z, P, Pp, zm, Fst + stage_of(z) * FBE));
-    S::st(R + rrow + c, v);
-    rm1 = v;
-    ph1 = S::ld(Pp + prow + c);   // phi(c, z0+1): lower z neighbour of red(z0+2)
-    halo_red(z, R);
+    const int z = z0, par = (y + z) & 1;
+    const C zm = S::ld(Pst + 1 * PBE + pbase + par);
+    rm1 = red_at(par, false, 2, 3, zm);
+    S::st(Rr + 1 * RBE + rbase + par, rm1);
+    ph1 = S::ld(Pst + 3 * PBE + pbase + par);   // phi(z0+1) at the red column of planes z0, z0+2
+    halo_red(z, 1, 2, 3, Rr + 1 * RBE);
   }
   __syncthreads();
   if (tid == 0) {
     fence_proxy_async();
-    issue(zl + NS);
+    issue(zl + NS, 0);
   }
-  int sk = (rs + 1) % 3;   // ring slot of plane k
+  // rotating stages of planes k, k+1, k+2 and ring slots of planes k, k+1
+  int qk = 2, qk1 = 3, qk2 = 4 % NS, iq = 1;
+  T* Rk = Rr + 1 * RBE;
+  T* Rk1 = Rr + 2 * RBE;
+  T* Rk2 = Rr + 0 * RBE;
+  T* o = out + ((long long)z0 * d.ey + y) * d.px + xa;
+  const long long osz = d.sz();
   for (int k = z0; k < z1; k++) {
     wait_next();   // plane k + 2
-    const int sp = sk == 2 ? 0 : sk + 1;
-    // red(k+1): column of planes k+1 and k-1
-    const int zr = k + 1;
-    const int cr = xa + ((y + zr) & 1);
-    const T* P = Pst + stage_of(zr) * PBE;
-    const T* Pp = Pst + stage_of(zr + 1) * PBE;
-    T* Rp = Rr + sp * RBE;
-    const C rp = stored<T>(red_at(cr, zr, P, Pp, ph0, Fst + stage_of(zr) * FBE));
-    S::st(Rp + rrow + cr, rp);
+    const int zr = k + 1, par = (y + zr) & 1;
+    const C rp = red_at(par, zr >= nz, qk1, qk2, ph0);
+    S::st(Rk1 + rbase + par, rp);
     ph0 = ph1;
-    ph1 = S::ld(Pp + prow + cr);
-    halo_red(zr, Rp);
+    ph1 = S::ld(Pst + qk2 * PBE + pbase + par);
+    halo_red(zr, qk, qk1, qk2, Rk1);
     __syncthreads();
     if (tid == 0) {
       fence_proxy_async();
-      issue(k - 1 + NS);
+      issue(k - 1 + NS, iq);   // stage of plane k-1
     }
     if (row_out) {
-      // black(k) at column cr (black on plane k), red(k) at the other column of the pair
-      const T* Rk = Rr + sk * RBE;
-      const int ri = rrow + cr;
-      const C ax = S::ld(Rk + ri + 1) + S::ld(Rk + ri - 1);
-      const C ay = S::ld(Rk + ri + RW) + S::ld(Rk + ri - RW);
+      // black(k) at column xa + par (black on plane k), red(k) at the other column
+      const T* Rb = Rk + rbase + par;
+      const C ax = S::ld(Rb + 1) + S::ld(Rb - 1);
+      const C ay = S::ld(Rb + RW) + S::ld(Rb - RW);
       const C az = rp + rm2;
-      const C f = S::ld(Fst + stage_of(k) * FBE + frow + cr);
+      const C f = S::ld(Fst + qk * FBE + fbase + par);
       C vb;
       if (ISO) vb = fma((ax + ay) + az, cf.c1[0], f);
       else vb = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
-      const bool red_first = cr != xa;   // red(k) sits at xa
-      const C v0 = red_first ? rm1 : vb, v1 = red_first ? vb : rm1;
-      T* o = out + ((long long)k * d.ey + y) * d.px + xa;
-      if (xa >= 1 && xa + 1 < nx) {
+      const C v0 = par ? rm1 : vb, v1 = par ? vb : rm1;
+      if (st_pair) {
         St2<T>::st(o, v0, v1);
       } else {
-        if (xa >= 1 && xa < nx) S::st(o, v0);
-        if (xa + 1 >= 1 && xa + 1 < nx) S::st(o + 1, v1);
+        if (st_a) S::st(o, v0);
+        if (st_b) S::st(o + 1, v1);
       }
     }
+    o += osz;
     rm2 = rm1;
     rm1 = rp;
-    sk = sp;
+    T* t = Rk;
+    Rk = Rk1;
+    Rk1 = Rk2;
+    Rk2 = t;
+    iq = qk;
+    qk = qk1;
+    qk1 = qk2;
+    qk2 = nxt(qk2);
   }
   if (!ok && fault != nullptr) atomicExch(fault, 1);
 }
@@ -296,6 +292,8 @@ template <typename T, bool ISO>
 static cudaError_t rb_sweep_t(const Dims& d, const double h[3], const void* pin, void* pout,
                               const void* fs, const DevState* st, int* fault, cudaStream_t s) {
   using C = typename St<T>::C;
+  // 6 planes in the ring (3 in flight) keep 3 blocks of 512 threads per SM for FP32;
+  // deeper rings measured slower (fewer resident blocks)
   constexpr int TY = 14, NS = 6;
   using Gm = SweepGeom<T, TY, NS>;
   auto kern = k_rb_sweep<T, ISO, TY, NS>;
@@ -409,37 +407,56 @@ __global__ void __launch_bounds__(NT)
   if (tid == 0)
     for (int pz = pz_lo; pz < pz_lo + NS; pz++) issue(pz);
 
+  // this thread's residual nodes of the footprint (fixed for every plane): staged phi
+  // offset, fs offset, footprint index, and whether the node is interior in x and y
+  constexpr int NFP = DW * DH;
+  constexpr int PERD = (NFP + NT - 1) / NT;
+  int pp_e[PERD], ff_e[PERD];
+  bool in_e[PERD];
+#pragma unroll
+  for (int e = 0; e < PERD; e++) {
+    const int idx = tid + e * NT;
+    const int r = idx / DW, c = idx - r * DW;
+    const int fx = 2 * I0 - 1 + c, fy = 2 * J0 - 1 + r;   // fine nodes
+    const int col = fx + G - 1 - bxs;
+    pp_e[e] = (fy + G - 1 - bys) * WP + col;
+    ff_e[e] = (fy + G - 1 - byf) * WP + col;
+    in_e[e] = idx < NFP && fx >= 1 && fx < nfx && fy >= 1 && fy < nfy;
+  }
   // this thread's coarse nodes (in-tile index t, t + NT, ...)
   constexpr int NCT = TXC * TYC;
   constexpr int PER = (NCT + NT - 1) / NT;
   C pm[PER], p0[PER];
 #pragma unroll
   for (int e = 0; e < PER; e++) { pm[e] = (C)0; p0[e] = (C)0; }
+  auto wrap = [](int q) { return q >= NS ? q - NS : (q < 0 ? q + NS : q); };
 
+  int qc = G;   // stage of residual plane pc: phi plane pc sits in stage (pc - pz_lo) % NS, pc_lo - pz_lo = G
   for (int pc = pc_lo; pc <= pc_hi; pc++) {
     wait_upto(pc + G);
     const int fz = pc - G + 1;   // fine node index of this residual plane
-    const TF* Pc = Pst + ((pc - pz_lo) % NS) * PBE;
-    const TF* F = Fst + ((pc + G - pz_lo) % NS) * FBE;
-    for (int idx = tid; idx < DW * DH; idx += NT) {
-      const int r = idx / DW, c = idx - r * DW;
-      const int fx = 2 * I0 - 1 + c, fy = 2 * J0 - 1 + r;   // fine nodes
+    const bool zin = fz >= 1 && fz < nfz;
+    const TF* Pc = Pst + qc * PBE;
+    const TF* Pz1p = Pst + wrap(qc + 1) * PBE;
+    const TF* Pz1m = Pst + wrap(qc - 1) * PBE;
+    const TF* Pz2p = Pst + wrap(qc + 2) * PBE;
+    const TF* Pz2m = Pst + wrap(qc - 2) * PBE;
+    const TF* F = Fst + wrap(qc + G) * FBE;
+#pragma unroll
+    for (int e = 0; e < PERD; e++) {
+      const int idx = tid + e * NT;
+      if (idx >= NFP) break;
       C dl = (C)0;
-      if (fx >= 1 && fx < nfx && fy >= 1 && fy < nfy && fz >= 1 && fz < nfz) {
-        const int col = fx + G - 1 - bxs;
-        const int pp = (fy + G - 1 - bys) * WP + col;
-        const TF* Pz1p = Pst + ((pc + 1 - pz_lo) % NS) * PBE;
-        const TF* Pz1m = Pst + ((pc - 1 - pz_lo) % NS) * PBE;
+      if (zin && in_e[e]) {
+        const int pp = pp_e[e];
         const C ax = S::ld(Pc + pp + 1) + S::ld(Pc + pp - 1);
         const C ay = S::ld(Pc + pp + WP) + S::ld(Pc + pp - WP);
         const C az = S::ld(Pz1p + pp) + S::ld(Pz1m + pp);
-        const C f = S::ld(F + (fy + G - 1 - byf) * WP + col);
+        const C f = S::ld(F + ff_e[e]);
         C v;
         if (ISO) v = fma((ax + ay) + az, cf.c1[0], f);
         else v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
         if (G == 2) {
-          const TF* Pz2p = Pst + ((pc + 2 - pz_lo) % NS) * PBE;
-          const TF* Pz2m = Pst + ((pc - 2 + NS - pz_lo) % NS) * PBE;
           const C bx = S::ld(Pc + pp + 2) + S::ld(Pc + pp - 2);
           const C by = S::ld(Pc + pp + 2 * WP) + S::ld(Pc + pp - 2 * WP);
           const C bz = S::ld(Pz2p + pp) + S::ld(Pz2m + pp);
@@ -480,8 +497,9 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();
     if (tid == 0) {
       fence_proxy_async();
-      issue(pc - G + NS);
+      issue(pc - G + NS);   // stage of phi plane pc - G
     }
+    qc = wrap(qc + 1);
   }
   wait_upto(pz_hi);
   if (!ok && fault != nullptr) atomicExch(fault, 1);
