@@ -196,6 +196,55 @@ const char* poisson_last_error(void);
  * precision (used for admission control); 0 for invalid arguments. */
 size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max, int prec);
 
+/* ------------------------------------------------------------------ batched executor
+ * Many Cartesian multigrid solves of different grid sizes advanced together
+ * (continuous batching): one step advances every active solve by the same
+ * number of V-cycles (FP64) or refinement steps (PS_MIXED_FP32) through one
+ * launch of a captured CUDA graph whose phase kernels (colour passes, residual,
+ * full weighting, coarsest CG, prolongation, norm) walk device-resident work
+ * lists of (solve, level, tile) items.  Adding or removing a solve only rewrites
+ * those lists; the graph, captured once per iteration count, serves any mix of
+ * sizes.  Each solve runs the V(nu1, nu2) iteration of Sec. 2.1.3 on its own
+ * handle's hierarchy, with its own reductions: its result does not depend on
+ * what else is in the batch, and equals a separate poisson_solve up to the
+ * rounding of the norms and of the coarsest CG's dot products (different
+ * reduction trees).  Sweeps always use the per-colour passes.
+ * Calls on one batch must not overlap; a handle added to a batch must not be
+ * used for anything else until it is removed. */
+typedef struct ps_batch_ctx* ps_batch;
+
+/* capacity: slots (1..1024); max_n: largest interval count per axis of the
+ * grids that will be added (16..8192; sets the number of level phases);
+ * stencil_order 2 or 4; prec PS_FP64 or PS_MIXED_FP32 (FP64 refinement around
+ * FP32 inner V-cycles, inner_cycles per step); nu1 >= 1, nu2 >= 0. */
+ps_status poisson_batch_create(int capacity, int max_n, int stencil_order, int prec, int nu1, int nu2,
+                               int inner_cycles, ps_batch* out);
+void poisson_batch_destroy(ps_batch b);
+
+/* Start a solve in a free slot on handle h (Cartesian, same stencil order,
+ * multigrid-able, coarsest level of at most 4096 unknowns): multipole boundary
+ * or given boundary data, scaled right-hand side and initial residual are
+ * enqueued after the caller's work on CUDA's default stream.  rho_dev / phi_dev
+ * as for poisson_solve; they must stay valid until poisson_batch_remove.
+ * *slot receives the slot index.  PS_ERR_INVALID_ARG when the batch is full. */
+ps_status poisson_batch_add(ps_batch b, ps_handle h, const double* rho_dev, double* phi_dev, double tol,
+                            int max_iter, int* slot);
+
+/* Enqueue `iterations` (1..64) iterations of every active solve (one graph
+ * launch; no host synchronisation).  Finished solves are skipped. */
+ps_status poisson_batch_step(ps_batch b, int iterations);
+
+/* Wait for the batch and report every slot: status[i] = -1 free, 0 running,
+ * 1 converged, 2 iteration budget exhausted, 3 diverged, 4 fault;
+ * iterations[i] (optional) = iterations taken.  Arrays hold `capacity` entries. */
+ps_status poisson_batch_poll(ps_batch b, int32_t* status, int32_t* iterations);
+
+/* End the solve in `slot`: copies the potential to the caller's phi (ordered
+ * before later work on CUDA's default stream), fills info (may be NULL) and
+ * frees the slot.  Returns PS_OK, PS_NOT_CONVERGED or PS_DIVERGED like
+ * poisson_solve. */
+ps_status poisson_batch_remove(ps_batch b, int slot, ps_info* info);
+
 /* ------------------------------------------------------------------ kernel timing
  * Opt-in timing of the hot kernels of a handle's solves with CUDA events
  * recorded on the solve stream around each launch (finest-level sweeps,

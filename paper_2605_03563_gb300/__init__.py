@@ -240,4 +240,66 @@ def solve_batch(solvers, rhos, phis, tols, method="mg", prec="fp64", nu1=2, nu2=
             for i, s in enumerate(solvers)]
 
 
+class Batch:
+    """Batched multigrid executor (poisson_batch_*): many CartesianSolver handles of
+    different sizes advanced together by one CUDA-graph launch per step.
+
+    add() starts a solve in a free slot and returns the slot; step(k) enqueues k
+    V-cycles (FP64) or refinement steps (mixed_fp32) of every active solve; poll()
+    returns per-slot (status, iterations) arrays (status -1 free, 0 running,
+    1 converged, 2 budget exhausted, 3 diverged, 4 fault); remove(slot) copies the
+    potential back and returns the SolveInfo."""
+
+    def __init__(self, capacity, max_n, order=2, prec="fp64", nu1=2, nu2=2, inner_cycles=1):
+        self._b = C.c_void_p()
+        self.capacity = int(capacity)
+        check(lib().poisson_batch_create(self.capacity, int(max_n), int(order), PRECISIONS[prec],
+                                         int(nu1), int(nu2), int(inner_cycles), C.byref(self._b)),
+              "poisson_batch_create")
+        self._keep = {}
+
+    def add(self, solver, rho, phi, tol=1e-10, max_iter=100) -> int:
+        slot = C.c_int(-1)
+        check(lib().poisson_batch_add(self._b, solver._h, _ptr(rho), _ptr(phi), float(tol),
+                                      int(max_iter), C.byref(slot)), "poisson_batch_add")
+        self._keep[slot.value] = (solver, rho, phi)
+        return slot.value
+
+    def step(self, iterations=1):
+        check(lib().poisson_batch_step(self._b, int(iterations)), "poisson_batch_step")
+
+    def poll(self):
+        st = (C.c_int32 * self.capacity)()
+        it = (C.c_int32 * self.capacity)()
+        check(lib().poisson_batch_poll(self._b, st, it), "poisson_batch_poll")
+        return list(st), list(it)
+
+    def remove(self, slot) -> SolveInfo:
+        info = capi.PsInfo()
+        solver = self._keep[slot][0]
+        st = lib().poisson_batch_remove(self._b, int(slot), C.byref(info))
+        check(st, "poisson_batch_remove", allow=(capi.PS_OK, capi.PS_NOT_CONVERGED, capi.PS_DIVERGED))
+        del self._keep[slot]
+        nmom = (solver.lmax + 1) ** 2 if getattr(solver, "multipole", False) else 0
+        return SolveInfo.from_c(info, min(nmom, 81))
+
+    def close(self):
+        if self._b:
+            lib().poisson_batch_destroy(self._b)
+            self._b = C.c_void_p()
+            self._keep = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 from . import ops  # noqa: E402

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpoisson.so")
-SOURCES = ["cart_kernels.cu", "tiled_kernels.cu", "multipole.cu", "spherical.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["cart_kernels.cu", "tiled_kernels.cu", "batch.cu", "multipole.cu", "spherical.cu", "solver.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -61,7 +61,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
     if jobs or not os.path.exists(LIB) or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs]
+        cmd = [cc, "-shared", *ARCH, "-Xlinker", "--no-undefined", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

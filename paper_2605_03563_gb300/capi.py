@@ -88,6 +88,14 @@ SIGNATURES = {
                                            C.POINTER(C.c_double), C.c_int, C.c_double,
                                            C.c_void_p, C.c_void_p]),
     "ps_op_spherical_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "poisson_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.POINTER(C.c_void_p)]),
+    "poisson_batch_destroy": (None, [C.c_void_p]),
+    "poisson_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                    C.c_int, C.POINTER(C.c_int)]),
+    "poisson_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "poisson_batch_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "poisson_batch_remove": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(PsInfo)]),
 }
 
 _lib = None

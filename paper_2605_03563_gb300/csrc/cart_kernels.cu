@@ -19,6 +19,7 @@
 #include <cstdio>
 
 #include "cart_kernels.cuh"
+#include "stencil.cuh"
 
 namespace ps {
 
@@ -65,34 +66,6 @@ static inline dim3 point_grid(const Dims& d) {
 int cart_partials_count(const Dims& d) {
   const dim3 g = point_grid(d);
   return g.x * g.y * g.z;
-}
-
-// ------------------------------------------------------------------ stencil core
-// phi_GS without the diagonal: sum of weighted neighbours plus fs.
-template <int G, bool ISO, typename T, typename C>
-__device__ __forceinline__ C gs_value(const T* __restrict__ phi, long long p, long long sy,
-                                      long long sz, const Coef<C>& cf, C fs) {
-  using S = St<T>;
-  C ax = S::ld(phi + p + 1) + S::ld(phi + p - 1);
-  C ay = S::ld(phi + p + sy) + S::ld(phi + p - sy);
-  C az = S::ld(phi + p + sz) + S::ld(phi + p - sz);
-  C v;
-  if (ISO) {
-    v = fma((ax + ay) + az, cf.c1[0], fs);
-  } else {
-    v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], fs)));
-  }
-  if (G == 2) {
-    C bx = S::ld(phi + p + 2) + S::ld(phi + p - 2);
-    C by = S::ld(phi + p + 2 * sy) + S::ld(phi + p - 2 * sy);
-    C bz = S::ld(phi + p + 2 * sz) + S::ld(phi + p - 2 * sz);
-    if (ISO) {
-      v = fma((bx + by) + bz, cf.c2[0], v);
-    } else {
-      v = fma(bx, cf.c2[0], fma(by, cf.c2[1], fma(bz, cf.c2[2], v)));
-    }
-  }
-  return v;
 }
 
 // Same with every interior neighbour read as zero (reference norm only).
@@ -165,6 +138,8 @@ __global__ void __launch_bounds__(BX* BY)
   double oscale = out_scale;
   if (st != nullptr) oscale = st->scale_next;
   if (i < G + d.ni() && j < G + d.nj()) {
+    // two z nodes per trip: their loads and FP64 chains are independent
+#pragma unroll 2
     for (int k = k0; k < k1; k++) {
       const long long p = d.at(i, j, k);
       C dl;
@@ -177,8 +152,12 @@ __global__ void __launch_bounds__(BX* BY)
       if (RED == 2 && dout != DT_F64) {
         // refinement pass: the stored inner right-hand side is FP32/BF16, so the
         // sum of squares and the max run on the FP32 pipe over the scaled value
-        // (O(1) by the choice of the power-of-two scale; exact to undo)
-        const float v = (float)(dd * oscale);
+        // (O(1) by the choice of the power-of-two scale; exact to undo).  While
+        // the scale is a moderate power of two it is applied after the
+        // conversion, in FP32: the same value as converting the scaled double for
+        // every element in FP32's normal range, one FP64 instruction fewer.
+        const float v = (oscale <= 0x1p100 && oscale >= 0x1p-100) ? (float)dd * (float)oscale
+                                                                  : (float)(dd * oscale);
         s2f = fmaf(v, v, s2f);
         mxf = fmaxf(mxf, fabsf(v));
         if (dout == DT_F32) ((float*)out)[p] = v;
@@ -702,121 +681,12 @@ cudaError_t launch_apply(const Dims& d, int order, const double h[3], int dt, co
 }
 
 // ------------------------------------------------------------------ coarsest-level CG
-// One CTA solves -A e = d * fs (zero boundary, e0 = 0) by CG (Sec. 2.1.3: the
-// coarsest level is solved with CG) until ||r|| <= tol ||r0|| or max_iter
-// iterations.  Each thread owns up to PPT unknowns and keeps their x, r, q in
-// registers; only the search direction p lives in shared memory (on the full
-// ghosted layout, zero boundary), because the stencil reads neighbours.
-// GB300's FP64 pipe is narrow, so the FP64 work that is not per unknown is done
-// once: each dot product is one per-thread partial in shared memory summed by
-// warp 0 (a strided loop, then one shuffle tree), and thread 0 alone forms
-// alpha, beta and the convergence test and hands them out through shared memory.
-// About 100 threads with several unknowns each keep the pipe busy with
-// independent work while the block's barriers stay cheap.
 template <int G, bool ISO, typename TF, typename TE, int PPT, int MAXT>
 __global__ void __launch_bounds__(MAXT)
     k_coarse_cg(Dims d, Coef<double> cf, const TF* __restrict__ fs, TE* __restrict__ e,
                 double tol, int max_iter, DevState* __restrict__ st) {
   extern __shared__ double p[];
-  __shared__ double part[MAXT];
-  __shared__ double scal[2];   // alpha / beta handed out by thread 0
-  __shared__ int stop;
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
-  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
-  const int nint = ni * nj * nk;
-  const long long n = d.size();
-  const long long sy = d.sy(), sz = d.sz();
-  // block sum of v into lane values of warp 0 (valid in thread 0)
-  auto block_sum0 = [&](double v) -> double {
-    part[tid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (tid < 32) {
-      for (int i = lane; i < nthr; i += 32) t += part[i];
-      t = warp_sum(t);
-    }
-    return t;
-  };
-  for (long long u = tid; u < n; u += nthr) p[u] = 0.0;
-  long long c[PPT];
-  double x[PPT], r[PPT], q[PPT];
-  bool own[PPT];
-#pragma unroll
-  for (int k = 0; k < PPT; k++) {
-    const int u = tid + k * nthr;
-    own[k] = u < nint;
-    const int uu = own[k] ? u : 0;
-    const int i = uu % ni, t = uu / ni;
-    c[k] = d.at(i + G, t % nj + G, t / nj + G);
-    x[k] = 0.0;
-    r[k] = 0.0;
-    q[k] = 0.0;
-  }
-  __syncthreads();
-  double loc = 0.0;
-#pragma unroll
-  for (int k = 0; k < PPT; k++) {
-    if (own[k]) {
-      const double b = cf.d * (double)St<TF>::ld(fs + c[k]);
-      r[k] = b;
-      p[c[k]] = b;
-      loc = fma(b, b, loc);
-    }
-  }
-  // thread 0 keeps rr, ref and the iteration count
-  double rr = block_sum0(loc);
-  double ref = 0.0;
-  int it = 0;
-  if (tid == 0) {
-    ref = sqrt(rr);
-    stop = !(ref > 0.0) || max_iter <= 0;
-  }
-  __syncthreads();
-  while (!stop) {
-    loc = 0.0;
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-      if (own[k]) {
-        const double pc = p[c[k]];
-        q[k] = cf.d * (pc - gs_value<G, ISO>(p, c[k], sy, sz, cf, 0.0));
-        loc = fma(pc, q[k], loc);
-      }
-    }
-    const double pq = block_sum0(loc);
-    if (tid == 0) scal[0] = rr / pq;
-    __syncthreads();
-    const double alpha = scal[0];
-    loc = 0.0;
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-      if (own[k]) {
-        x[k] = fma(alpha, p[c[k]], x[k]);
-        r[k] = fma(-alpha, q[k], r[k]);
-        loc = fma(r[k], r[k], loc);
-      }
-    }
-    const double rrn = block_sum0(loc);
-    if (tid == 0) {
-      it++;
-      stop = sqrt(rrn) <= tol * ref || it >= max_iter;
-      scal[1] = rrn / rr;
-      rr = rrn;
-    }
-    __syncthreads();   // every thread is past its stencil reads of p
-    if (stop) break;
-    const double beta = scal[1];
-#pragma unroll
-    for (int k = 0; k < PPT; k++)
-      if (own[k]) p[c[k]] = fma(beta, p[c[k]], r[k]);
-    __syncthreads();   // p complete
-  }
-#pragma unroll
-  for (int k = 0; k < PPT; k++)
-    if (own[k]) St<TE>::st(e + c[k], (typename St<TE>::C)x[k]);
-  if (tid == 0 && st != nullptr) {
-    st->coarse_iter_last = it;
-    st->coarse_iter_total += it;
-  }
+  coarse_cg_block<G, ISO, TF, TE, PPT, MAXT>(d, cf, fs, e, tol, max_iter, st, p);
 }
 
 size_t coarse_cg_smem_bytes(const Dims& d) { return (size_t)d.size() * sizeof(double); }
@@ -874,16 +744,6 @@ cudaError_t launch_coarse_cg(const Dims& d, int order, const double h[3], int dt
 }
 
 // ------------------------------------------------------------------ norm finisher
-// Set the enclosing graph's while-condition (chunk > 0 marks a graph body):
-// continue while not done and below the iteration budget of this step, so
-// every graph launch ends after a bounded number of iterations.
-__device__ __forceinline__ void set_loop(const DevState* st, unsigned long long cond, int chunk) {
-  if (chunk > 0) {
-    const unsigned int more = (st->done == DONE_NO && st->iter < st->chunk_end) ? 1u : 0u;
-    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, more);
-  }
-}
-
 __global__ void k_set_budget(DevState* st, int k) { st->chunk_end = st->iter + k; }
 
 __global__ void k_init_state(DevState* st, double tol, int max_iter) {
@@ -921,59 +781,7 @@ cudaError_t launch_set_budget(DevState* st, int k, cudaStream_t s) {
 __global__ void k_finish_norm(const double* __restrict__ partials, int nblocks, double dscale,
                               int mode, DevState* __restrict__ st, unsigned long long cond,
                               int chunk) {
-  __shared__ double red[64];
-  double s = 0.0, m = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    s += partials[2 * b];
-    m = fmax(m, partials[2 * b + 1]);
-  }
-  double a[1] = {s};
-  block_sum<1>(a, red);
-  // max over the block
-  m = warp_max(m);
-  __shared__ double mx[32];
-  if ((threadIdx.x & 31) == 0) mx[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int w = 1; w < (int)(blockDim.x + 31) / 32; w++) m = fmax(m, mx[w]);
-  m = fmax(m, mx[0]);
-  const double S = a[0];
-  const double rr = dscale * dscale * S;
-  if (mode == 0) {
-    double ref = sqrt(rr);
-    st->ref = ref > 0.0 ? ref : 1.0;
-    st->amax = m;
-    st->scale_next = m > 0.0 ? exp2(-rint(log2(m))) : 1.0;
-    return;
-  }
-  if (st->done && mode == 2) {
-    set_loop(st, cond, chunk);
-    return;
-  }
-  if (st->fault) {
-    st->done = DONE_FAULT;
-    set_loop(st, cond, chunk);
-    return;
-  }
-  st->rr = rr;
-  st->amax = m;
-  const double rel = sqrt(rr) / st->ref;
-  st->rel = rel;
-  // IR: the scale of the next stored inner right-hand side (power of two)
-  st->scale_cur = st->scale_next;
-  st->scale_next = m > 0.0 ? exp2(-rint(log2(m))) : 1.0;
-  if (mode == 1) {
-    st->iter = 0;
-    st->rel0 = rel;
-    st->done = rel <= st->tol ? DONE_CONVERGED : (st->max_iter <= 0 ? DONE_MAXITER : DONE_NO);
-    if (!isfinite(rel)) st->done = DONE_DIVERGED;
-    return;
-  }
-  st->iter += 1;
-  if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
-  else if (rel <= st->tol) st->done = DONE_CONVERGED;
-  else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
-  set_loop(st, cond, chunk);
+  finish_norm_block(partials, nblocks, dscale, mode, st, cond, chunk);
 }
 
 cudaError_t launch_finish_norm(const double* partials, int nblocks, double dscale, int mode,

@@ -24,6 +24,7 @@
 
 #include "cart_kernels.cuh"
 #include "tiled_kernels.cuh"
+#include "batch.cuh"
 #include "multipole.cuh"
 #include "spherical.cuh"
 
@@ -174,6 +175,7 @@ struct ps_ctx {
   cudaStream_t cap = nullptr;
   double* phi0 = nullptr;  // internal finest-level potential (Cartesian) / unknowns (spherical)
   Active act;
+  bool in_batch = false;           // the handle's hierarchy is advanced by a batch
   DevState* st_active = nullptr;   // the state the loop gate reads (= st)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
@@ -870,6 +872,192 @@ size_t cart_bytes(const ps_grid* g, int order, int lmax, int prec, bool multipol
   return b;
 }
 
+
+// ====================================================================== batched executor (host)
+struct BSlotHost {
+  ps_ctx* h = nullptr;
+  double* phi_user = nullptr;
+  long long iters_at_add = 0;
+};
+
+}  // namespace
+
+struct ps_batch_ctx {
+  int cap = 0, order = 2, prec = 0, nu1 = 2, nu2 = 2, inner = 1, nlev_max = 0;
+  cudaStream_t stream = nullptr, capstream = nullptr;
+  std::vector<BSlotHost> slots;
+  std::vector<BSlot> hslots;
+  BSlot* dslots = nullptr;
+  BItem* ditems = nullptr;
+  size_t items_cap = 0;
+  BList* dlists = nullptr;
+  int* dstatus = nullptr;
+  int* hstatus = nullptr;   // pinned
+  std::map<int, cudaGraphExec_t> graphs;   // by iterations per step
+  size_t graph_smem = 0;                   // coarsest-CG shared memory the graphs were built with
+  bool dirty = true;
+  int kernels_per_iter = 0;
+};
+
+namespace {
+
+void destroy_batch_graphs(ps_batch_ctx* b) {
+  for (auto& kv : b->graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+// Rebuild the work lists and upload the slot descriptors (after a change of
+// the batch's composition).
+ps_status batch_rebuild(ps_batch_ctx* b) {
+  const int L = PS_BMAX_LEVELS;
+  std::vector<std::vector<BItem>> lists(BL_NKINDS * L);
+  size_t smem = 8;
+  for (int si = 0; si < b->cap; si++) {
+    BSlot& sd = b->hslots[si];
+    if (!sd.active) continue;
+    ps_ctx* h = b->slots[si].h;
+    const int nl = sd.nlev;
+    for (int l = 0; l + 1 < nl; l++) {
+      int gx, gy, gz;
+      batch_tiles_sweep(sd.lv[l].d, b->order, sd.lv[l].zc, &gx, &gy, &gz);
+      for (int z = 0; z < gz; z++)
+        for (int y = 0; y < gy; y++)
+          for (int x = 0; x < gx; x++) lists[BL_SWEEP * L + l].push_back({si, l, x, y, z, 0});
+      batch_tiles_points(sd.lv[l + 1].d, sd.lv[l + 1].zc, &gx, &gy, &gz);
+      for (int z = 0; z < gz; z++)
+        for (int y = 0; y < gy; y++)
+          for (int x = 0; x < gx; x++) lists[BL_COARSE_PT * L + l].push_back({si, l, x, y, z, 0});
+      batch_tiles_cells(sd.lv[l + 1].d, sd.lv[l + 1].zc, &gx, &gy, &gz);
+      for (int z = 0; z < gz; z++)
+        for (int y = 0; y < gy; y++)
+          for (int x = 0; x < gx; x++) lists[BL_CELLS * L + l].push_back({si, l, x, y, z, 0});
+    }
+    lists[BL_CG * L + (nl - 1)].push_back({si, nl - 1, 0, 0, 0, 0});
+    smem = std::max(smem, coarse_cg_smem_bytes(sd.lv[nl - 1].d));
+    int gx, gy, gz, np = 0;
+    if (b->prec == 0) {
+      batch_tiles_sweep(sd.lv[0].d, b->order, sd.lv[0].zc, &gx, &gy, &gz);
+      for (int z = 0; z < gz; z++)
+        for (int y = 0; y < gy; y++)
+          for (int x = 0; x < gx; x++) lists[BL_NORM0 * L].push_back({si, 0, x, y, z, np++});
+    } else {
+      batch_tiles_points(sd.lv[0].d, sd.lv[0].zc, &gx, &gy, &gz);
+      for (int z = 0; z < gz; z++)
+        for (int y = 0; y < gy; y++)
+          for (int x = 0; x < gx; x++) lists[BL_PT0 * L].push_back({si, 0, x, y, z, np++});
+    }
+    sd.nparts = np;
+    ps_status r = ensure_partials(h, np);
+    if (r != PS_OK) return r;
+    sd.partials = h->partials;
+    lists[BL_SLOTS * L].push_back({si, 0, 0, 0, 0, 0});
+  }
+  std::vector<BItem> items;
+  std::vector<BList> heads(BL_NKINDS * L);
+  for (size_t q = 0; q < lists.size(); q++) {
+    heads[q].off = (int)items.size();
+    heads[q].count = (int)lists[q].size();
+    items.insert(items.end(), lists[q].begin(), lists[q].end());
+  }
+  if (items.size() > b->items_cap) {
+    // the graphs hold the item array's address: rebuild them with the new one
+    TRY(cudaStreamSynchronize(b->stream));
+    destroy_batch_graphs(b);
+    cudaFree(b->ditems);
+    b->ditems = nullptr;
+    b->items_cap = std::max<size_t>(items.size() * 2, 4096);
+    TRY(cudaMalloc(&b->ditems, b->items_cap * sizeof(BItem)));
+  }
+  if (smem > b->graph_smem) {
+    TRY(cudaStreamSynchronize(b->stream));
+    destroy_batch_graphs(b);
+    b->graph_smem = smem;
+  }
+  if (!items.empty())
+    TRY(cudaMemcpyAsync(b->ditems, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice, b->stream));
+  TRY(cudaMemcpyAsync(b->dlists, heads.data(), heads.size() * sizeof(BList), cudaMemcpyHostToDevice, b->stream));
+  TRY(cudaMemcpyAsync(b->dslots, b->hslots.data(), b->hslots.size() * sizeof(BSlot), cudaMemcpyHostToDevice, b->stream));
+  // the host vectors are pageable: the copies above complete before returning
+  b->dirty = false;
+  return PS_OK;
+}
+
+// One V-cycle of every active solve over the work lists (levels are indexed
+// from the finest; a solve's coarsest level is solved where it occurs).
+cudaError_t batch_vcycle(ps_batch_ctx* b, int dt, cudaStream_t s) {
+  const BArgs a{b->dslots, b->ditems, b->dlists};
+  const int L = PS_BMAX_LEVELS, ncol = b->order == 2 ? 2 : 3;
+  cudaError_t e;
+  for (int l = 0; l + 1 < b->nlev_max; l++) {
+    for (int it = 0; it < b->nu1; it++)
+      for (int c = 0; c < ncol; c++)
+        if ((e = launch_b_sweep(a, b->order, dt, BL_SWEEP * L + l, c, s)) != cudaSuccess) return e;
+    if ((e = launch_b_delta_skip(a, b->order, dt, BL_SWEEP * L + l, s)) != cudaSuccess) return e;
+    if ((e = launch_b_restrict(a, dt, BL_COARSE_PT * L + l, s)) != cudaSuccess) return e;
+    if ((e = launch_b_coarse(a, b->order, dt, BL_CG * L + l + 1, b->cap, b->graph_smem, COARSE_TOL, s)) != cudaSuccess) return e;
+  }
+  for (int l = b->nlev_max - 2; l >= 0; l--) {
+    if ((e = launch_b_prolong(a, dt, BL_CELLS * L + l, s)) != cudaSuccess) return e;
+    for (int it = 0; it < b->nu2; it++)
+      for (int c = 0; c < ncol; c++)
+        if ((e = launch_b_sweep(a, b->order, dt, BL_SWEEP * L + l, c, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One iteration of every active solve: a V-cycle and its convergence check
+// (FP64), or a refinement step (mixed FP32).
+cudaError_t batch_iteration(ps_batch_ctx* b, cudaStream_t s) {
+  const BArgs a{b->dslots, b->ditems, b->dlists};
+  const int L = PS_BMAX_LEVELS;
+  cudaError_t e;
+  if (b->prec == 0) {
+    if ((e = batch_vcycle(b, DT_F64, s)) != cudaSuccess) return e;
+    if ((e = launch_b_norm(a, b->order, BL_NORM0 * L, s)) != cudaSuccess) return e;
+    return launch_b_finish(a, BL_SLOTS * L, b->cap, s);
+  }
+  if ((e = launch_b_zero(a, DT_F32, BL_PT0 * L, s)) != cudaSuccess) return e;
+  for (int c = 0; c < b->inner; c++)
+    if ((e = batch_vcycle(b, DT_F32, s)) != cudaSuccess) return e;
+  if ((e = launch_b_correct(a, BL_PT0 * L, s)) != cudaSuccess) return e;
+  if ((e = launch_b_delta_ir(a, b->order, BL_PT0 * L, s)) != cudaSuccess) return e;
+  return launch_b_finish(a, BL_SLOTS * L, b->cap, s);
+}
+
+ps_status batch_graph(ps_batch_ctx* b, int iters, cudaGraphExec_t* out) {
+  auto it = b->graphs.find(iters);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return PS_OK;
+  }
+  TRY(cudaStreamBeginCapture(b->capstream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t eb = cudaSuccess;
+  for (int k = 0; k < iters && eb == cudaSuccess; k++) eb = batch_iteration(b, b->capstream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->capstream, &graph);
+  if (eb != cudaSuccess) e = eb;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PS_ERR_CUDA, "building the batch step graph: %s", cudaGetErrorString(e));
+  b->graphs[iters] = exec;
+  *out = exec;
+  return PS_OK;
+}
+
+void batch_level_desc(ps_ctx* h, const Level& L, BLevel* out) {
+  memset(out, 0, sizeof(*out));
+  out->d = L.d;
+  out->cf64 = make_coef<double>(L.d, L.h, h->order);
+  out->cf32 = make_coef<float>(L.d, L.h, h->order);
+  out->phi = L.phi;
+  out->fs = L.fs;
+  out->tmp = L.tmp;
+  out->dt = L.dt;
+  out->iso = (L.h[0] == L.h[1] && L.h[1] == L.h[2]) ? 1 : 0;
+  out->zc = batch_zchunk(L.d);
+}
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1197,6 +1385,180 @@ ps_status poisson_solve_batch(ps_handle* hs, const double* const* rho, double* c
     if (si != PS_OK && worst == PS_OK) worst = si;
   }
   return worst;
+}
+
+
+// ---------------------------------------------------------------------- batched executor
+ps_status poisson_batch_create(int capacity, int max_n, int stencil_order, int prec, int nu1, int nu2,
+                               int inner_cycles, ps_batch* out) {
+  if (!out) return fail(PS_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (capacity < 1 || capacity > 1024) return fail(PS_ERR_INVALID_ARG, "capacity must be in 1..1024 (got %d)", capacity);
+  if (stencil_order != 2 && stencil_order != 4) return fail(PS_ERR_INVALID_ARG, "stencil_order must be 2 or 4");
+  if (prec != PS_FP64 && prec != PS_MIXED_FP32)
+    return fail(PS_ERR_UNSUPPORTED, "batches run in FP64 or with FP32 refinement (precision %d)", prec);
+  if (nu1 < 1 || nu2 < 0) return fail(PS_ERR_INVALID_ARG, "batches need nu1 >= 1 and nu2 >= 0");
+  if (prec == PS_MIXED_FP32 && inner_cycles < 1) return fail(PS_ERR_INVALID_ARG, "inner_cycles must be >= 1");
+  const int nmax[3] = {max_n, max_n, max_n};
+  std::vector<std::array<int, 3>> lv;
+  if (max_n < 16 || max_n > 8192) return fail(PS_ERR_INVALID_ARG, "max_n must be in 16..8192");
+  levels_for(nmax, &lv);
+  int nlev_max = (int)lv.size();
+  // a grid no larger than max_n on every axis has at most this many levels
+  for (int n = 16; n <= max_n; n++) {
+    const int nn[3] = {n, n, n};
+    levels_for(nn, &lv);
+    nlev_max = std::max(nlev_max, (int)lv.size());
+  }
+  if (nlev_max > PS_BMAX_LEVELS) return fail(PS_ERR_INVALID_ARG, "max_n too large for a batch");
+  ps_batch_ctx* b = new ps_batch_ctx();
+  b->cap = capacity;
+  b->order = stencil_order;
+  b->prec = prec;
+  b->nu1 = nu1;
+  b->nu2 = nu2;
+  b->inner = prec == PS_FP64 ? 1 : inner_cycles;
+  b->nlev_max = nlev_max;
+  b->slots.resize(capacity);
+  b->hslots.assign(capacity, BSlot());
+  for (auto& sd : b->hslots) memset(&sd, 0, sizeof(sd));
+  b->kernels_per_iter = batch_kernels_per_iteration(nlev_max, stencil_order, prec == PS_FP64 ? 0 : 1, nu1, nu2, b->inner);
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&b->capstream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMalloc(&b->dslots, (size_t)capacity * sizeof(BSlot))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dlists, (size_t)BL_NKINDS * PS_BMAX_LEVELS * sizeof(BList))) != cudaSuccess ||
+      (e = cudaMalloc(&b->dstatus, (size_t)capacity * 2 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMallocHost(&b->hstatus, (size_t)capacity * 2 * sizeof(int))) != cudaSuccess) {
+    poisson_batch_destroy(b);
+    return fail(e == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA, "batch allocation: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return PS_OK;
+}
+
+void poisson_batch_destroy(ps_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  destroy_batch_graphs(b);
+  for (auto& sl : b->slots)
+    if (sl.h) sl.h->in_batch = false;
+  cudaFree(b->dslots);
+  cudaFree(b->ditems);
+  cudaFree(b->dlists);
+  cudaFree(b->dstatus);
+  if (b->hstatus) cudaFreeHost(b->hstatus);
+  if (b->capstream) cudaStreamDestroy(b->capstream);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+ps_status poisson_batch_add(ps_batch b, ps_handle h, const double* rho_dev, double* phi_dev, double tol,
+                            int max_iter, int* slot) {
+  if (!b || !h || !slot) return fail(PS_ERR_INVALID_ARG, "NULL batch, handle or slot");
+  *slot = -1;
+  if (!rho_dev || !phi_dev) return fail(PS_ERR_INVALID_ARG, "rho and phi must be device pointers");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(PS_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (max_iter < 0) return fail(PS_ERR_INVALID_ARG, "max_iter must be >= 0");
+  if (h->sph) return fail(PS_ERR_UNSUPPORTED, "batches hold Cartesian multigrid solves");
+  if (h->order != b->order) return fail(PS_ERR_INVALID_ARG, "the handle's stencil order differs from the batch's");
+  if (h->nlev < 2) return fail(PS_ERR_INVALID_ARG, "multigrid needs all interval counts even and >= 16");
+  if (h->nlev > b->nlev_max) return fail(PS_ERR_INVALID_ARG, "grid larger than the batch's max_n");
+  if (h->act.on || h->in_batch) return fail(PS_ERR_INVALID_ARG, "the handle has a solve in flight");
+  const Dims& dc = h->dims.back();
+  if ((long long)dc.ni() * dc.nj() * dc.nk() > 16 * 256)
+    return fail(PS_ERR_UNSUPPORTED, "coarsest level too large for the batched coarsest CG (at most 4096 unknowns)");
+  int si = -1;
+  for (int i = 0; i < b->cap; i++)
+    if (!b->hslots[i].active) { si = i; break; }
+  if (si < 0) return fail(PS_ERR_INVALID_ARG, "the batch is full");
+  cudaStream_t s = b->stream;
+  // start after everything the caller enqueued on CUDA's default stream
+  TRY(cudaEventRecord(h->ev_in, 0));
+  TRY(cudaStreamWaitEvent(s, h->ev_in, 0));
+  h->nlaunch = 0;
+  ps_status r;
+  if ((r = cart_prepare(h, rho_dev, phi_dev, tol, max_iter, s)) != PS_OK) return r;
+  Hier* H = b->prec == PS_FP64 ? &h->h64 : &h->hmx[0];
+  if ((r = build_hier(h, b->prec == PS_FP64 ? 0 : 1, H)) != PS_OK) return r;
+  if (b->prec == PS_FP64) {
+    H->lv[0].phi = h->phi0;
+    TRY(norm_pass(h, h->phi0, 1, DT_F64, nullptr, s));
+  } else {
+    TRY(norm_pass(h, h->phi0, 1, H->lv[0].dt, H->lv[0].fs, s));
+  }
+  BSlot& sd = b->hslots[si];
+  memset(&sd, 0, sizeof(sd));
+  for (int l = 0; l < h->nlev; l++) batch_level_desc(h, H->lv[l], &sd.lv[l]);
+  sd.st = h->st;
+  sd.phi64 = h->phi0;
+  sd.fs64 = h->fs64;
+  sd.cf0 = make_coef<double>(h->d0, h->h0, h->order);
+  sd.dscale = sd.cf0.d;
+  sd.nlev = h->nlev;
+  sd.active = 1;
+  b->slots[si].h = h;
+  b->slots[si].phi_user = phi_dev;
+  h->in_batch = true;
+  h->act = Active();
+  h->act.inner_per_iter = b->prec == PS_FP64 ? 0 : b->inner;
+  h->hst->iter = 0;
+  h->hst->done = DONE_NO;
+  b->dirty = true;
+  *slot = si;
+  return PS_OK;
+}
+
+ps_status poisson_batch_step(ps_batch b, int iterations) {
+  if (!b) return fail(PS_ERR_INVALID_ARG, "NULL batch");
+  if (iterations < 1 || iterations > 64) return fail(PS_ERR_INVALID_ARG, "iterations must be in 1..64");
+  ps_status r;
+  if (b->dirty && (r = batch_rebuild(b)) != PS_OK) return r;
+  cudaGraphExec_t g = nullptr;
+  if ((r = batch_graph(b, iterations, &g)) != PS_OK) return r;
+  TRY(cudaGraphLaunch(g, b->stream));
+  for (int i = 0; i < b->cap; i++)
+    if (b->hslots[i].active) b->slots[i].h->nlaunch += (long long)b->kernels_per_iter * iterations;
+  return PS_OK;
+}
+
+ps_status poisson_batch_poll(ps_batch b, int32_t* status, int32_t* iterations) {
+  if (!b || !status) return fail(PS_ERR_INVALID_ARG, "NULL batch or status");
+  if (b->dirty) {
+    ps_status r = batch_rebuild(b);
+    if (r != PS_OK) return r;
+  }
+  TRY(launch_b_gather(b->dslots, b->cap, b->dstatus, b->stream));
+  TRY(cudaMemcpyAsync(b->hstatus, b->dstatus, (size_t)b->cap * 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->cap; i++) {
+    status[i] = b->hstatus[2 * i];
+    if (iterations) iterations[i] = b->hstatus[2 * i + 1];
+  }
+  return PS_OK;
+}
+
+ps_status poisson_batch_remove(ps_batch b, int slot, ps_info* info) {
+  if (!b || slot < 0 || slot >= b->cap || !b->hslots[slot].active)
+    return fail(PS_ERR_INVALID_ARG, "no solve in batch slot %d", slot);
+  ps_ctx* h = b->slots[slot].h;
+  cudaStream_t s = b->stream;
+  TRY(cudaEventRecord(h->ev[2], s));
+  TRY(copy_rows(b->slots[slot].phi_user, h->du, h->phi0, h->d0, s));
+  TRY(cudaEventRecord(h->ev_out, s));
+  TRY(cudaStreamWaitEvent(0, h->ev_out, 0));
+  ps_status r = read_state(h, s);
+  b->hslots[slot].active = 0;
+  b->slots[slot] = BSlotHost();
+  h->in_batch = false;
+  b->dirty = true;
+  if (r != PS_OK) return r;
+  ps_status out = PS_OK;
+  if (h->hst->done == DONE_MAXITER || h->hst->done == DONE_NO) out = PS_NOT_CONVERGED;
+  else if (h->hst->done == DONE_DIVERGED) out = PS_DIVERGED;
+  else if (h->hst->done == DONE_FAULT) return fail(PS_ERR_TIMEOUT, "a kernel's wait did not complete; the result is invalid");
+  fill_info(h, info, out, true);
+  return out;
 }
 
 ps_status poisson_profile_enable(ps_handle h, int enable) {
