@@ -176,7 +176,8 @@ def run_serving(args, rank, world):
     torch.cuda.set_device(dev)
     reqs = W.serving_stream(n_requests=args.requests, rate_hz=200.0, seed=5)
     srv = PoissonServer(dev, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), prec=args.prec,
-                        cycles_per_step=args.cycles_per_step, max_active=args.max_active)
+                        cycles_per_step=args.cycles_per_step, max_active=args.max_active,
+                        executor=args.executor, max_n=max(r.n for r in reqs))
     # pre-warm: a few handles per size with their loop graphs captured
     warm_reqs = []
     sizes = sorted({r.n for r in reqs})
@@ -205,7 +206,7 @@ def run_serving(args, rank, world):
             "data": "synthetic", "scaling": "weak",
             "config": {"workload": "2000 requests, Poisson arrivals 200/s, cubes {32..256}^3, 1-16 "
                                    "Gaussian blobs, tol 1e-6/1e-10, 30% warm-started sequences",
-                       "requests": len(reqs), "max_active": args.max_active,
+                       "requests": len(reqs), "max_active": args.max_active, "executor": args.executor,
                        "cycles_per_step": args.cycles_per_step, "budget_gb": args.budget_gb},
             "latency_p50_ms": summ["latency_p50_ms"], "latency_p99_ms": summ["latency_p99_ms"],
             "latency_mean_ms": summ["latency_mean_ms"], "by_tol": by_tol,
@@ -324,6 +325,9 @@ def main():
     ap.add_argument("--cycles-per-step", type=int, default=2)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--prewarm", type=int, default=4)
+    ap.add_argument("--executor", default="hybrid", choices=["batch", "streams", "hybrid"],
+                    help="serving: batched executor (one graph launch per tick for all solves), "
+                         "per-request graphs, or the batch for grids up to 96^3 and graphs above")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the timings of the other configurations (1, 3, 4)")
     ap.add_argument("--tile-min-n", type=int, default=0,

@@ -1,7 +1,7 @@
 // Batched multigrid executor: phase kernels over work lists (see batch.cuh).
 //
-// Every kernel walks its list with a grid-stride loop over items; an item is one
-// 32 x 8 x zc tile of one level of one solve.  The per-node arithmetic is that of
+// Every kernel walks its list with a grid-stride loop over the list's tiles; a
+// tile is 32 x 8 x zc nodes (or cells) of one level of one solve.  The per-node arithmetic is that of
 // the per-solve kernels (colour pass, residual on the non-last colours, full
 // weighting, trilinear prolongation, norm after a sweep, refinement residual),
 // so a solve advanced in a batch follows the same iteration as alone.  Per-solve
@@ -43,6 +43,29 @@ void batch_tiles_cells(const Dims& coarse, int zc, int* gx, int* gy, int* gz) {
   *gz = (coarse.nz + zc - 1) / zc;
 }
 
+// The tile with list-wide number t: its entry, and (bx, by, bz, number in the solve).
+struct BTile {
+  int slot, level, bx, by, bz, local;
+};
+__device__ __forceinline__ BTile find_tile(const BItem* __restrict__ items, const BList& L, int t) {
+  int lo = 0, hi = L.count - 1;
+  while (lo < hi) {   // last entry with first <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[L.off + mid].first <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const BItem e = items[L.off + lo];
+  BTile r;
+  r.slot = e.slot;
+  r.level = e.level;
+  r.local = t - e.first;
+  r.bx = r.local % e.gx;
+  const int q = r.local / e.gx;
+  r.by = q % e.gy;
+  r.bz = q / e.gy;
+  return r;
+}
+
 template <typename C> __device__ __forceinline__ const Coef<C>& coef_of(const BLevel& lv);
 template <> __device__ __forceinline__ const Coef<double>& coef_of<double>(const BLevel& lv) { return lv.cf64; }
 template <> __device__ __forceinline__ const Coef<float>& coef_of<float>(const BLevel& lv) { return lv.cf32; }
@@ -60,8 +83,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_sweep(BArgs a, int list, int colo
   using S = St<T>;
   constexpr int NCOL = G == 1 ? 2 : 3;
   const BList L = a.lists[list];
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;
     const BLevel& lv = sl.lv[item.level];
@@ -92,8 +115,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_delta_skip(BArgs a, int list) {
   using S = St<T>;
   constexpr int NCOL = G == 1 ? 2 : 3;
   const BList L = a.lists[list];
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;
     const BLevel& lv = sl.lv[item.level];
@@ -133,8 +156,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_restrict(BArgs a, int list) {
   using C = typename St<T>::C;
   using S = St<T>;
   const BList L = a.lists[list];
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;
     const BLevel& lf = sl.lv[item.level];
@@ -178,8 +201,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_prolong(BArgs a, int list) {
   using C = typename St<T>::C;
   using S = St<T>;
   const BList L = a.lists[list];
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;
     const BLevel& lf = sl.lv[item.level];
@@ -248,7 +271,7 @@ __global__ void __launch_bounds__(256) kb_coarse(BArgs a, int list, double tol) 
   extern __shared__ double p[];
   const BList L = a.lists[list];
   if ((int)blockIdx.x >= L.count) return;
-  const BItem item = a.items[L.off + blockIdx.x];
+  const BItem item = a.items[L.off + blockIdx.x];   // one tile per entry
   const BSlot& sl = a.slots[item.slot];
   if (sl.st->done) return;
   const BLevel& lv = sl.lv[item.level];
@@ -268,8 +291,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_norm(BArgs a, int list) {
   __shared__ double sh[8];
   const BList L = a.lists[list];
   const int tid = threadIdx.x + BBX * threadIdx.y;
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;   // uniform over the block
     const BLevel& lv = sl.lv[0];
@@ -301,8 +324,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_norm(BArgs a, int list) {
       double v = tid < 8 ? sh[tid] : 0.0;
       v = warp_sum(v);
       if (tid == 0) {
-        sl.partials[2 * item.pidx] = v;
-        sl.partials[2 * item.pidx + 1] = 0.0;
+        sl.partials[2 * item.local] = v;
+        sl.partials[2 * item.local + 1] = 0.0;
       }
     }
     __syncthreads();
@@ -323,8 +346,8 @@ __global__ void __launch_bounds__(1024) kb_finish(BArgs a, int list) {
 template <typename T>
 __global__ void __launch_bounds__(BBX* BBY) kb_zero(BArgs a, int list) {
   const BList L = a.lists[list];
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;
     const BLevel& lv = sl.lv[item.level];
@@ -342,8 +365,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_zero(BArgs a, int list) {
 // phi64 += e / scale (as k_correct), level-0 point tiles
 __global__ void __launch_bounds__(BBX* BBY) kb_correct(BArgs a, int list) {
   const BList L = a.lists[list];
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;
     const BLevel& lv = sl.lv[0];
@@ -370,8 +393,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_delta_ir(BArgs a, int list) {
   __shared__ double sh[64];
   const BList L = a.lists[list];
   const int tid = threadIdx.x + BBX * threadIdx.y;
-  for (int it = blockIdx.x; it < L.count; it += gridDim.x) {
-    const BItem item = a.items[L.off + it];
+  for (int it = blockIdx.x; it < L.total; it += gridDim.x) {
+    const BTile item = find_tile(a.items, L, it);
     const BSlot& sl = a.slots[item.slot];
     if (sl.st->done) continue;   // uniform over the block
     const BLevel& lv = sl.lv[0];
@@ -406,8 +429,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_delta_ir(BArgs a, int list) {
       u = warp_sum(u);
       m = warp_max(m);
       if (tid == 0) {
-        sl.partials[2 * item.pidx] = u;
-        sl.partials[2 * item.pidx + 1] = m;
+        sl.partials[2 * item.local] = u;
+        sl.partials[2 * item.local + 1] = m;
       }
     }
     __syncthreads();

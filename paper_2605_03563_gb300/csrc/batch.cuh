@@ -7,9 +7,11 @@
 // FP32): a fixed sequence of phase launches -- colour passes, residual,
 // restriction, coarsest CG, prolongation, norm -- per level index, captured once
 // into a plain CUDA graph.  Each phase kernel walks a device-resident work list
-// of (slot, level, tile) items with a grid-stride loop, so the same graph serves
-// any mix of grid sizes; a change of the batch's composition only rewrites the
-// lists and the slot descriptors.  Items of finished solves are skipped.
+// with a grid-stride loop over the list's tiles; an entry of the list holds one
+// solve's tiles of one level, and a block finds the entry of its tile by binary
+// search over the prefix offsets.  So the same graph serves any mix of grid
+// sizes, and a change of the batch's composition only rewrites small lists and
+// the slot descriptors.  Tiles of finished solves are skipped.
 #pragma once
 #include "cart_kernels.cuh"
 
@@ -46,14 +48,16 @@ struct BSlot {
   int pad_;
 };
 
-// One unit of work: a tile (bx, by, bz) of level `level` of solve `slot`;
-// pidx numbers the tiles of a norm pass within the solve.
+// One solve's share of a list: `tiles` tiles of level `level` (a gx x gy x gz
+// grid of tiles, x fastest), numbered first .. first+tiles-1 within the list.
+// A tile's number inside its solve is also the index of its norm partial.
 struct BItem {
-  int slot, level, bx, by, bz, pidx;
+  int slot, level, first, tiles, gx, gy;
 };
 
+// off/count: entries of the list; total: tiles over all entries.
 struct BList {
-  int off, count;
+  int off, count, total, pad_;
 };
 
 // Work-list kinds; list index = kind * PS_BMAX_LEVELS + level.

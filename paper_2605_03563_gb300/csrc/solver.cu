@@ -912,52 +912,49 @@ void destroy_batch_graphs(ps_batch_ctx* b) {
 ps_status batch_rebuild(ps_batch_ctx* b) {
   const int L = PS_BMAX_LEVELS;
   std::vector<std::vector<BItem>> lists(BL_NKINDS * L);
+  std::vector<int> totals(BL_NKINDS * L, 0);
+  auto push = [&](int list, int si, int level, int gx, int gy, int gz) {
+    const int tiles = gx * gy * gz;
+    lists[list].push_back({si, level, totals[list], tiles, gx, gy});
+    totals[list] += tiles;
+  };
   size_t smem = 8;
   for (int si = 0; si < b->cap; si++) {
     BSlot& sd = b->hslots[si];
     if (!sd.active) continue;
     ps_ctx* h = b->slots[si].h;
     const int nl = sd.nlev;
+    int gx, gy, gz;
     for (int l = 0; l + 1 < nl; l++) {
-      int gx, gy, gz;
       batch_tiles_sweep(sd.lv[l].d, b->order, sd.lv[l].zc, &gx, &gy, &gz);
-      for (int z = 0; z < gz; z++)
-        for (int y = 0; y < gy; y++)
-          for (int x = 0; x < gx; x++) lists[BL_SWEEP * L + l].push_back({si, l, x, y, z, 0});
+      push(BL_SWEEP * L + l, si, l, gx, gy, gz);
       batch_tiles_points(sd.lv[l + 1].d, sd.lv[l + 1].zc, &gx, &gy, &gz);
-      for (int z = 0; z < gz; z++)
-        for (int y = 0; y < gy; y++)
-          for (int x = 0; x < gx; x++) lists[BL_COARSE_PT * L + l].push_back({si, l, x, y, z, 0});
+      push(BL_COARSE_PT * L + l, si, l, gx, gy, gz);
       batch_tiles_cells(sd.lv[l + 1].d, sd.lv[l + 1].zc, &gx, &gy, &gz);
-      for (int z = 0; z < gz; z++)
-        for (int y = 0; y < gy; y++)
-          for (int x = 0; x < gx; x++) lists[BL_CELLS * L + l].push_back({si, l, x, y, z, 0});
+      push(BL_CELLS * L + l, si, l, gx, gy, gz);
     }
-    lists[BL_CG * L + (nl - 1)].push_back({si, nl - 1, 0, 0, 0, 0});
+    push(BL_CG * L + (nl - 1), si, nl - 1, 1, 1, 1);
     smem = std::max(smem, coarse_cg_smem_bytes(sd.lv[nl - 1].d));
-    int gx, gy, gz, np = 0;
     if (b->prec == 0) {
       batch_tiles_sweep(sd.lv[0].d, b->order, sd.lv[0].zc, &gx, &gy, &gz);
-      for (int z = 0; z < gz; z++)
-        for (int y = 0; y < gy; y++)
-          for (int x = 0; x < gx; x++) lists[BL_NORM0 * L].push_back({si, 0, x, y, z, np++});
+      push(BL_NORM0 * L, si, 0, gx, gy, gz);
     } else {
       batch_tiles_points(sd.lv[0].d, sd.lv[0].zc, &gx, &gy, &gz);
-      for (int z = 0; z < gz; z++)
-        for (int y = 0; y < gy; y++)
-          for (int x = 0; x < gx; x++) lists[BL_PT0 * L].push_back({si, 0, x, y, z, np++});
+      push(BL_PT0 * L, si, 0, gx, gy, gz);
     }
-    sd.nparts = np;
-    ps_status r = ensure_partials(h, np);
+    sd.nparts = gx * gy * gz;   // one norm partial per level-0 tile
+    ps_status r = ensure_partials(h, sd.nparts);
     if (r != PS_OK) return r;
     sd.partials = h->partials;
-    lists[BL_SLOTS * L].push_back({si, 0, 0, 0, 0, 0});
+    push(BL_SLOTS * L, si, 0, 1, 1, 1);
   }
   std::vector<BItem> items;
   std::vector<BList> heads(BL_NKINDS * L);
   for (size_t q = 0; q < lists.size(); q++) {
     heads[q].off = (int)items.size();
     heads[q].count = (int)lists[q].size();
+    heads[q].total = totals[q];
+    heads[q].pad_ = 0;
     items.insert(items.end(), lists[q].begin(), lists[q].end());
   }
   if (items.size() > b->items_cap) {
@@ -966,7 +963,7 @@ ps_status batch_rebuild(ps_batch_ctx* b) {
     destroy_batch_graphs(b);
     cudaFree(b->ditems);
     b->ditems = nullptr;
-    b->items_cap = std::max<size_t>(items.size() * 2, 4096);
+    b->items_cap = std::max<size_t>(items.size() * 2, 1024);
     TRY(cudaMalloc(&b->ditems, b->items_cap * sizeof(BItem)));
   }
   if (smem > b->graph_smem) {

@@ -1,10 +1,11 @@
 """Continuous batching: every request's result is the same alone and in the mix.
 
 A small stream with two grid sizes, two tolerances and warm-started sequences
-is served once with up to 8 solves in flight (their kernels overlap on the
-GPU) and once strictly one at a time; each request's potential must match
+is served once with up to 8 solves in flight and once strictly one at a time,
+with the batched executor (one graph launch per tick for all solves) and with
+per-request graphs on separate streams; each request's potential must match
 bit for bit (well inside the 1e-10 FP64 tolerance), with equal iteration
-counts.  Also: warm starts help, the HBM budget gates admission, the
+counts, and the two executors agree to 1e-12.  Also: warm starts help, the HBM budget gates admission, the
 autotuner returns a converged configuration.
 """
 import numpy as np
@@ -41,10 +42,12 @@ def _serve(pkg, reqs, max_active, **kw):
     return {r.rid: r for r in res}, phis, stats
 
 
-def test_results_identical_alone_and_in_the_mix(pkg):
+@pytest.mark.parametrize("executor", ["batch", "streams", "hybrid"])
+def test_results_identical_alone_and_in_the_mix(pkg, executor):
     reqs = _stream()
-    mix, phi_mix, st_mix = _serve(pkg, reqs, max_active=8)
-    solo, phi_solo, st_solo = _serve(pkg, reqs, max_active=1)
+    kw = dict(executor=executor, max_n=64, batch_max_n=32)
+    mix, phi_mix, st_mix = _serve(pkg, reqs, max_active=8, **kw)
+    solo, phi_solo, st_solo = _serve(pkg, reqs, max_active=1, **kw)
     assert st_mix["peak_active"] > 1 and st_solo["peak_active"] == 1
     assert len(mix) == len(reqs) == len(solo)
     for rid, r in mix.items():
@@ -52,6 +55,18 @@ def test_results_identical_alone_and_in_the_mix(pkg):
         assert r.iterations == solo[rid].iterations
         assert r.rel_residual <= r.tol
         assert torch.equal(phi_mix[rid], phi_solo[rid]), rid
+
+
+def test_batch_and_stream_executors_agree(pkg):
+    """The batched executor and the per-request graphs give the same iteration
+    counts and potentials equal to 1e-12 (the reductions group differently)."""
+    reqs = _stream()
+    bat, phi_b, _ = _serve(pkg, reqs, max_active=8, executor="batch", max_n=64)
+    stm, phi_s, _ = _serve(pkg, reqs, max_active=8, executor="streams")
+    for rid, r in bat.items():
+        assert r.iterations == stm[rid].iterations
+        err = float((phi_b[rid] - phi_s[rid]).abs().max() / phi_s[rid].abs().max())
+        assert err <= 1e-12, (rid, err)
 
 
 def test_warm_starts_take_fewer_cycles(pkg):
