@@ -192,6 +192,13 @@ def run_serving(args, rank, world):
     t0 = time.perf_counter()
     results, stats = srv.run(reqs, realtime=True)
     wall = time.perf_counter() - t0
+    # saturated throughput: the same requests all available at once (the
+    # arrival rate no longer caps solves/s)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    off_results, off_stats = srv.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    off_wall = time.perf_counter() - t1
     clk = clocks.stop()
     srv.close()
     summ = summarize(results)
@@ -212,6 +219,9 @@ def run_serving(args, rank, world):
             "latency_mean_ms": summ["latency_mean_ms"], "by_tol": by_tol,
             "converged": summ["converged"], "makespan_s": summ["makespan_s"], "wall_s": wall,
             "peak_active": stats["peak_active"], "ticks": stats["ticks"],
+            "saturated": {"solves_per_s": len(off_results) / off_wall, "wall_s": off_wall,
+                          "converged": sum(1 for r in off_results if r.status == 0),
+                          "ticks": off_stats["ticks"]},
             "warm_started": sum(1 for r in results if r.warm), "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -306,6 +316,76 @@ def other_configs(dev, reps=3):
             "rel_residual": info.rel_residual, "t_mp_ms": info.t_mp_ms,
             "ms_per_iteration": ms / max(info.iterations, 1),
             "glups_per_iteration": nunk * info.iterations / (ms / 1e3) / 1e9}
+    return out
+
+
+# ------------------------------------------------------------------ batched throughput
+def batched_throughput(dev, per_size=8, sizes=(32, 64, 96, 128, 192, 256), reps=2):
+    """Solves/s to relative residual 1e-10 on a fixed set of grids of the serving
+    mix (per_size Gaussian-mixture densities of every size): the plain FP64 path
+    (one poisson_solve after another) against the batched executor (every grid
+    in one batch, one graph launch per step) in FP64 and with FP32 refinement.
+    Potentials of the batched mixed mode are compared with the FP64 ones."""
+    import torch
+    import workloads as W
+    import paper_2605_03563_gb300 as P
+    grids = []
+    for n in sizes:
+        for k in range(per_size):
+            rho = W.gaussian_blobs_device(n, W.gaussian_blob_params(1000 + 17 * n + k, 1 + (k % 16)), dev)
+            grids.append((n, rho))
+    solvers = [P.CartesianSolver(n, bc="multipole", lmax=LMAX) for n, _ in grids]
+    phis64 = [torch.zeros_like(r) for _, r in grids]
+    out = {"grids": len(grids), "sizes": list(sizes), "per_size": per_size, "tol": TOL}
+    try:
+        def plain():
+            for s, (n, rho), phi in zip(solvers, grids, phis64):
+                phi.zero_()
+                s.solve(rho, phi, tol=TOL, method="mg", max_iter=100)
+        plain()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            plain()
+            torch.cuda.synchronize()
+            t.append(time.perf_counter() - t0)
+        out["plain_fp64_solves_per_s"] = len(grids) / min(t)
+
+        def batched(prec, inner):
+            with P.Batch(len(grids), max(sizes), prec=prec, inner_cycles=inner) as b:
+                phis = [torch.zeros_like(r) for _, r in grids]
+
+                def run():
+                    for p_ in phis:
+                        p_.zero_()
+                    slots = [b.add(s, rho, p_, tol=TOL, max_iter=100)
+                             for s, (_, rho), p_ in zip(solvers, grids, phis)]
+                    while True:
+                        st, _ = b.poll()
+                        if all(st[sl] != 0 for sl in slots):
+                            break
+                        b.step(2)
+                    infos = [b.remove(sl) for sl in slots]
+                    torch.cuda.synchronize()
+                    return infos
+                run()
+                ts = []
+                for _ in range(reps):
+                    t0 = time.perf_counter()
+                    infos = run()
+                    ts.append(time.perf_counter() - t0)
+                assert all(i.converged for i in infos)
+                err = max(float((p_ - q).abs().max() / q.abs().max()) for p_, q in zip(phis, phis64))
+                return len(grids) / min(ts), err
+        out["batched_fp64_solves_per_s"], e64 = batched("fp64", 1)
+        out["batched_mixed_fp32_solves_per_s"], emx = batched("mixed_fp32", 2)
+        out["batched_fp64_max_rel_diff_vs_plain"] = e64
+        out["batched_mixed_max_rel_diff_vs_plain_fp64"] = emx
+        out["mixed_batched_vs_plain_fp64"] = out["batched_mixed_fp32_solves_per_s"] / out["plain_fp64_solves_per_s"]
+    finally:
+        for s in solvers:
+            s.close()
     return out
 
 
@@ -537,8 +617,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_sample()
     configs = None
+    batched = None
     if rank == 0 and not args.no_configs:
         configs = other_configs(dev)
+        batched = batched_throughput(dev)
 
     solver.close()
     if rank == 0:
@@ -560,6 +642,7 @@ def main():
             "rho_conv": infos[-1].rho_conv,
             "mixed": mixed,
             "other_configs": configs,
+            "batched": batched,
             "roofline": roof,
             "kernels": kernels,
             "profiled_region_ms_per_step": prof_region_ms,
