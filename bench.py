@@ -378,11 +378,49 @@ def batched_throughput(dev, per_size=8, sizes=(32, 64, 96, 128, 192, 256), reps=
                 assert all(i.converged for i in infos)
                 err = max(float((p_ - q).abs().max() / q.abs().max()) for p_, q in zip(phis, phis64))
                 return len(grids) / min(ts), err
+        def hybrid(prec, inner, batch_max_n=96):
+            # grids up to batch_max_n share the batched executor's graph launches;
+            # larger ones run their own loop graphs (tile kernels on their finest
+            # levels) on their handles' streams, concurrently with the batch
+            small = [i for i, (n, _) in enumerate(grids) if n <= batch_max_n]
+            large = [i for i, (n, _) in enumerate(grids) if n > batch_max_n]
+            phis = [torch.zeros_like(r) for _, r in grids]
+            with P.Batch(max(1, len(small)), batch_max_n, prec=prec, inner_cycles=inner) as b:
+                def run():
+                    for p_ in phis:
+                        p_.zero_()
+                    for i in large:
+                        solvers[i].begin(grids[i][1], phis[i], tol=TOL, method="mg", prec=prec,
+                                         max_iter=100, inner_cycles=inner)
+                        solvers[i].step(100)        # the loop graph stops at convergence
+                    slots = [b.add(solvers[i], grids[i][1], phis[i], tol=TOL, max_iter=100) for i in small]
+                    while slots:
+                        st, _ = b.poll()
+                        if all(st[sl] != 0 for sl in slots):
+                            break
+                        b.step(2)
+                    infos = [b.remove(sl) for sl in slots] + [solvers[i].end() for i in large]
+                    torch.cuda.synchronize()
+                    return infos
+                run()
+                ts = []
+                for _ in range(reps):
+                    t0 = time.perf_counter()
+                    infos = run()
+                    ts.append(time.perf_counter() - t0)
+            assert all(i.converged for i in infos)
+            err = max(float((p_ - q).abs().max() / q.abs().max()) for p_, q in zip(phis, phis64))
+            return len(grids) / min(ts), err
         out["batched_fp64_solves_per_s"], e64 = batched("fp64", 1)
         out["batched_mixed_fp32_solves_per_s"], emx = batched("mixed_fp32", 2)
+        out["hybrid_fp64_solves_per_s"], eh64 = hybrid("fp64", 1)
+        out["hybrid_mixed_fp32_solves_per_s"], ehmx = hybrid("mixed_fp32", 2)
         out["batched_fp64_max_rel_diff_vs_plain"] = e64
         out["batched_mixed_max_rel_diff_vs_plain_fp64"] = emx
+        out["hybrid_fp64_max_rel_diff_vs_plain"] = eh64
+        out["hybrid_mixed_max_rel_diff_vs_plain_fp64"] = ehmx
         out["mixed_batched_vs_plain_fp64"] = out["batched_mixed_fp32_solves_per_s"] / out["plain_fp64_solves_per_s"]
+        out["mixed_hybrid_vs_plain_fp64"] = out["hybrid_mixed_fp32_solves_per_s"] / out["plain_fp64_solves_per_s"]
     finally:
         for s in solvers:
             s.close()

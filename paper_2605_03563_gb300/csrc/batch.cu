@@ -37,6 +37,14 @@ void batch_tiles_points(const Dims& d, int zc, int* gx, int* gy, int* gz) {
   *gz = (d.nk() + zc - 1) / zc;
 }
 
+int batch_norm_partials(const Dims& d, int order) {
+  const int zc = batch_zchunk(d);
+  int sx, sy, sz, px, py, pz;
+  batch_tiles_sweep(d, order, zc, &sx, &sy, &sz);
+  batch_tiles_points(d, zc, &px, &py, &pz);
+  return std::max(sx * sy * sz, px * py * pz);
+}
+
 void batch_tiles_cells(const Dims& coarse, int zc, int* gx, int* gy, int* gz) {
   *gx = (coarse.nx + BBX - 1) / BBX;
   *gy = (coarse.ny + BBY - 1) / BBY;

@@ -77,6 +77,9 @@ void batch_tiles_sweep(const Dims& d, int order, int zc, int* gx, int* gy, int* 
 void batch_tiles_points(const Dims& d, int zc, int* gx, int* gy, int* gz);
 void batch_tiles_cells(const Dims& coarse, int zc, int* gx, int* gy, int* gz);
 int batch_zchunk(const Dims& d);
+// norm partials a batch writes for a solve whose finest level is d (one per
+// level-0 sweep or point tile, whichever is more)
+int batch_norm_partials(const Dims& d, int order);
 
 // Phase launches (grid-stride over list `list`).  Every launcher takes the
 // descriptor and work-list arrays in device memory.

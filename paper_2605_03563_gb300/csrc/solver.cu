@@ -481,8 +481,28 @@ ps_status read_state(ps_ctx* h, cudaStream_t s) {
   return PS_OK;
 }
 
+// Drop the handle's instantiated graphs (they hold the addresses of its
+// buffers); they are captured again on next use.
+void drop_graphs(ps_ctx* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+  for (auto& kv : h->pgraphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto& rec : kv.second.slots) {
+      cudaEventDestroy(rec.a);
+      cudaEventDestroy(rec.b);
+    }
+  }
+  h->pgraphs.clear();
+}
+
+// Grow the norm-partials buffer.  A reallocation invalidates every graph that
+// captured the old address, so those are dropped with it.
 ps_status ensure_partials(ps_ctx* h, int nblk) {
   if (nblk <= h->npart) return PS_OK;
+  drop_graphs(h);
   cudaFree(h->partials);
   h->partials = nullptr;
   TRY(cudaMalloc(&h->partials, (size_t)nblk * 2 * sizeof(double)));
@@ -1160,7 +1180,8 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
     for (int a = 0; a < 3; a++) h->h0[a] = h->hs[0][a];
     if ((s = alloc_zero((void**)&h->fs64, (size_t)h->d0.size() * 8, &h->bytes)) != PS_OK) return bail(s);
     if ((s = alloc_zero((void**)&h->phi0, (size_t)h->d0.size() * 8, &h->bytes)) != PS_OK) return bail(s);
-    if ((s = ensure_partials(h, std::max(cart_partials_count(h->d0), delta_colours_partials(h->d0, stencil_order)))) != PS_OK) return bail(s);
+    if ((s = ensure_partials(h, std::max({cart_partials_count(h->d0), delta_colours_partials(h->d0, stencil_order),
+                                                  batch_norm_partials(h->d0, stencil_order)}))) != PS_OK) return bail(s);
     if (b.outer == PS_BC_MULTIPOLE) {
       build_multipole_tables(l_max, &h->mpt);
       if ((e = cart_multipole_alloc(h->du, l_max, h->mpt, &h->mp)) != cudaSuccess)
@@ -1189,18 +1210,7 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
 
 void poisson_destroy(ps_handle h) {
   if (!h) return;
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  for (auto& kv : h->graphs)
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-  h->graphs.clear();
-  for (auto& kv : h->pgraphs) {
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    for (auto& rec : kv.second.slots) {
-      cudaEventDestroy(rec.a);
-      cudaEventDestroy(rec.b);
-    }
-  }
-  h->pgraphs.clear();
+  drop_graphs(h);
   cudaFree(h->phi0);
   if (h->cap) cudaStreamDestroy(h->cap);
   free_hier(&h->h64);

@@ -180,3 +180,33 @@ def test_batch_rejects_bad_arguments(pkg):
         rho = _rho(64, 2, 1)
         with pytest.raises(pkg.capi.PoissonError):
             b.add(big, rho, torch.zeros_like(rho))   # larger than max_n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_handle_reused_between_batch_and_solo(pkg, prec):
+    """A handle that solved on its own (its loop graph captured), then ran in a
+    batch, then solves on its own again (poisson_solve and begin/step/end)
+    gives the same potential every time: the batch leaves no buffer the
+    handle's captured graphs point to changed or freed."""
+    n = 128
+    rho = _rho(n, 2, 41)
+    other = _rho(64, 2, 42)
+    with pkg.CartesianSolver(n, bc="multipole", lmax=4) as s, \
+            pkg.CartesianSolver(64, bc="multipole", lmax=4) as s2:
+        p1 = torch.zeros_like(rho)
+        i1 = s.solve(rho, p1, tol=1e-10, method="mg", prec=prec, max_iter=60, inner_cycles=2)
+        with pkg.Batch(2, n, prec=prec, inner_cycles=2) as b:
+            (ib, _), (pb, _) = _run_batch(pkg, b, [s, s2], [rho, other], [1e-10, 1e-10])
+        p2 = torch.zeros_like(rho)
+        i2 = s.solve(rho, p2, tol=1e-10, method="mg", prec=prec, max_iter=60, inner_cycles=2)
+        p3 = torch.zeros_like(rho)
+        s.begin(rho, p3, tol=1e-10, method="mg", prec=prec, max_iter=60, inner_cycles=2)
+        s.step(60)
+        i3 = s.end()
+        torch.cuda.synchronize()
+    assert i1.converged and ib.converged and i2.converged and i3.converged
+    assert i1.iterations == i2.iterations == i3.iterations
+    # the batch's FP32 colour passes round differently from the solo tile kernels
+    assert abs(ib.iterations - i1.iterations) <= (0 if prec == "fp64" else 1)
+    assert torch.equal(p1, p2) and torch.equal(p1, p3)
+    assert _relerr(pb, p1) <= (1e-12 if prec == "fp64" else 1e-9)
