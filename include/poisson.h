@@ -322,6 +322,14 @@ ps_status ps_op_restrict(const ps_grid* fine_grid, int stencil_order, int dtype,
 ps_status ps_op_prolong(const ps_grid* fine_grid, int stencil_order, int dtype,
                         const void* e_coarse_dev, void* phi_fine_dev, void* stream);
 
+/* out[i] = x[i] * 2^e rounded to the nearest FP32 value (ties to even), for
+ * finite x and -100 <= e <= 100 (otherwise PS_ERR_INVALID_ARG).  This is the
+ * conversion the mixed-precision multigrid (Sec. 2.1.3) applies when it stores
+ * the scaled FP64 residual as the FP32/BF16 inner right-hand side; it runs on
+ * the integer pipe.  x_dev and out_dev are device arrays of n elements owned by
+ * the caller. */
+ps_status ps_op_scale_to_fp32(const double* x_dev, int64_t n, int e, float* out_dev, void* stream);
+
 /* Multipole moments q_lm (Eq. outer_multipole) of rho over the interior nodes
  * about `origin`, (l_max+1)^2 doubles into q_host (synchronises). */
 ps_status ps_op_multipole_moments(const ps_grid* grid, int stencil_order, const double* rho_dev,

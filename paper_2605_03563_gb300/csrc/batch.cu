@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(BBX* BBY) kb_delta_ir(BArgs a, int list) {
     const BLevel& lv = sl.lv[0];
     const Dims d = lv.d;
     const double oscale = sl.st->scale_next;
-    const bool fast = oscale <= 0x1p100 && oscale >= 0x1p-100;
+    const int oexp = pow2_exponent(oscale);
     const int i = item.bx * BBX + threadIdx.x + G;
     const int j = item.by * BBY + threadIdx.y + G;
     const int k0 = item.bz * lv.zc + G, k1 = min(k0 + lv.zc, G + d.nk());
@@ -421,16 +421,23 @@ __global__ void __launch_bounds__(BBX* BBY) kb_delta_ir(BArgs a, int list) {
       for (int k = k0; k < k1; k++) {
         const long long q = d.at(i, j, k);
         const double dd = gs_any<G>(lv.iso, phi, q, sy, sz, sl.cf0, fs[q]) - phi[q];
-        const float v = fast ? (float)dd * (float)oscale : (float)(dd * oscale);
+        const float v = oexp != INT_MIN ? f64_to_f32_pow2(dd, oexp) : (float)(dd * oscale);
         s2f = fmaf(v, v, s2f);
         mxf = fmaxf(mxf, fabsf(v));
         out[q] = v;
       }
     }
-    double s2 = (double)s2f / (oscale * oscale), mx = (double)mxf / oscale;
-    s2 = warp_sum(s2);
-    mx = warp_max(mx);
-    if ((tid & 31) == 0) { sh[tid >> 5] = s2; sh[32 + (tid >> 5)] = mx; }
+    // FP32 warp sums of the scaled values, unscaled once per warp, FP64 across warps
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s2f += __shfl_xor_sync(0xffffffffu, s2f, o);
+      mxf = fmaxf(mxf, __shfl_xor_sync(0xffffffffu, mxf, o));
+    }
+    if ((tid & 31) == 0) {
+      const double inv = inverse_scale(oscale);
+      sh[tid >> 5] = (double)s2f * inv * inv;
+      sh[32 + (tid >> 5)] = (double)mxf * inv;
+    }
     __syncthreads();
     if (tid < 32) {
       double u = tid < 8 ? sh[tid] : 0.0, m = tid < 8 ? sh[32 + tid] : 0.0;

@@ -118,6 +118,38 @@ __device__ __forceinline__ void block_sum_max(double s, double m, double* partia
   }
 }
 
+// Block {sum, max} of FP32 per-thread values of a scaled quantity x * scale:
+// warps reduce in FP32 (the per-thread sums already are FP32), each warp's
+// result is unscaled once in FP64 and the warps are combined in FP64, so the
+// FP64 pipe sees a few instructions per warp instead of per thread.
+__device__ __forceinline__ void block_sum_max_scaled(float s, float m, double scale, double* partials) {
+  __shared__ double sh[64];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if (lane == 0) {
+    const double inv = inverse_scale(scale);
+    sh[warp] = (double)s * inv * inv;
+    sh[32 + warp] = (double)m * inv;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double a = lane < nw ? sh[lane] : 0.0;
+    double b = lane < nw ? sh[32 + lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_max(b);
+    if (lane == 0) {
+      int bid = block_linear_id();
+      partials[2 * bid] = a;
+      partials[2 * bid + 1] = b;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ delta pass
 // RED: 0 no reduction, 1 sum of delta^2, 2 sum of delta^2 and max |delta|.
 template <int G, bool ISO, typename TI, int RED>
@@ -137,6 +169,8 @@ __global__ void __launch_bounds__(BX* BY)
   float s2f = 0.0f, mxf = 0.0f;
   double oscale = out_scale;
   if (st != nullptr) oscale = st->scale_next;
+  // a power-of-two scale 2^e (|e| <= 100) is applied inside the integer-pipe conversion
+  const int oexp = pow2_exponent(oscale);
   if (i < G + d.ni() && j < G + d.nj()) {
     // two z nodes per trip: their loads and FP64 chains are independent
 #pragma unroll 2
@@ -152,12 +186,10 @@ __global__ void __launch_bounds__(BX* BY)
       if (RED == 2 && dout != DT_F64) {
         // refinement pass: the stored inner right-hand side is FP32/BF16, so the
         // sum of squares and the max run on the FP32 pipe over the scaled value
-        // (O(1) by the choice of the power-of-two scale; exact to undo).  While
-        // the scale is a moderate power of two it is applied after the
-        // conversion, in FP32: the same value as converting the scaled double for
-        // every element in FP32's normal range, one FP64 instruction fewer.
-        const float v = (oscale <= 0x1p100 && oscale >= 0x1p-100) ? (float)dd * (float)oscale
-                                                                  : (float)(dd * oscale);
+        // (O(1) by the choice of the power-of-two scale; exact to undo).  The
+        // scaled value is rounded to FP32 on the integer pipe (no FP64 conversion
+        // or multiply).
+        const float v = oexp != INT_MIN ? f64_to_f32_pow2(dd, oexp) : (float)(dd * oscale);
         s2f = fmaf(v, v, s2f);
         mxf = fmaxf(mxf, fabsf(v));
         if (dout == DT_F32) ((float*)out)[p] = v;
@@ -180,8 +212,8 @@ __global__ void __launch_bounds__(BX* BY)
     }
   }
   if (RED == 2 && dout != DT_F64) {
-    s2 += (double)s2f / (oscale * oscale);
-    mx = fmax(mx, (double)mxf / oscale);
+    block_sum_max_scaled(s2f, mxf, oscale, partials);
+    return;
   }
   if (RED >= 1) block_sum_max(s2, mx, partials);
 }
@@ -770,6 +802,20 @@ __global__ void k_loop_gate(const DevState* st, unsigned long long cond) {
 
 cudaError_t launch_loop_gate(const DevState* st, unsigned long long cond, cudaStream_t s) {
   k_loop_gate<<<1, 1, 0, s>>>(st, cond);
+  return cudaGetLastError();
+}
+
+// out[i] = x[i] * 2^e rounded to FP32 by the refinement residual's conversion
+__global__ void k_pow2_to_f32(const double* __restrict__ x, long long n, int e, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = f64_to_f32_pow2(x[i], e);
+}
+
+cudaError_t launch_pow2_to_f32(const double* x, long long n, int e, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  const int blocks = (int)std::min<long long>(want, 8LL * 152);
+  k_pow2_to_f32<<<blocks, 256, 0, s>>>(x, n, e, out);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 // are deterministic: a fixed xor-shuffle tree per warp, a fixed tree per block,
 // per-block partials summed in block order by a single-block finisher.
 #pragma once
+#include <climits>
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -130,6 +131,56 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
       v[q] = warp_sum(x);
     }
   }
+}
+
+// 1/p for p = 2^e, |e| <= 1022, by negating the exponent field (an integer
+// subtraction; no FP64 division); other p divide.
+__device__ __forceinline__ double inverse_scale(double p) {
+  const long long b = __double_as_longlong(p);
+  const long long e = (b >> 52) & 0x7ff;
+  if ((b & 0x000fffffffffffffLL) == 0 && b > 0 && e >= 1 && e <= 2045)
+    return __longlong_as_double(0x7fe0000000000000LL - b);
+  return 1.0 / p;
+}
+
+// Exponent e of p when p = 2^e exactly with |e| <= 100, else INT_MIN.
+__device__ __forceinline__ int pow2_exponent(double p) {
+  const long long b = __double_as_longlong(p);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  return ((b & 0x000fffffffffffffLL) == 0 && b > 0 && e >= -100 && e <= 100) ? e : INT_MIN;
+}
+
+// x * 2^e rounded to the nearest binary32 (ties to even), for finite x and
+// |e| <= 100, computed on the integer pipe from the binary64 encoding
+// (IEEE 754 round-to-nearest-even applied to the 53-bit significand):
+//   result exponent fe = ex - 1023 + 127 + e; normal results keep the top 23
+//   fraction bits and round on the 29 dropped ones; results below the binary32
+//   normal range shift the significand (implicit bit included) right by
+//   29 + 1 - fe; a carry out of the fraction moves into the exponent, which
+//   also yields the smallest normal and infinity where they are the rounded
+//   values.  It replaces a conversion instruction of the FP64 pipe.
+__device__ __forceinline__ float f64_to_f32_pow2(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return __uint_as_float(sign);   // zero, or below 2^-1022 (2^-922 after scaling): rounds to 0
+  const int fe = ex - 1023 + 127 + e;
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long frac = b & 0x000fffffffffffffull;
+  if (fe >= 1) {
+    const unsigned m = (unsigned)(frac >> 29);
+    const unsigned rest = (unsigned)frac & 0x1fffffffu;
+    unsigned r = ((unsigned)fe << 23) | m;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) r += 1u;
+    return __uint_as_float(sign | r);
+  }
+  const int sh = 30 - fe;   // >= 30
+  if (sh > 54) return __uint_as_float(sign);   // below half the smallest subnormal
+  const unsigned long long sig = frac | 0x0010000000000000ull;
+  unsigned q = (unsigned)(sig >> sh);
+  const unsigned long long rest = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  if (rest > half || (rest == half && (q & 1u))) q += 1u;
+  return __uint_as_float(sign | q);
 }
 
 __device__ __forceinline__ int block_linear_id() {

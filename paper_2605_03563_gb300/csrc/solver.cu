@@ -1727,6 +1727,13 @@ ps_status ps_op_prolong(const ps_grid* grid, int order, int dtype, const void* e
   return PS_OK;
 }
 
+ps_status ps_op_scale_to_fp32(const double* x, int64_t n, int e, float* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return fail(PS_ERR_INVALID_ARG, "NULL buffer or negative n");
+  if (e < -100 || e > 100) return fail(PS_ERR_INVALID_ARG, "e must be in -100..100 (got %d)", e);
+  TRY(launch_pow2_to_f32(x, (long long)n, e, out, (cudaStream_t)stream));
+  return PS_OK;
+}
+
 ps_status ps_op_multipole_moments(const ps_grid* grid, int order, const double* rho, const double origin[3],
                                   int l_max, double* q_host, void* stream) {
   Dims d;

@@ -7,12 +7,12 @@
 // library-layout level array (rows padded to 32 elements).
 //
 // k_rb_sweep: one whole red-black Gauss-Seidel sweep of the 7-point operator
-//   (Sec. 2.1.1, red = (i+j+k) even first), out of place.  Red updates of a
-//   plane are computed on the tile plus a one-node halo into a shared ring of
-//   three planes; black updates read only that ring.  Halo red values equal the
-//   neighbouring tile's (same operands, same arithmetic), so the result is the
-//   sequential red-then-black sweep bit for bit, while HBM traffic is one read
-//   of phi and fs and one write of phi per sweep instead of per colour.
+//   (Sec. 2.1.1, red = (i+j+k) even first), out of place.  Each warp marches a
+//   strip of rows with the red values of three planes in registers; red values
+//   just outside a strip or tile are recomputed from the same operands with the
+//   same arithmetic, so the result is the sequential red-then-black sweep bit
+//   for bit, while HBM traffic is one read of phi and fs and one write of phi
+//   per sweep instead of per colour.
 //
 // k_resid_restrict: the fine residual delta = phi_GS - phi of each plane is
 //   computed into shared memory on the tile's (2T+1)^2 footprint and folded at
@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "tiled_kernels.cuh"
 #include "tma.cuh"
@@ -81,222 +82,297 @@ __host__ __device__ constexpr int xhalo() {
 }
 
 // ================================================================== red-black sweep
-// Block = NW = TY + 2 warps over a 64 x TY tile.  Warp w owns ring row w, i.e.
-// grid row y = y0 - 1 + w (w = 0 and w = TY + 1 are halo rows that only
-// compute red values); lane l owns the x pair (x0 + 2l, x0 + 2l + 1), of which
-// exactly one node is red on every plane.  Because x0 is even, the red column
-// of a row alternates with the plane and is the same for all lanes of a warp,
-// so the warp never diverges on colour.  The red node of a lane on plane z and
-// on plane z +- 2 is the same column, so each lane keeps in registers the red
-// values of planes k-1, k, k+1 (the black update's z neighbours and the red
-// half of the output pair) and the old potential of its red column one plane
-// up (the next-but-one red update's lower z neighbour).  Warp 0 also computes
-// the red values of the two halo columns x0 - 1 and x0 + 64 (one of them is red
-// in each row), which the edge lanes' black updates read.
-template <typename T, int TY, int NS>
+// Register-blocked z-march.  Block = NWC warps over a 64 x TY tile (TY = R NWC);
+// warp w owns the R grid rows ys .. ys+R-1 (ys = y0 + w R), lane l the x pair
+// (xa, xa+1), xa = x0 + 2l, of which exactly one node is red on every row and
+// plane: with ys and xa even, row r of plane p has its red node at xa + ((r+p)&1).
+// Each step k of the march
+//   * computes red(k+1) on rows -1 .. R of the strip (the two outer rows repeat
+//     the neighbouring strips' arithmetic, so no warp waits for another's reds)
+//     from the plane k+1 pairs held in registers, the plane k+2 pairs it loads
+//     from the staged ring, and the old value of plane k kept from the last step;
+//   * computes the red value of plane k+1 at the x-halo column of each row
+//     (x0 - 1 or x0 + 64, whichever is red), lanes 0 .. R-1 one row each;
+//   * finishes black(k) on rows 0 .. R-1 from the reds of planes k-1, k, k+1
+//     (in-plane x neighbours from the adjacent lane by shuffle, the tile edges from
+//     the halo reds) and stores the (red, black) pair of plane k.
+// Every value repeats the colour passes' arithmetic on the same operands, so the
+// result equals the sequential red-then-black sweep bit for bit.  Shared memory
+// holds only the TMA ring of phi and fs planes; one barrier per plane releases
+// the oldest stage to the next copy.
+template <typename T, int R, int NWC, int NS>
 struct SweepGeom {
+  static_assert(R % 2 == 0, "rows per warp must be even (red column parity)");
   static constexpr int TX = 64;
-  static constexpr int NW = TY + 2;                // warps: ring rows y0-1 .. y0+TY
-  static constexpr int NTH = 32 * NW;
+  static constexpr int TY = R * NWC;
+  static constexpr int NTH = 32 * NWC;
   static constexpr int XH = xhalo<T>();
   static constexpr int WP = TX + 2 * XH;           // staged row width (phi and fs)
   static constexpr int HP = TY + 4;                // phi rows: y0-2 .. y0+TY+1
   static constexpr int HF = TY + 2;                // fs rows:  y0-1 .. y0+TY
-  static constexpr int RW = TX + 2, RH = TY + 2;   // red ring: x0-1..x0+TX, y0-1..y0+TY
   static constexpr int PBYTES = WP * HP * (int)sizeof(T);
   static constexpr int FBYTES = WP * HF * (int)sizeof(T);
   static constexpr int PB = align_up(PBYTES, 128), FB = align_up(FBYTES, 128);
-  static constexpr int RB = align_up(RW * RH * (int)sizeof(T), 128);
-  static constexpr int SMEM = NS * (PB + FB) + 3 * RB + NS * 8;
+  static constexpr int SMEM = NS * (PB + FB) + NS * 8;
 };
 
-template <typename T, bool ISO, int TY, int NS>
-__global__ void __launch_bounds__(32 * (TY + 2))
-    k_rb_sweep(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mF, Dims d,
-               Coef<typename St<T>::C> cf, T* __restrict__ out, int zc, const DevState* __restrict__ st,
-               int* __restrict__ fault) {
-  using C = typename St<T>::C;
+// two adjacent staged values as floats (the pair is 2-element aligned)
+template <typename T> __device__ __forceinline__ float2 ld_pair(const T* p);
+template <> __device__ __forceinline__ float2 ld_pair<float>(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+template <> __device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+__device__ __forceinline__ float pick(float2 v, int c) { return c ? v.y : v.x; }
+
+template <bool ISO>
+__device__ __forceinline__ float gs7(float ax, float ay, float az, float f, const Coef<float>& cf) {
+  if (ISO) return fma((ax + ay) + az, cf.c1[0], f);
+  return fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
+}
+
+// Per-thread state of the march and one step of it (KP = parity of plane k).
+template <typename T, bool ISO, int R, int NWC, int NS>
+struct RbMarch {
   using S = St<T>;
-  using Gm = SweepGeom<T, TY, NS>;
-  constexpr int TX = Gm::TX, NW = Gm::NW, XH = Gm::XH, WP = Gm::WP, RW = Gm::RW;
-  constexpr int PBE = Gm::PB / (int)sizeof(T), FBE = Gm::FB / (int)sizeof(T), RBE = Gm::RB / (int)sizeof(T);
+  using Gm = SweepGeom<T, R, NWC, NS>;
+  static constexpr int WP = Gm::WP;
+  static constexpr int NR = R + 2;   // red rows -1 .. R   (index i = r + 1)
+  static constexpr int NP = R + 4;   // phi rows -2 .. R+1 (index i = r + 2)
+  static constexpr int PBE = Gm::PB / (int)sizeof(T), FBE = Gm::FB / (int)sizeof(T);
+  static constexpr unsigned FULL = 0xffffffffu;
+
+  const T* Pst;
+  const T* Fst;
+  unsigned long long* bar;
+  Coef<float> cf;
+  int l, x0, nx, nz, ny, ys, z0, pofs, hbase, hfbase;
+  unsigned bm0, bm1;      // boundary bits of the red rows, per red column parity
+  bool col_a, col_b, h_rowb;
+  T* o;                   // output of (xa, ys) on the next black plane
+  long long osz, opy;
+  // pipeline
+  bool ok;
+  int wq, qk, qk1, qk2;
+  unsigned wph;
+  // registers carried from step to step
+  float zlo[NR];          // phi(k) at the red column of plane k+1
+  float rm[R], r0[NR], rp[NR];   // red(k-1) (rows 0..R-1), red(k), red(k+1)
+  float fb[R];            // fs(k) at the black column
+  float hk, hk1;          // halo reds of planes k, k+1 (lane l < R: row l)
+
+  __device__ __forceinline__ void wait_next() {
+    mbar_wait(&bar[wq], wph, ok);
+    if (++wq == NS) { wq = 0; wph ^= 1u; }
+  }
+
+  template <int KP>
+  __device__ __forceinline__ void step(int k, float2 (&A)[NP], float2 (&B)[NP]) {
+    constexpr int PR = KP ^ 1;   // parity of plane k + 1
+    wait_next();                 // plane k + 2
+    const T* P0 = Pst + qk * PBE;
+    const T* P1 = Pst + qk1 * PBE;
+    const T* P2 = Pst + qk2 * PBE;
+    const T* F1 = Fst + qk1 * FBE;
+#pragma unroll
+    for (int i = 0; i < NP; i++) B[i] = ld_pair(P2 + pofs + i * WP);
+    float2 ff[NR];
+#pragma unroll
+    for (int i = 0; i < NR; i++) ff[i] = ld_pair(F1 + pofs + i * WP);
+    const bool pb = k + 1 <= 0 || k + 1 >= nz;
+    // red(k+1), rows -1 .. R
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+      const int c = (i + 1 + PR) & 1;   // red column of row i-1 (compile-time)
+      const float2 a = A[i + 1];
+      float nb;
+      if (c == 0) {
+        nb = __shfl_up_sync(FULL, a.y, 1);
+        if (l == 0) nb = S::ld(P1 + pofs + (i + 1) * WP - 1);
+      } else {
+        nb = __shfl_down_sync(FULL, a.x, 1);
+        if (l == 31) nb = S::ld(P1 + pofs + (i + 1) * WP + 2);
+      }
+      const float ax = nb + (c ? a.x : a.y);
+      const float ay = pick(A[i], c) + pick(A[i + 2], c);
+      const float az = pick(B[i + 1], c) + zlo[i];
+      const float v = gs7<ISO>(ax, ay, az, pick(ff[i], c), cf);
+      const bool bnd = pb || (((c ? bm1 : bm0) >> i) & 1u);
+      rp[i] = stored<T>(bnd ? pick(a, c) : v);
+    }
+    // halo red(k+1) of row l (lanes 0 .. R-1)
+    if (l < R) {
+      const int c = (l + PR) & 1;
+      const int hc = c ? -1 : Gm::TX;   // x0 - 1 is red where the pair's red is odd
+      const int pi = hbase + hc;
+      const float ax = S::ld(P1 + pi + 1) + S::ld(P1 + pi - 1);
+      const float ay = S::ld(P1 + pi + WP) + S::ld(P1 + pi - WP);
+      const float az = S::ld(P2 + pi) + S::ld(P0 + pi);
+      const float v = gs7<ISO>(ax, ay, az, S::ld(F1 + hfbase + hc), cf);
+      const int hx = x0 + hc;
+      const bool bnd = pb || h_rowb || hx <= 0 || hx >= nx;
+      hk1 = stored<T>(bnd ? S::ld(P1 + pi) : v);
+    }
+    // black(k), rows 0 .. R-1, and the store of plane k
+    if (k >= z0) {
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int cb = (r + KP + 1) & 1;   // black column on plane k
+        const float own = r0[r + 1];       // red(k) in the pair
+        const float hv = __shfl_sync(FULL, hk, r);
+        float nb;
+        if (cb == 0) {
+          nb = __shfl_up_sync(FULL, own, 1);
+          if (l == 0) nb = hv;
+        } else {
+          nb = __shfl_down_sync(FULL, own, 1);
+          if (l == 31) nb = hv;
+        }
+        const float ax = nb + own;
+        const float ay = r0[r] + r0[r + 2];
+        const float az = rp[r + 1] + rm[r];
+        const float vb = gs7<ISO>(ax, ay, az, fb[r], cf);
+        const float v0 = cb ? own : vb, v1 = cb ? vb : own;
+        const int yy = ys + r;
+        if (yy >= 1 && yy < ny) {
+          T* orow = o + r * opy;
+          if (col_a && col_b) {
+            St2<T>::st(orow, v0, v1);
+          } else {
+            if (col_a) S::st(orow, v0);
+            if (col_b) S::st(orow + 1, v1);
+          }
+        }
+      }
+      o += osz;
+    }
+    // carry to step k + 1
+#pragma unroll
+    for (int r = 0; r < R; r++) rm[r] = r0[r + 1];
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+      r0[i] = rp[i];
+      zlo[i] = pick(A[i + 1], (i + 1 + KP) & 1);   // phi(k+1) at the red column of plane k+2
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) fb[r] = pick(ff[r + 1], ((r + PR) & 1) ^ 1);
+    hk = hk1;
+  }
+};
+
+template <typename T, bool ISO, int R, int NWC, int NS>
+__global__ void __launch_bounds__(32 * NWC)
+    k_rb_sweep(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mF, Dims d,
+               Coef<float> cf, T* __restrict__ out, int zc, const DevState* __restrict__ st,
+               int* __restrict__ fault) {
+  using S = St<T>;
+  using Gm = SweepGeom<T, R, NWC, NS>;
+  using M = RbMarch<T, ISO, R, NWC, NS>;
+  constexpr int WP = Gm::WP, XH = Gm::XH, NR = M::NR, NP = M::NP, PBE = M::PBE, FBE = M::FBE;
   extern __shared__ __align__(128) unsigned char smem[];
   T* Pst = reinterpret_cast<T*>(smem);
   T* Fst = reinterpret_cast<T*>(smem + NS * Gm::PB);
-  T* Rr = reinterpret_cast<T*>(smem + NS * (Gm::PB + Gm::FB));
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + NS * (Gm::PB + Gm::FB) + 3 * Gm::RB);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + NS * (Gm::PB + Gm::FB));
 
   if (st != nullptr && st->done) return;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int nx = d.nx, ny = d.ny, nz = d.nz;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = 1 + blockIdx.z * zc;
-  const int z1 = min(z0 + zc, nz);     // output planes [z0, z1)
-  const int zl = z0 - 2, zh = z1 + 1;  // staged planes [zl, zh]; plane z sits in stage (z - zl) % NS
+  const int x0 = blockIdx.x * Gm::TX, y0 = blockIdx.y * Gm::TY;
+  const int z0 = 1 + blockIdx.z * zc;   // zc is even: z0 is odd in every block
+  const int z1 = min(z0 + zc, nz);      // output planes [z0, z1)
+  const int zl = z0 - 2, zh = z1 + 1;   // staged planes [zl, zh]
   if (tid == 0) {
     for (int q = 0; q < NS; q++) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
-
   auto issue = [&](int z, int q) {   // thread 0: stage q <- plane z
     if (z > zh) return;
     mbar_expect_tx(&bar[q], Gm::PBYTES + Gm::FBYTES);
     tma_load_3d(Pst + q * PBE, &mP, x0 - XH, y0 - 2, z, &bar[q]);
     tma_load_3d(Fst + q * FBE, &mF, x0 - XH, y0 - 1, z, &bar[q]);
   };
-  // planes are waited for in order; (wq, wph) = stage and phase of the next one
-  bool ok = true;
-  int wq = 0;
-  unsigned wph = 0;
-  auto wait_next = [&]() {
-    mbar_wait(&bar[wq], wph, ok);
-    if (++wq == NS) { wq = 0; wph ^= 1u; }
-  };
-  auto nxt = [](int q) { return q + 1 == NS ? 0 : q + 1; };
-
-  const int y = y0 - 1 + w;                        // this warp's grid row
-  const bool row_out = w >= 1 && w <= TY && y >= 1 && y < ny;
-  const bool row_bnd = y <= 0 || y >= ny;
-  const int xa = x0 + 2 * l;
-  // boundary or outside in x, for the pair's even / odd column
-  const bool bnd_e = row_bnd || xa <= 0 || xa >= nx;
-  const bool bnd_o = row_bnd || xa + 1 >= nx;
-  const bool st_pair = row_out && xa >= 1 && xa + 1 < nx;
-  const bool st_a = row_out && xa >= 1 && xa < nx, st_b = row_out && xa + 1 < nx;
-  const int pbase = (w + 1) * WP + XH + 2 * l;     // P index of (xa, y)
-  const int fbase = w * WP + XH + 2 * l;           // F index of (xa, y)
-  const int rbase = w * RW + 1 + 2 * l;            // R index of (xa, y)
-
-  // red value at column xa + par of this warp's row on plane z (stage qz, plane z+1 in
-  // stage qp), zm = old phi one plane down; returns the value as stored
-  auto red_at = [&](int par, bool zb, int qz, int qp, C zm) -> C {
-    const T* P = Pst + qz * PBE + pbase + par;
-    C v;
-    if (zb || (par ? bnd_o : bnd_e)) {
-      v = S::ld(P);
-    } else {
-      const C ax = S::ld(P + 1) + S::ld(P - 1);
-      const C ay = S::ld(P + WP) + S::ld(P - WP);
-      const C az = S::ld(Pst + qp * PBE + pbase + par) + zm;
-      const C f = S::ld(Fst + qz * FBE + fbase + par);
-      if (ISO) v = fma((ax + ay) + az, cf.c1[0], f);
-      else v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
-    }
-    return stored<T>(v);
-  };
-  // warp 0: red value of the halo column of ring row l (l < NW) on plane z
-  auto halo_red = [&](int z, int qm, int qz, int qp, T* R) {
-    if (w != 0 || l >= NW) return;
-    const int yy = y0 - 1 + l;
-    const int hc = ((yy + z) & 1) ? x0 - 1 : x0 + TX;
-    const T* P = Pst + qz * PBE;
-    const int pc = (l + 1) * WP + XH + (hc - x0);
-    C v;
-    if (yy <= 0 || yy >= ny || z <= 0 || z >= nz || hc <= 0 || hc >= nx) {
-      v = S::ld(P + pc);
-    } else {
-      const C ax = S::ld(P + pc + 1) + S::ld(P + pc - 1);
-      const C ay = S::ld(P + pc + WP) + S::ld(P + pc - WP);
-      const C az = S::ld(Pst + qp * PBE + pc) + S::ld(Pst + qm * PBE + pc);
-      const C f = S::ld(Fst + qz * FBE + l * WP + XH + (hc - x0));
-      if (ISO) v = fma((ax + ay) + az, cf.c1[0], f);
-      else v = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
-    }
-    S::st(R + l * RW + 1 + (hc - x0), v);
-  };
-
   if (tid == 0)
     for (int q = 0; q < NS; q++) issue(zl + q, q);
-  // prologue: red values of planes z0-1 (stages 0,1,2 = planes z0-2, z0-1, z0) and z0
-  wait_next();
-  wait_next();
-  wait_next();
-  C rm2, rm1, ph0, ph1;   // red(k-1), red(k); old phi one plane above the red column of planes k+1, k+2
-  {
-    const int z = z0 - 1, par = (y + z) & 1;
-    const C zm = S::ld(Pst + 0 * PBE + pbase + par);
-    rm2 = red_at(par, z <= 0, 1, 2, zm);
-    S::st(Rr + 0 * RBE + rbase + par, rm2);
-    ph0 = S::ld(Pst + 2 * PBE + pbase + par);   // phi(z0) at the red column of planes z0-1, z0+1
-    halo_red(z, 0, 1, 2, Rr + 0 * RBE);
-  }
-  wait_next();   // plane z0 + 1 in stage 3
-  {
-    const int z = z0, par = (y + z) & 1;
-    const C zm = S::ld(Pst + 1 * PBE + pbase + par);
-    rm1 = red_at(par, false, 2, 3, zm);
-    S::st(Rr + 1 * RBE + rbase + par, rm1);
-    ph1 = S::ld(Pst + 3 * PBE + pbase + par);   // phi(z0+1) at the red column of planes z0, z0+2
-    halo_red(z, 1, 2, 3, Rr + 1 * RBE);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    fence_proxy_async();
-    issue(zl + NS, 0);
-  }
-  // rotating stages of planes k, k+1, k+2 and ring slots of planes k, k+1
-  int qk = 2, qk1 = 3, qk2 = 4 % NS, iq = 1;
-  T* Rk = Rr + 1 * RBE;
-  T* Rk1 = Rr + 2 * RBE;
-  T* Rk2 = Rr + 0 * RBE;
-  T* o = out + ((long long)z0 * d.ey + y) * d.px + xa;
-  const long long osz = d.sz();
-  for (int k = z0; k < z1; k++) {
-    wait_next();   // plane k + 2
-    const int zr = k + 1, par = (y + zr) & 1;
-    const C rp = red_at(par, zr >= nz, qk1, qk2, ph0);
-    S::st(Rk1 + rbase + par, rp);
-    ph0 = ph1;
-    ph1 = S::ld(Pst + qk2 * PBE + pbase + par);
-    halo_red(zr, qk, qk1, qk2, Rk1);
+
+  M m;
+  m.Pst = Pst;
+  m.Fst = Fst;
+  m.bar = bar;
+  m.cf = cf;
+  m.l = l;
+  m.x0 = x0;
+  m.nx = nx;
+  m.ny = ny;
+  m.nz = nz;
+  m.ys = y0 + w * R;
+  m.z0 = z0;
+  const int xa = x0 + 2 * l;
+  const int prow = w * R * WP + XH;   // staged phi row of grid row ys-2 / fs row of ys-1, at x0
+  m.pofs = prow + 2 * l;
+  unsigned rowb = 0;
+#pragma unroll
+  for (int i = 0; i < NR; i++)
+    if (m.ys + i - 1 <= 0 || m.ys + i - 1 >= ny) rowb |= 1u << i;
+  m.bm0 = (xa <= 0 || xa >= nx) ? ~0u : rowb;
+  m.bm1 = (xa + 1 >= nx) ? ~0u : rowb;
+  m.col_a = xa >= 1 && xa < nx;
+  m.col_b = xa + 1 < nx;
+  m.h_rowb = m.ys + l <= 0 || m.ys + l >= ny;
+  m.hbase = prow + (l + 2) * WP;
+  m.hfbase = prow + (l + 1) * WP;
+  m.o = out + ((long long)z0 * d.ey + m.ys) * d.px + xa;
+  m.osz = d.sz();
+  m.opy = d.px;
+  m.ok = true;
+  m.wq = 0;
+  m.wph = 0;
+  m.hk = m.hk1 = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; i++) m.rm[i] = m.fb[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < NR; i++) m.r0[i] = 0.f;
+
+  // prologue: phi(zl) at the red column of plane zl+1 (zl is odd: parity 0), pairs of plane zl+1
+  float2 PA[NP], PB2[NP];   // phi pairs of planes k+1 and k+2 (roles alternate by step)
+  m.wait_next();
+  m.wait_next();
+#pragma unroll
+  for (int i = 0; i < NR; i++) m.zlo[i] = S::ld(Pst + m.pofs + (i + 1) * WP + ((i + 1) & 1));
+#pragma unroll
+  for (int i = 0; i < NP; i++) PA[i] = ld_pair(Pst + PBE + m.pofs + i * WP);
+  m.qk = 0;
+  m.qk1 = 1;
+  m.qk2 = 2 % NS;
+  auto release = [&](int k) {   // the stage of plane k takes plane k + NS
     __syncthreads();
     if (tid == 0) {
       fence_proxy_async();
-      issue(k - 1 + NS, iq);   // stage of plane k-1
+      issue(k + NS, m.qk);
     }
-    if (row_out) {
-      // black(k) at column xa + par (black on plane k), red(k) at the other column
-      const T* Rb = Rk + rbase + par;
-      const C ax = S::ld(Rb + 1) + S::ld(Rb - 1);
-      const C ay = S::ld(Rb + RW) + S::ld(Rb - RW);
-      const C az = rp + rm2;
-      const C f = S::ld(Fst + qk * FBE + fbase + par);
-      C vb;
-      if (ISO) vb = fma((ax + ay) + az, cf.c1[0], f);
-      else vb = fma(ax, cf.c1[0], fma(ay, cf.c1[1], fma(az, cf.c1[2], f)));
-      const C v0 = par ? rm1 : vb, v1 = par ? vb : rm1;
-      if (st_pair) {
-        St2<T>::st(o, v0, v1);
-      } else {
-        if (st_a) S::st(o, v0);
-        if (st_b) S::st(o + 1, v1);
-      }
+    m.qk = m.qk1;
+    m.qk1 = m.qk2;
+    m.qk2 = m.qk2 + 1 == NS ? 0 : m.qk2 + 1;
+  };
+  for (int k = zl; k < z1; k += 2) {
+    m.template step<1>(k, PA, PB2);   // zl is odd
+    release(k);
+    if (k + 1 < z1) {
+      m.template step<0>(k + 1, PB2, PA);
+      release(k + 1);
     }
-    o += osz;
-    rm2 = rm1;
-    rm1 = rp;
-    T* t = Rk;
-    Rk = Rk1;
-    Rk1 = Rk2;
-    Rk2 = t;
-    iq = qk;
-    qk = qk1;
-    qk1 = qk2;
-    qk2 = nxt(qk2);
   }
-  if (!ok && fault != nullptr) atomicExch(fault, 1);
+  if (!m.ok && fault != nullptr) atomicExch(fault, 1);
 }
 
 template <typename T, bool ISO>
 static cudaError_t rb_sweep_t(const Dims& d, const double h[3], const void* pin, void* pout,
                               const void* fs, const DevState* st, int* fault, cudaStream_t s) {
-  using C = typename St<T>::C;
-  // 6 planes in the ring (3 in flight) keep 3 blocks of 512 threads per SM for FP32;
-  // deeper rings measured slower (fewer resident blocks)
-  constexpr int TY = 14, NS = 6;
-  using Gm = SweepGeom<T, TY, NS>;
-  auto kern = k_rb_sweep<T, ISO, TY, NS>;
+  // 8 warps of 4 rows (a 64 x 32 tile) and a 5-plane ring: two blocks per SM
+  constexpr int R = 4, NWC = 8, NS = 5;
+  using Gm = SweepGeom<T, R, NWC, NS>;
+  auto kern = k_rb_sweep<T, ISO, R, NWC, NS>;
   static int blocks_per_sm = 0;
   if (blocks_per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
@@ -305,18 +381,20 @@ static cudaError_t rb_sweep_t(const Dims& d, const double h[3], const void* pin,
     if (e != cudaSuccess) return e;
     blocks_per_sm = std::max(1, blocks_per_sm);
   }
-  const int dt = sizeof(T) == 8 ? DT_F64 : sizeof(T) == 4 ? DT_F32 : DT_BF16;
+  const int dt = sizeof(T) == 4 ? DT_F32 : DT_BF16;
   CUtensorMap mP, mF;
   if (!encode_level_map(&mP, dt, pin, d, Gm::WP, Gm::HP) || !encode_level_map(&mF, dt, fs, d, Gm::WP, Gm::HF))
     return cudaErrorInvalidValue;
-  const int gx = (d.nx - 1) / Gm::TX + 1, gy = (d.ny - 1) / TY + 1;
+  const int gx = (d.nx - 1) / Gm::TX + 1, gy = (d.ny - 1) / Gm::TY + 1;
   const int nk = d.nz - 1;
-  // one wave: as many z-chunks per tile column as keep every block resident
+  // one wave: as many z-chunks per tile column as keep every block resident;
+  // chunks hold an even number of planes (every chunk starts on an odd plane)
   const int slots = sm_count() * blocks_per_sm;
   const int nchunk = std::max(1, std::min(nk, slots / (gx * gy)));
-  const int zc = (nk + nchunk - 1) / nchunk;
+  int zc = (nk + nchunk - 1) / nchunk;
+  zc += zc & 1;
   const dim3 grid(gx, gy, (nk + zc - 1) / zc);
-  Coef<C> cf = make_coef<C>(d, h, 2);
+  const Coef<float> cf = make_coef<float>(d, h, 2);
   kern<<<grid, Gm::NTH, Gm::SMEM, s>>>(mP, mF, d, cf, (T*)pout, zc, st, fault);
   return cudaGetLastError();
 }

@@ -75,3 +75,13 @@ def multipole_boundary(n, order, q, origin, lmax, G, phi, lo=(0, 0, 0), hi=(1, 1
     o = (C.c_double * 3)(*origin)
     check(lib().ps_op_multipole_boundary(C.byref(g), order, qq, o, lmax, float(G), _p(phi), _s(stream)),
           "ps_op_multipole_boundary")
+
+
+def scale_to_fp32(x, e, out, stream=None):
+    """out = x * 2^e rounded to FP32 (the refinement residual's conversion);
+    x float64, out float32, both contiguous CUDA tensors of the same size."""
+    import torch
+    if x.dtype != torch.float64 or out.dtype != torch.float32 or x.numel() != out.numel():
+        raise ValueError("x must be float64 and out float32 of the same size")
+    check(lib().ps_op_scale_to_fp32(_p(x), x.numel(), int(e), _p(out), _s(stream)), "ps_op_scale_to_fp32")
+
