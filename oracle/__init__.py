@@ -11,8 +11,10 @@ Modules
 -------
 grid        grid conventions and the MG level hierarchy
 operators   7-point / 13-point Cartesian Laplacians, residuals
-spherical   variable-coefficient spherical Laplacian (Eq. 2)
-smoothers   multicolour Gauss-Seidel / SOR sweeps (Sec. 2.1.1), omega (Eqs. 3-5)
+spherical   variable-coefficient spherical Laplacian (Eq. 2), red-black SOR with
+            position-dependent weights (Eq. omega_n with Eq. local_rjac)
+smoothers   multicolour Gauss-Seidel / SOR sweeps (Sec. 2.1.1), omega (Eqs. 3-5,
+            the Chebyshev sequence of Eq. omega_n)
 transfer    full-weighting restriction and P = 8 R^T prolongation (Sec. 2.1.3)
 krylov      CG (Sec. 2.1.2) and right-Jacobi-preconditioned BiCGSTAB
 multigrid   V-cycle, MG solve, FP64 iterative-refinement driver

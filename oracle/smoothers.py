@@ -16,6 +16,12 @@ nodes of a colour may be updated from the same residual evaluation.
 
 Eqs. 3-5: omega_opt = 2 / (1 + sqrt(1 - rJ^2)),
 rJ = sum_a h_a^-2 cos(pi/N_a) / sum_a h_a^-2, omega_opt,a = 2 / (1 + pi/N).
+
+Eq. omega_n (Chebyshev acceleration, Sec. 2.1.1): omega_0 = 1,
+omega_1 = 1 / (1 - rJ^2 / 2), omega_{n+1} = 1 / (1 - rJ^2 omega_n / 4); the
+paper starts the sequence from n = 1.  The paper cites the red-black scheme in
+which the index advances once per colour pass (half sweep); that reading is
+taken here: pass n of a solve (n = 1, 2, ... over colour passes) uses omega_n.
 """
 from __future__ import annotations
 
@@ -41,19 +47,27 @@ def colour_mask(grid: CartGrid, colour: int, ncol: int) -> np.ndarray:
     return (s % ncol) == colour
 
 
+def sweep_colour(phi: np.ndarray, f: np.ndarray, grid: CartGrid, colour: int, omega: float,
+                 ncol: int | None = None) -> None:
+    """SOR update of the nodes of one colour, in place on phi's interior."""
+    if ncol is None:
+        ncol = ncolours(grid.order)
+    a_pp = diagonal(grid)
+    I = grid.interior
+    mask = colour_mask(grid, colour, ncol)
+    r = residual(phi, f, grid)[I]
+    inner = phi[I]
+    inner[mask] += omega * r[mask] / a_pp
+    phi[I] = inner
+
+
 def sweep(phi: np.ndarray, f: np.ndarray, grid: CartGrid, omega: float = 1.0,
           ncol: int | None = None) -> None:
     """One full multicolour GS/SOR step, in place on phi's interior."""
     if ncol is None:
         ncol = ncolours(grid.order)
-    a_pp = diagonal(grid)
-    I = grid.interior
     for c in range(ncol):
-        mask = colour_mask(grid, c, ncol)
-        r = residual(phi, f, grid)[I]
-        inner = phi[I]
-        inner[mask] += omega * r[mask] / a_pp
-        phi[I] = inner
+        sweep_colour(phi, f, grid, c, omega, ncol)
 
 
 def rjac_uniform(grid: CartGrid) -> float:
@@ -71,3 +85,24 @@ def omega_opt(rj: float) -> float:
 def omega_opt_a(n: int) -> float:
     """Eq. 5 (large-N approximation)."""
     return 2.0 / (1.0 + math.pi / n)
+
+
+def omega_next(rj: float, omega_n: float) -> float:
+    """Eq. omega_n: omega_{n+1} from omega_n."""
+    return 1.0 / (1.0 - rj * rj * omega_n / 4.0)
+
+
+def omega_first(rj: float) -> float:
+    """Eq. omega_n: omega_1."""
+    return 1.0 / (1.0 - rj * rj / 2.0)
+
+
+def omega_sequence(rj: float, count: int) -> list:
+    """omega_1 .. omega_count of Eq. omega_n (the sequence the paper uses)."""
+    out = []
+    w = omega_first(rj)
+    for _ in range(count):
+        out.append(w)
+        w = omega_next(rj, w)
+    return out
+

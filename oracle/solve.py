@@ -19,8 +19,9 @@ import numpy as np
 from . import multigrid, multipole
 from .grid import CartGrid
 from .operators import norm2, reference_norm, residual
-from .smoothers import sweep
-from .spherical import SphericalOperator, bicgstab_solve
+from .smoothers import (ncolours, omega_first, omega_next, omega_opt, rjac_uniform, sweep,
+                        sweep_colour)
+from .spherical import SphericalOperator, bicgstab_solve, sor_solve_spherical
 
 
 @dataclass
@@ -33,15 +34,31 @@ class SolveInfo:
     moments: np.ndarray | None = None
 
 
-def sor_solve(phi, f, grid: CartGrid, omega: float, tol: float, max_iter: int):
+def sor_solve(phi, f, grid: CartGrid, omega: float, tol: float, max_iter: int,
+              schedule: str = "fixed"):
+    """SOR steps (Sec. 2.1.1) until the relative residual reaches tol.
+    schedule: "fixed" (the given omega), "opt" (Eq. 3 with rJ of Eq. 4) or
+    "chebyshev" (omega_n of Eq. omega_n from n = 1, one n per colour pass)."""
     ref = reference_norm(phi, f, grid)
     if ref == 0.0:
         ref = 1.0
     hist = [norm2(residual(phi, f, grid), grid) / ref]
     if hist[-1] <= tol:
         return 0, True, hist
+    ncol = ncolours(grid.order)
+    rj = rjac_uniform(grid)
+    w = omega_first(rj)
     for it in range(1, max_iter + 1):
-        sweep(phi, f, grid, omega)
+        if schedule == "fixed":
+            sweep(phi, f, grid, omega)
+        elif schedule == "opt":
+            sweep(phi, f, grid, omega_opt(rj))
+        elif schedule == "chebyshev":
+            for c in range(ncol):
+                sweep_colour(phi, f, grid, c, w, ncol)
+                w = omega_next(rj, w)
+        else:
+            raise ValueError(schedule)
         hist.append(norm2(residual(phi, f, grid), grid) / ref)
         if hist[-1] <= tol:
             return it, True, hist
@@ -51,7 +68,7 @@ def sor_solve(phi, f, grid: CartGrid, omega: float, tol: float, max_iter: int):
 def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: str, tol: float,
                     max_iter: int = 10000, G: float = 1.0, bc: str = "dirichlet", lmax: int = 4,
                     origin=None, omega: float = 1.0, nu1: int = 2, nu2: int = 2,
-                    inner: int = 1) -> SolveInfo:
+                    inner: int = 1, sor_schedule: str = "fixed") -> SolveInfo:
     """method in {"sor", "cg", "mg", "ir"}; phi is updated in place."""
     f = 4.0 * math.pi * G * rho
     q = None
@@ -61,7 +78,7 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
         q = multipole.moments_cartesian(rho, grid, origin, lmax)
         multipole.apply_cartesian_bc(phi, grid, q, origin, lmax, G)
     if method == "sor":
-        it, conv, hist = sor_solve(phi, f, grid, omega, tol, max_iter)
+        it, conv, hist = sor_solve(phi, f, grid, omega, tol, max_iter, sor_schedule)
     elif method == "cg":
         res = multigrid.cg_on_grid(phi, f, grid, tol, max_iter)
         it, conv, hist = res.iterations, res.converged, res.history
@@ -76,14 +93,19 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
 
 def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
                     max_iter: int = 20000, G: float = 1.0, bc: str = "multipole",
-                    lmax: int = 6, exact_dots: bool = False) -> SolveInfo:
-    """Right-Jacobi BiCGSTAB on the spherical grid; phi in the ghosted layout."""
+                    lmax: int = 6, exact_dots: bool = False, method: str = "bicgstab",
+                    omega: float = 1.0, sor_schedule: str = "chebyshev") -> SolveInfo:
+    """Right-Jacobi BiCGSTAB (or red-black SOR) on the spherical grid; phi in
+    the ghosted layout."""
     op = SphericalOperator(r, th, ph)
     f = 4.0 * math.pi * G * rho
     q = None
     if bc == "multipole":
         q = multipole.moments_spherical(rho, r, th, ph, lmax)
         phi[1:-1, 1:-1, -1] = multipole.spherical_outer_ghost(q, r, th, ph, lmax, G)
+    if method == "sor":
+        it, conv, hist = sor_solve_spherical(phi, f, op, tol, max_iter, sor_schedule, omega)
+        return SolveInfo(it, conv, hist[-1], multigrid.convergence_factor(hist), hist, q)
     from . import krylov
     res = bicgstab_solve(phi, f, op, tol, max_iter,
                          dot=krylov.exact_dot if exact_dots else krylov.numpy_dot)

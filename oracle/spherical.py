@@ -114,3 +114,87 @@ def bicgstab_solve(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator, tol
                           dot=dot)
     Pfield[U] = res.x.reshape(shp)
     return res
+
+
+# ------------------------------------------------------------------ red-black SOR
+# Sec. 2.1.1: the spherical implementation is red-black SOR whose weights depend
+# on position: the sequence of Eq. omega_n (from n = 1, one n per colour pass)
+# is run per node with the local Jacobi spectral radius of Eq. local_rjac,
+#   rJ = [cos(pi/Nr) dr^-2 + cos(pi/Nt) (r dt)^-2 + cos(pi/Np) (r sin t dp)^-2]
+#        / [dr^-2 + (r dt)^-2 + (r sin t dp)^-2].
+# Readings: N_r, N_theta, N_phi are the numbers of unknown nodes per axis; dr_i
+# is the width the flux form divides by, (r_{i+1} - r_{i-1}) / 2 with the
+# operator's ghost radii; dt and dp are the uniform angular spacings.  The
+# colour of node (i, j, k) is (i + j + k) mod 2: the mirror ghost P_{-1} = P_1
+# and the periodic ghosts (Nphi even) take their values from nodes of the other
+# colour, so the nodes of one colour never couple.
+
+def rjac_local(dr, r, dt, sin_t, dp, nr: int, nt: int, nph: int):
+    """Eq. local_rjac for broadcastable arrays of the local spacings."""
+    wr = 1.0 / np.asarray(dr, dtype=np.float64) ** 2
+    wt = 1.0 / (np.asarray(r, dtype=np.float64) * dt) ** 2
+    wp = 1.0 / (np.asarray(r, dtype=np.float64) * np.asarray(sin_t, dtype=np.float64) * dp) ** 2
+    num = math.cos(math.pi / nr) * wr + math.cos(math.pi / nt) * wt + math.cos(math.pi / nph) * wp
+    return num / (wr + wt + wp)
+
+
+def local_rjac_table(op: SphericalOperator) -> np.ndarray:
+    """rJ of every (theta_j, r_i), shape (Ntheta, Nr)."""
+    re = op.re
+    dr = 0.5 * (re[2:] - re[:-2])
+    return rjac_local(dr[None, :], op.r[None, :], op.dth, op.sin_c[:, None], op.dph,
+                      op.nr, op.nt, op.np_)
+
+
+def sor_colour(P: np.ndarray, f: np.ndarray, op: SphericalOperator, colour: int, omega) -> None:
+    """P += omega (f - L P) / diag on the unknown nodes of one colour (in place);
+    omega is a scalar or an (Ntheta, Nr) array."""
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    r = f[U] - op.apply(P)
+    k = np.arange(op.np_)[:, None, None]
+    j = np.arange(op.nt)[None, :, None]
+    i = np.arange(op.nr)[None, None, :]
+    mask = ((i + j + k) % 2) == colour
+    w = np.broadcast_to(np.asarray(omega, dtype=np.float64), (op.nt, op.nr))[None, :, :]
+    inner = P[U]
+    upd = w * r / op.diagonal()
+    inner[mask] += upd[mask]
+    P[U] = inner
+
+
+def sor_solve_spherical(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator, tol: float,
+                        max_iter: int, schedule: str = "chebyshev", omega: float = 1.0):
+    """Red-black SOR steps until ||f - L P|| <= tol ||b||, b = f - L(boundary part
+    of P) as for BiCGSTAB.  schedule: "fixed" (omega), "opt" (Eq. 3 with the local
+    rJ) or "chebyshev" (Eq. omega_n with the local rJ).  Returns (steps,
+    converged, relative-residual history)."""
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    bdry = np.zeros(op.shape)
+    bdry[:, :, -1] = Pfield[:, :, -1]
+    b = f[U] - op.apply(bdry)
+    ref = float(np.sqrt(np.sum(b * b)))
+    if ref == 0.0:
+        ref = 1.0
+    rel = lambda: float(np.sqrt(np.sum((f[U] - op.apply(Pfield)) ** 2))) / ref
+    hist = [rel()]
+    if hist[-1] <= tol:
+        return 0, True, hist
+    rj = local_rjac_table(op)
+    w = 1.0 / (1.0 - rj * rj / 2.0)             # omega_1
+    wopt = 2.0 / (1.0 + np.sqrt(1.0 - rj * rj))  # Eq. 3
+    for it in range(1, max_iter + 1):
+        for c in (0, 1):
+            if schedule == "chebyshev":
+                sor_colour(Pfield, f, op, c, w)
+                w = 1.0 / (1.0 - rj * rj * w / 4.0)
+            elif schedule == "opt":
+                sor_colour(Pfield, f, op, c, wopt)
+            elif schedule == "fixed":
+                sor_colour(Pfield, f, op, c, omega)
+            else:
+                raise ValueError(schedule)
+        hist.append(rel())
+        if hist[-1] <= tol:
+            return it, True, hist
+    return max_iter, False, hist
+

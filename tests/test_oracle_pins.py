@@ -571,3 +571,134 @@ def test_lognormal_generator_statistics():
     assert abs(np.std(np.log(core)) - 1.0) < 1e-12
     assert abs(np.mean(np.log(core)) + 0.5) < 1e-12
     np.testing.assert_array_equal(rho[1], rho[-2])   # node N repeats node 0
+
+
+# ------------------------------------------------------------------ SOR schedules
+
+def test_omega_sequence_is_chebyshev_and_tends_to_eq3():
+    """Eq. omega_n: the recurrence equals the Chebyshev form
+    omega_n = 2 T_n(1/rJ) / (rJ T_{n+1}(1/rJ)) (numpy's Chebyshev series), falls
+    monotonically from omega_1 and tends to omega_opt of Eq. 3 from above."""
+    from numpy.polynomial import chebyshev as Ch
+    for rj in (0.5, 0.9, math.cos(math.pi / 16), math.cos(math.pi / 64)):
+        seq = SM.omega_sequence(rj, 6000)
+        x = 1.0 / rj
+        for n in (1, 2, 3, 7, 20):
+            tn = Ch.chebval(x, [0] * n + [1])
+            tn1 = Ch.chebval(x, [0] * (n + 1) + [1])
+            assert abs(seq[n - 1] - 2 * tn / (rj * tn1)) < 1e-12 * seq[n - 1]
+        assert all(b <= a for a, b in zip(seq[:50], seq[1:51])) and seq[1] < seq[0]
+        assert abs(seq[-1] - SM.omega_opt(rj)) < 1e-12
+        assert min(seq) >= SM.omega_opt(rj) - 1e-14
+
+
+def test_rjac_uniform_is_the_jacobi_spectral_radius():
+    """Eq. 4 is the spectral radius of the Jacobi iteration I - D^-1 A of the
+    7-point Dirichlet Laplacian: dense eigenvalues on an anisotropic grid."""
+    n = (6, 8, 10)
+    g = cart_grid(n, lo=(0, 0, 0), hi=(1.0, 0.7, 1.6))
+    Ds = [_lap1d(n[a], g.h[a], 2) for a in range(3)]
+    I = [np.eye(n[a] - 1) for a in range(3)]
+    A = (np.kron(I[2], np.kron(I[1], Ds[0])) + np.kron(I[2], np.kron(Ds[1], I[0]))
+         + np.kron(Ds[2], np.kron(I[1], I[0])))
+    J = np.eye(A.shape[0]) - A / np.diag(A)[:, None]
+    rho = np.max(np.abs(np.linalg.eigvals(J)))
+    assert abs(rho - SM.rjac_uniform(g)) < 1e-12
+
+
+def test_rjac_local_special_cases():
+    """Eq. local_rjac: equal physical spacings and extents give cos(pi/N); a
+    dominant phi term gives cos(pi/N_phi); with the metric factors omitted it is
+    Eq. 4 of a Cartesian grid."""
+    N = 24
+    r, dt = 2.0, 0.1
+    rj = SP.rjac_local(r * dt, r, dt, 1.0, dt, N, N, N)
+    assert abs(rj - math.cos(math.pi / N)) < 1e-15
+    rj = SP.rjac_local(1.0, 1.0, 1.0, 1e-6, 1.0, 10, 20, 40)
+    assert abs(rj - math.cos(math.pi / 40)) < 1e-9
+    g = cart_grid((16, 32, 64), lo=(0, 0, 0), hi=(1.0, 0.5, 2.0))
+    rj = SP.rjac_local(g.h[0], 1.0, g.h[1], 1.0, g.h[2], 16, 32, 64)
+    assert abs(rj - SM.rjac_uniform(g)) < 1e-15
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("schedule", ["chebyshev", "opt"])
+def test_sor_schedules_reach_dense_solution(order, schedule):
+    """Chebyshev and Eq. 3 weights converge to numpy.linalg.solve's solution and
+    need fewer steps than Gauss-Seidel."""
+    n = 8
+    g = cart_grid(n, order)
+    gen = W.rng(12)
+    rho = np.zeros(g.shape)
+    rho[g.interior] = gen.standard_normal(rho[g.interior].shape)
+    x = np.linalg.solve(_dense_matrix(n, order), (4 * math.pi * rho[g.interior]).ravel())
+    phi = g.zeros()
+    info = S.solve_cartesian(rho, phi, g, "sor", 1e-13, max_iter=5000, sor_schedule=schedule)
+    assert info.converged
+    got = phi[g.interior].ravel()
+    assert np.max(np.abs(got - x)) / np.max(np.abs(x)) < 1e-11
+    gs = S.solve_cartesian(rho, g.zeros(), g, "sor", 1e-13, max_iter=5000, omega=1.0)
+    assert info.iterations < gs.iterations
+
+
+def _sph_dense(op):
+    nunk = op.nr * op.nt * op.np_
+    A = np.zeros((nunk, nunk))
+    for c in range(nunk):
+        e = np.zeros(op.shape)
+        e[1:-1, 1:-1, 1:-1].flat[c] = 1.0
+        A[:, c] = op.apply(e).ravel()
+    return A
+
+
+@pytest.mark.parametrize("schedule", ["chebyshev", "opt", "fixed"])
+def test_spherical_sor_matches_dense_solve(schedule):
+    r, th, ph = W.spherical_coords(6, 6, 8, 0.1, 1.0)
+    op = SP.SphericalOperator(r, th, ph)
+    A = _sph_dense(op)
+    rho = W.spherical_density(r, th, ph)
+    f = 4 * math.pi * rho
+    bd = np.zeros(op.shape)
+    bd[:, :, -1] = -1.0
+    x = np.linalg.solve(A, f[1:-1, 1:-1, 1:-1].ravel() - op.apply(bd).ravel())
+    phi = np.zeros(op.shape)
+    phi[:, :, -1] = -1.0
+    it, conv, hist = SP.sor_solve_spherical(phi, f, op, 1e-13, 20000, schedule, omega=1.0)
+    assert conv
+    np.testing.assert_allclose(phi[1:-1, 1:-1, 1:-1].ravel(), x, rtol=1e-10)
+
+
+def test_spherical_colour_pass_is_sequential_gauss_seidel():
+    """With omega = 1 one colour pass equals node-by-node Gauss-Seidel over the
+    nodes of that colour in any order (the mirror and periodic ghosts couple
+    only nodes of different colours): brute force with the dense matrix."""
+    r, th, ph = W.spherical_coords(6, 4, 8, 0.2, 1.0)
+    op = SP.SphericalOperator(r, th, ph)
+    A = _sph_dense(op)
+    gen = W.rng(5)
+    f = np.zeros(op.shape)
+    f[1:-1, 1:-1, 1:-1] = gen.standard_normal((8, 4, 6))
+    P = np.zeros(op.shape)
+    P[1:-1, 1:-1, 1:-1] = gen.standard_normal((8, 4, 6))
+    x = P[1:-1, 1:-1, 1:-1].ravel().copy()      # zero outer ghost: L P = A x
+    b = f[1:-1, 1:-1, 1:-1].ravel()
+    k, j, i = np.unravel_index(np.arange(x.size), (8, 4, 6))
+    for c in (0, 1):
+        idx = np.nonzero((i + j + k) % 2 == c)[0]
+        for p in gen.permutation(idx):
+            x[p] += (b[p] - A[p] @ x) / A[p, p]
+        SP.sor_colour(P, f, op, c, 1.0)
+    np.testing.assert_allclose(P[1:-1, 1:-1, 1:-1].ravel(), x, rtol=1e-12, atol=1e-12)
+
+
+def test_spherical_local_chebyshev_beats_gauss_seidel():
+    r, th, ph = W.spherical_coords(16, 8, 16, 0.1, 1.0)
+    op = SP.SphericalOperator(r, th, ph)
+    rho = W.spherical_density(r, th, ph)
+    f = 4 * math.pi * rho
+    runs = {}
+    for sched in ("chebyshev", "fixed"):
+        phi = np.zeros(op.shape)
+        phi[:, :, -1] = -1.0
+        runs[sched] = SP.sor_solve_spherical(phi, f, op, 1e-8, 20000, sched, omega=1.0)[0]
+    assert runs["chebyshev"] < runs["fixed"] / 2
