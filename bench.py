@@ -232,11 +232,13 @@ def run_serving(args, rank, world):
 def other_configs(dev, reps=3):
     """Time-to-tolerance of the other workloads, each through the public API on
     device-resident inputs (median of `reps` solves after one warm-up):
-      config 1: 32^3 uniform sphere, analytic Dirichlet boundary, SOR (omega 1.8) and CG to 1e-10;
+      config 1: 32^3 uniform sphere, analytic Dirichlet boundary, SOR (omega 1.8, the Chebyshev
+                weights of Eq. omega_n and omega_opt of Eq. 3) and CG to 1e-10;
       config 3: 512^3 lognormal density, 13-point, multipole l_max = 8, MG to 1e-10 in FP64 and
                 in the FP32-smoothing / BF16-finest refinement mode;
       config 4: 256 x 128 x 256 spherical grid, multipole l_max = 6, Jacobi-BiCGSTAB in FP64 to 1e-8
-                (the exact solution rounded to FP64 sits near 1e-9 on this grid)."""
+                (the exact solution rounded to FP64 sits near 1e-9 on this grid), and red-black
+                SOR with per-node Chebyshev weights from the local rJ of Eq. local_rjac."""
     import torch
     import workloads as W
     import paper_2605_03563_gb300 as P
@@ -260,14 +262,16 @@ def other_configs(dev, reps=3):
     phi0 = torch.from_numpy(phi0_np).to(dev)
     c1 = {}
     with P.CartesianSolver(32) as s:
-        for method, omega in (("sor", 1.8), ("cg", 1.0)):
+        for name, method, omega, sched in (("sor", "sor", 1.8, "fixed"), ("sor_chebyshev", "sor", 1.0, "chebyshev"),
+                                           ("sor_optimal", "sor", 1.0, "optimal"), ("cg", "cg", 1.0, "fixed")):
             phi = phi0.clone()
 
             def run():
                 phi.copy_(phi0)
-                return s.solve(rho1, phi, tol=1e-10, method=method, omega=omega, max_iter=20000)
+                return s.solve(rho1, phi, tol=1e-10, method=method, omega=omega, max_iter=20000,
+                               sor_schedule=sched)
             ms, info = timed(run, 10)
-            c1[method] = {"time_to_1e-10_ms": ms, "iterations": info.iterations,
+            c1[name] = {"time_to_1e-10_ms": ms, "iterations": info.iterations,
                           "rel_residual": info.rel_residual, "converged": info.converged,
                           "glups_per_step": 31 ** 3 * info.iterations / (ms / 1e3) / 1e9}
     out["config1_32_sphere_sor_cg"] = c1
@@ -316,6 +320,15 @@ def other_configs(dev, reps=3):
             "rel_residual": info.rel_residual, "t_mp_ms": info.t_mp_ms,
             "ms_per_iteration": ms / max(info.iterations, 1),
             "glups_per_iteration": nunk * info.iterations / (ms / 1e3) / 1e9}
+
+        def run_sor():
+            phi.zero_()
+            return s.solve(rho4, phi, tol=1e-8, max_iter=40000, method="sor", sor_schedule="chebyshev")
+        ms, info = timed(run_sor, 1)
+        out["config4_spherical_sor_chebyshev_fp64"] = {
+            "time_to_1e-8_ms": ms, "iterations": info.iterations, "converged": info.converged,
+            "rel_residual": info.rel_residual, "ms_per_step": ms / max(info.iterations, 1),
+            "glups_per_step": nunk * info.iterations / (ms / 1e3) / 1e9}
     return out
 
 

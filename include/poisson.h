@@ -108,8 +108,21 @@ typedef struct {
                             operator, fused residual + restriction); 0 = library default (16),
                             < 0 = never.  Results are bitwise the same either way.  FP64 levels
                             always use the per-colour passes. */
-  int32_t reserved_;     /* set to 0 */
+  int32_t sor_schedule;  /* PS_SOR weights (ps_sor_schedule): the given omega, the Chebyshev
+                            sequence of Eq. omega_n, or omega_opt of Eq. 3; 0 = given omega */
 } ps_solve_opts;
+
+/* SOR weights (Sec. 2.1.1).  rJ is the Jacobi spectral radius estimate: Eq. 4
+ * on Cartesian grids (interval counts and spacings of the grid), the local
+ * Eq. local_rjac on spherical grids (unknown-node counts per axis, the radial
+ * width (r_{i+1} - r_{i-1})/2 of the flux form, r_i dtheta, r_i sin(theta_j)
+ * dphi), which makes the weights position-dependent there.
+ *   PS_SOR_FIXED      ps_solve_opts.omega everywhere;
+ *   PS_SOR_CHEBYSHEV  omega_1 = 1/(1 - rJ^2/2), omega_{n+1} = 1/(1 - rJ^2 omega_n/4)
+ *                     (Eq. omega_n from n = 1), n advancing once per colour pass;
+ *   PS_SOR_OPTIMAL    omega_opt = 2/(1 + sqrt(1 - rJ^2)) (Eq. 3).
+ * ps_solve_opts.omega is ignored by the last two. */
+typedef enum { PS_SOR_FIXED = 0, PS_SOR_CHEBYSHEV = 1, PS_SOR_OPTIMAL = 2 } ps_sor_schedule;
 
 typedef struct {
   int32_t iterations;        /* steps taken (V-cycles, Krylov iterations, SOR steps, IR steps) */

@@ -20,6 +20,8 @@ __all__ = ["CartesianSolver", "SphericalSolver", "SolveInfo", "ops", "capi", "wo
 
 METHODS = {"sor": capi.PS_SOR, "cg": capi.PS_CG, "mg": capi.PS_MG, "bicgstab": capi.PS_BICGSTAB}
 PRECISIONS = {"fp64": capi.PS_FP64, "mixed_fp32": capi.PS_MIXED_FP32, "mixed_bf16": capi.PS_MIXED_BF16}
+# SOR weights: the given omega, Eq. omega_n's Chebyshev sequence, omega_opt of Eq. 3
+SOR_SCHEDULES = {"fixed": 0, "chebyshev": 1, "optimal": 2}
 
 
 @dataclass
@@ -112,11 +114,11 @@ class _Handle:
 
     # ---- asynchronous, steppable solves (continuous batching)
     def begin(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
-              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0):
+              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0, sor_schedule="fixed"):
         """Start a solve whose state stays on the device; rho/phi must stay alive until end()."""
         self._opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
                                       int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
-                                      int(tile_min_n))
+                                      int(tile_min_n), SOR_SCHEDULES[sor_schedule])
         self._keep = (rho, phi)
         check(lib().poisson_solve_begin(self._h, _ptr(rho), _ptr(phi), float(tol),
                                         C.byref(self._opts)), "poisson_solve_begin")
@@ -142,10 +144,10 @@ class _Handle:
         return SolveInfo.from_c(info, min(nmom, 81))
 
     def _solve(self, rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-               stream, nmom, tile_min_n=0):
+               stream, nmom, tile_min_n=0, sor_schedule="fixed"):
         opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
                                 int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
-                                int(tile_min_n))
+                                int(tile_min_n), SOR_SCHEDULES[sor_schedule])
         info = capi.PsInfo()
         st = lib().poisson_solve(self._h, _ptr(rho), _ptr(phi), float(tol), C.byref(opts),
                                  C.byref(info))
@@ -180,12 +182,15 @@ class CartesianSolver(_Handle):
         return (nz + 2 * g - 1, ny + 2 * g - 1, nx + 2 * g - 1)
 
     def solve(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
-              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0) -> SolveInfo:
+              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0,
+              sor_schedule="fixed") -> SolveInfo:
         """tile_min_n: levels with at least this many intervals per axis use the TMA tile
-        kernels (0 = library default, negative = never); results are bitwise identical."""
+        kernels (0 = library default, negative = never); results are bitwise identical.
+        sor_schedule (method "sor"): "fixed" (omega), "chebyshev" (Eq. omega_n) or
+        "optimal" (Eq. 3), the last two with rJ of Eq. 4."""
         nmom = (self.lmax + 1) ** 2 if self.multipole else 0
         return self._solve(rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-                           stream, min(nmom, 81), tile_min_n)
+                           stream, min(nmom, 81), tile_min_n, sor_schedule)
 
 
 class SphericalSolver(_Handle):
@@ -213,10 +218,13 @@ class SphericalSolver(_Handle):
         return (np_ + 2, nt + 2, nr + 2)
 
     def solve(self, rho, phi, tol=1e-10, prec="fp64", max_iter=20000, inner_cycles=0,
-              stream=None) -> SolveInfo:
+              stream=None, method="bicgstab", omega=1.0, sor_schedule="chebyshev") -> SolveInfo:
+        """method "bicgstab" (right-Jacobi BiCGSTAB) or "sor" (red-black SOR, FP64, with
+        sor_schedule "fixed" (omega), "chebyshev" (Eq. omega_n) or "optimal" (Eq. 3), the
+        last two per node with the local rJ of Eq. local_rjac)."""
         nmom = (self.lmax + 1) ** 2 if self.multipole else 0
-        return self._solve(rho, phi, tol, "bicgstab", prec, 1.0, 0, 0, max_iter, inner_cycles,
-                           stream, min(nmom, 81))
+        return self._solve(rho, phi, tol, method, prec, omega, 0, 0, max_iter, inner_cycles,
+                           stream, min(nmom, 81), 0, sor_schedule)
 
     def apply(self, phi, out, stream=None):
         check(lib().ps_op_spherical_apply(self._h, _ptr(phi), _ptr(out), _stream(stream)),

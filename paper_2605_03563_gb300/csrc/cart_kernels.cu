@@ -347,11 +347,16 @@ cudaError_t launch_delta_after_sweep(const Dims& d, int order, const double h[3]
 template <int G, bool ISO, typename T, bool OM1>
 __global__ void __launch_bounds__(BX* BY)
     k_sweep(Dims d, Coef<typename St<T>::C> cf, T* __restrict__ phi, const T* __restrict__ fs,
-            int colour, typename St<T>::C omega, const DevState* __restrict__ st) {
+            int colour, typename St<T>::C omega, const DevState* __restrict__ st,
+            const double* __restrict__ wtab, int wlen) {
   using C = typename St<T>::C;
   using S = St<T>;
   constexpr int NCOL = G == 1 ? 2 : 3;
   if (st != nullptr && st->done) return;
+  // scheduled weights: colour pass n = NCOL * (completed steps) + colour of the
+  // solve takes wtab[n] (the sequence of Eq. omega_n from n = 1), its last entry
+  // once the sequence has reached its limit
+  if (!OM1 && wtab != nullptr && st != nullptr) omega = (C)wtab[min(st->iter * NCOL + colour, wlen - 1)];
   const int t = blockIdx.x * BX + threadIdx.x;
   const int jn = blockIdx.y * BY + threadIdx.y + 1;
   if (jn > d.nj()) return;
@@ -415,7 +420,8 @@ __global__ void __launch_bounds__(BX* BY)
 
 template <int G, bool ISO, typename T>
 static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* phi, const void* fs,
-                           int colour, double omega, const DevState* st, cudaStream_t s) {
+                           int colour, double omega, const DevState* st, const double* wtab, int wlen,
+                           cudaStream_t s) {
   using C = typename St<T>::C;
   constexpr int NCOL = G == 1 ? 2 : 3;
   Coef<C> cf = make_coef<C>(d, h, order);
@@ -423,31 +429,32 @@ static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* ph
   const int gx = (per_row + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY;
   const int zc = zchunk_for(gx * gy, d.nk());
   dim3 grid(gx, gy, (d.nk() + zc - 1) / zc);
-  if (omega == 1.0)
-    k_sweep<G, ISO, T, true><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st);
+  if (omega == 1.0 && wtab == nullptr)
+    k_sweep<G, ISO, T, true><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st, nullptr, 0);
   else
-    k_sweep<G, ISO, T, false><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st);
+    k_sweep<G, ISO, T, false><<<grid, dim3(BX, BY), 0, s>>>(d, cf, (T*)phi, (const T*)fs, colour, (C)omega, st, wtab, wlen);
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t sweep_dispatch(const Dims& d, int order, const double h[3], void* phi,
                                   const void* fs, int colour, double omega, const DevState* st,
-                                  cudaStream_t s) {
+                                  const double* wtab, int wlen, cudaStream_t s) {
   bool iso = is_iso(h);
   if (order == 2)
-    return iso ? sweep_t<1, true, T>(d, h, order, phi, fs, colour, omega, st, s)
-               : sweep_t<1, false, T>(d, h, order, phi, fs, colour, omega, st, s);
-  return iso ? sweep_t<2, true, T>(d, h, order, phi, fs, colour, omega, st, s)
-             : sweep_t<2, false, T>(d, h, order, phi, fs, colour, omega, st, s);
+    return iso ? sweep_t<1, true, T>(d, h, order, phi, fs, colour, omega, st, wtab, wlen, s)
+               : sweep_t<1, false, T>(d, h, order, phi, fs, colour, omega, st, wtab, wlen, s);
+  return iso ? sweep_t<2, true, T>(d, h, order, phi, fs, colour, omega, st, wtab, wlen, s)
+             : sweep_t<2, false, T>(d, h, order, phi, fs, colour, omega, st, wtab, wlen, s);
 }
 
 cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int dt, void* phi,
                                 const void* fs, int colour, double omega, const DevState* st,
-                                cudaStream_t s) {
-  if (dt == DT_F64) return sweep_dispatch<double>(d, order, h, phi, fs, colour, omega, st, s);
-  if (dt == DT_F32) return sweep_dispatch<float>(d, order, h, phi, fs, colour, omega, st, s);
-  return sweep_dispatch<__nv_bfloat16>(d, order, h, phi, fs, colour, omega, st, s);
+                                cudaStream_t s, const double* wtab, int wlen) {
+  if (wtab != nullptr && (st == nullptr || wlen < 1)) return cudaErrorInvalidValue;
+  if (dt == DT_F64) return sweep_dispatch<double>(d, order, h, phi, fs, colour, omega, st, wtab, wlen, s);
+  if (dt == DT_F32) return sweep_dispatch<float>(d, order, h, phi, fs, colour, omega, st, wtab, wlen, s);
+  return sweep_dispatch<__nv_bfloat16>(d, order, h, phi, fs, colour, omega, st, wtab, wlen, s);
 }
 
 // ------------------------------------------------------------------ restriction

@@ -38,9 +38,11 @@ cudaError_t launch_delta_after_sweep(const Dims& d, int order, const double h[3]
                                      const void* fs, int dout, void* out, cudaStream_t s);
 
 // One colour pass of the multicolour GS/SOR sweep (skipped once st->done, if st given).
+// With wtab (wlen >= 1 entries, st required) the pass's weight is
+// wtab[min(ncolours * st->iter + colour, wlen - 1)] instead of omega.
 cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int dt, void* phi,
                                 const void* fs, int colour, double omega, const DevState* st,
-                                cudaStream_t s);
+                                cudaStream_t s, const double* wtab = nullptr, int wlen = 0);
 
 // fs = factor * f on interior nodes, both of storage dt
 cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,

@@ -159,6 +159,10 @@ struct ps_ctx {
   void* sv[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int sv_dt = -1;
   double* sz = nullptr;   // BiCGSTAB group-wise increments of the iterate (FP64)
+  double* sph_w = nullptr;   // spherical SOR weights, two buffers of Ntheta * Nr
+  // Cartesian SOR: weights of the Chebyshev sequence, one per colour pass
+  double* sor_wtab = nullptr;
+  int sor_wlen = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   size_t bytes = 0;
   // profiler
@@ -345,15 +349,16 @@ Work work_of(const Level& L, int order) {
   return w;
 }
 
-cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState* st, cudaStream_t s) {
+cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState* st, cudaStream_t s,
+                        const double* wtab = nullptr, int wlen = 0) {
   const int ncol = h->order == 2 ? 2 : 3;
   const Work w = work_of(L, h->order);
   cudaError_t e;
   for (int c = 0; c < ncol; c++) {
     // one colour pass reads phi everywhere, fs and phi on its colour, writes phi on its colour
     prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, w.n * w.S * (1.0 + 2.0 / ncol),
-               w.n / ncol * (6.0 * w.G + (omega != 1.0 ? 2.0 : 0.0)), w.fp64, s);
-    e = (h->nlaunch += 1, launch_sweep_colour(L.d, h->order, L.h, L.dt, L.phi, L.fs, c, omega, st, s));
+               w.n / ncol * (6.0 * w.G + (omega != 1.0 || wtab ? 2.0 : 0.0)), w.fp64, s);
+    e = (h->nlaunch += 1, launch_sweep_colour(L.d, h->order, L.h, L.dt, L.phi, L.fs, c, omega, st, s, wtab, wlen));
     prof_end(h, s);
     if (e != cudaSuccess) return e;
   }
@@ -595,6 +600,37 @@ ps_status begin_ir(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   return PS_OK;
 }
 
+// Eq. 4: Jacobi spectral radius of the Cartesian grid (interval counts and spacings).
+double rjac_cartesian(const ps_ctx* h) {
+  const int n[3] = {h->d0.nx, h->d0.ny, h->d0.nz};
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < 3; a++) {
+    const double w = 1.0 / (h->h0[a] * h->h0[a]);
+    num += std::cos(M_PI / n[a]) * w;
+    den += w;
+  }
+  return num / den;
+}
+
+// Weights of Eq. omega_n from n = 1 until the sequence stops changing in FP64
+// (or 65536 entries), one per colour pass; the kernels keep the last entry.
+ps_status sor_chebyshev_table(ps_ctx* h, double rj) {
+  if (h->sor_wtab) return PS_OK;   // fixed by the grid
+  std::vector<double> w;
+  double v = 1.0 / (1.0 - rj * rj / 2.0);
+  for (int n = 0; n < 65536; n++) {
+    w.push_back(v);
+    const double nv = 1.0 / (1.0 - rj * rj * v / 4.0);
+    if (nv == v) break;
+    v = nv;
+  }
+  ps_status r = alloc_zero((void**)&h->sor_wtab, w.size() * sizeof(double), &h->bytes);
+  if (r != PS_OK) return r;
+  TRY(cudaMemcpy(h->sor_wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  h->sor_wlen = (int)w.size();
+  return PS_OK;
+}
+
 ps_status begin_sor(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   double* phi = h->phi0;
   TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
@@ -603,14 +639,25 @@ ps_status begin_sor(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   for (int a = 0; a < 3; a++) L0.h[a] = h->h0[a];
   L0.phi = phi;
   L0.fs = h->fs64;
-  const double omega = o->omega;
-  h->act.body = [h, L0, phi, omega](unsigned long long cond, int chunk, cudaStream_t q) mutable -> cudaError_t {
-    cudaError_t e = sweep_level(h, L0, 0, omega, h->st, q);
+  const double rj = rjac_cartesian(h);
+  double omega = o->omega;
+  if (o->sor_schedule == PS_SOR_OPTIMAL) omega = 2.0 / (1.0 + std::sqrt(1.0 - rj * rj));
+  const double* wtab = nullptr;
+  int wlen = 0;
+  if (o->sor_schedule == PS_SOR_CHEBYSHEV) {
+    ps_status r = sor_chebyshev_table(h, rj);
+    if (r != PS_OK) return r;
+    wtab = h->sor_wtab;
+    wlen = h->sor_wlen;
+  }
+  h->act.body = [h, L0, phi, omega, wtab, wlen](unsigned long long cond, int chunk, cudaStream_t q) mutable -> cudaError_t {
+    cudaError_t e = sweep_level(h, L0, 0, omega, h->st, q, wtab, wlen);
     if (e != cudaSuccess) return e;
     return norm_pass(h, phi, 2, DT_F64, nullptr, q, cond, chunk);
   };
   char key[64];
-  snprintf(key, sizeof(key), "sor:%.17g", omega);
+  if (wtab) snprintf(key, sizeof(key), "sor:chebyshev");
+  else snprintf(key, sizeof(key), "sor:%.17g", omega);
   h->act.key = key;
   h->act.chunk = KRYLOV_GRAPH_CHUNK;
   h->act.plain_chunk = KRYLOV_CHUNK;
@@ -700,6 +747,59 @@ ps_status bicg_start(ps_ctx* h, int dt, const double* rho, double fscale, double
 // keeps every vector in FP64; the mixed precisions keep the Krylov vectors in
 // FP32 and the iterate, the right-hand side, the replaced residuals and every
 // dot product in FP64.
+// Spherical red-black SOR (Sec. 2.1.1) in FP64, stopping on ||f - L x|| <=
+// tol ||b||, b = f - L(boundary part of x) as for BiCGSTAB.  The weights are
+// the given omega, or per node from the local rJ of Eq. local_rjac: omega_opt
+// of Eq. 3, or the sequence of Eq. omega_n advanced by every colour pass in two
+// alternating buffers (pass colour 0 reads buffer 0 and writes buffer 1).
+ps_status begin_sph_sor(ps_ctx* h, const double* rho, double fscale, double* x, double tol,
+                        const ps_solve_opts* o, cudaStream_t s) {
+  const SphDims d = h->sd;
+  ps_status r;
+  if ((r = ensure_partials(h, sph_resnorm_blocks(d))) != PS_OK) return r;
+  const size_t nq = (size_t)d.nr * d.nt;
+  const int sched = o->sor_schedule;
+  if (sched != PS_SOR_FIXED && !h->sph_w)
+    if ((r = alloc_zero((void**)&h->sph_w, 2 * nq * sizeof(double), &h->bytes)) != PS_OK) return r;
+  int nb = 0;
+  TRY((h->nlaunch += 1, launch_init_state(h->st, tol, o->max_iter, s)));
+  TRY((h->nlaunch += 1, launch_bicg_resid(d, h->stab, DT_F64, 0, rho, fscale, x, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 0, h->st, s)));
+  TRY((h->nlaunch += 1, launch_sph_resnorm(d, h->stab, x, rho, fscale, h->partials, &nb, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
+  if (sched != PS_SOR_FIXED)
+    TRY((h->nlaunch += 1, launch_sph_sor_weights(d, h->stab, sched == PS_SOR_CHEBYSHEV, h->sph_w, s)));
+  double* w0 = h->sph_w;
+  double* w1 = h->sph_w ? h->sph_w + nq : nullptr;
+  const double omega = o->omega;
+  h->act.body = [h, d, rho, fscale, x, sched, omega, w0, w1](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    const double n = (double)d.nr * d.nt * d.np;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 2 && e == cudaSuccess; c++) {
+      const double* wc = sched == PS_SOR_FIXED ? nullptr : (sched == PS_SOR_OPTIMAL || c == 0 ? w0 : w1);
+      double* wn = sched == PS_SOR_CHEBYSHEV ? (c == 0 ? w1 : w0) : nullptr;
+      // a pass reads x everywhere, rho and x on its colour, writes x on its colour
+      prof_begin(h, PC_SWEEP0, n * 16.0, n / 2 * 17.0, 1, q);
+      e = (h->nlaunch += 1, launch_sph_sor(d, h->stab, x, rho, fscale, c, omega, wc, wn, h->st, q));
+      prof_end(h, q);
+    }
+    int nbl = 0;
+    if (e == cudaSuccess) {
+      prof_begin(h, PC_NORM0, n * 16.0, n * 15.0, 1, q);
+      e = (h->nlaunch += 1, launch_sph_resnorm(d, h->stab, x, rho, fscale, h->partials, &nbl, q));
+      prof_end(h, q);
+    }
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, nbl, 1.0, 3, h->st, q, cond, chunk));
+    return e;
+  };
+  char key[64];
+  snprintf(key, sizeof(key), "sphsor:%d:%.17g", sched, sched == PS_SOR_FIXED ? omega : 0.0);
+  h->act.key = key;
+  h->act.chunk = KRYLOV_GRAPH_CHUNK;
+  h->act.plain_chunk = KRYLOV_CHUNK;
+  return PS_OK;
+}
+
 ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, const ps_solve_opts* o,
                     cudaStream_t s) {
   ps_status r;
@@ -712,6 +812,7 @@ ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, 
   double* phi = h->phi0;
   TRY(cudaMemcpyAsync(phi, phi_user, (size_t)h->sd.size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
   const double fscale = 4.0 * M_PI * h->bc.G;
+  if (o->method == PS_SOR) return begin_sph_sor(h, rho, fscale, phi, tol, o, s);
   h->act.chunk = KRYLOV_GRAPH_CHUNK;
   h->act.plain_chunk = KRYLOV_CHUNK;
   const int dt = o->prec == PS_FP64 ? DT_F64 : DT_F32;
@@ -1220,6 +1321,8 @@ void poisson_destroy(ps_handle h) {
   cudaFree(h->cg_r);
   cudaFree(h->cg_p);
   cudaFree(h->cg_q);
+  cudaFree(h->sph_w);
+  cudaFree(h->sor_wtab);
   cart_multipole_free(&h->mp);
   sph_tables_free(&h->stab);
   for (auto& p : h->sv) cudaFree(p);
@@ -1257,14 +1360,19 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   if (opts) o = *opts;
   if (o.max_iter < 0) return fail(PS_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (o.prec < PS_FP64 || o.prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", o.prec);
+  if (o.sor_schedule < PS_SOR_FIXED || o.sor_schedule > PS_SOR_OPTIMAL)
+    return fail(PS_ERR_INVALID_ARG, "unknown SOR schedule %d", o.sor_schedule);
+  if (o.method == PS_SOR && o.sor_schedule == PS_SOR_FIXED && !(o.omega > 0.0 && o.omega < 2.0))
+    return fail(PS_ERR_INVALID_ARG, "SOR needs 0 < omega < 2");
   if (h->sph) {
-    if (o.method != PS_BICGSTAB) return fail(PS_ERR_UNSUPPORTED, "spherical grids are solved by BiCGSTAB (method %d)", o.method);
+    if (o.method != PS_BICGSTAB && o.method != PS_SOR)
+      return fail(PS_ERR_UNSUPPORTED, "spherical grids are solved by BiCGSTAB or SOR (method %d)", o.method);
+    if (o.method == PS_SOR && o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "SOR runs in FP64 only");
     if (o.prec == PS_MIXED_BF16) return fail(PS_ERR_UNSUPPORTED, "BF16 storage is a multigrid option");
   } else if (o.method == PS_MG) {
     if (h->nlev < 2) return fail(PS_ERR_INVALID_ARG, "multigrid needs all interval counts even and >= 16");
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1) return fail(PS_ERR_INVALID_ARG, "nu1, nu2 >= 0 with nu1 + nu2 >= 1");
   } else if (o.method == PS_SOR) {
-    if (!(o.omega > 0.0 && o.omega < 2.0)) return fail(PS_ERR_INVALID_ARG, "SOR needs 0 < omega < 2");
     if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "SOR runs in FP64 only");
   } else if (o.method == PS_CG) {
     if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "CG runs in FP64 only");

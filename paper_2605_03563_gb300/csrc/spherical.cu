@@ -81,6 +81,78 @@ cudaError_t launch_sph_apply(const SphDims& d, const SphTables& t, const double*
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ red-black SOR
+// Thread (t, j, k) updates the node i = 2t + ((colour + j + k) & 1) of its row,
+// the one of this colour.  The mirror ghost P_{-1} = P_1 and the periodic
+// ghosts take values of nodes of the other colour (Nphi even), so a pass never
+// reads a value it writes.
+__global__ void __launch_bounds__(SBX* SBY)
+    k_sph_sor(SphDims d, Tab<double> tb, double* __restrict__ x, const double* __restrict__ rho,
+              double fscale, int colour, double omega, const double* __restrict__ wc,
+              double* __restrict__ wn, const double* __restrict__ rj2, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int t = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  if (j >= d.nt) return;
+  const int i = 2 * t + ((colour + j + k) & 1);
+  if (i >= d.nr) return;
+  const long long c = d.at(i, j, k);
+  const int q = j * d.nr + i;
+  const double r = fscale * rho[c] - sph_L<double, double>(d, tb, x, i, j, k, c);
+  const double w = wc != nullptr ? wc[q] : omega;
+  x[c] = fma(w * r, tb.inv_diag[q], x[c]);
+  // the first node of this colour in the column (i, j) advances its weight
+  if (wn != nullptr && k == ((colour + i + j) & 1)) wn[q] = 1.0 / (1.0 - rj2[q] * w / 4.0);
+}
+
+__global__ void __launch_bounds__(SBX* SBY)
+    k_sph_resnorm(SphDims d, Tab<double> tb, const double* __restrict__ x,
+                  const double* __restrict__ rho, double fscale, double* __restrict__ partials) {
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  double r2 = 0.0;
+  if (i < d.nr && j < d.nt) {
+    const long long c = d.at(i, j, k);
+    const double r = fscale * rho[c] - sph_L<double, double>(d, tb, x, i, j, k, c);
+    r2 = r * r;
+  }
+  block_sum2(r2, 0.0, partials);
+}
+
+__global__ void k_sph_sor_weights(int n, const double* __restrict__ rj2, int chebyshev, double* __restrict__ w) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  w[q] = chebyshev ? 1.0 / (1.0 - rj2[q] / 2.0) : 2.0 / (1.0 + sqrt(1.0 - rj2[q]));
+}
+
+cudaError_t launch_sph_sor(const SphDims& d, const SphTables& t, double* x, const double* rho,
+                           double fscale, int colour, double omega, const double* wc, double* wn,
+                           const DevState* st, cudaStream_t s) {
+  if (wn != nullptr && (wc == nullptr || t.rj2 == nullptr)) return cudaErrorInvalidValue;
+  const int half = (d.nr + 1) / 2;
+  const dim3 grid((half + SBX - 1) / SBX, (d.nt + SBY - 1) / SBY, d.np);
+  k_sph_sor<<<grid, dim3(SBX, SBY), 0, s>>>(d, tab_of<double>(t), x, rho, fscale, colour, omega, wc, wn, t.rj2, st);
+  return cudaGetLastError();
+}
+
+int sph_resnorm_blocks(const SphDims& d) {
+  const dim3 g = sph_grid(d);
+  return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_sph_resnorm(const SphDims& d, const SphTables& t, const double* x,
+                               const double* rho, double fscale, double* partials, int* nblk,
+                               cudaStream_t s) {
+  k_sph_resnorm<<<sph_grid(d), dim3(SBX, SBY), 0, s>>>(d, tab_of<double>(t), x, rho, fscale, partials);
+  if (nblk) *nblk = sph_resnorm_blocks(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sph_sor_weights(const SphDims& d, const SphTables& t, int chebyshev, double* w,
+                                   cudaStream_t s) {
+  const int n = d.nr * d.nt;
+  k_sph_sor_weights<<<(n + 255) / 256, 256, 0, s>>>(n, t.rj2, chebyshev, w);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ BiCGSTAB kernels
 // One iteration: v = L phat; alpha; s = r - alpha v, shat = B^-1 s; t = L shat;
 // omega; x += alpha phat + omega shat, r = s - omega t; then either the
@@ -588,6 +660,20 @@ cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th
   if ((e = upload(&t->th_mf, to_f(tm), &t->bytes)) != cudaSuccess) return e;
   if ((e = upload(&t->phf, to_f(pp), &t->bytes)) != cudaSuccess) return e;
   if ((e = upload(&t->inv_diagf, to_f(idg), &t->bytes)) != cudaSuccess) return e;
+  // Eq. local_rjac: rJ at (theta_j, r_i) from the radial width of the flux form,
+  // r_i dtheta and r_i sin(theta_j) dphi; stored squared for the SOR weights
+  std::vector<double> rjsq((size_t)nr * nt);
+  const double cr = std::cos(M_PI / nr), ct = std::cos(M_PI / nt), cp = std::cos(M_PI / np);
+  for (int j = 0; j < nt; j++)
+    for (int i = 0; i < nr; i++) {
+      const double ri = re[i + 1], dr = 0.5 * (re[i + 2] - re[i]);
+      const double wr = 1.0 / (dr * dr);
+      const double wt = 1.0 / ((ri * dth) * (ri * dth));
+      const double wp = 1.0 / ((ri * sth[j] * dph) * (ri * sth[j] * dph));
+      const double rj = (cr * wr + ct * wt + cp * wp) / (wr + wt + wp);
+      rjsq[(size_t)j * nr + i] = rj * rj;
+    }
+  if ((e = upload(&t->rj2, rjsq, &t->bytes)) != cudaSuccess) return e;
   // multipole tables
   t->lmax = lmax;
   if (lmax >= 0) {
@@ -644,7 +730,7 @@ cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th
 void sph_tables_free(SphTables* t) {
   void* ptrs[] = {t->rad_p, t->rad_m, t->inv_r2, t->th_p, t->th_m, t->ph, t->inv_diag,
                   t->rad_pf, t->rad_mf, t->inv_r2f, t->th_pf, t->th_mf, t->phf, t->inv_diagf,
-                  t->cosT, t->sinT, t->Pn, t->Rw, t->sinth, t->Fc, t->Fs, t->q};
+                  t->cosT, t->sinT, t->Pn, t->Rw, t->sinth, t->Fc, t->Fs, t->q, t->rj2};
   for (void* p : ptrs) cudaFree(p);
   *t = SphTables();
 }

@@ -39,6 +39,8 @@ struct SphTables {
   double* Fs = nullptr;
   double* q = nullptr;      // [(L+1)^2]
   double r_ghost = 0.0;     // outer ghost radius
+  // SOR: rJ^2 of Eq. local_rjac per (theta_j, r_i) [Ntheta * Nr]
+  double* rj2 = nullptr;
   size_t bytes = 0;
 };
 
@@ -75,6 +77,23 @@ int bicg_iter_kernels(int dt);
 // scalar finisher for the reference / initial residual (mode 0/1)
 cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
                               cudaStream_t s);
+
+// ---- red-black SOR (Sec. 2.1.1) on the spherical grid, FP64.
+// One colour pass: nodes with (i + j + k) mod 2 == colour take
+// x += w (fscale rho - L x) * inv_diag; w = omega, or wc[j*Nr + i] when wc is
+// given.  With wn given as well, the pass also writes the next pass's weights
+// wn = 1 / (1 - rJ^2 wc / 4) (Eq. omega_n per node).  Skipped once st->done.
+cudaError_t launch_sph_sor(const SphDims& d, const SphTables& t, double* x, const double* rho,
+                           double fscale, int colour, double omega, const double* wc, double* wn,
+                           const DevState* st, cudaStream_t s);
+// partials {sum r^2, 0} of r = fscale rho - L x over the unknown nodes; *nblk = blocks
+cudaError_t launch_sph_resnorm(const SphDims& d, const SphTables& t, const double* x,
+                               const double* rho, double fscale, double* partials, int* nblk,
+                               cudaStream_t s);
+int sph_resnorm_blocks(const SphDims& d);
+// w[j*Nr + i] = omega_1 (chebyshev) or omega_opt (Eq. 3) of the local rJ
+cudaError_t launch_sph_sor_weights(const SphDims& d, const SphTables& t, int chebyshev, double* w,
+                                   cudaStream_t s);
 
 // multipole: q <- moments of rho (unknown nodes, dV = r^2 sin t dr dt dp);
 // outer ghost of phi <- expansion at r_ghost

@@ -46,7 +46,10 @@ __device__ __forceinline__ void set_loop(const DevState* st, unsigned long long 
 
 // Sum a residual pass's per-block partials {sum delta^2, max |delta|} in block
 // order, record the norm in the state and decide convergence (one block).
-// mode: 0 = reference norm, 1 = initial residual, 2 = iteration check.
+// mode: 0 = reference norm, 1 = initial residual, 2 = iteration check, 3 =
+// iteration check that calls only a non-finite norm divergence (SOR on graded
+// spherical grids: its non-normal iteration grows the residual a
+// hundred-to-thousandfold before it converges).
 __device__ __forceinline__ void finish_norm_block(const double* __restrict__ partials, int nblocks,
                                                   double dscale, int mode, DevState* __restrict__ st,
                                                   unsigned long long cond, int chunk) {
@@ -75,7 +78,7 @@ __device__ __forceinline__ void finish_norm_block(const double* __restrict__ par
     st->scale_next = m > 0.0 ? exp2(-rint(log2(m))) : 1.0;
     return;
   }
-  if (st->done && mode == 2) {
+  if (st->done && mode >= 2) {
     set_loop(st, cond, chunk);
     return;
   }
@@ -99,7 +102,7 @@ __device__ __forceinline__ void finish_norm_block(const double* __restrict__ par
     return;
   }
   st->iter += 1;
-  if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
+  if (!isfinite(rel) || (mode == 2 && rel > 1e3 * fmax(st->rel0, 1.0))) st->done = DONE_DIVERGED;
   else if (rel <= st->tol) st->done = DONE_CONVERGED;
   else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
   set_loop(st, cond, chunk);
