@@ -10,6 +10,10 @@ usual short recurrences:
             stop when ||r|| <= tol * ref; beta = (r.r)_new/(r.r)_old;
             p = r + beta p.
 
+Preconditioned CG with the multicolour Gauss-Seidel preconditioner of
+Sec. 2.1.2 (see multigrid.pcg_on_grid for B): the same recurrences with
+z = B^-1 r in place of r in the direction and in rho = r.z.
+
 BiCGSTAB (van der Vorst; non-symmetric A, here the spherical Laplacian) with
 right preconditioning by B^-1 = diag(A)^-1 (the preconditioner is applied to a
 vector, never formed as a product, Sec. 2.1.2):
@@ -87,6 +91,37 @@ def cg(apply_A, b: np.ndarray, x0: np.ndarray, tol: float, max_iter: int,
         beta = rr_new / rr
         p = r + beta * p
         rr = rr_new
+    return KrylovResult(x, max_iter, False, hist)
+
+
+def pcg(apply_A, apply_Minv, b: np.ndarray, x0: np.ndarray, tol: float, max_iter: int,
+        ref: float, dot=numpy_dot) -> KrylovResult:
+    """Preconditioned CG (Sec. 2.1.2: the iteration for A B^-1, B^-1 applied to a
+    vector): z = B^-1 r, p = z, rho = r.z; q = A p, alpha = rho/(p.q),
+    x += alpha p, r -= alpha q; stop on ||r|| <= tol * ref (the unpreconditioned
+    residual, as for CG); z = B^-1 r, beta = (r.z)_new / rho, p = z + beta p."""
+    x = x0.copy()
+    r = b - apply_A(x)
+    rr = dot(r, r)
+    hist = [np.sqrt(rr) / ref]
+    if hist[-1] <= tol:
+        return KrylovResult(x, 0, True, hist)
+    z = apply_Minv(r)
+    p = z.copy()
+    rho = dot(r, z)
+    for it in range(1, max_iter + 1):
+        q = apply_A(p)
+        alpha = rho / dot(p, q)
+        x += alpha * p
+        r -= alpha * q
+        hist.append(np.sqrt(dot(r, r)) / ref)
+        if hist[-1] <= tol:
+            return KrylovResult(x, it, True, hist)
+        z = apply_Minv(r)
+        rho_new = dot(r, z)
+        beta = rho_new / rho
+        rho = rho_new
+        p = z + beta * p
     return KrylovResult(x, max_iter, False, hist)
 
 

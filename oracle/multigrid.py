@@ -60,6 +60,56 @@ def cg_on_grid(phi: np.ndarray, f: np.ndarray, grid: CartGrid, tol: float, max_i
     return res
 
 
+def sgs_preconditioner(grid: CartGrid):
+    """B^-1 of Sec. 2.1.2's multicolour Gauss-Seidel preconditioner for the SPD
+    matrix -A_0 (zero boundary), as a function of a flat residual vector.
+
+    The paper writes B as the block lower triangular part of A in colour order
+    (D + L) and solves with it block-wise, one colour at a time.  CG needs a
+    symmetric positive definite B, so the reading taken here is the symmetric
+    form B = (D + L) D^-1 (D + U): Gauss-Seidel colour passes on -A_0 z = r
+    from z = 0 in ascending colour order (that is (D + L)^-1 r), then in
+    descending order; the first descending pass would repeat the last
+    ascending one exactly (its operands are unchanged), so it is skipped:
+    2 ncol - 1 passes."""
+    from .smoothers import ncolours, sweep_colour
+    ncol = ncolours(grid.order)
+    I = grid.interior
+    shape_int = grid.zeros()[I].shape
+
+    def apply(r):
+        z = grid.zeros()
+        rhs = grid.zeros()
+        rhs[I] = -r.reshape(shape_int)      # A_0 z = -r  <=>  -A_0 z = r
+        for c in list(range(ncol)) + list(range(ncol - 2, -1, -1)):
+            sweep_colour(z, rhs, grid, c, 1.0, ncol)
+        return z[I].ravel().copy()
+    return apply
+
+
+def pcg_on_grid(phi: np.ndarray, f: np.ndarray, grid: CartGrid, tol: float, max_iter: int):
+    """Multicolour-Gauss-Seidel-preconditioned CG for A phi = f (boundary data of
+    phi fixed), on the SPD system -A_0 x = -(f - A b) as cg_on_grid."""
+    I = grid.interior
+    shape_int = phi[I].shape
+
+    def apply_spd(v):
+        full = grid.zeros()
+        full[I] = v.reshape(shape_int)
+        return -laplacian(full, grid)[I].ravel()
+
+    bpart = phi.copy()
+    bpart[I] = 0.0
+    rhs = -(f[I] - laplacian(bpart, grid)[I]).ravel()
+    ref = reference_norm(phi, f, grid)
+    if ref == 0.0:
+        ref = 1.0
+    res = krylov.pcg(apply_spd, sgs_preconditioner(grid), rhs, phi[I].ravel().copy(), tol,
+                     max_iter, ref)
+    phi[I] = res.x.reshape(shape_int)
+    return res
+
+
 def vcycle(levels, l: int, phi: np.ndarray, f: np.ndarray, nu1: int, nu2: int,
            omega: float = 1.0, coarse_tol: float = COARSE_TOL) -> None:
     grid = levels[l]

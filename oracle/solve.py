@@ -69,7 +69,7 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
                     max_iter: int = 10000, G: float = 1.0, bc: str = "dirichlet", lmax: int = 4,
                     origin=None, omega: float = 1.0, nu1: int = 2, nu2: int = 2,
                     inner: int = 1, sor_schedule: str = "fixed") -> SolveInfo:
-    """method in {"sor", "cg", "mg", "ir"}; phi is updated in place."""
+    """method in {"sor", "cg", "pcg", "mg", "ir"}; phi is updated in place."""
     f = 4.0 * math.pi * G * rho
     q = None
     if bc == "multipole":
@@ -81,6 +81,9 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
         it, conv, hist = sor_solve(phi, f, grid, omega, tol, max_iter, sor_schedule)
     elif method == "cg":
         res = multigrid.cg_on_grid(phi, f, grid, tol, max_iter)
+        it, conv, hist = res.iterations, res.converged, res.history
+    elif method == "pcg":
+        res = multigrid.pcg_on_grid(phi, f, grid, tol, max_iter)
         it, conv, hist = res.iterations, res.converged, res.history
     elif method == "mg":
         it, conv, hist = multigrid.mg_solve(phi, f, grid, tol, max_iter, nu1, nu2)

@@ -61,7 +61,7 @@ def _dense_matrix(n, order):
 
 
 @pytest.mark.parametrize("order", [2, 4])
-@pytest.mark.parametrize("method", ["cg", "mg", "sor", "ir"])
+@pytest.mark.parametrize("method", ["cg", "pcg", "mg", "sor", "ir"])
 def test_dense_direct_solve(order, method):
     """8^3 intervals, zero boundary, random rho: iterative solutions agree with
     numpy.linalg.solve on a Kronecker-sum matrix assembled independently."""
@@ -702,3 +702,42 @@ def test_spherical_local_chebyshev_beats_gauss_seidel():
         phi[:, :, -1] = -1.0
         runs[sched] = SP.sor_solve_spherical(phi, f, op, 1e-8, 20000, sched, omega=1.0)[0]
     assert runs["chebyshev"] < runs["fixed"] / 2
+
+
+# ------------------------------------------------------------------ preconditioned CG
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_sgs_preconditioner_is_symmetric_gauss_seidel(order):
+    """The colour passes apply (D + U)^-1 D (D + L)^-1 of -A_0 split in colour
+    order (dense blocks from the independently assembled Kronecker sum), and
+    that matrix is symmetric positive definite, as CG needs."""
+    from oracle import multigrid as MG
+    n = 6
+    g = cart_grid(n, order)
+    A = -_dense_matrix(n, order)
+    ncol = {2: 2, 4: 3}[order]
+    m = n - 1
+    k, j, i = np.unravel_index(np.arange(m ** 3), (m, m, m))
+    col = (i + j + k + 3) % ncol          # node index = array index + 1 per axis
+    lower = col[:, None] > col[None, :]
+    upper = col[:, None] < col[None, :]
+    same = (col[:, None] == col[None, :]) & ~np.eye(m ** 3, dtype=bool)
+    assert np.all(A[same] == 0.0)         # one colour never couples with itself
+    D = np.diag(np.diag(A))
+    L = np.where(lower, A, 0.0)
+    U = np.where(upper, A, 0.0)
+    Minv = np.linalg.solve(D + U, D @ np.linalg.inv(D + L))
+    r = W.rng(21).standard_normal(m ** 3)
+    z = MG.sgs_preconditioner(g)(r)
+    np.testing.assert_allclose(z, Minv @ r, rtol=1e-12, atol=1e-14 * np.max(np.abs(z)))
+    assert np.max(np.abs(Minv - Minv.T)) <= 1e-12 * np.max(np.abs(Minv))
+    assert np.min(np.linalg.eigvalsh(0.5 * (Minv + Minv.T))) > 0.0
+
+
+def test_pcg_needs_fewer_iterations_than_cg():
+    rho, phi, _ = W.uniform_sphere(32)
+    g = cart_grid(32)
+    it_cg = S.solve_cartesian(rho, phi.copy(), g, "cg", 1e-10).iterations
+    it_pcg = S.solve_cartesian(rho, phi.copy(), g, "pcg", 1e-10).iterations
+    assert it_pcg < 0.7 * it_cg
+
