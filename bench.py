@@ -233,7 +233,8 @@ def other_configs(dev, reps=3):
     """Time-to-tolerance of the other workloads, each through the public API on
     device-resident inputs (median of `reps` solves after one warm-up):
       config 1: 32^3 uniform sphere, analytic Dirichlet boundary, SOR (omega 1.8, the Chebyshev
-                weights of Eq. omega_n and omega_opt of Eq. 3) and CG to 1e-10;
+                weights of Eq. omega_n and omega_opt of Eq. 3), CG and multicolour-Gauss-Seidel-
+                preconditioned CG to 1e-10;
       config 3: 512^3 lognormal density, 13-point, multipole l_max = 8, MG to 1e-10 in FP64 and
                 in the FP32-smoothing / BF16-finest refinement mode;
       config 4: 256 x 128 x 256 spherical grid, multipole l_max = 6, Jacobi-BiCGSTAB in FP64 to 1e-8
@@ -263,7 +264,8 @@ def other_configs(dev, reps=3):
     c1 = {}
     with P.CartesianSolver(32) as s:
         for name, method, omega, sched in (("sor", "sor", 1.8, "fixed"), ("sor_chebyshev", "sor", 1.0, "chebyshev"),
-                                           ("sor_optimal", "sor", 1.0, "optimal"), ("cg", "cg", 1.0, "fixed")):
+                                           ("sor_optimal", "sor", 1.0, "optimal"), ("cg", "cg", 1.0, "fixed"),
+                                           ("pcg", "pcg", 1.0, "fixed")):
             phi = phi0.clone()
 
             def run():

@@ -78,7 +78,15 @@ typedef struct {
   double G;
 } ps_bc;
 
-typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3 } ps_method;
+/* PS_SOR red-black / multicolour SOR (Sec. 2.1.1; Cartesian and spherical);
+ * PS_CG conjugate gradients (Sec. 2.1.2); PS_PCG CG preconditioned by
+ * multicolour Gauss-Seidel (Sec. 2.1.2) in its symmetric form
+ * B = (D + L) D^-1 (D + U), D, L, U the blocks of -A in colour order, applied
+ * as colour passes ascending then descending (2, 3 colours for the 7-, 13-point
+ * stencils); PS_MG geometric multigrid (Sec. 2.1.3); PS_BICGSTAB right-Jacobi
+ * BiCGSTAB (spherical grids).  CG and PCG stop on the unpreconditioned
+ * residual and run in FP64. */
+typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3, PS_PCG = 4 } ps_method;
 
 /* PS_FP64: every kernel computes and stores in FP64.
  * PS_MIXED_FP32: Cartesian: FP64 iterative refinement (outer residual,

@@ -18,7 +18,7 @@ from .capi import lib, check
 
 __all__ = ["CartesianSolver", "SphericalSolver", "SolveInfo", "ops", "capi", "workspace_bytes"]
 
-METHODS = {"sor": capi.PS_SOR, "cg": capi.PS_CG, "mg": capi.PS_MG, "bicgstab": capi.PS_BICGSTAB}
+METHODS = {"sor": capi.PS_SOR, "cg": capi.PS_CG, "pcg": capi.PS_PCG, "mg": capi.PS_MG, "bicgstab": capi.PS_BICGSTAB}
 PRECISIONS = {"fp64": capi.PS_FP64, "mixed_fp32": capi.PS_MIXED_FP32, "mixed_bf16": capi.PS_MIXED_BF16}
 # SOR weights: the given omega, Eq. omega_n's Chebyshev sequence, omega_opt of Eq. 3
 SOR_SCHEDULES = {"fixed": 0, "chebyshev": 1, "optimal": 2}

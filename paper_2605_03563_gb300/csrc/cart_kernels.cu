@@ -936,12 +936,106 @@ __global__ void __launch_bounds__(BX* BY)
   }
 }
 
-// which 0: alpha = rr / (p.q) ; which 1: convergence check, beta ; which 2: init
+// ------------------------------------------------------------------ PCG preconditioner
+// z = B^-1 r for the multicolour Gauss-Seidel preconditioner of Sec. 2.1.2 in
+// its symmetric form B = (D + L) D^-1 (D + U) of -A_0 (colour order): colour
+// passes on -A_0 z = r from z = 0, ascending, then descending without the
+// repeated middle pass.  A pass sets z_p = r_p / d + sum c1 z_nb (the scaled
+// Gauss-Seidel value) on the nodes of its colour.  Thread t of a row owns the
+// NCOL consecutive nodes 1 + NCOL t .. NCOL t + NCOL, one of each colour.
+// MODE 0: first pass (colour 0; the block's other nodes are set to 0);
+// MODE 1: a later pass; MODE 2: the last pass (colour 0), which also sums r.z
+// over the whole block (the other colours are final) into per-block partials.
+template <int G, bool ISO, int MODE>
+__global__ void __launch_bounds__(BX* BY)
+    k_pcg_pass(Dims d, Coef<double> cf, const double* __restrict__ r, double* __restrict__ z,
+               int colour, double* __restrict__ partials, const DevState* __restrict__ st) {
+  constexpr int NCOL = G == 1 ? 2 : 3;
+  if (st->done) return;   // uniform: the partials are not read either
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn = blockIdx.y * BY + threadIdx.y + 1;
+  const int zc = zchunk(d.nk());
+  const int kn0 = blockIdx.z * zc + 1;
+  const int kn1 = min(kn0 + zc, d.nk() + 1);
+  const long long sy = d.sy(), sz = d.sz();
+  double s2 = 0.0;
+  if (jn <= d.nj()) {
+    for (int kn = kn0; kn < kn1; kn++) {
+      const int r0 = ((colour - jn - kn - 1) % NCOL + NCOL) % NCOL;   // offset of the colour's node in the block
+      const int in = 1 + r0 + NCOL * t;
+      if (MODE == 0) {
+#pragma unroll
+        for (int m = 0; m < NCOL; m++) {
+          const int ib = 1 + NCOL * t + m;
+          if (ib > d.ni()) break;
+          const long long p = d.at(ib + G - 1, jn + G - 1, kn + G - 1);
+          z[p] = ib == in ? r[p] * cf.inv_d : 0.0;
+        }
+        continue;
+      }
+      if (in <= d.ni()) {
+        const long long p = d.at(in + G - 1, jn + G - 1, kn + G - 1);
+        z[p] = gs_value<G, ISO>(z, p, sy, sz, cf, r[p] * cf.inv_d);
+      }
+      if (MODE == 2) {
+#pragma unroll
+        for (int m = 0; m < NCOL; m++) {
+          const int ib = 1 + NCOL * t + m;
+          if (ib > d.ni()) break;
+          const long long p = d.at(ib + G - 1, jn + G - 1, kn + G - 1);
+          s2 = fma(r[p], z[p], s2);
+        }
+      }
+    }
+  }
+  if (MODE == 2) block_sum_max(s2, 0.0, partials);
+}
+
+static dim3 pcg_grid(const Dims& d, int order) {
+  const int ncol = order == 2 ? 2 : 3;
+  const int per_row = (d.ni() + ncol - 1) / ncol;
+  const int gx = (per_row + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY;
+  const int zc = zchunk_for(gx * gy, d.nk());
+  return dim3(gx, gy, (d.nk() + zc - 1) / zc);
+}
+
+int pcg_partials_count(const Dims& d, int order) {
+  const dim3 g = pcg_grid(d, order);
+  return (int)(g.x * g.y * g.z);
+}
+
+template <int G, bool ISO>
+static cudaError_t pcg_precond_t(const Dims& d, const Coef<double>& cf, const double* r, double* z,
+                                 double* partials, const DevState* st, cudaStream_t s) {
+  constexpr int NCOL = G == 1 ? 2 : 3;
+  const dim3 grid = pcg_grid(d, 2 * G), blk(BX, BY);
+  k_pcg_pass<G, ISO, 0><<<grid, blk, 0, s>>>(d, cf, r, z, 0, partials, st);
+  for (int c = 1; c < NCOL; c++) k_pcg_pass<G, ISO, 1><<<grid, blk, 0, s>>>(d, cf, r, z, c, partials, st);
+  for (int c = NCOL - 2; c >= 1; c--) k_pcg_pass<G, ISO, 1><<<grid, blk, 0, s>>>(d, cf, r, z, c, partials, st);
+  k_pcg_pass<G, ISO, 2><<<grid, blk, 0, s>>>(d, cf, r, z, 0, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_precond(const Dims& d, int order, const double h[3], const double* r, double* z,
+                               double* partials, const DevState* st, cudaStream_t s) {
+  const Coef<double> cf = make_coef<double>(d, h, order);
+  const bool iso = is_iso(h);
+  if (order == 2) return iso ? pcg_precond_t<1, true>(d, cf, r, z, partials, st, s)
+                             : pcg_precond_t<1, false>(d, cf, r, z, partials, st, s);
+  return iso ? pcg_precond_t<2, true>(d, cf, r, z, partials, st, s)
+             : pcg_precond_t<2, false>(d, cf, r, z, partials, st, s);
+}
+
+int pcg_precond_kernels(int order) { return order == 2 ? 3 : 5; }
+
+// which 0: alpha = rho / (p.q); 1: convergence check on r.r, then (CG) beta = rr/rho, rho = rr;
+// 2: start (rho = rr, initial check); 3: convergence check only (PCG);
+// 4: PCG beta = (r.z)/rho, rho = r.z; 5: PCG start, rho = r.z
 __global__ void k_cg_scalar(const double* __restrict__ partials, int nblocks, int which,
                             DevState* __restrict__ st, unsigned long long cond, int chunk) {
   __shared__ double red[32];
   if (which != 2 && st->done) {
-    if (which == 1 && threadIdx.x == 0) set_loop(st, cond, chunk);
+    if ((which == 1 || which == 3) && threadIdx.x == 0) set_loop(st, cond, chunk);
     return;
   }
   double s = 0.0;
@@ -953,17 +1047,24 @@ __global__ void k_cg_scalar(const double* __restrict__ partials, int nblocks, in
   if (which == 0) {
     st->pq = S;
     st->alpha = st->rho / S;
-  } else if (which == 1) {
+  } else if (which == 1 || which == 3) {
     st->iter += 1;
     st->rr = S;
     double rel = sqrt(S) / st->ref;
     st->rel = rel;
-    st->beta = S / st->rho;
-    st->rho = S;
+    if (which == 1) {
+      st->beta = S / st->rho;
+      st->rho = S;
+    }
     if (!isfinite(rel) || rel > 1e3 * fmax(st->rel0, 1.0)) st->done = DONE_DIVERGED;
     else if (rel <= st->tol) st->done = DONE_CONVERGED;
     else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
     set_loop(st, cond, chunk);
+  } else if (which == 4) {
+    st->beta = S / st->rho;
+    st->rho = S;
+  } else if (which == 5) {
+    st->rho = S;
   } else {
     st->rho = S;
     st->rr = S;

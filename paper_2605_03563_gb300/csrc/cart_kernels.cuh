@@ -97,9 +97,17 @@ cudaError_t launch_cg_update(const Dims& d, double* x, double* r, const double* 
 // p = r + beta p
 cudaError_t launch_cg_pupdate(const Dims& d, const double* r, double* p, const DevState* st,
                               cudaStream_t s);
-// scalar steps: which = 0: alpha = rho/pq ; which = 1: convergence + beta
+// scalar steps: which = 0: alpha = rho/pq; 1: convergence + beta (CG); 2: start;
+// 3: convergence only (PCG); 4: PCG beta = r.z/rho; 5: PCG start, rho = r.z
 cudaError_t launch_cg_scalar(const double* partials, int nblocks, int which, DevState* st,
                              cudaStream_t s, unsigned long long cond = 0, int chunk = 0);
+// PCG (Sec. 2.1.2): z = B^-1 r with the multicolour symmetric Gauss-Seidel
+// preconditioner (pcg_precond_kernels(order) launches; skipped once st->done);
+// the last pass writes per-block partials {r.z, 0} (pcg_partials_count blocks).
+cudaError_t launch_pcg_precond(const Dims& d, int order, const double h[3], const double* r, double* z,
+                               double* partials, const DevState* st, cudaStream_t s);
+int pcg_partials_count(const Dims& d, int order);
+int pcg_precond_kernels(int order);
 
 int cart_partials_count(const Dims& d);
 

@@ -150,7 +150,7 @@ struct ps_ctx {
   std::vector<std::array<double, 3>> hs;
   Hier h64, hmx[2];
   double* fs64 = nullptr;
-  double *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
+  double *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_z = nullptr;
   MultipoleTables mpt;
   CartMultipoleDev mp;
   // spherical
@@ -689,6 +689,54 @@ ps_status begin_cg(ps_ctx* h, cudaStream_t s) {
     return e;
   };
   h->act.key = "cg";
+  h->act.chunk = KRYLOV_GRAPH_CHUNK;
+  h->act.plain_chunk = KRYLOV_CHUNK;
+  return PS_OK;
+}
+
+// CG preconditioned by multicolour symmetric Gauss-Seidel (Sec. 2.1.2): the CG
+// recurrences with z = B^-1 r in the direction and in rho = r.z; stopping on
+// the unpreconditioned residual as CG.
+ps_status begin_pcg(ps_ctx* h, cudaStream_t s) {
+  ps_status r;
+  const size_t n = (size_t)h->d0.size();
+  if (!h->cg_r) {
+    if ((r = alloc_zero((void**)&h->cg_r, n * 8, &h->bytes)) != PS_OK) return r;
+    if ((r = alloc_zero((void**)&h->cg_p, n * 8, &h->bytes)) != PS_OK) return r;
+    if ((r = alloc_zero((void**)&h->cg_q, n * 8, &h->bytes)) != PS_OK) return r;
+  }
+  if (!h->cg_z && (r = alloc_zero((void**)&h->cg_z, n * 8, &h->bytes)) != PS_OK) return r;
+  const int nbz = pcg_partials_count(h->d0, h->order);
+  if ((r = ensure_partials(h, nbz)) != PS_OK) return r;
+  double* phi = h->phi0;
+  const int nb = cart_partials_count(h->d0);
+  TRY((h->nlaunch += 1, launch_cg_init(h->d0, h->order, h->h0, phi, h->fs64, h->cg_r, h->cg_p, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 2, h->st, s)));
+  TRY((h->nlaunch += pcg_precond_kernels(h->order), launch_pcg_precond(h->d0, h->order, h->h0, h->cg_r, h->cg_z, h->partials, h->st, s)));
+  TRY((h->nlaunch += 1, launch_cg_scalar(h->partials, nbz, 5, h->st, s)));
+  TRY(cudaMemcpyAsync(h->cg_p, h->cg_z, n * 8, cudaMemcpyDeviceToDevice, s));
+  h->act.body = [h, phi, nb, nbz](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    const double nn = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+    const int ncol = h->order == 2 ? 2 : 3;
+    cudaError_t e;
+    prof_begin(h, PC_KRYLOV, nn * 16.0, nn * (6.0 * (h->order / 2) + 3.0), 1, q);
+    e = (h->nlaunch += 1, launch_cg_apply(h->d0, h->order, h->h0, h->cg_p, h->cg_q, h->partials, h->st, q));
+    prof_end(h, q);
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 0, h->st, q));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_update(h->d0, phi, h->cg_r, h->cg_p, h->cg_q, h->partials, h->st, q));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_scalar(h->partials, nb, 3, h->st, q, cond, chunk));
+    if (e == cudaSuccess) {
+      // 2 ncol - 1 colour passes, each reading z around and r on its colour
+      prof_begin(h, PC_SWEEP0, nn * 8.0 * (2 * ncol - 1) * (1.0 + 2.0 / ncol),
+                 nn / ncol * (2 * ncol - 1) * (6.0 * (h->order / 2) + 1.0), 1, q);
+      e = (h->nlaunch += pcg_precond_kernels(h->order), launch_pcg_precond(h->d0, h->order, h->h0, h->cg_r, h->cg_z, h->partials, h->st, q));
+      prof_end(h, q);
+    }
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_scalar(h->partials, nbz, 4, h->st, q));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_cg_pupdate(h->d0, h->cg_z, h->cg_p, h->st, q));
+    return e;
+  };
+  h->act.key = "pcg";
   h->act.chunk = KRYLOV_GRAPH_CHUNK;
   h->act.plain_chunk = KRYLOV_CHUNK;
   return PS_OK;
@@ -1321,6 +1369,7 @@ void poisson_destroy(ps_handle h) {
   cudaFree(h->cg_r);
   cudaFree(h->cg_p);
   cudaFree(h->cg_q);
+  cudaFree(h->cg_z);
   cudaFree(h->sph_w);
   cudaFree(h->sor_wtab);
   cart_multipole_free(&h->mp);
@@ -1374,7 +1423,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1) return fail(PS_ERR_INVALID_ARG, "nu1, nu2 >= 0 with nu1 + nu2 >= 1");
   } else if (o.method == PS_SOR) {
     if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "SOR runs in FP64 only");
-  } else if (o.method == PS_CG) {
+  } else if (o.method == PS_CG || o.method == PS_PCG) {
     if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "CG runs in FP64 only");
   } else {
     return fail(PS_ERR_INVALID_ARG, "method %d is not available on Cartesian grids", o.method);
@@ -1398,6 +1447,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
     if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, s)) != PS_OK) return r;
     if (o.method == PS_MG) r = o.prec == PS_FP64 ? begin_mg64(h, &o, s) : begin_ir(h, &o, s);
     else if (o.method == PS_SOR) r = begin_sor(h, &o, s);
+    else if (o.method == PS_PCG) r = begin_pcg(h, s);
     else r = begin_cg(h, s);
   }
   if (r != PS_OK) return r;

@@ -94,3 +94,30 @@ def test_spherical_sor_rejects_mixed_precision(pkg):
     with pkg.SphericalSolver(r, th, ph) as s:
         with pytest.raises(pkg.capi.PoissonError):
             s.solve(dev(rho), dev(np.zeros(rho.shape)), method="sor", prec="mixed_fp32")
+
+
+# ------------------------------------------------------------------ preconditioned CG
+@pytest.mark.parametrize("n,order", [(32, 2), (16, 4), (24, 2)])
+def test_pcg_matches_oracle(pkg, n, order):
+    """CG preconditioned by multicolour symmetric Gauss-Seidel (Sec. 2.1.2):
+    iteration counts equal to the oracle's, potentials within 1e-10; ragged
+    rows (24^3: 23 interior nodes, an odd count) exercise the colour blocks."""
+    if order == 2 and n == 32:
+        rho, phi0, _ = W.uniform_sphere(n)
+    elif order == 2:
+        rho = np.abs(W.rng(31).standard_normal(W.cart_shape(n, 2)))
+        phi0 = np.zeros(W.cart_shape(n, 2))
+    else:
+        rho, phi0, _ = W.manufactured_sine(n, order)
+    g = cart_grid(n, order)
+    phi_o = phi0.copy()
+    info_o = OS.solve_cartesian(rho, phi_o, g, "pcg", 1e-10, max_iter=5000)
+    phi_t = dev(phi0)
+    with pkg.CartesianSolver(n, order) as s:
+        info = s.solve(dev(rho), phi_t, tol=1e-10, method="pcg", max_iter=5000)
+        phi_c = dev(phi0)
+        info_c = s.solve(dev(rho), phi_c, tol=1e-10, method="cg", max_iter=5000)
+    assert info.converged and info_o.converged
+    assert info.iterations == info_o.iterations, (info.iterations, info_o.iterations)
+    assert rel_err(host(phi_t), phi_o) <= FP64_TOL
+    assert info.iterations < info_c.iterations
