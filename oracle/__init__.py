@@ -17,7 +17,9 @@ smoothers   multicolour Gauss-Seidel / SOR sweeps (Sec. 2.1.1), omega (Eqs. 3-5,
             the Chebyshev sequence of Eq. omega_n)
 transfer    full-weighting restriction and P = 8 R^T prolongation (Sec. 2.1.3)
 krylov      CG (Sec. 2.1.2) and right-Jacobi-preconditioned BiCGSTAB
-multigrid   V-cycle, MG solve, FP64 iterative-refinement driver
+multigrid   V-cycle, MG solve, FP64 iterative-refinement driver, PCG
+compact     compact 2nd/4th/6th-order stencils, SPAI smoothers (Table 1), Galerkin
+            coarse operators and their multigrid (Sec. 2.1.3)
 multipole   real spherical harmonics, moments and boundary potential (Sec. 2.2)
 solve       the whole-solve drivers that mirror the C ABI's poisson_solve
 """

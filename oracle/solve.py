@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import multigrid, multipole
+from . import compact, multigrid, multipole
 from .grid import CartGrid
 from .operators import norm2, reference_norm, residual
 from .smoothers import (ncolours, omega_first, omega_next, omega_opt, rjac_uniform, sweep,
@@ -68,7 +68,7 @@ def sor_solve(phi, f, grid: CartGrid, omega: float, tol: float, max_iter: int,
 def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: str, tol: float,
                     max_iter: int = 10000, G: float = 1.0, bc: str = "dirichlet", lmax: int = 4,
                     origin=None, omega: float = 1.0, nu1: int = 2, nu2: int = 2,
-                    inner: int = 1, sor_schedule: str = "fixed") -> SolveInfo:
+                    inner: int = 1, sor_schedule: str = "fixed", compact_order: int = 0) -> SolveInfo:
     """method in {"sor", "cg", "pcg", "mg", "ir"}; phi is updated in place."""
     f = 4.0 * math.pi * G * rho
     q = None
@@ -85,6 +85,9 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
     elif method == "pcg":
         res = multigrid.pcg_on_grid(phi, f, grid, tol, max_iter)
         it, conv, hist = res.iterations, res.converged, res.history
+    elif method == "mg" and compact_order:
+        # compact stencil of that order, SPAI smoothing, Galerkin coarse operators (Sec. 2.1.3)
+        it, conv, hist = compact.mg_solve(phi, f, grid, compact_order, tol, max_iter, nu1, nu2)
     elif method == "mg":
         it, conv, hist = multigrid.mg_solve(phi, f, grid, tol, max_iter, nu1, nu2)
     elif method == "ir":
