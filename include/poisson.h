@@ -118,6 +118,14 @@ typedef struct {
                             always use the per-colour passes. */
   int32_t sor_schedule;  /* PS_SOR weights (ps_sor_schedule): the given omega, the Chebyshev
                             sequence of Eq. omega_n, or omega_opt of Eq. 3; 0 = given omega */
+  int32_t compact_order; /* PS_MG on a stencil_order 2 handle with equal spacings: 0 = the
+                            7-point stencil with red-black Gauss-Seidel (above); 2, 4 or 6 =
+                            the compact radius-one discretisation of that order (Sec. 2.1.3),
+                            L_h phi = R_h (4 pi G rho), smoothed by the SPAI smoother of
+                            Eq. richardson with Table 1's coefficients, Galerkin coarse
+                            operators R A P, coarsest level by CG; FP64 only.  The
+                            relative residual is ||R_h f - L_h phi|| / ||R_h f - L_h phi0||. */
+  int32_t reserved_;     /* set to 0 */
 } ps_solve_opts;
 
 /* SOR weights (Sec. 2.1.1).  rJ is the Jacobi spectral radius estimate: Eq. 4

@@ -114,11 +114,12 @@ class _Handle:
 
     # ---- asynchronous, steppable solves (continuous batching)
     def begin(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
-              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0, sor_schedule="fixed"):
+              max_iter=100, inner_cycles=1, stream=None, tile_min_n=0, sor_schedule="fixed",
+              compact_order=0):
         """Start a solve whose state stays on the device; rho/phi must stay alive until end()."""
         self._opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
                                       int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
-                                      int(tile_min_n), SOR_SCHEDULES[sor_schedule])
+                                      int(tile_min_n), SOR_SCHEDULES[sor_schedule], int(compact_order))
         self._keep = (rho, phi)
         check(lib().poisson_solve_begin(self._h, _ptr(rho), _ptr(phi), float(tol),
                                         C.byref(self._opts)), "poisson_solve_begin")
@@ -144,10 +145,10 @@ class _Handle:
         return SolveInfo.from_c(info, min(nmom, 81))
 
     def _solve(self, rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-               stream, nmom, tile_min_n=0, sor_schedule="fixed"):
+               stream, nmom, tile_min_n=0, sor_schedule="fixed", compact_order=0):
         opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
                                 int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
-                                int(tile_min_n), SOR_SCHEDULES[sor_schedule])
+                                int(tile_min_n), SOR_SCHEDULES[sor_schedule], int(compact_order))
         info = capi.PsInfo()
         st = lib().poisson_solve(self._h, _ptr(rho), _ptr(phi), float(tol), C.byref(opts),
                                  C.byref(info))
@@ -183,14 +184,17 @@ class CartesianSolver(_Handle):
 
     def solve(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
               max_iter=100, inner_cycles=1, stream=None, tile_min_n=0,
-              sor_schedule="fixed") -> SolveInfo:
+              sor_schedule="fixed", compact_order=0) -> SolveInfo:
         """tile_min_n: levels with at least this many intervals per axis use the TMA tile
         kernels (0 = library default, negative = never); results are bitwise identical.
         sor_schedule (method "sor"): "fixed" (omega), "chebyshev" (Eq. omega_n) or
-        "optimal" (Eq. 3), the last two with rJ of Eq. 4."""
+        "optimal" (Eq. 3), the last two with rJ of Eq. 4.
+        compact_order (method "mg", order-2 handle, equal spacings): 2, 4 or 6 selects the
+        compact discretisation of that order with SPAI smoothing and Galerkin coarse
+        operators (Sec. 2.1.3); 0 the 7-point / 13-point stencil with Gauss-Seidel."""
         nmom = (self.lmax + 1) ** 2 if self.multipole else 0
         return self._solve(rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-                           stream, min(nmom, 81), tile_min_n, sor_schedule)
+                           stream, min(nmom, 81), tile_min_n, sor_schedule, compact_order)
 
 
 class SphericalSolver(_Handle):

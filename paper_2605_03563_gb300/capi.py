@@ -37,7 +37,7 @@ class PsSolveOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("prec", C.c_int32), ("omega", C.c_double),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("max_iter", C.c_int32),
                 ("inner_cycles", C.c_int32), ("stream", C.c_void_p), ("tile_min_n", C.c_int32),
-                ("sor_schedule", C.c_int32)]
+                ("sor_schedule", C.c_int32), ("compact_order", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class PsInfo(C.Structure):

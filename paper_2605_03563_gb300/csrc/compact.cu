@@ -1,0 +1,357 @@
+// Compact radius-one stencils, SPAI smoothing and Galerkin coarse operators
+// (Sec. 2.1.3), FP64.
+//
+// Compact schemes L_h u = R_h f of order 2, 4, 6 (isotropic spacing; weights
+// from Taylor matching, as the paper cites compact schemes without printing
+// them):
+//   order 2: L = (-6, 1, 0, 0)/h^2,          R f = f
+//   order 4: L = (-24, 2, 1, 0)/(6 h^2),     R f = f/2 + (1/12) sum_faces f
+//   order 6: L = (-128, 14, 3, 1)/(30 h^2),  R f = (67/120) f + (1/18) sum_faces f
+//            + (1/90) sum_edges f - (1/240) sum_{+-2 e_a} f
+// (weights per offset class centre / faces / edges / corners).  The +-2
+// offsets of the order-6 right-hand side reach one layer past the node array
+// at the first interior layer; there f is the cubic extrapolation
+// 4 f_0 - 6 f_1 + 4 f_2 - f_3 along that axis.
+//
+// The 27-point kernels march z with the in-plane sums of three planes in
+// registers: per plane C (centre), F (4 in-plane faces), E (4 in-plane
+// diagonals), so that
+//   (A u)(z) = w0 C(z) + w1 (F(z) + C(z-1) + C(z+1)) + w2 (E(z) + F(z-1) + F(z+1))
+//            + w3 (E(z-1) + E(z+1)),
+// about 15 FP64 instructions per node instead of 27.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "compact.cuh"
+#include "stencil.cuh"
+
+namespace ps {
+
+static constexpr int CBX = 32, CBY = 8, CZC = 16;
+
+W27 compact_lhs(int order, double h) {
+  const double ih2 = 1.0 / (h * h);
+  W27 a{};
+  if (order == 2) {
+    a = W27{{-6.0, 1.0, 0.0, 0.0}};
+  } else if (order == 4) {
+    a = W27{{-24.0 / 6.0, 2.0 / 6.0, 1.0 / 6.0, 0.0}};
+  } else {
+    a = W27{{-128.0 / 30.0, 14.0 / 30.0, 3.0 / 30.0, 1.0 / 30.0}};
+  }
+  for (double& v : a.w) v *= ih2;
+  return a;
+}
+
+// R A P on a 9^3-node fine grid around one coarse delta: prolong the delta
+// (trilinear: per axis 1, 1/2), apply A on the fine interior, restrict with
+// full weighting (per axis 1/4, 1/2, 1/4) at the coarse neighbours.
+W27 galerkin27(const W27& A) {
+  const int N = 9;   // fine nodes 0..8, coarse delta at fine node 4 (coarse node 2)
+  auto idx = [&](int i, int j, int k) { return (k * N + j) * N + i; };
+  std::vector<double> pe(N * N * N, 0.0), ape(N * N * N, 0.0);
+  auto wp = [](int d) { return d == 0 ? 1.0 : (std::abs(d) == 1 ? 0.5 : 0.0); };
+  for (int k = 0; k < N; k++)
+    for (int j = 0; j < N; j++)
+      for (int i = 0; i < N; i++) pe[idx(i, j, k)] = wp(i - 4) * wp(j - 4) * wp(k - 4);
+  for (int k = 1; k < N - 1; k++)
+    for (int j = 1; j < N - 1; j++)
+      for (int i = 1; i < N - 1; i++) {
+        double s = 0.0;
+        for (int dz = -1; dz <= 1; dz++)
+          for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++)
+              s += A.w[(dx != 0) + (dy != 0) + (dz != 0)] * pe[idx(i + dx, j + dy, k + dz)];
+        ape[idx(i, j, k)] = s;
+      }
+  auto wr = [](int d) { return d == 0 ? 0.5 : 0.25; };
+  double sum[4] = {0, 0, 0, 0};
+  int cnt[4] = {0, 0, 0, 0};
+  for (int Dz = -1; Dz <= 1; Dz++)
+    for (int Dy = -1; Dy <= 1; Dy++)
+      for (int Dx = -1; Dx <= 1; Dx++) {
+        double s = 0.0;
+        for (int ez = -1; ez <= 1; ez++)
+          for (int ey = -1; ey <= 1; ey++)
+            for (int ex = -1; ex <= 1; ex++)
+              s += wr(ex) * wr(ey) * wr(ez) * ape[idx(4 + 2 * Dx + ex, 4 + 2 * Dy + ey, 4 + 2 * Dz + ez)];
+        const int c = (Dx != 0) + (Dy != 0) + (Dz != 0);
+        sum[c] += s;
+        cnt[c]++;
+      }
+  W27 out;
+  for (int c = 0; c < 4; c++) out.w[c] = sum[c] / cnt[c];
+  return out;
+}
+
+// in-plane sums of plane k at (i, j): centre, 4 faces, 4 diagonals
+struct Plane {
+  double c, f, e;
+};
+
+template <bool ZI>
+__device__ __forceinline__ Plane plane_sums(const Dims& d, const double* __restrict__ u, int i, int j, int k) {
+  const long long sy = d.sy();
+  const long long p = d.at(i, j, k);
+  auto ld = [&](long long q, int ii, int jj) -> double {
+    if (ZI && ii >= 1 && ii <= d.ni() && jj >= 1 && jj <= d.nj() && k >= 1 && k <= d.nk()) return 0.0;
+    return u[q];
+  };
+  Plane s;
+  s.c = ld(p, i, j);
+  s.f = (ld(p - 1, i - 1, j) + ld(p + 1, i + 1, j)) + (ld(p - sy, i, j - 1) + ld(p + sy, i, j + 1));
+  s.e = (ld(p - sy - 1, i - 1, j - 1) + ld(p - sy + 1, i + 1, j - 1)) +
+        (ld(p + sy - 1, i - 1, j + 1) + ld(p + sy + 1, i + 1, j + 1));
+  return s;
+}
+
+__device__ __forceinline__ double apply_planes(const double w[4], const Plane& m, const Plane& c, const Plane& p) {
+  return fma(w[0], c.c, fma(w[1], (c.f + (m.c + p.c)), fma(w[2], (c.e + (m.f + p.f)), w[3] * (m.e + p.e))));
+}
+
+// per-block {sum, 0} into partials[2 b], partials[2 b + 1] (blocks of CBX x CBY threads)
+__device__ __forceinline__ void block_partial(double v, double* __restrict__ partials) {
+  __shared__ double sh[CBX * CBY / 32];
+  const int tid = threadIdx.x + CBX * threadIdx.y;
+  v = warp_sum(v);
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double a = tid < CBX * CBY / 32 ? sh[tid] : 0.0;
+    a = warp_sum(a);
+    if (tid == 0) {
+      const int bid = block_linear_id();
+      partials[2 * bid] = a;
+      partials[2 * bid + 1] = 0.0;
+    }
+  }
+}
+
+// MODE 0: r = b - A u (ZI: u's interior read as 0), partials if given; MODE 1: u -= omega M r
+template <int MODE, bool ZI>
+__global__ void __launch_bounds__(CBX* CBY)
+    k_c27(Dims d, W27 W, double omega, const double* __restrict__ src, const double* __restrict__ b,
+          double* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;   // uniform
+  const int i = blockIdx.x * CBX + threadIdx.x + 1;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
+  double s2 = 0.0;
+  if (i <= d.ni() && j <= d.nj()) {
+    Plane pm = plane_sums<ZI>(d, src, i, j, k0 - 1);
+    Plane pc = plane_sums<ZI>(d, src, i, j, k0);
+    for (int k = k0; k < k1; k++) {
+      const Plane pn = plane_sums<ZI>(d, src, i, j, k + 1);
+      const double a = apply_planes(W.w, pm, pc, pn);
+      const long long q = d.at(i, j, k);
+      if (MODE == 0) {
+        const double r = b[q] - a;
+        dst[q] = r;
+        s2 = fma(r, r, s2);
+      } else {
+        dst[q] = fma(-omega, a, dst[q]);
+      }
+      pm = pc;
+      pc = pn;
+    }
+  }
+  if (MODE == 0 && partials != nullptr) block_partial(s2, partials);
+}
+
+static dim3 c27_grid(const Dims& d) {
+  return dim3((d.ni() + CBX - 1) / CBX, (d.nj() + CBY - 1) / CBY, (d.nk() + CZC - 1) / CZC);
+}
+
+int c27_blocks(const Dims& d) {
+  const dim3 g = c27_grid(d);
+  return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const double* b, double* r,
+                             int zero_interior, double* partials, const DevState* st, cudaStream_t s) {
+  if (d.g != 1) return cudaErrorInvalidValue;
+  if (zero_interior)
+    k_c27<0, true><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+  else
+    k_c27<0, false><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const double* r, double* u,
+                            const DevState* st, cudaStream_t s) {
+  if (d.g != 1) return cudaErrorInvalidValue;
+  k_c27<1, false><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, M, omega, r, nullptr, u, nullptr, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ right-hand side
+// f value of node (i, j, k) of the dense layout du, one extrapolated layer on
+// every side (cubic along the axis that leaves the array)
+__device__ __forceinline__ double f_ext(const Dims& du, const double* __restrict__ rho, int i, int j, int k) {
+  const int ni = du.nx, nj = du.ny, nk = du.nz;   // node indices 0..n
+  auto at = [&](int a, int b, int c) { return rho[du.at(a, b, c)]; };
+  if (i < 0) return 4 * at(0, j, k) - 6 * at(1, j, k) + 4 * at(2, j, k) - at(3, j, k);
+  if (i > ni) return 4 * at(ni, j, k) - 6 * at(ni - 1, j, k) + 4 * at(ni - 2, j, k) - at(ni - 3, j, k);
+  if (j < 0) return 4 * at(i, 0, k) - 6 * at(i, 1, k) + 4 * at(i, 2, k) - at(i, 3, k);
+  if (j > nj) return 4 * at(i, nj, k) - 6 * at(i, nj - 1, k) + 4 * at(i, nj - 2, k) - at(i, nj - 3, k);
+  if (k < 0) return 4 * at(i, j, 0) - 6 * at(i, j, 1) + 4 * at(i, j, 2) - at(i, j, 3);
+  if (k > nk) return 4 * at(i, j, nk) - 6 * at(i, j, nk - 1) + 4 * at(i, j, nk - 2) - at(i, j, nk - 3);
+  return at(i, j, k);
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(CBX* CBY)
+    k_c27_rhs(Dims d, Dims du, const double* __restrict__ rho, double fscale, double* __restrict__ b) {
+  const int i = blockIdx.x * CBX + threadIdx.x + 1;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
+  if (i > d.ni() || j > d.nj()) return;
+  for (int k = k0; k < k1; k++) {
+    double v;
+    if (ORDER == 2) {
+      v = rho[du.at(i, j, k)];
+    } else {
+      double c = 0, fa = 0, ed = 0;
+      for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+          for (int dx = -1; dx <= 1; dx++) {
+            const int cl = (dx != 0) + (dy != 0) + (dz != 0);
+            if (cl == 3) continue;
+            const double x = rho[du.at(i + dx, j + dy, k + dz)];
+            if (cl == 0) c += x;
+            else if (cl == 1) fa += x;
+            else ed += x;
+          }
+      if (ORDER == 4) {
+        v = 0.5 * c + fa / 12.0;
+      } else {
+        const double ax = (f_ext(du, rho, i - 2, j, k) + f_ext(du, rho, i + 2, j, k)) +
+                          (f_ext(du, rho, i, j - 2, k) + f_ext(du, rho, i, j + 2, k)) +
+                          (f_ext(du, rho, i, j, k - 2) + f_ext(du, rho, i, j, k + 2));
+        v = (67.0 / 120.0) * c + fa / 18.0 + ed / 90.0 - ax / 240.0;
+      }
+    }
+    b[d.at(i, j, k)] = fscale * v;
+  }
+}
+
+cudaError_t launch_c27_rhs(const Dims& d, const Dims& du, int order, const double* rho, double fscale,
+                           double* b, cudaStream_t s) {
+  if (d.g != 1 || du.g != 1) return cudaErrorInvalidValue;
+  if (order == 6 && (d.nx < 4 || d.ny < 4 || d.nz < 4)) return cudaErrorInvalidValue;
+  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  if (order == 2) k_c27_rhs<2><<<g, blk, 0, s>>>(d, du, rho, fscale, b);
+  else if (order == 4) k_c27_rhs<4><<<g, blk, 0, s>>>(d, du, rho, fscale, b);
+  else k_c27_rhs<6><<<g, blk, 0, s>>>(d, du, rho, fscale, b);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ coarsest level
+// CG on -A u = -b from u = 0 (A negative definite), one CTA: x, r, q over the
+// unknowns and p over all nodes (zero boundary) in shared memory.
+static constexpr int CCG_THREADS = 1024;
+
+__device__ double ccg_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[32] = t;
+  __syncthreads();
+  return red[32];
+}
+
+__global__ void __launch_bounds__(CCG_THREADS)
+    k_c27_coarse_cg(Dims d, W27 A, const double* __restrict__ b, double* __restrict__ u, double tol,
+                    const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  extern __shared__ double sm[];
+  const int nx = d.nx + 1, ny = d.ny + 1, nz = d.nz + 1;   // nodes per axis
+  const int nn = nx * ny * nz;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk(), nu = ni * nj * nk;
+  double* p = sm;              // [nn] all nodes, boundary zero
+  double* x = p + nn;          // [nu]
+  double* r = x + nu;
+  double* q = r + nu;
+  double* red = q + nu;        // [33]
+  auto node = [&](int t) {     // unknown t -> node index in p
+    const int i = t % ni + 1, j = (t / ni) % nj + 1, k = t / (ni * nj) + 1;
+    return (k * ny + j) * nx + i;
+  };
+  auto gidx = [&](int t) {
+    const int i = t % ni + 1, j = (t / ni) % nj + 1, k = t / (ni * nj) + 1;
+    return d.at(i, j, k);
+  };
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) p[t] = 0.0;
+  __syncthreads();
+  double loc = 0.0;
+  for (int t = threadIdx.x; t < nu; t += blockDim.x) {
+    const double v = -b[gidx(t)];
+    x[t] = 0.0;
+    r[t] = v;
+    p[node(t)] = v;
+    loc = fma(v, v, loc);
+  }
+  double rr = ccg_sum(loc, red);
+  const double ref = sqrt(rr) > 0.0 ? sqrt(rr) : 1.0;
+  const int sy = nx, sz = nx * ny;
+  for (int it = 0; it < nu && sqrt(rr) / ref > tol; it++) {
+    loc = 0.0;
+    for (int t = threadIdx.x; t < nu; t += blockDim.x) {
+      const int c = node(t);
+      const double f = (p[c - 1] + p[c + 1]) + (p[c - sy] + p[c + sy]) + (p[c - sz] + p[c + sz]);
+      const double e = ((p[c - sy - 1] + p[c - sy + 1]) + (p[c + sy - 1] + p[c + sy + 1])) +
+                       ((p[c - sz - 1] + p[c - sz + 1]) + (p[c + sz - 1] + p[c + sz + 1])) +
+                       ((p[c - sz - sy] + p[c - sz + sy]) + (p[c + sz - sy] + p[c + sz + sy]));
+      const double k8 = ((p[c - sz - sy - 1] + p[c - sz - sy + 1]) + (p[c - sz + sy - 1] + p[c - sz + sy + 1])) +
+                        ((p[c + sz - sy - 1] + p[c + sz - sy + 1]) + (p[c + sz + sy - 1] + p[c + sz + sy + 1]));
+      const double v = -(A.w[0] * p[c] + A.w[1] * f + A.w[2] * e + A.w[3] * k8);
+      q[t] = v;
+      loc = fma(p[c], v, loc);
+    }
+    const double pq = ccg_sum(loc, red);
+    const double alpha = rr / pq;
+    loc = 0.0;
+    for (int t = threadIdx.x; t < nu; t += blockDim.x) {
+      x[t] = fma(alpha, p[node(t)], x[t]);
+      const double v = fma(-alpha, q[t], r[t]);
+      r[t] = v;
+      loc = fma(v, v, loc);
+    }
+    const double rn = ccg_sum(loc, red);
+    const double beta = rn / rr;
+    rr = rn;
+    for (int t = threadIdx.x; t < nu; t += blockDim.x) {
+      const int c = node(t);
+      p[c] = fma(beta, p[c], r[t]);
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nu; t += blockDim.x) u[gidx(t)] = x[t];
+}
+
+size_t c27_coarse_smem(const Dims& d) {
+  const size_t nn = (size_t)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  const size_t nu = (size_t)d.ni() * d.nj() * d.nk();
+  return (nn + 3 * nu + 33) * sizeof(double);
+}
+
+cudaError_t launch_c27_coarse_cg(const Dims& d, const W27& A, const double* b, double* u, double tol,
+                                 const DevState* st, cudaStream_t s) {
+  const size_t smem = c27_coarse_smem(d);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static size_t opted = 0;
+  if (smem > 48 * 1024 && smem > opted) {
+    cudaError_t e = cudaFuncSetAttribute(k_c27_coarse_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    opted = smem;
+  }
+  k_c27_coarse_cg<<<1, CCG_THREADS, smem, s>>>(d, A, b, u, tol, st);
+  return cudaGetLastError();
+}
+
+}  // namespace ps

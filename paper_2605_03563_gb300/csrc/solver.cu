@@ -19,6 +19,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,7 @@
 #include "batch.cuh"
 #include "multipole.cuh"
 #include "spherical.cuh"
+#include "compact.cuh"
 
 namespace ps {
 
@@ -691,6 +693,115 @@ ps_status begin_cg(ps_ctx* h, cudaStream_t s) {
   h->act.key = "cg";
   h->act.chunk = KRYLOV_GRAPH_CHUNK;
   h->act.plain_chunk = KRYLOV_CHUNK;
+  return PS_OK;
+}
+
+// ------------------------------------------------------------------ compact stencils + SPAI MG
+// Table 1: omega, alpha, beta, gamma, delta of the SPAI smoother M of Eq.
+// Smoother for compact orders 2, 4, 6.  The order-6 row prints delta equal to
+// its mu (a garbled cell); delta = 0.0151 is the value that minimises the local
+// Fourier smoothing factor with the printed omega, alpha, beta and gamma.
+static const double kSpai[3][5] = {{1.3699, 0.1432, 0.0284, 0.0081, 0.0025},
+                                   {0.9363, 0.2807, 0.0329, 0.0166, 0.0044},
+                                   {0.3543, 0.7064, 0.1005, 0.0363, 0.0151}};
+static const double kCompactCoarseTol = 1e-2;   // coarsest CG, as the geometric MG
+
+struct CompactLevels {
+  std::vector<W27> A, M;
+  std::vector<double> omega;
+};
+
+// One V-cycle of the compact multigrid (Sec. 2.1.3): SPAI steps
+// u -= omega M (b - A u), residual, full weighting into the coarse right-hand
+// side, the coarse error from zero, trilinear correction, SPAI steps; the
+// coarsest level by CG.  Level l: u = phi, b = fs, r = tmp.
+cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, int nu1, int nu2, cudaStream_t s) {
+  Level& L = H->lv[l];
+  const int last = (int)H->lv.size() - 1;
+  double* u = (double*)L.phi;
+  double* b = (double*)L.fs;
+  const DevState* st = h->st;
+  cudaError_t e;
+  if (l == last) {
+    prof_begin(h, PC_COARSE, 0.0, 0.0, 1, s);
+    e = (h->nlaunch += 1, launch_c27_coarse_cg(L.d, C.A[l], b, u, kCompactCoarseTol, st, s));
+    prof_end(h, s);
+    return e;
+  }
+  double* r = (double*)L.tmp;
+  const double n = (double)L.d.ni() * L.d.nj() * L.d.nk();
+  auto smooth = [&](int steps) -> cudaError_t {
+    for (int it = 0; it < steps; it++) {
+      prof_begin(h, l == 0 ? PC_DELTA0 : PC_SWEEP_C, n * 24.0, n * 16.0, 1, s);
+      cudaError_t e2 = (h->nlaunch += 1, launch_c27_resid(L.d, C.A[l], u, b, r, 0, nullptr, st, s));
+      prof_end(h, s);
+      if (e2 != cudaSuccess) return e2;
+      prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 24.0, n * 16.0, 1, s);
+      e2 = (h->nlaunch += 1, launch_c27_spai(L.d, C.M[l], C.omega[l], r, u, st, s));
+      prof_end(h, s);
+      if (e2 != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
+  };
+  if ((e = smooth(nu1)) != cudaSuccess) return e;
+  if (l == 0) prof_begin(h, PC_DELTA0, n * 24.0, n * 16.0, 1, s);
+  e = (h->nlaunch += 1, launch_c27_resid(L.d, C.A[l], u, b, r, 0, nullptr, st, s));
+  if (l == 0) prof_end(h, s);
+  if (e != cudaSuccess) return e;
+  Level& Cl = H->lv[l + 1];
+  if (l == 0) prof_begin(h, PC_RESTRICT0, n * 8.0 + n, n * 4.5, 1, s);
+  e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, DT_F64, r, DT_F64, Cl.fs, 1.0, s));
+  if (l == 0) prof_end(h, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(Cl.phi, 0, (size_t)Cl.d.size() * sizeof(double), s)) != cudaSuccess) return e;
+  if ((e = vcycle_compact(h, H, C, l + 1, nu1, nu2, s)) != cudaSuccess) return e;
+  if (l == 0) prof_begin(h, PC_PROLONG0, n * 16.0 + n, n * 4.0, 1, s);
+  e = (h->nlaunch += 1, launch_prolong(L.d, Cl.d, DT_F64, Cl.phi, DT_F64, u, s));
+  if (l == 0) prof_end(h, s);
+  if (e != cudaSuccess) return e;
+  return smooth(nu2);
+}
+
+ps_status begin_mg_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o, cudaStream_t s) {
+  ps_status r = build_hier(h, 0, &h->h64);
+  if (r != PS_OK) return r;
+  Hier* H = &h->h64;
+  double* phi = h->phi0;
+  H->lv[0].phi = phi;
+  const int order = o->compact_order;
+  auto C = std::make_shared<CompactLevels>();
+  for (int l = 0; l < h->nlev; l++) {
+    const double hl = H->lv[l].h[0];
+    C->A.push_back(l == 0 ? compact_lhs(order, hl) : galerkin27(C->A.back()));
+    const double* k = kSpai[order / 2 - 1];
+    C->M.push_back(W27{{k[1] * hl * hl, k[2] * hl * hl, k[3] * hl * hl, k[4] * hl * hl}});
+    C->omega.push_back(k[0]);
+  }
+  const int nb = c27_blocks(h->d0);
+  if ((r = ensure_partials(h, nb)) != PS_OK) return r;
+  double* b = h->fs64;
+  double* rr = (double*)H->lv[0].tmp;
+  // b = R_h (4 pi G rho); reference ||b - A u0|| (u0: boundary data only); initial residual
+  TRY((h->nlaunch += 1, launch_c27_rhs(h->d0, h->du, order, rho, 4.0 * M_PI * h->bc.G, b, s)));
+  TRY((h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, 1, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 0, h->st, s)));
+  TRY((h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, 0, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
+  const int nu1 = o->nu1, nu2 = o->nu2;
+  h->act.body = [h, H, C, phi, b, rr, nb, nu1, nu2](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    cudaError_t e = vcycle_compact(h, H, *C, 0, nu1, nu2, q);
+    const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+    if (e == cudaSuccess) {
+      prof_begin(h, PC_NORM0, n * 24.0, n * 17.0, 1, q);
+      e = (h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, 0, h->partials, h->st, q));
+      prof_end(h, q);
+    }
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, q, cond, chunk));
+    return e;
+  };
+  h->act.key = "mgc:" + std::to_string(order) + ":" + std::to_string(nu1) + ":" + std::to_string(nu2);
+  h->act.chunk = MG_CHUNK;
+  h->act.plain_chunk = 1;
   return PS_OK;
 }
 
@@ -1421,6 +1532,15 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   } else if (o.method == PS_MG) {
     if (h->nlev < 2) return fail(PS_ERR_INVALID_ARG, "multigrid needs all interval counts even and >= 16");
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1) return fail(PS_ERR_INVALID_ARG, "nu1, nu2 >= 0 with nu1 + nu2 >= 1");
+    if (o.compact_order != 0) {
+      if (o.compact_order != 2 && o.compact_order != 4 && o.compact_order != 6)
+        return fail(PS_ERR_INVALID_ARG, "compact_order must be 0, 2, 4 or 6 (got %d)", o.compact_order);
+      if (h->order != 2) return fail(PS_ERR_INVALID_ARG, "compact stencils need a handle created with stencil_order 2 (radius-one layout)");
+      if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "the compact-stencil multigrid runs in FP64");
+      if (!(std::fabs(h->h0[0] - h->h0[1]) <= 1e-14 * h->h0[0] && std::fabs(h->h0[1] - h->h0[2]) <= 1e-14 * h->h0[0]))
+        return fail(PS_ERR_INVALID_ARG, "compact stencils and SPAI smoothers need equal spacings on every axis");
+      if (c27_coarse_smem(h->dims.back()) > 200 * 1024) return fail(PS_ERR_INVALID_ARG, "coarsest level too large for the compact coarse CG");
+    }
   } else if (o.method == PS_SOR) {
     if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "SOR runs in FP64 only");
   } else if (o.method == PS_CG || o.method == PS_PCG) {
@@ -1445,7 +1565,8 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
     r = begin_sph(h, rho_dev, phi_dev, tol, &o, s);
   } else {
     if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, s)) != PS_OK) return r;
-    if (o.method == PS_MG) r = o.prec == PS_FP64 ? begin_mg64(h, &o, s) : begin_ir(h, &o, s);
+    if (o.method == PS_MG && o.compact_order != 0) r = begin_mg_compact(h, rho_dev, &o, s);
+    else if (o.method == PS_MG) r = o.prec == PS_FP64 ? begin_mg64(h, &o, s) : begin_ir(h, &o, s);
     else if (o.method == PS_SOR) r = begin_sor(h, &o, s);
     else if (o.method == PS_PCG) r = begin_pcg(h, s);
     else r = begin_cg(h, s);
