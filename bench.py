@@ -334,6 +334,53 @@ def other_configs(dev, reps=3):
     return out
 
 
+# ------------------------------------------------------------------ compact-stencil MG (Table 4's method)
+def compact_mg(dev, sizes=(256, 512), nus=(1, 2, 3), reps=2, precs=("fp64", "mixed_fp32")):
+    """The paper's sixth-order multigrid (Sec. 2.1.3: compact radius-one stencil,
+    SPAI smoothing with Table 1's coefficients, Galerkin coarse operators) on the
+    two-sphere problem of Sec. 3.1 (two (1 - w^2)^2 spheres, radii 0.08, masses 1
+    and 2, centred at z = 0.4 and -0.2 on [-1, 1]^3), multipole boundary l_max 4,
+    cold start to residual reduction 1e-6, as in Table 4: V-cycles, t_mp, t_iter,
+    t_s (per V-cycle) and s_s = (N-1)^3 / t_s; in FP64 and as FP64 refinement
+    around FP32 inner V-cycles (one refinement step = 2 inner V-cycles; t_s per
+    inner V-cycle)."""
+    import torch
+    import workloads as W
+    import paper_2605_03563_gb300 as P
+    out = {}
+    for n in sizes:
+        rho = torch.from_numpy(W.smooth_sphere_density(n, 2, [(0.0, 0.0, 0.4), (0.0, 0.0, -0.2)],
+                                                       [0.08, 0.08], [1.0, 2.0])).to(dev)
+        with P.CartesianSolver(n, 2, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), bc="multipole", lmax=4) as s:
+            for prec, nu in [(p_, nu_) for p_ in precs for nu_ in nus]:
+                phi = torch.zeros_like(rho)
+
+                def run():
+                    phi.zero_()
+                    return s.solve(rho, phi, tol=1e-6, method="mg", prec=prec, nu1=nu, nu2=nu, max_iter=40,
+                                   inner_cycles=2, compact_order=6)
+                run()
+                torch.cuda.synchronize()
+                ts, info = [], None
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    info = run()
+                    b.record()
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                ms = min(ts)
+                t_iter = ms - info.t_mp_ms
+                cyc = max(info.iterations * (2 if prec != "fp64" else 1), 1)
+                out[f"n{n - 1}_nu{nu}_{prec}"] = {
+                    "v_cycles": cyc, "steps": info.iterations, "converged": info.converged,
+                    "rel_residual": info.rel_residual, "time_to_1e-6_ms": ms, "t_mp_ms": info.t_mp_ms,
+                    "t_iter_ms": t_iter, "t_s_ms": t_iter / cyc, "rho_conv": info.rho_conv,
+                    "s_s_gzups": (n - 1) ** 3 / (t_iter / cyc / 1e3) / 1e9}
+        del rho
+    return out
+
+
 # ------------------------------------------------------------------ batched throughput
 def batched_throughput(dev, per_size=8, sizes=(32, 64, 96, 128, 192, 256), reps=2):
     """Solves/s to relative residual 1e-10 on a fixed set of grids of the serving

@@ -123,8 +123,10 @@ typedef struct {
                             the compact radius-one discretisation of that order (Sec. 2.1.3),
                             L_h phi = R_h (4 pi G rho), smoothed by the SPAI smoother of
                             Eq. richardson with Table 1's coefficients, Galerkin coarse
-                            operators R A P, coarsest level by CG; FP64 only.  The
-                            relative residual is ||R_h f - L_h phi|| / ||R_h f - L_h phi0||. */
+                            operators R A P, coarsest level by CG; PS_FP64, or
+                            PS_MIXED_FP32: FP64 refinement around FP32 inner V-cycles
+                            (inner_cycles per step).  The relative residual is
+                            ||R_h f - L_h phi|| / ||R_h f - L_h phi0||. */
   int32_t reserved_;     /* set to 0 */
 } ps_solve_opts;
 

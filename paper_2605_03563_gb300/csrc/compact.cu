@@ -23,6 +23,7 @@
 #include <cmath>
 #include <vector>
 
+#include "cart_kernels.cuh"
 #include "compact.cuh"
 #include "stencil.cuh"
 
@@ -86,19 +87,20 @@ W27 galerkin27(const W27& A) {
 }
 
 // in-plane sums of plane k at (i, j): centre, 4 faces, 4 diagonals
+template <typename C>
 struct Plane {
-  double c, f, e;
+  C c, f, e;
 };
 
-template <bool ZI>
-__device__ __forceinline__ Plane plane_sums(const Dims& d, const double* __restrict__ u, int i, int j, int k) {
+template <bool ZI, typename T, typename C = typename St<T>::C>
+__device__ __forceinline__ Plane<C> plane_sums(const Dims& d, const T* __restrict__ u, int i, int j, int k) {
   const long long sy = d.sy();
   const long long p = d.at(i, j, k);
-  auto ld = [&](long long q, int ii, int jj) -> double {
-    if (ZI && ii >= 1 && ii <= d.ni() && jj >= 1 && jj <= d.nj() && k >= 1 && k <= d.nk()) return 0.0;
-    return u[q];
+  auto ld = [&](long long q, int ii, int jj) -> C {
+    if (ZI && ii >= 1 && ii <= d.ni() && jj >= 1 && jj <= d.nj() && k >= 1 && k <= d.nk()) return (C)0;
+    return (C)u[q];
   };
-  Plane s;
+  Plane<C> s;
   s.c = ld(p, i, j);
   s.f = (ld(p - 1, i - 1, j) + ld(p + 1, i + 1, j)) + (ld(p - sy, i, j - 1) + ld(p + sy, i, j + 1));
   s.e = (ld(p - sy - 1, i - 1, j - 1) + ld(p - sy + 1, i + 1, j - 1)) +
@@ -106,7 +108,8 @@ __device__ __forceinline__ Plane plane_sums(const Dims& d, const double* __restr
   return s;
 }
 
-__device__ __forceinline__ double apply_planes(const double w[4], const Plane& m, const Plane& c, const Plane& p) {
+template <typename C>
+__device__ __forceinline__ C apply_planes(const C w[4], const Plane<C>& m, const Plane<C>& c, const Plane<C>& p) {
   return fma(w[0], c.c, fma(w[1], (c.f + (m.c + p.c)), fma(w[2], (c.e + (m.f + p.f)), w[3] * (m.e + p.e))));
 }
 
@@ -128,29 +131,34 @@ __device__ __forceinline__ void block_partial(double v, double* __restrict__ par
   }
 }
 
-// MODE 0: r = b - A u (ZI: u's interior read as 0), partials if given; MODE 1: u -= omega M r
-template <int MODE, bool ZI>
+// MODE 0: r = b - A u (ZI: u's interior read as 0; r stored as TR), partials if
+// given; MODE 1: u -= omega M r.  Arithmetic in the compute type of T (FP64 for
+// FP64 storage, FP32 for FP32 storage).
+template <int MODE, bool ZI, typename T, typename TR>
 __global__ void __launch_bounds__(CBX* CBY)
-    k_c27(Dims d, W27 W, double omega, const double* __restrict__ src, const double* __restrict__ b,
-          double* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
+    k_c27(Dims d, W27 W, double omega, const T* __restrict__ src, const T* __restrict__ b,
+          TR* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
+  using C = typename St<T>::C;
   if (st != nullptr && st->done) return;   // uniform
   const int i = blockIdx.x * CBX + threadIdx.x + 1;
   const int j = blockIdx.y * CBY + threadIdx.y + 1;
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
+  const C w[4] = {(C)W.w[0], (C)W.w[1], (C)W.w[2], (C)W.w[3]};
+  const C om = (C)omega;
   double s2 = 0.0;
   if (i <= d.ni() && j <= d.nj()) {
-    Plane pm = plane_sums<ZI>(d, src, i, j, k0 - 1);
-    Plane pc = plane_sums<ZI>(d, src, i, j, k0);
+    Plane<C> pm = plane_sums<ZI>(d, src, i, j, k0 - 1);
+    Plane<C> pc = plane_sums<ZI>(d, src, i, j, k0);
     for (int k = k0; k < k1; k++) {
-      const Plane pn = plane_sums<ZI>(d, src, i, j, k + 1);
-      const double a = apply_planes(W.w, pm, pc, pn);
+      const Plane<C> pn = plane_sums<ZI>(d, src, i, j, k + 1);
+      const C a = apply_planes<C>(w, pm, pc, pn);
       const long long q = d.at(i, j, k);
       if (MODE == 0) {
-        const double r = b[q] - a;
-        dst[q] = r;
-        s2 = fma(r, r, s2);
+        const C r = (C)b[q] - a;
+        dst[q] = (TR)r;
+        s2 = fma((double)r, (double)r, s2);
       } else {
-        dst[q] = fma(-omega, a, dst[q]);
+        dst[q] = (TR)fma(-om, a, (C)dst[q]);
       }
       pm = pc;
       pc = pn;
@@ -172,16 +180,46 @@ cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const
                              int zero_interior, double* partials, const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
   if (zero_interior)
-    k_c27<0, true><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+    k_c27<0, true, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
   else
-    k_c27<0, false><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+    k_c27<0, false, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void* u, const void* b, int dt_r,
+                                void* r, double* partials, const DevState* st, cudaStream_t s, int zero_interior) {
+  if (d.g != 1) return cudaErrorInvalidValue;
+  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  if (zero_interior && dt == DT_F64 && dt_r == DT_F32)
+    k_c27<0, true, double, float><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+  else if (zero_interior)
+    return cudaErrorInvalidValue;
+  else if (dt == DT_F64 && dt_r == DT_F64)
+    k_c27<0, false, double, double><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
+  else if (dt == DT_F64 && dt_r == DT_F32)
+    k_c27<0, false, double, float><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+  else if (dt == DT_F32 && dt_r == DT_F32)
+    k_c27<0, false, float, float><<<g, blk, 0, s>>>(d, A, 0.0, (const float*)u, (const float*)b, (float*)r, partials, st);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const double* r, double* u,
                             const DevState* st, cudaStream_t s) {
+  return launch_c27_spai_dt(d, M, omega, DT_F64, r, u, st, s);
+}
+
+cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt, const void* r, void* u,
+                               const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
-  k_c27<1, false><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, M, omega, r, nullptr, u, nullptr, st);
+  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  if (dt == DT_F64)
+    k_c27<1, false, double, double><<<g, blk, 0, s>>>(d, M, omega, (const double*)r, nullptr, (double*)u, nullptr, st);
+  else if (dt == DT_F32)
+    k_c27<1, false, float, float><<<g, blk, 0, s>>>(d, M, omega, (const float*)r, nullptr, (float*)u, nullptr, st);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -265,8 +303,9 @@ __device__ double ccg_sum(double v, double* red) {
   return red[32];
 }
 
+template <typename T>
 __global__ void __launch_bounds__(CCG_THREADS)
-    k_c27_coarse_cg(Dims d, W27 A, const double* __restrict__ b, double* __restrict__ u, double tol,
+    k_c27_coarse_cg(Dims d, W27 A, const T* __restrict__ b, T* __restrict__ u, double tol,
                     const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   extern __shared__ double sm[];
@@ -290,7 +329,7 @@ __global__ void __launch_bounds__(CCG_THREADS)
   __syncthreads();
   double loc = 0.0;
   for (int t = threadIdx.x; t < nu; t += blockDim.x) {
-    const double v = -b[gidx(t)];
+    const double v = -(double)b[gidx(t)];
     x[t] = 0.0;
     r[t] = v;
     p[node(t)] = v;
@@ -331,7 +370,7 @@ __global__ void __launch_bounds__(CCG_THREADS)
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < nu; t += blockDim.x) u[gidx(t)] = x[t];
+  for (int t = threadIdx.x; t < nu; t += blockDim.x) u[gidx(t)] = (T)x[t];
 }
 
 size_t c27_coarse_smem(const Dims& d) {
@@ -340,18 +379,31 @@ size_t c27_coarse_smem(const Dims& d) {
   return (nn + 3 * nu + 33) * sizeof(double);
 }
 
-cudaError_t launch_c27_coarse_cg(const Dims& d, const W27& A, const double* b, double* u, double tol,
-                                 const DevState* st, cudaStream_t s) {
+template <typename T>
+static cudaError_t coarse_cg_t(const Dims& d, const W27& A, const T* b, T* u, double tol, const DevState* st,
+                               cudaStream_t s) {
   const size_t smem = c27_coarse_smem(d);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static size_t opted = 0;
   if (smem > 48 * 1024 && smem > opted) {
-    cudaError_t e = cudaFuncSetAttribute(k_c27_coarse_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_c27_coarse_cg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     opted = smem;
   }
-  k_c27_coarse_cg<<<1, CCG_THREADS, smem, s>>>(d, A, b, u, tol, st);
+  k_c27_coarse_cg<T><<<1, CCG_THREADS, smem, s>>>(d, A, b, u, tol, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_c27_coarse_cg(const Dims& d, const W27& A, const double* b, double* u, double tol,
+                                 const DevState* st, cudaStream_t s) {
+  return coarse_cg_t<double>(d, A, b, u, tol, st, s);
+}
+
+cudaError_t launch_c27_coarse_cg_dt(const Dims& d, const W27& A, int dt, const void* b, void* u, double tol,
+                                    const DevState* st, cudaStream_t s) {
+  if (dt == DT_F64) return coarse_cg_t<double>(d, A, (const double*)b, (double*)u, tol, st, s);
+  if (dt == DT_F32) return coarse_cg_t<float>(d, A, (const float*)b, (float*)u, tol, st, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ps

@@ -36,4 +36,16 @@ cudaError_t launch_c27_coarse_cg(const Dims& d, const W27& A, const double* b, d
                                  const DevState* st, cudaStream_t s);
 size_t c27_coarse_smem(const Dims& d);
 
+// Storage-typed variants for the FP32 inner cycles of the refinement (dt: DT_F64
+// or DT_F32 storage of u and b, arithmetic in the matching precision; r may be
+// stored in FP32 from FP64 arithmetic -- the refinement's outer residual).
+cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void* u, const void* b, int dt_r,
+                                void* r, double* partials, const DevState* st, cudaStream_t s,
+                                int zero_interior = 0);
+cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt, const void* r, void* u,
+                               const DevState* st, cudaStream_t s);
+// coarsest CG in FP64 arithmetic on FP32 or FP64 storage
+cudaError_t launch_c27_coarse_cg_dt(const Dims& d, const W27& A, int dt, const void* b, void* u, double tol,
+                                    const DevState* st, cudaStream_t s);
+
 }  // namespace ps

@@ -718,45 +718,48 @@ struct CompactLevels {
 cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, int nu1, int nu2, cudaStream_t s) {
   Level& L = H->lv[l];
   const int last = (int)H->lv.size() - 1;
-  double* u = (double*)L.phi;
-  double* b = (double*)L.fs;
+  const int dt = L.dt;   // DT_F64 (FP64 multigrid) or DT_F32 (inner cycles of the refinement)
+  const double S = (double)dt_size(dt);
+  const int fp64 = dt == DT_F64;
+  void* u = L.phi;
+  void* b = L.fs;
   const DevState* st = h->st;
   cudaError_t e;
   if (l == last) {
     prof_begin(h, PC_COARSE, 0.0, 0.0, 1, s);
-    e = (h->nlaunch += 1, launch_c27_coarse_cg(L.d, C.A[l], b, u, kCompactCoarseTol, st, s));
+    e = (h->nlaunch += 1, launch_c27_coarse_cg_dt(L.d, C.A[l], dt, b, u, kCompactCoarseTol, st, s));
     prof_end(h, s);
     return e;
   }
-  double* r = (double*)L.tmp;
+  void* r = L.tmp;
   const double n = (double)L.d.ni() * L.d.nj() * L.d.nk();
   auto smooth = [&](int steps) -> cudaError_t {
     for (int it = 0; it < steps; it++) {
-      prof_begin(h, l == 0 ? PC_DELTA0 : PC_SWEEP_C, n * 24.0, n * 16.0, 1, s);
-      cudaError_t e2 = (h->nlaunch += 1, launch_c27_resid(L.d, C.A[l], u, b, r, 0, nullptr, st, s));
+      prof_begin(h, l == 0 ? PC_DELTA0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
+      cudaError_t e2 = (h->nlaunch += 1, launch_c27_resid_dt(L.d, C.A[l], dt, u, b, dt, r, nullptr, st, s));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
-      prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 24.0, n * 16.0, 1, s);
-      e2 = (h->nlaunch += 1, launch_c27_spai(L.d, C.M[l], C.omega[l], r, u, st, s));
+      prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
+      e2 = (h->nlaunch += 1, launch_c27_spai_dt(L.d, C.M[l], C.omega[l], dt, r, u, st, s));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
     }
     return cudaSuccess;
   };
   if ((e = smooth(nu1)) != cudaSuccess) return e;
-  if (l == 0) prof_begin(h, PC_DELTA0, n * 24.0, n * 16.0, 1, s);
-  e = (h->nlaunch += 1, launch_c27_resid(L.d, C.A[l], u, b, r, 0, nullptr, st, s));
+  if (l == 0) prof_begin(h, PC_DELTA0, n * 3.0 * S, n * 16.0, fp64, s);
+  e = (h->nlaunch += 1, launch_c27_resid_dt(L.d, C.A[l], dt, u, b, dt, r, nullptr, st, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
   Level& Cl = H->lv[l + 1];
-  if (l == 0) prof_begin(h, PC_RESTRICT0, n * 8.0 + n, n * 4.5, 1, s);
-  e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, DT_F64, r, DT_F64, Cl.fs, 1.0, s));
+  if (l == 0) prof_begin(h, PC_RESTRICT0, n * S * 9.0 / 8.0, n * 4.5, fp64, s);
+  e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, dt, r, Cl.dt, Cl.fs, 1.0, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(Cl.phi, 0, (size_t)Cl.d.size() * sizeof(double), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(Cl.phi, 0, (size_t)Cl.d.size() * dt_size(Cl.dt), s)) != cudaSuccess) return e;
   if ((e = vcycle_compact(h, H, C, l + 1, nu1, nu2, s)) != cudaSuccess) return e;
-  if (l == 0) prof_begin(h, PC_PROLONG0, n * 16.0 + n, n * 4.0, 1, s);
-  e = (h->nlaunch += 1, launch_prolong(L.d, Cl.d, DT_F64, Cl.phi, DT_F64, u, s));
+  if (l == 0) prof_begin(h, PC_PROLONG0, n * S * 17.0 / 8.0, n * 4.0, fp64, s);
+  e = (h->nlaunch += 1, launch_prolong(L.d, Cl.d, Cl.dt, Cl.phi, dt, u, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
   return smooth(nu2);
@@ -800,6 +803,63 @@ ps_status begin_mg_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
     return e;
   };
   h->act.key = "mgc:" + std::to_string(order) + ":" + std::to_string(nu1) + ":" + std::to_string(nu2);
+  h->act.chunk = MG_CHUNK;
+  h->act.plain_chunk = 1;
+  return PS_OK;
+}
+
+// Compact multigrid inside FP64 iterative refinement: the outer residual
+// r = R_h f - L_h phi in FP64 (stored as the FP32 right-hand side of the inner
+// cycles), inner V-cycles on L e = r in FP32 storage and arithmetic (the
+// 27-point passes are then bound by HBM instead of the FP64 pipe; coarsest CG in
+// FP64 arithmetic), phi += e in FP64.  The stopping test is on the FP64 outer
+// residual, as for the FP64 multigrid.
+ps_status begin_ir_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o, cudaStream_t s) {
+  Hier* H = &h->hmx[0];
+  ps_status r = build_hier(h, 1, H);
+  if (r != PS_OK) return r;
+  const int order = o->compact_order;
+  auto C = std::make_shared<CompactLevels>();
+  for (int l = 0; l < h->nlev; l++) {
+    const double hl = H->lv[l].h[0];
+    C->A.push_back(l == 0 ? compact_lhs(order, hl) : galerkin27(C->A.back()));
+    const double* k = kSpai[order / 2 - 1];
+    C->M.push_back(W27{{k[1] * hl * hl, k[2] * hl * hl, k[3] * hl * hl, k[4] * hl * hl}});
+    C->omega.push_back(k[0]);
+  }
+  const int nb = c27_blocks(h->d0);
+  if ((r = ensure_partials(h, nb)) != PS_OK) return r;
+  double* phi = h->phi0;
+  double* b64 = h->fs64;
+  Level& L0 = H->lv[0];
+  TRY((h->nlaunch += 1, launch_c27_rhs(h->d0, h->du, order, rho, 4.0 * M_PI * h->bc.G, b64, s)));
+  TRY((h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], DT_F64, phi, b64, DT_F32, L0.fs, h->partials, nullptr, s, 1)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 0, h->st, s)));
+  TRY((h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], DT_F64, phi, b64, DT_F32, L0.fs, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
+  const int nu1 = o->nu1, nu2 = o->nu2, inner = std::max(1, o->inner_cycles);
+  h->act.inner_per_iter = inner;
+  h->act.body = [h, H, C, phi, b64, nb, nu1, nu2, inner](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+    Level& L = H->lv[0];
+    cudaError_t e = cudaMemsetAsync(L.phi, 0, (size_t)L.d.size() * sizeof(float), q);
+    for (int c = 0; c < inner && e == cudaSuccess; c++) e = vcycle_compact(h, H, *C, 0, nu1, nu2, q);
+    const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+    if (e == cudaSuccess) {
+      prof_begin(h, PC_CORRECT0, n * 20.0, n, 1, q);
+      // the partials carry no max, so the state keeps scale 1 and e is added unscaled
+      e = (h->nlaunch += 1, launch_correct(h->d0, DT_F32, L.phi, 1.0, phi, h->st, q));
+      prof_end(h, q);
+    }
+    if (e == cudaSuccess) {
+      prof_begin(h, PC_NORM0, n * 20.0, n * 17.0, 1, q);
+      e = (h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], DT_F64, phi, b64, DT_F32, L.fs, h->partials, h->st, q));
+      prof_end(h, q);
+    }
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, q, cond, chunk));
+    return e;
+  };
+  h->act.key = "irc:" + std::to_string(order) + ":" + std::to_string(nu1) + ":" + std::to_string(nu2) + ":" +
+               std::to_string(inner);
   h->act.chunk = MG_CHUNK;
   h->act.plain_chunk = 1;
   return PS_OK;
@@ -1536,7 +1596,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
       if (o.compact_order != 2 && o.compact_order != 4 && o.compact_order != 6)
         return fail(PS_ERR_INVALID_ARG, "compact_order must be 0, 2, 4 or 6 (got %d)", o.compact_order);
       if (h->order != 2) return fail(PS_ERR_INVALID_ARG, "compact stencils need a handle created with stencil_order 2 (radius-one layout)");
-      if (o.prec != PS_FP64) return fail(PS_ERR_UNSUPPORTED, "the compact-stencil multigrid runs in FP64");
+      if (o.prec == PS_MIXED_BF16) return fail(PS_ERR_UNSUPPORTED, "the compact-stencil multigrid runs in FP64 or with FP32 refinement");
       if (!(std::fabs(h->h0[0] - h->h0[1]) <= 1e-14 * h->h0[0] && std::fabs(h->h0[1] - h->h0[2]) <= 1e-14 * h->h0[0]))
         return fail(PS_ERR_INVALID_ARG, "compact stencils and SPAI smoothers need equal spacings on every axis");
       if (c27_coarse_smem(h->dims.back()) > 200 * 1024) return fail(PS_ERR_INVALID_ARG, "coarsest level too large for the compact coarse CG");
@@ -1565,7 +1625,8 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
     r = begin_sph(h, rho_dev, phi_dev, tol, &o, s);
   } else {
     if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, s)) != PS_OK) return r;
-    if (o.method == PS_MG && o.compact_order != 0) r = begin_mg_compact(h, rho_dev, &o, s);
+    if (o.method == PS_MG && o.compact_order != 0)
+      r = o.prec == PS_FP64 ? begin_mg_compact(h, rho_dev, &o, s) : begin_ir_compact(h, rho_dev, &o, s);
     else if (o.method == PS_MG) r = o.prec == PS_FP64 ? begin_mg64(h, &o, s) : begin_ir(h, &o, s);
     else if (o.method == PS_SOR) r = begin_sor(h, &o, s);
     else if (o.method == PS_PCG) r = begin_pcg(h, s);
