@@ -718,9 +718,11 @@ def main():
         cpu = cpu_baseline_sample()
     configs = None
     batched = None
+    compact = None
     if rank == 0 and not args.no_configs:
         configs = other_configs(dev)
         batched = batched_throughput(dev)
+        compact = compact_mg(dev)
 
     solver.close()
     if rank == 0:
@@ -743,6 +745,7 @@ def main():
             "mixed": mixed,
             "other_configs": configs,
             "batched": batched,
+            "compact_mg_table4": compact,
             "roofline": roof,
             "kernels": kernels,
             "profiled_region_ms_per_step": prof_region_ms,

@@ -134,7 +134,9 @@ __device__ __forceinline__ void block_partial(double v, double* __restrict__ par
 // MODE 0: r = b - A u (ZI: u's interior read as 0; r stored as TR), partials if
 // given; MODE 1: u -= omega M r.  Arithmetic in the compute type of T (FP64 for
 // FP64 storage, FP32 for FP32 storage).
-template <int MODE, bool ZI, typename T, typename TR>
+// NORM: the residual pass also forms per-block partials of r^2 (in FP64; FP32
+// inner passes skip it, so they touch no FP64 instruction).
+template <int MODE, bool ZI, typename T, typename TR, bool NORM = true>
 __global__ void __launch_bounds__(CBX* CBY)
     k_c27(Dims d, W27 W, double omega, const T* __restrict__ src, const T* __restrict__ b,
           TR* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(CBX* CBY)
       if (MODE == 0) {
         const C r = (C)b[q] - a;
         dst[q] = (TR)r;
-        s2 = fma((double)r, (double)r, s2);
+        if (NORM) s2 = fma((double)r, (double)r, s2);
       } else {
         dst[q] = (TR)fma(-om, a, (C)dst[q]);
       }
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(CBX* CBY)
       pc = pn;
     }
   }
-  if (MODE == 0 && partials != nullptr) block_partial(s2, partials);
+  if (MODE == 0 && NORM && partials != nullptr) block_partial(s2, partials);
 }
 
 static dim3 c27_grid(const Dims& d) {
@@ -198,6 +200,8 @@ cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void*
     k_c27<0, false, double, double><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
   else if (dt == DT_F64 && dt_r == DT_F32)
     k_c27<0, false, double, float><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+  else if (dt == DT_F32 && dt_r == DT_F32 && partials == nullptr)
+    k_c27<0, false, float, float, false><<<g, blk, 0, s>>>(d, A, 0.0, (const float*)u, (const float*)b, (float*)r, nullptr, st);
   else if (dt == DT_F32 && dt_r == DT_F32)
     k_c27<0, false, float, float><<<g, blk, 0, s>>>(d, A, 0.0, (const float*)u, (const float*)b, (float*)r, partials, st);
   else
