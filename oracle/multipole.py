@@ -15,6 +15,13 @@ P_l^m is the associated Legendre function without the Condon-Shortley phase
 index l*l + l + m.  Here this is evaluated directly per node in spherical
 coordinates about the expansion origin.
 
+Eq. inner_multipole / Eq. inner_expansion (spherical grids with r_in > 0):
+    qbar_lm = sum_cells dV sqrt(4 pi/(2l+1)) rho(x') r'^-(l+1) Y_lm(x'),
+    Phi(x) = -G sum qbar_lm r^l sqrt(4 pi/(2l+1)) Y_lm(x),
+the expansion of the potential inside the innermost mass, written on the inner
+ghost shell r_{-1} = 2 r_0 - r_1 when the inner boundary is this one instead of
+the Neumann mirror.
+
 Cartesian grids: the sum runs over interior nodes with dV = hx hy hz; the
 potential is written on every non-interior node (the boundary layer and, for
 the 13-point stencil, the ghost layer).  Spherical grids: dV = r^2 sin(theta)
@@ -193,3 +200,74 @@ def spherical_outer_ghost(q: np.ndarray, r, th, ph, lmax: int, G: float) -> np.n
     dy = rN * np.sin(T) * np.sin(P)
     dz = rN * np.cos(T)
     return potential_points(q, dx, dy, dz, lmax, G)
+
+
+# ---------------------------------------------------------------- inner expansion (spherical)
+
+def inner_moments_points(values_dv: np.ndarray, dx, dy, dz, lmax: int) -> np.ndarray:
+    """Eq. inner_multipole: qbar_lm = sum (rho dV) sqrt(4pi/(2l+1)) r^-(l+1) Y_lm."""
+    r, theta, phi = _spherical(dx, dy, dz)
+    Y = real_sph_harm(lmax, theta, phi)
+    q = np.zeros((lmax + 1) ** 2)
+    for l in range(lmax + 1):
+        fac = math.sqrt(4 * math.pi / (2 * l + 1))
+        rl = r ** (-(l + 1))
+        for m in range(-l, l + 1):
+            q[idx(l, m)] = np.sum(values_dv * fac * rl * Y[idx(l, m)])
+    return q
+
+
+def inner_potential_points(qbar: np.ndarray, dx, dy, dz, lmax: int, G: float) -> np.ndarray:
+    """Eq. inner_expansion at points given relative to the origin."""
+    r, theta, phi = _spherical(dx, dy, dz)
+    Y = real_sph_harm(lmax, theta, phi)
+    out = np.zeros_like(r)
+    for l in range(lmax + 1):
+        fac = math.sqrt(4 * math.pi / (2 * l + 1))
+        rl = r ** l
+        for m in range(-l, l + 1):
+            out += qbar[idx(l, m)] * rl * fac * Y[idx(l, m)]
+    return -G * out
+
+
+def _spherical_cells(rho, r, th, ph):
+    re = radial_extended(r)
+    dr = 0.5 * (re[2:] - re[:-2])
+    dth = math.pi / th.size
+    dph = 2.0 * math.pi / ph.size
+    P, T, R = np.meshgrid(ph, th, r, indexing="ij")
+    dV = R * R * np.sin(T) * np.broadcast_to(dr[None, None, :], R.shape) * dth * dph
+    return (rho[1:-1, 1:-1, 1:-1] * dV, R * np.sin(T) * np.cos(P), R * np.sin(T) * np.sin(P),
+            R * np.cos(T))
+
+
+def inner_moments_spherical(rho: np.ndarray, r, th, ph, lmax: int) -> np.ndarray:
+    vals, dx, dy, dz = _spherical_cells(rho, r, th, ph)
+    return inner_moments_points(vals, dx, dy, dz, lmax)
+
+
+def spherical_inner_ghost(qbar: np.ndarray, r, th, ph, lmax: int, G: float) -> np.ndarray:
+    """Potential on the inner ghost shell r_{-1}, shape (Nphi, Ntheta)."""
+    r0 = radial_extended(r)[0]
+    P, T = np.meshgrid(ph, th, indexing="ij")
+    return inner_potential_points(qbar, r0 * np.sin(T) * np.cos(P), r0 * np.sin(T) * np.sin(P),
+                                  r0 * np.cos(T), lmax, G)
+
+
+def direct_legendre_inner(vals, src, lmax: int, G: float, points) -> np.ndarray:
+    """Independent form of the truncated inner expansion via the addition
+    theorem: -G sum rho dV sum_{l<=lmax} r^l / r'^(l+1) P_l(cos gamma)."""
+    rs = np.linalg.norm(src, axis=1)
+    out = []
+    for p in points:
+        p = np.asarray(p, dtype=np.float64)
+        rp = np.linalg.norm(p)
+        cg = src @ p / (rs * rp)
+        total = 0.0
+        for l in range(lmax + 1):
+            c = np.zeros(l + 1)
+            c[l] = 1.0
+            total += np.sum(vals * rp ** l / rs ** (l + 1) * np.polynomial.legendre.legval(cg, c))
+        out.append(-G * total)
+    return np.array(out)
+

@@ -100,15 +100,19 @@ def solve_cartesian(rho: np.ndarray, phi: np.ndarray, grid: CartGrid, method: st
 def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
                     max_iter: int = 20000, G: float = 1.0, bc: str = "multipole",
                     lmax: int = 6, exact_dots: bool = False, method: str = "bicgstab",
-                    omega: float = 1.0, sor_schedule: str = "chebyshev") -> SolveInfo:
+                    omega: float = 1.0, sor_schedule: str = "chebyshev",
+                    inner_bc: str = "neumann") -> SolveInfo:
     """Right-Jacobi BiCGSTAB (or red-black SOR) on the spherical grid; phi in
     the ghosted layout."""
-    op = SphericalOperator(r, th, ph)
+    op = SphericalOperator(r, th, ph, inner="dirichlet" if inner_bc == "multipole" else "neumann")
     f = 4.0 * math.pi * G * rho
     q = None
     if bc == "multipole":
         q = multipole.moments_spherical(rho, r, th, ph, lmax)
         phi[1:-1, 1:-1, -1] = multipole.spherical_outer_ghost(q, r, th, ph, lmax, G)
+    if inner_bc == "multipole":
+        qb = multipole.inner_moments_spherical(rho, r, th, ph, lmax)
+        phi[1:-1, 1:-1, 0] = multipole.spherical_inner_ghost(qb, r, th, ph, lmax, G)
     if method == "sor":
         it, conv, hist = sor_solve_spherical(phi, f, op, tol, max_iter, sor_schedule, omega)
         return SolveInfo(it, conv, hist[-1], multigrid.convergence_factor(hist), hist, q)

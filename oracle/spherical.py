@@ -12,7 +12,8 @@ phi_k = 2 pi k / Nphi:
 with r_{i+-1/2} the arithmetic midpoints and sin(t_{-1/2}) = sin(t_{Nt-1/2}) = 0
 at the poles (Sec. 2.2: angular boundaries follow the coordinate symmetries;
 phi is periodic).  The operator is not symmetric, hence BiCGSTAB (Sec. 2.1.2).
-Inner boundary: Neumann by a mirror ghost P_{-1} = P_1 at r_{-1} = 2 r_0 - r_1.
+Inner boundary: Neumann by a mirror ghost P_{-1} = P_1 at r_{-1} = 2 r_0 - r_1,
+or Dirichlet data on that ghost shell (the inner multipole expansion).
 Outer boundary: Dirichlet ghost at r_N (multipole potential or given data).
 
 Layout: (Nphi+2, Ntheta+2, Nr+2), r fastest, node (i,j,k) at [k+1, j+1, i+1].
@@ -28,7 +29,13 @@ from .multipole import radial_extended
 
 
 class SphericalOperator:
-    def __init__(self, r, th, ph):
+    """inner = "neumann": mirror ghost P_{-1} = P_1; "dirichlet": the inner ghost
+    shell holds data (the inner multipole expansion of Sec. 2.2)."""
+
+    def __init__(self, r, th, ph, inner: str = "neumann"):
+        if inner not in ("neumann", "dirichlet"):
+            raise ValueError(inner)
+        self.inner = inner
         self.r = np.asarray(r, dtype=np.float64)
         self.th = np.asarray(th, dtype=np.float64)
         self.ph = np.asarray(ph, dtype=np.float64)
@@ -49,7 +56,8 @@ class SphericalOperator:
 
     def fill_ghosts(self, P: np.ndarray) -> None:
         """Inner mirror and periodic phi ghosts (outer ghost untouched)."""
-        P[:, :, 0] = P[:, :, 2]
+        if self.inner == "neumann":
+            P[:, :, 0] = P[:, :, 2]
         P[0, :, :] = P[self.np_, :, :]
         P[self.np_ + 1, :, :] = P[1, :, :]
 
@@ -105,6 +113,8 @@ def bicgstab_solve(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator, tol
 
     bdry = np.zeros(op.shape)
     bdry[:, :, -1] = Pfield[:, :, -1]
+    if op.inner == "dirichlet":
+        bdry[:, :, 0] = Pfield[:, :, 0]
     b = (f[U] - op.apply(bdry)).ravel()
     ref = float(np.sqrt(b @ b))
     if ref == 0.0:
@@ -171,6 +181,8 @@ def sor_solve_spherical(Pfield: np.ndarray, f: np.ndarray, op: SphericalOperator
     U = (slice(1, -1), slice(1, -1), slice(1, -1))
     bdry = np.zeros(op.shape)
     bdry[:, :, -1] = Pfield[:, :, -1]
+    if op.inner == "dirichlet":
+        bdry[:, :, 0] = Pfield[:, :, 0]
     b = f[U] - op.apply(bdry)
     ref = float(np.sqrt(np.sum(b * b)))
     if ref == 0.0:

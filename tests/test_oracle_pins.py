@@ -854,3 +854,92 @@ def test_compact_mg_matches_dense_solve():
     it, conv, hist = CP.mg_solve(phi, f, g, 6, 1e-13, 60)
     assert conv
     assert np.max(np.abs(phi[g.interior].ravel() - x)) <= 1e-11 * np.max(np.abs(x))
+
+
+# ------------------------------------------------------------------ inner multipole boundary (spherical)
+
+def test_inner_expansion_matches_addition_theorem():
+    """Eqs. inner_multipole / inner_expansion against the independent
+    addition-theorem form -G sum rho dV sum_l r^l / r'^(l+1) P_l(cos gamma), for
+    masses outside radius 0.5 and points inside radius 0.3."""
+    gen = W.rng(23)
+    n = 400
+    d = gen.standard_normal((n, 3))
+    src = d / np.linalg.norm(d, axis=1)[:, None] * gen.uniform(0.5, 1.0, n)[:, None]
+    vals = gen.uniform(0.1, 1.0, n)
+    pts = gen.standard_normal((12, 3))
+    pts = pts / np.linalg.norm(pts, axis=1)[:, None] * gen.uniform(0.05, 0.3, 12)[:, None]
+    lmax = 6
+    qb = MP.inner_moments_points(vals, src[:, 0], src[:, 1], src[:, 2], lmax)
+    got = MP.inner_potential_points(qb, pts[:, 0], pts[:, 1], pts[:, 2], lmax, 1.0)
+    ref = MP.direct_legendre_inner(vals, src, lmax, 1.0, pts)
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+def test_inner_expansion_converges_to_green_sum():
+    """Inside the innermost mass the truncated inner expansion approaches the
+    direct Green's sum -G sum rho dV / |x - x'| as l_max grows."""
+    gen = W.rng(24)
+    c = np.array([0.0, 0.3, 0.6])
+    src = c + 0.05 * gen.standard_normal((300, 3))
+    vals = np.full(300, 1.0 / 300)
+    pts = np.array([[0.05, 0.0, 0.0], [0.0, -0.1, 0.05], [0.08, 0.08, -0.08]])
+    ref = np.array([-np.sum(vals / np.linalg.norm(src - p, axis=1)) for p in pts])
+    errs = []
+    for lmax in (1, 3, 6):
+        qb = MP.inner_moments_points(vals, src[:, 0], src[:, 1], src[:, 2], lmax)
+        got = MP.inner_potential_points(qb, pts[:, 0], pts[:, 1], pts[:, 2], lmax, 1.0)
+        errs.append(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3, errs
+
+
+def test_bicgstab_with_inner_dirichlet_ghost_matches_dense():
+    r, th, ph = W.spherical_coords(6, 6, 8, 0.1, 1.0)
+    op = SP.SphericalOperator(r, th, ph, inner="dirichlet")
+    nunk = 6 * 6 * 8
+    A = np.zeros((nunk, nunk))
+    for c in range(nunk):
+        e = np.zeros(op.shape)
+        e[1:-1, 1:-1, 1:-1].flat[c] = 1.0
+        A[:, c] = op.apply(e).ravel()
+    gen = W.rng(25)
+    rho = W.spherical_density(r, th, ph)
+    f = 4 * math.pi * rho
+    phi = np.zeros(op.shape)
+    phi[:, :, -1] = -1.0
+    phi[1:-1, 1:-1, 0] = gen.uniform(-3.0, -2.0, (8, 6))
+    phi[0] = phi[8]
+    phi[9] = phi[1]
+    bd = phi.copy()
+    bd[1:-1, 1:-1, 1:-1] = 0.0
+    x = np.linalg.solve(A, f[1:-1, 1:-1, 1:-1].ravel() - op.apply(bd).ravel())
+    res = SP.bicgstab_solve(phi, f, op, 1e-13, 2000)
+    assert res.converged
+    np.testing.assert_allclose(phi[1:-1, 1:-1, 1:-1].ravel(), x, rtol=1e-10)
+
+
+def test_spherical_inner_multipole_shell_closed_form_second_order():
+    """A smooth shell rho = sin^2(pi (r-a)/(b-a)) on a < r < b inside the grid,
+    inner and outer multipole boundaries: the potential converges at second
+    order in the radial spacing to -G [M(r)/r + 4 pi int_r^inf rho r' dr']
+    (quadrature), the exact exterior/interior solution of a spherical shell."""
+    from scipy.integrate import quad
+    a, b, r_in, r_out = 0.3, 0.8, 0.2, 1.0
+    rho_r = lambda x: math.sin(math.pi * (x - a) / (b - a)) ** 2 if a < x < b else 0.0
+    def exact(x):
+        m = 4 * math.pi * quad(lambda t: rho_r(t) * t * t, a, min(max(x, a), b), limit=200)[0]
+        o = 4 * math.pi * quad(lambda t: rho_r(t) * t, max(min(x, b), a), b, limit=200)[0]
+        return -(m / x + o)
+    errs = []
+    for nr, nt in ((32, 8), (64, 16)):   # the moments' theta quadrature is second order too
+        r = r_in + (r_out - r_in) * (np.arange(nr) + 0.5) / nr
+        th = (np.arange(nt) + 0.5) * math.pi / nt
+        ph = 2 * math.pi * np.arange(8) / 8
+        rho = np.zeros((10, nt + 2, nr + 2))
+        rho[1:-1, 1:-1, 1:-1] = np.array([rho_r(x) for x in r])[None, None, :]
+        phi = np.zeros(rho.shape)
+        info = S.solve_spherical(rho, phi, r, th, ph, 1e-12, max_iter=4000, lmax=2, inner_bc="multipole")
+        assert info.converged
+        ex = np.array([exact(x) for x in r])
+        errs.append(np.max(np.abs(phi[1:-1, 1:-1, 1:-1] - ex[None, None, :])) / np.max(np.abs(ex)))
+    assert 3.0 <= errs[0] / errs[1] <= 5.0, errs
