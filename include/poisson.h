@@ -66,7 +66,14 @@ typedef struct {
 } ps_grid;
 
 typedef enum { PS_BC_DIRICHLET_GIVEN = 0, PS_BC_MULTIPOLE = 1 } ps_outer_bc;
-typedef enum { PS_INNER_NONE = 0, PS_INNER_NEUMANN = 1 } ps_inner_bc;
+/* Inner radial boundary of a spherical grid (Cartesian grids take PS_INNER_NONE):
+ * PS_INNER_NEUMANN: mirror ghost Phi_{-1} = Phi_1 at r_{-1} = 2 r_0 - r_1;
+ * PS_INNER_MULTIPOLE: Dirichlet ghost at r_{-1} from the inner expansion
+ *   Phi = -G sum qbar_lm r^l sqrt(4 pi/(2l+1)) Y_lm (Eq. inner_expansion) with
+ *   qbar_lm = sum rho dV sqrt(4 pi/(2l+1)) Y_lm / r'^(l+1) (Eq. inner_multipole)
+ *   over the unknown nodes (Sec. 2.2, for r_in > 0; zero-pad the density near
+ *   r_in for accuracy).  Needs l_max >= 0 and r_{-1} > 0. */
+typedef enum { PS_INNER_NONE = 0, PS_INNER_NEUMANN = 1, PS_INNER_MULTIPOLE = 2 } ps_inner_bc;
 
 /* origin: expansion centre of the multipole boundary (Cartesian; Sec. 2.2
  * recommends keeping it near the centre of mass); the spherical grid always

@@ -199,10 +199,12 @@ class CartesianSolver(_Handle):
 
 class SphericalSolver(_Handle):
     """Spherical grid with node coordinates r (increasing), theta_j = (j+1/2) pi/Nt,
-    phi_k = 2 pi k/Np; Neumann inner boundary, multipole or given outer boundary.
+    phi_k = 2 pi k/Np; Neumann or multipole inner boundary, multipole or given outer boundary.
     Fields are float64 tensors of shape (Np+2, Nt+2, Nr+2) (r fastest)."""
 
-    def __init__(self, r, theta, phi, bc="multipole", lmax=6, G=1.0):
+    def __init__(self, r, theta, phi, bc="multipole", lmax=6, G=1.0, inner="neumann"):
+        """inner: "neumann" (mirror ghost) or "multipole" (Dirichlet ghost from the inner
+        expansion of Sec. 2.2)."""
         super().__init__()
         import numpy as np
         self._coords = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (r, theta, phi)]
@@ -211,7 +213,8 @@ class SphericalSolver(_Handle):
         grid = capi.make_grid(self.n, kind=capi.PS_GRID_SPHERICAL)
         ptrs = (C.c_void_p * 3)(*[a.ctypes.data for a in self._coords])
         b = capi.PsBC(capi.PS_BC_MULTIPOLE if bc == "multipole" else capi.PS_BC_DIRICHLET_GIVEN,
-                      capi.PS_INNER_NEUMANN, (C.c_double * 3)(0, 0, 0), float(G))
+                      capi.PS_INNER_MULTIPOLE if inner == "multipole" else capi.PS_INNER_NEUMANN,
+                      (C.c_double * 3)(0, 0, 0), float(G))
         self.multipole = bc == "multipole"
         check(lib().poisson_create(C.byref(grid), C.cast(ptrs, C.POINTER(C.c_void_p)), 2,
                                    C.byref(b), lmax, C.byref(self._h)), "poisson_create")

@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_UNSUPPORTED", 3:
                 4: "PS_ERR_CUDA", 5: "PS_NOT_CONVERGED", 6: "PS_DIVERGED", 7: "PS_ERR_TIMEOUT"}
 PS_GRID_CART_UNIFORM, PS_GRID_SPHERICAL = 0, 1
 PS_BC_DIRICHLET_GIVEN, PS_BC_MULTIPOLE = 0, 1
-PS_INNER_NONE, PS_INNER_NEUMANN = 0, 1
+PS_INNER_NONE, PS_INNER_NEUMANN, PS_INNER_MULTIPOLE = 0, 1, 2
 PS_SOR, PS_CG, PS_MG, PS_BICGSTAB, PS_PCG = 0, 1, 2, 3, 4
 PS_FP64, PS_MIXED_FP32, PS_MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2

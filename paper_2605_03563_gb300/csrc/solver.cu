@@ -1023,10 +1023,11 @@ ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, 
                     cudaStream_t s) {
   ps_status r;
   TRY(cudaEventRecord(h->ev[0], s));
-  if (h->bc.outer == PS_BC_MULTIPOLE) {
-    TRY((h->nlaunch += 2, launch_sph_moments(h->sd, h->stab, rho, s)));
-    TRY((h->nlaunch += 1, launch_sph_face(h->sd, h->stab, h->bc.G, phi_user, s)));
-  }
+  const bool inner_mp = h->bc.inner == PS_INNER_MULTIPOLE;
+  if (h->bc.outer == PS_BC_MULTIPOLE || inner_mp)
+    TRY((h->nlaunch += inner_mp ? 3 : 2, launch_sph_moments(h->sd, h->stab, rho, s)));
+  if (h->bc.outer == PS_BC_MULTIPOLE) TRY((h->nlaunch += 1, launch_sph_face(h->sd, h->stab, h->bc.G, phi_user, s)));
+  if (inner_mp) TRY((h->nlaunch += 1, launch_sph_face_inner(h->sd, h->stab, h->bc.G, phi_user, s)));
   TRY(cudaEventRecord(h->ev[1], s));
   double* phi = h->phi0;
   TRY(cudaMemcpyAsync(phi, phi_user, (size_t)h->sd.size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1454,7 +1455,9 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
       const double want = 2.0 * M_PI * k / np;
       if (std::fabs(coords_host[2][k] - want) > 1e-9) return fail(PS_ERR_INVALID_ARG, "phi_k must be 2 pi k / Nphi");
     }
-    if (b.inner != PS_INNER_NEUMANN) return fail(PS_ERR_UNSUPPORTED, "spherical grids support the Neumann inner boundary only");
+    if (b.inner != PS_INNER_NEUMANN && b.inner != PS_INNER_MULTIPOLE)
+      return fail(PS_ERR_UNSUPPORTED, "spherical grids take the Neumann or the multipole inner boundary");
+    if (b.inner == PS_INNER_MULTIPOLE && l_max < 0) return fail(PS_ERR_INVALID_ARG, "the multipole inner boundary needs l_max >= 0");
   } else {
     return fail(PS_ERR_INVALID_ARG, "unknown grid kind %d", grid->kind);
   }
@@ -1516,8 +1519,12 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
     h->sd.nr = grid->n[0];
     h->sd.nt = grid->n[1];
     h->sd.np = grid->n[2];
+    const bool inner_mp = b.inner == PS_INNER_MULTIPOLE;
+    h->sd.inner_ghost = inner_mp ? 1 : 0;
+    if (inner_mp && !(2.0 * coords_host[0][0] - coords_host[0][1] > 0.0))
+      return bail(fail(PS_ERR_INVALID_ARG, "the multipole inner boundary needs the ghost radius 2 r_0 - r_1 > 0"));
     if ((e = sph_tables_build(h->sd, coords_host[0], coords_host[1], coords_host[2],
-                              b.outer == PS_BC_MULTIPOLE ? l_max : -1, &h->stab)) != cudaSuccess)
+                              b.outer == PS_BC_MULTIPOLE || inner_mp ? l_max : -1, &h->stab, inner_mp)) != cudaSuccess)
       return bail(fail(PS_ERR_OOM, "spherical tables: %s", cudaGetErrorString(e)));
     h->bytes += h->stab.bytes;
     if ((s = alloc_zero((void**)&h->phi0, (size_t)h->sd.size() * 8, &h->bytes)) != PS_OK) return bail(s);

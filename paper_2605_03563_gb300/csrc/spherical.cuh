@@ -11,6 +11,7 @@ namespace ps {
 // ((k+1)*(nt+2) + (j+1))*(nr+2) + (i+1).
 struct SphDims {
   int nr, nt, np;
+  int inner_ghost;   // 0: Neumann mirror P_{-1} = P_1; 1: the inner ghost shell holds Dirichlet data
   __host__ __device__ long long sy() const { return nr + 2; }
   __host__ __device__ long long sz() const { return (long long)(nr + 2) * (nt + 2); }
   __host__ __device__ long long size() const { return sz() * (np + 2); }
@@ -41,11 +42,16 @@ struct SphTables {
   double r_ghost = 0.0;     // outer ghost radius
   // SOR: rJ^2 of Eq. local_rjac per (theta_j, r_i) [Ntheta * Nr]
   double* rj2 = nullptr;
+  // inner expansion (Eqs. inner_multipole / inner_expansion): radial weights
+  // r_i^(1-l) dr_i dtheta dphi [(L+1) * Nr], moments qbar [(L+1)^2], ghost radius
+  double* Rw_in = nullptr;
+  double* q_in = nullptr;
+  double r_ghost_in = 0.0;
   size_t bytes = 0;
 };
 
 cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th, const double* ph,
-                             int lmax, SphTables* t);
+                             int lmax, SphTables* t, bool inner_multipole = false);
 void sph_tables_free(SphTables* t);
 
 // out = L phi on unknown nodes (phi's outer ghost as given, mirror + periodic by index)
@@ -101,5 +107,9 @@ cudaError_t launch_sph_moments(const SphDims& d, const SphTables& t, const doubl
                                cudaStream_t s);
 cudaError_t launch_sph_face(const SphDims& d, const SphTables& t, double G, double* phi,
                             cudaStream_t s);
+// inner ghost shell of phi <- Eq. inner_expansion at r_ghost_in (after launch_sph_moments
+// with the inner tables, which then also forms qbar)
+cudaError_t launch_sph_face_inner(const SphDims& d, const SphTables& t, double G, double* phi,
+                                  cudaStream_t s);
 
 }  // namespace ps
