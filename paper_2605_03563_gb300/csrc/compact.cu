@@ -26,6 +26,7 @@
 #include "cart_kernels.cuh"
 #include "compact.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace ps {
 
@@ -92,21 +93,47 @@ struct Plane {
   C c, f, e;
 };
 
+// the 3 x 3 neighbourhood of (i, j) on plane k (ZI: interior nodes read as 0)
+template <typename C>
+struct Raw9 {
+  C c, xm, xp, ym, yp, mm, pm, mp, pp;
+};
+
 template <bool ZI, typename T, typename C = typename St<T>::C>
-__device__ __forceinline__ Plane<C> plane_sums(const Dims& d, const T* __restrict__ u, int i, int j, int k) {
+__device__ __forceinline__ Raw9<C> plane_load(const Dims& d, const T* __restrict__ u, int i, int j, int k) {
   const long long sy = d.sy();
   const long long p = d.at(i, j, k);
   auto ld = [&](long long q, int ii, int jj) -> C {
     if (ZI && ii >= 1 && ii <= d.ni() && jj >= 1 && jj <= d.nj() && k >= 1 && k <= d.nk()) return (C)0;
     return (C)u[q];
   };
+  Raw9<C> v;
+  v.c = ld(p, i, j);
+  v.xm = ld(p - 1, i - 1, j);
+  v.xp = ld(p + 1, i + 1, j);
+  v.ym = ld(p - sy, i, j - 1);
+  v.yp = ld(p + sy, i, j + 1);
+  v.mm = ld(p - sy - 1, i - 1, j - 1);
+  v.pm = ld(p - sy + 1, i + 1, j - 1);
+  v.mp = ld(p + sy - 1, i - 1, j + 1);
+  v.pp = ld(p + sy + 1, i + 1, j + 1);
+  return v;
+}
+
+template <typename C>
+__device__ __forceinline__ Plane<C> plane_of(const Raw9<C>& v) {
   Plane<C> s;
-  s.c = ld(p, i, j);
-  s.f = (ld(p - 1, i - 1, j) + ld(p + 1, i + 1, j)) + (ld(p - sy, i, j - 1) + ld(p + sy, i, j + 1));
-  s.e = (ld(p - sy - 1, i - 1, j - 1) + ld(p - sy + 1, i + 1, j - 1)) +
-        (ld(p + sy - 1, i - 1, j + 1) + ld(p + sy + 1, i + 1, j + 1));
+  s.c = v.c;
+  s.f = (v.xm + v.xp) + (v.ym + v.yp);
+  s.e = (v.mm + v.pm) + (v.mp + v.pp);
   return s;
 }
+
+// stencil weights in the arithmetic precision of the kernel (converted on the host)
+template <typename C>
+struct Wts {
+  C w[4];
+};
 
 template <typename C>
 __device__ __forceinline__ C apply_planes(const C w[4], const Plane<C>& m, const Plane<C>& c, const Plane<C>& p) {
@@ -136,24 +163,28 @@ __device__ __forceinline__ void block_partial(double v, double* __restrict__ par
 // FP64 storage, FP32 for FP32 storage).
 // NORM: the residual pass also forms per-block partials of r^2 (in FP64; FP32
 // inner passes skip it, so they touch no FP64 instruction).
+// The loads of plane k + 2 are issued before the arithmetic of plane k, so two
+// planes of loads are in flight per thread.
 template <int MODE, bool ZI, typename T, typename TR, bool NORM = true>
 __global__ void __launch_bounds__(CBX* CBY)
-    k_c27(Dims d, W27 W, double omega, const T* __restrict__ src, const T* __restrict__ b,
-          TR* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
+    k_c27(Dims d, Wts<typename St<T>::C> W, typename St<T>::C om, const T* __restrict__ src,
+          const T* __restrict__ b, TR* __restrict__ dst, double* __restrict__ partials,
+          const DevState* __restrict__ st) {
   using C = typename St<T>::C;
   if (st != nullptr && st->done) return;   // uniform
   const int i = blockIdx.x * CBX + threadIdx.x + 1;
   const int j = blockIdx.y * CBY + threadIdx.y + 1;
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
-  const C w[4] = {(C)W.w[0], (C)W.w[1], (C)W.w[2], (C)W.w[3]};
-  const C om = (C)omega;
   double s2 = 0.0;
   if (i <= d.ni() && j <= d.nj()) {
-    Plane<C> pm = plane_sums<ZI>(d, src, i, j, k0 - 1);
-    Plane<C> pc = plane_sums<ZI>(d, src, i, j, k0);
+    Plane<C> pm = plane_of(plane_load<ZI>(d, src, i, j, k0 - 1));
+    Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
+    Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
     for (int k = k0; k < k1; k++) {
-      const Plane<C> pn = plane_sums<ZI>(d, src, i, j, k + 1);
-      const C a = apply_planes<C>(w, pm, pc, pn);
+      Raw9<C> nn = nx;
+      if (k + 2 <= k1) nn = plane_load<ZI>(d, src, i, j, k + 2);   // plane k1 <= nk + 1 exists
+      const Plane<C> pn = plane_of(nx);
+      const C a = apply_planes<C>(W.w, pm, pc, pn);
       const long long q = d.at(i, j, k);
       if (MODE == 0) {
         const C r = (C)b[q] - a;
@@ -164,9 +195,15 @@ __global__ void __launch_bounds__(CBX* CBY)
       }
       pm = pc;
       pc = pn;
+      nx = nn;
     }
   }
   if (MODE == 0 && NORM && partials != nullptr) block_partial(s2, partials);
+}
+
+template <typename C>
+static Wts<C> wts(const W27& a) {
+  return Wts<C>{{(C)a.w[0], (C)a.w[1], (C)a.w[2], (C)a.w[3]}};
 }
 
 static dim3 c27_grid(const Dims& d) {
@@ -182,9 +219,9 @@ cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const
                              int zero_interior, double* partials, const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
   if (zero_interior)
-    k_c27<0, true, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+    k_c27<0, true, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
   else
-    k_c27<0, false, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, A, 0.0, u, b, r, partials, st);
+    k_c27<0, false, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
   return cudaGetLastError();
 }
 
@@ -193,17 +230,17 @@ cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void*
   if (d.g != 1) return cudaErrorInvalidValue;
   const dim3 g = c27_grid(d), blk(CBX, CBY);
   if (zero_interior && dt == DT_F64 && dt_r == DT_F32)
-    k_c27<0, true, double, float><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+    k_c27<0, true, double, float><<<g, blk, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
   else if (zero_interior)
     return cudaErrorInvalidValue;
   else if (dt == DT_F64 && dt_r == DT_F64)
-    k_c27<0, false, double, double><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
+    k_c27<0, false, double, double><<<g, blk, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
   else if (dt == DT_F64 && dt_r == DT_F32)
-    k_c27<0, false, double, float><<<g, blk, 0, s>>>(d, A, 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+    k_c27<0, false, double, float><<<g, blk, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
   else if (dt == DT_F32 && dt_r == DT_F32 && partials == nullptr)
-    k_c27<0, false, float, float, false><<<g, blk, 0, s>>>(d, A, 0.0, (const float*)u, (const float*)b, (float*)r, nullptr, st);
+    k_c27<0, false, float, float, false><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, nullptr, st);
   else if (dt == DT_F32 && dt_r == DT_F32)
-    k_c27<0, false, float, float><<<g, blk, 0, s>>>(d, A, 0.0, (const float*)u, (const float*)b, (float*)r, partials, st);
+    k_c27<0, false, float, float><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, partials, st);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -219,11 +256,124 @@ cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt
   if (d.g != 1) return cudaErrorInvalidValue;
   const dim3 g = c27_grid(d), blk(CBX, CBY);
   if (dt == DT_F64)
-    k_c27<1, false, double, double><<<g, blk, 0, s>>>(d, M, omega, (const double*)r, nullptr, (double*)u, nullptr, st);
+    k_c27<1, false, double, double><<<g, blk, 0, s>>>(d, wts<double>(M), omega, (const double*)r, nullptr, (double*)u, nullptr, st);
   else if (dt == DT_F32)
-    k_c27<1, false, float, float><<<g, blk, 0, s>>>(d, M, omega, (const float*)r, nullptr, (float*)u, nullptr, st);
+    k_c27<1, false, float, float><<<g, blk, 0, s>>>(d, wts<float>(M), (float)omega, (const float*)r, nullptr, (float*)u, nullptr, st);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ TMA-staged FP32 passes
+// The FP32 passes of the inner cycles stream the 27-point source through a
+// ring of TMA-staged planes (box 40 x 10 starting at x = 32 bx - 4: a 32 x 8
+// tile of nodes 32 bx + 1 .. 32 bx + 32 with one-node halos, widened in x to
+// whole 16-byte granules), so each value is loaded into shared
+// memory once instead of being fetched nine times per plane through L1; the
+// second array (b, or the potential updated in place) is read once per node
+// from global memory.  Same arithmetic, in the same order, as k_c27.
+static constexpr int TTX = 32, TTY = 8, TXH = 4;
+static constexpr int TWP = TTX + 2 * TXH, THP = TTY + 2, TNS = 4;
+static constexpr int TPB = TWP * THP * 4;   // bytes per staged FP32 plane
+static constexpr int TPBA = (TPB + 127) / 128 * 128;
+
+template <int MODE>
+__global__ void __launch_bounds__(TTX* TTY)
+    k_c27_tma(const __grid_constant__ CUtensorMap mS, Dims d, Wts<float> W, float om,
+              const float* __restrict__ b, float* __restrict__ dst, int zc, const DevState* __restrict__ st,
+              int* __restrict__ fault) {
+  __shared__ __align__(128) unsigned char smem[TNS * TPBA];
+  __shared__ __align__(8) unsigned long long bar[TNS];
+  if (st != nullptr && st->done) return;   // uniform
+  const int tid = threadIdx.x + TTX * threadIdx.y;
+  const int x0 = blockIdx.x * TTX + 1, y0 = blockIdx.y * TTY + 1;   // first node of the tile
+  const int xs = x0 - 1 - TXH;                                         // box x start: 32 bx - 4, a multiple of 4
+  const int k0 = 1 + blockIdx.z * zc, k1 = min(k0 + zc, d.nk() + 1);  // output planes [k0, k1)
+  const int zl = k0 - 1, zh = k1;                                      // staged planes [zl, zh]
+  float* ring = reinterpret_cast<float*>(smem);
+  if (tid == 0) {
+    for (int q = 0; q < TNS; q++) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int z) {   // thread 0: stage of plane z
+    if (z > zh) return;
+    const int q = (z - zl) % TNS;
+    mbar_expect_tx(&bar[q], TPB);
+    tma_load_3d(ring + q * (TPBA / 4), &mS, xs, y0 - 1, z, &bar[q]);
+  };
+  if (tid == 0)
+    for (int z = zl; z < zl + TNS; z++) issue(z);
+  bool ok = true;
+  int wq = 0;
+  unsigned wph = 0;
+  auto wait_next = [&]() {
+    mbar_wait(&bar[wq], wph, ok);
+    if (++wq == TNS) { wq = 0; wph ^= 1u; }
+  };
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool in = i <= d.ni() && j <= d.nj();
+  const int sc = (ty + 1) * TWP + (tx + TXH + 1);   // staged index of (i, j): column i - xs
+  auto sums = [&](int z) -> Plane<float> {
+    const float* P = ring + ((z - zl) % TNS) * (TPBA / 4);
+    Raw9<float> v;
+    v.c = P[sc];
+    v.xm = P[sc - 1];
+    v.xp = P[sc + 1];
+    v.ym = P[sc - TWP];
+    v.yp = P[sc + TWP];
+    v.mm = P[sc - TWP - 1];
+    v.pm = P[sc - TWP + 1];
+    v.mp = P[sc + TWP - 1];
+    v.pp = P[sc + TWP + 1];
+    return plane_of(v);
+  };
+  wait_next();
+  wait_next();
+  Plane<float> pm = sums(zl), pc = sums(zl + 1);
+  for (int k = k0; k < k1; k++) {
+    wait_next();   // plane k + 1
+    const Plane<float> pn = sums(k + 1);
+    if (in) {
+      const float a = apply_planes<float>(W.w, pm, pc, pn);
+      const long long q = d.at(i, j, k);
+      if (MODE == 0) dst[q] = b[q] - a;
+      else dst[q] = fmaf(-om, a, dst[q]);
+    }
+    pm = pc;
+    pc = pn;
+    __syncthreads();   // plane k - 1 is no longer read
+    if (tid == 0) {
+      fence_proxy_async();
+      issue(k - 1 + TNS);
+    }
+  }
+  if (!ok && fault != nullptr) atomicExch(fault, 1);
+}
+
+static int g_sms = 0;
+
+cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, const float* src, const float* b,
+                           float* dst, const DevState* st, int* fault, cudaStream_t s) {
+  if (d.g != 1) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  if (!encode_level_map(&map, DT_F32, src, d, TWP, THP)) return cudaErrorInvalidValue;
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 152;
+  }
+  const int gx = (d.ni() + TTX - 1) / TTX, gy = (d.nj() + TTY - 1) / TTY, nk = d.nk();
+  // about two waves of 8 blocks per SM, z-chunks of at least 8 planes
+  const int want = std::max(1, 16 * g_sms / (gx * gy));
+  const int zc = std::max(8, (nk + want - 1) / want);
+  const dim3 grid(gx, gy, (nk + zc - 1) / zc), blk(TTX, TTY);
+  if (mode == 0)
+    k_c27_tma<0><<<grid, blk, 0, s>>>(map, d, wts<float>(W), 0.0f, b, dst, zc, st, fault);
+  else
+    k_c27_tma<1><<<grid, blk, 0, s>>>(map, d, wts<float>(W), (float)omega, nullptr, dst, zc, st, fault);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,10 @@ cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void*
                                 int zero_interior = 0);
 cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt, const void* r, void* u,
                                const DevState* st, cudaStream_t s);
+// TMA-staged FP32 passes (mode 0: dst = b - A src; mode 1: dst -= omega M src) on
+// level layouts with 16-byte aligned rows; a TMA wait that times out sets *fault
+cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, const float* src, const float* b,
+                           float* dst, const DevState* st, int* fault, cudaStream_t s);
 // coarsest CG in FP64 arithmetic on FP32 or FP64 storage
 cudaError_t launch_c27_coarse_cg_dt(const Dims& d, const W27& A, int dt, const void* b, void* u, double tol,
                                     const DevState* st, cudaStream_t s);

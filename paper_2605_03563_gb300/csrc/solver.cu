@@ -733,14 +733,21 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   }
   void* r = L.tmp;
   const double n = (double)L.d.ni() * L.d.nj() * L.d.nk();
+  // residual pass: FP64 levels march z through L1, FP32 levels stage planes by TMA
+  auto resid = [&](void* out) -> cudaError_t {
+    if (fp64) return launch_c27_resid_dt(L.d, C.A[l], dt, u, b, dt, out, nullptr, st, s);
+    return launch_c27_tma(L.d, C.A[l], 0.0, 0, (const float*)u, (const float*)b, (float*)out, st, &h->st->fault, s);
+  };
   auto smooth = [&](int steps) -> cudaError_t {
     for (int it = 0; it < steps; it++) {
       prof_begin(h, l == 0 ? PC_DELTA0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
-      cudaError_t e2 = (h->nlaunch += 1, launch_c27_resid_dt(L.d, C.A[l], dt, u, b, dt, r, nullptr, st, s));
+      cudaError_t e2 = (h->nlaunch += 1, resid(r));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
       prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
-      e2 = (h->nlaunch += 1, launch_c27_spai_dt(L.d, C.M[l], C.omega[l], dt, r, u, st, s));
+      e2 = (h->nlaunch += 1, fp64 ? launch_c27_spai_dt(L.d, C.M[l], C.omega[l], dt, r, u, st, s)
+                                  : launch_c27_tma(L.d, C.M[l], C.omega[l], 1, (const float*)r, nullptr,
+                                                   (float*)u, st, &h->st->fault, s));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
     }
@@ -748,7 +755,7 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   };
   if ((e = smooth(nu1)) != cudaSuccess) return e;
   if (l == 0) prof_begin(h, PC_DELTA0, n * 3.0 * S, n * 16.0, fp64, s);
-  e = (h->nlaunch += 1, launch_c27_resid_dt(L.d, C.A[l], dt, u, b, dt, r, nullptr, st, s));
+  e = (h->nlaunch += 1, resid(r));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
   Level& Cl = H->lv[l + 1];
