@@ -509,7 +509,14 @@ def main():
                     help="serving: batched executor (one graph launch per tick for all solves), "
                          "per-request graphs, or the batch for grids up to 96^3 and graphs above")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the timings of the other configurations (1, 3, 4)")
+                    help="skip the timings of the other configurations, the batched executor and "
+                         "the compact multigrid (same as --configs none)")
+    ap.add_argument("--configs", default="other,batched,compact",
+                    help="comma-separated subset of other (configurations 1, 3, 4), batched "
+                         "(batched executor throughput) and compact (sixth-order multigrid on the "
+                         "two-sphere problem), or none")
+    ap.add_argument("--compact-sizes", default="256,512",
+                    help="grid sizes (intervals) of the compact multigrid timings")
     ap.add_argument("--tile-min-n", type=int, default=0,
                     help="levels with at least this many intervals use the TMA tile kernels "
                          "(0 = library default, -1 = never)")
@@ -719,10 +726,17 @@ def main():
     configs = None
     batched = None
     compact = None
-    if rank == 0 and not args.no_configs:
-        configs = other_configs(dev)
-        batched = batched_throughput(dev)
-        compact = compact_mg(dev)
+    extra = set() if args.no_configs else {c.strip() for c in args.configs.split(",") if c.strip()}
+    unknown = extra - {"other", "batched", "compact", "none"}
+    if unknown:
+        raise SystemExit(f"--configs: unknown entries {sorted(unknown)}")
+    if rank == 0:
+        if "other" in extra:
+            configs = other_configs(dev)
+        if "batched" in extra:
+            batched = batched_throughput(dev)
+        if "compact" in extra:
+            compact = compact_mg(dev, sizes=tuple(int(v) for v in args.compact_sizes.split(",")))
 
     solver.close()
     if rank == 0:
