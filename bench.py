@@ -377,6 +377,21 @@ def compact_mg(dev, sizes=(256, 512), nus=(1, 2, 3), reps=2, precs=("fp64", "mix
                     "rel_residual": info.rel_residual, "time_to_1e-6_ms": ms, "t_mp_ms": info.t_mp_ms,
                     "t_iter_ms": t_iter, "t_s_ms": t_iter / cyc, "rho_conv": info.rho_conv,
                     "s_s_gzups": (n - 1) ** 3 / (t_iter / cyc / 1e3) / 1e9}
+                if nu == max(nus):
+                    # per-kernel CUDA-event times of one more solve (plain graphs with
+                    # event nodes around the hot kernels)
+                    s.profile(True)
+                    s.profile_read()
+                    run()
+                    torch.cuda.synchronize()
+                    pr = s.profile_read()
+                    s.profile(False)
+                    out[f"n{n - 1}_nu{nu}_{prec}"]["kernels"] = {
+                        k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 5),
+                            "total_ms": round(v["total_ms"], 4),
+                            "GB/s": round(v["bytes_per_launch"] / (v["avg_ms"] / 1e3) / 1e9, 1)
+                            if v["avg_ms"] > 0 else None}
+                        for k, v in sorted(pr.items(), key=lambda kv: -kv[1]["total_ms"])}
         del rho
     return out
 

@@ -201,6 +201,79 @@ __global__ void __launch_bounds__(CBX* CBY)
   if (MODE == 0 && NORM && partials != nullptr) block_partial(s2, partials);
 }
 
+// per-block {v, 0} into p[2 b], p[2 b + 1] and {w, 0} into q[2 b], q[2 b + 1]
+__device__ __forceinline__ void block_partial2(double v, double w, double* __restrict__ p, double* __restrict__ q) {
+  __shared__ double sh[2][CBX * CBY / 32];
+  const int tid = threadIdx.x + CBX * threadIdx.y;
+  v = warp_sum(v);
+  w = warp_sum(w);
+  if ((tid & 31) == 0) {
+    sh[0][tid >> 5] = v;
+    sh[1][tid >> 5] = w;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double a = tid < CBX * CBY / 32 ? sh[0][tid] : 0.0;
+    double c = tid < CBX * CBY / 32 ? sh[1][tid] : 0.0;
+    a = warp_sum(a);
+    c = warp_sum(c);
+    if (tid == 0) {
+      const int bid = block_linear_id();
+      p[2 * bid] = a;
+      p[2 * bid + 1] = 0.0;
+      q[2 * bid] = c;
+      q[2 * bid + 1] = 0.0;
+    }
+  }
+}
+
+// Initial residual pass of a compact solve (FP64 arithmetic): r = b - A u
+// stored as TR with per-block partials of r^2, and in the same pass the
+// reference residual b - A u0 of the boundary data alone (u0: u with its
+// interior zeroed), whose partials go to partials + 2 nblocks.  A u0 vanishes
+// unless a node has a boundary node among its 26 neighbours, so only the
+// first and last interior layers of each axis evaluate it; elsewhere the
+// reference residual is b.  Both sums are the ones two separate passes
+// (interior zeroed, then full) would form, in the same order.
+template <typename TR>
+__global__ void __launch_bounds__(CBX* CBY)
+    k_c27_init(Dims d, Wts<double> W, const double* __restrict__ u, const double* __restrict__ b,
+               TR* __restrict__ r, double* __restrict__ partials, int nblocks) {
+  const int i = blockIdx.x * CBX + threadIdx.x + 1;
+  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
+  double s2 = 0.0, s0 = 0.0;
+  if (i <= d.ni() && j <= d.nj()) {
+    const bool side = i == 1 || i == d.ni() || j == 1 || j == d.nj();
+    Plane<double> pm = plane_of(plane_load<false>(d, u, i, j, k0 - 1));
+    Plane<double> pc = plane_of(plane_load<false>(d, u, i, j, k0));
+    Raw9<double> nx = plane_load<false>(d, u, i, j, k0 + 1);
+    for (int k = k0; k < k1; k++) {
+      Raw9<double> nn = nx;
+      if (k + 2 <= k1) nn = plane_load<false>(d, u, i, j, k + 2);
+      const Plane<double> pn = plane_of(nx);
+      const double a = apply_planes<double>(W.w, pm, pc, pn);
+      const long long q = d.at(i, j, k);
+      const double bq = b[q];
+      const double rv = bq - a;
+      r[q] = (TR)rv;
+      s2 = fma(rv, rv, s2);
+      double r0 = bq;
+      if (side || k == 1 || k == d.nk()) {
+        const double a0 = apply_planes<double>(W.w, plane_of(plane_load<true>(d, u, i, j, k - 1)),
+                                               plane_of(plane_load<true>(d, u, i, j, k)),
+                                               plane_of(plane_load<true>(d, u, i, j, k + 1)));
+        r0 = bq - a0;
+      }
+      s0 = fma(r0, r0, s0);
+      pm = pc;
+      pc = pn;
+      nx = nn;
+    }
+  }
+  block_partial2(s2, s0, partials, partials + 2 * nblocks);
+}
+
 template <typename C>
 static Wts<C> wts(const W27& a) {
   return Wts<C>{{(C)a.w[0], (C)a.w[1], (C)a.w[2], (C)a.w[3]}};
@@ -241,6 +314,20 @@ cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void*
     k_c27<0, false, float, float, false><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, nullptr, st);
   else if (dt == DT_F32 && dt_r == DT_F32)
     k_c27<0, false, float, float><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, partials, st);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c27_init(const Dims& d, const W27& A, const double* u, const double* b, int dt_r, void* r,
+                            double* partials, cudaStream_t s) {
+  if (d.g != 1) return cudaErrorInvalidValue;
+  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  const int nb = c27_blocks(d);
+  if (dt_r == DT_F64)
+    k_c27_init<double><<<g, blk, 0, s>>>(d, wts<double>(A), u, b, (double*)r, partials, nb);
+  else if (dt_r == DT_F32)
+    k_c27_init<float><<<g, blk, 0, s>>>(d, wts<double>(A), u, b, (float*)r, partials, nb);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -377,6 +464,175 @@ cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ fused FP32 smoothing step
+// One SPAI step u' = u - omega M (b - A u) of an inner FP32 level in a single
+// pass, out of place (u' goes to another array, so no block reads a value
+// that a neighbouring block has already replaced).  Each block owns a 32 x 8
+// tile and a z-chunk; per plane it forms the residual on the tile with a
+// one-node halo (34 x 10 nodes, zero at boundary nodes) into a 3-plane ring in
+// shared memory, then applies M to the residual planes k - 1, k, k + 1.
+// u (box 40 x 12 from x = 32 bx - 4, y = y0 - 2) and b (box 40 x 10 from
+// y = y0 - 1) arrive by TMA, one stage per plane z holding both boxes.  The
+// arithmetic is that of the residual pass followed by the SPAI pass of
+// k_c27_tma, operation for operation, so both routes give the same bits; the
+// fused one moves 12 bytes per node instead of 24.
+static constexpr int FTX = 32, FTY = 8;              // output tile
+static constexpr int FRX = FTX + 2, FRY = FTY + 2;   // residual region: 34 x 10
+static constexpr int FUW = 40, FUH = FTY + 4;        // staged u box
+static constexpr int FBW = 40, FBH = FTY + 2;        // staged b box
+static constexpr int FNS = 8;                        // stages (planes of u and b), a power of two
+static constexpr int FRS = 4;                        // residual planes in the ring, a power of two
+static constexpr int FUB = FUW * FUH * 4, FBB = FBW * FBH * 4;
+static constexpr int FUBA = (FUB + 127) / 128 * 128, FBBA = (FBB + 127) / 128 * 128;
+static constexpr int FSTAGE = FUBA + FBBA;
+static constexpr int FTHREADS = 352;                 // 11 warps
+static_assert((FNS & (FNS - 1)) == 0 && (FRS & (FRS - 1)) == 0 && FRS >= 3, "ring sizes");
+static_assert(FRX == 32 + 2 && 2 * FRY <= 32 && FTHREADS == 32 * (FRY + 1) && FTX == 32, "thread roles");
+
+// Thread roles: warps 0..9 form the residual on row ry = warp, columns
+// rx = lane (0..31) of the 34 x 10 region, warp 10 on its columns 32 and 33;
+// warps 0..7 then write output row oy = warp, column ox = lane.  A warp's
+// shared-memory reads of one row are 32 consecutive words (no bank conflict).
+__global__ void __launch_bounds__(FTHREADS)
+    k_c27_smooth(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mB, Dims d,
+                 Wts<float> WA, Wts<float> WM, float om, float* __restrict__ dst, int zc,
+                 const DevState* __restrict__ st, int* __restrict__ fault) {
+  __shared__ __align__(128) unsigned char smem[FNS * FSTAGE];
+  __shared__ float rring[FRS][FRX * FRY];
+  __shared__ __align__(8) unsigned long long bar[FNS];
+  if (st != nullptr && st->done) return;   // uniform
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * FTX + 1, y0 = blockIdx.y * FTY + 1;   // first output node
+  const int xs = x0 - 5;                                              // box x start: 32 bx - 4
+  const int k0 = 1 + blockIdx.z * zc, k1 = min(k0 + zc, d.nk() + 1);  // output planes [k0, k1)
+  const int zl = k0 - 2, zh = k1 + 1;                                 // staged planes [zl, zh]
+  if (tid == 0) {
+    for (int q = 0; q < FNS; q++) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto stage = [&](int z) -> unsigned { return (unsigned)(z - zl) & (FNS - 1); };
+  auto ubox = [&](int z) -> float* { return reinterpret_cast<float*>(smem + stage(z) * FSTAGE); };
+  auto bbox = [&](int z) -> float* { return reinterpret_cast<float*>(smem + stage(z) * FSTAGE + FUBA); };
+  auto rbuf = [&](int z) -> float* { return rring[(unsigned)(z - zl) & (FRS - 1)]; };
+  auto issue = [&](int z) {   // thread 0: stage of plane z
+    if (z > zh) return;
+    unsigned long long* br = &bar[stage(z)];
+    mbar_expect_tx(br, FUB + FBB);
+    tma_load_3d(ubox(z), &mU, xs, y0 - 2, z, br);
+    tma_load_3d(bbox(z), &mB, xs, y0 - 1, z, br);
+  };
+  if (tid == 0)
+    for (int z = zl; z < zl + FNS; z++) issue(z);
+  bool ok = true;
+  int wq = 0;
+  unsigned wph = 0;
+  auto wait_next = [&]() {
+    mbar_wait(&bar[wq], wph, ok);
+    if (++wq == FNS) { wq = 0; wph ^= 1u; }
+  };
+  // residual node of this thread: (x0 - 1 + rx, y0 - 1 + ry)
+  const bool redge = warp == FRY;
+  const int rx = redge ? FTX + (lane & 1) : lane, ry = redge ? lane >> 1 : warp;
+  const bool rthr = warp < FRY || (redge && lane < 2 * FRY);
+  const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
+  const bool rin = rthr && gx >= 1 && gx <= d.ni() && gy >= 1 && gy <= d.nj();
+  const int su = (ry + 1) * FUW + (rx + 4);   // u box index of the residual node
+  const int sb = ry * FBW + (rx + 4);         // b box index
+  const int sw = ry * FRX + rx;               // residual ring index
+  auto sums9 = [](const float* P, int c, int w) -> Plane<float> {
+    Raw9<float> v;
+    v.c = P[c];
+    v.xm = P[c - 1];
+    v.xp = P[c + 1];
+    v.ym = P[c - w];
+    v.yp = P[c + w];
+    v.mm = P[c - w - 1];
+    v.pm = P[c - w + 1];
+    v.mp = P[c + w - 1];
+    v.pp = P[c + w + 1];
+    return plane_of(v);
+  };
+  Plane<float> um{}, uc{};
+  // residual plane z from u planes z - 1 (um), z (uc), z + 1 (read here); zero off the interior
+  auto rstep = [&](int z) {
+    if (!rthr) return;
+    const Plane<float> un = sums9(ubox(z + 1), su, FUW);
+    float rv = 0.0f;
+    if (rin && z >= 1 && z <= d.nk()) rv = bbox(z)[sb] - apply_planes<float>(WA.w, um, uc, un);
+    rbuf(z)[sw] = rv;
+    um = uc;
+    uc = un;
+  };
+  // output node of this thread (warps 0..7): (x0 + lane, y0 + warp)
+  const bool othr = warp < FTY;
+  const int i = x0 + lane, j = y0 + warp;
+  const bool oin = othr && i <= d.ni() && j <= d.nj();
+  const int sr = (warp + 1) * FRX + (lane + 1);   // residual ring index of the output node
+  const int so = (warp + 2) * FUW + (lane + 5);   // u box index of the output node
+  // prologue: residual planes k0 - 1 and k0 (u planes k0 - 2 .. k0 + 1)
+  wait_next();
+  wait_next();
+  wait_next();
+  if (rthr) {
+    um = sums9(ubox(zl), su, FUW);
+    uc = sums9(ubox(zl + 1), su, FUW);
+  }
+  rstep(k0 - 1);
+  wait_next();
+  rstep(k0);
+  __syncthreads();
+  if (tid == 0) {   // planes k0 - 2 and k0 - 1 are no longer read
+    fence_proxy_async();
+    issue(zl + FNS);
+    issue(zl + 1 + FNS);
+  }
+  Plane<float> rm{}, rc{};
+  if (othr) {
+    rm = sums9(rbuf(k0 - 1), sr, FRX);
+    rc = sums9(rbuf(k0), sr, FRX);
+  }
+  const long long sz = d.sz();
+  float* out = dst + d.at(min(i, d.ni()), min(j, d.nj()), k0);
+  for (int k = k0; k < k1; k++, out += sz) {
+    wait_next();   // plane k + 2
+    rstep(k + 1);
+    __syncthreads();   // residual plane k + 1 complete; every thread is past output k - 1
+    if (tid == 0 && k > k0) {
+      fence_proxy_async();
+      issue(k - 1 + FNS);   // plane k - 1 is no longer read
+    }
+    if (othr) {
+      const Plane<float> rn = sums9(rbuf(k + 1), sr, FRX);
+      if (oin) *out = fmaf(-om, apply_planes<float>(WM.w, rm, rc, rn), ubox(k)[so]);
+      rm = rc;
+      rc = rn;
+    }
+  }
+  if (!ok && fault != nullptr) atomicExch(fault, 1);
+}
+
+cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
+                              const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
+  if (d.g != 1 || u == dst) return cudaErrorInvalidValue;
+  CUtensorMap mu, mb;
+  if (!encode_level_map(&mu, DT_F32, u, d, FUW, FUH)) return cudaErrorInvalidValue;
+  if (!encode_level_map(&mb, DT_F32, b, d, FBW, FBH)) return cudaErrorInvalidValue;
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 152;
+  }
+  const int gx = (d.ni() + FTX - 1) / FTX, gy = (d.nj() + FTY - 1) / FTY, nk = d.nk();
+  // about two waves of 5 blocks per SM, z-chunks of at least 16 planes (3 extra staged planes each)
+  const int want = std::max(1, 10 * g_sms / (gx * gy));
+  const int zc = std::max(16, (nk + want - 1) / want);
+  const dim3 grid(gx, gy, (nk + zc - 1) / zc);
+  k_c27_smooth<<<grid, FTHREADS, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ right-hand side
 // f value of node (i, j, k) of the dense layout du, one extrapolated layer on
 // every side (cubic along the axis that leaves the array)
@@ -392,39 +648,72 @@ __device__ __forceinline__ double f_ext(const Dims& du, const double* __restrict
   return at(i, j, k);
 }
 
+// R_h of the compact schemes as a z-march over in-plane sums (the 27-point
+// classes of R_h are the classes of A's stencil): per node
+//   b = W0 C(z) + W1 (F(z) + C(z-1) + C(z+1)) + W2 (E(z) + F(z-1) + F(z+1))
+//     + W3 (sum of the six +-2 offsets)
+// with the source scale folded into the weights on the host (no division on
+// the device).
 template <int ORDER>
 __global__ void __launch_bounds__(CBX* CBY)
-    k_c27_rhs(Dims d, Dims du, const double* __restrict__ rho, double fscale, double* __restrict__ b) {
+    k_c27_rhs(Dims d, Dims du, const double* __restrict__ rho, Wts<double> W, double* __restrict__ b) {
   const int i = blockIdx.x * CBX + threadIdx.x + 1;
   const int j = blockIdx.y * CBY + threadIdx.y + 1;
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
   if (i > d.ni() || j > d.nj()) return;
+  if (ORDER == 2) {
+    for (int k = k0; k < k1; k++) b[d.at(i, j, k)] = W.w[0] * rho[du.at(i, j, k)];
+    return;
+  }
+  const long long sy = du.sy();
+  // planes k - 1 .. k + 2 of interior nodes stay inside the node array 0..n
+  // up to k + 2 = n; the +-2 offsets past it are extrapolated (f_ext)
+  auto load9 = [&](int k) -> Raw9<double> {
+    const long long p = du.at(i, j, k);
+    Raw9<double> v;
+    v.c = rho[p];
+    v.xm = rho[p - 1];
+    v.xp = rho[p + 1];
+    v.ym = rho[p - sy];
+    v.yp = rho[p + sy];
+    v.mm = rho[p - sy - 1];
+    v.pm = rho[p - sy + 1];
+    v.mp = rho[p + sy - 1];
+    v.pp = rho[p + sy + 1];
+    return v;
+  };
+  const bool side = i == 1 || i == d.ni() || j == 1 || j == d.nj();   // x or y offsets +-2 leave the array
+  Plane<double> pm = plane_of(load9(k0 - 1)), pc = plane_of(load9(k0));
+  Raw9<double> nx = load9(k0 + 1);
+  double cm2 = ORDER == 6 ? f_ext(du, rho, i, j, k0 - 2) : 0.0;   // centre of plane k - 2
   for (int k = k0; k < k1; k++) {
+    Raw9<double> nn = nx;
+    if (k + 2 <= d.nk() + 1) nn = load9(k + 2);   // issued before the arithmetic of plane k
+    const Plane<double> pn = plane_of(nx);
+    const double fa = pc.f + (pm.c + pn.c);
     double v;
-    if (ORDER == 2) {
-      v = rho[du.at(i, j, k)];
+    if (ORDER == 4) {
+      v = fma(W.w[0], pc.c, W.w[1] * fa);
     } else {
-      double c = 0, fa = 0, ed = 0;
-      for (int dz = -1; dz <= 1; dz++)
-        for (int dy = -1; dy <= 1; dy++)
-          for (int dx = -1; dx <= 1; dx++) {
-            const int cl = (dx != 0) + (dy != 0) + (dz != 0);
-            if (cl == 3) continue;
-            const double x = rho[du.at(i + dx, j + dy, k + dz)];
-            if (cl == 0) c += x;
-            else if (cl == 1) fa += x;
-            else ed += x;
-          }
-      if (ORDER == 4) {
-        v = 0.5 * c + fa / 12.0;
+      const double ed = pc.e + (pm.f + pn.f);
+      const double cp2 = k + 2 <= d.nk() + 1 ? nn.c : f_ext(du, rho, i, j, k + 2);
+      double xs, ys;
+      if (side) {
+        xs = f_ext(du, rho, i - 2, j, k) + f_ext(du, rho, i + 2, j, k);
+        ys = f_ext(du, rho, i, j - 2, k) + f_ext(du, rho, i, j + 2, k);
       } else {
-        const double ax = (f_ext(du, rho, i - 2, j, k) + f_ext(du, rho, i + 2, j, k)) +
-                          (f_ext(du, rho, i, j - 2, k) + f_ext(du, rho, i, j + 2, k)) +
-                          (f_ext(du, rho, i, j, k - 2) + f_ext(du, rho, i, j, k + 2));
-        v = (67.0 / 120.0) * c + fa / 18.0 + ed / 90.0 - ax / 240.0;
+        const long long p = du.at(i, j, k);
+        xs = rho[p - 2] + rho[p + 2];
+        ys = rho[p - 2 * sy] + rho[p + 2 * sy];
       }
+      const double ax = (xs + ys) + (cm2 + cp2);
+      v = fma(W.w[0], pc.c, fma(W.w[1], fa, fma(W.w[2], ed, W.w[3] * ax)));
+      cm2 = pm.c;
     }
-    b[d.at(i, j, k)] = fscale * v;
+    b[d.at(i, j, k)] = v;
+    pm = pc;
+    pc = pn;
+    nx = nn;
   }
 }
 
@@ -433,9 +722,15 @@ cudaError_t launch_c27_rhs(const Dims& d, const Dims& du, int order, const doubl
   if (d.g != 1 || du.g != 1) return cudaErrorInvalidValue;
   if (order == 6 && (d.nx < 4 || d.ny < 4 || d.nz < 4)) return cudaErrorInvalidValue;
   const dim3 g = c27_grid(d), blk(CBX, CBY);
-  if (order == 2) k_c27_rhs<2><<<g, blk, 0, s>>>(d, du, rho, fscale, b);
-  else if (order == 4) k_c27_rhs<4><<<g, blk, 0, s>>>(d, du, rho, fscale, b);
-  else k_c27_rhs<6><<<g, blk, 0, s>>>(d, du, rho, fscale, b);
+  // R_h weights per class (centre, faces, edges, +-2 offsets) times the source scale
+  if (order == 2) {
+    k_c27_rhs<2><<<g, blk, 0, s>>>(d, du, rho, Wts<double>{{fscale, 0.0, 0.0, 0.0}}, b);
+  } else if (order == 4) {
+    k_c27_rhs<4><<<g, blk, 0, s>>>(d, du, rho, Wts<double>{{fscale * 0.5, fscale / 12.0, 0.0, 0.0}}, b);
+  } else {
+    k_c27_rhs<6><<<g, blk, 0, s>>>(
+        d, du, rho, Wts<double>{{fscale * (67.0 / 120.0), fscale / 18.0, fscale / 90.0, -fscale / 240.0}}, b);
+  }
   return cudaGetLastError();
 }
 

@@ -24,6 +24,12 @@ W27 galerkin27(const W27& fine);
 cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const double* b, double* r,
                              int zero_interior, double* partials, const DevState* st, cudaStream_t s);
 int c27_blocks(const Dims& d);
+// Initial residual of a compact solve: r = b - A u (stored FP64 or FP32 per
+// dt_r) with per-block partials {sum r^2, 0} at partials[0 .. 2 nb) and the
+// reference residual b - A u0 (u0: boundary data of u only) as partials at
+// partials[2 nb .. 4 nb), nb = c27_blocks(d), in one pass.
+cudaError_t launch_c27_init(const Dims& d, const W27& A, const double* u, const double* b, int dt_r, void* r,
+                            double* partials, cudaStream_t s);
 // u -= omega M r on the interior (Eq. richardson for A = -L_h with M of Eq. Smoother)
 cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const double* r, double* u,
                             const DevState* st, cudaStream_t s);
@@ -46,6 +52,12 @@ cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt
                                const DevState* st, cudaStream_t s);
 // TMA-staged FP32 passes (mode 0: dst = b - A src; mode 1: dst -= omega M src) on
 // level layouts with 16-byte aligned rows; a TMA wait that times out sets *fault
+// One SPAI smoothing step u' = u - omega M (b - A u) of an FP32 level in one
+// pass, written to dst (dst != u; u's boundary nodes read as the boundary
+// data, dst's boundary nodes are left as they are).  TMA-staged; a stage wait
+// that times out sets *fault.
+cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
+                              const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s);
 cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, const float* src, const float* b,
                            float* dst, const DevState* st, int* fault, cudaStream_t s);
 // coarsest CG in FP64 arithmetic on FP32 or FP64 storage

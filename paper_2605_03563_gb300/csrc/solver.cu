@@ -76,12 +76,12 @@ using namespace ps;
 // Kernel classes of the opt-in profiler.
 enum ProfClass {
   PC_SWEEP0 = 0, PC_DELTA0, PC_RESTRICT0, PC_PROLONG0, PC_NORM0, PC_COARSE, PC_MOMENTS, PC_FACES,
-  PC_SWEEP_C, PC_CORRECT0, PC_KRYLOV, PC_RBSWEEP0, PC_RBSWEEP_C, PC_RESTRICT_FUSED0, PC_COUNT
+  PC_SWEEP_C, PC_CORRECT0, PC_KRYLOV, PC_RBSWEEP0, PC_RBSWEEP_C, PC_RESTRICT_FUSED0, PC_RHS0, PC_COUNT
 };
 static const char* kProfNames[PC_COUNT] = {
   "sweep_colour_finest", "residual_finest", "restrict_finest", "prolong_finest", "norm_finest",
   "coarse_cg", "multipole_moments", "multipole_boundary", "sweep_colour_coarse", "ir_correct",
-  "krylov_vector", "sweep_fused_finest", "sweep_fused_coarse", "resid_restrict_finest"};
+  "krylov_vector", "sweep_fused_finest", "sweep_fused_coarse", "resid_restrict_finest", "rhs_finest"};
 
 // One iteration of a solve, enqueued on a stream; cond/chunk are set when it is
 // being captured into a loop graph.
@@ -521,7 +521,7 @@ ps_status ensure_partials(ps_ctx* h, int nblk) {
 // Multipole boundary (t_mp), scaled right-hand side, state reset and reference
 // norm, all enqueued on s without a host round trip.
 ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, int max_iter,
-                       cudaStream_t s) {
+                       bool own_rhs, cudaStream_t s) {
   TRY(cudaEventRecord(h->ev[0], s));
   if (h->bc.outer == PS_BC_MULTIPOLE) {
     const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
@@ -539,10 +539,12 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
   TRY(cudaEventRecord(h->ev[1], s));
   Coef<double> cf = make_coef<double>(h->d0, h->h0, h->order);
   const double fscale = -4.0 * M_PI * h->bc.G * cf.inv_d;
-  TRY((h->nlaunch += 1, launch_scale_rhs(h->d0, h->du, fscale, rho, DT_F64, h->fs64, s)));
+  if (!own_rhs) TRY((h->nlaunch += 1, launch_scale_rhs(h->d0, h->du, fscale, rho, DT_F64, h->fs64, s)));
   TRY((h->nlaunch += 1, launch_init_state(h->st, tol, max_iter, s)));
   // iterate on the handle's own (pitched) copy of phi: captured loop graphs reference it
   TRY(copy_rows(h->phi0, h->d0, phi, h->du, s));
+  // the compact schemes form R_h f and their reference norm themselves
+  if (own_rhs) return PS_OK;
   // reference norm ||f - A phi0||, phi0 = boundary data only
   TRY((h->nlaunch += 1, launch_delta(h->d0, h->order, h->h0, DT_F64, h->phi0, h->fs64, DT_F64, nullptr, 1.0, true, h->partials, nullptr, s)));
   TRY((h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), cf.d, 0, h->st, s)));
@@ -732,6 +734,9 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
     return e;
   }
   void* r = L.tmp;
+  // FP32 levels smooth out of place, alternating between phi and phib; u is
+  // the array that holds the current iterate
+  void* ub = fp64 ? nullptr : L.phib;
   const double n = (double)L.d.ni() * L.d.nj() * L.d.nk();
   // residual pass: FP64 levels march z through L1, FP32 levels stage planes by TMA
   auto resid = [&](void* out) -> cudaError_t {
@@ -740,14 +745,23 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   };
   auto smooth = [&](int steps) -> cudaError_t {
     for (int it = 0; it < steps; it++) {
+      cudaError_t e2;
+      if (!fp64) {
+        // residual and SPAI step in one pass: reads u and b, writes the other array
+        prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 3.0 * S, n * 32.0, 0, s);
+        e2 = (h->nlaunch += 1, launch_c27_smooth(L.d, C.A[l], C.M[l], C.omega[l], (const float*)u,
+                                                 (const float*)b, (float*)ub, st, &h->st->fault, s));
+        prof_end(h, s);
+        if (e2 != cudaSuccess) return e2;
+        std::swap(u, ub);
+        continue;
+      }
       prof_begin(h, l == 0 ? PC_DELTA0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
-      cudaError_t e2 = (h->nlaunch += 1, resid(r));
+      e2 = (h->nlaunch += 1, resid(r));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
       prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
-      e2 = (h->nlaunch += 1, fp64 ? launch_c27_spai_dt(L.d, C.M[l], C.omega[l], dt, r, u, st, s)
-                                  : launch_c27_tma(L.d, C.M[l], C.omega[l], 1, (const float*)r, nullptr,
-                                                   (float*)u, st, &h->st->fault, s));
+      e2 = (h->nlaunch += 1, launch_c27_spai_dt(L.d, C.M[l], C.omega[l], dt, r, u, st, s));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
     }
@@ -769,7 +783,28 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   e = (h->nlaunch += 1, launch_prolong(L.d, Cl.d, Cl.dt, Cl.phi, dt, u, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
-  return smooth(nu2);
+  if ((e = smooth(nu2)) != cudaSuccess) return e;
+  // an odd number of out-of-place steps leaves the iterate in phib
+  if (u != L.phi) e = cudaMemcpyAsync(L.phi, u, (size_t)L.d.size() * dt_size(dt), cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
+// b = R_h (4 pi G rho), then the initial residual r (stored as dt_r) and the
+// reference norm ||b - A u0|| in one pass; the state takes the reference
+// first, then the initial relative residual.
+static cudaError_t compact_prologue(ps_ctx* h, int order, const W27& A0, const double* rho, const double* phi,
+                                    double* b, int dt_r, void* r, int nb, cudaStream_t s) {
+  const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+  prof_begin(h, PC_RHS0, n * 16.0, n * (order == 6 ? 19.0 : 12.0), 1, s);
+  cudaError_t e = (h->nlaunch += 1, launch_c27_rhs(h->d0, h->du, order, rho, 4.0 * M_PI * h->bc.G, b, s));
+  prof_end(h, s);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, PC_NORM0, n * (16.0 + (double)dt_size(dt_r)), n * 18.0, 1, s);
+  e = (h->nlaunch += 1, launch_c27_init(h->d0, A0, phi, b, dt_r, r, h->partials, s));
+  prof_end(h, s);
+  if (e != cudaSuccess) return e;
+  if ((e = (h->nlaunch += 1, launch_finish_norm(h->partials + 2 * nb, nb, 1.0, 0, h->st, s))) != cudaSuccess) return e;
+  return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s));
 }
 
 ps_status begin_mg_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o, cudaStream_t s) {
@@ -788,15 +823,12 @@ ps_status begin_mg_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
     C->omega.push_back(k[0]);
   }
   const int nb = c27_blocks(h->d0);
-  if ((r = ensure_partials(h, nb)) != PS_OK) return r;
+  if ((r = ensure_partials(h, 2 * nb)) != PS_OK) return r;
   double* b = h->fs64;
   double* rr = (double*)H->lv[0].tmp;
-  // b = R_h (4 pi G rho); reference ||b - A u0|| (u0: boundary data only); initial residual
-  TRY((h->nlaunch += 1, launch_c27_rhs(h->d0, h->du, order, rho, 4.0 * M_PI * h->bc.G, b, s)));
-  TRY((h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, 1, h->partials, nullptr, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 0, h->st, s)));
-  TRY((h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, 0, h->partials, nullptr, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
+  // b = R_h (4 pi G rho); initial residual and reference ||b - A u0|| (u0:
+  // boundary data only) in one pass
+  TRY(compact_prologue(h, order, C->A[0], rho, phi, b, DT_F64, rr, nb, s));
   const int nu1 = o->nu1, nu2 = o->nu2;
   h->act.body = [h, H, C, phi, b, rr, nb, nu1, nu2](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
     cudaError_t e = vcycle_compact(h, H, *C, 0, nu1, nu2, q);
@@ -835,15 +867,18 @@ ps_status begin_ir_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
     C->omega.push_back(k[0]);
   }
   const int nb = c27_blocks(h->d0);
-  if ((r = ensure_partials(h, nb)) != PS_OK) return r;
+  if ((r = ensure_partials(h, 2 * nb)) != PS_OK) return r;
   double* phi = h->phi0;
   double* b64 = h->fs64;
   Level& L0 = H->lv[0];
-  TRY((h->nlaunch += 1, launch_c27_rhs(h->d0, h->du, order, rho, 4.0 * M_PI * h->bc.G, b64, s)));
-  TRY((h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], DT_F64, phi, b64, DT_F32, L0.fs, h->partials, nullptr, s, 1)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 0, h->st, s)));
-  TRY((h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], DT_F64, phi, b64, DT_F32, L0.fs, h->partials, nullptr, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
+  // the out-of-place smoothing steps take the zero boundary of the inner
+  // error equation from the second array of every smoothed level
+  for (int l = 0; l + 1 < h->nlev; l++) {
+    Level& L = H->lv[l];
+    if (!L.phib) return fail(PS_ERR_CUDA, "compact refinement: level %d has no second array", l);
+    TRY(cudaMemsetAsync(L.phib, 0, (size_t)L.d.size() * dt_size(L.dt), s));
+  }
+  TRY(compact_prologue(h, order, C->A[0], rho, phi, b64, DT_F32, L0.fs, nb, s));
   const int nu1 = o->nu1, nu2 = o->nu2, inner = std::max(1, o->inner_cycles);
   h->act.inner_per_iter = inner;
   h->act.body = [h, H, C, phi, b64, nb, nu1, nu2, inner](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
@@ -1511,7 +1546,9 @@ ps_status poisson_create(const ps_grid* grid, const double* const coords_host[3]
     if ((s = alloc_zero((void**)&h->fs64, (size_t)h->d0.size() * 8, &h->bytes)) != PS_OK) return bail(s);
     if ((s = alloc_zero((void**)&h->phi0, (size_t)h->d0.size() * 8, &h->bytes)) != PS_OK) return bail(s);
     if ((s = ensure_partials(h, std::max({cart_partials_count(h->d0), delta_colours_partials(h->d0, stencil_order),
-                                                  batch_norm_partials(h->d0, stencil_order)}))) != PS_OK) return bail(s);
+                                                  batch_norm_partials(h->d0, stencil_order),
+                                                  stencil_order == 2 ? 2 * c27_blocks(h->d0) : 0}))) != PS_OK)
+      return bail(s);
     if (b.outer == PS_BC_MULTIPOLE) {
       build_multipole_tables(l_max, &h->mpt);
       if ((e = cart_multipole_alloc(h->du, l_max, h->mpt, &h->mp)) != cudaSuccess)
@@ -1638,7 +1675,8 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   if (h->sph) {
     r = begin_sph(h, rho_dev, phi_dev, tol, &o, s);
   } else {
-    if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, s)) != PS_OK) return r;
+    const bool compact = o.method == PS_MG && o.compact_order != 0;
+    if ((r = cart_prepare(h, rho_dev, phi_dev, tol, o.max_iter, compact, s)) != PS_OK) return r;
     if (o.method == PS_MG && o.compact_order != 0)
       r = o.prec == PS_FP64 ? begin_mg_compact(h, rho_dev, &o, s) : begin_ir_compact(h, rho_dev, &o, s);
     else if (o.method == PS_MG) r = o.prec == PS_FP64 ? begin_mg64(h, &o, s) : begin_ir(h, &o, s);
@@ -1839,7 +1877,7 @@ ps_status poisson_batch_add(ps_batch b, ps_handle h, const double* rho_dev, doub
   TRY(cudaStreamWaitEvent(s, h->ev_in, 0));
   h->nlaunch = 0;
   ps_status r;
-  if ((r = cart_prepare(h, rho_dev, phi_dev, tol, max_iter, s)) != PS_OK) return r;
+  if ((r = cart_prepare(h, rho_dev, phi_dev, tol, max_iter, false, s)) != PS_OK) return r;
   Hier* H = b->prec == PS_FP64 ? &h->h64 : &h->hmx[0];
   if ((r = build_hier(h, b->prec == PS_FP64 ? 0 : 1, H)) != PS_OK) return r;
   if (b->prec == PS_FP64) {
