@@ -21,6 +21,7 @@
 // about 15 FP64 instructions per node instead of 27.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "cart_kernels.cuh"
@@ -140,6 +141,22 @@ __device__ __forceinline__ C apply_planes(const C w[4], const Plane<C>& m, const
   return fma(w[0], c.c, fma(w[1], (c.f + (m.c + p.c)), fma(w[2], (c.e + (m.f + p.f)), w[3] * (m.e + p.e))));
 }
 
+// Per-plane split of a 27-point class stencil w (centre, faces, edges,
+// corners): with the in-plane sums (C, F, E) of planes z - 1, z, z + 1,
+//   (A u)(z) = P(z) + Q(z - 1) + Q(z + 1),
+//   P = w0 C + w1 F + w2 E,   Q = w1 C + w2 F + w3 E,
+// so each plane's Q serves the nodes above and below it.  With nw = -s w
+// (s = 1 for a residual, omega for a SPAI step) the pass value is
+//   base - s P - s Q(z - 1) - s Q(z + 1) = base + nP + (nQ(z - 1) + nQ(z + 1)).
+template <typename C>
+__device__ __forceinline__ C plane_q(const C nw[4], const Plane<C>& p) {
+  return fma(nw[1], p.c, fma(nw[2], p.f, nw[3] * p.e));
+}
+template <typename C>
+__device__ __forceinline__ C plane_p_plus(const C nw[4], const Plane<C>& p, C base, C qm, C qp) {
+  return fma(nw[0], p.c, fma(nw[1], p.f, fma(nw[2], p.e, base))) + (qm + qp);
+}
+
 // per-block {sum, 0} into partials[2 b], partials[2 b + 1] (blocks of CBX x CBY threads)
 __device__ __forceinline__ void block_partial(double v, double* __restrict__ partials) {
   __shared__ double sh[CBX * CBY / 32];
@@ -177,25 +194,49 @@ __global__ void __launch_bounds__(CBX* CBY)
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
   double s2 = 0.0;
   if (i <= d.ni() && j <= d.nj()) {
-    Plane<C> pm = plane_of(plane_load<ZI>(d, src, i, j, k0 - 1));
-    Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
-    Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
-    for (int k = k0; k < k1; k++) {
-      Raw9<C> nn = nx;
-      if (k + 2 <= k1) nn = plane_load<ZI>(d, src, i, j, k + 2);   // plane k1 <= nk + 1 exists
-      const Plane<C> pn = plane_of(nx);
-      const C a = apply_planes<C>(W.w, pm, pc, pn);
-      const long long q = d.at(i, j, k);
-      if (MODE == 0) {
-        const C r = (C)b[q] - a;
-        dst[q] = (TR)r;
-        if (NORM) s2 = fma((double)r, (double)r, s2);
-      } else {
-        dst[q] = (TR)fma(-om, a, (C)dst[q]);
+    if constexpr (std::is_same<C, double>::value) {
+      // FP64: the per-plane split of the stencil (14 FP64 operations per node)
+      Wts<C> nw;
+      for (int a = 0; a < 4; a++) nw.w[a] = MODE == 0 ? -W.w[a] : -om * W.w[a];
+      Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
+      C qm = plane_q(nw.w, plane_of(plane_load<ZI>(d, src, i, j, k0 - 1)));
+      C qc = plane_q(nw.w, pc);
+      Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
+      for (int k = k0; k < k1; k++) {
+        Raw9<C> nn = nx;
+        if (k + 2 <= k1) nn = plane_load<ZI>(d, src, i, j, k + 2);   // plane k1 <= nk + 1 exists
+        const Plane<C> pn = plane_of(nx);
+        const C qn = plane_q(nw.w, pn);
+        const long long q = d.at(i, j, k);
+        const C v = plane_p_plus(nw.w, pc, MODE == 0 ? (C)b[q] : (C)dst[q], qm, qn);
+        dst[q] = (TR)v;
+        if (MODE == 0 && NORM) s2 = fma((double)v, (double)v, s2);
+        qm = qc;
+        qc = qn;
+        pc = pn;
+        nx = nn;
       }
-      pm = pc;
-      pc = pn;
-      nx = nn;
+    } else {
+      Plane<C> pm = plane_of(plane_load<ZI>(d, src, i, j, k0 - 1));
+      Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
+      Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
+      for (int k = k0; k < k1; k++) {
+        Raw9<C> nn = nx;
+        if (k + 2 <= k1) nn = plane_load<ZI>(d, src, i, j, k + 2);   // plane k1 <= nk + 1 exists
+        const Plane<C> pn = plane_of(nx);
+        const C a = apply_planes<C>(W.w, pm, pc, pn);
+        const long long q = d.at(i, j, k);
+        if (MODE == 0) {
+          const C r = (C)b[q] - a;
+          dst[q] = (TR)r;
+          if (NORM) s2 = fma((double)r, (double)r, s2);
+        } else {
+          dst[q] = (TR)fma(-om, a, (C)dst[q]);
+        }
+        pm = pc;
+        pc = pn;
+        nx = nn;
+      }
     }
   }
   if (MODE == 0 && NORM && partials != nullptr) block_partial(s2, partials);
@@ -227,14 +268,15 @@ __device__ __forceinline__ void block_partial2(double v, double w, double* __res
   }
 }
 
-// Initial residual pass of a compact solve (FP64 arithmetic): r = b - A u
-// stored as TR with per-block partials of r^2, and in the same pass the
+// Initial residual pass of a compact solve (FP64 arithmetic, the per-plane
+// split of the stencil): r = b - A u stored as TR with per-block partials of
+// r^2, and in the same pass the
 // reference residual b - A u0 of the boundary data alone (u0: u with its
 // interior zeroed), whose partials go to partials + 2 nblocks.  A u0 vanishes
 // unless a node has a boundary node among its 26 neighbours, so only the
 // first and last interior layers of each axis evaluate it; elsewhere the
 // reference residual is b.  Both sums are the ones two separate passes
-// (interior zeroed, then full) would form, in the same order.
+// (interior zeroed, then full) of k_c27 would form, in the same order.
 template <typename TR>
 __global__ void __launch_bounds__(CBX* CBY)
     k_c27_init(Dims d, Wts<double> W, const double* __restrict__ u, const double* __restrict__ b,
@@ -245,28 +287,31 @@ __global__ void __launch_bounds__(CBX* CBY)
   double s2 = 0.0, s0 = 0.0;
   if (i <= d.ni() && j <= d.nj()) {
     const bool side = i == 1 || i == d.ni() || j == 1 || j == d.nj();
-    Plane<double> pm = plane_of(plane_load<false>(d, u, i, j, k0 - 1));
+    Wts<double> nw;
+    for (int a = 0; a < 4; a++) nw.w[a] = -W.w[a];
     Plane<double> pc = plane_of(plane_load<false>(d, u, i, j, k0));
+    double qm = plane_q(nw.w, plane_of(plane_load<false>(d, u, i, j, k0 - 1)));
+    double qc = plane_q(nw.w, pc);
     Raw9<double> nx = plane_load<false>(d, u, i, j, k0 + 1);
     for (int k = k0; k < k1; k++) {
       Raw9<double> nn = nx;
       if (k + 2 <= k1) nn = plane_load<false>(d, u, i, j, k + 2);
       const Plane<double> pn = plane_of(nx);
-      const double a = apply_planes<double>(W.w, pm, pc, pn);
+      const double qn = plane_q(nw.w, pn);
       const long long q = d.at(i, j, k);
       const double bq = b[q];
-      const double rv = bq - a;
+      const double rv = plane_p_plus(nw.w, pc, bq, qm, qn);
       r[q] = (TR)rv;
       s2 = fma(rv, rv, s2);
       double r0 = bq;
       if (side || k == 1 || k == d.nk()) {
-        const double a0 = apply_planes<double>(W.w, plane_of(plane_load<true>(d, u, i, j, k - 1)),
-                                               plane_of(plane_load<true>(d, u, i, j, k)),
-                                               plane_of(plane_load<true>(d, u, i, j, k + 1)));
-        r0 = bq - a0;
+        r0 = plane_p_plus(nw.w, plane_of(plane_load<true>(d, u, i, j, k)), bq,
+                          plane_q(nw.w, plane_of(plane_load<true>(d, u, i, j, k - 1))),
+                          plane_q(nw.w, plane_of(plane_load<true>(d, u, i, j, k + 1))));
       }
       s0 = fma(r0, r0, s0);
-      pm = pc;
+      qm = qc;
+      qc = qn;
       pc = pn;
       nx = nn;
     }
