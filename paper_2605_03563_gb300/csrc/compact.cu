@@ -512,147 +512,192 @@ cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, 
 // ------------------------------------------------------------------ fused FP32 smoothing step
 // One SPAI step u' = u - omega M (b - A u) of an inner FP32 level in a single
 // pass, out of place (u' goes to another array, so no block reads a value
-// that a neighbouring block has already replaced).  Each block owns a 32 x 8
-// tile and a z-chunk; per plane it forms the residual on the tile with a
-// one-node halo (34 x 10 nodes, zero at boundary nodes) into a 3-plane ring in
-// shared memory, then applies M to the residual planes k - 1, k, k + 1.
-// u (box 40 x 12 from x = 32 bx - 4, y = y0 - 2) and b (box 40 x 10 from
-// y = y0 - 1) arrive by TMA, one stage per plane z holding both boxes.  The
-// arithmetic is that of the residual pass followed by the SPAI pass of
-// k_c27_tma, operation for operation, so both routes give the same bits; the
-// fused one moves 12 bytes per node instead of 24.
-static constexpr int FTX = 32, FTY = 8;              // output tile
-static constexpr int FRX = FTX + 2, FRY = FTY + 2;   // residual region: 34 x 10
-static constexpr int FUW = 40, FUH = FTY + 4;        // staged u box
-static constexpr int FBW = 40, FBH = FTY + 2;        // staged b box
-static constexpr int FNS = 8;                        // stages (planes of u and b), a power of two
-static constexpr int FRS = 4;                        // residual planes in the ring, a power of two
-static constexpr int FUB = FUW * FUH * 4, FBB = FBW * FBH * 4;
-static constexpr int FUBA = (FUB + 127) / 128 * 128, FBBA = (FBB + 127) / 128 * 128;
-static constexpr int FSTAGE = FUBA + FBBA;
-static constexpr int FTHREADS = 352;                 // 11 warps
-static_assert((FNS & (FNS - 1)) == 0 && (FRS & (FRS - 1)) == 0 && FRS >= 3, "ring sizes");
-static_assert(FRX == 32 + 2 && 2 * FRY <= 32 && FTHREADS == 32 * (FRY + 1) && FTX == 32, "thread roles");
+// that a neighbouring block has already replaced), register-blocked.
+//
+// A block of GW warps owns a 30 x (GW GR) tile of outputs and a z-chunk;
+// warp w owns the strip of GR output rows y0 + GR w .., lane l the column
+// x = x0 - 1 + l (lanes 1..30 write; lanes 0 and 31 only supply the
+// residual's x-neighbours).  Per plane of the z-march each warp
+//  - forms the in-plane sums (centre, faces, diagonals) of u on its GR + 2
+//    residual rows from GR + 4 staged u rows, sharing the pair sums
+//    u(x-1) + u(x+1) between rows;
+//  - forms the residual r = b - A u of plane k + 1 on those rows (zero off
+//    the interior) from the sums of planes k, k + 1, k + 2 held in registers;
+//  - takes r's x-neighbours by shuffles, forms its in-plane sums on the GR
+//    output rows and writes u'(k) from the sums of planes k - 1, k, k + 1.
+// The residual rows next to a strip edge are also formed by the neighbouring
+// strip, so warps never exchange residuals.  u (box 40 x (GW GR + 4)) and b
+// (box 40 x (GW GR + 2)), both from x = 4 floor((x0 - 2) / 4), arrive by TMA,
+// one stage per plane; one block barrier per plane returns a stage to the
+// copy engine.  The sums and the stencil arithmetic are those of the residual
+// pass followed by the SPAI pass of k_c27_tma, in the same association, so
+// the results are bit-identical to that route; traffic is 12 bytes per node
+// instead of 24.
+static constexpr int GW = 4, GR = 4;                  // warps per block, output rows per warp
+static constexpr int GTX = 30, GTY = GW * GR;         // output tile
+static constexpr int GRR = GR + 2, GUR = GR + 4;      // residual rows and u rows per warp
+static constexpr int GBW = 40, GUH = GTY + 4, GBH = GTY + 2;
+static constexpr int GNS = 6;                         // stages (planes of u and b)
+static constexpr int GUB = GBW * GUH * 4, GBB = GBW * GBH * 4;
+static constexpr int GUBA = (GUB + 127) / 128 * 128, GBBA = (GBB + 127) / 128 * 128;
+static constexpr int GSTAGE = GUBA + GBBA;
 
-// Thread roles: warps 0..9 form the residual on row ry = warp, columns
-// rx = lane (0..31) of the 34 x 10 region, warp 10 on its columns 32 and 33;
-// warps 0..7 then write output row oy = warp, column ox = lane.  A warp's
-// shared-memory reads of one row are 32 consecutive words (no bank conflict).
-__global__ void __launch_bounds__(FTHREADS)
+struct SmoothMarch {
+  float us[3][GRR][3];   // u sums (c, f, e) of three planes on the residual rows
+  float rs[3][GR][3];    // residual sums of three planes on the output rows
+};
+
+__device__ __forceinline__ void c27_usums(const float* __restrict__ U, float (&S)[GRR][3]) {
+  float c[GUR], a[GUR];
+#pragma unroll
+  for (int s = 0; s < GUR; s++) {
+    c[s] = U[s * GBW];
+    a[s] = U[s * GBW - 1] + U[s * GBW + 1];
+  }
+#pragma unroll
+  for (int t = 0; t < GRR; t++) {
+    S[t][0] = c[t + 1];
+    S[t][1] = a[t + 1] + (c[t] + c[t + 2]);
+    S[t][2] = a[t] + a[t + 2];
+  }
+}
+
+__device__ __forceinline__ Plane<float> pl3(const float (&v)[3]) { return Plane<float>{v[0], v[1], v[2]}; }
+
+__device__ __forceinline__ void c27_rsums(const float (&r)[GRR], float (&R)[GR][3]) {
+  float ar[GRR];
+#pragma unroll
+  for (int t = 0; t < GRR; t++) {
+    const float l = __shfl_up_sync(0xffffffffu, r[t], 1);
+    const float h = __shfl_down_sync(0xffffffffu, r[t], 1);
+    ar[t] = l + h;
+  }
+#pragma unroll
+  for (int q = 0; q < GR; q++) {
+    R[q][0] = r[q + 1];
+    R[q][1] = ar[q + 1] + (r[q] + r[q + 2]);
+    R[q][2] = ar[q] + ar[q + 2];
+  }
+}
+
+__global__ void __launch_bounds__(32 * GW, 4)
     k_c27_smooth(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mB, Dims d,
                  Wts<float> WA, Wts<float> WM, float om, float* __restrict__ dst, int zc,
                  const DevState* __restrict__ st, int* __restrict__ fault) {
-  __shared__ __align__(128) unsigned char smem[FNS * FSTAGE];
-  __shared__ float rring[FRS][FRX * FRY];
-  __shared__ __align__(8) unsigned long long bar[FNS];
+  __shared__ __align__(128) unsigned char smem[GNS * GSTAGE];
+  __shared__ __align__(8) unsigned long long bar[GNS];
   if (st != nullptr && st->done) return;   // uniform
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * FTX + 1, y0 = blockIdx.y * FTY + 1;   // first output node
-  const int xs = x0 - 5;                                              // box x start: 32 bx - 4
+  const int x0 = blockIdx.x * GTX + 1, y0b = blockIdx.y * GTY + 1;   // first output node of the tile
+  const int xs = ((x0 - 2) >> 2) << 2;                               // box x start, a multiple of 4
   const int k0 = 1 + blockIdx.z * zc, k1 = min(k0 + zc, d.nk() + 1);  // output planes [k0, k1)
   const int zl = k0 - 2, zh = k1 + 1;                                 // staged planes [zl, zh]
   if (tid == 0) {
-    for (int q = 0; q < FNS; q++) mbar_init(&bar[q], 1);
+    for (int q = 0; q < GNS; q++) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto stage = [&](int z) -> unsigned { return (unsigned)(z - zl) & (FNS - 1); };
-  auto ubox = [&](int z) -> float* { return reinterpret_cast<float*>(smem + stage(z) * FSTAGE); };
-  auto bbox = [&](int z) -> float* { return reinterpret_cast<float*>(smem + stage(z) * FSTAGE + FUBA); };
-  auto rbuf = [&](int z) -> float* { return rring[(unsigned)(z - zl) & (FRS - 1)]; };
+  auto stage = [&](int z) -> int { return (z - zl) % GNS; };
   auto issue = [&](int z) {   // thread 0: stage of plane z
     if (z > zh) return;
+    unsigned char* p = smem + stage(z) * GSTAGE;
     unsigned long long* br = &bar[stage(z)];
-    mbar_expect_tx(br, FUB + FBB);
-    tma_load_3d(ubox(z), &mU, xs, y0 - 2, z, br);
-    tma_load_3d(bbox(z), &mB, xs, y0 - 1, z, br);
+    mbar_expect_tx(br, GUB + GBB);
+    tma_load_3d(p, &mU, xs, y0b - 2, z, br);
+    tma_load_3d(p + GUBA, &mB, xs, y0b - 1, z, br);
   };
   if (tid == 0)
-    for (int z = zl; z < zl + FNS; z++) issue(z);
+    for (int z = zl; z < zl + GNS; z++) issue(z);
   bool ok = true;
   int wq = 0;
   unsigned wph = 0;
   auto wait_next = [&]() {
     mbar_wait(&bar[wq], wph, ok);
-    if (++wq == FNS) { wq = 0; wph ^= 1u; }
+    if (++wq == GNS) { wq = 0; wph ^= 1u; }
   };
-  // residual node of this thread: (x0 - 1 + rx, y0 - 1 + ry)
-  const bool redge = warp == FRY;
-  const int rx = redge ? FTX + (lane & 1) : lane, ry = redge ? lane >> 1 : warp;
-  const bool rthr = warp < FRY || (redge && lane < 2 * FRY);
-  const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
-  const bool rin = rthr && gx >= 1 && gx <= d.ni() && gy >= 1 && gy <= d.nj();
-  const int su = (ry + 1) * FUW + (rx + 4);   // u box index of the residual node
-  const int sb = ry * FBW + (rx + 4);         // b box index
-  const int sw = ry * FRX + rx;               // residual ring index
-  auto sums9 = [](const float* P, int c, int w) -> Plane<float> {
-    Raw9<float> v;
-    v.c = P[c];
-    v.xm = P[c - 1];
-    v.xp = P[c + 1];
-    v.ym = P[c - w];
-    v.yp = P[c + w];
-    v.mm = P[c - w - 1];
-    v.pm = P[c - w + 1];
-    v.mp = P[c + w - 1];
-    v.pp = P[c + w + 1];
-    return plane_of(v);
+  // this lane's residual column and its rows y0w - 1 + t (t = 0 .. GR + 1)
+  const int x = x0 - 1 + lane;
+  const int y0w = y0b + GR * warp;
+  const int col = x - xs;   // box column of x (1 .. 36)
+  const bool xin = x >= 1 && x <= d.ni();
+  bool rok[GRR];
+#pragma unroll
+  for (int t = 0; t < GRR; t++) rok[t] = xin && y0w - 1 + t >= 1 && y0w - 1 + t <= d.nj();
+  bool oin[GR];
+#pragma unroll
+  for (int q = 0; q < GR; q++) oin[q] = lane >= 1 && lane <= GTX && x <= d.ni() && y0w + q <= d.nj();
+  auto ubase = [&](int z) -> const float* {   // u row y0w - 2 at column x
+    return reinterpret_cast<const float*>(smem + stage(z) * GSTAGE) + GR * warp * GBW + col;
   };
-  Plane<float> um{}, uc{};
-  // residual plane z from u planes z - 1 (um), z (uc), z + 1 (read here); zero off the interior
-  auto rstep = [&](int z) {
-    if (!rthr) return;
-    const Plane<float> un = sums9(ubox(z + 1), su, FUW);
-    float rv = 0.0f;
-    if (rin && z >= 1 && z <= d.nk()) rv = bbox(z)[sb] - apply_planes<float>(WA.w, um, uc, un);
-    rbuf(z)[sw] = rv;
-    um = uc;
-    uc = un;
+  auto bbase = [&](int z) -> const float* {   // b row y0w - 1 at column x
+    return reinterpret_cast<const float*>(smem + stage(z) * GSTAGE + GUBA) + GR * warp * GBW + col;
   };
-  // output node of this thread (warps 0..7): (x0 + lane, y0 + warp)
-  const bool othr = warp < FTY;
-  const int i = x0 + lane, j = y0 + warp;
-  const bool oin = othr && i <= d.ni() && j <= d.nj();
-  const int sr = (warp + 1) * FRX + (lane + 1);   // residual ring index of the output node
-  const int so = (warp + 2) * FUW + (lane + 5);   // u box index of the output node
+  // residual of plane z on the residual rows from the u sums of planes z - 1, z, z + 1
+  auto resid = [&](int z, const float (&Sm)[GRR][3], const float (&Sc)[GRR][3], const float (&Sn)[GRR][3],
+                   float (&r)[GRR]) {
+    const bool zin = z >= 1 && z <= d.nk();
+    const float* B = bbase(z);
+#pragma unroll
+    for (int t = 0; t < GRR; t++) {
+      float rv = 0.0f;
+      if (zin && rok[t]) rv = B[t * GBW] - apply_planes<float>(WA.w, pl3(Sm[t]), pl3(Sc[t]), pl3(Sn[t]));
+      r[t] = rv;
+    }
+  };
+  const long long sy = d.sy(), sz = d.sz();
+  float* ob = dst + d.at(min(max(x, 1), d.ni()), min(y0w, d.nj()), k0);   // output row y0w, plane k0
+  SmoothMarch m;
   // prologue: residual planes k0 - 1 and k0 (u planes k0 - 2 .. k0 + 1)
-  wait_next();
-  wait_next();
-  wait_next();
-  if (rthr) {
-    um = sums9(ubox(zl), su, FUW);
-    uc = sums9(ubox(zl + 1), su, FUW);
+  {
+    float r[GRR];
+    wait_next();
+    c27_usums(ubase(zl), m.us[0]);
+    wait_next();
+    c27_usums(ubase(zl + 1), m.us[1]);
+    wait_next();
+    c27_usums(ubase(zl + 2), m.us[2]);
+    resid(k0 - 1, m.us[0], m.us[1], m.us[2], r);
+    c27_rsums(r, m.rs[0]);
+    wait_next();
+    c27_usums(ubase(zl + 3), m.us[0]);
+    resid(k0, m.us[1], m.us[2], m.us[0], r);
+    c27_rsums(r, m.rs[1]);
   }
-  rstep(k0 - 1);
-  wait_next();
-  rstep(k0);
   __syncthreads();
-  if (tid == 0) {   // planes k0 - 2 and k0 - 1 are no longer read
+  if (tid == 0) {   // planes k0 - 2 .. k0 are no longer read
     fence_proxy_async();
-    issue(zl + FNS);
-    issue(zl + 1 + FNS);
+    issue(zl + GNS);
+    issue(zl + 1 + GNS);
+    issue(zl + 2 + GNS);
   }
-  Plane<float> rm{}, rc{};
-  if (othr) {
-    rm = sums9(rbuf(k0 - 1), sr, FRX);
-    rc = sums9(rbuf(k0), sr, FRX);
-  }
-  const long long sz = d.sz();
-  float* out = dst + d.at(min(i, d.ni()), min(j, d.nj()), k0);
-  for (int k = k0; k < k1; k++, out += sz) {
+  // output plane k; P = (k - k0) mod 3 fixes the register slots:
+  // u sums of planes k, k + 1, k + 2 in us[(P+2)%3], us[P], us[(P+1)%3],
+  // residual sums of planes k - 1, k, k + 1 in rs[P], rs[(P+1)%3], rs[(P+2)%3]
+  auto step = [&](auto Pc, int k) {
+    constexpr int P = decltype(Pc)::value;
+    constexpr int UK = (P + 2) % 3, UK1 = P, UK2 = (P + 1) % 3;
+    constexpr int RM = P, RC = (P + 1) % 3, RN = (P + 2) % 3;
     wait_next();   // plane k + 2
-    rstep(k + 1);
-    __syncthreads();   // residual plane k + 1 complete; every thread is past output k - 1
-    if (tid == 0 && k > k0) {
+    c27_usums(ubase(k + 2), m.us[UK2]);
+    float r[GRR];
+    resid(k + 1, m.us[UK], m.us[UK1], m.us[UK2], r);
+    c27_rsums(r, m.rs[RN]);
+#pragma unroll
+    for (int q = 0; q < GR; q++)
+      if (oin[q])
+        ob[q * sy] = fmaf(-om, apply_planes<float>(WM.w, pl3(m.rs[RM][q]), pl3(m.rs[RC][q]), pl3(m.rs[RN][q])),
+                          m.us[UK][q + 1][0]);
+    ob += sz;
+    __syncthreads();   // plane k + 1 (its b) is no longer read
+    if (tid == 0) {
       fence_proxy_async();
-      issue(k - 1 + FNS);   // plane k - 1 is no longer read
+      issue(k + 1 + GNS);
     }
-    if (othr) {
-      const Plane<float> rn = sums9(rbuf(k + 1), sr, FRX);
-      if (oin) *out = fmaf(-om, apply_planes<float>(WM.w, rm, rc, rn), ubox(k)[so]);
-      rm = rc;
-      rc = rn;
-    }
+  };
+  for (int k = k0; k < k1; k += 3) {
+    step(std::integral_constant<int, 0>(), k);
+    if (k + 1 < k1) step(std::integral_constant<int, 1>(), k + 1);
+    if (k + 2 < k1) step(std::integral_constant<int, 2>(), k + 2);
   }
   if (!ok && fault != nullptr) atomicExch(fault, 1);
 }
@@ -661,20 +706,20 @@ cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double 
                               const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
   if (d.g != 1 || u == dst) return cudaErrorInvalidValue;
   CUtensorMap mu, mb;
-  if (!encode_level_map(&mu, DT_F32, u, d, FUW, FUH)) return cudaErrorInvalidValue;
-  if (!encode_level_map(&mb, DT_F32, b, d, FBW, FBH)) return cudaErrorInvalidValue;
+  if (!encode_level_map(&mu, DT_F32, u, d, GBW, GUH)) return cudaErrorInvalidValue;
+  if (!encode_level_map(&mb, DT_F32, b, d, GBW, GBH)) return cudaErrorInvalidValue;
   if (g_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_sms <= 0) g_sms = 152;
   }
-  const int gx = (d.ni() + FTX - 1) / FTX, gy = (d.nj() + FTY - 1) / FTY, nk = d.nk();
-  // about two waves of 5 blocks per SM, z-chunks of at least 16 planes (3 extra staged planes each)
-  const int want = std::max(1, 10 * g_sms / (gx * gy));
+  const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + GTY - 1) / GTY, nk = d.nk();
+  // about three waves of 4 blocks per SM, z-chunks of at least 16 planes (4 extra staged planes each)
+  const int want = std::max(1, 12 * g_sms / (gx * gy));
   const int zc = std::max(16, (nk + want - 1) / want);
   const dim3 grid(gx, gy, (nk + zc - 1) / zc);
-  k_c27_smooth<<<grid, FTHREADS, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
+  k_c27_smooth<<<grid, 32 * GW, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
   return cudaGetLastError();
 }
 
