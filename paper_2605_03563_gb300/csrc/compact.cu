@@ -176,8 +176,8 @@ __device__ __forceinline__ void block_partial(double v, double* __restrict__ par
 }
 
 // MODE 0: r = b - A u (ZI: u's interior read as 0; r stored as TR), partials if
-// given; MODE 1: u -= omega M r.  Arithmetic in the compute type of T (FP64 for
-// FP64 storage, FP32 for FP32 storage).
+// given; MODE 1: u -= omega M r.  Arithmetic in FP32 (FP32 storage; the FP64
+// passes run k_c27_f64).
 // NORM: the residual pass also forms per-block partials of r^2 (in FP64; FP32
 // inner passes skip it, so they touch no FP64 instruction).
 // The loads of plane k + 2 are issued before the arithmetic of plane k, so two
@@ -194,29 +194,7 @@ __global__ void __launch_bounds__(CBX* CBY)
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
   double s2 = 0.0;
   if (i <= d.ni() && j <= d.nj()) {
-    if constexpr (std::is_same<C, double>::value) {
-      // FP64: the per-plane split of the stencil (14 FP64 operations per node)
-      Wts<C> nw;
-      for (int a = 0; a < 4; a++) nw.w[a] = MODE == 0 ? -W.w[a] : -om * W.w[a];
-      Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
-      C qm = plane_q(nw.w, plane_of(plane_load<ZI>(d, src, i, j, k0 - 1)));
-      C qc = plane_q(nw.w, pc);
-      Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
-      for (int k = k0; k < k1; k++) {
-        Raw9<C> nn = nx;
-        if (k + 2 <= k1) nn = plane_load<ZI>(d, src, i, j, k + 2);   // plane k1 <= nk + 1 exists
-        const Plane<C> pn = plane_of(nx);
-        const C qn = plane_q(nw.w, pn);
-        const long long q = d.at(i, j, k);
-        const C v = plane_p_plus(nw.w, pc, MODE == 0 ? (C)b[q] : (C)dst[q], qm, qn);
-        dst[q] = (TR)v;
-        if (MODE == 0 && NORM) s2 = fma((double)v, (double)v, s2);
-        qm = qc;
-        qc = qn;
-        pc = pn;
-        nx = nn;
-      }
-    } else {
+    {
       Plane<C> pm = plane_of(plane_load<ZI>(d, src, i, j, k0 - 1));
       Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
       Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
@@ -319,6 +297,125 @@ __global__ void __launch_bounds__(CBX* CBY)
   block_partial2(s2, s0, partials, partials + 2 * nblocks);
 }
 
+// per-block {sum, 0} into partials[2 b], partials[2 b + 1] for blocks of NT threads
+template <int NT>
+__device__ __forceinline__ void block_partial_nt(double v, double* __restrict__ partials) {
+  __shared__ double sh[NT / 32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  v = warp_sum(v);
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double a = tid < NT / 32 ? sh[tid] : 0.0;
+    a = warp_sum(a);
+    if (tid == 0) {
+      const int bid = block_linear_id();
+      partials[2 * bid] = a;
+      partials[2 * bid + 1] = 0.0;
+    }
+  }
+}
+
+// FP64 passes (GB300's FP64 pipe bounds them, so they minimise FP64
+// instructions): MODE 0: r = b - A u stored as TR (ZI: u's interior read as 0),
+// per-block partials of r^2 if given; MODE 1: u -= omega M r.  A thread owns
+// FRB consecutive rows of one column and marches z: per plane it loads the
+// FRB + 2 rows x 3 columns around them, forms the pair sums u(x-1) + u(x+1)
+// once per row and from them the in-plane sums (centre, faces, diagonals) of
+// its rows, and applies the per-plane split P(z) + Q(z - 1) + Q(z + 1) of the
+// stencil: 12.5 FP64 operations per node.  The loads of plane k + 2 are issued
+// before the arithmetic of plane k.  Blocks of 32 x (CBY / FRB) threads cover
+// the 32 x 8 tiles of c27_grid, so the partials count is c27_blocks(d).
+static constexpr int FRB = 4;
+template <int MODE, bool ZI, typename TR, bool NORM>
+__global__ void __launch_bounds__(CBX*(CBY / FRB))
+    k_c27_f64(Dims d, Wts<double> W, double om, const double* __restrict__ src, const double* __restrict__ b,
+              TR* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;   // uniform
+  const int i = blockIdx.x * CBX + threadIdx.x + 1;
+  const int j0 = blockIdx.y * CBY + threadIdx.y * FRB + 1;   // rows j0 .. j0 + FRB - 1
+  const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
+  double s2 = 0.0;
+  if (i <= d.ni() && j0 <= d.nj()) {
+    Wts<double> nw;
+#pragma unroll
+    for (int a = 0; a < 4; a++) nw.w[a] = MODE == 0 ? -W.w[a] : -om * W.w[a];
+    const long long sz = d.sz();
+    // rows j0 - 1 + s; rows past the ghost row nj + 1 are clamped to it: they
+    // only feed rows that are not written
+    long long roff[FRB + 2];
+    bool rin[FRB + 2];
+#pragma unroll
+    for (int s = 0; s < FRB + 2; s++) {
+      const int y = min(j0 - 1 + s, d.nj() + 1);
+      roff[s] = (long long)y * d.sy() + i;
+      rin[s] = y >= 1 && y <= d.nj();
+    }
+    const bool cin = i >= 1 && i <= d.ni(), lin = i - 1 >= 1, hin = i + 1 <= d.ni();
+    // raw values of one plane: rows s = 0 .. FRB + 1, columns i - 1, i, i + 1
+    auto load = [&](int k, double (&v)[FRB + 2][3]) {
+      const double* p = src + (long long)k * sz;
+      const bool kin = k >= 1 && k <= d.nk();
+#pragma unroll
+      for (int s = 0; s < FRB + 2; s++) {
+        v[s][0] = (ZI && kin && rin[s] && lin) ? 0.0 : p[roff[s] - 1];
+        v[s][1] = (ZI && kin && rin[s] && cin) ? 0.0 : p[roff[s]];
+        v[s][2] = (ZI && kin && rin[s] && hin) ? 0.0 : p[roff[s] + 1];
+      }
+    };
+    // in-plane sums of the thread's rows and their Q
+    auto sums = [&](const double (&v)[FRB + 2][3], double (&C)[FRB], double (&F)[FRB], double (&E)[FRB],
+                    double (&Q)[FRB]) {
+      double a[FRB + 2];
+#pragma unroll
+      for (int s = 0; s < FRB + 2; s++) a[s] = v[s][0] + v[s][2];
+#pragma unroll
+      for (int q = 0; q < FRB; q++) {
+        C[q] = v[q + 1][1];
+        F[q] = a[q + 1] + (v[q][1] + v[q + 2][1]);
+        E[q] = a[q] + a[q + 2];
+        Q[q] = fma(nw.w[1], C[q], fma(nw.w[2], F[q], nw.w[3] * E[q]));
+      }
+    };
+    double v[FRB + 2][3], vn[FRB + 2][3];
+    double C[FRB], F[FRB], E[FRB], qm[FRB], qc[FRB];
+    {
+      double tC[FRB], tF[FRB], tE[FRB];
+      load(k0 - 1, v);
+      sums(v, tC, tF, tE, qm);
+    }
+    load(k0, v);
+    sums(v, C, F, E, qc);
+    load(k0 + 1, v);
+    for (int k = k0; k < k1; k++) {
+      if (k + 2 <= k1) load(k + 2, vn);   // plane k1 <= nk + 1 exists
+      double nC[FRB], nF[FRB], nE[FRB], qn[FRB];
+      sums(v, nC, nF, nE, qn);
+      const long long base = (long long)k * sz;
+#pragma unroll
+      for (int q = 0; q < FRB; q++) {
+        if (j0 + q <= d.nj()) {
+          const long long o = base + roff[q + 1];
+          const double bv = MODE == 0 ? b[o] : (double)dst[o];
+          const double val = fma(nw.w[0], C[q], fma(nw.w[1], F[q], fma(nw.w[2], E[q], bv))) + (qm[q] + qn[q]);
+          dst[o] = (TR)val;
+          if (MODE == 0 && NORM) s2 = fma(val, val, s2);
+        }
+        qm[q] = qc[q];
+        qc[q] = qn[q];
+        C[q] = nC[q];
+        F[q] = nF[q];
+        E[q] = nE[q];
+      }
+#pragma unroll
+      for (int s = 0; s < FRB + 2; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) v[s][c] = vn[s][c];
+    }
+  }
+  if (MODE == 0 && NORM && partials != nullptr) block_partial_nt<CBX*(CBY / FRB)>(s2, partials);
+}
+
 template <typename C>
 static Wts<C> wts(const W27& a) {
   return Wts<C>{{(C)a.w[0], (C)a.w[1], (C)a.w[2], (C)a.w[3]}};
@@ -337,24 +434,24 @@ cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const
                              int zero_interior, double* partials, const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
   if (zero_interior)
-    k_c27<0, true, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
+    k_c27_f64<0, true, double, true><<<c27_grid(d), dim3(CBX, CBY / FRB), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
   else
-    k_c27<0, false, double, double><<<c27_grid(d), dim3(CBX, CBY), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
+    k_c27_f64<0, false, double, true><<<c27_grid(d), dim3(CBX, CBY / FRB), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void* u, const void* b, int dt_r,
                                 void* r, double* partials, const DevState* st, cudaStream_t s, int zero_interior) {
   if (d.g != 1) return cudaErrorInvalidValue;
-  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  const dim3 g = c27_grid(d), blk(CBX, CBY), b64(CBX, CBY / FRB);
   if (zero_interior && dt == DT_F64 && dt_r == DT_F32)
-    k_c27<0, true, double, float><<<g, blk, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+    k_c27_f64<0, true, float, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
   else if (zero_interior)
     return cudaErrorInvalidValue;
   else if (dt == DT_F64 && dt_r == DT_F64)
-    k_c27<0, false, double, double><<<g, blk, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
+    k_c27_f64<0, false, double, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
   else if (dt == DT_F64 && dt_r == DT_F32)
-    k_c27<0, false, double, float><<<g, blk, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
+    k_c27_f64<0, false, float, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
   else if (dt == DT_F32 && dt_r == DT_F32 && partials == nullptr)
     k_c27<0, false, float, float, false><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, nullptr, st);
   else if (dt == DT_F32 && dt_r == DT_F32)
@@ -386,9 +483,9 @@ cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const dou
 cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt, const void* r, void* u,
                                const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
-  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  const dim3 g = c27_grid(d), blk(CBX, CBY), b64(CBX, CBY / FRB);
   if (dt == DT_F64)
-    k_c27<1, false, double, double><<<g, blk, 0, s>>>(d, wts<double>(M), omega, (const double*)r, nullptr, (double*)u, nullptr, st);
+    k_c27_f64<1, false, double, false><<<g, b64, 0, s>>>(d, wts<double>(M), omega, (const double*)r, nullptr, (double*)u, nullptr, st);
   else if (dt == DT_F32)
     k_c27<1, false, float, float><<<g, blk, 0, s>>>(d, wts<float>(M), (float)omega, (const float*)r, nullptr, (float*)u, nullptr, st);
   else
