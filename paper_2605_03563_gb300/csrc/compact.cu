@@ -157,6 +157,15 @@ __device__ __forceinline__ C plane_p_plus(const C nw[4], const Plane<C>& p, C ba
   return fma(nw[0], p.c, fma(nw[1], p.f, fma(nw[2], p.e, base))) + (qm + qp);
 }
 
+// FP64 value stored as TR; FP32 stores round on the integer pipe (ties to
+// even, the same value as the conversion instruction) instead of taking an
+// FP64-pipe conversion.
+template <typename TR>
+__device__ __forceinline__ TR store_as(double v) {
+  if constexpr (std::is_same<TR, float>::value) return f64_to_f32_pow2(v, 0);
+  else return (TR)v;
+}
+
 // per-block {sum, 0} into partials[2 b], partials[2 b + 1] (blocks of CBX x CBY threads)
 __device__ __forceinline__ void block_partial(double v, double* __restrict__ partials) {
   __shared__ double sh[CBX * CBY / 32];
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(CBX* CBY)
       const long long q = d.at(i, j, k);
       const double bq = b[q];
       const double rv = plane_p_plus(nw.w, pc, bq, qm, qn);
-      r[q] = (TR)rv;
+      r[q] = store_as<TR>(rv);
       s2 = fma(rv, rv, s2);
       double r0 = bq;
       if (side || k == 1 || k == d.nk()) {
@@ -398,7 +407,7 @@ __global__ void __launch_bounds__(CBX*(CBY / FRB))
           const long long o = base + roff[q + 1];
           const double bv = MODE == 0 ? b[o] : (double)dst[o];
           const double val = fma(nw.w[0], C[q], fma(nw.w[1], F[q], fma(nw.w[2], E[q], bv))) + (qm[q] + qn[q]);
-          dst[o] = (TR)val;
+          dst[o] = store_as<TR>(val);
           if (MODE == 0 && NORM) s2 = fma(val, val, s2);
         }
         qm[q] = qc[q];
@@ -840,67 +849,115 @@ __device__ __forceinline__ double f_ext(const Dims& du, const double* __restrict
 //   b = W0 C(z) + W1 (F(z) + C(z-1) + C(z+1)) + W2 (E(z) + F(z-1) + F(z+1))
 //     + W3 (sum of the six +-2 offsets)
 // with the source scale folded into the weights on the host (no division on
-// the device).
+// the device).  As in k_c27_f64 a thread owns FRB consecutive rows of one
+// column: per plane it loads the (FRB + 2) x 3 neighbourhood and forms the
+// pair sums f(x-1) + f(x+1) once per row; the +-2 offsets in y come from those
+// rows where they lie inside them, in z from the centres of planes k - 2 and
+// k + 2 kept or prefetched in registers, and past the node array from the
+// cubic extrapolation (f_ext).
 template <int ORDER>
-__global__ void __launch_bounds__(CBX* CBY)
+__global__ void __launch_bounds__(CBX*(CBY / FRB))
     k_c27_rhs(Dims d, Dims du, const double* __restrict__ rho, Wts<double> W, double* __restrict__ b) {
   const int i = blockIdx.x * CBX + threadIdx.x + 1;
-  const int j = blockIdx.y * CBY + threadIdx.y + 1;
+  const int j0 = blockIdx.y * CBY + threadIdx.y * FRB + 1;   // rows j0 .. j0 + FRB - 1
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
-  if (i > d.ni() || j > d.nj()) return;
+  if (i > d.ni() || j0 > d.nj()) return;
+  const long long sy = du.sy(), sz = du.sz();
   if (ORDER == 2) {
-    for (int k = k0; k < k1; k++) b[d.at(i, j, k)] = W.w[0] * rho[du.at(i, j, k)];
+    for (int k = k0; k < k1; k++)
+#pragma unroll
+      for (int q = 0; q < FRB; q++)
+        if (j0 + q <= d.nj()) b[d.at(i, j0 + q, k)] = W.w[0] * rho[du.at(i, j0 + q, k)];
     return;
   }
-  const long long sy = du.sy();
-  // planes k - 1 .. k + 2 of interior nodes stay inside the node array 0..n
-  // up to k + 2 = n; the +-2 offsets past it are extrapolated (f_ext)
-  auto load9 = [&](int k) -> Raw9<double> {
-    const long long p = du.at(i, j, k);
-    Raw9<double> v;
-    v.c = rho[p];
-    v.xm = rho[p - 1];
-    v.xp = rho[p + 1];
-    v.ym = rho[p - sy];
-    v.yp = rho[p + sy];
-    v.mm = rho[p - sy - 1];
-    v.pm = rho[p - sy + 1];
-    v.mp = rho[p + sy - 1];
-    v.pp = rho[p + sy + 1];
-    return v;
-  };
-  const bool side = i == 1 || i == d.ni() || j == 1 || j == d.nj();   // x or y offsets +-2 leave the array
-  Plane<double> pm = plane_of(load9(k0 - 1)), pc = plane_of(load9(k0));
-  Raw9<double> nx = load9(k0 + 1);
-  double cm2 = ORDER == 6 ? f_ext(du, rho, i, j, k0 - 2) : 0.0;   // centre of plane k - 2
-  for (int k = k0; k < k1; k++) {
-    Raw9<double> nn = nx;
-    if (k + 2 <= d.nk() + 1) nn = load9(k + 2);   // issued before the arithmetic of plane k
-    const Plane<double> pn = plane_of(nx);
-    const double fa = pc.f + (pm.c + pn.c);
-    double v;
-    if (ORDER == 4) {
-      v = fma(W.w[0], pc.c, W.w[1] * fa);
-    } else {
-      const double ed = pc.e + (pm.f + pn.f);
-      const double cp2 = k + 2 <= d.nk() + 1 ? nn.c : f_ext(du, rho, i, j, k + 2);
-      double xs, ys;
-      if (side) {
-        xs = f_ext(du, rho, i - 2, j, k) + f_ext(du, rho, i + 2, j, k);
-        ys = f_ext(du, rho, i, j - 2, k) + f_ext(du, rho, i, j + 2, k);
-      } else {
-        const long long p = du.at(i, j, k);
-        xs = rho[p - 2] + rho[p + 2];
-        ys = rho[p - 2 * sy] + rho[p + 2 * sy];
-      }
-      const double ax = (xs + ys) + (cm2 + cp2);
-      v = fma(W.w[0], pc.c, fma(W.w[1], fa, fma(W.w[2], ed, W.w[3] * ax)));
-      cm2 = pm.c;
+  const int ny = du.ny, nz = du.nz;   // last node index along y and z
+  // rows j0 - 1 + s of the node array, clamped to it: a clamped row only
+  // feeds rows that are not written
+  long long roff[FRB + 2];
+#pragma unroll
+  for (int s = 0; s < FRB + 2; s++) roff[s] = (long long)min(j0 - 1 + s, ny) * sy + i;
+  auto load = [&](int k, double (&v)[FRB + 2][3]) {
+    const double* p = rho + (long long)k * sz;
+#pragma unroll
+    for (int s = 0; s < FRB + 2; s++) {
+      v[s][0] = p[roff[s] - 1];
+      v[s][1] = p[roff[s]];
+      v[s][2] = p[roff[s] + 1];
     }
-    b[d.at(i, j, k)] = v;
-    pm = pc;
-    pc = pn;
-    nx = nn;
+  };
+  auto sums = [&](const double (&v)[FRB + 2][3], double (&C)[FRB], double (&F)[FRB], double (&E)[FRB]) {
+    double a[FRB + 2];
+#pragma unroll
+    for (int s = 0; s < FRB + 2; s++) a[s] = v[s][0] + v[s][2];
+#pragma unroll
+    for (int q = 0; q < FRB; q++) {
+      C[q] = v[q + 1][1];
+      F[q] = a[q + 1] + (v[q][1] + v[q + 2][1]);
+      E[q] = a[q] + a[q + 2];
+    }
+  };
+  const bool side_x = i == 1 || i == d.ni();   // x offsets +-2 leave the array
+  double v[FRB + 2][3], vn[FRB + 2][3];
+  double Cm[FRB], Fm[FRB], Cc[FRB], Fc[FRB], Ec[FRB], cm2[FRB];
+  {
+    double Em[FRB];
+    load(k0 - 1, v);
+    sums(v, Cm, Fm, Em);
+  }
+  load(k0, v);
+  sums(v, Cc, Fc, Ec);
+  double Sc[FRB + 2];   // centres of the loaded rows of plane k (for the y offsets +-2)
+#pragma unroll
+  for (int s = 0; s < FRB + 2; s++) Sc[s] = v[s][1];
+  if (ORDER == 6)
+#pragma unroll
+    for (int q = 0; q < FRB; q++) cm2[q] = f_ext(du, rho, i, min(j0 + q, d.nj()), k0 - 2);   // centres of plane k0 - 2
+  load(k0 + 1, v);
+  for (int k = k0; k < k1; k++) {
+    if (k + 2 <= nz) load(k + 2, vn);   // issued before the arithmetic of plane k
+    double Cn[FRB], Fn[FRB], En[FRB];
+    sums(v, Cn, Fn, En);
+    const double* p = rho + (long long)k * sz;
+#pragma unroll
+    for (int q = 0; q < FRB; q++) {
+      // rows past nj are not written; their offsets use row nj so that f_ext
+      // only ever extrapolates along one axis
+      const int j = min(j0 + q, d.nj());
+      const double fa = Fc[q] + (Cm[q] + Cn[q]);
+      double val;
+      if (ORDER == 4) {
+        val = fma(W.w[0], Cc[q], W.w[1] * fa);
+      } else {
+        const double ed = Ec[q] + (Fm[q] + Fn[q]);
+        double xs;
+        if (side_x) xs = f_ext(du, rho, i - 2, j, k) + f_ext(du, rho, i + 2, j, k);
+        else xs = p[roff[q + 1] - 2] + p[roff[q + 1] + 2];
+        // y - 2 is loaded row q - 1 for q >= 1, y + 2 loaded row q + 3 for q + 3 <= FRB + 1
+        double ym2, yp2;
+        if (q >= 1) ym2 = Sc[q - 1];
+        else ym2 = j - 2 >= 0 ? p[(long long)(j - 2) * sy + i] : f_ext(du, rho, i, j - 2, k);
+        if (j + 2 > ny) yp2 = f_ext(du, rho, i, j + 2, k);
+        else if (q + 3 <= FRB + 1) yp2 = Sc[q + 3];
+        else yp2 = p[(long long)(j + 2) * sy + i];
+        const double ys = ym2 + yp2;
+        const double cp2 = k + 2 <= nz ? vn[q + 1][1] : f_ext(du, rho, i, j, k + 2);
+        const double ax = (xs + ys) + (cm2[q] + cp2);
+        val = fma(W.w[0], Cc[q], fma(W.w[1], fa, fma(W.w[2], ed, W.w[3] * ax)));
+        cm2[q] = Cm[q];
+      }
+      if (j0 + q <= d.nj()) b[d.at(i, j, k)] = val;
+      Cm[q] = Cc[q];
+      Fm[q] = Fc[q];
+      Cc[q] = Cn[q];
+      Fc[q] = Fn[q];
+      Ec[q] = En[q];
+    }
+#pragma unroll
+    for (int s = 0; s < FRB + 2; s++) {
+      Sc[s] = v[s][1];
+#pragma unroll
+      for (int c = 0; c < 3; c++) v[s][c] = vn[s][c];
+    }
   }
 }
 
@@ -908,7 +965,7 @@ cudaError_t launch_c27_rhs(const Dims& d, const Dims& du, int order, const doubl
                            double* b, cudaStream_t s) {
   if (d.g != 1 || du.g != 1) return cudaErrorInvalidValue;
   if (order == 6 && (d.nx < 4 || d.ny < 4 || d.nz < 4)) return cudaErrorInvalidValue;
-  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  const dim3 g = c27_grid(d), blk(CBX, CBY / FRB);
   // R_h weights per class (centre, faces, edges, +-2 offsets) times the source scale
   if (order == 2) {
     k_c27_rhs<2><<<g, blk, 0, s>>>(d, du, rho, Wts<double>{{fscale, 0.0, 0.0, 0.0}}, b);
