@@ -119,3 +119,44 @@ def test_compact_fp32_refinement_matches_fp64(pkg, order):
                        max_iter=60, inner_cycles=2, compact_order=order)
     assert info.converged and info.rel_residual <= 1e-10
     assert rel_err(host(phi_t), phi_o) <= 1e-7
+
+
+def test_compact_fp32_refinement_odd_smoothing_count(pkg):
+    """V(1,2) inner cycles: the out-of-place FP32 smoothing steps end in the
+    second array on every level and are copied back; the refinement still
+    agrees with the FP64 oracle's V(1,2) solution to 1e-7."""
+    n = 40
+    rho = W.gaussian_blobs(n, seed=9)
+    g = cart_grid(n)
+    phi_o = np.zeros(W.cart_shape(n, 2))
+    info_o = OS.solve_cartesian(rho, phi_o, g, "mg", 1e-10, max_iter=60, bc="multipole", lmax=4, nu1=1,
+                                nu2=2, compact_order=6)
+    assert info_o.converged
+    phi_t = dev(np.zeros(W.cart_shape(n, 2)))
+    with pkg.CartesianSolver(n, bc="multipole", lmax=4) as s:
+        info = s.solve(dev(rho), phi_t, tol=1e-10, method="mg", prec="mixed_fp32", nu1=1, nu2=2,
+                       max_iter=60, inner_cycles=2, compact_order=6)
+    assert info.converged and info.rel_residual <= 1e-10
+    assert rel_err(host(phi_t), phi_o) <= 1e-7
+
+
+def test_compact_fp32_refinement_after_other_solves_on_the_handle(pkg):
+    """The second arrays of the FP32 levels are shared with the 7-point fused
+    sweeps; a compact refinement after a 7-point mixed solve (and after a
+    compact one) on the same handle gives bit-identical results to a fresh
+    handle's."""
+    n = 48
+    rho = dev(W.gaussian_blobs(n, seed=10))
+    kw = dict(tol=1e-10, method="mg", prec="mixed_fp32", nu1=2, nu2=2, max_iter=60, inner_cycles=2,
+              compact_order=6)
+    with pkg.CartesianSolver(n, bc="multipole", lmax=4) as fresh:
+        ref = dev(np.zeros(W.cart_shape(n, 2)))
+        fresh.solve(rho, ref, **kw)
+    with pkg.CartesianSolver(n, bc="multipole", lmax=4) as s:
+        other = dev(np.zeros(W.cart_shape(n, 2)))
+        s.solve(rho, other, tol=1e-10, method="mg", prec="mixed_fp32", max_iter=60, inner_cycles=2)
+        for _ in range(2):
+            got = dev(np.zeros(W.cart_shape(n, 2)))
+            info = s.solve(rho, got, **kw)
+            assert info.converged
+            assert torch.equal(got, ref)
