@@ -229,82 +229,6 @@ __global__ void __launch_bounds__(CBX* CBY)
   if (MODE == 0 && NORM && partials != nullptr) block_partial(s2, partials);
 }
 
-// per-block {v, 0} into p[2 b], p[2 b + 1] and {w, 0} into q[2 b], q[2 b + 1]
-__device__ __forceinline__ void block_partial2(double v, double w, double* __restrict__ p, double* __restrict__ q) {
-  __shared__ double sh[2][CBX * CBY / 32];
-  const int tid = threadIdx.x + CBX * threadIdx.y;
-  v = warp_sum(v);
-  w = warp_sum(w);
-  if ((tid & 31) == 0) {
-    sh[0][tid >> 5] = v;
-    sh[1][tid >> 5] = w;
-  }
-  __syncthreads();
-  if (tid < 32) {
-    double a = tid < CBX * CBY / 32 ? sh[0][tid] : 0.0;
-    double c = tid < CBX * CBY / 32 ? sh[1][tid] : 0.0;
-    a = warp_sum(a);
-    c = warp_sum(c);
-    if (tid == 0) {
-      const int bid = block_linear_id();
-      p[2 * bid] = a;
-      p[2 * bid + 1] = 0.0;
-      q[2 * bid] = c;
-      q[2 * bid + 1] = 0.0;
-    }
-  }
-}
-
-// Initial residual pass of a compact solve (FP64 arithmetic, the per-plane
-// split of the stencil): r = b - A u stored as TR with per-block partials of
-// r^2, and in the same pass the
-// reference residual b - A u0 of the boundary data alone (u0: u with its
-// interior zeroed), whose partials go to partials + 2 nblocks.  A u0 vanishes
-// unless a node has a boundary node among its 26 neighbours, so only the
-// first and last interior layers of each axis evaluate it; elsewhere the
-// reference residual is b.  Both sums are the ones two separate passes
-// (interior zeroed, then full) of k_c27 would form, in the same order.
-template <typename TR>
-__global__ void __launch_bounds__(CBX* CBY)
-    k_c27_init(Dims d, Wts<double> W, const double* __restrict__ u, const double* __restrict__ b,
-               TR* __restrict__ r, double* __restrict__ partials, int nblocks) {
-  const int i = blockIdx.x * CBX + threadIdx.x + 1;
-  const int j = blockIdx.y * CBY + threadIdx.y + 1;
-  const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
-  double s2 = 0.0, s0 = 0.0;
-  if (i <= d.ni() && j <= d.nj()) {
-    const bool side = i == 1 || i == d.ni() || j == 1 || j == d.nj();
-    Wts<double> nw;
-    for (int a = 0; a < 4; a++) nw.w[a] = -W.w[a];
-    Plane<double> pc = plane_of(plane_load<false>(d, u, i, j, k0));
-    double qm = plane_q(nw.w, plane_of(plane_load<false>(d, u, i, j, k0 - 1)));
-    double qc = plane_q(nw.w, pc);
-    Raw9<double> nx = plane_load<false>(d, u, i, j, k0 + 1);
-    for (int k = k0; k < k1; k++) {
-      Raw9<double> nn = nx;
-      if (k + 2 <= k1) nn = plane_load<false>(d, u, i, j, k + 2);
-      const Plane<double> pn = plane_of(nx);
-      const double qn = plane_q(nw.w, pn);
-      const long long q = d.at(i, j, k);
-      const double bq = b[q];
-      const double rv = plane_p_plus(nw.w, pc, bq, qm, qn);
-      r[q] = store_as<TR>(rv);
-      s2 = fma(rv, rv, s2);
-      double r0 = bq;
-      if (side || k == 1 || k == d.nk()) {
-        r0 = plane_p_plus(nw.w, plane_of(plane_load<true>(d, u, i, j, k)), bq,
-                          plane_q(nw.w, plane_of(plane_load<true>(d, u, i, j, k - 1))),
-                          plane_q(nw.w, plane_of(plane_load<true>(d, u, i, j, k + 1))));
-      }
-      s0 = fma(r0, r0, s0);
-      qm = qc;
-      qc = qn;
-      pc = pn;
-      nx = nn;
-    }
-  }
-  block_partial2(s2, s0, partials, partials + 2 * nblocks);
-}
 
 // per-block {sum, 0} into partials[2 b], partials[2 b + 1] for blocks of NT threads
 template <int NT>
@@ -325,6 +249,34 @@ __device__ __forceinline__ void block_partial_nt(double v, double* __restrict__ 
   }
 }
 
+// per-block {v, 0} into p[2 b], p[2 b + 1] and {w, 0} into q[2 b], q[2 b + 1], blocks of NT threads
+template <int NT>
+__device__ __forceinline__ void block_partial2_nt(double v, double w, double* __restrict__ p,
+                                                  double* __restrict__ q) {
+  __shared__ double sh[2][NT / 32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  v = warp_sum(v);
+  w = warp_sum(w);
+  if ((tid & 31) == 0) {
+    sh[0][tid >> 5] = v;
+    sh[1][tid >> 5] = w;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double a = tid < NT / 32 ? sh[0][tid] : 0.0;
+    double c = tid < NT / 32 ? sh[1][tid] : 0.0;
+    a = warp_sum(a);
+    c = warp_sum(c);
+    if (tid == 0) {
+      const int bid = block_linear_id();
+      p[2 * bid] = a;
+      p[2 * bid + 1] = 0.0;
+      q[2 * bid] = c;
+      q[2 * bid + 1] = 0.0;
+    }
+  }
+}
+
 // FP64 passes (GB300's FP64 pipe bounds them, so they minimise FP64
 // instructions): MODE 0: r = b - A u stored as TR (ZI: u's interior read as 0),
 // per-block partials of r^2 if given; MODE 1: u -= omega M r.  A thread owns
@@ -335,16 +287,23 @@ __device__ __forceinline__ void block_partial_nt(double v, double* __restrict__ 
 // stencil: 12.5 FP64 operations per node.  The loads of plane k + 2 are issued
 // before the arithmetic of plane k.  Blocks of 32 x (CBY / FRB) threads cover
 // the 32 x 8 tiles of c27_grid, so the partials count is c27_blocks(d).
+// INIT (initial residual of a compact solve): also the reference residual
+// b - A u0 of the boundary data alone (u0: u with its interior zeroed), whose
+// partials go to partials + 2 nblocks; A u0 vanishes unless a node has a
+// boundary node among its 26 neighbours, so only the first and last interior
+// layers of each axis evaluate it (per node, with zero-interior loads), and
+// elsewhere the reference residual is b.
 static constexpr int FRB = 4;
-template <int MODE, bool ZI, typename TR, bool NORM>
+template <int MODE, bool ZI, typename TR, bool NORM, bool INIT = false>
 __global__ void __launch_bounds__(CBX*(CBY / FRB))
     k_c27_f64(Dims d, Wts<double> W, double om, const double* __restrict__ src, const double* __restrict__ b,
-              TR* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st) {
+              TR* __restrict__ dst, double* __restrict__ partials, const DevState* __restrict__ st,
+              int nblocks = 0) {
   if (st != nullptr && st->done) return;   // uniform
   const int i = blockIdx.x * CBX + threadIdx.x + 1;
   const int j0 = blockIdx.y * CBY + threadIdx.y * FRB + 1;   // rows j0 .. j0 + FRB - 1
   const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
-  double s2 = 0.0;
+  double s2 = 0.0, s0 = 0.0;
   if (i <= d.ni() && j0 <= d.nj()) {
     Wts<double> nw;
 #pragma unroll
@@ -409,6 +368,17 @@ __global__ void __launch_bounds__(CBX*(CBY / FRB))
           const double val = fma(nw.w[0], C[q], fma(nw.w[1], F[q], fma(nw.w[2], E[q], bv))) + (qm[q] + qn[q]);
           dst[o] = store_as<TR>(val);
           if (MODE == 0 && NORM) s2 = fma(val, val, s2);
+          if constexpr (INIT) {
+            // reference residual b - A u0 (u0: u with its interior zeroed); A u0
+            // vanishes unless a boundary node is among the 26 neighbours
+            const int j = j0 + q;
+            double r0 = bv;
+            if (i == 1 || i == d.ni() || j == 1 || j == d.nj() || k == 1 || k == d.nk())
+              r0 = plane_p_plus(nw.w, plane_of(plane_load<true>(d, src, i, j, k)), bv,
+                                plane_q(nw.w, plane_of(plane_load<true>(d, src, i, j, k - 1))),
+                                plane_q(nw.w, plane_of(plane_load<true>(d, src, i, j, k + 1))));
+            s0 = fma(r0, r0, s0);
+          }
         }
         qm[q] = qc[q];
         qc[q] = qn[q];
@@ -422,7 +392,8 @@ __global__ void __launch_bounds__(CBX*(CBY / FRB))
         for (int c = 0; c < 3; c++) v[s][c] = vn[s][c];
     }
   }
-  if (MODE == 0 && NORM && partials != nullptr) block_partial_nt<CBX*(CBY / FRB)>(s2, partials);
+  if constexpr (INIT) block_partial2_nt<CBX*(CBY / FRB)>(s2, s0, partials, partials + 2 * nblocks);
+  else if (MODE == 0 && NORM && partials != nullptr) block_partial_nt<CBX*(CBY / FRB)>(s2, partials);
 }
 
 template <typename C>
@@ -473,12 +444,12 @@ cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void*
 cudaError_t launch_c27_init(const Dims& d, const W27& A, const double* u, const double* b, int dt_r, void* r,
                             double* partials, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
-  const dim3 g = c27_grid(d), blk(CBX, CBY);
+  const dim3 g = c27_grid(d), b64(CBX, CBY / FRB);
   const int nb = c27_blocks(d);
   if (dt_r == DT_F64)
-    k_c27_init<double><<<g, blk, 0, s>>>(d, wts<double>(A), u, b, (double*)r, partials, nb);
+    k_c27_f64<0, false, double, true, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, u, b, (double*)r, partials, nullptr, nb);
   else if (dt_r == DT_F32)
-    k_c27_init<float><<<g, blk, 0, s>>>(d, wts<double>(A), u, b, (float*)r, partials, nb);
+    k_c27_f64<0, false, float, true, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, u, b, (float*)r, partials, nullptr, nb);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
