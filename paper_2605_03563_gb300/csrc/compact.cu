@@ -184,50 +184,6 @@ __device__ __forceinline__ void block_partial(double v, double* __restrict__ par
   }
 }
 
-// MODE 0: r = b - A u (ZI: u's interior read as 0; r stored as TR), partials if
-// given; MODE 1: u -= omega M r.  Arithmetic in FP32 (FP32 storage; the FP64
-// passes run k_c27_f64).
-// NORM: the residual pass also forms per-block partials of r^2 (in FP64; FP32
-// inner passes skip it, so they touch no FP64 instruction).
-// The loads of plane k + 2 are issued before the arithmetic of plane k, so two
-// planes of loads are in flight per thread.
-template <int MODE, bool ZI, typename T, typename TR, bool NORM = true>
-__global__ void __launch_bounds__(CBX* CBY)
-    k_c27(Dims d, Wts<typename St<T>::C> W, typename St<T>::C om, const T* __restrict__ src,
-          const T* __restrict__ b, TR* __restrict__ dst, double* __restrict__ partials,
-          const DevState* __restrict__ st) {
-  using C = typename St<T>::C;
-  if (st != nullptr && st->done) return;   // uniform
-  const int i = blockIdx.x * CBX + threadIdx.x + 1;
-  const int j = blockIdx.y * CBY + threadIdx.y + 1;
-  const int k0 = blockIdx.z * CZC + 1, k1 = min(k0 + CZC, d.nk() + 1);
-  double s2 = 0.0;
-  if (i <= d.ni() && j <= d.nj()) {
-    {
-      Plane<C> pm = plane_of(plane_load<ZI>(d, src, i, j, k0 - 1));
-      Plane<C> pc = plane_of(plane_load<ZI>(d, src, i, j, k0));
-      Raw9<C> nx = plane_load<ZI>(d, src, i, j, k0 + 1);
-      for (int k = k0; k < k1; k++) {
-        Raw9<C> nn = nx;
-        if (k + 2 <= k1) nn = plane_load<ZI>(d, src, i, j, k + 2);   // plane k1 <= nk + 1 exists
-        const Plane<C> pn = plane_of(nx);
-        const C a = apply_planes<C>(W.w, pm, pc, pn);
-        const long long q = d.at(i, j, k);
-        if (MODE == 0) {
-          const C r = (C)b[q] - a;
-          dst[q] = (TR)r;
-          if (NORM) s2 = fma((double)r, (double)r, s2);
-        } else {
-          dst[q] = (TR)fma(-om, a, (C)dst[q]);
-        }
-        pm = pc;
-        pc = pn;
-        nx = nn;
-      }
-    }
-  }
-  if (MODE == 0 && NORM && partials != nullptr) block_partial(s2, partials);
-}
 
 
 // per-block {sum, 0} into partials[2 b], partials[2 b + 1] for blocks of NT threads
@@ -411,31 +367,18 @@ int c27_blocks(const Dims& d) {
 }
 
 cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const double* b, double* r,
-                             int zero_interior, double* partials, const DevState* st, cudaStream_t s) {
-  if (d.g != 1) return cudaErrorInvalidValue;
-  if (zero_interior)
-    k_c27_f64<0, true, double, true><<<c27_grid(d), dim3(CBX, CBY / FRB), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
-  else
-    k_c27_f64<0, false, double, true><<<c27_grid(d), dim3(CBX, CBY / FRB), 0, s>>>(d, wts<double>(A), 0.0, u, b, r, partials, st);
-  return cudaGetLastError();
+                             double* partials, const DevState* st, cudaStream_t s) {
+  return launch_c27_resid_dt(d, A, u, b, DT_F64, r, partials, st, s);
 }
 
-cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void* u, const void* b, int dt_r,
-                                void* r, double* partials, const DevState* st, cudaStream_t s, int zero_interior) {
+cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, const double* u, const double* b, int dt_r, void* r,
+                                double* partials, const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
-  const dim3 g = c27_grid(d), blk(CBX, CBY), b64(CBX, CBY / FRB);
-  if (zero_interior && dt == DT_F64 && dt_r == DT_F32)
-    k_c27_f64<0, true, float, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
-  else if (zero_interior)
-    return cudaErrorInvalidValue;
-  else if (dt == DT_F64 && dt_r == DT_F64)
-    k_c27_f64<0, false, double, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (double*)r, partials, st);
-  else if (dt == DT_F64 && dt_r == DT_F32)
-    k_c27_f64<0, false, float, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, (const double*)u, (const double*)b, (float*)r, partials, st);
-  else if (dt == DT_F32 && dt_r == DT_F32 && partials == nullptr)
-    k_c27<0, false, float, float, false><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, nullptr, st);
-  else if (dt == DT_F32 && dt_r == DT_F32)
-    k_c27<0, false, float, float><<<g, blk, 0, s>>>(d, wts<float>(A), 0.0f, (const float*)u, (const float*)b, (float*)r, partials, st);
+  const dim3 g = c27_grid(d), b64(CBX, CBY / FRB);
+  if (dt_r == DT_F64)
+    k_c27_f64<0, false, double, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, u, b, (double*)r, partials, st);
+  else if (dt_r == DT_F32)
+    k_c27_f64<0, false, float, true><<<g, b64, 0, s>>>(d, wts<double>(A), 0.0, u, b, (float*)r, partials, st);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -457,40 +400,27 @@ cudaError_t launch_c27_init(const Dims& d, const W27& A, const double* u, const 
 
 cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const double* r, double* u,
                             const DevState* st, cudaStream_t s) {
-  return launch_c27_spai_dt(d, M, omega, DT_F64, r, u, st, s);
-}
-
-cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt, const void* r, void* u,
-                               const DevState* st, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
-  const dim3 g = c27_grid(d), blk(CBX, CBY), b64(CBX, CBY / FRB);
-  if (dt == DT_F64)
-    k_c27_f64<1, false, double, false><<<g, b64, 0, s>>>(d, wts<double>(M), omega, (const double*)r, nullptr, (double*)u, nullptr, st);
-  else if (dt == DT_F32)
-    k_c27<1, false, float, float><<<g, blk, 0, s>>>(d, wts<float>(M), (float)omega, (const float*)r, nullptr, (float*)u, nullptr, st);
-  else
-    return cudaErrorInvalidValue;
+  k_c27_f64<1, false, double, false><<<c27_grid(d), dim3(CBX, CBY / FRB), 0, s>>>(d, wts<double>(M), omega, r, nullptr,
+                                                                                 u, nullptr, st);
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ TMA-staged FP32 passes
-// The FP32 passes of the inner cycles stream the 27-point source through a
-// ring of TMA-staged planes (box 40 x 10 starting at x = 32 bx - 4: a 32 x 8
-// tile of nodes 32 bx + 1 .. 32 bx + 32 with one-node halos, widened in x to
-// whole 16-byte granules), so each value is loaded into shared
-// memory once instead of being fetched nine times per plane through L1; the
-// second array (b, or the potential updated in place) is read once per node
-// from global memory.  Same arithmetic, in the same order, as k_c27.
+// ------------------------------------------------------------------ TMA-staged FP32 residual
+// The FP32 residual r = b - A u before a restriction streams u through a ring
+// of TMA-staged planes (box 40 x 10 starting at x = 32 bx - 4: a 32 x 8 tile of
+// nodes 32 bx + 1 .. 32 bx + 32 with one-node halos, widened in x to whole
+// 16-byte granules), so each value is loaded into shared memory once instead
+// of being fetched nine times per plane through L1; b is read once per node
+// from global memory.
 static constexpr int TTX = 32, TTY = 8, TXH = 4;
 static constexpr int TWP = TTX + 2 * TXH, THP = TTY + 2, TNS = 4;
 static constexpr int TPB = TWP * THP * 4;   // bytes per staged FP32 plane
 static constexpr int TPBA = (TPB + 127) / 128 * 128;
 
-template <int MODE>
 __global__ void __launch_bounds__(TTX* TTY)
-    k_c27_tma(const __grid_constant__ CUtensorMap mS, Dims d, Wts<float> W, float om,
-              const float* __restrict__ b, float* __restrict__ dst, int zc, const DevState* __restrict__ st,
-              int* __restrict__ fault) {
+    k_c27_tma(const __grid_constant__ CUtensorMap mS, Dims d, Wts<float> W, const float* __restrict__ b,
+              float* __restrict__ dst, int zc, const DevState* __restrict__ st, int* __restrict__ fault) {
   __shared__ __align__(128) unsigned char smem[TNS * TPBA];
   __shared__ __align__(8) unsigned long long bar[TNS];
   if (st != nullptr && st->done) return;   // uniform
@@ -547,8 +477,7 @@ __global__ void __launch_bounds__(TTX* TTY)
     if (in) {
       const float a = apply_planes<float>(W.w, pm, pc, pn);
       const long long q = d.at(i, j, k);
-      if (MODE == 0) dst[q] = b[q] - a;
-      else dst[q] = fmaf(-om, a, dst[q]);
+      dst[q] = b[q] - a;
     }
     pm = pc;
     pc = pn;
@@ -563,8 +492,8 @@ __global__ void __launch_bounds__(TTX* TTY)
 
 static int g_sms = 0;
 
-cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, const float* src, const float* b,
-                           float* dst, const DevState* st, int* fault, cudaStream_t s) {
+cudaError_t launch_c27_tma(const Dims& d, const W27& W, const float* src, const float* b, float* dst,
+                           const DevState* st, int* fault, cudaStream_t s) {
   if (d.g != 1) return cudaErrorInvalidValue;
   CUtensorMap map;
   if (!encode_level_map(&map, DT_F32, src, d, TWP, THP)) return cudaErrorInvalidValue;
@@ -579,10 +508,7 @@ cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, 
   const int want = std::max(1, 16 * g_sms / (gx * gy));
   const int zc = std::max(8, (nk + want - 1) / want);
   const dim3 grid(gx, gy, (nk + zc - 1) / zc), blk(TTX, TTY);
-  if (mode == 0)
-    k_c27_tma<0><<<grid, blk, 0, s>>>(map, d, wts<float>(W), 0.0f, b, dst, zc, st, fault);
-  else
-    k_c27_tma<1><<<grid, blk, 0, s>>>(map, d, wts<float>(W), (float)omega, nullptr, dst, zc, st, fault);
+  k_c27_tma<<<grid, blk, 0, s>>>(map, d, wts<float>(W), b, dst, zc, st, fault);
   return cudaGetLastError();
 }
 
@@ -606,10 +532,10 @@ cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, 
 // strip, so warps never exchange residuals.  u (box 40 x (GW GR + 4)) and b
 // (box 40 x (GW GR + 2)), both from x = 4 floor((x0 - 2) / 4), arrive by TMA,
 // one stage per plane; one block barrier per plane returns a stage to the
-// copy engine.  The sums and the stencil arithmetic are those of the residual
-// pass followed by the SPAI pass of k_c27_tma, in the same association, so
-// the results are bit-identical to that route; traffic is 12 bytes per node
-// instead of 24.
+// copy engine.  The sums (plane_of's association) and the stencil arithmetic
+// (apply_planes) are those of a residual pass (k_c27_tma) followed by a
+// separate SPAI pass u -= omega M r, so the results are bit-identical to that
+// two-pass route; traffic is 12 bytes per node instead of 24.
 static constexpr int GW = 4, GR = 4;                  // warps per block, output rows per warp
 static constexpr int GTX = 30, GTY = GW * GR;         // output tile
 static constexpr int GRR = GR + 2, GUR = GR + 4;      // residual rows and u rows per warp

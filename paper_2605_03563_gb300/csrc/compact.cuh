@@ -19,10 +19,14 @@ W27 compact_lhs(int order, double h);
 // isotropic 27-point A: the coarse stencil is again isotropic with radius one.
 W27 galerkin27(const W27& fine);
 
-// r = b - A u on the interior (zero_interior: u's interior read as 0, for the
-// reference norm); with partials, per-block {sum r^2, 0} (c27_blocks(d) blocks).
+// r = b - A u on the interior (FP64 arithmetic); with partials, per-block
+// {sum r^2, 0} (c27_blocks(d) blocks).
 cudaError_t launch_c27_resid(const Dims& d, const W27& A, const double* u, const double* b, double* r,
-                             int zero_interior, double* partials, const DevState* st, cudaStream_t s);
+                             double* partials, const DevState* st, cudaStream_t s);
+// the same with r stored as dt_r (DT_F64 or DT_F32: the refinement's outer
+// residual, rounded to FP32 on the integer pipe)
+cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, const double* u, const double* b, int dt_r, void* r,
+                                double* partials, const DevState* st, cudaStream_t s);
 int c27_blocks(const Dims& d);
 // Initial residual of a compact solve: r = b - A u (stored FP64 or FP32 per
 // dt_r) with per-block partials {sum r^2, 0} at partials[0 .. 2 nb) and the
@@ -42,24 +46,16 @@ cudaError_t launch_c27_coarse_cg(const Dims& d, const W27& A, const double* b, d
                                  const DevState* st, cudaStream_t s);
 size_t c27_coarse_smem(const Dims& d);
 
-// Storage-typed variants for the FP32 inner cycles of the refinement (dt: DT_F64
-// or DT_F32 storage of u and b, arithmetic in the matching precision; r may be
-// stored in FP32 from FP64 arithmetic -- the refinement's outer residual).
-cudaError_t launch_c27_resid_dt(const Dims& d, const W27& A, int dt, const void* u, const void* b, int dt_r,
-                                void* r, double* partials, const DevState* st, cudaStream_t s,
-                                int zero_interior = 0);
-cudaError_t launch_c27_spai_dt(const Dims& d, const W27& M, double omega, int dt, const void* r, void* u,
-                               const DevState* st, cudaStream_t s);
-// TMA-staged FP32 passes (mode 0: dst = b - A src; mode 1: dst -= omega M src) on
-// level layouts with 16-byte aligned rows; a TMA wait that times out sets *fault
-// One SPAI smoothing step u' = u - omega M (b - A u) of an FP32 level in one
-// pass, written to dst (dst != u; u's boundary nodes read as the boundary
-// data, dst's boundary nodes are left as they are).  TMA-staged; a stage wait
-// that times out sets *fault.
+// FP32 passes of the refinement's inner cycles on level layouts with 16-byte
+// aligned rows (TMA-staged; a stage wait that times out sets *fault).
+// One SPAI smoothing step u' = u - omega M (b - A u) in one pass, written to
+// dst (dst != u; u's boundary nodes read as the boundary data, dst's boundary
+// nodes are left as they are).
 cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
                               const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s);
-cudaError_t launch_c27_tma(const Dims& d, const W27& W, double omega, int mode, const float* src, const float* b,
-                           float* dst, const DevState* st, int* fault, cudaStream_t s);
+// dst = b - A src on the interior
+cudaError_t launch_c27_tma(const Dims& d, const W27& W, const float* src, const float* b, float* dst,
+                           const DevState* st, int* fault, cudaStream_t s);
 // coarsest CG in FP64 arithmetic on FP32 or FP64 storage
 cudaError_t launch_c27_coarse_cg_dt(const Dims& d, const W27& A, int dt, const void* b, void* u, double tol,
                                     const DevState* st, cudaStream_t s);

@@ -740,8 +740,8 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   const double n = (double)L.d.ni() * L.d.nj() * L.d.nk();
   // residual pass: FP64 levels march z through L1, FP32 levels stage planes by TMA
   auto resid = [&](void* out) -> cudaError_t {
-    if (fp64) return launch_c27_resid_dt(L.d, C.A[l], dt, u, b, dt, out, nullptr, st, s);
-    return launch_c27_tma(L.d, C.A[l], 0.0, 0, (const float*)u, (const float*)b, (float*)out, st, &h->st->fault, s);
+    if (fp64) return launch_c27_resid_dt(L.d, C.A[l], (const double*)u, (const double*)b, DT_F64, out, nullptr, st, s);
+    return launch_c27_tma(L.d, C.A[l], (const float*)u, (const float*)b, (float*)out, st, &h->st->fault, s);
   };
   auto smooth = [&](int steps) -> cudaError_t {
     for (int it = 0; it < steps; it++) {
@@ -761,7 +761,7 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
       prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, n * 3.0 * S, n * 16.0, fp64, s);
-      e2 = (h->nlaunch += 1, launch_c27_spai_dt(L.d, C.M[l], C.omega[l], dt, r, u, st, s));
+      e2 = (h->nlaunch += 1, launch_c27_spai(L.d, C.M[l], C.omega[l], (const double*)r, (double*)u, st, s));
       prof_end(h, s);
       if (e2 != cudaSuccess) return e2;
     }
@@ -835,7 +835,7 @@ ps_status begin_mg_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
     const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
     if (e == cudaSuccess) {
       prof_begin(h, PC_NORM0, n * 24.0, n * 17.0, 1, q);
-      e = (h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, 0, h->partials, h->st, q));
+      e = (h->nlaunch += 1, launch_c27_resid(h->d0, C->A[0], phi, b, rr, h->partials, h->st, q));
       prof_end(h, q);
     }
     if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, q, cond, chunk));
@@ -894,7 +894,7 @@ ps_status begin_ir_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
     }
     if (e == cudaSuccess) {
       prof_begin(h, PC_NORM0, n * 20.0, n * 17.0, 1, q);
-      e = (h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], DT_F64, phi, b64, DT_F32, L.fs, h->partials, h->st, q));
+      e = (h->nlaunch += 1, launch_c27_resid_dt(h->d0, C->A[0], phi, b64, DT_F32, L.fs, h->partials, h->st, q));
       prof_end(h, q);
     }
     if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 2, h->st, q, cond, chunk));
