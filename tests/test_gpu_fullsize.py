@@ -8,7 +8,9 @@ so these tests check what it can compute one by one at full size:
     direct addition-theorem form -G sum rho dV sum_l r'^l/r^(l+1) P_l(cos g)
     over the full density (the GPU uses monomial moments + solid harmonics);
   * the monopole moment against the total mass sum rho h^3;
-  * mixed-precision refinement against the FP64 GPU potential (<= 1e-7).
+  * mixed-precision refinement against the FP64 GPU potential (<= 1e-7);
+  * for the compact sixth-order multigrid (255^3), the oracle's compact residual
+    of the FP64 and FP32-refinement potentials against the reported one.
 """
 import math
 
@@ -122,3 +124,40 @@ def test_config4_spherical_full(pkg):
     np.testing.assert_allclose(info.moments[:49], q, rtol=0, atol=1e-12 * abs(q[0]))
     shell = OM.spherical_outer_ghost(q, r, th, ph_, 6, 1.0)
     np.testing.assert_allclose(P[1:-1, 1:-1, -1], shell, rtol=1e-12)
+
+
+def test_compact_sixth_order_two_spheres_255(pkg):
+    """The compact timings' workload (Sec. 3.1's two spheres on [-1, 1]^3,
+    sixth-order compact stencil, SPAI V(3,3), Galerkin coarse operators,
+    multipole l_max 4, residual reduction 1e-6) at 255^3 interior nodes, in
+    FP64 and with FP32 refinement: the oracle's compact residual
+    ||R_h f - L_h phi|| / ||R_h f - L_h phi0|| of each GPU potential meets the
+    tolerance and equals the relative residual the GPU reported; the monopole
+    equals the total mass."""
+    from oracle import compact as OC
+    n, lo, hi = 256, (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    rho = W.smooth_sphere_density(n, 2, [(0.0, 0.0, 0.4), (0.0, 0.0, -0.2)], [0.08, 0.08], [1.0, 2.0])
+    g = cart_grid(n, 2, lo, hi)
+    b = OC.compact_rhs(4 * math.pi * rho, g, 6)
+    wA = OC.level_operators([g], 6)[0]
+    interior = g.interior
+
+    def rel_res(ph):
+        ph0 = ph.copy()
+        ph0[interior] = 0.0
+        r = OC.residual27(ph, b, g, wA)[interior]
+        r0 = OC.residual27(ph0, b, g, wA)[interior]
+        return float(np.sqrt(np.sum(r * r)) / np.sqrt(np.sum(r0 * r0)))
+
+    mass = float(np.sum(rho[interior]) * g.h[0] * g.h[1] * g.h[2])
+    rho_t = torch.from_numpy(rho).cuda()
+    with pkg.CartesianSolver(n, 2, lo=lo, hi=hi, bc="multipole", lmax=4) as s:
+        for prec in ("fp64", "mixed_fp32"):
+            phi = torch.zeros_like(rho_t)
+            info = s.solve(rho_t, phi, tol=1e-6, method="mg", prec=prec, nu1=3, nu2=3, max_iter=40,
+                           inner_cycles=2, compact_order=6)
+            assert info.converged, (prec, info)
+            rel = rel_res(phi.cpu().numpy())
+            assert rel <= 1e-6 * (1 + 1e-6), (prec, rel)
+            assert abs(rel - info.rel_residual) <= 1e-6 * rel, (prec, rel, info.rel_residual)
+            assert abs(info.moments[0] - mass) <= 1e-13 * mass
