@@ -520,22 +520,24 @@ cudaError_t launch_c27_tma(const Dims& d, const W27& W, const float* src, const 
 // A block of GW warps owns a 30 x (GW GR) tile of outputs and a z-chunk;
 // warp w owns the strip of GR output rows y0 + GR w .., lane l the column
 // x = x0 - 1 + l (lanes 1..30 write; lanes 0 and 31 only supply the
-// residual's x-neighbours).  Per plane of the z-march each warp
-//  - forms the in-plane sums (centre, faces, diagonals) of u on its GR + 2
-//    residual rows from GR + 4 staged u rows, sharing the pair sums
-//    u(x-1) + u(x+1) between rows;
-//  - forms the residual r = b - A u of plane k + 1 on those rows (zero off
-//    the interior) from the sums of planes k, k + 1, k + 2 held in registers;
-//  - takes r's x-neighbours by shuffles, forms its in-plane sums on the GR
-//    output rows and writes u'(k) from the sums of planes k - 1, k, k + 1.
+// residual's x-neighbours).  Both stencils are applied through their
+// per-plane split (A u)(z) = P(z) + Q(z - 1) + Q(z + 1), P and Q formed from
+// the in-plane sums (centre, faces, diagonals) of each plane, so a thread
+// carries two numbers per row and plane instead of three sums.  Per plane of
+// the z-march each warp
+//  - forms P and Q of u(k + 2) on its GR + 2 residual rows from GR + 4 staged
+//    u rows, sharing the pair sums u(x-1) + u(x+1) between rows;
+//  - forms the residual r(k + 1) = b - (P(k + 1) + (Q(k) + Q(k + 2))) on those
+//    rows (zero off the interior);
+//  - takes r's x-neighbours by shuffles, forms P and Q of -omega M r(k + 1) on
+//    the GR output rows and writes u'(k) = (u(k) + P(k)) + (Q(k - 1) + Q(k + 1)).
 // The residual rows next to a strip edge are also formed by the neighbouring
 // strip, so warps never exchange residuals.  u (box 40 x (GW GR + 4)) and b
 // (box 40 x (GW GR + 2)), both from x = 4 floor((x0 - 2) / 4), arrive by TMA,
-// one stage per plane; one block barrier per plane returns a stage to the
-// copy engine.  The sums (plane_of's association) and the stencil arithmetic
-// (apply_planes) are those of a residual pass (k_c27_tma) followed by a
-// separate SPAI pass u -= omega M r, so the results are bit-identical to that
-// two-pass route; traffic is 12 bytes per node instead of 24.
+// one stage per plane, and plane k stays staged until u'(k) is written (its
+// centres); one block barrier per plane returns a stage to the copy engine.
+// Traffic is 12 bytes per node instead of 24 for a residual pass followed by a
+// SPAI pass; the results equal that route's up to FP32 rounding.
 static constexpr int GW = 4, GR = 4;                  // warps per block, output rows per warp
 static constexpr int GTX = 30, GTY = GW * GR;         // output tile
 static constexpr int GRR = GR + 2, GUR = GR + 4;      // residual rows and u rows per warp
@@ -545,12 +547,18 @@ static constexpr int GUB = GBW * GUH * 4, GBB = GBW * GBH * 4;
 static constexpr int GUBA = (GUB + 127) / 128 * 128, GBBA = (GBB + 127) / 128 * 128;
 static constexpr int GSTAGE = GUBA + GBBA;
 
-struct SmoothMarch {
-  float us[3][GRR][3];   // u sums (c, f, e) of three planes on the residual rows
-  float rs[3][GR][3];    // residual sums of three planes on the output rows
-};
+// Per-plane split of a class stencil w on the in-plane sums (C, F, E) of one
+// plane: P = w0 C + w1 F + w2 E and Q = w1 C + w2 F + w3 E, so that
+// (A u)(z) = P(z) + Q(z - 1) + Q(z + 1).
+__device__ __forceinline__ void pq_split(const float (&w)[4], float c, float f, float e, float& P, float& Q) {
+  P = fmaf(w[0], c, fmaf(w[1], f, w[2] * e));
+  Q = fmaf(w[1], c, fmaf(w[2], f, w[3] * e));
+}
 
-__device__ __forceinline__ void c27_usums(const float* __restrict__ U, float (&S)[GRR][3]) {
+// u of one staged plane on the residual rows: P and Q of its in-plane sums
+// (the pair sums u(x-1) + u(x+1) shared between rows)
+__device__ __forceinline__ void c27_upq(const float* __restrict__ U, const float (&w)[4], float (&P)[GRR],
+                                        float (&Q)[GRR]) {
   float c[GUR], a[GUR];
 #pragma unroll
   for (int s = 0; s < GUR; s++) {
@@ -558,16 +566,12 @@ __device__ __forceinline__ void c27_usums(const float* __restrict__ U, float (&S
     a[s] = U[s * GBW - 1] + U[s * GBW + 1];
   }
 #pragma unroll
-  for (int t = 0; t < GRR; t++) {
-    S[t][0] = c[t + 1];
-    S[t][1] = a[t + 1] + (c[t] + c[t + 2]);
-    S[t][2] = a[t] + a[t + 2];
-  }
+  for (int t = 0; t < GRR; t++) pq_split(w, c[t + 1], a[t + 1] + (c[t] + c[t + 2]), a[t] + a[t + 2], P[t], Q[t]);
 }
 
-__device__ __forceinline__ Plane<float> pl3(const float (&v)[3]) { return Plane<float>{v[0], v[1], v[2]}; }
-
-__device__ __forceinline__ void c27_rsums(const float (&r)[GRR], float (&R)[GR][3]) {
+// the residual of one plane on the residual rows: P and Q (of -omega M) of its
+// in-plane sums on the output rows, x-neighbours by shuffles
+__device__ __forceinline__ void c27_rpq(const float (&r)[GRR], const float (&w)[4], float (&P)[GR], float (&Q)[GR]) {
   float ar[GRR];
 #pragma unroll
   for (int t = 0; t < GRR; t++) {
@@ -576,14 +580,15 @@ __device__ __forceinline__ void c27_rsums(const float (&r)[GRR], float (&R)[GR][
     ar[t] = l + h;
   }
 #pragma unroll
-  for (int q = 0; q < GR; q++) {
-    R[q][0] = r[q + 1];
-    R[q][1] = ar[q + 1] + (r[q] + r[q + 2]);
-    R[q][2] = ar[q] + ar[q + 2];
-  }
+  for (int q = 0; q < GR; q++) pq_split(w, r[q + 1], ar[q + 1] + (r[q] + r[q + 2]), ar[q] + ar[q + 2], P[q], Q[q]);
 }
 
-__global__ void __launch_bounds__(32 * GW, 4)
+struct SmoothMarch {
+  float up[3][GRR], uq[3][GRR];   // P and Q of u on the residual rows, three planes
+  float mp[3][GR], mq[3][GR];     // P and Q of the residual under -omega M on the output rows
+};
+
+__global__ void __launch_bounds__(32 * GW, 5)
     k_c27_smooth(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mB, Dims d,
                  Wts<float> WA, Wts<float> WM, float om, float* __restrict__ dst, int zc,
                  const DevState* __restrict__ st, int* __restrict__ fault) {
@@ -635,66 +640,69 @@ __global__ void __launch_bounds__(32 * GW, 4)
   auto bbase = [&](int z) -> const float* {   // b row y0w - 1 at column x
     return reinterpret_cast<const float*>(smem + stage(z) * GSTAGE + GUBA) + GR * warp * GBW + col;
   };
-  // residual of plane z on the residual rows from the u sums of planes z - 1, z, z + 1
-  auto resid = [&](int z, const float (&Sm)[GRR][3], const float (&Sc)[GRR][3], const float (&Sn)[GRR][3],
+  float nm[4];   // -omega M
+#pragma unroll
+  for (int a = 0; a < 4; a++) nm[a] = -om * WM.w[a];
+  // residual of plane z on the residual rows: b - (P(z) + (Q(z - 1) + Q(z + 1))), zero off the interior
+  auto resid = [&](int z, const float (&Pc)[GRR], const float (&Qm)[GRR], const float (&Qn)[GRR],
                    float (&r)[GRR]) {
     const bool zin = z >= 1 && z <= d.nk();
     const float* B = bbase(z);
 #pragma unroll
     for (int t = 0; t < GRR; t++) {
       float rv = 0.0f;
-      if (zin && rok[t]) rv = B[t * GBW] - apply_planes<float>(WA.w, pl3(Sm[t]), pl3(Sc[t]), pl3(Sn[t]));
+      if (zin && rok[t]) rv = B[t * GBW] - (Pc[t] + (Qm[t] + Qn[t]));
       r[t] = rv;
     }
   };
   const long long sy = d.sy(), sz = d.sz();
   float* ob = dst + d.at(min(max(x, 1), d.ni()), min(y0w, d.nj()), k0);   // output row y0w, plane k0
   SmoothMarch m;
-  // prologue: residual planes k0 - 1 and k0 (u planes k0 - 2 .. k0 + 1)
+  // prologue: residual planes k0 - 1 and k0 (u planes k0 - 2 .. k0 + 1); u
+  // plane z's split sits in slot (z - zl) mod 3, the residual's of plane z in
+  // slot (z - k0 + 1) mod 3
   {
     float r[GRR];
     wait_next();
-    c27_usums(ubase(zl), m.us[0]);
+    c27_upq(ubase(zl), WA.w, m.up[0], m.uq[0]);
     wait_next();
-    c27_usums(ubase(zl + 1), m.us[1]);
+    c27_upq(ubase(zl + 1), WA.w, m.up[1], m.uq[1]);
     wait_next();
-    c27_usums(ubase(zl + 2), m.us[2]);
-    resid(k0 - 1, m.us[0], m.us[1], m.us[2], r);
-    c27_rsums(r, m.rs[0]);
+    c27_upq(ubase(zl + 2), WA.w, m.up[2], m.uq[2]);
+    resid(k0 - 1, m.up[1], m.uq[0], m.uq[2], r);
+    c27_rpq(r, nm, m.mp[0], m.mq[0]);
     wait_next();
-    c27_usums(ubase(zl + 3), m.us[0]);
-    resid(k0, m.us[1], m.us[2], m.us[0], r);
-    c27_rsums(r, m.rs[1]);
+    c27_upq(ubase(zl + 3), WA.w, m.up[0], m.uq[0]);
+    resid(k0, m.up[2], m.uq[1], m.uq[0], r);
+    c27_rpq(r, nm, m.mp[1], m.mq[1]);
   }
   __syncthreads();
-  if (tid == 0) {   // planes k0 - 2 .. k0 are no longer read
+  if (tid == 0) {   // planes k0 - 2 and k0 - 1 are no longer read (plane k0 keeps the centres of output k0)
     fence_proxy_async();
     issue(zl + GNS);
     issue(zl + 1 + GNS);
-    issue(zl + 2 + GNS);
   }
   // output plane k; P = (k - k0) mod 3 fixes the register slots:
-  // u sums of planes k, k + 1, k + 2 in us[(P+2)%3], us[P], us[(P+1)%3],
-  // residual sums of planes k - 1, k, k + 1 in rs[P], rs[(P+1)%3], rs[(P+2)%3]
+  // u splits of planes k, k + 1, k + 2 in slots (P+2)%3, P, (P+1)%3,
+  // residual splits of planes k - 1, k, k + 1 in slots P, (P+1)%3, (P+2)%3
   auto step = [&](auto Pc, int k) {
     constexpr int P = decltype(Pc)::value;
     constexpr int UK = (P + 2) % 3, UK1 = P, UK2 = (P + 1) % 3;
     constexpr int RM = P, RC = (P + 1) % 3, RN = (P + 2) % 3;
     wait_next();   // plane k + 2
-    c27_usums(ubase(k + 2), m.us[UK2]);
+    c27_upq(ubase(k + 2), WA.w, m.up[UK2], m.uq[UK2]);
     float r[GRR];
-    resid(k + 1, m.us[UK], m.us[UK1], m.us[UK2], r);
-    c27_rsums(r, m.rs[RN]);
+    resid(k + 1, m.up[UK1], m.uq[UK], m.uq[UK2], r);
+    c27_rpq(r, nm, m.mp[RN], m.mq[RN]);
+    const float* U = ubase(k) + 2 * GBW;   // u row y0w, plane k
 #pragma unroll
     for (int q = 0; q < GR; q++)
-      if (oin[q])
-        ob[q * sy] = fmaf(-om, apply_planes<float>(WM.w, pl3(m.rs[RM][q]), pl3(m.rs[RC][q]), pl3(m.rs[RN][q])),
-                          m.us[UK][q + 1][0]);
+      if (oin[q]) ob[q * sy] = (U[q * GBW] + m.mp[RC][q]) + (m.mq[RM][q] + m.mq[RN][q]);
     ob += sz;
-    __syncthreads();   // plane k + 1 (its b) is no longer read
+    __syncthreads();   // plane k (its u) and plane k + 1 (its b) are no longer read
     if (tid == 0) {
       fence_proxy_async();
-      issue(k + 1 + GNS);
+      issue(k + GNS);
     }
   };
   for (int k = k0; k < k1; k += 3) {
