@@ -406,111 +406,8 @@ cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const dou
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ TMA-staged FP32 residual
-// The FP32 residual r = b - A u before a restriction streams u through a ring
-// of TMA-staged planes (box 40 x 10 starting at x = 32 bx - 4: a 32 x 8 tile of
-// nodes 32 bx + 1 .. 32 bx + 32 with one-node halos, widened in x to whole
-// 16-byte granules), so each value is loaded into shared memory once instead
-// of being fetched nine times per plane through L1; b is read once per node
-// from global memory.
-static constexpr int TTX = 32, TTY = 8, TXH = 4;
-static constexpr int TWP = TTX + 2 * TXH, THP = TTY + 2, TNS = 4;
-static constexpr int TPB = TWP * THP * 4;   // bytes per staged FP32 plane
-static constexpr int TPBA = (TPB + 127) / 128 * 128;
-
-__global__ void __launch_bounds__(TTX* TTY)
-    k_c27_tma(const __grid_constant__ CUtensorMap mS, Dims d, Wts<float> W, const float* __restrict__ b,
-              float* __restrict__ dst, int zc, const DevState* __restrict__ st, int* __restrict__ fault) {
-  __shared__ __align__(128) unsigned char smem[TNS * TPBA];
-  __shared__ __align__(8) unsigned long long bar[TNS];
-  if (st != nullptr && st->done) return;   // uniform
-  const int tid = threadIdx.x + TTX * threadIdx.y;
-  const int x0 = blockIdx.x * TTX + 1, y0 = blockIdx.y * TTY + 1;   // first node of the tile
-  const int xs = x0 - 1 - TXH;                                         // box x start: 32 bx - 4, a multiple of 4
-  const int k0 = 1 + blockIdx.z * zc, k1 = min(k0 + zc, d.nk() + 1);  // output planes [k0, k1)
-  const int zl = k0 - 1, zh = k1;                                      // staged planes [zl, zh]
-  float* ring = reinterpret_cast<float*>(smem);
-  if (tid == 0) {
-    for (int q = 0; q < TNS; q++) mbar_init(&bar[q], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  auto issue = [&](int z) {   // thread 0: stage of plane z
-    if (z > zh) return;
-    const int q = (z - zl) % TNS;
-    mbar_expect_tx(&bar[q], TPB);
-    tma_load_3d(ring + q * (TPBA / 4), &mS, xs, y0 - 1, z, &bar[q]);
-  };
-  if (tid == 0)
-    for (int z = zl; z < zl + TNS; z++) issue(z);
-  bool ok = true;
-  int wq = 0;
-  unsigned wph = 0;
-  auto wait_next = [&]() {
-    mbar_wait(&bar[wq], wph, ok);
-    if (++wq == TNS) { wq = 0; wph ^= 1u; }
-  };
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = x0 + tx, j = y0 + ty;
-  const bool in = i <= d.ni() && j <= d.nj();
-  const int sc = (ty + 1) * TWP + (tx + TXH + 1);   // staged index of (i, j): column i - xs
-  auto sums = [&](int z) -> Plane<float> {
-    const float* P = ring + ((z - zl) % TNS) * (TPBA / 4);
-    Raw9<float> v;
-    v.c = P[sc];
-    v.xm = P[sc - 1];
-    v.xp = P[sc + 1];
-    v.ym = P[sc - TWP];
-    v.yp = P[sc + TWP];
-    v.mm = P[sc - TWP - 1];
-    v.pm = P[sc - TWP + 1];
-    v.mp = P[sc + TWP - 1];
-    v.pp = P[sc + TWP + 1];
-    return plane_of(v);
-  };
-  wait_next();
-  wait_next();
-  Plane<float> pm = sums(zl), pc = sums(zl + 1);
-  for (int k = k0; k < k1; k++) {
-    wait_next();   // plane k + 1
-    const Plane<float> pn = sums(k + 1);
-    if (in) {
-      const float a = apply_planes<float>(W.w, pm, pc, pn);
-      const long long q = d.at(i, j, k);
-      dst[q] = b[q] - a;
-    }
-    pm = pc;
-    pc = pn;
-    __syncthreads();   // plane k - 1 is no longer read
-    if (tid == 0) {
-      fence_proxy_async();
-      issue(k - 1 + TNS);
-    }
-  }
-  if (!ok && fault != nullptr) atomicExch(fault, 1);
-}
-
 static int g_sms = 0;
 
-cudaError_t launch_c27_tma(const Dims& d, const W27& W, const float* src, const float* b, float* dst,
-                           const DevState* st, int* fault, cudaStream_t s) {
-  if (d.g != 1) return cudaErrorInvalidValue;
-  CUtensorMap map;
-  if (!encode_level_map(&map, DT_F32, src, d, TWP, THP)) return cudaErrorInvalidValue;
-  if (g_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 152;
-  }
-  const int gx = (d.ni() + TTX - 1) / TTX, gy = (d.nj() + TTY - 1) / TTY, nk = d.nk();
-  // about two waves of 8 blocks per SM, z-chunks of at least 8 planes
-  const int want = std::max(1, 16 * g_sms / (gx * gy));
-  const int zc = std::max(8, (nk + want - 1) / want);
-  const dim3 grid(gx, gy, (nk + zc - 1) / zc), blk(TTX, TTY);
-  k_c27_tma<<<grid, blk, 0, s>>>(map, d, wts<float>(W), b, dst, zc, st, fault);
-  return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------ fused FP32 smoothing step
 // One SPAI step u' = u - omega M (b - A u) of an inner FP32 level in a single
@@ -588,6 +485,9 @@ struct SmoothMarch {
   float mp[3][GR], mq[3][GR];     // P and Q of the residual under -omega M on the output rows
 };
 
+// RESID: the same march writes the residual r = b - A u of the output rows
+// instead (the residual before a restriction), with no M stencil.
+template <bool RESID>
 __global__ void __launch_bounds__(32 * GW, 5)
     k_c27_smooth(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mB, Dims d,
                  Wts<float> WA, Wts<float> WM, float om, float* __restrict__ dst, int zc,
@@ -674,7 +574,13 @@ __global__ void __launch_bounds__(32 * GW, 5)
     wait_next();
     c27_upq(ubase(zl + 3), WA.w, m.up[0], m.uq[0]);
     resid(k0, m.up[2], m.uq[1], m.uq[0], r);
-    c27_rpq(r, nm, m.mp[1], m.mq[1]);
+    if (RESID) {
+#pragma unroll
+      for (int q = 0; q < GR; q++)
+        if (oin[q]) ob[q * sy] = r[q + 1];
+    } else {
+      c27_rpq(r, nm, m.mp[1], m.mq[1]);
+    }
   }
   __syncthreads();
   if (tid == 0) {   // planes k0 - 2 and k0 - 1 are no longer read (plane k0 keeps the centres of output k0)
@@ -693,12 +599,21 @@ __global__ void __launch_bounds__(32 * GW, 5)
     c27_upq(ubase(k + 2), WA.w, m.up[UK2], m.uq[UK2]);
     float r[GRR];
     resid(k + 1, m.up[UK1], m.uq[UK], m.uq[UK2], r);
-    c27_rpq(r, nm, m.mp[RN], m.mq[RN]);
-    const float* U = ubase(k) + 2 * GBW;   // u row y0w, plane k
+    if (RESID) {
+      // r of plane k + 1 (plane k0 was written by the prologue)
+      ob += sz;
+      if (k + 1 < k1)
 #pragma unroll
-    for (int q = 0; q < GR; q++)
-      if (oin[q]) ob[q * sy] = (U[q * GBW] + m.mp[RC][q]) + (m.mq[RM][q] + m.mq[RN][q]);
-    ob += sz;
+        for (int q = 0; q < GR; q++)
+          if (oin[q]) ob[q * sy] = r[q + 1];
+    } else {
+      c27_rpq(r, nm, m.mp[RN], m.mq[RN]);
+      const float* U = ubase(k) + 2 * GBW;   // u row y0w, plane k
+#pragma unroll
+      for (int q = 0; q < GR; q++)
+        if (oin[q]) ob[q * sy] = (U[q * GBW] + m.mp[RC][q]) + (m.mq[RM][q] + m.mq[RN][q]);
+      ob += sz;
+    }
     __syncthreads();   // plane k (its u) and plane k + 1 (its b) are no longer read
     if (tid == 0) {
       fence_proxy_async();
@@ -713,8 +628,9 @@ __global__ void __launch_bounds__(32 * GW, 5)
   if (!ok && fault != nullptr) atomicExch(fault, 1);
 }
 
-cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
-                              const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
+template <bool RESID>
+static cudaError_t launch_march(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
+                                const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
   if (d.g != 1 || u == dst) return cudaErrorInvalidValue;
   CUtensorMap mu, mb;
   if (!encode_level_map(&mu, DT_F32, u, d, GBW, GUH)) return cudaErrorInvalidValue;
@@ -726,12 +642,23 @@ cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double 
     if (g_sms <= 0) g_sms = 152;
   }
   const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + GTY - 1) / GTY, nk = d.nk();
-  // about three waves of 4 blocks per SM, z-chunks of at least 16 planes (4 extra staged planes each)
+  // about two to three waves of 5 blocks per SM, z-chunks of at least 16 planes (4 extra staged planes each)
   const int want = std::max(1, 12 * g_sms / (gx * gy));
   const int zc = std::max(16, (nk + want - 1) / want);
   const dim3 grid(gx, gy, (nk + zc - 1) / zc);
-  k_c27_smooth<<<grid, 32 * GW, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
+  k_c27_smooth<RESID><<<grid, 32 * GW, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st,
+                                               fault);
   return cudaGetLastError();
+}
+
+cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
+                              const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
+  return launch_march<false>(d, A, M, omega, u, b, dst, st, fault, s);
+}
+
+cudaError_t launch_c27_resid_f32(const Dims& d, const W27& A, const float* u, const float* b, float* r,
+                                 const DevState* st, int* fault, cudaStream_t s) {
+  return launch_march<true>(d, A, A, 0.0, u, b, r, st, fault, s);
 }
 
 // ------------------------------------------------------------------ right-hand side

@@ -53,9 +53,9 @@ size_t c27_coarse_smem(const Dims& d);
 // nodes are left as they are).
 cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
                               const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s);
-// dst = b - A src on the interior
-cudaError_t launch_c27_tma(const Dims& d, const W27& W, const float* src, const float* b, float* dst,
-                           const DevState* st, int* fault, cudaStream_t s);
+// r = b - A u on the interior (the residual before a restriction; r != u)
+cudaError_t launch_c27_resid_f32(const Dims& d, const W27& A, const float* u, const float* b, float* r,
+                                 const DevState* st, int* fault, cudaStream_t s);
 // coarsest CG in FP64 arithmetic on FP32 or FP64 storage
 cudaError_t launch_c27_coarse_cg_dt(const Dims& d, const W27& A, int dt, const void* b, void* u, double tol,
                                     const DevState* st, cudaStream_t s);

@@ -738,10 +738,11 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   // the array that holds the current iterate
   void* ub = fp64 ? nullptr : L.phib;
   const double n = (double)L.d.ni() * L.d.nj() * L.d.nk();
-  // residual pass: FP64 levels march z through L1, FP32 levels stage planes by TMA
+  // residual pass: FP64 levels march z through L1 (four rows per thread), FP32
+  // levels run the register-blocked TMA march of the smoothing step
   auto resid = [&](void* out) -> cudaError_t {
     if (fp64) return launch_c27_resid_dt(L.d, C.A[l], (const double*)u, (const double*)b, DT_F64, out, nullptr, st, s);
-    return launch_c27_tma(L.d, C.A[l], (const float*)u, (const float*)b, (float*)out, st, &h->st->fault, s);
+    return launch_c27_resid_f32(L.d, C.A[l], (const float*)u, (const float*)b, (float*)out, st, &h->st->fault, s);
   };
   auto smooth = [&](int steps) -> cudaError_t {
     for (int it = 0; it < steps; it++) {
