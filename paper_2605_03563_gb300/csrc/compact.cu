@@ -1,5 +1,6 @@
 // Compact radius-one stencils, SPAI smoothing and Galerkin coarse operators
-// (Sec. 2.1.3), FP64.
+// (Sec. 2.1.3): FP64 passes, and the FP32 passes of the refinement's inner
+// cycles.
 //
 // Compact schemes L_h u = R_h f of order 2, 4, 6 (isotropic spacing; weights
 // from Taylor matching, as the paper cites compact schemes without printing
@@ -13,12 +14,14 @@
 // at the first interior layer; there f is the cubic extrapolation
 // 4 f_0 - 6 f_1 + 4 f_2 - f_3 along that axis.
 //
-// The 27-point kernels march z with the in-plane sums of three planes in
-// registers: per plane C (centre), F (4 in-plane faces), E (4 in-plane
-// diagonals), so that
+// The 27-point kernels march z and form per plane the in-plane sums C
+// (centre), F (4 in-plane faces), E (4 in-plane diagonals), so that
 //   (A u)(z) = w0 C(z) + w1 (F(z) + C(z-1) + C(z+1)) + w2 (E(z) + F(z-1) + F(z+1))
-//            + w3 (E(z-1) + E(z+1)),
-// about 15 FP64 instructions per node instead of 27.
+//            + w3 (E(z-1) + E(z+1))
+//            = P(z) + Q(z-1) + Q(z+1),  P = w0 C + w1 F + w2 E,  Q = w1 C + w2 F + w3 E;
+// a thread owns several rows of a column, so the pair sums u(x-1) + u(x+1)
+// serve the rows above and below as well (12.5 FP64 operations per node for
+// a residual instead of 27 multiply-adds).
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
