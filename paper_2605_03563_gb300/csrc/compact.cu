@@ -139,11 +139,6 @@ struct Wts {
   C w[4];
 };
 
-template <typename C>
-__device__ __forceinline__ C apply_planes(const C w[4], const Plane<C>& m, const Plane<C>& c, const Plane<C>& p) {
-  return fma(w[0], c.c, fma(w[1], (c.f + (m.c + p.c)), fma(w[2], (c.e + (m.f + p.f)), w[3] * (m.e + p.e))));
-}
-
 // Per-plane split of a 27-point class stencil w (centre, faces, edges,
 // corners): with the in-plane sums (C, F, E) of planes z - 1, z, z + 1,
 //   (A u)(z) = P(z) + Q(z - 1) + Q(z + 1),
@@ -168,26 +163,6 @@ __device__ __forceinline__ TR store_as(double v) {
   if constexpr (std::is_same<TR, float>::value) return f64_to_f32_pow2(v, 0);
   else return (TR)v;
 }
-
-// per-block {sum, 0} into partials[2 b], partials[2 b + 1] (blocks of CBX x CBY threads)
-__device__ __forceinline__ void block_partial(double v, double* __restrict__ partials) {
-  __shared__ double sh[CBX * CBY / 32];
-  const int tid = threadIdx.x + CBX * threadIdx.y;
-  v = warp_sum(v);
-  if ((tid & 31) == 0) sh[tid >> 5] = v;
-  __syncthreads();
-  if (tid < 32) {
-    double a = tid < CBX * CBY / 32 ? sh[tid] : 0.0;
-    a = warp_sum(a);
-    if (tid == 0) {
-      const int bid = block_linear_id();
-      partials[2 * bid] = a;
-      partials[2 * bid + 1] = 0.0;
-    }
-  }
-}
-
-
 
 // per-block {sum, 0} into partials[2 b], partials[2 b + 1] for blocks of NT threads
 template <int NT>
