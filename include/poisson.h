@@ -234,6 +234,22 @@ const char* poisson_last_error(void);
  * precision (used for admission control); 0 for invalid arguments. */
 size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max, int prec);
 
+/* Operators of the compact-stencil multigrid (Sec. 2.1.3), computed on the
+ * host exactly as a compact solve builds them (no GPU work).  For compact
+ * order 2, 4 or 6 and finest spacing h > 0, level l = 0 .. nlevels-1 has
+ * spacing h 2^l and
+ *   a[4 l .. 4 l + 3]  the class weights (centre, faces, edges, corners;
+ *                      absolute units) of its operator: the compact L_h on
+ *                      level 0, the Galerkin product R A P of the level above
+ *                      (full weighting R, trilinear P = 8 R^T) below it;
+ *   m[4 l .. 4 l + 3]  the SPAI smoother M = h_l^2 (alpha, beta, gamma, delta)
+ *                      of Table 1 (Eq. Smoother);
+ *   omega[l]           its relaxation weight (Eq. richardson).
+ * All three are host arrays owned by the caller; m and omega may be NULL.
+ * Errors: PS_ERR_INVALID_ARG for an order other than 2, 4, 6, h <= 0 or not
+ * finite, nlevels < 1 or > 30, or a NULL a. */
+ps_status poisson_compact_operators(int order, double h, int nlevels, double* a, double* m, double* omega);
+
 /* ------------------------------------------------------------------ batched executor
  * Many Cartesian multigrid solves of different grid sizes advanced together
  * (continuous batching): one step advances every active solve by the same

@@ -70,6 +70,8 @@ SIGNATURES = {
     "poisson_destroy": (None, [C.c_void_p]),
     "poisson_last_error": (C.c_char_p, []),
     "poisson_workspace_bytes": (C.c_size_t, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_int]),
+    "poisson_compact_operators": (C.c_int, [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "poisson_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "poisson_profile_read": (C.c_int, [C.c_void_p, C.POINTER(PsKernelStat), C.c_int]),
     "ps_op_apply": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -713,6 +713,20 @@ struct CompactLevels {
   std::vector<double> omega;
 };
 
+// Level operators of the compact multigrid for the spacings hl of its levels
+// (finest first): compact L_h on the finest, Galerkin products below, the
+// SPAI smoother of Table 1 scaled by h_l^2 on every level.
+static CompactLevels make_compact_levels(int order, const std::vector<double>& hl) {
+  CompactLevels C;
+  const double* k = kSpai[order / 2 - 1];
+  for (size_t l = 0; l < hl.size(); l++) {
+    C.A.push_back(l == 0 ? compact_lhs(order, hl[0]) : galerkin27(C.A.back()));
+    C.M.push_back(W27{{k[1] * hl[l] * hl[l], k[2] * hl[l] * hl[l], k[3] * hl[l] * hl[l], k[4] * hl[l] * hl[l]}});
+    C.omega.push_back(k[0]);
+  }
+  return C;
+}
+
 // One V-cycle of the compact multigrid (Sec. 2.1.3): SPAI steps
 // u -= omega M (b - A u), residual, full weighting into the coarse right-hand
 // side, the coarse error from zero, trilinear correction, SPAI steps; the
@@ -815,14 +829,9 @@ ps_status begin_mg_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
   double* phi = h->phi0;
   H->lv[0].phi = phi;
   const int order = o->compact_order;
-  auto C = std::make_shared<CompactLevels>();
-  for (int l = 0; l < h->nlev; l++) {
-    const double hl = H->lv[l].h[0];
-    C->A.push_back(l == 0 ? compact_lhs(order, hl) : galerkin27(C->A.back()));
-    const double* k = kSpai[order / 2 - 1];
-    C->M.push_back(W27{{k[1] * hl * hl, k[2] * hl * hl, k[3] * hl * hl, k[4] * hl * hl}});
-    C->omega.push_back(k[0]);
-  }
+  std::vector<double> hl;
+  for (int l = 0; l < h->nlev; l++) hl.push_back(H->lv[l].h[0]);
+  auto C = std::make_shared<CompactLevels>(make_compact_levels(order, hl));
   const int nb = c27_blocks(h->d0);
   if ((r = ensure_partials(h, 2 * nb)) != PS_OK) return r;
   double* b = h->fs64;
@@ -859,14 +868,9 @@ ps_status begin_ir_compact(ps_ctx* h, const double* rho, const ps_solve_opts* o,
   ps_status r = build_hier(h, 1, H);
   if (r != PS_OK) return r;
   const int order = o->compact_order;
-  auto C = std::make_shared<CompactLevels>();
-  for (int l = 0; l < h->nlev; l++) {
-    const double hl = H->lv[l].h[0];
-    C->A.push_back(l == 0 ? compact_lhs(order, hl) : galerkin27(C->A.back()));
-    const double* k = kSpai[order / 2 - 1];
-    C->M.push_back(W27{{k[1] * hl * hl, k[2] * hl * hl, k[3] * hl * hl, k[4] * hl * hl}});
-    C->omega.push_back(k[0]);
-  }
+  std::vector<double> hl;
+  for (int l = 0; l < h->nlev; l++) hl.push_back(H->lv[l].h[0]);
+  auto C = std::make_shared<CompactLevels>(make_compact_levels(order, hl));
   const int nb = c27_blocks(h->d0);
   if ((r = ensure_partials(h, 2 * nb)) != PS_OK) return r;
   double* phi = h->phi0;
@@ -1445,6 +1449,25 @@ void batch_level_desc(ps_ctx* h, const Level& L, BLevel* out) {
 extern "C" {
 
 const char* poisson_last_error(void) { return g_err.c_str(); }
+
+ps_status poisson_compact_operators(int order, double h, int nlevels, double* a, double* m, double* omega) {
+  if (order != 2 && order != 4 && order != 6)
+    return fail(PS_ERR_INVALID_ARG, "compact order must be 2, 4 or 6 (got %d)", order);
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(PS_ERR_INVALID_ARG, "h must be positive and finite");
+  if (nlevels < 1 || nlevels > 30) return fail(PS_ERR_INVALID_ARG, "nlevels must be in 1..30 (got %d)", nlevels);
+  if (!a) return fail(PS_ERR_INVALID_ARG, "a must not be NULL");
+  std::vector<double> hl;
+  for (int l = 0; l < nlevels; l++) hl.push_back(std::ldexp(h, l));
+  const CompactLevels C = make_compact_levels(order, hl);
+  for (int l = 0; l < nlevels; l++) {
+    for (int c = 0; c < 4; c++) {
+      a[4 * l + c] = C.A[l].w[c];
+      if (m) m[4 * l + c] = C.M[l].w[c];
+    }
+    if (omega) omega[l] = C.omega[l];
+  }
+  return PS_OK;
+}
 
 size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max, int prec) {
   if (!grid) return 0;

@@ -85,3 +85,17 @@ def scale_to_fp32(x, e, out, stream=None):
         raise ValueError("x must be float64 and out float32 of the same size")
     check(lib().ps_op_scale_to_fp32(_p(x), x.numel(), int(e), _p(out), _s(stream)), "ps_op_scale_to_fp32")
 
+
+def compact_operators(order, h, nlevels):
+    """Level operators of the compact-stencil multigrid (Sec. 2.1.3) as a compact
+    solve builds them, computed on the host: per level l (spacing h 2^l) the
+    class weights (centre, faces, edges, corners) of the operator (compact L_h,
+    then Galerkin products), the SPAI weights M and omega of Table 1.  Returns
+    (a, m, omega) as nested lists [nlevels][4], [nlevels][4], [nlevels]."""
+    a = (C.c_double * (4 * nlevels))()
+    m = (C.c_double * (4 * nlevels))()
+    w = (C.c_double * nlevels)()
+    check(lib().poisson_compact_operators(int(order), float(h), int(nlevels), a, m, w),
+          "poisson_compact_operators")
+    return ([list(a[4 * l:4 * l + 4]) for l in range(nlevels)],
+            [list(m[4 * l:4 * l + 4]) for l in range(nlevels)], list(w))
