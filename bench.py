@@ -25,6 +25,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -61,7 +62,10 @@ class ClockSampler:
 
     def __init__(self, gpu_id=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to BENCH_CLOCKS_DIR (default: the system temp directory);
+        # the bench line carries their summary
+        base = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(base, f"clocks_{os.getpid()}.csv")
         self.gpu_id = gpu_id
 
     def start(self):
