@@ -110,17 +110,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ reference arm (CPU oracle)
-def run_reference(args, rank, world):
-    if rank != 0:
-        return 0
-    import numpy as np
+# ------------------------------------------------------------------ the CPU oracle on the host cores
+def _oracle_replica(conn, n):
+    """One oracle process: builds the n^3 workload (density, multipole boundary,
+    hierarchy), then runs one FP64 V(2,2) cycle per "go" and answers with its
+    duration.  numpy runs these stencil loops on one thread, so the host's
+    cores are used by running one such process per core."""
     import workloads as W
     from oracle import multigrid as OMG, multipole as OM
     from oracle.grid import cart_grid, hierarchy
-    # each step is one FP64 V(2,2) cycle of the same 256^3 workload (the oracle needs
-    # ~10 s per cycle); for long runs the sample shrinks to the 128^3 grid
-    n = N if (args.steps + args.warmup) <= 16 else 128
     g = cart_grid(n)
     rho = W.gaussian_blobs(n, seed=SEED)
     phi = g.zeros()
@@ -128,42 +126,128 @@ def run_reference(args, rank, world):
     OM.apply_cartesian_bc(phi, g, q, (0.5, 0.5, 0.5), LMAX, 1.0)
     f = 4 * math.pi * rho
     levels = hierarchy(g)
-    for _ in range(args.warmup):
+    conn.send("ready")
+    while conn.recv() == "go":
+        t0 = time.perf_counter()
         OMG.vcycle(levels, 0, phi, f, 2, 2)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        OMG.vcycle(levels, 0, phi, f, 2, 2)
-    dt = time.perf_counter() - t0
-    value = (n - 1) ** 3 * args.steps / dt / 1e9
-    sample = f"{args.steps} FP64 V(2,2) cycles of the {n}^3 workload (oracle/multigrid.vcycle, numpy)"
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+def host_replicas(max_procs=None):
+    """How many oracle processes the host takes: one per core, at most one per
+    2 GB of available memory (a 256^3 oracle V-cycle peaks near 1.2 GB)."""
+    cores = os.cpu_count() or 1
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        avail = None
+    n = cores if avail is None else max(1, min(cores, int(avail // 2e9)))
+    env = os.environ.get("BENCH_CPU_PROCS")
+    if env:
+        n = max(1, min(n, int(env)))
+    if max_procs is not None:
+        n = max(1, min(n, max_procs))
+    return n
+
+
+class OracleReplicas:
+    """P spawned oracle processes on the same workload; step() runs one V-cycle
+    in each at once and returns the wall time of the slowest."""
+
+    def __init__(self, procs, n=N):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for _ in range(procs):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_replica, args=(b, n), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            if c.recv() != "ready":
+                raise RuntimeError("oracle replica failed to start")
+
+    def step(self):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("go")
+        per = [c.recv() for c in self.conns]
+        return time.perf_counter() - t0, per
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send("stop")
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.terminate()
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step is one
+    FP64 V(2,2) cycle of the same 256^3 workload in each of P processes (one per
+    core, memory permitting).  value = P x (N-1)^3 unknown updates / step time,
+    the unit of the GPU arm."""
+    if rank != 0:
+        return 0
+    procs = host_replicas()
+    reps = OracleReplicas(procs)
+    try:
+        for _ in range(args.warmup):
+            reps.step()
+        walls = []
+        for _ in range(args.steps):
+            walls.append(reps.step()[0])
+    finally:
+        reps.close()
+    dt = sum(walls)
+    value = procs * (N - 1) ** 3 * args.steps / dt / 1e9
+    sample = (f"{args.steps} steps, each one FP64 V(2,2) cycle of the 256^3 workload in each of {procs} "
+              f"single-threaded numpy processes (oracle/multigrid.vcycle); host has {os.cpu_count()} cores")
     line = {"impl": "reference", "metric": "GLUPS (fine-grid unknown updates/s over the whole solve)",
             "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_n": n},
-            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": WORKLOAD, "sample_n": N},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": procs, "kind": "oracle",
+                             "host_cores": os.cpu_count(), "threads_per_process": 1, "sample": sample},
             "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def cpu_baseline_sample():
-    """The oracle on the host: one FP64 V(2,2) cycle of the same 256^3 workload."""
-    import workloads as W
-    from oracle import multigrid as OMG
-    from oracle.grid import cart_grid, hierarchy
-    g = cart_grid(N)
-    rho = W.gaussian_blobs(N, seed=SEED)
-    phi = g.zeros()
-    f = 4 * math.pi * rho
-    levels = hierarchy(g)
-    t0 = time.perf_counter()
-    OMG.vcycle(levels, 0, phi, f, 2, 2)
-    dt = time.perf_counter() - t0
-    return {"value": (N - 1) ** 3 / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"one FP64 V(2,2) cycle of the 256^3 workload on the host ({dt:.1f} s, "
-                      "numpy, single thread)"}
+    """The oracle on the host: one FP64 V(2,2) cycle of the same 256^3 workload
+    on one core, then one on every core at once (one process per core)."""
+    reps = OracleReplicas(1)
+    try:
+        t1 = reps.step()[0]
+    finally:
+        reps.close()
+    procs = host_replicas()
+    if procs > 1:
+        reps = OracleReplicas(procs)
+        try:
+            tp = reps.step()[0]
+        finally:
+            reps.close()
+    else:
+        tp = t1
+    one = (N - 1) ** 3 / t1 / 1e9
+    allc = procs * (N - 1) ** 3 / tp / 1e9
+    return {"value": allc, "unit": "GLUPS", "cores": procs, "kind": "oracle",
+            "single_core_value": one, "host_cores": os.cpu_count(),
+            "sample": f"one FP64 V(2,2) cycle of the 256^3 workload per process, {procs} single-threaded "
+                      f"numpy processes at once ({tp:.1f} s); alone on one core {t1:.1f} s"}
 
 
 # ------------------------------------------------------------------ serving stream
@@ -520,6 +604,107 @@ def batched_throughput(dev, per_size=8, sizes=(32, 64, 96, 128, 192, 256), reps=
     return out
 
 
+# ------------------------------------------------------------------ FP64 pipe peak, bench line
+def fp64_peak(dev):
+    """Measured FP64 instruction rate of this GPU (G instructions/s, warp lanes
+    counted one by one): the library's probe kernel, 8 blocks per SM, timed
+    with CUDA events (best of 3 after one warm-up launch), for fused
+    multiply-adds and for adds."""
+    import torch
+    from paper_2605_03563_gb300 import ops
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    out = torch.empty(blocks, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for kind, name in ((0, "dfma"), (1, "dadd")):
+        times, n = [], 0.0
+        for it in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            n = ops.probe_fp64(kind, blocks, 2048, out, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(a.elapsed_time(b))
+        res[name] = n / (min(times) / 1e3) / 1e9
+    return res
+
+
+HEADLINE_MAX_BYTES = 3072
+
+
+def _r(x, nd=4):
+    if isinstance(x, float):
+        return float(f"{x:.{nd}g}")
+    return x
+
+
+def _clip(x, n=240):
+    return x[:n] if isinstance(x, str) else x
+
+
+def write_details(full):
+    """Everything the run measured, as one JSON file in BENCH_DETAILS_DIR (default:
+    the system temp directory); returns its path."""
+    base = os.environ.get("BENCH_DETAILS_DIR") or tempfile.gettempdir()
+    try:
+        os.makedirs(base, exist_ok=True)
+        path = os.path.join(base, f"bench_details_{os.getpid()}.json")
+        with open(path, "w") as f:
+            json.dump(full, f, indent=1)
+        return path
+    except OSError:
+        return None
+
+
+def headline(full, details_path=None):
+    """The one line rank 0 prints: the keys a reader of the run needs (metric,
+    value, timing, config, roofline, CPU baseline, end-to-end, clocks, and the
+    FP64-vs-mixed figures), a few KB at most; everything else stays in the
+    details file."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "gpu_launches")
+    line = {k: full.get(k) for k in keep}
+    cfg = full.get("config") or {}
+    line["config"] = {k: cfg[k] for k in ("workload", "n_intervals", "l_max", "tol", "v_cycles_per_solve",
+                                           "l2", "parallelism") if k in cfg}
+    if isinstance(line["config"].get("workload"), str):
+        line["config"]["workload"] = line["config"]["workload"][:400]
+    t = full.get("time_to_1e-10_ms") or {}
+    line["time_to_1e-10_ms"] = {k: _r(v) for k, v in t.items()}
+    mixed = {}
+    for prec, m in (full.get("mixed") or {}).items():
+        mixed[prec] = {k: _r(m.get(k)) for k in ("time_to_1e-10_ms", "speedup_vs_fp64", "inner_cycles",
+                                                  "ir_steps", "max_rel_diff_vs_fp64_gpu", "converged")}
+    line["mixed"] = mixed
+    roof = full.get("roofline") or {}
+    line["roofline"] = {k: _r(v) for k, v in roof.items()
+                        if k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic",
+                                 "hbm_achieved_gbs", "hbm_peak_gbs", "hbm_frac", "hbm_frac_3S",
+                                 "algorithmic_bytes_per_launch", "algorithmic_bytes_3S", "avg_launch_ms",
+                                 "fp64_dadd_peak", "peak_source")}
+    cpu = full.get("cpu_baseline")
+    line["cpu_baseline"] = None if cpu is None else {k: _clip(_r(v)) for k, v in cpu.items()}
+    e2e = full.get("e2e") or {}
+    line["e2e"] = {k: _clip(_r(v)) for k, v in e2e.items()}
+    clk = full.get("clocks")
+    line["clocks"] = clk
+    b = full.get("batched") or {}
+    if b:
+        line["batched"] = {k: _r(b[k]) for k in ("plain_fp64_solves_per_s", "batched_mixed_fp32_solves_per_s",
+                                                  "hybrid_mixed_fp32_solves_per_s", "mixed_batched_vs_plain_fp64",
+                                                  "mixed_hybrid_vs_plain_fp64") if k in b}
+    line["details"] = details_path if details_path is None or len(details_path) < 200 else None
+    text = json.dumps(line)
+    for drop in ("batched", "mixed", "details"):
+        if len(text) <= HEADLINE_MAX_BYTES:
+            break
+        line.pop(drop, None)
+        text = json.dumps(line)
+    return line
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -760,14 +945,22 @@ def main():
     avg_s = dom["avg_ms"] / 1e3
     gbs = dom["bytes_per_launch"] / avg_s / 1e9
     gops = dom["ops_per_launch"] / avg_s / 1e9
+    fp64_rate = fp64_peak(dev)
     if dom["fp64"]:
-        roof = {"bound": "alu", "kernel": dom_name, "achieved": gops, "peak": FP64_PIPE_PEAK_GOPS,
-                "unit": "Gop/s (FP64 pipe instructions, FMA = 1)", "frac": gops / FP64_PIPE_PEAK_GOPS,
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": gops, "peak": fp64_rate["dfma"],
+                "unit": "G FP64 instr/s (FMA = 1)", "frac": gops / fp64_rate["dfma"],
                 "traffic": traffic, "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
                 "hbm_frac": gbs / peaks["hbm_gbs"],
                 "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
                 "ops_per_launch": dom["ops_per_launch"], "avg_launch_ms": dom["avg_ms"],
-                "peak_source": "nominal FP64 rate 1.25 TFLOP/s / 2 (FMA); hbm peak " + peak_src}
+                "fp64_dadd_peak": fp64_rate["dadd"],
+                "peak_source": "measured in this run: ps_probe_fp64 (DFMA chains, CUDA events); hbm " + peak_src}
+        if dom_name == "sweep_colour_finest":
+            # the survey's count: 3S per unknown per full red-black sweep, i.e. 12 B
+            # per unknown per colour pass (FP64)
+            sb = unknowns * 3 * 8 / 2
+            roof["hbm_frac_3S"] = sb / avg_s / 1e9 / peaks["hbm_gbs"]
+            roof["algorithmic_bytes_3S"] = sb
     else:
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": gbs, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": traffic,
@@ -797,7 +990,7 @@ def main():
     if rank == 0:
         sorted_ms = sorted(step_ms)
         p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
-        line = {
+        full = {
             "metric": "GLUPS (fine-grid unknown updates/s over the whole solve) + time-to-1e-10",
             "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -816,6 +1009,7 @@ def main():
             "batched": batched,
             "compact_mg_table4": compact,
             "roofline": roof,
+            "fp64_pipe_gops": fp64_rate,
             "kernels": kernels,
             "profiled_region_ms_per_step": prof_region_ms,
             "cpu_baseline": cpu,
@@ -826,6 +1020,9 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
         }
+        path = write_details(full)
+        line = headline(full, path)
+        log("bench details:", json.dumps(full))
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

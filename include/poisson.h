@@ -347,16 +347,20 @@ ps_status ps_op_residual(const ps_grid* grid, int stencil_order, int dtype, cons
  * allocate device memory -- code whose device memory is owned by an external
  * pool or arena, latency-critical loops where an allocation may stall or
  * fail, hosts with a no-allocation policy.  It computes the same r = f - A phi
- * on interior nodes and ||r||_2^2 (into *norm2_host unless NULL, which
- * synchronises the stream) but calls no cudaMalloc/cudaFree: its scratch
+ * on interior nodes and ||r||_2^2 but calls no cudaMalloc/cudaFree: its scratch
  * (per-block partial sums) is one fixed 256 KB array in device global memory
- * that every device loading the library keeps until exit.
+ * that every device loading the library keeps until exit.  When norm2_host is
+ * non-NULL, ||r||^2 is copied back and the stream is synchronised; with NULL
+ * the call is asynchronous and ||r||^2 stays only in the shared scratch.
  *   - Grids whose launch needs more than 32768 thread blocks (beyond about
  *     512^3 intervals) are rejected with PS_ERR_INVALID_ARG before GPU work.
  *   - All calls on a device share that array: calls whose kernels can
  *     overlap on the GPU race on it and must be serialised by the caller.
  *   - The first call on each device looks up the array's device address with
- *     that device current; make it before any stream capture. */
+ *     that device current; make it before any stream capture.  The address is
+ *     kept for the life of the process: after cudaDeviceReset (or any other
+ *     teardown of the device's primary context) it is stale, so do not call
+ *     this entry point on that device again in the same process. */
 ps_status ps_op_residual_noalloc(const ps_grid* grid, int stencil_order, const double* phi_dev,
                                  const double* f_dev, double* r_dev, double* norm2_host,
                                  void* stream);
@@ -400,6 +404,20 @@ ps_status ps_op_multipole_boundary(const ps_grid* grid, int stencil_order, const
  * inner mirror ghost and periodic phi (ghost slots of phi are read, not
  * written).  Uses the coordinates of handle h (spherical). */
 ps_status ps_op_spherical_apply(ps_handle h, const double* phi_dev, double* out_dev, void* stream);
+
+/* ------------------------------------------------------------------ measurement support
+ * FP64 pipe throughput probe (no paper counterpart: it supplies the measured
+ * peak against which the FP64-bound kernels' rooflines are stated).  Launches
+ * `blocks` blocks of 256 threads; each thread runs 8 independent chains of
+ * `iters` FP64 instructions -- fused multiply-adds for kind 0, adds for kind 1
+ * -- and each block writes one double to out_dev[block] (device array of
+ * `blocks` doubles owned by the caller).  *instructions_host (may be NULL)
+ * receives the number of FP64 instructions the launch issues (warp lanes
+ * counted one by one); the caller times the launch on `stream`.
+ * Errors: PS_ERR_INVALID_ARG for kind not 0/1, blocks outside 1..2^20, iters
+ * outside 1..2^24 or a NULL out_dev; PS_ERR_CUDA if the launch fails. */
+ps_status ps_probe_fp64(int kind, int blocks, int iters, double* out_dev, double* instructions_host,
+                        void* stream);
 
 #ifdef __cplusplus
 }

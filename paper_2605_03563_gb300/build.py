@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpoisson.so")
 SOURCES = ["cart_kernels.cu", "tiled_kernels.cu", "batch.cu", "compact.cu", "multipole.cu", "spherical.cu",
-           "solver.cu", "noalloc.cu"]
+           "solver.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

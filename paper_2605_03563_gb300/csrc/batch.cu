@@ -16,7 +16,8 @@
 namespace ps {
 
 static constexpr int BBX = 32, BBY = 8;
-static constexpr int kBGrid = 8 * 152;   // blocks of a tile phase launch (grid-stride)
+// blocks of a tile phase launch (grid-stride): 8 per SM
+static int bgrid() { return 8 * device_sm_count(); }
 
 int batch_zchunk(const Dims& d) {
   const int nk = d.nk();
@@ -470,35 +471,35 @@ static const dim3 kTile(BBX, BBY);
 
 cudaError_t launch_b_sweep(const BArgs& a, int order, int dt, int list, int colour, cudaStream_t s) {
   if (order == 2) {
-    if (dt == DT_F64) kb_sweep<1, double><<<kBGrid, kTile, 0, s>>>(a, list, colour);
-    else kb_sweep<1, float><<<kBGrid, kTile, 0, s>>>(a, list, colour);
+    if (dt == DT_F64) kb_sweep<1, double><<<bgrid(), kTile, 0, s>>>(a, list, colour);
+    else kb_sweep<1, float><<<bgrid(), kTile, 0, s>>>(a, list, colour);
   } else {
-    if (dt == DT_F64) kb_sweep<2, double><<<kBGrid, kTile, 0, s>>>(a, list, colour);
-    else kb_sweep<2, float><<<kBGrid, kTile, 0, s>>>(a, list, colour);
+    if (dt == DT_F64) kb_sweep<2, double><<<bgrid(), kTile, 0, s>>>(a, list, colour);
+    else kb_sweep<2, float><<<bgrid(), kTile, 0, s>>>(a, list, colour);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_delta_skip(const BArgs& a, int order, int dt, int list, cudaStream_t s) {
   if (order == 2) {
-    if (dt == DT_F64) kb_delta_skip<1, double><<<kBGrid, kTile, 0, s>>>(a, list);
-    else kb_delta_skip<1, float><<<kBGrid, kTile, 0, s>>>(a, list);
+    if (dt == DT_F64) kb_delta_skip<1, double><<<bgrid(), kTile, 0, s>>>(a, list);
+    else kb_delta_skip<1, float><<<bgrid(), kTile, 0, s>>>(a, list);
   } else {
-    if (dt == DT_F64) kb_delta_skip<2, double><<<kBGrid, kTile, 0, s>>>(a, list);
-    else kb_delta_skip<2, float><<<kBGrid, kTile, 0, s>>>(a, list);
+    if (dt == DT_F64) kb_delta_skip<2, double><<<bgrid(), kTile, 0, s>>>(a, list);
+    else kb_delta_skip<2, float><<<bgrid(), kTile, 0, s>>>(a, list);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_restrict(const BArgs& a, int dt, int list, cudaStream_t s) {
-  if (dt == DT_F64) kb_restrict<double><<<kBGrid, kTile, 0, s>>>(a, list);
-  else kb_restrict<float><<<kBGrid, kTile, 0, s>>>(a, list);
+  if (dt == DT_F64) kb_restrict<double><<<bgrid(), kTile, 0, s>>>(a, list);
+  else kb_restrict<float><<<bgrid(), kTile, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_prolong(const BArgs& a, int dt, int list, cudaStream_t s) {
-  if (dt == DT_F64) kb_prolong<double><<<kBGrid, kTile, 0, s>>>(a, list);
-  else kb_prolong<float><<<kBGrid, kTile, 0, s>>>(a, list);
+  if (dt == DT_F64) kb_prolong<double><<<bgrid(), kTile, 0, s>>>(a, list);
+  else kb_prolong<float><<<bgrid(), kTile, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 
@@ -524,8 +525,8 @@ cudaError_t launch_b_coarse(const BArgs& a, int order, int dt, int list, int max
 }
 
 cudaError_t launch_b_norm(const BArgs& a, int order, int list, cudaStream_t s) {
-  if (order == 2) kb_norm<1><<<kBGrid, kTile, 0, s>>>(a, list);
-  else kb_norm<2><<<kBGrid, kTile, 0, s>>>(a, list);
+  if (order == 2) kb_norm<1><<<bgrid(), kTile, 0, s>>>(a, list);
+  else kb_norm<2><<<bgrid(), kTile, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 
@@ -535,19 +536,19 @@ cudaError_t launch_b_finish(const BArgs& a, int list, int max_blocks, cudaStream
 }
 
 cudaError_t launch_b_zero(const BArgs& a, int dt, int list, cudaStream_t s) {
-  if (dt == DT_F64) kb_zero<double><<<kBGrid, kTile, 0, s>>>(a, list);
-  else kb_zero<float><<<kBGrid, kTile, 0, s>>>(a, list);
+  if (dt == DT_F64) kb_zero<double><<<bgrid(), kTile, 0, s>>>(a, list);
+  else kb_zero<float><<<bgrid(), kTile, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_correct(const BArgs& a, int list, cudaStream_t s) {
-  kb_correct<<<kBGrid, kTile, 0, s>>>(a, list);
+  kb_correct<<<bgrid(), kTile, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_delta_ir(const BArgs& a, int order, int list, cudaStream_t s) {
-  if (order == 2) kb_delta_ir<1><<<kBGrid, kTile, 0, s>>>(a, list);
-  else kb_delta_ir<2><<<kBGrid, kTile, 0, s>>>(a, list);
+  if (order == 2) kb_delta_ir<1><<<bgrid(), kTile, 0, s>>>(a, list);
+  else kb_delta_ir<2><<<bgrid(), kTile, 0, s>>>(a, list);
   return cudaGetLastError();
 }
 

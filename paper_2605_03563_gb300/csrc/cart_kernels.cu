@@ -13,7 +13,7 @@
 // Launch geometry of the point kernels: 32 x 8 threads per block over (x, y)
 // and a z-chunk of nodes per thread chosen per level (zchunk_for): deep chunks
 // on the large finest levels, one node per thread on small levels so that the
-// launch still fills the 152 SMs instead of serialising memory latency along z.
+// launch still fills every SM instead of serialising memory latency along z.
 // Kernels recover the chunk from gridDim.z.
 #include <algorithm>
 #include <cstdio>
@@ -24,10 +24,9 @@
 namespace ps {
 
 static constexpr int BX = 32, BY = 8, ZCH = 16;
-static constexpr int kTargetBlocks = 8 * 152;
-
 static inline int zchunk_for(int gxy, int nk) {
-  long long z = (long long)gxy * nk / kTargetBlocks;
+  // about 8 blocks per SM
+  long long z = (long long)gxy * nk / (8LL * device_sm_count());
   return (int)std::max(1LL, std::min((long long)ZCH, z));
 }
 
@@ -824,7 +823,7 @@ __global__ void k_pow2_to_f32(const double* __restrict__ x, long long n, int e, 
 cudaError_t launch_pow2_to_f32(const double* x, long long n, int e, float* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const long long want = (n + 255) / 256;
-  const int blocks = (int)std::min<long long>(want, 8LL * 152);
+  const int blocks = (int)std::min<long long>(want, 8LL * device_sm_count());
   k_pow2_to_f32<<<blocks, 256, 0, s>>>(x, n, e, out);
   return cudaGetLastError();
 }

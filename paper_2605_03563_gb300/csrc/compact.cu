@@ -384,8 +384,6 @@ cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const dou
   return cudaGetLastError();
 }
 
-static int g_sms = 0;
-
 
 // ------------------------------------------------------------------ fused FP32 smoothing step
 // One SPAI step u' = u - omega M (b - A u) of an inner FP32 level in a single
@@ -613,15 +611,10 @@ static cudaError_t launch_march(const Dims& d, const W27& A, const W27& M, doubl
   CUtensorMap mu, mb;
   if (!encode_level_map(&mu, DT_F32, u, d, GBW, GUH)) return cudaErrorInvalidValue;
   if (!encode_level_map(&mb, DT_F32, b, d, GBW, GBH)) return cudaErrorInvalidValue;
-  if (g_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 152;
-  }
+  const int sms = device_sm_count();
   const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + GTY - 1) / GTY, nk = d.nk();
   // about two to three waves of 5 blocks per SM, z-chunks of at least 16 planes (4 extra staged planes each)
-  const int want = std::max(1, 12 * g_sms / (gx * gy));
+  const int want = std::max(1, 12 * sms / (gx * gy));
   const int zc = std::max(16, (nk + want - 1) / want);
   const dim3 grid(gx, gy, (nk + zc - 1) / zc);
   k_c27_smooth<RESID><<<grid, 32 * GW, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st,

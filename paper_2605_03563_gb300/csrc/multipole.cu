@@ -359,10 +359,10 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ host launchers
-// z-chunks of pass 1: enough columns x chunks for about 152 x 1024 threads
+// z-chunks of pass 1: enough columns x chunks for about 1024 threads per SM
 static int mp_chunks(const Dims& d) {
   const long long cols = (long long)d.ni() * d.nj();
-  long long nc = (152LL * 1024 + cols - 1) / cols;
+  long long nc = (device_sm_count() * 1024LL + cols - 1) / cols;
   nc = std::max(nc, (long long)((d.nk() + MP_KC_MAX - 1) / MP_KC_MAX));
   return (int)std::max(1LL, std::min(nc, (long long)d.nk()));
 }

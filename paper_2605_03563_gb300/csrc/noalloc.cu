@@ -22,7 +22,10 @@
 //    has to be cleared between calls;
 //  * the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//    before any stream capture.  The address is cached for the life of the
+//    process, so it goes stale if the device's primary context is torn down
+//    (cudaDeviceReset): the entry point must not be called on that device
+//    again afterwards.
 #include <mutex>
 
 #include "cart_kernels.cuh"

@@ -233,4 +233,7 @@ enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3, DON
 
 namespace ps {
 void set_error(const char* fmt, ...);
+// Streaming multiprocessors of the current device (queried once per device and
+// cached); launch geometries scale with it.
+int device_sm_count();
 }

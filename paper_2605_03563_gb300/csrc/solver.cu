@@ -11,6 +11,7 @@
 // Convergence is decided on the device; the host reads the small state once per
 // V-cycle / refinement step, or once per chunk of Krylov/SOR iterations (the
 // kernels of an iteration body skip their work once the state says done).
+#include <atomic>
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -41,6 +42,18 @@ void set_error(const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_err = buf;
+}
+
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
 }
 
 static size_t dt_size(int dt) { return dt == DT_F64 ? 8 : dt == DT_F32 ? 4 : 2; }

@@ -62,16 +62,7 @@ bool encode_level_map(CUtensorMap* map, int dt, const void* base, const Dims& d,
   return r == CUDA_SUCCESS;
 }
 
-static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
+static int sm_count() { return device_sm_count(); }
 
 static constexpr int NT = 256;   // threads per block of both tile kernels
 

@@ -99,3 +99,17 @@ def compact_operators(order, h, nlevels):
           "poisson_compact_operators")
     return ([list(a[4 * l:4 * l + 4]) for l in range(nlevels)],
             [list(m[4 * l:4 * l + 4]) for l in range(nlevels)], list(w))
+
+
+def probe_fp64(kind, blocks, iters, out, stream=None):
+    """Launch the FP64 pipe throughput probe (kind 0: fused multiply-adds, 1:
+    adds) on `stream`; out is a float64 CUDA tensor of at least `blocks`
+    elements.  Returns the number of FP64 instructions the launch issues; the
+    caller times it."""
+    import torch
+    if out.dtype != torch.float64 or out.numel() < blocks:
+        raise ValueError("out must be float64 with at least `blocks` elements")
+    n = C.c_double()
+    check(lib().ps_probe_fp64(int(kind), int(blocks), int(iters), _p(out), C.byref(n), _s(stream)),
+          "ps_probe_fp64")
+    return n.value

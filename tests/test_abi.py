@@ -22,7 +22,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(poisson_\w+|ps_op_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(poisson_\w+|ps_op_\w+|ps_probe_\w+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported_and_bound(lib):

@@ -67,3 +67,18 @@ def test_noalloc_rejects_grids_beyond_its_scratch(capi):
     st = lib.ps_op_residual_noalloc(C.byref(g), 2, p, p, p, None, None)
     assert st == capi.PS_ERR_INVALID_ARG
     assert b"reduction slots" in lib.poisson_last_error()
+
+
+def test_noalloc_at_the_edge_of_its_scratch(capi):
+    # (2, 2048, 2048) intervals at order 2 launch exactly 1 x 256 x 128 = 32768
+    # blocks, every reduction slot of the fixed scratch: accepted, and equal to
+    # the allocating entry point
+    _call_both(capi, (2, 2048, 2048), 2, (1.0, 1.0, 1.0), 3)
+    # one more z-chunk of blocks (1 x 256 x 129 = 33024) is rejected before any GPU work
+    lib = capi.lib()
+    g = capi.make_grid((2, 2048, 2050))
+    dummy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p = C.c_void_p(dummy.data_ptr())
+    st = lib.ps_op_residual_noalloc(C.byref(g), 2, p, p, p, None, None)
+    assert st == capi.PS_ERR_INVALID_ARG
+    assert b"33024 reduction slots" in lib.poisson_last_error()
