@@ -523,6 +523,59 @@ def test_bicgstab_restarts_through_an_exact_breakdown():
     np.testing.assert_allclose(res.x, np.linalg.solve(A, b), rtol=0, atol=1e-12)
 
 
+def _textbook_right_jacobi_bicgstab(K, inv, b, k):
+    """k passes of van der Vorst's BiCGSTAB (Saad, Iterative Methods, Alg. 7.7)
+    applied to the right-preconditioned system K u = b with K = A diag(inv),
+    x = diag(inv) u, written from the textbook with the dense product K formed
+    explicitly.  Returns x_k and the recursive residual norms ||r_0..r_k||."""
+    u = np.zeros_like(b)
+    r = b.copy()
+    r0s = r.copy()
+    p = r.copy()
+    norms = [float(np.sqrt(r @ r))]
+    for _ in range(k):
+        Kp = K @ p
+        a = (r @ r0s) / (Kp @ r0s)
+        s = r - a * Kp
+        Ks = K @ s
+        w = (Ks @ s) / (Ks @ Ks)
+        u = u + a * p + w * s
+        r_new = s - w * Ks
+        beta = ((r_new @ r0s) / (r @ r0s)) * (a / w)
+        p = r_new + beta * (p - w * Kp)
+        r = r_new
+        norms.append(float(np.sqrt(r @ r)))
+    return inv * u, norms
+
+
+def test_bicgstab_without_replacement_is_the_textbook_iteration():
+    """With residual replacement switched off (it fires only when the budget
+    ends) the oracle's BiCGSTAB is van der Vorst's method: on a small
+    non-symmetric, diagonally graded system its iterate after k passes and its
+    recursive residual norms equal a textbook transcription of Saad's Alg. 7.7
+    for K = A diag(A)^-1, pass for pass.  A wrong alpha, omega or beta (sign,
+    index, operand) changes the iterates at the first or second pass."""
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = 40
+    A = rng.standard_normal((n, n)) * 0.35
+    A += np.diag(rng.uniform(2.0, 12.0, n))
+    assert np.max(np.abs(A - A.T)) > 0.1
+    b = rng.standard_normal(n)
+    inv = 1.0 / np.diag(A)
+    K = A * inv[None, :]
+    ref = float(np.linalg.norm(b))
+    for k in range(1, 13):
+        res = krylov.bicgstab(lambda v: A @ v, inv, b, np.zeros(n), 1e-30, k, ref, replace=0.0)
+        xk, norms = _textbook_right_jacobi_bicgstab(K, inv, b, k)
+        np.testing.assert_allclose(res.x, xk, rtol=0, atol=1e-11 * np.max(np.abs(xk)))
+        # recursive norms of passes 1..k-1 (the last entry is the replaced, true residual)
+        np.testing.assert_allclose(np.array(res.history[:k]) * ref, norms[:k], rtol=1e-9)
+        true = float(np.linalg.norm(b - A @ xk))
+        assert res.history[k] * ref == pytest.approx(true, rel=1e-6, abs=1e-13)
+    # the iteration really converges on this system (the comparison is not of noise)
+    assert norms[-1] < 1e-6 * norms[0]
+
+
 def test_bicgstab_stops_on_the_true_residual():
     """On the graded log-r grid (48x24x48, r_in = 0.01) the recursively updated
     BiCGSTAB residual drifts from b - A x: stopping on it leaves a true
