@@ -158,7 +158,7 @@ def test_spherical_padded_grid_multipole_boundaries(pkg):
     """Sec. 2.2's zero padding: density only on the active logarithmic range,
     extensions inward (polynomial, to r_in/2) and outward (logarithmic), both
     expansions written at the extended ends; BiCGSTAB against the oracle."""
-    from paper_2605_03563_gb300.radial import padded_log_radii
+    from workloads import padded_log_radii
     r, active = padded_log_radii(0.1, 1.0, 24, n_pad_in=6, n_pad_out=6)
     th = (np.arange(8) + 0.5) * np.pi / 8
     ph = 2 * np.pi * np.arange(16) / 16

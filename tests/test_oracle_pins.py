@@ -469,6 +469,34 @@ def test_spherical_radial_closed_form_second_order():
     assert 3.5 < errs[0] / errs[1] < 4.6 and 3.5 < errs[1] / errs[2] < 4.6, errs
 
 
+def test_fp64_residual_floor_of_the_spherical_workload():
+    """Why the 256 x 128 x 256 spherical workload stops at relative residual
+    1e-8 and not 1e-10: no FP64 potential can have a much smaller residual.
+    Storing the exact discrete solution x* in FP64 perturbs every unknown by
+    its rounding error, |d_i| <= ulp(x_i)/2, and the residual of fl(x*) is
+    then exactly -A d.  The pole and inner-radius coefficients of the
+    spherical operator reach 1e11, so ||A d|| / ||b|| is about 5e-10 for
+    rounding errors of that size (measured here with d uniform in
+    +-ulp(x_i)/2 about the Gauss's-law potential of the r^-2 density, whose
+    magnitude the angular factors change by under 20%): a floor 5 times above
+    1e-10 and a fifth of 1e-8."""
+    r, th, ph = W.spherical_coords(256, 128, 256, 0.01, 1.0)
+    op = SP.SphericalOperator(r, th, ph)
+    rho = W.spherical_density(r, th, ph)
+    f = 4 * math.pi * rho
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    q = MP.moments_spherical(rho, r, th, ph, 6)
+    bd = np.zeros(op.shape)
+    bd[1:-1, 1:-1, -1] = MP.spherical_outer_ghost(q, r, th, ph, 6, 1.0)
+    ref = float(np.linalg.norm(f[U] - op.apply(bd)))
+    x = np.broadcast_to(_sph_exact(r, r[0], r[-1])[None, None, :], op.apply(bd).shape)
+    rng = np.random.Generator(np.random.PCG64(11))
+    d = np.zeros(op.shape)
+    d[U] = np.spacing(x) * rng.uniform(-0.5, 0.5, x.shape)
+    floor = float(np.linalg.norm(op.apply(d))) / ref
+    assert 2e-10 < floor < 2e-9, floor
+
+
 def test_spherical_operator_annihilates_harmonics():
     """x^2 - y^2 and 2z^2 - x^2 - y^2 are harmonic: the truncation error of the
     discrete operator on them falls as h^2."""

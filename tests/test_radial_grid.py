@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from paper_2605_03563_gb300.radial import padded_log_radii
+from workloads import padded_log_radii
 
 
 def test_padded_grid_structure_and_smooth_join():
