@@ -914,6 +914,51 @@ def test_mg_spai_convergence_factor_matches_table2():
         assert rhos[1] < rhos[0]
 
 
+def test_sixth_order_mg_cycles_match_table4_and_do_not_depend_on_depth():
+    """Table 4's method (sixth-order compact stencil, SPAI V(nu,nu), Galerkin
+    coarse operators, multipole l_max 4) on the two-sphere problem of Sec. 3.1
+    at 63^3 unknowns, cold start to residual reduction 1e-6: the V-cycle counts
+    lie within 2 of the printed ones (7, 4, 3 for nu = 1, 2, 3 on DGX and LUMI;
+    nano5 prints 4 for nu = 3).  Table 2 quotes its factors for "seven coarse
+    levels" (511^3 down to a 3^3 coarsest grid); coarsening to 3^3 instead of
+    7^3 unknowns changes nothing here: the coarsest level is solved to
+    relative accuracy 1e-2, well below the factor of one cycle."""
+    import dataclasses
+    from oracle import multigrid as MG
+    n = 64
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    g = cart_grid(n, 2, lo, hi)
+    rho = W.smooth_sphere_density(n, 2, [(0.0, 0.0, 0.4), (0.0, 0.0, -0.2)], [0.08, 0.08], [1.0, 2.0])
+    phi_b = g.zeros()
+    q = MP.moments_cartesian(rho, g, (0.0, 0.0, 0.0), 4)
+    MP.apply_cartesian_bc(phi_b, g, q, (0.0, 0.0, 0.0), 4, 1.0)
+    f = 4 * math.pi * rho
+    printed = {1: 7, 2: 4, 3: 3}
+    rhos = {}
+    for nu, cyc in printed.items():
+        phi = phi_b.copy()
+        it, conv, hist = CP.mg_solve(phi, f, g, 6, 1e-6, 40, nu, nu)
+        assert conv and abs(it - cyc) <= 2, (nu, it, cyc)
+        rhos[nu] = MG.convergence_factor(hist)
+    assert rhos[1] > rhos[2] > rhos[3]
+
+    def deeper(grid):
+        levels = [grid]
+        while all(v % 2 == 0 and v >= 8 for v in levels[-1].n):
+            levels.append(dataclasses.replace(levels[-1], n=tuple(v // 2 for v in levels[-1].n)))
+        return levels
+    assert [L.n[0] for L in deeper(g)] == [64, 32, 16, 8, 4]
+    orig = CP.hierarchy
+    CP.hierarchy = deeper
+    try:
+        phi = phi_b.copy()
+        it, conv, hist = CP.mg_solve(phi, f, g, 6, 1e-6, 40, 2, 2)
+    finally:
+        CP.hierarchy = orig
+    assert conv
+    assert abs(MG.convergence_factor(hist) - rhos[2]) <= 0.01 * rhos[2]
+
+
 def test_compact_mg_matches_dense_solve():
     """16^3, zero boundary, random rho: the SPAI multigrid solution of the
     compact 6th-order system equals numpy.linalg.solve on the dense 27-point
