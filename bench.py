@@ -250,6 +250,70 @@ def cpu_baseline_sample():
                       f"numpy processes at once ({tp:.1f} s); alone on one core {t1:.1f} s"}
 
 
+# ------------------------------------------------------------------ spherical workload (config 4)
+def run_spherical(args, rank, world):
+    """256 x 128 x 256 spherical grid (r log-spaced 0.01..1, theta cell-centred,
+    phi periodic), rho = r^-2 (1 + 0.1 cos 2 phi)(1 + 0.2 cos^2 theta), multipole
+    outer boundary l_max = 6, Neumann inner boundary.  One step = one cold-start
+    solve to relative residual --sph-tol (1e-8: the FP64 rounding floor of this
+    grid is about 5e-10) or --max-iter iterations: right-Jacobi BiCGSTAB in
+    FP64 (--prec fp64) or FP64 refinement around FP32 BiCGSTAB (--prec
+    mixed_fp32), or red-black SOR with the local Chebyshev weights (--workload
+    sph_sor).  --plain-graphs runs the solves with kernel timing on, whose plain
+    graphs (no conditional nodes) a profiler can see into."""
+    import torch
+    import workloads as W
+    import paper_2605_03563_gb300 as P
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    r, th, ph = W.spherical_coords(256, 128, 256, 0.01, 1.0)
+    rho = torch.from_numpy(W.spherical_density(r, th, ph)).to(dev)
+    phi = torch.zeros_like(rho)
+    sor = args.workload == "sph_sor"
+    kw = dict(tol=args.sph_tol, max_iter=args.max_iter or 60000)
+    if sor:
+        kw.update(method="sor", sor_schedule="chebyshev")
+    else:
+        kw.update(prec=args.prec)
+    stream = torch.cuda.current_stream()
+    with P.SphericalSolver(r, th, ph, bc="multipole", lmax=6) as s:
+        if args.plain_graphs:
+            s.profile(True)
+        for _ in range(args.warmup):
+            s.solve(rho, phi.zero_(), **kw)
+        clocks = ClockSampler()
+        clocks.start()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        infos = []
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for k in range(args.steps):
+            infos.append(s.solve(rho, phi.zero_(), **kw))
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        prof = s.profile_read() if args.plain_graphs else {}
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    its = sum(i.iterations for i in infos)
+    nunk = 256 * 128 * 256
+    line = {"metric": "time-to-tolerance (spherical BiCGSTAB / SOR, config 4)",
+            "value": total_ms / args.steps, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+            "dtype": "f64" if (sor or args.prec == "fp64") else "f32+f64", "data": "synthetic",
+            "config": {"workload": "256x128x256 spherical, l_max 6, " + ("red-black SOR (local Chebyshev)" if sor
+                                                                         else "Jacobi-BiCGSTAB " + args.prec),
+                       "tol": args.sph_tol, "max_iter": kw["max_iter"], "plain_graphs": bool(args.plain_graphs)},
+            "iterations": infos[-1].iterations, "rel_residual": infos[-1].rel_residual,
+            "converged": infos[-1].converged, "ms_per_iteration": total_ms / max(its, 1),
+            "glups_per_iteration": nunk * its / (total_ms / 1e3) / 1e9,
+            "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 5)} for k, v in prof.items()},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ serving stream
 def run_serving(args, rank, world):
     """2000 Cartesian solve requests (Poisson arrivals, mean 200/s, cubes 32..256,
@@ -714,7 +778,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mg256", choices=["mg256", "serving"])
+    ap.add_argument("--workload", default="mg256", choices=["mg256", "serving", "sph", "sph_sor"])
+    ap.add_argument("--sph-tol", type=float, default=1e-8, help="spherical workloads: relative residual")
+    ap.add_argument("--max-iter", type=int, default=0, help="spherical workloads: iteration cap (0 = 60000)")
+    ap.add_argument("--plain-graphs", action="store_true",
+                    help="spherical workloads: solve with kernel timing on (plain graphs a profiler can see into)")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed_fp32", "mixed_bf16"])
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--max-active", type=int, default=64)
@@ -746,6 +814,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serving":
         return run_serving(args, rank, world)
+    if args.workload in ("sph", "sph_sor"):
+        return run_spherical(args, rank, world)
 
     import numpy as np
     import torch

@@ -98,10 +98,11 @@ typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3, PS_PCG = 4 } p
 /* PS_FP64: every kernel computes and stores in FP64.
  * PS_MIXED_FP32: Cartesian: FP64 iterative refinement (outer residual,
  *   correction, norms, multipole moments and coarsest solve in FP64) around
- *   FP32 inner V-cycles.  Spherical: BiCGSTAB with FP32 Krylov vectors and the
- *   iterate, right-hand side, true residuals and dot products in FP64.  Its
- *   convergence needs cond(A B^-1) * 2^-24 well below 1, which strongly graded
- *   grids violate; it then ends with PS_NOT_CONVERGED.
+ *   FP32 inner V-cycles.  Spherical: FP64 iterative refinement around inner
+ *   BiCGSTAB solves with FP32 Krylov vectors (iterate, right-hand side, true
+ *   residuals and dot products in FP64): each inner solve starts a new Krylov
+ *   process from the FP64 true residual and runs until its recursive residual
+ *   has dropped 2^-k-fold, k = inner_cycles (0 = 4).
  * PS_MIXED_BF16: as PS_MIXED_FP32, with the finest inner level stored in BF16
  *   (Cartesian; spherical treats it as PS_MIXED_FP32).
  * Spherical BiCGSTAB in either precision stops on the true residual b - A x,
@@ -115,7 +116,8 @@ typedef struct {
   double omega;          /* SOR weight (Sec. 2.1.1); MG smoothing uses 1 */
   int32_t nu1, nu2;      /* V(nu1,nu2) pre-/post-smoothing sweeps */
   int32_t max_iter;      /* SOR steps / CG or BiCGSTAB iterations / V-cycles / IR steps */
-  int32_t inner_cycles;  /* Cartesian mixed modes: inner V-cycles per IR step (spherical: unused) */
+  int32_t inner_cycles;  /* Cartesian mixed modes: inner V-cycles per IR step; spherical
+                            PS_MIXED_FP32: the inner solve's reduction 2^-inner_cycles (0 = 4) */
   void* stream;          /* cudaStream_t; NULL = CUDA's default stream */
   int32_t tile_min_n;    /* Cartesian MG, mixed modes: FP32/BF16 inner levels (other than the
                             coarsest) with at least this many intervals on every axis run the
@@ -134,7 +136,9 @@ typedef struct {
                             PS_MIXED_FP32: FP64 refinement around FP32 inner V-cycles
                             (inner_cycles per step).  The relative residual is
                             ||R_h f - L_h phi|| / ||R_h f - L_h phi0||. */
-  int32_t reserved_;     /* set to 0 */
+  int32_t use_tuning;    /* Cartesian PS_MG: 1 = take nu1, nu2, inner_cycles, tile_min_n and the
+                            fused sweep's tile shape from the handle's tuning for this precision
+                            (poisson_set_tuning), when one is set; 0 = use the fields above */
 } ps_solve_opts;
 
 /* SOR weights (Sec. 2.1.1).  rJ is the Jacobi spectral radius estimate: Eq. 4
@@ -227,6 +231,33 @@ ps_status poisson_solve_batch(ps_handle* hs, const double* const* rho_dev, doubl
 /* Release the handle and everything it allocated (NULL is a no-op). */
 void poisson_destroy(ps_handle h);
 
+/* Tuned settings of a handle (no paper counterpart: the autotuner's output).
+ * For one precision of Cartesian multigrid solves they replace the solve
+ * options nu1, nu2 (V(nu1, nu2), Sec. 2.1.3), inner_cycles (inner V-cycles
+ * per refinement step), tile_min_n and the tile shape of the TMA-staged fused
+ * red-black sweep of FP32/BF16 levels whenever ps_solve_opts.use_tuning is 1:
+ *   sweep_tile 0 = the storage type's default, 1 = 4 rows per warp x 4 warps
+ *   (64 x 16 tile), 2 = 2 x 4 (64 x 8), 3 = 8 x 4 (64 x 32), 4 = 4 x 8 (64 x 32);
+ * every shape gives the same result bit for bit.  The autotuner times whole
+ * solves per (grid size, order, precision, tolerance) and a caller installs
+ * its choice here; solves without use_tuning are unaffected. */
+typedef struct {
+  int32_t nu1, nu2;        /* >= 0, nu1 + nu2 >= 1 */
+  int32_t inner_cycles;    /* >= 1 (mixed precisions) */
+  int32_t tile_min_n;      /* as ps_solve_opts.tile_min_n */
+  int32_t sweep_tile;      /* 0 .. 4 */
+  int32_t reserved_;       /* set to 0 */
+} ps_tuning;
+
+/* Install (t != NULL) or clear (t == NULL) the tuning of precision prec
+ * (ps_precision) on handle h.  Host only; PS_ERR_INVALID_ARG for a NULL or
+ * spherical handle, an unknown precision or out-of-range fields. */
+ps_status poisson_set_tuning(ps_handle h, int prec, const ps_tuning* t);
+
+/* *is_set = 1 and *out = the tuning of precision prec if one is installed,
+ * else *is_set = 0 (out untouched).  Host only. */
+ps_status poisson_get_tuning(ps_handle h, int prec, ps_tuning* out, int* is_set);
+
 /* Thread-local text of the last error (never NULL; "" when none). */
 const char* poisson_last_error(void);
 
@@ -314,7 +345,7 @@ typedef struct {
   double bytes_per_launch;   /* algorithmic bytes of one launch */
   double ops_per_launch;     /* arithmetic instructions of one launch (FMA = 1) */
   int32_t fp64;              /* 1 when the arithmetic runs on the FP64 pipe */
-  int32_t pad;
+  int32_t variant;           /* tile shape of the last timed launch (fused sweeps: 1..4), else 0 */
 } ps_kernel_stat;
 
 /* enable != 0 starts recording (events are created lazily; at most 16384
@@ -418,6 +449,19 @@ ps_status ps_op_spherical_apply(ps_handle h, const double* phi_dev, double* out_
  * outside 1..2^24 or a NULL out_dev; PS_ERR_CUDA if the launch fails. */
 ps_status ps_probe_fp64(int kind, int blocks, int iters, double* out_dev, double* instructions_host,
                         void* stream);
+
+/* Failure-detection check of the bounded device waits (no paper counterpart).
+ * The TMA tile kernels wait on mbarriers with a time limit read from the
+ * global timer: 2 s for a kernel's first failing wait, 1 ms for every wait
+ * after one has failed; a wait that runs out marks the kernel faulty and the
+ * solve ends with PS_ERR_TIMEOUT instead of hanging the GPU.  This call runs
+ * exactly that wait in one warp on an mbarrier that nothing ever arrives at
+ * (first_wait != 0: the 2 s limit; 0: the 1 ms limit), synchronises `stream`
+ * and returns PS_ERR_TIMEOUT with *waited_ms_host (may be NULL) = the time the
+ * wait took.  out_dev: caller-owned device scratch of 3 int64.  No copy is in
+ * flight and the context stays usable afterwards.  Errors: PS_ERR_INVALID_ARG
+ * for a NULL out_dev, PS_ERR_CUDA if the launch or copy fails. */
+ps_status ps_probe_bounded_wait(int first_wait, long long* out_dev, double* waited_ms_host, void* stream);
 
 #ifdef __cplusplus
 }

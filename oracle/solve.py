@@ -101,9 +101,11 @@ def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
                     max_iter: int = 20000, G: float = 1.0, bc: str = "multipole",
                     lmax: int = 6, exact_dots: bool = False, method: str = "bicgstab",
                     omega: float = 1.0, sor_schedule: str = "chebyshev",
-                    inner_bc: str = "neumann") -> SolveInfo:
+                    inner_bc: str = "neumann", dot=None) -> SolveInfo:
     """Right-Jacobi BiCGSTAB (or red-black SOR) on the spherical grid; phi in
-    the ghosted layout."""
+    the ghosted layout.  dot (BiCGSTAB): how inner products are summed, a
+    callable (a, b) -> float; default numpy's, or exactly rounded with
+    exact_dots."""
     op = SphericalOperator(r, th, ph, inner="dirichlet" if inner_bc == "multipole" else "neumann")
     f = 4.0 * math.pi * G * rho
     q = None
@@ -117,7 +119,8 @@ def solve_spherical(rho: np.ndarray, phi: np.ndarray, r, th, ph, tol: float,
         it, conv, hist = sor_solve_spherical(phi, f, op, tol, max_iter, sor_schedule, omega)
         return SolveInfo(it, conv, hist[-1], multigrid.convergence_factor(hist), hist, q)
     from . import krylov
-    res = bicgstab_solve(phi, f, op, tol, max_iter,
-                         dot=krylov.exact_dot if exact_dots else krylov.numpy_dot)
+    if dot is None:
+        dot = krylov.exact_dot if exact_dots else krylov.numpy_dot
+    res = bicgstab_solve(phi, f, op, tol, max_iter, dot=dot)
     return SolveInfo(res.iterations, res.converged, res.history[-1],
                      multigrid.convergence_factor(res.history), res.history, q)

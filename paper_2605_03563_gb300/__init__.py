@@ -103,8 +103,29 @@ class _Handle:
             out[e.name.decode()] = dict(launches=e.launches, total_ms=e.total_ms,
                                         avg_ms=e.total_ms / max(e.launches, 1),
                                         bytes_per_launch=e.bytes_per_launch,
-                                        ops_per_launch=e.ops_per_launch, fp64=bool(e.fp64))
+                                        ops_per_launch=e.ops_per_launch, fp64=bool(e.fp64),
+                                        variant=e.variant)
         return out
+
+    # ---- tuned settings (poisson_set_tuning)
+    def set_tuning(self, prec, nu1=2, nu2=2, inner_cycles=1, tile_min_n=0, sweep_tile=0):
+        """Install the tuned multigrid settings used by solves with tuned=True."""
+        t = capi.PsTuning(int(nu1), int(nu2), int(inner_cycles), int(tile_min_n), int(sweep_tile), 0)
+        check(lib().poisson_set_tuning(self._h, PRECISIONS[prec], C.byref(t)), "poisson_set_tuning")
+
+    def clear_tuning(self, prec):
+        check(lib().poisson_set_tuning(self._h, PRECISIONS[prec], None), "poisson_set_tuning")
+
+    def get_tuning(self, prec):
+        """The installed tuning of a precision as a dict, or None."""
+        t = capi.PsTuning()
+        is_set = C.c_int()
+        check(lib().poisson_get_tuning(self._h, PRECISIONS[prec], C.byref(t), C.byref(is_set)),
+              "poisson_get_tuning")
+        if not is_set.value:
+            return None
+        return dict(nu1=t.nu1, nu2=t.nu2, inner_cycles=t.inner_cycles, tile_min_n=t.tile_min_n,
+                    sweep_tile=t.sweep_tile)
 
     def __enter__(self):
         return self
@@ -115,11 +136,12 @@ class _Handle:
     # ---- asynchronous, steppable solves (continuous batching)
     def begin(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
               max_iter=100, inner_cycles=1, stream=None, tile_min_n=0, sor_schedule="fixed",
-              compact_order=0):
+              compact_order=0, tuned=False):
         """Start a solve whose state stays on the device; rho/phi must stay alive until end()."""
         self._opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
                                       int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
-                                      int(tile_min_n), SOR_SCHEDULES[sor_schedule], int(compact_order))
+                                      int(tile_min_n), SOR_SCHEDULES[sor_schedule], int(compact_order),
+                                      1 if tuned else 0)
         self._keep = (rho, phi)
         check(lib().poisson_solve_begin(self._h, _ptr(rho), _ptr(phi), float(tol),
                                         C.byref(self._opts)), "poisson_solve_begin")
@@ -145,10 +167,11 @@ class _Handle:
         return SolveInfo.from_c(info, min(nmom, 81))
 
     def _solve(self, rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-               stream, nmom, tile_min_n=0, sor_schedule="fixed", compact_order=0):
+               stream, nmom, tile_min_n=0, sor_schedule="fixed", compact_order=0, tuned=False):
         opts = capi.PsSolveOpts(METHODS[method], PRECISIONS[prec], float(omega), int(nu1),
                                 int(nu2), int(max_iter), int(inner_cycles), _stream(stream),
-                                int(tile_min_n), SOR_SCHEDULES[sor_schedule], int(compact_order))
+                                int(tile_min_n), SOR_SCHEDULES[sor_schedule], int(compact_order),
+                                1 if tuned else 0)
         info = capi.PsInfo()
         st = lib().poisson_solve(self._h, _ptr(rho), _ptr(phi), float(tol), C.byref(opts),
                                  C.byref(info))
@@ -184,17 +207,37 @@ class CartesianSolver(_Handle):
 
     def solve(self, rho, phi, tol=1e-10, method="mg", prec="fp64", omega=1.0, nu1=2, nu2=2,
               max_iter=100, inner_cycles=1, stream=None, tile_min_n=0,
-              sor_schedule="fixed", compact_order=0) -> SolveInfo:
+              sor_schedule="fixed", compact_order=0, tuned=False) -> SolveInfo:
         """tile_min_n: levels with at least this many intervals per axis use the TMA tile
         kernels (0 = library default, negative = never); results are bitwise identical.
         sor_schedule (method "sor"): "fixed" (omega), "chebyshev" (Eq. omega_n) or
         "optimal" (Eq. 3), the last two with rJ of Eq. 4.
         compact_order (method "mg", order-2 handle, equal spacings): 2, 4 or 6 selects the
         compact discretisation of that order with SPAI smoothing and Galerkin coarse
-        operators (Sec. 2.1.3); 0 the 7-point / 13-point stencil with Gauss-Seidel."""
+        operators (Sec. 2.1.3); 0 the 7-point / 13-point stencil with Gauss-Seidel.
+        tuned (method "mg"): take nu1, nu2, inner_cycles, tile_min_n and the fused sweep's
+        tile shape from the handle's tuning for prec (set_tuning, or use_table) when one
+        is installed."""
         nmom = (self.lmax + 1) ** 2 if self.multipole else 0
         return self._solve(rho, phi, tol, method, prec, omega, nu1, nu2, max_iter, inner_cycles,
-                           stream, min(nmom, 81), tile_min_n, sor_schedule, compact_order)
+                           stream, min(nmom, 81), tile_min_n, sor_schedule, compact_order, tuned)
+
+    def use_table(self, prec="fp64", tol=1e-10, table=None):
+        """Install the autotuner's entry for this grid (n, order, prec, tol) from a table
+        (dict or path; default: the package's table file) on the handle.  Returns the
+        installed settings, or None when the table has no entry (the handle keeps the
+        library defaults)."""
+        from . import autotune
+        if table is None or isinstance(table, str):
+            table = autotune.load(table) if table else autotune.load()
+        if len(set(self.n)) != 1:
+            return None
+        e = autotune.lookup(table, self.n[0], self.order, prec, tol)
+        if not e:
+            self.clear_tuning(prec)
+            return None
+        self.set_tuning(prec, e["nu1"], e["nu2"], e["inner"], e.get("tile_min_n", 0), e.get("sweep_tile", 0))
+        return self.get_tuning(prec)
 
 
 class SphericalSolver(_Handle):

@@ -1,10 +1,19 @@
-"""Autotuner for the multigrid cycle shape and the refinement inner loop.
+"""Autotuner for the multigrid cycle shape, the refinement inner loop and the
+tile shape of the fused red-black sweep.
 
 For a grid size, stencil order, precision and tolerance it times whole solves
-of a seeded Gaussian-mixture density (the serving workload's recipe) for each
-candidate (nu1, nu2, inner V-cycles per refinement step) and keeps the fastest
-time to tolerance.  Results are cached in a JSON table keyed by
-"n:order:prec:tol" so servers and benchmarks can reuse them.
+of a seeded Gaussian-mixture density (the serving workload's recipe) and keeps
+the fastest time to tolerance:
+  1. every candidate (nu1, nu2) x inner V-cycles per refinement step with the
+     library's default tile;
+  2. for the mixed precisions of the 7-point stencil, every compiled tile shape
+     of the TMA-staged fused sweep (poisson_set_tuning's sweep_tile 1..4) with
+     the winner of step 1 (the shapes give bitwise equal results, so only the
+     time differs).
+Each candidate runs through the handle's tuning (set_tuning + tuned=True), the
+same path a tuned caller takes.  Results are cached in a JSON table keyed by
+"n:order:prec:tol"; CartesianSolver.use_table and PoissonServer(tuning_table=)
+install an entry on a handle.
 """
 from __future__ import annotations
 
@@ -13,6 +22,7 @@ import os
 import statistics
 
 DEFAULT_CANDIDATES = [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3)]
+SWEEP_TILES = (1, 2, 3, 4)
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_table.json")
 
 
@@ -36,7 +46,8 @@ def save(table: dict, path: str = TABLE) -> None:
 
 
 def tune(n: int, order: int = 2, prec: str = "fp64", tol: float = 1e-10, device=None,
-         cycles=DEFAULT_CANDIDATES, inners=None, reps: int = 3, seed: int = 2, lmax: int = 4):
+         cycles=DEFAULT_CANDIDATES, inners=None, tiles=None, reps: int = 3, seed: int = 2,
+         lmax: int = 4):
     """Time every candidate and return the best settings with all timings."""
     import torch
     import workloads as W
@@ -44,28 +55,38 @@ def tune(n: int, order: int = 2, prec: str = "fp64", tol: float = 1e-10, device=
     device = device or torch.device("cuda", torch.cuda.current_device())
     if inners is None:
         inners = (1,) if prec == "fp64" else (1, 2, 3)
+    if tiles is None:
+        tiles = SWEEP_TILES if (prec != "fp64" and order == 2) else ()
     rho = W.gaussian_blobs_device(n, W.gaussian_blob_params(seed), device, order=order)
     phi = torch.zeros_like(rho)
     trials = []
     with CartesianSolver(n, order, bc="multipole", lmax=lmax) as s:
+        def run(nu1, nu2, inner, tile):
+            s.set_tuning(prec, nu1, nu2, inner, 0, tile)
+            times, info = [], None
+            for r in range(reps + 1):
+                phi.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                info = s.solve(rho, phi, tol=tol, method="mg", prec=prec, max_iter=200, tuned=True)
+                b.record()
+                torch.cuda.synchronize()
+                if r > 0:
+                    times.append(a.elapsed_time(b))
+            if info.converged:
+                trials.append({"nu1": nu1, "nu2": nu2, "inner": inner, "sweep_tile": tile,
+                               "ms": statistics.median(times), "iterations": info.iterations})
         for (nu1, nu2) in cycles:
             for inner in inners:
-                times = []
-                for r in range(reps + 1):
-                    phi.zero_()
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record()
-                    info = s.solve(rho, phi, tol=tol, method="mg", prec=prec, nu1=nu1, nu2=nu2,
-                                   inner_cycles=inner, max_iter=200)
-                    b.record()
-                    torch.cuda.synchronize()
-                    if r > 0:
-                        times.append(a.elapsed_time(b))
-                if info.converged:
-                    trials.append({"nu1": nu1, "nu2": nu2, "inner": inner,
-                                   "ms": statistics.median(times), "iterations": info.iterations})
+                run(nu1, nu2, inner, 0)
+        if not trials:
+            raise RuntimeError(f"no candidate converged for n={n} order={order} prec={prec} tol={tol:g}")
+        best = min(trials, key=lambda t: t["ms"])
+        for tile in tiles:
+            run(best["nu1"], best["nu2"], best["inner"], tile)
+        s.clear_tuning(prec)
     best = min(trials, key=lambda t: t["ms"])
-    return dict(best, trials=trials)
+    return dict(best, tile_min_n=0, trials=trials)
 
 
 def tune_table(sizes, order=2, prec="fp64", tol=1e-10, path: str = TABLE, **kw) -> dict:
@@ -80,4 +101,5 @@ def lookup(table: dict, n: int, order=2, prec="fp64", tol=1e-10):
     e = table.get(key(n, order, prec, tol))
     if not e:
         return {}
-    return {"nu1": e["nu1"], "nu2": e["nu2"], "inner": e["inner"]}
+    return {"nu1": e["nu1"], "nu2": e["nu2"], "inner": e["inner"],
+            "sweep_tile": e.get("sweep_tile", 0), "tile_min_n": e.get("tile_min_n", 0)}

@@ -37,7 +37,7 @@ class PsSolveOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("prec", C.c_int32), ("omega", C.c_double),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("max_iter", C.c_int32),
                 ("inner_cycles", C.c_int32), ("stream", C.c_void_p), ("tile_min_n", C.c_int32),
-                ("sor_schedule", C.c_int32), ("compact_order", C.c_int32), ("reserved_", C.c_int32)]
+                ("sor_schedule", C.c_int32), ("compact_order", C.c_int32), ("use_tuning", C.c_int32)]
 
 
 class PsInfo(C.Structure):
@@ -50,7 +50,12 @@ class PsInfo(C.Structure):
 class PsKernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
                 ("bytes_per_launch", C.c_double), ("ops_per_launch", C.c_double),
-                ("fp64", C.c_int32), ("pad", C.c_int32)]
+                ("fp64", C.c_int32), ("variant", C.c_int32)]
+
+
+class PsTuning(C.Structure):
+    _fields_ = [("nu1", C.c_int32), ("nu2", C.c_int32), ("inner_cycles", C.c_int32),
+                ("tile_min_n", C.c_int32), ("sweep_tile", C.c_int32), ("reserved_", C.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -72,6 +77,8 @@ SIGNATURES = {
     "poisson_workspace_bytes": (C.c_size_t, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_int]),
     "poisson_compact_operators": (C.c_int, [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "poisson_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(PsTuning)]),
+    "poisson_get_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(PsTuning), C.POINTER(C.c_int)]),
     "poisson_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "poisson_profile_read": (C.c_int, [C.c_void_p, C.POINTER(PsKernelStat), C.c_int]),
     "ps_op_apply": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -93,6 +100,7 @@ SIGNATURES = {
     "ps_op_scale_to_fp32": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "ps_probe_fp64": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double),
                                 C.c_void_p]),
+    "ps_probe_bounded_wait": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "poisson_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.POINTER(C.c_void_p)]),
     "poisson_batch_destroy": (None, [C.c_void_p]),

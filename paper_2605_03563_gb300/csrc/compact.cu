@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(32 * GW, 5)
     }
   }
   __syncthreads();
-  if (tid == 0) {   // planes k0 - 2 and k0 - 1 are no longer read (plane k0 keeps the centres of output k0)
+  if (tid == 0 && ok) {   // planes k0 - 2 and k0 - 1 are no longer read (plane k0 keeps the centres of output k0)
     fence_proxy_async();
     issue(zl + GNS);
     issue(zl + 1 + GNS);
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(32 * GW, 5)
       ob += sz;
     }
     __syncthreads();   // plane k (its u) and plane k + 1 (its b) are no longer read
-    if (tid == 0) {
+    if (tid == 0 && ok) {   // after a failed wait no new copy is issued
       fence_proxy_async();
       issue(k + GNS);
     }

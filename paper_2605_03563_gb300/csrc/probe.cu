@@ -10,6 +10,7 @@
 // warps per SM to hide the pipe's latency, and writes one value per block so
 // that no chain can be removed.
 #include "ps_common.cuh"
+#include "tma.cuh"
 
 namespace ps {
 namespace {
@@ -45,10 +46,63 @@ __global__ void __launch_bounds__(kThreads) k_probe_fp64(int iters, double a, do
   }
 }
 
+// One warp waits on an mbarrier that nothing ever arrives at, through the same
+// bounded wait the TMA tile kernels use (the first wait of a kernel, or a wait
+// after an earlier one has failed), then reports whether it gave up and how
+// long it waited.
+__global__ void k_probe_bounded_wait(int first_wait, long long* out) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  bool ok = first_wait != 0;
+  const unsigned long long t0 = global_ns();
+  mbar_wait(&bar, 0, ok);
+  const unsigned long long t1 = global_ns();
+  const bool phase_done = mbar_try_wait(&bar, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = phase_done ? 0 : 1;          // 1: the wait gave up (the phase never completed)
+    out[1] = (long long)(t1 - t0);
+    out[2] = ok ? 0 : 1;                  // the kernel's fault state after the wait
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  }
+}
+
 }  // namespace
 }  // namespace ps
 
 using namespace ps;
+
+extern "C" ps_status ps_probe_bounded_wait(int first_wait, long long* out_dev, double* waited_ms_host,
+                                           void* stream) {
+  if (out_dev == nullptr) {
+    set_error("ps_probe_bounded_wait: out_dev must be non-NULL");
+    return PS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_probe_bounded_wait<<<1, 32, 0, s>>>(first_wait != 0 ? 1 : 0, out_dev);
+  long long h[3] = {0, 0, 0};
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, out_dev, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error("ps_probe_bounded_wait: %s", cudaGetErrorString(e));
+    return PS_ERR_CUDA;
+  }
+  if (waited_ms_host) *waited_ms_host = (double)h[1] * 1e-6;
+  if (h[0] != 0 && h[2] != 0) {
+    set_error("ps_probe_bounded_wait: the bounded wait ran out after %.3f ms", (double)h[1] * 1e-6);
+    return PS_ERR_TIMEOUT;
+  }
+  if (h[0] != 0) {
+    set_error("ps_probe_bounded_wait: the wait returned without its phase and without a fault");
+    return PS_ERR_CUDA;
+  }
+  return PS_OK;
+}
 
 extern "C" ps_status ps_probe_fp64(int kind, int blocks, int iters, double* out_dev,
                                    double* instructions_host, void* stream) {

@@ -215,6 +215,11 @@ struct DevState {
   int restart;        // the next direction update restarts rhat = p = r
   int replace;        // the true residual replaces the recurrence one this iteration
   int fault;          // a tile kernel's TMA copy did not complete in time
+  double replace_drop;     // BiCGSTAB: replace when ||r|| <= replace_drop * rmax
+  int restart_on_replace;  // BiCGSTAB: restart rhat = p = r at every replacement
+  int iter_repl;           // BiCGSTAB: iteration of the last replacement
+  int discard;             // refinement form: the inner solve failed, drop its increments
+  int inner_cap;           // refinement form: most iterations of the current inner solve
 };
 
 enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3, DONE_FAULT = 4 };

@@ -113,6 +113,7 @@ struct Active {
   int chunk = 32, plain_chunk = 1;
   bool plain_steps = false;
   bool count_replacements = false;   // inner_cycles reports FP32 BiCGSTAB residual replacements
+  int sweep_tile = 0;                 // tile variant of the fused FP32/BF16 sweeps (0 = default)
   long long body_kernels = 0;
   int inner_per_iter = 0;
 };
@@ -128,6 +129,7 @@ struct ProfRec {
   cudaEvent_t a, b;
   double bytes, ops;
   int fp64;
+  int variant;
 };
 
 // Per-kernel-class totals of timed launches.
@@ -135,6 +137,7 @@ struct ProfAcc {
   long long n = 0;
   double ms = 0.0, bytes = 0.0, ops = 0.0;
   int fp64 = 0;
+  int variant = 0;
 };
 
 // A captured iteration body with CUDA-event record nodes around its hot
@@ -175,6 +178,9 @@ struct ps_ctx {
   int sv_dt = -1;
   double* sz = nullptr;   // BiCGSTAB group-wise increments of the iterate (FP64)
   double* sph_w = nullptr;   // spherical SOR weights, two buffers of Ntheta * Nr
+  double* sph_g = nullptr;   // spherical SOR: scaled right-hand side -f / a_c (field layout)
+  ps_tuning tun[3] = {};     // tuned multigrid settings per precision (poisson_set_tuning)
+  int has_tun[3] = {0, 0, 0};
   // Cartesian SOR: weights of the Chebyshev sequence, one per colour pass
   double* sor_wtab = nullptr;
   int sor_wlen = 0;
@@ -212,7 +218,7 @@ ps_status fail(ps_status s, const char* fmt, ...) {
 }
 
 // Profiler: begin/end pair around one launch on stream s.
-void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStream_t s) {
+void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStream_t s, int variant = 0) {
   std::vector<ProfRec>& sink = h->cap_slots ? *h->cap_slots : h->recs;
   if (!h->prof || sink.size() >= 16384) return;
   ProfRec r;
@@ -220,6 +226,7 @@ void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStre
   r.bytes = bytes;
   r.ops = ops;
   r.fp64 = fp64;
+  r.variant = variant;
   for (cudaEvent_t* e : {&r.a, &r.b}) {
     if (!h->ev_pool.empty()) {
       *e = h->ev_pool.back();
@@ -407,8 +414,9 @@ cudaError_t smooth(ps_ctx* h, Level& L, int l, int count, cudaStream_t s) {
       for (int half = 0; half < 2; half++) {
         const void* src = half == 0 ? L.phi : L.phib;
         void* dst = half == 0 ? L.phib : L.phi;
-        prof_begin(h, l == 0 ? PC_RBSWEEP0 : PC_RBSWEEP_C, w.n * 3.0 * w.S, w.n * 6.0 * w.G, w.fp64, s);
-        e = (h->nlaunch += 1, launch_rb_sweep(L.d, h->order, L.h, L.dt, src, dst, L.fs, nullptr, &h->st->fault, s));
+        const int tile = h->act.sweep_tile != 0 ? h->act.sweep_tile : rb_sweep_default_tile(L.dt);
+        prof_begin(h, l == 0 ? PC_RBSWEEP0 : PC_RBSWEEP_C, w.n * 3.0 * w.S, w.n * 6.0 * w.G, w.fp64, s, tile);
+        e = (h->nlaunch += 1, launch_rb_sweep(L.d, h->order, L.h, L.dt, src, dst, L.fs, nullptr, &h->st->fault, s, tile));
         prof_end(h, s);
         if (e != cudaSuccess) return e;
       }
@@ -610,7 +618,8 @@ ps_status begin_ir(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
     return norm_pass(h, phi, 2, L0->dt, L0->fs, q, cond, chunk);
   };
   h->act.key = "ir" + std::to_string(p) + ":" + std::to_string(nu1) + ":" + std::to_string(nu2) +
-               ":" + std::to_string(inner) + ":" + std::to_string(o->tile_min_n);
+               ":" + std::to_string(inner) + ":" + std::to_string(o->tile_min_n) + ":" +
+               std::to_string(h->act.sweep_tile);
   h->act.chunk = MG_CHUNK;
   h->act.plain_chunk = 1;
   h->act.inner_per_iter = inner;
@@ -992,14 +1001,15 @@ ps_status sph_vectors(ps_ctx* h, int dt) {
 // vectors of storage dt and return its iteration body.  x is the FP64 iterate.
 // vectors: 0 r, 1 rhat, 2 p, 3 phat, 4 v, 5 s, 6 shat, 7 t
 ps_status bicg_start(ps_ctx* h, int dt, const double* rho, double fscale, double* x, DevState* st,
-                     double tol, int max_iter, cudaStream_t s, Body* body) {
+                     double tol, int max_iter, cudaStream_t s, Body* body, double drop = 0.01,
+                     int restart_on_replace = 0) {
   int nb = 0;
   void** v = h->sv;
   TRY((h->nlaunch += 1, launch_init_state(st, tol, max_iter, s)));
   TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 0, rho, fscale, x, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
   TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 0, st, s)));
   TRY((h->nlaunch += 1, launch_bicg_resid(h->sd, h->stab, dt, 1, rho, fscale, x, v[0], v[1], v[2], v[3], h->partials, &nb, s)));
-  TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 1, st, s)));
+  TRY((h->nlaunch += 1, launch_bicg_start(h->partials, nb, 1, st, s, drop, restart_on_replace)));
   if (!h->sz) {
     ps_status r = alloc_zero((void**)&h->sz, (size_t)h->sd.size() * sizeof(double), &h->bytes);
     if (r != PS_OK) return r;
@@ -1035,40 +1045,47 @@ ps_status begin_sph_sor(ps_ctx* h, const double* rho, double fscale, double* x, 
                         const ps_solve_opts* o, cudaStream_t s) {
   const SphDims d = h->sd;
   ps_status r;
-  if ((r = ensure_partials(h, sph_resnorm_blocks(d))) != PS_OK) return r;
+  const int nb = sph_sor2_blocks(d);
+  if ((r = ensure_partials(h, std::max(2 * nb, sph_resnorm_blocks(d)))) != PS_OK) return r;
   const size_t nq = (size_t)d.nr * d.nt;
   const int sched = o->sor_schedule;
   if (sched != PS_SOR_FIXED && !h->sph_w)
     if ((r = alloc_zero((void**)&h->sph_w, 2 * nq * sizeof(double), &h->bytes)) != PS_OK) return r;
-  int nb = 0;
+  if (!h->sph_g)
+    if ((r = alloc_zero((void**)&h->sph_g, (size_t)d.size() * sizeof(double), &h->bytes)) != PS_OK) return r;
+  int nb0 = 0;
   TRY((h->nlaunch += 1, launch_init_state(h->st, tol, o->max_iter, s)));
-  TRY((h->nlaunch += 1, launch_bicg_resid(d, h->stab, DT_F64, 0, rho, fscale, x, nullptr, nullptr, nullptr, nullptr, h->partials, &nb, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 0, h->st, s)));
-  TRY((h->nlaunch += 1, launch_sph_resnorm(d, h->stab, x, rho, fscale, h->partials, &nb, s)));
-  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb, 1.0, 1, h->st, s)));
+  TRY((h->nlaunch += 1, launch_bicg_resid(d, h->stab, DT_F64, 0, rho, fscale, x, nullptr, nullptr, nullptr, nullptr, h->partials, &nb0, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb0, 1.0, 0, h->st, s)));
+  TRY((h->nlaunch += 1, launch_sph_resnorm(d, h->stab, x, rho, fscale, h->partials, &nb0, s)));
+  TRY((h->nlaunch += 1, launch_finish_norm(h->partials, nb0, 1.0, 1, h->st, s)));
+  TRY((h->nlaunch += 1, launch_sph_gs(d, h->stab, rho, fscale, h->sph_g, s)));
   if (sched != PS_SOR_FIXED)
     TRY((h->nlaunch += 1, launch_sph_sor_weights(d, h->stab, sched == PS_SOR_CHEBYSHEV, h->sph_w, s)));
   double* w0 = h->sph_w;
   double* w1 = h->sph_w ? h->sph_w + nq : nullptr;
   const double omega = o->omega;
-  h->act.body = [h, d, rho, fscale, x, sched, omega, w0, w1](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+  const double* g = h->sph_g;
+  // one step: red pass, black pass (with the black nodes' residuals after it),
+  // red nodes' residuals, norm and convergence check
+  h->act.body = [h, d, g, x, sched, omega, w0, w1, nb](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
     const double n = (double)d.nr * d.nt * d.np;
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < 2 && e == cudaSuccess; c++) {
       const double* wc = sched == PS_SOR_FIXED ? nullptr : (sched == PS_SOR_OPTIMAL || c == 0 ? w0 : w1);
       double* wn = sched == PS_SOR_CHEBYSHEV ? (c == 0 ? w1 : w0) : nullptr;
-      // a pass reads x everywhere, rho and x on its colour, writes x on its colour
-      prof_begin(h, PC_SWEEP0, n * 16.0, n / 2 * 17.0, 1, q);
-      e = (h->nlaunch += 1, launch_sph_sor(d, h->stab, x, rho, fscale, c, omega, wc, wn, h->st, q));
+      // a pass reads x everywhere, g and x on its colour, writes x on its colour;
+      // 8 FP64 instructions per red update, 13 (+4 for the residual) per black one
+      prof_begin(h, PC_SWEEP0, n * 16.0, n / 2 * (c == 0 ? 8.0 : 17.0), 1, q);
+      e = (h->nlaunch += 1, launch_sph_sor2(d, h->stab, x, g, c, omega, wc, wn, c == 1 ? h->partials : nullptr, h->st, q));
       prof_end(h, q);
     }
-    int nbl = 0;
     if (e == cudaSuccess) {
-      prof_begin(h, PC_NORM0, n * 16.0, n * 15.0, 1, q);
-      e = (h->nlaunch += 1, launch_sph_resnorm(d, h->stab, x, rho, fscale, h->partials, &nbl, q));
+      prof_begin(h, PC_NORM0, n * 12.0, n / 2 * 14.0, 1, q);
+      e = (h->nlaunch += 1, launch_sph_rednorm(d, h->stab, x, g, h->partials + 2 * nb, h->st, q));
       prof_end(h, q);
     }
-    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, nbl, 1.0, 3, h->st, q, cond, chunk));
+    if (e == cudaSuccess) e = (h->nlaunch += 1, launch_finish_norm(h->partials, 2 * nb, 1.0, 3, h->st, q, cond, chunk));
     return e;
   };
   char key[64];
@@ -1099,7 +1116,14 @@ ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, 
   if ((r = sph_vectors(h, dt)) != PS_OK) return r;
   h->act.key = dt == DT_F64 ? "bicg64" : "bicg32";
   h->act.count_replacements = dt != DT_F64;
-  return bicg_start(h, dt, rho, fscale, phi, h->st, tol, o->max_iter, s, &h->act.body);
+  if (dt == DT_F64) return bicg_start(h, dt, rho, fscale, phi, h->st, tol, o->max_iter, s, &h->act.body);
+  // FP32 Krylov vectors: iterative refinement.  Each inner FP32 BiCGSTAB runs
+  // until its recursive residual has dropped 2^-k-fold (k = inner_cycles, 4 by
+  // default: at 256 x 128 x 256 k = 2, 3, 4 took 39651, 57552, 37487
+  // iterations to 1e-8), then x takes the FP64 increments, the FP64 true
+  // residual replaces r and a new Krylov process starts from it.
+  const int k = o->inner_cycles > 0 ? std::min(o->inner_cycles, 30) : 4;
+  return bicg_start(h, dt, rho, fscale, phi, h->st, tol, o->max_iter, s, &h->act.body, std::ldexp(1.0, -k), 1);
 }
 
 // ------------------------------------------------------------------ stepping
@@ -1204,6 +1228,7 @@ ps_status step_active(ps_ctx* h, int k) {
         a.bytes = rec.bytes;
         a.ops = rec.ops;
         a.fp64 = rec.fp64;
+        a.variant = rec.variant;
       }
     }
     h->act.plain_steps = true;
@@ -1482,6 +1507,31 @@ ps_status poisson_compact_operators(int order, double h, int nlevels, double* a,
   return PS_OK;
 }
 
+ps_status poisson_set_tuning(ps_handle h, int prec, const ps_tuning* t) {
+  if (!h || h->sph) return fail(PS_ERR_INVALID_ARG, "poisson_set_tuning needs a Cartesian handle");
+  if (prec < PS_FP64 || prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", prec);
+  if (!t) {
+    h->has_tun[prec] = 0;
+    return PS_OK;
+  }
+  if (t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 < 1 || t->nu1 > 64 || t->nu2 > 64)
+    return fail(PS_ERR_INVALID_ARG, "tuning: nu1, nu2 in 0..64 with nu1 + nu2 >= 1");
+  if (t->inner_cycles < 1 || t->inner_cycles > 64) return fail(PS_ERR_INVALID_ARG, "tuning: inner_cycles in 1..64");
+  if (t->sweep_tile < 0 || t->sweep_tile > kRbSweepTiles)
+    return fail(PS_ERR_INVALID_ARG, "tuning: sweep_tile in 0..%d", kRbSweepTiles);
+  h->tun[prec] = *t;
+  h->has_tun[prec] = 1;
+  return PS_OK;
+}
+
+ps_status poisson_get_tuning(ps_handle h, int prec, ps_tuning* out, int* is_set) {
+  if (!h || !out || !is_set) return fail(PS_ERR_INVALID_ARG, "poisson_get_tuning: NULL argument");
+  if (prec < PS_FP64 || prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", prec);
+  *is_set = h->has_tun[prec];
+  if (*is_set) *out = h->tun[prec];
+  return PS_OK;
+}
+
 size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max, int prec) {
   if (!grid) return 0;
   if (grid->kind == PS_GRID_CART_UNIFORM) {
@@ -1492,8 +1542,8 @@ size_t poisson_workspace_bytes(const ps_grid* grid, int stencil_order, int l_max
     const size_t n = (size_t)(grid->n[0] + 2) * (grid->n[1] + 2) * (grid->n[2] + 2);
     const size_t vec = prec == PS_FP64 ? 8 : 4;
     // 8 Krylov vectors, the FP64 iterate and its increments, and the
-    // (r, theta) diagonal tables
-    return n * (8 * vec + 16) + (size_t)grid->n[0] * grid->n[1] * 16;
+    // (r, theta) tables (diagonal, rJ, the SOR form)
+    return n * (8 * vec + 16) + (size_t)grid->n[0] * grid->n[1] * 80;
   }
   return 0;
 }
@@ -1630,6 +1680,7 @@ void poisson_destroy(ps_handle h) {
   cudaFree(h->cg_q);
   cudaFree(h->cg_z);
   cudaFree(h->sph_w);
+  cudaFree(h->sph_g);
   cudaFree(h->sor_wtab);
   cart_multipole_free(&h->mp);
   sph_tables_free(&h->stab);
@@ -1668,6 +1719,15 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   if (opts) o = *opts;
   if (o.max_iter < 0) return fail(PS_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (o.prec < PS_FP64 || o.prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", o.prec);
+  int sweep_tile = 0;
+  if (o.use_tuning && !h->sph && o.method == PS_MG && h->has_tun[o.prec]) {
+    const ps_tuning& t = h->tun[o.prec];
+    o.nu1 = t.nu1;
+    o.nu2 = t.nu2;
+    o.inner_cycles = t.inner_cycles;
+    o.tile_min_n = t.tile_min_n;
+    sweep_tile = t.sweep_tile;
+  }
   if (o.sor_schedule < PS_SOR_FIXED || o.sor_schedule > PS_SOR_OPTIMAL)
     return fail(PS_ERR_INVALID_ARG, "unknown SOR schedule %d", o.sor_schedule);
   if (o.method == PS_SOR && o.sor_schedule == PS_SOR_FIXED && !(o.omega > 0.0 && o.omega < 2.0))
@@ -1699,6 +1759,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   Active& a = h->act;
   a = Active();
   a.o = o;
+  a.sweep_tile = sweep_tile;
   a.tol = tol;
   a.rho = rho_dev;
   a.phi_user = phi_dev;
@@ -2012,7 +2073,7 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
     fail(PS_ERR_CUDA, "profile_read: synchronisation failed");
     return -1;
   }
-  struct Acc { int64_t n = 0; double ms = 0, bytes = 0, ops = 0; int fp64 = 0; };
+  struct Acc { int64_t n = 0; double ms = 0, bytes = 0, ops = 0; int fp64 = 0, variant = 0; };
   std::vector<Acc> acc(PC_COUNT);
   for (int c = 0; c < PC_COUNT; c++) {
     acc[c].n = h->acc[c].n;
@@ -2020,6 +2081,7 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
     acc[c].bytes = h->acc[c].bytes;
     acc[c].ops = h->acc[c].ops;
     acc[c].fp64 = h->acc[c].fp64;
+    acc[c].variant = h->acc[c].variant;
     h->acc[c] = ProfAcc();
   }
   for (auto& r : h->recs) {
@@ -2031,6 +2093,7 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
       a.bytes = r.bytes;
       a.ops = r.ops;
       a.fp64 = r.fp64;
+      a.variant = r.variant;
     }
     h->ev_pool.push_back(r.a);
     h->ev_pool.push_back(r.b);
@@ -2048,6 +2111,7 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
       o.bytes_per_launch = acc[c].bytes;
       o.ops_per_launch = acc[c].ops;
       o.fp64 = acc[c].fp64;
+      o.variant = acc[c].variant;
     }
     k++;
   }

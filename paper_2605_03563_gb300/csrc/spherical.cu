@@ -46,7 +46,13 @@ __device__ __forceinline__ C sph_L(const SphDims& d, const Tab<C>& tb, const T* 
   const C pjp = j == d.nt - 1 ? pc : (C)p[c + sy];
   const C pkm = (C)(k == 0 ? p[c + (long long)(d.np - 1) * sz] : p[c - sz]);
   const C pkp = (C)(k == d.np - 1 ? p[c - (long long)(d.np - 1) * sz] : p[c + sz]);
-  const C ang = fma(tb.th_p[j], pjp - pc, fma(-tb.th_m[j], pc - pjm, tb.ph[j] * ((pkp + pkm) - (C)2 * pc)));
+  // FP32 (the refinement's inner vectors): the phi term as a sum of differences,
+  // so that its rounding is relative to the differences and not to |p| (the
+  // coefficient ph_j / r_i^2 reaches 1e11 at the inner poles)
+  C kk;
+  if constexpr (sizeof(C) == 4) kk = (pkp - pc) + (pkm - pc);
+  else kk = (pkp + pkm) - (C)2 * pc;
+  const C ang = fma(tb.th_p[j], pjp - pc, fma(-tb.th_m[j], pc - pjm, tb.ph[j] * kk));
   return fma(tb.rad_p[i], pip - pc, fma(-tb.rad_m[i], pc - pim, tb.inv_r2[i] * ang));
 }
 
@@ -153,6 +159,158 @@ cudaError_t launch_sph_sor_weights(const SphDims& d, const SphTables& t, int che
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ red-black SOR, scaled form
+// A thread owns the node pair (2t, 2t+1) of row (j, k) for the k of its chunk
+// of phi planes; in colour pass c it updates the member p = (c + j + k) & 1 of
+// each pair (exactly one per row and plane).  The per-(j, i) coefficients of
+// both members stay in registers for the whole chunk.  Per update: x_GS from
+// five fused multiply-adds and one add, then x += w (x_GS - x): 8 FP64
+// instructions (the flux form with a separate residual took about 16).
+static constexpr int SOR_TX = 32, SOR_TY = 8, SOR_KC = 8;
+
+__global__ void __launch_bounds__(256)
+    k_sph_gs(SphDims d, const double* __restrict__ ac, const double* __restrict__ rho, double fscale,
+             double* __restrict__ g) {
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  if (i >= d.nr || j >= d.nt) return;
+  const long long c = d.at(i, j, k);
+  g[c] = -(fscale * rho[c]) / ac[j * d.nr + i];
+}
+
+struct SorCoef {
+  double bip, bim, bjp, bjm, bk, ac, w, rj2;
+};
+
+// MODE 0 (red pass): update x_GS = sum b x_nb + g in sum form (8 FP64
+// instructions): its rounding, about ulp(x), is that of storing x.
+// MODE 1 (black pass): update with delta = x_GS - x in difference form,
+// sum b (x_nb - x) + g (12 instructions), whose rounding is relative to the
+// differences, and accumulate the black residual after the update,
+// r = a_c (x_new - x_GS) = a_c (w - 1) delta.
+// MODE 2 (red residuals after the black pass): r = -a_c delta in difference form.
+// The residual norm needs the difference form: in sum form its rounding,
+// a_c ulp(x), reaches 1e-8 of ||b|| on graded grids whose pole coefficients
+// reach 1e11, and SOR would stagnate there.
+template <int MODE>
+__global__ void __launch_bounds__(SOR_TX* SOR_TY)
+    k_sph_sor2(SphDims d, const double* __restrict__ tab, double* __restrict__ x, const double* __restrict__ g,
+               int colour, double omega, const double* __restrict__ wc, double* __restrict__ wn,
+               const double* __restrict__ rj2, double* __restrict__ partials, const DevState* __restrict__ st) {
+  if (st != nullptr && st->done) return;
+  const int t = blockIdx.x * SOR_TX + threadIdx.x, j = blockIdx.y * SOR_TY + threadIdx.y;
+  const int k0 = blockIdx.z * SOR_KC, k1 = min(k0 + SOR_KC, d.np);
+  const long long nq = (long long)d.nr * d.nt;
+  const long long sy = d.sy(), sz = d.sz(), wrap = (long long)(d.np - 1) * sz;
+  double acc = 0.0;
+  if (j < d.nt) {
+    // both members' coefficients in registers (selected, never indexed, so
+    // that they stay out of local memory)
+    auto load = [&](int p) {
+      SorCoef f;
+      const int i = min(2 * t + p, d.nr - 1);
+      const long long q = (long long)j * d.nr + i;
+      f.bip = tab[q];
+      f.bim = tab[nq + q];
+      f.bjp = tab[2 * nq + q];
+      f.bjm = tab[3 * nq + q];
+      f.bk = tab[4 * nq + q];
+      f.ac = tab[5 * nq + q];
+      f.w = wc != nullptr ? wc[q] : omega;
+      f.rj2 = wn != nullptr ? rj2[q] : 0.0;
+      return f;
+    };
+    const SorCoef c0 = load(0), c1 = load(1);
+    for (int k = k0; k < k1; k++) {
+      const int p = (colour + j + k) & 1;
+      const int i = 2 * t + p;
+      if (i >= d.nr) continue;
+      SorCoef f;
+      f.bip = p ? c1.bip : c0.bip;
+      f.bim = p ? c1.bim : c0.bim;
+      f.bjp = p ? c1.bjp : c0.bjp;
+      f.bjm = p ? c1.bjm : c0.bjm;
+      f.bk = p ? c1.bk : c0.bk;
+      f.ac = p ? c1.ac : c0.ac;
+      f.w = p ? c1.w : c0.w;
+      f.rj2 = p ? c1.rj2 : c0.rj2;
+      const long long c = d.at(i, j, k);
+      const double xc = x[c];
+      const double xim = (i == 0 && !d.inner_ghost) ? x[c + 1] : x[c - 1];
+      const double xip = x[c + 1];
+      const double xjm = j == 0 ? xc : x[c - sy];
+      const double xjp = j == d.nt - 1 ? xc : x[c + sy];
+      const double xkm = k == 0 ? x[c + wrap] : x[c - sz];
+      const double xkp = k == d.np - 1 ? x[c - wrap] : x[c + sz];
+      double delta;
+      if (MODE == 0) {
+        double gsv = fma(f.bk, xkp + xkm, g[c]);
+        gsv = fma(f.bjp, xjp, gsv);
+        gsv = fma(f.bjm, xjm, gsv);
+        gsv = fma(f.bip, xip, gsv);
+        gsv = fma(f.bim, xim, gsv);
+        delta = gsv - xc;
+      } else {
+        delta = fma(f.bk, (xkp - xc) + (xkm - xc), g[c]);
+        delta = fma(f.bjp, xjp - xc, delta);
+        delta = fma(f.bjm, xjm - xc, delta);
+        delta = fma(f.bip, xip - xc, delta);
+        delta = fma(f.bim, xim - xc, delta);
+      }
+      if (MODE == 2) {
+        const double e = f.ac * delta;
+        acc = fma(e, e, acc);
+        continue;
+      }
+      x[c] = fma(f.w, delta, xc);
+      if (MODE == 1) {
+        const double e = (f.w - 1.0) * f.ac * delta;
+        acc = fma(e, e, acc);
+      }
+      // the first node of this colour in the column (i, j) advances its weight
+      if (wn != nullptr && k == ((colour + i + j) & 1)) wn[(long long)j * d.nr + i] = 1.0 / (1.0 - f.rj2 * f.w / 4.0);
+    }
+  }
+  if (MODE != 0) block_sum2(acc, 0.0, partials);
+}
+
+static inline dim3 sor2_grid(const SphDims& d) {
+  const int half = (d.nr + 1) / 2;
+  return dim3((half + SOR_TX - 1) / SOR_TX, (d.nt + SOR_TY - 1) / SOR_TY, (d.np + SOR_KC - 1) / SOR_KC);
+}
+
+int sph_sor2_blocks(const SphDims& d) {
+  const dim3 g = sor2_grid(d);
+  return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_sph_gs(const SphDims& d, const SphTables& t, const double* rho, double fscale, double* g,
+                          cudaStream_t s) {
+  const long long nq = (long long)d.nr * d.nt;
+  k_sph_gs<<<sph_grid(d), dim3(SBX, SBY), 0, s>>>(d, t.sor_tab + 5 * nq, rho, fscale, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sph_sor2(const SphDims& d, const SphTables& t, double* x, const double* g, int colour,
+                            double omega, const double* wc, double* wn, double* partials,
+                            const DevState* st, cudaStream_t s) {
+  if (wn != nullptr && (wc == nullptr || t.rj2 == nullptr)) return cudaErrorInvalidValue;
+  const dim3 grid = sor2_grid(d), blk(SOR_TX, SOR_TY);
+  if (colour == 1) {
+    if (partials == nullptr) return cudaErrorInvalidValue;
+    k_sph_sor2<1><<<grid, blk, 0, s>>>(d, t.sor_tab, x, g, colour, omega, wc, wn, t.rj2, partials, st);
+  } else {
+    k_sph_sor2<0><<<grid, blk, 0, s>>>(d, t.sor_tab, x, g, colour, omega, wc, wn, t.rj2, nullptr, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sph_rednorm(const SphDims& d, const SphTables& t, const double* x, const double* g,
+                               double* partials, const DevState* st, cudaStream_t s) {
+  k_sph_sor2<2><<<sor2_grid(d), dim3(SOR_TX, SOR_TY), 0, s>>>(
+      d, t.sor_tab, const_cast<double*>(x), g, 0, 1.0, nullptr, nullptr, nullptr, partials, st);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ BiCGSTAB kernels
 // One iteration: v = L phat; alpha; s = r - alpha v, shat = B^-1 s; t = L shat;
 // omega; x += alpha phat + omega shat, r = s - omega t; then either the
@@ -165,7 +323,6 @@ cudaError_t launch_sph_sor_weights(const SphDims& d, const SphTables& t, int che
 // (every rounding of x is amplified by the pole coefficients, up to ~1e11).
 // The Krylov vectors are stored as T (double or float); x, the right-hand side
 // f = fscale * rho and all dot products are FP64.
-static constexpr double REPLACE_DROP = 0.01;
 
 //   mode 0: partials {|b|^2, |b|^2} for b = f - L(boundary part of x)
 //   mode 1: r = rhat = p = f - L x, phat = B^-1 r; partials {r.r, r.r}
@@ -212,6 +369,17 @@ __global__ void __launch_bounds__(SBX* SBY)
   block_sum2(s0, s1, partials);
 }
 
+// The vector kernels of an iteration march a chunk of BKC phi planes per
+// thread (block 32 r x 8 theta): the per-(r, theta) coefficients stay in
+// registers, the phi neighbours slide along the chunk, and a block's partial
+// dot products -- whose shuffle tree costs the FP64 pipe about ten instructions
+// per thread -- are formed once per BKC nodes instead of once per node.  The
+// arithmetic of every node is the one of sph_L.
+static constexpr int BKC = 4;
+static inline dim3 bk_grid(const SphDims& d) {
+  return dim3((d.nr + SBX - 1) / SBX, (d.nt + SBY - 1) / SBY, (d.np + BKC - 1) / BKC);
+}
+
 // dst = L src; partials {dst.w1, dst.dst (with_tt)}
 template <typename T>
 __global__ void __launch_bounds__(SBX* SBY)
@@ -220,15 +388,34 @@ __global__ void __launch_bounds__(SBX* SBY)
                  const DevState* __restrict__ st) {
   using C = typename St<T>::C;
   if (st->done) return;
-  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y;
+  const int k0 = blockIdx.z * BKC, k1 = min(k0 + BKC, d.np);
   double s0 = 0.0, s1 = 0.0;
   if (i < d.nr && j < d.nt) {
-    const long long c = d.at(i, j, k);
-    const C v = sph_L<T, C>(d, tb, src, i, j, k, c);
-    dst[c] = (T)v;
-    const double vd = (double)v;
-    s0 = vd * (double)w1[c];
-    if (with_tt) s1 = vd * vd;
+    const C rp = tb.rad_p[i], rm = tb.rad_m[i], ir2 = tb.inv_r2[i];
+    const C tp = tb.th_p[j], tm = tb.th_m[j], phc = tb.ph[j];
+    const long long sy = d.sy(), sz = d.sz(), wrap = (long long)(d.np - 1) * sz;
+    long long c = d.at(i, j, k0);
+    C pkm = (C)(k0 == 0 ? src[c + wrap] : src[c - sz]);
+    C pc = (C)src[c];
+    for (int k = k0; k < k1; k++, c += sz) {
+      const C pkp = (C)(k == d.np - 1 ? src[c - wrap] : src[c + sz]);
+      const C pim = (C)(i == 0 && !d.inner_ghost ? src[c + 1] : src[c - 1]);
+      const C pip = (C)src[c + 1];
+      const C pjm = j == 0 ? pc : (C)src[c - sy];
+      const C pjp = j == d.nt - 1 ? pc : (C)src[c + sy];
+      C kk;
+      if constexpr (sizeof(C) == 4) kk = (pkp - pc) + (pkm - pc);
+      else kk = (pkp + pkm) - (C)2 * pc;
+      const C ang = fma(tp, pjp - pc, fma(-tm, pc - pjm, phc * kk));
+      const C v = fma(rp, pip - pc, fma(-rm, pc - pim, ir2 * ang));
+      dst[c] = (T)v;
+      const double vd = (double)v;
+      s0 = fma(vd, (double)w1[c], s0);
+      if (with_tt) s1 = fma(vd, vd, s1);
+      pkm = pc;
+      pc = pkp;
+    }
   }
   block_sum2(s0, s1, partials);
 }
@@ -241,12 +428,17 @@ __global__ void __launch_bounds__(SBX* SBY)
   using C = typename St<T>::C;
   if (st->done) return;
   const C alpha = (C)st->alpha;
-  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y;
+  const int k0 = blockIdx.z * BKC, k1 = min(k0 + BKC, d.np);
   if (i >= d.nr || j >= d.nt) return;
-  const long long c = d.at(i, j, k);
-  const C s = fma(-alpha, (C)v[c], (C)r[c]);
-  sv[c] = (T)s;
-  shat[c] = (T)(s * tb.inv_diag[j * d.nr + i]);
+  const C idg = tb.inv_diag[j * d.nr + i];
+  const long long sz = d.sz();
+  long long c = d.at(i, j, k0);
+  for (int k = k0; k < k1; k++, c += sz) {
+    const C s = fma(-alpha, (C)v[c], (C)r[c]);
+    sv[c] = (T)s;
+    shat[c] = (T)(s * idg);
+  }
 }
 
 // z += alpha phat + omega shat (FP64 increments since the last replacement),
@@ -260,20 +452,26 @@ __global__ void __launch_bounds__(SBX* SBY)
   using C = typename St<T>::C;
   if (st->done) return;
   const double alpha = st->alpha, omega = st->omega;
-  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y;
+  const int k0 = blockIdx.z * BKC, k1 = min(k0 + BKC, d.np);
   double s0 = 0.0, s1 = 0.0;
   if (i < d.nr && j < d.nt) {
-    const long long c = d.at(i, j, k);
-    z[c] += fma(omega, (double)shat[c], alpha * (double)phat[c]);
-    const C rv = fma(-(C)omega, (C)tv[c], (C)sv[c]);
-    r[c] = (T)rv;
-    s0 = (double)rv * (double)rv;
-    s1 = (double)rv * (double)rhat[c];
+    const long long sz = d.sz();
+    long long c = d.at(i, j, k0);
+    for (int k = k0; k < k1; k++, c += sz) {
+      z[c] += fma(omega, (double)shat[c], alpha * (double)phat[c]);
+      const C rv = fma(-(C)omega, (C)tv[c], (C)sv[c]);
+      r[c] = (T)rv;
+      const double rd = (double)rv;
+      s0 = fma(rd, rd, s0);
+      s1 = fma(rd, (double)rhat[c], s1);
+    }
   }
   block_sum2(s0, s1, partials);
 }
 
-// Group-wise update at a replacement: x += z, z = 0.
+// Group-wise update at a replacement: x += z, z = 0 (refinement form: a
+// discarded inner solve leaves x as it was).
 __global__ void __launch_bounds__(SBX* SBY)
     k_bicg_fold(SphDims d, double* __restrict__ x, double* __restrict__ z,
                 const DevState* __restrict__ st) {
@@ -281,7 +479,7 @@ __global__ void __launch_bounds__(SBX* SBY)
   const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
   if (i >= d.nr || j >= d.nt) return;
   const long long c = d.at(i, j, k);
-  x[c] += z[c];
+  if (!st->discard) x[c] += z[c];
   z[c] = 0.0;
 }
 
@@ -295,20 +493,28 @@ __global__ void __launch_bounds__(SBX* SBY)
   if (st->done) return;
   const C beta = (C)st->beta, omega = (C)st->omega;
   const int restart = st->restart;
-  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y, k = blockIdx.z;
+  const int i = blockIdx.x * SBX + threadIdx.x, j = blockIdx.y * SBY + threadIdx.y;
+  const int k0 = blockIdx.z * BKC, k1 = min(k0 + BKC, d.np);
   if (i >= d.nr || j >= d.nt) return;
-  const long long c = d.at(i, j, k);
-  if (restart) {
-    const T rv = r[c];
-    rhat[c] = rv;
-    p[c] = rv;
-    phat[c] = (T)((C)rv * tb.inv_diag[j * d.nr + i]);
-    return;
+  const C idg = tb.inv_diag[j * d.nr + i];
+  const long long sz = d.sz();
+  long long c = d.at(i, j, k0);
+  for (int k = k0; k < k1; k++, c += sz) {
+    if (restart) {
+      const T rv = r[c];
+      rhat[c] = rv;
+      p[c] = rv;
+      phat[c] = (T)((C)rv * idg);
+      continue;
+    }
+    const C pv = fma(beta, fma(-omega, (C)v[c], (C)p[c]), (C)r[c]);
+    p[c] = (T)pv;
+    phat[c] = (T)(pv * idg);
   }
-  const C pv = fma(beta, fma(-omega, (C)v[c], (C)p[c]), (C)r[c]);
-  p[c] = (T)pv;
-  phat[c] = (T)(pv * tb.inv_diag[j * d.nr + i]);
 }
+
+// refinement form: most iterations of one inner FP32 solve
+static constexpr int kInnerCap = 256;
 
 __device__ __forceinline__ void bicg_set_loop(const DevState* st, unsigned long long cond, int chunk) {
   if (chunk > 0) {
@@ -374,12 +580,26 @@ __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int
   } else {
     st->iter += 1;
     const double rn = sqrt(v[0]);
-    if (!isfinite(rn) || st->broke || rn <= REPLACE_DROP * st->rmax || rn / st->ref <= st->tol ||
-        st->iter >= st->max_iter) {
+    // refinement form: rmax stays the inner solve's starting residual r0, and
+    // an inner solve also ends when its residual has grown 16-fold, turned
+    // non-finite (FP32 overflow in an excursion) or run inner_cap iterations.
+    // A solve that grew, overflowed, or hit the cap without getting below r0 is
+    // discarded (its increments dropped, x kept) and the next inner solve from
+    // the same x gets half as many iterations, so it stops before the
+    // excursion that ended this one; a successful solve restores the full cap.
+    bool inner_end = false;
+    if (st->restart_on_replace) {
+      const bool grew = !isfinite(rn) || rn > 16.0 * st->rmax;
+      const bool capped = st->iter - st->iter_repl >= st->inner_cap;
+      inner_end = grew || capped;
+      st->discard = grew || (capped && !(rn < st->rmax)) ? 1 : 0;
+    }
+    if (!isfinite(rn) || st->broke || rn <= st->replace_drop * st->rmax || rn / st->ref <= st->tol ||
+        st->iter >= st->max_iter || inner_end) {
       st->replace = 1;   // k_bicg_replace_finish decides and sets the loop
       return;
     }
-    st->rmax = fmax(st->rmax, rn);
+    if (!st->restart_on_replace) st->rmax = fmax(st->rmax, rn);
     st->rr = v[0];
     st->rel = rn / st->ref;
     bicg_direction(st, v[0], v[1]);
@@ -398,6 +618,10 @@ __global__ void k_bicg_replace_finish(const double* __restrict__ partials, int n
   if (threadIdx.x != 0) return;
   st->replace = 0;
   st->inner_cycles += 1;
+  if (st->restart_on_replace)
+    st->inner_cap = st->discard ? max(8, (st->iter - st->iter_repl) / 2) : kInnerCap;
+  st->discard = 0;
+  st->iter_repl = st->iter;
   const double rn = sqrt(v[0]);
   st->rmax = rn;
   st->rr = v[0];
@@ -405,12 +629,17 @@ __global__ void k_bicg_replace_finish(const double* __restrict__ partials, int n
   if (st->rel <= st->tol) st->done = DONE_CONVERGED;
   else if (!isfinite(rn)) st->done = DONE_DIVERGED;
   else if (st->iter >= st->max_iter) st->done = DONE_MAXITER;
-  else bicg_direction(st, v[0], v[1]);
+  else {
+    // refinement form (FP32 Krylov vectors): a new Krylov process starts from
+    // the FP64 true residual
+    if (st->restart_on_replace) st->broke = 1;
+    bicg_direction(st, v[0], v[1]);
+  }
   bicg_set_loop(st, cond, chunk);
 }
 
 __global__ void k_bicg_start(const double* __restrict__ partials, int nblk, int mode,
-                             DevState* __restrict__ st) {
+                             DevState* __restrict__ st, double replace_drop, int restart_on_replace) {
   __shared__ double sh[64];
   double v[2];
   sum_partials2(partials, nblk, sh, v);
@@ -424,6 +653,11 @@ __global__ void k_bicg_start(const double* __restrict__ partials, int nblk, int 
   st->rr = v[0];
   st->rho = v[1];
   st->rmax = sqrt(v[0]);
+  st->replace_drop = replace_drop;
+  st->restart_on_replace = restart_on_replace;
+  st->iter_repl = 0;
+  st->discard = 0;
+  st->inner_cap = kInnerCap;
   st->iter = 0;
   st->broke = 0;
   st->restart = 0;
@@ -451,8 +685,8 @@ cudaError_t launch_bicg_resid(const SphDims& d, const SphTables& t, int dt, int 
 }
 
 cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
-                              cudaStream_t s) {
-  k_bicg_start<<<1, 256, 0, s>>>(partials, nblk, mode, st);
+                              cudaStream_t s, double replace_drop, int restart_on_replace) {
+  k_bicg_start<<<1, 256, 0, s>>>(partials, nblk, mode, st, replace_drop, restart_on_replace);
   return cudaGetLastError();
 }
 
@@ -463,21 +697,21 @@ static cudaError_t iter_t(const SphDims& d, const SphTables& t, const double* rh
                           cudaStream_t s, unsigned long long cond, int chunk) {
   using C = typename St<T>::C;
   const Tab<C> tb = tab_of<C>(t);
-  const dim3 g = sph_grid(d), b(SBX, SBY);
-  const int nblk = g.x * g.y * g.z;
-  k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)phat, (T*)v, (const T*)rhat, 0, partials, st);
-  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 0, st, 0ull, 0);
-  k_bicg_s<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (const T*)v, (T*)sv, (T*)shat, st);
-  k_bicg_apply<T><<<g, b, 0, s>>>(d, tb, (const T*)shat, (T*)tv, (const T*)sv, 1, partials, st);
-  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 2, st, 0ull, 0);
-  k_bicg_xr<T><<<g, b, 0, s>>>(d, z, (T*)r, (const T*)rhat, (const T*)phat, (const T*)sv,
-                               (const T*)shat, (const T*)tv, partials, st);
-  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk, 3, st, cond, chunk);
+  const dim3 g = sph_grid(d), gk = bk_grid(d), b(SBX, SBY);
+  const int nblk = g.x * g.y * g.z, nblk_k = gk.x * gk.y * gk.z;
+  k_bicg_apply<T><<<gk, b, 0, s>>>(d, tb, (const T*)phat, (T*)v, (const T*)rhat, 0, partials, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk_k, 0, st, 0ull, 0);
+  k_bicg_s<T><<<gk, b, 0, s>>>(d, tb, (const T*)r, (const T*)v, (T*)sv, (T*)shat, st);
+  k_bicg_apply<T><<<gk, b, 0, s>>>(d, tb, (const T*)shat, (T*)tv, (const T*)sv, 1, partials, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk_k, 2, st, 0ull, 0);
+  k_bicg_xr<T><<<gk, b, 0, s>>>(d, z, (T*)r, (const T*)rhat, (const T*)phat, (const T*)sv,
+                                (const T*)shat, (const T*)tv, partials, st);
+  k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk_k, 3, st, cond, chunk);
   k_bicg_fold<<<g, b, 0, s>>>(d, x, z, st);
   k_bicg_resid<T><<<g, b, 0, s>>>(d, tab_of<double>(t), 2, rho, fscale, x, (T*)r, (T*)rhat,
                                   nullptr, nullptr, partials, st);
   k_bicg_replace_finish<<<1, 1024, 0, s>>>(partials, nblk, st, cond, chunk);
-  k_bicg_p<T><<<g, b, 0, s>>>(d, tb, (const T*)r, (T*)rhat, (T*)p, (const T*)v, (T*)phat, st);
+  k_bicg_p<T><<<gk, b, 0, s>>>(d, tb, (const T*)r, (T*)rhat, (T*)p, (const T*)v, (T*)phat, st);
   return cudaGetLastError();
 }
 
@@ -695,6 +929,22 @@ cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th
       rjsq[(size_t)j * nr + i] = rj * rj;
     }
   if ((e = upload(&t->rj2, rjsq, &t->bytes)) != cudaSuccess) return e;
+  {
+    const size_t nq = (size_t)nr * nt;
+    std::vector<double> sb(6 * nq);
+    for (int j = 0; j < nt; j++)
+      for (int i = 0; i < nr; i++) {
+        const size_t q = (size_t)j * nr + i;
+        const double ac = rp[i] + rm[i] + ir2[i] * (tp[j] + tm[j] + 2.0 * pp[j]);
+        sb[0 * nq + q] = rp[i] / ac;
+        sb[1 * nq + q] = rm[i] / ac;
+        sb[2 * nq + q] = ir2[i] * tp[j] / ac;
+        sb[3 * nq + q] = ir2[i] * tm[j] / ac;
+        sb[4 * nq + q] = ir2[i] * pp[j] / ac;
+        sb[5 * nq + q] = ac;
+      }
+    if ((e = upload(&t->sor_tab, sb, &t->bytes)) != cudaSuccess) return e;
+  }
   // multipole tables
   t->lmax = lmax;
   if (lmax >= 0) {
@@ -767,7 +1017,8 @@ cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th
 void sph_tables_free(SphTables* t) {
   void* ptrs[] = {t->rad_p, t->rad_m, t->inv_r2, t->th_p, t->th_m, t->ph, t->inv_diag,
                   t->rad_pf, t->rad_mf, t->inv_r2f, t->th_pf, t->th_mf, t->phf, t->inv_diagf,
-                  t->cosT, t->sinT, t->Pn, t->Rw, t->sinth, t->Fc, t->Fs, t->q, t->rj2, t->Rw_in, t->q_in};
+                  t->cosT, t->sinT, t->Pn, t->Rw, t->sinth, t->Fc, t->Fs, t->q, t->rj2, t->Rw_in, t->q_in,
+                  t->sor_tab};
   for (void* p : ptrs) cudaFree(p);
   *t = SphTables();
 }

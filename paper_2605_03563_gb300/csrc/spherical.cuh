@@ -47,6 +47,11 @@ struct SphTables {
   double* Rw_in = nullptr;
   double* q_in = nullptr;
   double r_ghost_in = 0.0;
+  // SOR in the scaled Gauss-Seidel form, per (theta_j, r_i) [6][Ntheta * Nr]:
+  // b_ip, b_im, b_jp, b_jm, b_k = the neighbour coefficients of L divided by
+  // a_c = -diag(L) > 0, and a_c itself (x_GS = sum b x_nb + g, g = -f / a_c,
+  // r = f - L x = a_c (x - x_GS))
+  double* sor_tab = nullptr;
   size_t bytes = 0;
 };
 
@@ -82,7 +87,7 @@ cudaError_t launch_bicg_iter(const SphDims& d, const SphTables& t, int dt, const
 int bicg_iter_kernels(int dt);
 // scalar finisher for the reference / initial residual (mode 0/1)
 cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevState* st,
-                              cudaStream_t s);
+                              cudaStream_t s, double replace_drop = 0.01, int restart_on_replace = 0);
 
 // ---- red-black SOR (Sec. 2.1.1) on the spherical grid, FP64.
 // One colour pass: nodes with (i + j + k) mod 2 == colour take
@@ -92,6 +97,20 @@ cudaError_t launch_bicg_start(const double* partials, int nblk, int mode, DevSta
 cudaError_t launch_sph_sor(const SphDims& d, const SphTables& t, double* x, const double* rho,
                            double fscale, int colour, double omega, const double* wc, double* wn,
                            const DevState* st, cudaStream_t s);
+// Red-black SOR step in the scaled form (tables sor_tab, g = -fscale rho / a_c
+// from launch_sph_gs): colour pass `colour` (0 red, then 1 black), thread per
+// (i pair, j) marching a chunk of phi planes.  The black pass (partials
+// required) also writes the per-block partials of sum r^2 over the black nodes
+// after their update (partials[0 .. nblk)); launch_sph_rednorm then adds the
+// red nodes' residuals (partials[nblk .. 2 nblk)).  Weights as launch_sph_sor.
+cudaError_t launch_sph_gs(const SphDims& d, const SphTables& t, const double* rho, double fscale,
+                          double* g, cudaStream_t s);
+cudaError_t launch_sph_sor2(const SphDims& d, const SphTables& t, double* x, const double* g, int colour,
+                            double omega, const double* wc, double* wn, double* partials,
+                            const DevState* st, cudaStream_t s);
+cudaError_t launch_sph_rednorm(const SphDims& d, const SphTables& t, const double* x, const double* g,
+                               double* partials, const DevState* st, cudaStream_t s);
+int sph_sor2_blocks(const SphDims& d);
 // partials {sum r^2, 0} of r = fscale rho - L x over the unknown nodes; *nblk = blocks
 cudaError_t launch_sph_resnorm(const SphDims& d, const SphTables& t, const double* x,
                                const double* rho, double fscale, double* partials, int* nblk,

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(32 * NWC)
   m.qk2 = 2 % NS;
   auto release = [&](int k) {   // the stage of plane k takes plane k + NS
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && m.ok) {   // after a failed wait no new copy is issued
       fence_proxy_async();
       issue(k + NS, m.qk);
     }
@@ -357,14 +357,10 @@ __global__ void __launch_bounds__(32 * NWC)
   if (!m.ok && fault != nullptr) atomicExch(fault, 1);
 }
 
-template <typename T, bool ISO>
+template <typename T, bool ISO, int R, int NWC>
 static cudaError_t rb_sweep_t(const Dims& d, const double h[3], const void* pin, void* pout,
                               const void* fs, const DevState* st, int* fault, cudaStream_t s) {
-  // 4 warps and a 5-plane ring; FP32: 4 rows per warp (64 x 16 tile, four blocks
-  // per SM), BF16: 8 rows (64 x 32 tile).  Measured at 256^3 among 2-8 rows,
-  // 4-8 warps and 4-6 stages: 0.043 ms FP32 (4 x 8 warps: 0.0447), 0.033 ms
-  // BF16 (4 x 8 warps: 0.044).
-  constexpr int R = sizeof(T) == 4 ? 4 : 8, NWC = 4, NS = 5;
+  constexpr int NS = 5;
   using Gm = SweepGeom<T, R, NWC, NS>;
   auto kern = k_rb_sweep<T, ISO, R, NWC, NS>;
   static int blocks_per_sm = 0;
@@ -393,21 +389,42 @@ static cudaError_t rb_sweep_t(const Dims& d, const double h[3], const void* pin,
   return cudaGetLastError();
 }
 
+template <typename T, int R, int NWC>
+static cudaError_t rb_sweep_iso(const Dims& d, const double h[3], const void* pin, void* pout,
+                                const void* fs, const DevState* st, int* fault, cudaStream_t s) {
+  if (h[0] == h[1] && h[1] == h[2]) return rb_sweep_t<T, true, R, NWC>(d, h, pin, pout, fs, st, fault, s);
+  return rb_sweep_t<T, false, R, NWC>(d, h, pin, pout, fs, st, fault, s);
+}
+
+// Tile variants (rows per warp x warps per block; 64 columns, 5-stage ring):
+// 1 = 4 x 4 (64 x 16 tile), 2 = 2 x 4 (64 x 8), 3 = 8 x 4 (64 x 32),
+// 4 = 4 x 8 (64 x 32).  0 picks the storage type's default: 1 for FP32, 3 for
+// BF16 (measured at 256^3 among 2-8 rows, 4-8 warps and 4-6 stages: 0.043 ms
+// FP32, 0.033 ms BF16).  The autotuner chooses among them per grid.
+int rb_sweep_default_tile(int dt) { return dt == DT_F32 ? 1 : 3; }
+
 template <typename T>
 static cudaError_t rb_sweep_dispatch(const Dims& d, const double h[3], const void* pin, void* pout,
-                                     const void* fs, const DevState* st, int* fault, cudaStream_t s) {
-  if (h[0] == h[1] && h[1] == h[2]) return rb_sweep_t<T, true>(d, h, pin, pout, fs, st, fault, s);
-  return rb_sweep_t<T, false>(d, h, pin, pout, fs, st, fault, s);
+                                     const void* fs, const DevState* st, int* fault, int tile, cudaStream_t s) {
+  switch (tile) {
+    case 1: return rb_sweep_iso<T, 4, 4>(d, h, pin, pout, fs, st, fault, s);
+    case 2: return rb_sweep_iso<T, 2, 4>(d, h, pin, pout, fs, st, fault, s);
+    case 3: return rb_sweep_iso<T, 8, 4>(d, h, pin, pout, fs, st, fault, s);
+    case 4: return rb_sweep_iso<T, 4, 8>(d, h, pin, pout, fs, st, fault, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // FP64 levels keep the colour passes (their sweeps are bound by the FP64 pipe),
 // so the fused sweep is built for the FP32 and BF16 inner levels only.
 cudaError_t launch_rb_sweep(const Dims& d, int order, const double h[3], int dt, const void* phi_in,
                             void* phi_out, const void* fs, const DevState* st, int* fault,
-                            cudaStream_t s) {
+                            cudaStream_t s, int tile) {
   if (order != 2 || d.g != 1 || dt == DT_F64) return cudaErrorNotSupported;
-  if (dt == DT_F32) return rb_sweep_dispatch<float>(d, h, phi_in, phi_out, fs, st, fault, s);
-  return rb_sweep_dispatch<__nv_bfloat16>(d, h, phi_in, phi_out, fs, st, fault, s);
+  if (tile < 0 || tile > kRbSweepTiles) return cudaErrorInvalidValue;
+  if (tile == 0) tile = rb_sweep_default_tile(dt);
+  if (dt == DT_F32) return rb_sweep_dispatch<float>(d, h, phi_in, phi_out, fs, st, fault, tile, s);
+  return rb_sweep_dispatch<__nv_bfloat16>(d, h, phi_in, phi_out, fs, st, fault, tile, s);
 }
 
 // ================================================================== residual + restriction
@@ -567,7 +584,7 @@ __global__ void __launch_bounds__(NT)
       }
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && ok) {   // after a failed wait no new copy is issued
       fence_proxy_async();
       issue(pc - G + NS);   // stage of phi plane pc - G
     }

@@ -12,10 +12,14 @@ namespace ps {
 // launch_sweep_colour.  phi_out must hold the same boundary values as phi_in.
 // Returns cudaErrorNotSupported for the 13-point operator.  Skipped entirely
 // once st->done (if st is given).  fault (optional): set to 1 if a tile copy
-// did not arrive in time.
+// did not arrive in time.  tile: 0 (the storage type's default) or one of the
+// kRbSweepTiles compiled tile shapes (see rb_sweep_default_tile); every shape
+// gives the same result bit for bit.
+constexpr int kRbSweepTiles = 4;
+int rb_sweep_default_tile(int dt);
 cudaError_t launch_rb_sweep(const Dims& d, int order, const double h[3], int dt, const void* phi_in,
                             void* phi_out, const void* fs, const DevState* st, int* fault,
-                            cudaStream_t s);
+                            cudaStream_t s, int tile = 0);
 
 // Fused residual and full-weighting restriction (Sec. 2.1.3):
 // fs_coarse = factor * R(phi_GS(phi) - phi) without storing the fine residual.

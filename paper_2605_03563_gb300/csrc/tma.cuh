@@ -6,7 +6,10 @@
 // then waits on the barrier's phase.  Waits are bounded by the global timer:
 // a copy that has not landed after kWaitNs sets the kernel's fault flag and the
 // kernel runs to completion with whatever the buffer holds, so a fault is
-// reported to the host instead of hanging the GPU.
+// reported to the host instead of hanging the GPU.  Once a wait of the issuing
+// thread has failed it issues no further copy; the copies already in flight
+// (at most one per stage) are waited for, in order, up to kDrainNs each, so a
+// CTA can only retire with a copy outstanding if that copy never completes.
 #pragma once
 
 #include <cuda.h>

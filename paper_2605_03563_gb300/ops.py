@@ -113,3 +113,17 @@ def probe_fp64(kind, blocks, iters, out, stream=None):
     check(lib().ps_probe_fp64(int(kind), int(blocks), int(iters), _p(out), C.byref(n), _s(stream)),
           "ps_probe_fp64")
     return n.value
+
+
+def probe_bounded_wait(first_wait, out, stream=None):
+    """Run the tile kernels' bounded mbarrier wait on a barrier nothing arrives
+    at (first_wait True: the 2 s limit of a kernel's first failing wait; False:
+    the 1 ms limit of later waits).  out: int64 CUDA tensor of at least 3
+    elements.  Returns (status, waited_ms); status is capi.PS_ERR_TIMEOUT when
+    the wait ran out as it must."""
+    import torch
+    if out.dtype != torch.int64 or out.numel() < 3:
+        raise ValueError("out must be int64 with at least 3 elements")
+    ms = C.c_double()
+    st = lib().ps_probe_bounded_wait(1 if first_wait else 0, _p(out), C.byref(ms), _s(stream))
+    return st, ms.value

@@ -106,7 +106,8 @@ class PoissonServer:
     def __init__(self, device, hbm_budget_bytes: int = 64 << 30, prec: str = "fp64",
                  cycles_per_step: int = 2, max_active: int = 64, lmax: int = 4, nu=(2, 2),
                  inner_cycles: int = 1, max_iter: int = 100, tuning: dict | None = None,
-                 executor: str = "hybrid", max_n: int = 256, batch_max_n: int = 96):
+                 executor: str = "hybrid", max_n: int = 256, batch_max_n: int = 96,
+                 tuning_table: dict | str | None = None):
         if executor not in ("batch", "streams", "hybrid"):
             raise ValueError("executor must be 'batch', 'streams' or 'hybrid'")
         self.device = device
@@ -119,6 +120,13 @@ class PoissonServer:
         self.inner = inner_cycles
         self.max_iter = max_iter
         self.tuning = tuning or {}
+        # the autotuner's table ("n:order:prec:tol" -> settings incl. the fused
+        # sweep's tile shape): requests that run on their own handle's loop graph
+        # are started with the tuned settings of their size and tolerance
+        if isinstance(tuning_table, str):
+            from .autotune import load
+            tuning_table = load(tuning_table)
+        self.tuning_table = tuning_table
         self.pool = HandlePool(prec, lmax)
         self.used = 0                  # bytes held by handles (idle or busy), fields and warm potentials
         self.warm = {}                 # seq_id -> (phi tensor, step) of the last finished step
@@ -178,6 +186,9 @@ class PoissonServer:
         slot = _Slot(req, solver, rho, phi, now, warm, self.field_bytes(n) + (self.pool.handle_bytes(n) if fresh else 0))
         if self.batch is not None and n <= self.batch_max_n:
             slot.bslot = self.batch.add(solver, rho, phi, tol=req.tol, max_iter=self.max_iter)
+        elif self.tuning_table is not None and solver.use_table(self.prec, req.tol, self.tuning_table):
+            solver.begin(rho, phi, tol=req.tol, method="mg", prec=self.prec, max_iter=self.max_iter,
+                         tuned=True)
         else:
             nu1, nu2, inner = self._settings(n)
             solver.begin(rho, phi, tol=req.tol, method="mg", prec=self.prec, nu1=nu1, nu2=nu2,

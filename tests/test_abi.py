@@ -44,7 +44,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"ps_grid": capi.PsGrid, "ps_bc": capi.PsBC, "ps_solve_opts": capi.PsSolveOpts,
-               "ps_info": capi.PsInfo, "ps_kernel_stat": capi.PsKernelStat}
+               "ps_info": capi.PsInfo, "ps_kernel_stat": capi.PsKernelStat,
+               "ps_tuning": capi.PsTuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "poisson.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

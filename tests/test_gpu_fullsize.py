@@ -126,6 +126,33 @@ def test_config4_spherical_full(pkg):
     np.testing.assert_allclose(P[1:-1, 1:-1, -1], shell, rtol=1e-12)
 
 
+def test_config4_spherical_mixed_full(pkg):
+    """The same workload with FP64 refinement around FP32-vector BiCGSTAB solves:
+    converges to 1e-8 (the oracle's residual of the GPU potential confirms it)
+    and agrees with the FP64 potential to 1e-7."""
+    tol = 1e-8
+    r, th, ph_ = W.spherical_coords(256, 128, 256, 0.01, 1.0)
+    rho = W.spherical_density(r, th, ph_)
+    rho_t = torch.from_numpy(rho).cuda()
+    with pkg.SphericalSolver(r, th, ph_, bc="multipole", lmax=6) as s:
+        ref = torch.zeros_like(rho_t)
+        info64 = s.solve(rho_t, ref, tol=tol, max_iter=30000)
+        assert info64.converged, info64
+        phi = torch.zeros_like(rho_t)
+        info = s.solve(rho_t, phi, tol=tol, prec="mixed_fp32", max_iter=80000)
+        assert info.converged, info
+    err = float((phi - ref).abs().max() / ref.abs().max())
+    assert err <= 1e-7, err
+    P = phi.cpu().numpy()
+    op = OSP.SphericalOperator(r, th, ph_)
+    f = 4 * math.pi * rho
+    U = (slice(1, -1), slice(1, -1), slice(1, -1))
+    bd = np.zeros(op.shape)
+    bd[:, :, -1] = P[:, :, -1]
+    rel = np.linalg.norm(f[U] - op.apply(P)) / np.linalg.norm(f[U] - op.apply(bd))
+    assert rel <= tol * (1 + 1e-3), rel
+
+
 def test_compact_sixth_order_two_spheres_255(pkg):
     """The compact timings' workload (Sec. 3.1's two spheres on [-1, 1]^3,
     sixth-order compact stencil, SPAI V(3,3), Galerkin coarse operators,
