@@ -100,9 +100,14 @@ typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3, PS_PCG = 4 } p
  *   correction, norms, multipole moments and coarsest solve in FP64) around
  *   FP32 inner V-cycles.  Spherical: FP64 iterative refinement around inner
  *   BiCGSTAB solves with FP32 Krylov vectors (iterate, right-hand side, true
- *   residuals and dot products in FP64): each inner solve starts a new Krylov
- *   process from the FP64 true residual and runs until its recursive residual
- *   has dropped 2^-k-fold, k = inner_cycles (0 = 4).
+ *   residuals and dot products in FP64).  Each inner solve applies right-Jacobi
+ *   BiCGSTAB to the volume-scaled correction equation V L e = V r (V the cell
+ *   volume r^2 dr sin(theta), which makes the flux form symmetric and keeps the
+ *   recursion free of the excursions that the unscaled one shows on graded
+ *   grids), starts from the FP64 true residual r and runs until its recursive
+ *   residual has dropped 2^-k-fold, k = inner_cycles (0 = 4); an inner solve
+ *   whose FP32 recursion overflows is discarded and retried with half the
+ *   iterations.  Convergence is decided on the FP64 true residual.
  * PS_MIXED_BF16: as PS_MIXED_FP32, with the finest inner level stored in BF16
  *   (Cartesian; spherical treats it as PS_MIXED_FP32).
  * Spherical BiCGSTAB in either precision stops on the true residual b - A x,

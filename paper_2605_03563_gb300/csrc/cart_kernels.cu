@@ -474,21 +474,24 @@ __global__ void __launch_bounds__(BX* BY)
   const int g = fd.g;
   const long long sy = fd.sy(), sz = fd.sz();
   const CF sc = (CF)(factor / 64.0);
+  // the (x, y)-weighted sum of fine plane 2K + 1 closes coarse plane K and opens
+  // K + 1: computed once per thread and carried (same values, same order)
+  auto plane_sum = [&](long long q0) -> CF {
+    CF rows[3];
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+      const long long q = q0 + dy * sy;
+      rows[dy + 1] = (St<TF>::ld(df + q - 1) + St<TF>::ld(df + q + 1)) + (CF)2 * St<TF>::ld(df + q);
+    }
+    return (rows[0] + rows[2]) + (CF)2 * rows[1];
+  };
+  CF below = plane_sum(fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K0 + g - 2));
   for (int K = K0; K < K1; K++) {
     const long long c = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
-    CF plane[3];
-#pragma unroll
-    for (int dz = -1; dz <= 1; dz++) {
-      CF rows[3];
-#pragma unroll
-      for (int dy = -1; dy <= 1; dy++) {
-        const long long q = c + dz * sz + dy * sy;
-        rows[dy + 1] = (St<TF>::ld(df + q - 1) + St<TF>::ld(df + q + 1)) + (CF)2 * St<TF>::ld(df + q);
-      }
-      plane[dz + 1] = (rows[0] + rows[2]) + (CF)2 * rows[1];
-    }
-    CF acc = (plane[0] + plane[2]) + (CF)2 * plane[1];
+    const CF mid = plane_sum(c), above = plane_sum(c + sz);
+    CF acc = (below + above) + (CF)2 * mid;
     St<TC>::st(fsc + cd.at(I + g - 1, J + g - 1, K + g - 1), (CC)(acc * sc));
+    below = above;
   }
 }
 
@@ -536,32 +539,32 @@ __global__ void __launch_bounds__(BX* BY)
   const long long csy = cd.sy(), csz = cd.sz();
   const long long fsy = fd.sy(), fsz = fd.sz();
   const CF half = (CF)0.5;
+  // the (x, y)-interpolated values of a coarse plane's cell face: [b][a]
+  auto face = [&](long long q0, CF (&v)[2][2]) {
+    CF c[2][2];   // [y][x]
+#pragma unroll
+    for (int y = 0; y < 2; y++) {
+      c[y][0] = (CF)St<TC>::ld(ec + q0 + y * csy);
+      c[y][1] = (CF)St<TC>::ld(ec + q0 + y * csy + 1);
+    }
+    CF vx[2][2];   // [y][a]
+#pragma unroll
+    for (int y = 0; y < 2; y++) {
+      vx[y][0] = c[y][0];
+      vx[y][1] = half * (c[y][0] + c[y][1]);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+      v[0][a] = vx[0][a];
+      v[1][a] = half * (vx[0][a] + vx[1][a]);
+    }
+  };
+  // the top face of cell K is the bottom face of cell K + 1: computed once
+  CF vy[2][2][2];   // [z][b][a]
+  face(cd.at(I + g - 1, J + g - 1, K0 + g - 1), vy[0]);
   for (int K = K0; K < K1; K++) {
     const long long c0 = cd.at(I + g - 1, J + g - 1, K + g - 1);
-    CF c[2][2][2];   // [z][y][x]
-#pragma unroll
-    for (int z = 0; z < 2; z++)
-#pragma unroll
-      for (int y = 0; y < 2; y++) {
-        c[z][y][0] = (CF)St<TC>::ld(ec + c0 + z * csz + y * csy);
-        c[z][y][1] = (CF)St<TC>::ld(ec + c0 + z * csz + y * csy + 1);
-      }
-    CF vx[2][2][2];   // [z][y][a]: x-interpolated
-#pragma unroll
-    for (int z = 0; z < 2; z++)
-#pragma unroll
-      for (int y = 0; y < 2; y++) {
-        vx[z][y][0] = c[z][y][0];
-        vx[z][y][1] = half * (c[z][y][0] + c[z][y][1]);
-      }
-    CF vy[2][2][2];   // [z][b][a]
-#pragma unroll
-    for (int z = 0; z < 2; z++)
-#pragma unroll
-      for (int a = 0; a < 2; a++) {
-        vy[z][0][a] = vx[z][0][a];
-        vy[z][1][a] = half * (vx[z][0][a] + vx[z][1][a]);
-      }
+    face(c0 + csz, vy[1]);
     const long long f0 = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
 #pragma unroll
     for (int cz = 0; cz < 2; cz++) {
@@ -578,6 +581,10 @@ __global__ void __launch_bounds__(BX* BY)
         }
       }
     }
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+      for (int a = 0; a < 2; a++) vy[0][b][a] = vy[1][b][a];
   }
 }
 

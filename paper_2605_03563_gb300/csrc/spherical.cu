@@ -24,15 +24,18 @@ namespace ps {
 
 static constexpr int SBX = 32, SBY = 8, MAXL = 16;
 
+// FP32 (the refinement form's inner solves) works on the volume-scaled system
+// V L e = V r: vol is V per (theta_j, r_i) and inv_diag is 1 / (V diag(L)).
 template <typename C> struct Tab {
   const C *rad_p, *rad_m, *inv_r2, *th_p, *th_m, *ph, *inv_diag;
+  const C* vol;   // FP32 only; nullptr for FP64
 };
 template <typename C> static Tab<C> tab_of(const SphTables& t);
 template <> Tab<double> tab_of<double>(const SphTables& t) {
-  return {t.rad_p, t.rad_m, t.inv_r2, t.th_p, t.th_m, t.ph, t.inv_diag};
+  return {t.rad_p, t.rad_m, t.inv_r2, t.th_p, t.th_m, t.ph, t.inv_diag, nullptr};
 }
 template <> Tab<float> tab_of<float>(const SphTables& t) {
-  return {t.rad_pf, t.rad_mf, t.inv_r2f, t.th_pf, t.th_mf, t.phf, t.inv_diagf};
+  return {t.rad_pf, t.rad_mf, t.inv_r2f, t.th_pf, t.th_mf, t.phf, t.inv_diag_vf, t.volf};
 }
 
 template <typename T, typename C>
@@ -330,7 +333,8 @@ cudaError_t launch_sph_rednorm(const SphDims& d, const SphTables& t, const doubl
 //           {r.r (FP64), rhat.r}
 template <typename T>
 __global__ void __launch_bounds__(SBX* SBY)
-    k_bicg_resid(SphDims d, Tab<double> tb, int mode, const double* __restrict__ rho, double fscale,
+    k_bicg_resid(SphDims d, Tab<double> tb, const double* __restrict__ vol, int mode,
+                 const double* __restrict__ rho, double fscale,
                  const double* __restrict__ x, T* __restrict__ r, T* __restrict__ rhat,
                  T* __restrict__ p, T* __restrict__ phat, double* __restrict__ partials,
                  const DevState* __restrict__ st) {
@@ -355,7 +359,18 @@ __global__ void __launch_bounds__(SBX* SBY)
     const double rv = __dsub_rn(__dmul_rn(fscale, rho[c]), Lx);
     s0 = rv * rv;
     s1 = s0;
-    if (mode == 1) {
+    if (sizeof(T) == 4 && mode != 0) {
+      // refinement form: the inner solve's residual is V r (its Krylov process
+      // restarts from it, so s1 is its squared norm); phat = (V D)^-1 V r = D^-1 r
+      const double rsv = rv * vol[j * d.nr + i];
+      s1 = rsv * rsv;
+      r[c] = (T)rsv;
+      if (mode == 1) {
+        rhat[c] = (T)rsv;
+        p[c] = (T)rsv;
+        phat[c] = (T)(rv * tb.inv_diag[j * d.nr + i]);
+      }
+    } else if (mode == 1) {
       r[c] = (T)rv;
       rhat[c] = (T)rv;
       p[c] = (T)rv;
@@ -394,6 +409,8 @@ __global__ void __launch_bounds__(SBX* SBY)
   if (i < d.nr && j < d.nt) {
     const C rp = tb.rad_p[i], rm = tb.rad_m[i], ir2 = tb.inv_r2[i];
     const C tp = tb.th_p[j], tm = tb.th_m[j], phc = tb.ph[j];
+    C vs = (C)1;
+    if constexpr (sizeof(C) == 4) vs = tb.vol[j * d.nr + i];
     const long long sy = d.sy(), sz = d.sz(), wrap = (long long)(d.np - 1) * sz;
     long long c = d.at(i, j, k0);
     C pkm = (C)(k0 == 0 ? src[c + wrap] : src[c - sz]);
@@ -408,7 +425,8 @@ __global__ void __launch_bounds__(SBX* SBY)
       if constexpr (sizeof(C) == 4) kk = (pkp - pc) + (pkm - pc);
       else kk = (pkp + pkm) - (C)2 * pc;
       const C ang = fma(tp, pjp - pc, fma(-tm, pc - pjm, phc * kk));
-      const C v = fma(rp, pip - pc, fma(-rm, pc - pim, ir2 * ang));
+      C v = fma(rp, pip - pc, fma(-rm, pc - pim, ir2 * ang));
+      if constexpr (sizeof(C) == 4) v *= vs;
       dst[c] = (T)v;
       const double vd = (double)v;
       s0 = fma(vd, (double)w1[c], s0);
@@ -513,8 +531,8 @@ __global__ void __launch_bounds__(SBX* SBY)
   }
 }
 
-// refinement form: most iterations of one inner FP32 solve
-static constexpr int kInnerCap = 256;
+// refinement form: no iteration cap on an inner FP32 solve until one overflows
+static constexpr int kNoCap = 1 << 30;
 
 __device__ __forceinline__ void bicg_set_loop(const DevState* st, unsigned long long cond, int chunk) {
   if (chunk > 0) {
@@ -580,26 +598,27 @@ __global__ void k_bicg_scalar(const double* __restrict__ partials, int nblk, int
   } else {
     st->iter += 1;
     const double rn = sqrt(v[0]);
-    // refinement form: rmax stays the inner solve's starting residual r0, and
-    // an inner solve also ends when its residual has grown 16-fold, turned
-    // non-finite (FP32 overflow in an excursion) or run inner_cap iterations.
-    // A solve that grew, overflowed, or hit the cap without getting below r0 is
-    // discarded (its increments dropped, x kept) and the next inner solve from
-    // the same x gets half as many iterations, so it stops before the
-    // excursion that ended this one; a successful solve restores the full cap.
+    // refinement form: an inner solve whose FP32 recursion overflowed (a
+    // non-finite residual: one of BiCGSTAB's excursions on graded grids grew
+    // past the FP32 range) is discarded -- its increments are dropped and x is
+    // kept -- and the next inner solve from the same x is capped at half as
+    // many iterations, so it stops before that excursion; a successful inner
+    // solve lifts the cap again.
     bool inner_end = false;
     if (st->restart_on_replace) {
-      const bool grew = !isfinite(rn) || rn > 16.0 * st->rmax;
-      const bool capped = st->iter - st->iter_repl >= st->inner_cap;
-      inner_end = grew || capped;
-      st->discard = grew || (capped && !(rn < st->rmax)) ? 1 : 0;
+      const bool bad = !isfinite(rn);
+      inner_end = bad || st->iter - st->iter_repl >= st->inner_cap;
+      st->discard = bad ? 1 : 0;
     }
-    if (!isfinite(rn) || st->broke || rn <= st->replace_drop * st->rmax || rn / st->ref <= st->tol ||
+    // (the refinement form's recursive norm is of V r; only its replaced, FP64
+    // true residual is compared with the tolerance)
+    const bool claims = !st->restart_on_replace && rn / st->ref <= st->tol;
+    if (!isfinite(rn) || st->broke || rn <= st->replace_drop * st->rmax || claims ||
         st->iter >= st->max_iter || inner_end) {
       st->replace = 1;   // k_bicg_replace_finish decides and sets the loop
       return;
     }
-    if (!st->restart_on_replace) st->rmax = fmax(st->rmax, rn);
+    st->rmax = fmax(st->rmax, rn);
     st->rr = v[0];
     st->rel = rn / st->ref;
     bicg_direction(st, v[0], v[1]);
@@ -619,11 +638,11 @@ __global__ void k_bicg_replace_finish(const double* __restrict__ partials, int n
   st->replace = 0;
   st->inner_cycles += 1;
   if (st->restart_on_replace)
-    st->inner_cap = st->discard ? max(8, (st->iter - st->iter_repl) / 2) : kInnerCap;
+    st->inner_cap = st->discard ? max(8, (st->iter - st->iter_repl) / 2) : kNoCap;
   st->discard = 0;
   st->iter_repl = st->iter;
   const double rn = sqrt(v[0]);
-  st->rmax = rn;
+  st->rmax = st->restart_on_replace ? sqrt(v[1]) : rn;   // refinement form: ||V r||
   st->rr = v[0];
   st->rel = rn / st->ref;
   if (st->rel <= st->tol) st->done = DONE_CONVERGED;
@@ -632,8 +651,12 @@ __global__ void k_bicg_replace_finish(const double* __restrict__ partials, int n
   else {
     // refinement form (FP32 Krylov vectors): a new Krylov process starts from
     // the FP64 true residual
-    if (st->restart_on_replace) st->broke = 1;
-    bicg_direction(st, v[0], v[1]);
+    if (st->restart_on_replace) {
+      st->broke = 1;
+      bicg_direction(st, v[1], v[1]);   // rho = ||V r||^2 of the new process
+    } else {
+      bicg_direction(st, v[0], v[1]);
+    }
   }
   bicg_set_loop(st, cond, chunk);
 }
@@ -652,12 +675,12 @@ __global__ void k_bicg_start(const double* __restrict__ partials, int nblk, int 
   }
   st->rr = v[0];
   st->rho = v[1];
-  st->rmax = sqrt(v[0]);
+  st->rmax = restart_on_replace ? sqrt(v[1]) : sqrt(v[0]);
   st->replace_drop = replace_drop;
   st->restart_on_replace = restart_on_replace;
   st->iter_repl = 0;
   st->discard = 0;
-  st->inner_cap = kInnerCap;
+  st->inner_cap = kNoCap;
   st->iter = 0;
   st->broke = 0;
   st->restart = 0;
@@ -676,10 +699,10 @@ cudaError_t launch_bicg_resid(const SphDims& d, const SphTables& t, int dt, int 
   const dim3 g = sph_grid(d), b(SBX, SBY);
   if (nblk) *nblk = g.x * g.y * g.z;
   if (dt == DT_F64)
-    k_bicg_resid<double><<<g, b, 0, s>>>(d, tab_of<double>(t), mode, rho, fscale, x, (double*)r,
+    k_bicg_resid<double><<<g, b, 0, s>>>(d, tab_of<double>(t), t.vol, mode, rho, fscale, x, (double*)r,
                                          (double*)rhat, (double*)p, (double*)phat, partials, nullptr);
   else
-    k_bicg_resid<float><<<g, b, 0, s>>>(d, tab_of<double>(t), mode, rho, fscale, x, (float*)r,
+    k_bicg_resid<float><<<g, b, 0, s>>>(d, tab_of<double>(t), t.vol, mode, rho, fscale, x, (float*)r,
                                         (float*)rhat, (float*)p, (float*)phat, partials, nullptr);
   return cudaGetLastError();
 }
@@ -708,7 +731,7 @@ static cudaError_t iter_t(const SphDims& d, const SphTables& t, const double* rh
                                 (const T*)shat, (const T*)tv, partials, st);
   k_bicg_scalar<<<1, 1024, 0, s>>>(partials, nblk_k, 3, st, cond, chunk);
   k_bicg_fold<<<g, b, 0, s>>>(d, x, z, st);
-  k_bicg_resid<T><<<g, b, 0, s>>>(d, tab_of<double>(t), 2, rho, fscale, x, (T*)r, (T*)rhat,
+  k_bicg_resid<T><<<g, b, 0, s>>>(d, tab_of<double>(t), t.vol, 2, rho, fscale, x, (T*)r, (T*)rhat,
                                   nullptr, nullptr, partials, st);
   k_bicg_replace_finish<<<1, 1024, 0, s>>>(partials, nblk, st, cond, chunk);
   k_bicg_p<T><<<gk, b, 0, s>>>(d, tb, (const T*)r, (T*)rhat, (T*)p, (const T*)v, (T*)phat, st);
@@ -915,6 +938,25 @@ cudaError_t sph_tables_build(const SphDims& d, const double* r, const double* th
   if ((e = upload(&t->th_mf, to_f(tm), &t->bytes)) != cudaSuccess) return e;
   if ((e = upload(&t->phf, to_f(pp), &t->bytes)) != cudaSuccess) return e;
   if ((e = upload(&t->inv_diagf, to_f(idg), &t->bytes)) != cudaSuccess) return e;
+  {
+    // cell volumes r_i^2 dr_i sin(theta_j) (dtheta dphi dropped), normalised to
+    // at most 1: the row scaling that makes the flux form symmetric
+    std::vector<double> vol((size_t)nr * nt), idv((size_t)nr * nt);
+    double vmax = 0.0;
+    for (int j = 0; j < nt; j++)
+      for (int i = 0; i < nr; i++) {
+        const double ri = re[i + 1], dr = 0.5 * (re[i + 2] - re[i]);
+        vol[(size_t)j * nr + i] = ri * ri * dr * std::sin(th[j]);
+        vmax = std::max(vmax, vol[(size_t)j * nr + i]);
+      }
+    for (size_t q = 0; q < vol.size(); q++) {
+      vol[q] /= vmax;
+      idv[q] = idg[q] / vol[q];
+    }
+    if ((e = upload(&t->vol, vol, &t->bytes)) != cudaSuccess) return e;
+    if ((e = upload(&t->volf, to_f(vol), &t->bytes)) != cudaSuccess) return e;
+    if ((e = upload(&t->inv_diag_vf, to_f(idv), &t->bytes)) != cudaSuccess) return e;
+  }
   // Eq. local_rjac: rJ at (theta_j, r_i) from the radial width of the flux form,
   // r_i dtheta and r_i sin(theta_j) dphi; stored squared for the SOR weights
   std::vector<double> rjsq((size_t)nr * nt);
@@ -1018,7 +1060,7 @@ void sph_tables_free(SphTables* t) {
   void* ptrs[] = {t->rad_p, t->rad_m, t->inv_r2, t->th_p, t->th_m, t->ph, t->inv_diag,
                   t->rad_pf, t->rad_mf, t->inv_r2f, t->th_pf, t->th_mf, t->phf, t->inv_diagf,
                   t->cosT, t->sinT, t->Pn, t->Rw, t->sinth, t->Fc, t->Fs, t->q, t->rj2, t->Rw_in, t->q_in,
-                  t->sor_tab};
+                  t->sor_tab, t->vol, t->volf, t->inv_diag_vf};
   for (void* p : ptrs) cudaFree(p);
   *t = SphTables();
 }

@@ -52,6 +52,11 @@ struct SphTables {
   // a_c = -diag(L) > 0, and a_c itself (x_GS = sum b x_nb + g, g = -f / a_c,
   // r = f - L x = a_c (x - x_GS))
   double* sor_tab = nullptr;
+  // refinement form (FP32 inner solves on V L e = V r): cell volumes V per
+  // (theta_j, r_i) normalised to at most 1 (FP64 and FP32) and 1 / (V diag(L)) (FP32)
+  double* vol = nullptr;
+  float* volf = nullptr;
+  float* inv_diag_vf = nullptr;
   size_t bytes = 0;
 };
 
