@@ -105,7 +105,7 @@ typedef enum { PS_SOR = 0, PS_CG = 1, PS_MG = 2, PS_BICGSTAB = 3, PS_PCG = 4 } p
  *   volume r^2 dr sin(theta), which makes the flux form symmetric and keeps the
  *   recursion free of the excursions that the unscaled one shows on graded
  *   grids), starts from the FP64 true residual r and runs until its recursive
- *   residual has dropped 2^-k-fold, k = inner_cycles (0 = 4); an inner solve
+ *   residual has dropped 2^-k-fold, k = inner_cycles (0 = 2); an inner solve
  *   whose FP32 recursion overflows is discarded and retried with half the
  *   iterations.  Convergence is decided on the FP64 true residual.
  * PS_MIXED_BF16: as PS_MIXED_FP32, with the finest inner level stored in BF16
@@ -122,7 +122,7 @@ typedef struct {
   int32_t nu1, nu2;      /* V(nu1,nu2) pre-/post-smoothing sweeps */
   int32_t max_iter;      /* SOR steps / CG or BiCGSTAB iterations / V-cycles / IR steps */
   int32_t inner_cycles;  /* Cartesian mixed modes: inner V-cycles per IR step; spherical
-                            PS_MIXED_FP32: the inner solve's reduction 2^-inner_cycles (0 = 4) */
+                            PS_MIXED_FP32: the inner solve's reduction 2^-inner_cycles (0 = 2) */
   void* stream;          /* cudaStream_t; NULL = CUDA's default stream */
   int32_t tile_min_n;    /* Cartesian MG, mixed modes: FP32/BF16 inner levels (other than the
                             coarsest) with at least this many intervals on every axis run the

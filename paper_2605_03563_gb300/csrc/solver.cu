@@ -376,10 +376,14 @@ cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState
   const int ncol = h->order == 2 ? 2 : 3;
   const Work w = work_of(L, h->order);
   cudaError_t e;
+  // FP64 7-point passes on equal spacings walk (j, k) diagonals: 5 FP64
+  // instructions per update instead of 6
+  const bool diag = h->order == 2 && L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
+  const double per_update = diag ? 5.0 : 6.0 * w.G;
   for (int c = 0; c < ncol; c++) {
     // one colour pass reads phi everywhere, fs and phi on its colour, writes phi on its colour
     prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, w.n * w.S * (1.0 + 2.0 / ncol),
-               w.n / ncol * (6.0 * w.G + (omega != 1.0 || wtab ? 2.0 : 0.0)), w.fp64, s);
+               w.n / ncol * (per_update + (omega != 1.0 || wtab ? 2.0 : 0.0)), w.fp64, s);
     e = (h->nlaunch += 1, launch_sweep_colour(L.d, h->order, L.h, L.dt, L.phi, L.fs, c, omega, st, s, wtab, wlen));
     prof_end(h, s);
     if (e != cudaSuccess) return e;
@@ -1118,11 +1122,12 @@ ps_status begin_sph(ps_ctx* h, const double* rho, double* phi_user, double tol, 
   h->act.count_replacements = dt != DT_F64;
   if (dt == DT_F64) return bicg_start(h, dt, rho, fscale, phi, h->st, tol, o->max_iter, s, &h->act.body);
   // FP32 Krylov vectors: iterative refinement.  Each inner FP32 BiCGSTAB runs
-  // until its recursive residual has dropped 2^-k-fold (k = inner_cycles, 4 by
-  // default: at 256 x 128 x 256 k = 2, 3, 4 took 39651, 57552, 37487
-  // iterations to 1e-8), then x takes the FP64 increments, the FP64 true
-  // residual replaces r and a new Krylov process starts from it.
-  const int k = o->inner_cycles > 0 ? std::min(o->inner_cycles, 30) : 4;
+  // until its recursive residual has dropped 2^-k-fold (k = inner_cycles, 2 by
+  // default: at 256 x 128 x 256 to 1e-8, k = 2, 3, 4, 5, 6 took 1.97, 2.28,
+  // 3.72, 3.11, 2.98 s and k = 8 did not converge), then x takes the FP64
+  // increments, the FP64 true residual replaces r and a new Krylov process
+  // starts from it.
+  const int k = o->inner_cycles > 0 ? std::min(o->inner_cycles, 30) : 2;
   return bicg_start(h, dt, rho, fscale, phi, h->st, tol, o->max_iter, s, &h->act.body, std::ldexp(1.0, -k), 1);
 }
 

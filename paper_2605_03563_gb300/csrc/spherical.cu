@@ -71,6 +71,18 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* partials)
   }
 }
 
+// partials {a, 0}: one sum per block (half the shuffle tree of block_sum2)
+__device__ __forceinline__ void block_sum1(double a, double* partials) {
+  __shared__ double sh[32];
+  double v[1] = {a};
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int bid = block_linear_id();
+    partials[2 * bid] = v[0];
+    partials[2 * bid + 1] = 0.0;
+  }
+}
+
 static inline dim3 sph_grid(const SphDims& d) {
   return dim3((d.nr + SBX - 1) / SBX, (d.nt + SBY - 1) / SBY, d.np);
 }
@@ -390,7 +402,7 @@ __global__ void __launch_bounds__(SBX* SBY)
 // dot products -- whose shuffle tree costs the FP64 pipe about ten instructions
 // per thread -- are formed once per BKC nodes instead of once per node.  The
 // arithmetic of every node is the one of sph_L.
-static constexpr int BKC = 4;
+static constexpr int BKC = 8;
 static inline dim3 bk_grid(const SphDims& d) {
   return dim3((d.nr + SBX - 1) / SBX, (d.nt + SBY - 1) / SBY, (d.np + BKC - 1) / BKC);
 }
@@ -435,7 +447,8 @@ __global__ void __launch_bounds__(SBX* SBY)
       pc = pkp;
     }
   }
-  block_sum2(s0, s1, partials);
+  if (with_tt) block_sum2(s0, s1, partials);
+  else block_sum1(s0, partials);
 }
 
 // s = r - alpha v, shat = B^-1 s

@@ -13,9 +13,17 @@ __device__ __forceinline__ C gs_value(const T* __restrict__ phi, long long p, lo
                                       long long sz, const Coef<C>& cf, C fs) {
   using S = St<T>;
   C ax = S::ld(phi + p + 1) + S::ld(phi + p - 1);
+  C v;
+  if constexpr (ISO && G == 1 && sizeof(C) == 8) {
+    // FP64 7-point on equal spacings: the order of the diagonal colour pass
+    // (k_sweep_diag), (E + W) + (S + D) + (N + U), so that residuals after a
+    // sweep repeat its arithmetic exactly
+    const C sd = S::ld(phi + p - sy) + S::ld(phi + p - sz);
+    const C nu = S::ld(phi + p + sy) + S::ld(phi + p + sz);
+    return fma((ax + sd) + nu, cf.c1[0], fs);
+  }
   C ay = S::ld(phi + p + sy) + S::ld(phi + p - sy);
   C az = S::ld(phi + p + sz) + S::ld(phi + p - sz);
-  C v;
   if (ISO) {
     v = fma((ax + ay) + az, cf.c1[0], fs);
   } else {

@@ -308,16 +308,22 @@ def test_spherical_bicgstab_matches_oracle(pkg, prec):
     """BiCGSTAB's iteration count on the graded log grid is set by rounding:
     the oracle itself needs a spread of counts depending only on how its inner
     products are summed.  The FP64 count must lie inside the spread of eight
-    valid summation orders, widened by 3% + 2; phi must agree to 1e-10."""
+    valid summation orders, widened by 3% + 2, and phi must agree to 1e-10.
+    Because the iteration paths differ, two solves that both stop at residual
+    1e-10 can differ by more than 1e-10 in phi on this grid (the oracle's own
+    1e-10 solution is 2e-11 from its 1e-12 one, another path's 1.2e-10), so the
+    FP64 comparison is made at residual 1e-12; the FP32-vector refinement form
+    runs to 1e-10 and must agree to 1e-7."""
+    tol = 1e-12 if prec == "fp64" else 1e-10
     r, th, ph, rho = _sph_problem()
     phi_o = np.zeros(rho.shape)
-    info_o = OS.solve_spherical(rho, phi_o, r, th, ph, 1e-10, lmax=6)
-    counts = {name: OS.solve_spherical(rho, np.zeros(rho.shape), r, th, ph, 1e-10, lmax=6, dot=dot).iterations
+    info_o = OS.solve_spherical(rho, phi_o, r, th, ph, tol, lmax=6)
+    counts = {name: OS.solve_spherical(rho, np.zeros(rho.shape), r, th, ph, tol, lmax=6, dot=dot).iterations
               for name, dot in _dot_orders().items()}
     lo_it, hi_it = min(counts.values()), max(counts.values())
     phi_t = dev(np.zeros(rho.shape))
     with pkg.SphericalSolver(r, th, ph, bc="multipole", lmax=6) as s:
-        info = s.solve(dev(rho), phi_t, tol=1e-10, prec=prec, max_iter=5000)
+        info = s.solve(dev(rho), phi_t, tol=tol, prec=prec, max_iter=5000)
     assert info.converged, info
     got = host(phi_t)
     U = (slice(1, -1), slice(1, -1), slice(1, -1))
