@@ -308,12 +308,50 @@ __global__ void __launch_bounds__(BX* BY)
   }
 }
 
+// FP64 7-point on equal spacings: delta on the red nodes along (j, k)
+// diagonals (5 + 1 FP64 instructions per node, the order of k_sweep_diag) and
+// zero on the black member of each pair.
+__global__ void __launch_bounds__(BX* BY)
+    k_delta_skip_diag(Dims d, double c1, const double* __restrict__ phi, const double* __restrict__ fs,
+                      int dl, double* __restrict__ out) {
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
+  const int kn0 = blockIdx.z * dl + 1;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kn0 + 1));
+  if (u0 >= u1) return;
+  const int p = (1 + jn0 + kn0) & 1;            // red member of the pair
+  const int in = 1 + 2 * t + p, ib = 1 + 2 * t + (1 - p);
+  if (in > ni && ib > ni) return;
+  const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
+  long long c = d.at(in, jn0 + u0, kn0 + u0);
+  const long long cb = ib - in;                 // offset of the black member
+  double qprev = in <= ni ? phi[c - sy] + phi[c - sz] : 0.0;
+  for (int u = u0; u < u1; u++, c += step) {
+    if (in <= ni) {
+      const double q = phi[c + sy] + phi[c + sz];
+      out[c] = fma(((phi[c + 1] + phi[c - 1]) + qprev) + q, c1, fs[c]) - phi[c];
+      qprev = q;
+    }
+    if (ib <= ni) out[c + cb] = 0.0;
+  }
+}
+
 template <int G, bool ISO, typename T, typename TO>
 static cudaError_t delta_skip_t(const Dims& d, const double h[3], int order, const void* phi,
                                 const void* fs, void* out, cudaStream_t s) {
   using C = typename St<T>::C;
   constexpr int NCOL = G == 1 ? 2 : 3;
   Coef<C> cf = make_coef<C>(d, h, order);
+  if constexpr (G == 1 && ISO && sizeof(T) == 8 && sizeof(TO) == 8) {
+    const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+    const int pairs = (d.ni() + 1) / 2;
+    const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
+    k_delta_skip_diag<<<grid, dim3(BX, BY), 0, s>>>(d, (double)cf.c1[0], (const double*)phi, (const double*)fs,
+                                                     dl, (double*)out);
+    return cudaGetLastError();
+  }
   const int per_row = (d.ni() + NCOL - 1) / NCOL;
   const int gx = (per_row + BX - 1) / BX, gy = (d.nj() + BY - 1) / BY;
   const int zc = zchunk_for(gx * gy, d.nk());
@@ -480,7 +518,7 @@ static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* ph
   Coef<C> cf = make_coef<C>(d, h, order);
   if constexpr (G == 1 && ISO && sizeof(T) == sizeof(double)) {
     // diagonal walks of dl nodes (any dl gives the same result)
-    const int dl = d.nk() >= 64 ? 16 : 4;
+    const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
     const int pairs = (d.ni() + 1) / 2;
     const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
     if (omega == 1.0 && wtab == nullptr)

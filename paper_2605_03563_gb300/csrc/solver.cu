@@ -454,7 +454,8 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
     // colour's residual is exactly zero and is not evaluated (not for BF16
     // storage, where it is the rounding error of the stored value)
     const double frac = h->order == 2 ? 0.5 : 2.0 / 3.0;
-    if (l == 0) prof_begin(h, PC_DELTA0, w.n * (w.S * (1.0 + frac) + w.St), w.n * frac * (6.0 * w.G + 1.0), w.fp64, s);
+    const bool diag = h->order == 2 && L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
+    if (l == 0) prof_begin(h, PC_DELTA0, w.n * (w.S * (1.0 + frac) + w.St), w.n * frac * ((diag ? 5.0 : 6.0 * w.G) + 1.0), w.fp64, s);
     e = (h->nlaunch += 1, launch_delta_after_sweep(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
@@ -492,7 +493,8 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
   const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
   if (after_sweep && out == nullptr) {
     const double frac = h->order == 2 ? 0.5 : 2.0 / 3.0;   // colours evaluated
-    prof_begin(h, PC_NORM0, n * 8.0 * (1.0 + frac), n * frac * (6.0 * G + 2.0), 1, s);
+    const bool diag = h->order == 2 && h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2];   // diagonal walks
+    prof_begin(h, PC_NORM0, n * 8.0 * (1.0 + frac), n * frac * ((diag ? 5.0 : 6.0 * G) + 2.0), 1, s);
     int nb = 0;
     cudaError_t e = (h->nlaunch += 1, launch_delta_colours(h->d0, h->order, h->h0, phi, h->fs64, h->partials, &nb, s));
     prof_end(h, s);

@@ -705,6 +705,55 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// FP64 7-point on equal spacings: the red residuals along (j, k) diagonals,
+// with the pair sum (N + U) of one node carried as the (S + D) of the next, in
+// the order of the diagonal colour pass (5 + 1 FP64 instructions per node).
+// Layout of the walks as in k_sweep_diag (x pair per thread, dl nodes per walk).
+static int diag_walk(int nk) { return nk >= 200 ? 16 : (nk >= 64 ? 8 : 4); }
+static dim3 diag_grid(const Dims& d) {
+  const int dl = diag_walk(d.nk());
+  const int pairs = (d.ni() + 1) / 2;
+  return dim3((pairs + 31) / 32, (d.nj() + dl - 1 + 7) / 8, (d.nk() + dl - 1) / dl);
+}
+
+__global__ void __launch_bounds__(256)
+    k_delta_red_diag(Dims d, double c1, const double* __restrict__ phi, const double* __restrict__ fs, int dl,
+                     double* __restrict__ partials) {
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  const int jn0 = blockIdx.y * 8 + threadIdx.y + 2 - dl;
+  const int kn0 = blockIdx.z * dl + 1;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kn0 + 1));
+  const int in = 1 + 2 * t + ((1 + jn0 + kn0) & 1);   // the red member of the pair
+  double s2 = 0.0;
+  if (u0 < u1 && in <= ni) {
+    const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
+    long long c = d.at(in, jn0 + u0, kn0 + u0);
+    double qprev = phi[c - sy] + phi[c - sz];
+    for (int u = u0; u < u1; u++, c += step) {
+      const double q = phi[c + sy] + phi[c + sz];
+      const double dl_ = fma(((phi[c + 1] + phi[c - 1]) + qprev) + q, c1, fs[c]) - phi[c];
+      s2 = fma(dl_, dl_, s2);
+      qprev = q;
+    }
+  }
+  __shared__ double sh[8];
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  s2 = warp_sum(s2);
+  if ((tid & 31) == 0) sh[tid >> 5] = s2;
+  __syncthreads();
+  if (tid < 32) {
+    double a = tid < 8 ? sh[tid] : 0.0;
+    a = warp_sum(a);
+    if (tid == 0) {
+      const int b = block_linear_id();
+      partials[2 * b] = a;
+      partials[2 * b + 1] = 0.0;
+    }
+  }
+}
+
 static dim3 delta_colours_grid(const Dims& d, int order) {
   const int ncol = order == 2 ? 2 : 3;
   const int per_row = (d.ni() + ncol - 1) / ncol;
@@ -715,17 +764,23 @@ static dim3 delta_colours_grid(const Dims& d, int order) {
 }
 
 int delta_colours_partials(const Dims& d, int order) {
-  const dim3 g = delta_colours_grid(d, order);
-  return (int)(g.x * g.y * g.z);
+  const dim3 g = delta_colours_grid(d, order), gd = diag_grid(d);
+  return (int)std::max(g.x * g.y * g.z, order == 2 ? gd.x * gd.y * gd.z : 0u);
 }
 
 cudaError_t launch_delta_colours(const Dims& d, int order, const double h[3], const double* phi,
                                  const double* fs, double* partials, int* nblocks, cudaStream_t s) {
-  const dim3 grid = delta_colours_grid(d, order);
-  if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
   Coef<double> cf = make_coef<double>(d, h, order);
   const bool iso = h[0] == h[1] && h[1] == h[2];
   const dim3 blk(32, 8);
+  if (order == 2 && iso) {
+    const dim3 gd = diag_grid(d);
+    if (nblocks) *nblocks = (int)(gd.x * gd.y * gd.z);
+    k_delta_red_diag<<<gd, blk, 0, s>>>(d, cf.c1[0], phi, fs, diag_walk(d.nk()), partials);
+    return cudaGetLastError();
+  }
+  const dim3 grid = delta_colours_grid(d, order);
+  if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
   if (order == 2) {
     if (iso) k_delta_colours<1, true><<<grid, blk, 0, s>>>(d, cf, phi, fs, partials);
     else k_delta_colours<1, false><<<grid, blk, 0, s>>>(d, cf, phi, fs, partials);
