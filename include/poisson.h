@@ -243,6 +243,10 @@ void poisson_destroy(ps_handle h);
  * red-black sweep of FP32/BF16 levels whenever ps_solve_opts.use_tuning is 1:
  *   sweep_tile 0 = the storage type's default, 1 = 4 rows per warp x 4 warps
  *   (64 x 16 tile), 2 = 2 x 4 (64 x 8), 3 = 8 x 4 (64 x 32), 4 = 4 x 8 (64 x 32);
+ * and the tile shape of the fused residual + restriction of FP32/BF16 7-point
+ * levels:
+ *   restrict_tile 0 = the default (3), 1 = 4 coarse rows per warp x 4 warps
+ *   (32 x 16 coarse tile), 2 = 2 x 4 (32 x 8), 3 = 3 x 4 (32 x 12);
  * every shape gives the same result bit for bit.  The autotuner times whole
  * solves per (grid size, order, precision, tolerance) and a caller installs
  * its choice here; solves without use_tuning are unaffected. */
@@ -251,7 +255,7 @@ typedef struct {
   int32_t inner_cycles;    /* >= 1 (mixed precisions) */
   int32_t tile_min_n;      /* as ps_solve_opts.tile_min_n */
   int32_t sweep_tile;      /* 0 .. 4 */
-  int32_t reserved_;       /* set to 0 */
+  int32_t restrict_tile;   /* 0 .. 3 */
 } ps_tuning;
 
 /* Install (t != NULL) or clear (t == NULL) the tuning of precision prec
@@ -347,8 +351,8 @@ typedef struct {
   char name[32];
   int64_t launches;
   double total_ms;
-  double bytes_per_launch;   /* algorithmic bytes of one launch */
-  double ops_per_launch;     /* arithmetic instructions of one launch (FMA = 1) */
+  double bytes_per_launch;   /* algorithmic bytes of one launch (mean over the class's launches) */
+  double ops_per_launch;     /* arithmetic instructions of one launch (FMA = 1; mean) */
   int32_t fp64;              /* 1 when the arithmetic runs on the FP64 pipe */
   int32_t variant;           /* tile shape of the last timed launch (fused sweeps: 1..4), else 0 */
 } ps_kernel_stat;

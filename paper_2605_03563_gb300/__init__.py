@@ -108,9 +108,10 @@ class _Handle:
         return out
 
     # ---- tuned settings (poisson_set_tuning)
-    def set_tuning(self, prec, nu1=2, nu2=2, inner_cycles=1, tile_min_n=0, sweep_tile=0):
+    def set_tuning(self, prec, nu1=2, nu2=2, inner_cycles=1, tile_min_n=0, sweep_tile=0, restrict_tile=0):
         """Install the tuned multigrid settings used by solves with tuned=True."""
-        t = capi.PsTuning(int(nu1), int(nu2), int(inner_cycles), int(tile_min_n), int(sweep_tile), 0)
+        t = capi.PsTuning(int(nu1), int(nu2), int(inner_cycles), int(tile_min_n), int(sweep_tile),
+                          int(restrict_tile))
         check(lib().poisson_set_tuning(self._h, PRECISIONS[prec], C.byref(t)), "poisson_set_tuning")
 
     def clear_tuning(self, prec):
@@ -125,7 +126,7 @@ class _Handle:
         if not is_set.value:
             return None
         return dict(nu1=t.nu1, nu2=t.nu2, inner_cycles=t.inner_cycles, tile_min_n=t.tile_min_n,
-                    sweep_tile=t.sweep_tile)
+                    sweep_tile=t.sweep_tile, restrict_tile=t.restrict_tile)
 
     def __enter__(self):
         return self
@@ -236,7 +237,8 @@ class CartesianSolver(_Handle):
         if not e:
             self.clear_tuning(prec)
             return None
-        self.set_tuning(prec, e["nu1"], e["nu2"], e["inner"], e.get("tile_min_n", 0), e.get("sweep_tile", 0))
+        self.set_tuning(prec, e["nu1"], e["nu2"], e["inner"], e.get("tile_min_n", 0), e.get("sweep_tile", 0),
+                        e.get("restrict_tile", 0))
         return self.get_tuning(prec)
 
 

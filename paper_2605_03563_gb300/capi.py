@@ -55,7 +55,7 @@ class PsKernelStat(C.Structure):
 
 class PsTuning(C.Structure):
     _fields_ = [("nu1", C.c_int32), ("nu2", C.c_int32), ("inner_cycles", C.c_int32),
-                ("tile_min_n", C.c_int32), ("sweep_tile", C.c_int32), ("reserved_", C.c_int32)]
+                ("tile_min_n", C.c_int32), ("sweep_tile", C.c_int32), ("restrict_tile", C.c_int32)]
 
 
 # exported symbol -> (restype, argtypes)

@@ -114,6 +114,7 @@ struct Active {
   bool plain_steps = false;
   bool count_replacements = false;   // inner_cycles reports FP32 BiCGSTAB residual replacements
   int sweep_tile = 0;                 // tile variant of the fused FP32/BF16 sweeps (0 = default)
+  int restrict_tile = 0;              // tile variant of the fused FP32/BF16 residual + restriction
   long long body_kernels = 0;
   int inner_per_iter = 0;
 };
@@ -216,6 +217,15 @@ ps_status fail(ps_status s, const char* fmt, ...) {
   g_err = buf;
   return s;
 }
+
+// Arithmetic instructions per fine node of the grid-transfer kernels (FMA = 1).
+// Full weighting: per coarse node two carried plane sums of 8 (three row sums of
+// an add and an FMA, then an add and an FMA), the z-triple (add, FMA) and the
+// scale: 19 per 8 fine nodes.  Trilinear prolongation: per coarse cell one face
+// (4 midpoints of an add and a multiply), 4 z-midpoints and 8 accumulations:
+// 24 per 8 fine nodes.
+constexpr double kRestrictOps = 19.0 / 8.0;
+constexpr double kProlongOps = 3.0;
 
 // Profiler: begin/end pair around one launch on stream s.
 void prof_begin(ps_ctx* h, int cls, double bytes, double ops, int fp64, cudaStream_t s, int variant = 0) {
@@ -445,8 +455,9 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
   if ((e = smooth(h, L, l, nu1, s)) != cudaSuccess) return e;
   Level& Cl = H.lv[l + 1];
   if (use_tiles(h, L, l)) {
-    if (l == 0) prof_begin(h, PC_RESTRICT_FUSED0, w.n * 2.0 * w.S + w.n / 8.0 * dt_size(Cl.dt), w.n * (6.0 * w.G + 3.0), w.fp64, s);
-    e = (h->nlaunch += 1, launch_resid_restrict(L.d, Cl.d, h->order, L.h, L.dt, L.phi, L.fs, Cl.dt, Cl.fs, 4.0, &h->st->fault, s));
+    const int rtile = h->order == 2 ? (h->act.restrict_tile != 0 ? h->act.restrict_tile : rr_default_tile(L.dt)) : 0;
+    if (l == 0) prof_begin(h, PC_RESTRICT_FUSED0, w.n * 2.0 * w.S + w.n / 8.0 * dt_size(Cl.dt), w.n * (6.0 * w.G + 3.0), w.fp64, s, rtile);
+    e = (h->nlaunch += 1, launch_resid_restrict(L.d, Cl.d, h->order, L.h, L.dt, L.phi, L.fs, Cl.dt, Cl.fs, 4.0, &h->st->fault, s, rtile));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
   } else if (nu1 >= 1 && L.dt != DT_BF16) {
@@ -459,7 +470,7 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
     e = (h->nlaunch += 1, launch_delta_after_sweep(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
-    if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * 4.5, w.St == 8.0, s);
+    if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * kRestrictOps, w.St == 8.0, s);
     e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
@@ -468,14 +479,14 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
     e = (h->nlaunch += 1, launch_delta(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, 1.0, false, nullptr, nullptr, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
-    if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * 4.5, w.St == 8.0, s);
+    if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * kRestrictOps, w.St == 8.0, s);
     e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(Cl.phi, 0, (size_t)Cl.d.size() * dt_size(Cl.dt), s)) != cudaSuccess) return e;
   if ((e = vcycle(h, H, l + 1, nu1, nu2, s)) != cudaSuccess) return e;
-  if (l == 0) prof_begin(h, PC_PROLONG0, w.n * 2.0 * w.S + w.n / 8.0 * dt_size(Cl.dt), w.n * 4.0, w.fp64, s);
+  if (l == 0) prof_begin(h, PC_PROLONG0, w.n * 2.0 * w.S + w.n / 8.0 * dt_size(Cl.dt), w.n * kProlongOps, w.fp64, s);
   e = (h->nlaunch += 1, launch_prolong(L.d, Cl.d, Cl.dt, Cl.phi, L.dt, L.phi, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
@@ -625,7 +636,7 @@ ps_status begin_ir(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   };
   h->act.key = "ir" + std::to_string(p) + ":" + std::to_string(nu1) + ":" + std::to_string(nu2) +
                ":" + std::to_string(inner) + ":" + std::to_string(o->tile_min_n) + ":" +
-               std::to_string(h->act.sweep_tile);
+               std::to_string(h->act.sweep_tile) + ":" + std::to_string(h->act.restrict_tile);
   h->act.chunk = MG_CHUNK;
   h->act.plain_chunk = 1;
   h->act.inner_per_iter = inner;
@@ -816,13 +827,13 @@ cudaError_t vcycle_compact(ps_ctx* h, Hier* H, const CompactLevels& C, int l, in
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
   Level& Cl = H->lv[l + 1];
-  if (l == 0) prof_begin(h, PC_RESTRICT0, n * S * 9.0 / 8.0, n * 4.5, fp64, s);
+  if (l == 0) prof_begin(h, PC_RESTRICT0, n * S * 9.0 / 8.0, n * kRestrictOps, fp64, s);
   e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, dt, r, Cl.dt, Cl.fs, 1.0, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(Cl.phi, 0, (size_t)Cl.d.size() * dt_size(Cl.dt), s)) != cudaSuccess) return e;
   if ((e = vcycle_compact(h, H, C, l + 1, nu1, nu2, s)) != cudaSuccess) return e;
-  if (l == 0) prof_begin(h, PC_PROLONG0, n * S * 17.0 / 8.0, n * 4.0, fp64, s);
+  if (l == 0) prof_begin(h, PC_PROLONG0, n * S * 17.0 / 8.0, n * kProlongOps, fp64, s);
   e = (h->nlaunch += 1, launch_prolong(L.d, Cl.d, Cl.dt, Cl.phi, dt, u, s));
   if (l == 0) prof_end(h, s);
   if (e != cudaSuccess) return e;
@@ -1232,8 +1243,8 @@ ps_status step_active(ps_ctx* h, int k) {
         ProfAcc& a = h->acc[rec.cls];
         a.n++;
         a.ms += ms;
-        a.bytes = rec.bytes;
-        a.ops = rec.ops;
+        a.bytes += rec.bytes;
+        a.ops += rec.ops;
         a.fp64 = rec.fp64;
         a.variant = rec.variant;
       }
@@ -1526,6 +1537,8 @@ ps_status poisson_set_tuning(ps_handle h, int prec, const ps_tuning* t) {
   if (t->inner_cycles < 1 || t->inner_cycles > 64) return fail(PS_ERR_INVALID_ARG, "tuning: inner_cycles in 1..64");
   if (t->sweep_tile < 0 || t->sweep_tile > kRbSweepTiles)
     return fail(PS_ERR_INVALID_ARG, "tuning: sweep_tile in 0..%d", kRbSweepTiles);
+  if (t->restrict_tile < 0 || t->restrict_tile > kRrTiles)
+    return fail(PS_ERR_INVALID_ARG, "tuning: restrict_tile in 0..%d", kRrTiles);
   h->tun[prec] = *t;
   h->has_tun[prec] = 1;
   return PS_OK;
@@ -1726,7 +1739,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   if (opts) o = *opts;
   if (o.max_iter < 0) return fail(PS_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (o.prec < PS_FP64 || o.prec > PS_MIXED_BF16) return fail(PS_ERR_INVALID_ARG, "unknown precision %d", o.prec);
-  int sweep_tile = 0;
+  int sweep_tile = 0, restrict_tile = 0;
   if (o.use_tuning && !h->sph && o.method == PS_MG && h->has_tun[o.prec]) {
     const ps_tuning& t = h->tun[o.prec];
     o.nu1 = t.nu1;
@@ -1734,6 +1747,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
     o.inner_cycles = t.inner_cycles;
     o.tile_min_n = t.tile_min_n;
     sweep_tile = t.sweep_tile;
+    restrict_tile = t.restrict_tile;
   }
   if (o.sor_schedule < PS_SOR_FIXED || o.sor_schedule > PS_SOR_OPTIMAL)
     return fail(PS_ERR_INVALID_ARG, "unknown SOR schedule %d", o.sor_schedule);
@@ -1767,6 +1781,7 @@ ps_status poisson_solve_begin(ps_handle h, const double* rho_dev, double* phi_de
   a = Active();
   a.o = o;
   a.sweep_tile = sweep_tile;
+  a.restrict_tile = restrict_tile;
   a.tol = tol;
   a.rho = rho_dev;
   a.phi_user = phi_dev;
@@ -2097,8 +2112,8 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
       Acc& a = acc[r.cls];
       a.n++;
       a.ms += ms;
-      a.bytes = r.bytes;
-      a.ops = r.ops;
+      a.bytes += r.bytes;
+      a.ops += r.ops;
       a.fp64 = r.fp64;
       a.variant = r.variant;
     }
@@ -2115,8 +2130,10 @@ int poisson_profile_read(ps_handle h, ps_kernel_stat* out, int max) {
       snprintf(o.name, sizeof(o.name), "%s", kProfNames[c]);
       o.launches = acc[c].n;
       o.total_ms = acc[c].ms;
-      o.bytes_per_launch = acc[c].bytes;
-      o.ops_per_launch = acc[c].ops;
+      // a class can mix launches of different work (a full residual and a
+      // one-colour residual are both convergence passes): report the mean
+      o.bytes_per_launch = acc[c].bytes / (double)acc[c].n;
+      o.ops_per_launch = acc[c].ops / (double)acc[c].n;
       o.fp64 = acc[c].fp64;
       o.variant = acc[c].variant;
     }

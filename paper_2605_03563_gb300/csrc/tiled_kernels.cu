@@ -594,6 +594,280 @@ __global__ void __launch_bounds__(NT)
   if (!ok && fault != nullptr) atomicExch(fault, 1);
 }
 
+// ------------------------------------------------------------------ register-blocked (7-point)
+// The FP32/BF16 7-point levels use k_resid_restrict_rb; the shared-memory
+// kernel above serves the 13-point operator and FP64 levels.
+
+// Block = NWC warps over a tile of 32 x TYC coarse nodes (TYC = RC NWC), i.e.
+// 64 fine columns.  Warp w owns the coarse rows Jw .. Jw+RC-1 (Jw = J0 + w RC)
+// and the fine residual rows 2Jw-1 .. 2Jw+2RC-1 (ND = 2RC+1 rows: the last is
+// also the first of the next strip and is computed by both); lane l owns the
+// fine x pair (2I, 2I+1), I = I0 + l, i.e. coarse column I.  Each step of the
+// z-march computes the residual of one fine plane z:
+//   * phi of planes z-1 and z is held in registers (rows -1 .. ND of the
+//     strip), plane z+1 is read from the staged ring, and the three roles
+//     rotate through three register arrays from step to step;
+//   * x neighbours come from the adjacent lane by shuffle (the tile's edge
+//     columns from the staged plane), and lanes 0 .. ND-1 compute the residual
+//     at x = 2 I0 - 1 (left of the tile) for row l+1, handed to lane 0;
+//   * full weighting runs in registers: a row sum per fine row (the 2I-1 term
+//     by shuffle), the (y-1, y, y+1) combination per coarse row, and the
+//     (z-1, z, z+1) combination of carried plane sums when z closes a coarse
+//     plane.
+// The residual and every weighted sum are formed in the order of
+// k_resid_restrict, so both kernels give the same coarse right-hand side bit
+// for bit.
+template <typename T, int RC, int NWC, int NS>
+struct RrbGeom {
+  static constexpr int TX = 64, TXC = 32, TYC = RC * NWC, NTH = 32 * NWC;
+  static constexpr int ND = 2 * RC + 1;    // fine residual rows of a strip
+  static constexpr int NPR = ND + 2;       // phi rows of a strip
+  static constexpr int XH = xhalo<T>();    // >= 4 columns: covers x0 - 2
+  static constexpr int WP = TX + 2 * XH;   // staged row width
+  static constexpr int HP = 2 * TYC + 3;   // phi rows 2J0-2 .. 2J0+2TYC
+  static constexpr int HF = 2 * TYC + 1;   // fs rows  2J0-1 .. 2J0+2TYC-1
+  static constexpr int PBYTES = WP * HP * (int)sizeof(T), FBYTES = WP * HF * (int)sizeof(T);
+  static constexpr int PB = align_up(PBYTES, 128), FB = align_up(FBYTES, 128);
+  static constexpr int SMEM = NS * (PB + FB) + NS * 8;
+};
+
+template <typename T, bool ISO, int RC, int NWC, int NS>
+struct RrbMarch {
+  using S = St<T>;
+  using Gm = RrbGeom<T, RC, NWC, NS>;
+  static constexpr int WP = Gm::WP, ND = Gm::ND, NPR = Gm::NPR;
+  static constexpr int PBE = Gm::PB / (int)sizeof(T), FBE = Gm::FB / (int)sizeof(T);
+  static constexpr unsigned FULL = 0xffffffffu;
+
+  const T* Pst;
+  const T* Fst;
+  unsigned long long* bar;
+  Coef<float> cf;
+  float sc;
+  int l, pofs, hofs, hfofs, nfz, K0, K1, dir;
+  unsigned rowin;    // bit i: fine row i of the strip (0 .. NPR-1) is interior
+  bool ain, bin;     // the pair's nodes are interior in x
+  bool hin;          // lane l < ND: the halo node (2 I0 - 1, row l + 1) is interior in x and y
+  unsigned jok;      // bit j: coarse row Jw + j is interior; 0 if coarse column I is not
+  float* o;          // coarse node (I, Jw, 0)
+  long long cpy, cpz;
+  bool ok;
+  int wq, qm, q0, q1;
+  unsigned wph;
+  float pm[RC], p0[RC];   // plane sums of the last odd and the last even fine plane
+
+  __device__ __forceinline__ void wait_next() {
+    mbar_wait(&bar[wq], wph, ok);
+    if (++wq == NS) { wq = 0; wph ^= 1u; }
+  }
+
+  // residual of fine plane z from Zm (the plane before z in the march), A
+  // (plane z); Z1 <- the plane after z.  z -/+ 1 enter only as the sum
+  // Z1 + Zm, the same value in either direction.
+  __device__ __forceinline__ void step(int z, const float2 (&Zm)[NPR], const float2 (&A)[NPR], float2 (&Z1)[NPR]) {
+    wait_next();   // plane z + dir (with fs of plane z)
+    const T* Pm = Pst + qm * PBE;
+    const T* P0 = Pst + q0 * PBE;
+    const T* P1 = Pst + q1 * PBE;
+    const T* F = Fst + q1 * FBE;
+#pragma unroll
+    for (int i = 0; i < NPR; i++) Z1[i] = ld_pair(P1 + pofs + i * WP);
+    const bool zin = z >= 1 && z < nfz;
+    // residual left of the tile, row l + 1 (lanes 0 .. ND-1)
+    float hd = 0.f;
+    if (l < ND) {
+      const float ax = S::ld(P0 + hofs + 1) + S::ld(P0 + hofs - 1);
+      const float ay = S::ld(P0 + hofs + WP) + S::ld(P0 + hofs - WP);
+      const float az = S::ld(P1 + hofs) + S::ld(Pm + hofs);
+      const float v = gs7<ISO>(ax, ay, az, S::ld(F + hfofs), cf);
+      if (zin && hin) hd = v - S::ld(P0 + hofs);
+    }
+    float rs[ND];   // row sums of coarse column I, fine rows 1 .. ND
+#pragma unroll
+    for (int i = 1; i <= ND; i++) {
+      const float2 a = A[i];
+      float lf = __shfl_up_sync(FULL, a.y, 1);
+      if (l == 0) lf = S::ld(P0 + pofs + i * WP - 1);
+      float rt = __shfl_down_sync(FULL, a.x, 1);
+      if (l == 31) rt = S::ld(P0 + pofs + i * WP + 2);
+      const float2 f = ld_pair(F + pofs + (i - 1) * WP);
+      const float va = gs7<ISO>(a.y + lf, A[i + 1].x + A[i - 1].x, Z1[i].x + Zm[i].x, f.x, cf);
+      const float vb = gs7<ISO>(rt + a.x, A[i + 1].y + A[i - 1].y, Z1[i].y + Zm[i].y, f.y, cf);
+      const bool rin = zin && ((rowin >> i) & 1u);
+      const float da = rin && ain ? va - a.x : 0.f;
+      const float db = rin && bin ? vb - a.y : 0.f;
+      float nb = __shfl_up_sync(FULL, db, 1);
+      const float hv = __shfl_sync(FULL, hd, i - 1);
+      if (l == 0) nb = hv;
+      rs[i - 1] = (nb + db) + 2.f * da;
+    }
+    if ((z & 1) == 0) {
+#pragma unroll
+      for (int j = 0; j < RC; j++) p0[j] = (rs[2 * j] + rs[2 * j + 2]) + 2.f * rs[2 * j + 1];
+    } else {
+      // odd z closes coarse plane K = (z - dir) / 2: its planes 2K -/+ 1 enter
+      // as the sum pm + pl, the same value in either direction
+      const int K = (z - dir) / 2;
+#pragma unroll
+      for (int j = 0; j < RC; j++) {
+        const float pl = (rs[2 * j] + rs[2 * j + 2]) + 2.f * rs[2 * j + 1];
+        if (K >= K0 && K < K1 && ((jok >> j) & 1u)) o[j * cpy + K * cpz] = ((pm[j] + pl) + 2.f * p0[j]) * sc;
+        pm[j] = pl;
+      }
+    }
+  }
+};
+
+// Blocks of odd z-chunks march down, even ones up: the fine planes two
+// adjacent chunks both read are then read by both near the same time (both at
+// the start or both at the end of their marches), so the second read hits L2.
+template <typename T, bool ISO, int RC, int NWC, int NS>
+__global__ void __launch_bounds__(32 * NWC, 2)
+    k_resid_restrict_rb(const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mF, Dims fd,
+                        Dims cd, Coef<float> cf, float* __restrict__ fsc, float sc, int kc,
+                        int* __restrict__ fault) {
+  using Gm = RrbGeom<T, RC, NWC, NS>;
+  using M = RrbMarch<T, ISO, RC, NWC, NS>;
+  constexpr int WP = Gm::WP, XH = Gm::XH, ND = Gm::ND, NPR = Gm::NPR, PBE = M::PBE, FBE = M::FBE;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* Pst = reinterpret_cast<T*>(smem);
+  T* Fst = reinterpret_cast<T*>(smem + NS * Gm::PB);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + NS * (Gm::PB + Gm::FB));
+
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const int I0 = blockIdx.x * Gm::TXC, J0 = blockIdx.y * Gm::TYC;
+  const int K0 = 1 + blockIdx.z * kc;
+  const int K1 = min(K0 + kc, cd.nz);   // coarse planes [K0, K1)
+  const int x0 = 2 * I0;
+  const int dir = (blockIdx.z & 1) ? -1 : 1;
+  const int np = 2 * (K1 - K0) + 3;                // staged phi planes 2K0-2 .. 2K1, t = 0 .. np-1
+  const int pfirst = dir > 0 ? 2 * K0 - 2 : 2 * K1;  // plane of t = 0
+  if (tid == 0) {
+    for (int q = 0; q < NS; q++) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // stage of the t-th phi plane p also carries fs of plane p - dir (t >= 2: a residual plane)
+  auto issue = [&](int t) {
+    if (t >= np) return;
+    const int q = t % NS;
+    const int p = pfirst + dir * t;
+    const bool withf = t >= 2;
+    mbar_expect_tx(&bar[q], Gm::PBYTES + (withf ? Gm::FBYTES : 0));
+    tma_load_3d(Pst + q * PBE, &mP, x0 - XH, 2 * J0 - 2, p, &bar[q]);
+    if (withf) tma_load_3d(Fst + q * FBE, &mF, x0 - XH, 2 * J0 - 1, p - dir, &bar[q]);
+  };
+  if (tid == 0)
+    for (int t = 0; t < NS; t++) issue(t);
+
+  M m;
+  m.Pst = Pst;
+  m.Fst = Fst;
+  m.bar = bar;
+  m.cf = cf;
+  m.sc = sc;
+  m.l = l;
+  m.nfz = fd.nz;
+  m.K0 = K0;
+  m.K1 = K1;
+  m.dir = dir;
+  const int Jw = J0 + w * RC;
+  const int y0 = 2 * Jw - 2;   // fine row of strip row 0
+  const int brow = 2 * w * RC;  // staged phi row of strip row 0; staged fs row of strip row 1
+  m.pofs = brow * WP + XH + 2 * l;
+  m.hofs = (brow + l + 1) * WP + XH - 1;
+  m.hfofs = (brow + l) * WP + XH - 1;
+  unsigned rowin = 0;
+#pragma unroll
+  for (int i = 0; i < NPR; i++)
+    if (y0 + i >= 1 && y0 + i < fd.ny) rowin |= 1u << i;
+  m.rowin = rowin;
+  const int xa = x0 + 2 * l;
+  m.ain = xa >= 1 && xa < fd.nx;
+  m.bin = xa + 1 < fd.nx;
+  m.hin = l < ND && x0 - 1 >= 1 && ((rowin >> (l + 1)) & 1u);
+  const int I = I0 + l;
+  unsigned jok = 0;
+  if (I >= 1 && I < cd.nx) {
+#pragma unroll
+    for (int j = 0; j < RC; j++)
+      if (Jw + j >= 1 && Jw + j < cd.ny) jok |= 1u << j;
+  }
+  m.jok = jok;
+  m.o = fsc + cd.at(min(I, cd.ex - 1), min(Jw, cd.ey - 1), 0);
+  m.cpy = cd.sy();
+  m.cpz = cd.sz();
+  m.ok = true;
+  m.wq = 0;
+  m.wph = 0;
+#pragma unroll
+  for (int j = 0; j < RC; j++) m.pm[j] = m.p0[j] = 0.f;
+
+  float2 X[NPR], Y[NPR], W[NPR];
+  m.wait_next();   // t = 0
+  m.wait_next();   // t = 1
+#pragma unroll
+  for (int i = 0; i < NPR; i++) {
+    X[i] = ld_pair(Pst + m.pofs + i * WP);
+    Y[i] = ld_pair(Pst + PBE + m.pofs + i * WP);
+  }
+  m.qm = 0;
+  m.q0 = 1;
+  m.q1 = 2 % NS;
+  auto release = [&](int t) {   // the stage of plane t - 1 takes plane t - 1 + NS
+    __syncthreads();
+    if (tid == 0 && m.ok) {     // after a failed wait no new copy is issued
+      fence_proxy_async();
+      issue(t - 1 + NS);
+    }
+    m.qm = m.q0;
+    m.q0 = m.q1;
+    m.q1 = m.q1 + 1 == NS ? 0 : m.q1 + 1;
+  };
+  const int tl = np - 2;   // residual planes t = 1 .. np-2
+  for (int t = 1; t <= tl; t += 3) {
+    m.step(pfirst + dir * t, X, Y, W);
+    release(t);
+    if (t + 1 <= tl) {
+      m.step(pfirst + dir * (t + 1), Y, W, X);
+      release(t + 1);
+    }
+    if (t + 2 <= tl) {
+      m.step(pfirst + dir * (t + 2), W, X, Y);
+      release(t + 2);
+    }
+  }
+  if (!m.ok && fault != nullptr) atomicExch(fault, 1);
+}
+
+template <typename T, bool ISO, int RC, int NWC, int NS>
+static cudaError_t rr_rb_t(const Dims& fd, const Dims& cd, const double h[3], const void* phi, const void* fs,
+                           void* fsc, double factor, int* fault, cudaStream_t s) {
+  using Gm = RrbGeom<T, RC, NWC, NS>;
+  auto kern = k_resid_restrict_rb<T, ISO, RC, NWC, NS>;
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, Gm::NTH, Gm::SMEM);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = std::max(1, blocks_per_sm);
+  }
+  const int dt = sizeof(T) == 4 ? DT_F32 : DT_BF16;
+  CUtensorMap mP, mF;
+  if (!encode_level_map(&mP, dt, phi, fd, Gm::WP, Gm::HP) || !encode_level_map(&mF, dt, fs, fd, Gm::WP, Gm::HF))
+    return cudaErrorInvalidValue;
+  const int gx = (cd.nx - 1) / Gm::TXC + 1, gy = (cd.ny - 1) / Gm::TYC + 1;
+  const int nk = cd.nz - 1;
+  const int slots = sm_count() * blocks_per_sm;
+  const int nchunk = std::max(1, std::min(nk, slots / (gx * gy)));
+  const int kc = (nk + nchunk - 1) / nchunk;
+  const dim3 grid(gx, gy, (nk + kc - 1) / kc);
+  const Coef<float> cf = make_coef<float>(fd, h, 2);
+  kern<<<grid, Gm::NTH, Gm::SMEM, s>>>(mP, mF, fd, cd, cf, (float*)fsc, (float)(factor / 64.0), kc, fault);
+  return cudaGetLastError();
+}
+
 template <typename TF, typename TC, int G, bool ISO>
 static cudaError_t rr_t(const Dims& fd, const Dims& cd, const double h[3], int order, const void* phi,
                         const void* fs, void* fsc, double factor, int* fault, cudaStream_t s) {
@@ -626,10 +900,34 @@ static cudaError_t rr_t(const Dims& fd, const Dims& cd, const double h[3], int o
   return cudaGetLastError();
 }
 
+// Tile variants of k_resid_restrict_rb (coarse rows per warp x warps per block,
+// 32 coarse columns, 5-stage ring): 1 = 4 x 4, 2 = 2 x 4, 3 = 3 x 4.  Every
+// variant gives the same coarse right-hand side bit for bit.  Default 3 (12
+// warps per SM; measured at 256^3 against 1 and 2, FP32 and BF16).
+int rr_default_tile(int) { return 3; }
+
+template <typename T, bool ISO>
+static cudaError_t rr_rb_tile(const Dims& fd, const Dims& cd, const double h[3], const void* phi, const void* fs,
+                              void* fsc, double factor, int* fault, int tile, cudaStream_t s) {
+  switch (tile) {
+    case 1: return rr_rb_t<T, ISO, 4, 4, 5>(fd, cd, h, phi, fs, fsc, factor, fault, s);
+    case 2: return rr_rb_t<T, ISO, 2, 4, 5>(fd, cd, h, phi, fs, fsc, factor, fault, s);
+    case 3: return rr_rb_t<T, ISO, 3, 4, 5>(fd, cd, h, phi, fs, fsc, factor, fault, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename TF, typename TC>
 static cudaError_t rr_dispatch(const Dims& fd, const Dims& cd, int order, const double h[3], const void* phi,
-                               const void* fs, void* fsc, double factor, int* fault, cudaStream_t s) {
+                               const void* fs, void* fsc, double factor, int* fault, int tile, cudaStream_t s) {
   const bool iso = h[0] == h[1] && h[1] == h[2];
+  if constexpr (!std::is_same<TF, double>::value && std::is_same<TC, float>::value) {
+    if (order == 2) {
+      if (tile == 0) tile = rr_default_tile(sizeof(TF) == 4 ? DT_F32 : DT_BF16);
+      return iso ? rr_rb_tile<TF, true>(fd, cd, h, phi, fs, fsc, factor, fault, tile, s)
+                 : rr_rb_tile<TF, false>(fd, cd, h, phi, fs, fsc, factor, fault, tile, s);
+    }
+  }
   if (order == 2)
     return iso ? rr_t<TF, TC, 1, true>(fd, cd, h, order, phi, fs, fsc, factor, fault, s)
                : rr_t<TF, TC, 1, false>(fd, cd, h, order, phi, fs, fsc, factor, fault, s);
@@ -639,10 +937,11 @@ static cudaError_t rr_dispatch(const Dims& fd, const Dims& cd, int order, const 
 
 cudaError_t launch_resid_restrict(const Dims& fine, const Dims& coarse, int order, const double h[3], int dt_f,
                                   const void* phi, const void* fs, int dt_c, void* fs_c,
-                                  double factor, int* fault, cudaStream_t s) {
-  if (dt_f == DT_F64 && dt_c == DT_F64) return rr_dispatch<double, double>(fine, coarse, order, h, phi, fs, fs_c, factor, fault, s);
-  if (dt_f == DT_F32 && dt_c == DT_F32) return rr_dispatch<float, float>(fine, coarse, order, h, phi, fs, fs_c, factor, fault, s);
-  if (dt_f == DT_BF16 && dt_c == DT_F32) return rr_dispatch<__nv_bfloat16, float>(fine, coarse, order, h, phi, fs, fs_c, factor, fault, s);
+                                  double factor, int* fault, cudaStream_t s, int tile) {
+  if (tile < 0 || tile > kRrTiles) return cudaErrorInvalidValue;
+  if (dt_f == DT_F64 && dt_c == DT_F64) return rr_dispatch<double, double>(fine, coarse, order, h, phi, fs, fs_c, factor, fault, tile, s);
+  if (dt_f == DT_F32 && dt_c == DT_F32) return rr_dispatch<float, float>(fine, coarse, order, h, phi, fs, fs_c, factor, fault, tile, s);
+  if (dt_f == DT_BF16 && dt_c == DT_F32) return rr_dispatch<__nv_bfloat16, float>(fine, coarse, order, h, phi, fs, fs_c, factor, fault, tile, s);
   return cudaErrorNotSupported;
 }
 

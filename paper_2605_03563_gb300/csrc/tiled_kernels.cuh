@@ -24,10 +24,15 @@ cudaError_t launch_rb_sweep(const Dims& d, int order, const double h[3], int dt,
 // Fused residual and full-weighting restriction (Sec. 2.1.3):
 // fs_coarse = factor * R(phi_GS(phi) - phi) without storing the fine residual.
 // Equal bit for bit to launch_delta into a buffer of the level's arithmetic
-// type followed by launch_restrict.
+// type followed by launch_restrict.  tile: 0 (the storage type's default, see
+// rr_default_tile) or one of the kRrTiles compiled tile shapes of the
+// register-blocked FP32/BF16 7-point kernel (ignored by the 13-point and FP64
+// kernel); every shape gives the same result bit for bit.
+constexpr int kRrTiles = 3;
+int rr_default_tile(int dt);
 cudaError_t launch_resid_restrict(const Dims& fine, const Dims& coarse, int order, const double h[3], int dt_f,
                                   const void* phi, const void* fs, int dt_c, void* fs_c,
-                                  double factor, int* fault, cudaStream_t s);
+                                  double factor, int* fault, cudaStream_t s, int tile = 0);
 
 // Residual norm pass after a completed omega = 1 colour sweep: nodes of the
 // last colour have delta = 0 exactly (the residual kernel repeats the sweep's

@@ -100,11 +100,11 @@ def test_hbm_budget_gates_admission(pkg):
 def test_autotuner_picks_a_converged_configuration(pkg):
     from paper_2605_03563_gb300 import autotune
     best = autotune.tune(32, prec="mixed_fp32", tol=1e-8, reps=1, cycles=[(1, 1), (2, 2)], inners=(1, 2),
-                         tiles=(1, 3))
+                         tiles=(1, 3), restrict_tiles=(1, 2))
     assert (best["nu1"], best["nu2"]) in [(1, 1), (2, 2)] and best["inner"] in (1, 2)
-    assert best["sweep_tile"] in (0, 1, 3)
+    assert best["sweep_tile"] in (0, 1, 3) and best["restrict_tile"] in (0, 1, 2)
     assert best["ms"] == min(t["ms"] for t in best["trials"])
-    assert len(best["trials"]) == 6
+    assert len(best["trials"]) == 8
 
 
 def test_tuned_tile_changes_the_launched_sweep_and_not_the_result(pkg, tmp_path):
@@ -124,28 +124,34 @@ def test_tuned_tile_changes_the_launched_sweep_and_not_the_result(pkg, tmp_path)
         info0 = s.solve(rho, ref, tol=tol, prec="mixed_fp32", nu1=1, nu2=2, inner_cycles=2)
         prof0 = s.profile_read()
         assert prof0["sweep_fused_finest"]["variant"] == 1          # FP32 default: 4 rows x 4 warps
-        s.set_tuning("mixed_fp32", nu1=1, nu2=2, inner_cycles=2, sweep_tile=3)
+        assert prof0["resid_restrict_finest"]["variant"] == 3       # 3 coarse rows x 4 warps
+        s.set_tuning("mixed_fp32", nu1=1, nu2=2, inner_cycles=2, sweep_tile=3, restrict_tile=2)
         assert s.get_tuning("mixed_fp32")["sweep_tile"] == 3
+        assert s.get_tuning("mixed_fp32")["restrict_tile"] == 2
         phi = torch.zeros_like(rho)
         info = s.solve(rho, phi, tol=tol, prec="mixed_fp32", tuned=True)   # nu1/nu2/inner from the tuning
         prof = s.profile_read()
         s.profile(False)
         assert prof["sweep_fused_finest"]["variant"] == 3
+        assert prof["resid_restrict_finest"]["variant"] == 2
         assert info.converged and info.iterations == info0.iterations
         assert info.inner_cycles == info0.inner_cycles
         assert torch.equal(phi, ref)
         # the same through the autotuner's table
         path = str(tmp_path / "table.json")
-        entry = {"nu1": 1, "nu2": 2, "inner": 2, "sweep_tile": 4, "tile_min_n": 0, "ms": 1.0, "trials": []}
+        entry = {"nu1": 1, "nu2": 2, "inner": 2, "sweep_tile": 4, "restrict_tile": 3, "tile_min_n": 0,
+                 "ms": 1.0, "trials": []}
         autotune.save({autotune.key(n, 2, "mixed_fp32", tol): entry}, path)
         got = s.use_table("mixed_fp32", tol, path)
-        assert got == {"nu1": 1, "nu2": 2, "inner_cycles": 2, "tile_min_n": 0, "sweep_tile": 4}
+        assert got == {"nu1": 1, "nu2": 2, "inner_cycles": 2, "tile_min_n": 0, "sweep_tile": 4,
+                       "restrict_tile": 3}
         assert s.use_table("mixed_fp32", 1e-6, path) is None and s.get_tuning("mixed_fp32") is None
         s.use_table("mixed_fp32", tol, path)
         s.profile(True)
         phi.zero_()
         s.solve(rho, phi, tol=tol, prec="mixed_fp32", tuned=True)
-        assert s.profile_read()["sweep_fused_finest"]["variant"] == 4
+        prof = s.profile_read()
+        assert prof["sweep_fused_finest"]["variant"] == 4 and prof["resid_restrict_finest"]["variant"] == 3
         s.profile(False)
         assert torch.equal(phi, ref)
     # the server starts a request of that size with the table's settings

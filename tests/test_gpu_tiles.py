@@ -74,3 +74,27 @@ def test_tiles_default_vs_oracle(pkg, n, order):
     assert info.iterations == info_o.iterations
     err = np.max(np.abs(phi - phi_o)) / np.max(np.abs(phi_o))
     assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("rtile", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["mixed_fp32", "mixed_bf16"])
+def test_every_restriction_tile_is_bitwise_equal(pkg, rtile, prec):
+    """Each compiled tile shape of the register-blocked residual + restriction
+    (z-chunks marching up and down) gives the two-kernel path's coarse
+    right-hand sides, hence the same solve bit for bit, on a grid ragged against
+    every tile (96 x 64 x 32 fine: 48 x 32 x 16 coarse against 32 x 8/12/16)."""
+    n, hi = (96, 64, 32), (1.0, 0.7, 0.45)
+    rho = np.abs(W.rng(5).standard_normal(W.cart_shape(n, 2)))
+    i_off, p_off = _solve(pkg, n, 2, hi, rho, prec, -1)
+    rho_t = torch.from_numpy(rho).cuda()
+    phi = torch.zeros_like(rho_t)
+    with pkg.CartesianSolver(n, 2, hi=hi, bc="multipole", lmax=4) as s:
+        s.set_tuning(prec, nu1=2, nu2=2, inner_cycles=2, tile_min_n=16, restrict_tile=rtile)
+        s.profile(True)
+        info = s.solve(rho_t, phi, tol=1e-10, method="mg", prec=prec, max_iter=60, tuned=True)
+        prof = s.profile_read()
+        s.profile(False)
+    torch.cuda.synchronize()
+    assert prof["resid_restrict_finest"]["variant"] == rtile
+    assert info.converged and info.iterations == i_off.iterations
+    assert np.array_equal(phi.cpu().numpy(), p_off)
