@@ -481,17 +481,16 @@ __global__ void __launch_bounds__(32 * GW, 5)
     fence_mbar_init();
   }
   __syncthreads();
-  auto stage = [&](int z) -> int { return (z - zl) % GNS; };
-  auto issue = [&](int z) {   // thread 0: stage of plane z
+  auto issue = [&](int z, int q) {   // thread 0: stage q <- plane z
     if (z > zh) return;
-    unsigned char* p = smem + stage(z) * GSTAGE;
-    unsigned long long* br = &bar[stage(z)];
+    unsigned char* p = smem + q * GSTAGE;
+    unsigned long long* br = &bar[q];
     mbar_expect_tx(br, GUB + GBB);
     tma_load_3d(p, &mU, xs, y0b - 2, z, br);
     tma_load_3d(p + GUBA, &mB, xs, y0b - 1, z, br);
   };
   if (tid == 0)
-    for (int z = zl; z < zl + GNS; z++) issue(z);
+    for (int q = 0; q < GNS; q++) issue(zl + q, q);
   bool ok = true;
   int wq = 0;
   unsigned wph = 0;
@@ -510,20 +509,18 @@ __global__ void __launch_bounds__(32 * GW, 5)
   bool oin[GR];
 #pragma unroll
   for (int q = 0; q < GR; q++) oin[q] = lane >= 1 && lane <= GTX && x <= d.ni() && y0w + q <= d.nj();
-  auto ubase = [&](int z) -> const float* {   // u row y0w - 2 at column x
-    return reinterpret_cast<const float*>(smem + stage(z) * GSTAGE) + GR * warp * GBW + col;
-  };
-  auto bbase = [&](int z) -> const float* {   // b row y0w - 1 at column x
-    return reinterpret_cast<const float*>(smem + stage(z) * GSTAGE + GUBA) + GR * warp * GBW + col;
-  };
+  // stage q's u row y0w - 2 and b row y0w - 1 at column x
+  const float* sU = reinterpret_cast<const float*>(smem) + GR * warp * GBW + col;
+  const float* sB = reinterpret_cast<const float*>(smem + GUBA) + GR * warp * GBW + col;
+  constexpr int SE = GSTAGE / 4;   // stage stride in floats
   float nm[4];   // -omega M
 #pragma unroll
   for (int a = 0; a < 4; a++) nm[a] = -om * WM.w[a];
   // residual of plane z on the residual rows: b - (P(z) + (Q(z - 1) + Q(z + 1))), zero off the interior
-  auto resid = [&](int z, const float (&Pc)[GRR], const float (&Qm)[GRR], const float (&Qn)[GRR],
+  auto resid = [&](int z, int q, const float (&Pc)[GRR], const float (&Qm)[GRR], const float (&Qn)[GRR],
                    float (&r)[GRR]) {
     const bool zin = z >= 1 && z <= d.nk();
-    const float* B = bbase(z);
+    const float* B = sB + q * SE;
 #pragma unroll
     for (int t = 0; t < GRR; t++) {
       float rv = 0.0f;
@@ -540,16 +537,16 @@ __global__ void __launch_bounds__(32 * GW, 5)
   {
     float r[GRR];
     wait_next();
-    c27_upq(ubase(zl), WA.w, m.up[0], m.uq[0]);
+    c27_upq(sU, WA.w, m.up[0], m.uq[0]);
     wait_next();
-    c27_upq(ubase(zl + 1), WA.w, m.up[1], m.uq[1]);
+    c27_upq(sU + SE, WA.w, m.up[1], m.uq[1]);
     wait_next();
-    c27_upq(ubase(zl + 2), WA.w, m.up[2], m.uq[2]);
-    resid(k0 - 1, m.up[1], m.uq[0], m.uq[2], r);
+    c27_upq(sU + 2 * SE, WA.w, m.up[2], m.uq[2]);
+    resid(k0 - 1, 1, m.up[1], m.uq[0], m.uq[2], r);
     c27_rpq(r, nm, m.mp[0], m.mq[0]);
     wait_next();
-    c27_upq(ubase(zl + 3), WA.w, m.up[0], m.uq[0]);
-    resid(k0, m.up[2], m.uq[1], m.uq[0], r);
+    c27_upq(sU + 3 * SE, WA.w, m.up[0], m.uq[0]);
+    resid(k0, 2, m.up[2], m.uq[1], m.uq[0], r);
     if (RESID) {
 #pragma unroll
       for (int q = 0; q < GR; q++)
@@ -561,9 +558,10 @@ __global__ void __launch_bounds__(32 * GW, 5)
   __syncthreads();
   if (tid == 0 && ok) {   // planes k0 - 2 and k0 - 1 are no longer read (plane k0 keeps the centres of output k0)
     fence_proxy_async();
-    issue(zl + GNS);
-    issue(zl + 1 + GNS);
+    issue(zl + GNS, 0);
+    issue(zl + 1 + GNS, 1);
   }
+  int s0 = 2, s1 = 3, s2 = 4;   // stages of planes k, k + 1, k + 2 (rotated after every step)
   // output plane k; P = (k - k0) mod 3 fixes the register slots:
   // u splits of planes k, k + 1, k + 2 in slots (P+2)%3, P, (P+1)%3,
   // residual splits of planes k - 1, k, k + 1 in slots P, (P+1)%3, (P+2)%3
@@ -572,9 +570,9 @@ __global__ void __launch_bounds__(32 * GW, 5)
     constexpr int UK = (P + 2) % 3, UK1 = P, UK2 = (P + 1) % 3;
     constexpr int RM = P, RC = (P + 1) % 3, RN = (P + 2) % 3;
     wait_next();   // plane k + 2
-    c27_upq(ubase(k + 2), WA.w, m.up[UK2], m.uq[UK2]);
+    c27_upq(sU + s2 * SE, WA.w, m.up[UK2], m.uq[UK2]);
     float r[GRR];
-    resid(k + 1, m.up[UK1], m.uq[UK], m.uq[UK2], r);
+    resid(k + 1, s1, m.up[UK1], m.uq[UK], m.uq[UK2], r);
     if (RESID) {
       // r of plane k + 1 (plane k0 was written by the prologue)
       ob += sz;
@@ -584,7 +582,7 @@ __global__ void __launch_bounds__(32 * GW, 5)
           if (oin[q]) ob[q * sy] = r[q + 1];
     } else {
       c27_rpq(r, nm, m.mp[RN], m.mq[RN]);
-      const float* U = ubase(k) + 2 * GBW;   // u row y0w, plane k
+      const float* U = sU + s0 * SE + 2 * GBW;   // u row y0w, plane k
 #pragma unroll
       for (int q = 0; q < GR; q++)
         if (oin[q]) ob[q * sy] = (U[q * GBW] + m.mp[RC][q]) + (m.mq[RM][q] + m.mq[RN][q]);
@@ -593,8 +591,11 @@ __global__ void __launch_bounds__(32 * GW, 5)
     __syncthreads();   // plane k (its u) and plane k + 1 (its b) are no longer read
     if (tid == 0 && ok) {   // after a failed wait no new copy is issued
       fence_proxy_async();
-      issue(k + GNS);
+      issue(k + GNS, s0);
     }
+    s0 = s1;
+    s1 = s2;
+    s2 = s2 + 1 == GNS ? 0 : s2 + 1;
   };
   for (int k = k0; k < k1; k += 3) {
     step(std::integral_constant<int, 0>(), k);
