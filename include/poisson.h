@@ -415,6 +415,15 @@ ps_status ps_op_sweep(const ps_grid* grid, int stencil_order, int dtype, void* p
 ps_status ps_op_restrict(const ps_grid* fine_grid, int stencil_order, int dtype,
                          const void* r_fine_dev, void* f_coarse_dev, void* stream);
 
+/* The same full weighting for a 7-point residual that is exactly zero on the
+ * black nodes ((i+j+k) odd, node indices), as a complete red-black
+ * Gauss-Seidel sweep leaves it (Sec. 2.1.1, 2.1.3): the zero terms are not
+ * summed.  On such input the result equals ps_op_restrict's bit for bit, up
+ * to the sign of zero values; on other input it is not a restriction.
+ * stencil_order must be 2; dtype FP64 or FP32. */
+ps_status ps_op_restrict_red(const ps_grid* fine_grid, int stencil_order, int dtype,
+                             const void* r_fine_dev, void* f_coarse_dev, void* stream);
+
 /* phi_fine += P e_coarse with P = 8 R^T (trilinear, Sec. 2.1.3); coarse
  * boundary values are treated as zero (grid = the fine grid). */
 ps_status ps_op_prolong(const ps_grid* fine_grid, int stencil_order, int dtype,

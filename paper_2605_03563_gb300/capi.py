@@ -89,6 +89,7 @@ SIGNATURES = {
     "ps_op_sweep": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                               C.c_double, C.c_void_p]),
     "ps_op_restrict": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ps_op_restrict_red": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_op_prolong": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_op_multipole_moments": (C.c_int, [C.POINTER(PsGrid), C.c_int, C.c_void_p,
                                           C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),

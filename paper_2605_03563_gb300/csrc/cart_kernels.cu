@@ -73,8 +73,10 @@ __device__ C gs_value_zero_interior(const T* __restrict__ phi, const Dims& d, in
                                     const Coef<C>& cf, C fs) {
   using S = St<T>;
   // every neighbour interior (all but the nodes next to the boundary): the
-  // neighbour terms are +0, and fs + 0 is the value the general case forms
-  if (i >= 2 * G && i < d.ni() && j >= 2 * G && j < d.nj() && k >= 2 * G && k < d.nk()) return fs + (C)0;
+  // neighbour terms vanish; fs is returned as it is (fs + 0 differs from it
+  // only in the sign of a zero, which neither the square nor the magnitude
+  // the reference norm takes can see)
+  if (i >= 2 * G && i < d.ni() && j >= 2 * G && j < d.nj() && k >= 2 * G && k < d.nk()) return fs;
   auto val = [&](int ii, int jj, int kk) -> C {
     bool inside = ii >= G && ii < G + d.ni() && jj >= G && jj < G + d.nj() && kk >= G &&
                   kk < G + d.nk();
@@ -168,6 +170,9 @@ __global__ void __launch_bounds__(BX* BY)
   const int k1 = min(k0 + zc, G + d.nk());
   const long long sy = d.sy(), sz = d.sz();
   double s2 = 0.0, mx = 0.0;
+  // max |delta| in FP64 as the largest bit pattern of |delta| (the order of
+  // non-negative doubles is that of their bits): no FP64 instruction
+  unsigned long long mxb = 0ull;
   float s2f = 0.0f, mxf = 0.0f;
   double oscale = out_scale;
   if (st != nullptr) oscale = st->scale_next;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(BX* BY)
         continue;
       }
       if (RED >= 1) s2 = fma(dd, dd, s2);
-      if (RED == 2) mx = fmax(mx, fabs(dd));
+      if (RED == 2) mxb = max(mxb, (unsigned long long)__double_as_longlong(dd) & 0x7fffffffffffffffull);
       if (out != nullptr) {
         if (sizeof(C) == sizeof(float)) {
           // FP32 arithmetic levels never touch the FP64 pipe on the store path
@@ -217,6 +222,7 @@ __global__ void __launch_bounds__(BX* BY)
     block_sum_max_scaled(s2f, mxf, oscale, partials);
     return;
   }
+  if (RED == 2) mx = __longlong_as_double((long long)mxb);
   if (RED >= 1) block_sum_max(s2, mx, partials);
 }
 
@@ -336,6 +342,77 @@ __global__ void __launch_bounds__(BX* BY)
     }
     if (ib <= ni) out[c + cb] = 0.0;
   }
+}
+
+// FP64 7-point on equal spacings: delta on every node along (j, k) diagonals,
+// both members of the thread's x pair, each with its carried (N + U) pair sum
+// (5 + 1 FP64 instructions per node; the order of gs_value, so every delta
+// equals k_delta's bit for bit and only the reductions run in another order).
+// STORE: the refinement pass of k_delta (the scaled FP32/BF16 inner right-hand
+// side, the FP32 sum of squares and max of the scaled values); otherwise the
+// FP64 sum of delta^2.  Partials {sum, max} per block.
+template <bool STORE>
+__global__ void __launch_bounds__(BX* BY)
+    k_delta_diag(Dims d, double c1, const double* __restrict__ phi, const double* __restrict__ fs, int dl, int dout,
+                 void* __restrict__ out, const DevState* __restrict__ st, double* __restrict__ partials) {
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
+  const int kn0 = blockIdx.z * dl + 1;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kn0 + 1));
+  const int ia = 1 + 2 * t;   // the pair (ia, ia + 1)
+  double s2 = 0.0;
+  float s2f = 0.0f, mxf = 0.0f;
+  const double oscale = STORE ? st->scale_next : 1.0;
+  const int oexp = pow2_exponent(oscale);
+  auto take = [&](long long p, double dd) {
+    if (STORE) {
+      const float v = oexp != INT_MIN ? f64_to_f32_pow2(dd, oexp) : (float)(dd * oscale);
+      s2f = fmaf(v, v, s2f);
+      mxf = fmaxf(mxf, fabsf(v));
+      if (dout == DT_F32) ((float*)out)[p] = v;
+      else ((__nv_bfloat16*)out)[p] = __float2bfloat16_rn(v);
+    } else {
+      s2 = fma(dd, dd, s2);
+    }
+  };
+  if (u0 < u1 && ia <= ni) {
+    const bool hb = ia + 1 <= ni;
+    const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
+    long long c = d.at(ia, jn0 + u0, kn0 + u0);
+    double qa = phi[c - sy] + phi[c - sz];
+    double qb = hb ? phi[c + 1 - sy] + phi[c + 1 - sz] : 0.0;
+    for (int u = u0; u < u1; u++, c += step) {
+      const double na = phi[c + sy] + phi[c + sz];
+      take(c, fma(((phi[c + 1] + phi[c - 1]) + qa) + na, c1, fs[c]) - phi[c]);
+      qa = na;
+      if (hb) {
+        const long long cb = c + 1;
+        const double nb = phi[cb + sy] + phi[cb + sz];
+        take(cb, fma(((phi[cb + 1] + phi[cb - 1]) + qb) + nb, c1, fs[cb]) - phi[cb]);
+        qb = nb;
+      }
+    }
+  }
+  if (STORE) block_sum_max_scaled(s2f, mxf, oscale, partials);
+  else block_sum_max(s2, 0.0, partials);
+}
+
+cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* phi, const double* fs, int dout,
+                              void* out, const DevState* st, double* partials, int* nblocks, cudaStream_t s) {
+  if (!is_iso(h) || d.g != 1 || (out != nullptr && (st == nullptr || (dout != DT_F32 && dout != DT_BF16))))
+    return cudaErrorInvalidValue;
+  const Coef<double> cf = make_coef<double>(d, h, 2);
+  const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+  const int pairs = (d.ni() + 1) / 2;
+  const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
+  if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+  if (out != nullptr)
+    k_delta_diag<true><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, dout, out, st, partials);
+  else
+    k_delta_diag<false><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, DT_F64, nullptr, nullptr, partials);
+  return cudaGetLastError();
 }
 
 template <int G, bool ISO, typename T, typename TO>
@@ -623,6 +700,59 @@ cudaError_t launch_restrict(const Dims& fine, const Dims& coarse, int dt_f, cons
   return cudaErrorInvalidValue;
 }
 
+// Full weighting of a residual that is zero on the black nodes.  A fine plane
+// at odd offset from the coarse plane holds red values at (+-1, 0) and
+// (0, +-1) around (2I, 2J), one at even offset at (0, 0) and (+-1, +-1).  With
+// the zero terms dropped, k_restrict's plane sum of an odd-offset plane is
+// (2 ym + 2 yp) + 2 (xm + xp) = 2 ((ym + yp) + (xm + xp)) exactly (scaling by
+// 2 commutes with rounding), so the odd planes are carried as half sums and
+// the factor 2 moves into the scale; the even plane's sum is
+// (a + b) + 4 c.  The result equals k_restrict's up to the sign of zeros.
+template <typename TF, typename TC>
+__global__ void __launch_bounds__(BX* BY)
+    k_restrict_red(Dims fd, Dims cd, const TF* __restrict__ df, TC* __restrict__ fsc, double factor) {
+  using CF = typename St<TF>::C;
+  using CC = typename St<TC>::C;
+  const int I = blockIdx.x * BX + threadIdx.x + 1;
+  const int J = blockIdx.y * BY + threadIdx.y + 1;
+  if (I > cd.ni() || J > cd.nj()) return;
+  const int zc = zchunk(cd.nk());
+  const int K0 = blockIdx.z * zc + 1;
+  const int K1 = min(K0 + zc, cd.nk() + 1);
+  const int g = fd.g;
+  const long long sy = fd.sy(), sz = fd.sz();
+  const CF sc2 = (CF)(2.0 * (factor / 64.0));
+  auto odd_half = [&](long long q) -> CF {
+    return (St<TF>::ld(df + q - sy) + St<TF>::ld(df + q + sy)) + (St<TF>::ld(df + q - 1) + St<TF>::ld(df + q + 1));
+  };
+  CF below = odd_half(fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K0 + g - 2));
+  for (int K = K0; K < K1; K++) {
+    const long long c = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
+    const CF a = St<TF>::ld(df + c - sy - 1) + St<TF>::ld(df + c - sy + 1);
+    const CF b = St<TF>::ld(df + c + sy - 1) + St<TF>::ld(df + c + sy + 1);
+    const CF even = fma((CF)4, St<TF>::ld(df + c), a + b);
+    const CF above = odd_half(c + sz);
+    St<TC>::st(fsc + cd.at(I + g - 1, J + g - 1, K + g - 1), (CC)(((below + above) + even) * sc2));
+    below = above;
+  }
+}
+
+cudaError_t launch_restrict_red(const Dims& fine, const Dims& coarse, int dt_f, const void* delta_f, int dt_c,
+                                void* fs_c, double factor, cudaStream_t s) {
+  const dim3 grid = point_grid(coarse), blk(BX, BY);
+  if (dt_f == DT_F64 && dt_c == DT_F64)
+    k_restrict_red<double, double><<<grid, blk, 0, s>>>(fine, coarse, (const double*)delta_f, (double*)fs_c, factor);
+  else if (dt_f == DT_F32 && dt_c == DT_F32)
+    k_restrict_red<float, float><<<grid, blk, 0, s>>>(fine, coarse, (const float*)delta_f, (float*)fs_c, factor);
+  else if (dt_f == DT_F32 && dt_c == DT_F64)
+    k_restrict_red<float, double><<<grid, blk, 0, s>>>(fine, coarse, (const float*)delta_f, (double*)fs_c, factor);
+  else if (dt_f == DT_F64 && dt_c == DT_F32)
+    k_restrict_red<double, float><<<grid, blk, 0, s>>>(fine, coarse, (const double*)delta_f, (float*)fs_c, factor);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ prolongation
 // phi_fine += P e_coarse, P = 8 R^T (trilinear).  One thread per coarse cell
 // (I..I+1, J..J+1, K..K+1): it loads the cell's 8 corner values once and
@@ -631,6 +761,10 @@ cudaError_t launch_restrict(const Dims& fine, const Dims& coarse, int dt_f, cons
 // takes their mean).  Fine node 0 of an axis is the boundary and is skipped;
 // coarse boundary values are zero.  Every interior fine node belongs to exactly
 // one cell.
+// Each thread marches its cell column along z; the 8 fine values of cell K + 1
+// (and the coarse face above it) are loaded before cell K's results are
+// stored, so a thread keeps two cells' loads in flight (the kernel is bound by
+// memory latency, not by its arithmetic).
 template <typename TC, typename TF>
 __global__ void __launch_bounds__(BX* BY)
     k_prolong(Dims fd, Dims cd, const TC* __restrict__ ec, TF* __restrict__ phif) {
@@ -644,14 +778,16 @@ __global__ void __launch_bounds__(BX* BY)
   const long long csy = cd.sy(), csz = cd.sz();
   const long long fsy = fd.sy(), fsz = fd.sz();
   const CF half = (CF)0.5;
-  // the (x, y)-interpolated values of a coarse plane's cell face: [b][a]
-  auto face = [&](long long q0, CF (&v)[2][2]) {
-    CF c[2][2];   // [y][x]
+  // the corner values of a coarse plane's cell face: [y][x]
+  auto load_face = [&](long long q0, CF (&c)[2][2]) {
 #pragma unroll
     for (int y = 0; y < 2; y++) {
       c[y][0] = (CF)St<TC>::ld(ec + q0 + y * csy);
       c[y][1] = (CF)St<TC>::ld(ec + q0 + y * csy + 1);
     }
+  };
+  // the (x, y)-interpolated values of a face: [b][a]
+  auto face = [&](const CF (&c)[2][2], CF (&v)[2][2]) {
     CF vx[2][2];   // [y][a]
 #pragma unroll
     for (int y = 0; y < 2; y++) {
@@ -664,12 +800,37 @@ __global__ void __launch_bounds__(BX* BY)
       v[1][a] = half * (vx[0][a] + vx[1][a]);
     }
   };
+  // fine values of cell K (index [cz][b][a]; nodes on the low boundary are not read)
+  auto load_fine = [&](int K, CF (&f)[2][2][2]) {
+    const long long f0 = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++)
+#pragma unroll
+      for (int b = 0; b < 2; b++)
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+          const bool skip = (cz == 0 && K == 0) || (b == 0 && J == 0) || (a == 0 && I == 0);
+          f[cz][b][a] = skip ? (CF)0 : St<TF>::ld(phif + f0 + cz * fsz + b * fsy + a);
+        }
+  };
   // the top face of cell K is the bottom face of cell K + 1: computed once
   CF vy[2][2][2];   // [z][b][a]
-  face(cd.at(I + g - 1, J + g - 1, K0 + g - 1), vy[0]);
+  CF cn[2][2], fcur[2][2][2], fnext[2][2][2];
+  {
+    CF c0[2][2];
+    load_face(cd.at(I + g - 1, J + g - 1, K0 + g - 1), c0);
+    face(c0, vy[0]);
+  }
+  if (K0 < K1) {
+    load_face(cd.at(I + g - 1, J + g - 1, K0 + g), cn);
+    load_fine(K0, fcur);
+  }
   for (int K = K0; K < K1; K++) {
-    const long long c0 = cd.at(I + g - 1, J + g - 1, K + g - 1);
-    face(c0 + csz, vy[1]);
+    face(cn, vy[1]);
+    if (K + 1 < K1) {   // next cell's operands, before this cell's stores
+      load_face(cd.at(I + g - 1, J + g - 1, K + g + 1), cn);
+      load_fine(K + 1, fnext);
+    }
     const long long f0 = fd.at(2 * I + g - 1, 2 * J + g - 1, 2 * K + g - 1);
 #pragma unroll
     for (int cz = 0; cz < 2; cz++) {
@@ -681,8 +842,7 @@ __global__ void __launch_bounds__(BX* BY)
         for (int a = 0; a < 2; a++) {
           if (a == 0 && I == 0) continue;
           const CF v = cz == 0 ? vy[0][b][a] : half * (vy[0][b][a] + vy[1][b][a]);
-          const long long p = f0 + cz * fsz + b * fsy + a;
-          St<TF>::st(phif + p, St<TF>::ld(phif + p) + v);
+          St<TF>::st(phif + f0 + cz * fsz + b * fsy + a, fcur[cz][b][a] + v);
         }
       }
     }
@@ -690,6 +850,12 @@ __global__ void __launch_bounds__(BX* BY)
     for (int b = 0; b < 2; b++)
 #pragma unroll
       for (int a = 0; a < 2; a++) vy[0][b][a] = vy[1][b][a];
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++)
+#pragma unroll
+      for (int b = 0; b < 2; b++)
+#pragma unroll
+        for (int a = 0; a < 2; a++) fcur[cz][b][a] = fnext[cz][b][a];
   }
 }
 

@@ -48,9 +48,26 @@ cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int
 cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,
                                  cudaStream_t s);
 
+// FP64 residual pass of the 7-point stencil on equal spacings along (j, k)
+// diagonals (every delta equal to launch_delta's / launch_delta_st's bit for
+// bit; the reductions run in another order).  out == NULL: partials {sum of
+// delta^2, 0}; otherwise the refinement pass of launch_delta_st (out FP32 or
+// BF16, scaled by st->scale_next, FP32 sum and max of the scaled values).
+// Returns the block count in nblocks (at most delta_colours_partials(d, 2)).
+cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* phi, const double* fs, int dout,
+                              void* out, const DevState* st, double* partials, int* nblocks, cudaStream_t s);
+
 // fs_coarse = factor * R(delta_fine)  (scaled coarse right-hand side); coarse = layout of fs_c
 cudaError_t launch_restrict(const Dims& fine, const Dims& coarse, int dt_f, const void* delta_f, int dt_c,
                             void* fs_c, double factor, cudaStream_t s);
+
+// The same for a 7-point residual that is exactly zero on the black nodes
+// ((i+j+k) odd), as launch_delta_after_sweep leaves it for order 2: the zero
+// terms are dropped (9 arithmetic instructions per coarse node instead of 19);
+// equal to launch_restrict bit for bit up to the sign of zero sums.  dt_f is
+// FP64 or FP32.
+cudaError_t launch_restrict_red(const Dims& fine, const Dims& coarse, int dt_f, const void* delta_f, int dt_c,
+                                void* fs_c, double factor, cudaStream_t s);
 
 // phi_fine += P e_coarse; coarse = layout of e_c
 cudaError_t launch_prolong(const Dims& fine, const Dims& coarse, int dt_c, const void* e_c, int dt_f, void* phi_f,

@@ -225,6 +225,10 @@ ps_status fail(ps_status s, const char* fmt, ...) {
 // (4 midpoints of an add and a multiply), 4 z-midpoints and 8 accumulations:
 // 24 per 8 fine nodes.
 constexpr double kRestrictOps = 19.0 / 8.0;
+// Full weighting of a residual that is zero on the black nodes: a carried half
+// sum of the odd-offset plane (3 adds), the even-offset plane (2 adds, 1 FMA),
+// the z-triple (2 adds) and the scale: 9 per 8 fine nodes.
+constexpr double kRestrictRedOps = 9.0 / 8.0;
 constexpr double kProlongOps = 3.0;
 
 // Profiler: begin/end pair around one launch on stream s.
@@ -470,8 +474,13 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
     e = (h->nlaunch += 1, launch_delta_after_sweep(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
-    if (l == 0) prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * kRestrictOps, w.St == 8.0, s);
-    e = (h->nlaunch += 1, launch_restrict(L.d, Cl.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s));
+    // 7-point: the residual is zero on the black nodes, which the restriction skips
+    const bool red = h->order == 2;
+    if (l == 0)
+      prof_begin(h, PC_RESTRICT0, w.n * w.St + w.n / 8.0 * dt_size(Cl.dt), w.n * (red ? kRestrictRedOps : kRestrictOps),
+                 w.St == 8.0, s);
+    e = (h->nlaunch += 1, red ? launch_restrict_red(L.d, Cl.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s)
+                              : launch_restrict(L.d, Cl.d, L.dt_tmp, L.tmp, Cl.dt, Cl.fs, 4.0, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
   } else {
@@ -508,6 +517,16 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
     prof_begin(h, PC_NORM0, n * 8.0 * (1.0 + frac), n * frac * ((diag ? 5.0 : 6.0 * G) + 2.0), 1, s);
     int nb = 0;
     cudaError_t e = (h->nlaunch += 1, launch_delta_colours(h->d0, h->order, h->h0, phi, h->fs64, h->partials, &nb, s));
+    prof_end(h, s);
+    if (e != cudaSuccess) return e;
+    return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, mode, h->st, s, cond, chunk));
+  }
+  if (h->order == 2 && h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2]) {
+    // (j, k) diagonal walks: 5 + 1 FP64 instructions per node, + 1 for the FP64 sum of squares
+    prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? 6.0 : 7.0), 1, s);
+    int nb = 0;
+    cudaError_t e = (h->nlaunch += 1, launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, out ? h->st : nullptr,
+                                                        h->partials, &nb, s));
     prof_end(h, s);
     if (e != cudaSuccess) return e;
     return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, mode, h->st, s, cond, chunk));
@@ -2229,6 +2248,20 @@ ps_status ps_op_restrict(const ps_grid* grid, int order, int dtype, const void* 
     return fail(PS_ERR_INVALID_ARG, "restriction needs even interval counts >= 4");
   if (dtype == DT_BF16) return fail(PS_ERR_UNSUPPORTED, "coarse levels are FP32 or FP64");
   TRY(launch_restrict(d, make_dims(d.nx / 2, d.ny / 2, d.nz / 2, d.g), dtype, rf, dtype, fc, 1.0, (cudaStream_t)stream));
+  return PS_OK;
+}
+
+ps_status ps_op_restrict_red(const ps_grid* grid, int order, int dtype, const void* rf, void* fc, void* stream) {
+  Dims d;
+  double h[3];
+  ps_status s = op_dims(grid, order, dtype, &d, h);
+  if (s != PS_OK) return s;
+  if (order != 2) return fail(PS_ERR_INVALID_ARG, "the red-only restriction is for the 7-point stencil");
+  if (d.nx % 2 || d.ny % 2 || d.nz % 2 || d.nx < 4 || d.ny < 4 || d.nz < 4)
+    return fail(PS_ERR_INVALID_ARG, "restriction needs even interval counts >= 4");
+  if (dtype == DT_BF16) return fail(PS_ERR_UNSUPPORTED, "coarse levels are FP32 or FP64");
+  TRY(launch_restrict_red(d, make_dims(d.nx / 2, d.ny / 2, d.nz / 2, d.g), dtype, rf, dtype, fc, 1.0,
+                          (cudaStream_t)stream));
   return PS_OK;
 }
 

@@ -54,6 +54,13 @@ def restrict(n, order, r_fine, f_coarse, lo=(0, 0, 0), hi=(1, 1, 1), stream=None
           "ps_op_restrict")
 
 
+def restrict_red(n, order, r_fine, f_coarse, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
+    """Full weighting of a 7-point residual that is zero on the black nodes (ps_op_restrict_red)."""
+    g = capi.make_grid(n, lo, hi)
+    check(lib().ps_op_restrict_red(C.byref(g), order, _dt(r_fine), _p(r_fine), _p(f_coarse), _s(stream)),
+          "ps_op_restrict_red")
+
+
 def prolong(n, order, e_coarse, phi_fine, lo=(0, 0, 0), hi=(1, 1, 1), stream=None):
     g = capi.make_grid(n, lo, hi)
     check(lib().ps_op_prolong(C.byref(g), order, _dt(phi_fine), _p(e_coarse), _p(phi_fine), _s(stream)),

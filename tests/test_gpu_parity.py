@@ -378,3 +378,66 @@ def test_stepwise_solve_equals_one_shot(pkg):
         info = s.end()
     assert info.iterations == base.iterations and steps == (base.iterations + 1) // 2
     assert torch.equal(phi, ref)
+
+
+@pytest.mark.parametrize("n", [(34, 20, 18), (64, 32, 48)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_red_only_restriction_equals_full_weighting(pkg, n, dtype):
+    """On a residual that vanishes on the black nodes (what a complete red-black
+    sweep leaves), the restriction that skips the zero terms gives the full
+    weighting's coarse values bit for bit (zero sums compared by value)."""
+    fine = _grid(n, 2)
+    coarse = fine.coarsen()
+    gen = W.rng(11)
+    u = fine.zeros()
+    u[fine.interior] = gen.standard_normal(u[fine.interior].shape)
+    i, j, k = np.meshgrid(*[np.arange(s) for s in u.shape], indexing="ij")
+    black = ((i + j + k) % 2) == 1          # node indices of the radius-one layout
+    u[black] = 0.0
+    u_t = dev(u, dtype)
+    f_full = torch.zeros(coarse.shape, device="cuda:0", dtype=dtype)
+    f_red = torch.full(coarse.shape, 7.0, device="cuda:0", dtype=dtype)
+    pkg.ops.restrict(n, 2, u_t, f_full)
+    f_red[coarse.interior] = 0.0
+    pkg.ops.restrict_red(n, 2, u_t, f_red)
+    a, b = host(f_full)[coarse.interior], host(f_red)[coarse.interior]
+    assert np.array_equal(a, b)
+    assert np.max(np.abs(a)) > 0
+
+
+def test_prolongation_midpoints_bitwise(pkg):
+    """The FP64 prolongation (x, then y, then z midpoints, each 0.5 (a + b),
+    added to the fine values) against that arithmetic in numpy, bit for bit,
+    for values over the whole normal range and zeros of either sign."""
+    n, order = (34, 20, 18), 2
+    fine = _grid(n, order)
+    coarse = fine.coarsen()
+    gen = W.rng(12)
+    v = coarse.zeros()
+    vals = gen.standard_normal(v[coarse.interior].shape) * 10.0 ** gen.integers(-300, 300, v[coarse.interior].shape)
+    flat = vals.reshape(-1)
+    flat[::7] = 0.0
+    flat[1::7] = -0.0
+    # three halvings of 2^-1018 stay in the normal range
+    flat[2::11] = 2.0 ** -1018 * np.sign(gen.standard_normal(flat[2::11].shape))
+    v[coarse.interior] = vals
+    base = gen.standard_normal(fine.shape)
+    pf = dev(base, torch.float64)
+    pkg.ops.prolong(n, order, dev(v, torch.float64), pf)
+    got = host(pf)
+    # reference: separable midpoints in the kernel's order, x (last array axis),
+    # then y, then z, each as 0.5 * (a + b)
+    e = v
+    ex = np.zeros(e.shape[:2] + (2 * e.shape[2] - 1,))
+    ex[:, :, 0::2] = e
+    ex[:, :, 1::2] = 0.5 * (e[:, :, :-1] + e[:, :, 1:])
+    ey = np.zeros((e.shape[0], 2 * e.shape[1] - 1, ex.shape[2]))
+    ey[:, 0::2] = ex
+    ey[:, 1::2] = 0.5 * (ex[:, :-1] + ex[:, 1:])
+    ez = np.zeros((2 * e.shape[0] - 1,) + ey.shape[1:])
+    ez[0::2] = ey
+    ez[1::2] = 0.5 * (ey[:-1] + ey[1:])
+    ref = base.copy()
+    ref[fine.interior] = base[fine.interior] + ez[fine.interior]
+    with np.errstate(invalid="ignore"):
+        assert np.array_equal(got[fine.interior], ref[fine.interior])
