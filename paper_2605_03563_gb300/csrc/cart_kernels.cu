@@ -69,7 +69,7 @@ int cart_partials_count(const Dims& d) {
 
 // Same with every interior neighbour read as zero (reference norm only).
 template <int G, typename T, typename C>
-__device__ C gs_value_zero_interior(const T* __restrict__ phi, const Dims& d, int i, int j, int k,
+__device__ __forceinline__ C gs_value_zero_interior(const T* __restrict__ phi, const Dims& d, int i, int j, int k,
                                     const Coef<C>& cf, C fs) {
   using S = St<T>;
   // every neighbour interior (all but the nodes next to the boundary): the
@@ -226,6 +226,35 @@ __global__ void __launch_bounds__(BX* BY)
   if (RED >= 1) block_sum_max(s2, mx, partials);
 }
 
+// Reference norm ||f - A phi0|| of the boundary data (interior read as zero),
+// FP64: on a node whose neighbours are all interior the value is fs itself,
+// so away from the boundary the pass reads fs alone, one FP64 FMA per node,
+// max |value| on the integer pipe.  Threads, their order over z and the block
+// reduction are those of k_delta, so the result equals its bits.
+template <int G>
+__global__ void __launch_bounds__(BX* BY)
+    k_ref_norm(Dims d, Coef<double> cf, const double* __restrict__ phi, const double* __restrict__ fs,
+               double* __restrict__ partials) {
+  const int i = blockIdx.x * BX + threadIdx.x + G;
+  const int j = blockIdx.y * BY + threadIdx.y + G;
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + G;
+  const int k1 = min(k0 + zc, G + d.nk());
+  double s2 = 0.0;
+  unsigned long long mxb = 0ull;
+  if (i < G + d.ni() && j < G + d.nj()) {
+    const bool inxy = i >= 2 * G && i < d.ni() && j >= 2 * G && j < d.nj();
+#pragma unroll 2
+    for (int k = k0; k < k1; k++) {
+      const long long p = d.at(i, j, k);
+      const double v = inxy && k >= 2 * G && k < d.nk() ? fs[p] : gs_value_zero_interior<G>(phi, d, i, j, k, cf, fs[p]);
+      s2 = fma(v, v, s2);
+      mxb = max(mxb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull);
+    }
+  }
+  block_sum_max(s2, __longlong_as_double((long long)mxb), partials);
+}
+
 template <int G, bool ISO, typename TI>
 static cudaError_t delta_t(const Dims& d, const double h[3], int order, const void* phi,
                            const void* fs, int dout, void* out, double out_scale,
@@ -242,6 +271,14 @@ static cudaError_t delta_t(const Dims& d, const double h[3], int order, const vo
   else
     k_delta<G, ISO, TI, 1><<<point_grid(d), dim3(BX, BY), 0, s>>>(
         d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ref_norm(const Dims& d, int order, const double h[3], const double* phi, const double* fs,
+                            double* partials, cudaStream_t s) {
+  const Coef<double> cf = make_coef<double>(d, h, order);
+  if (order == 2) k_ref_norm<1><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, cf, phi, fs, partials);
+  else k_ref_norm<2><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, cf, phi, fs, partials);
   return cudaGetLastError();
 }
 
@@ -333,14 +370,28 @@ __global__ void __launch_bounds__(BX* BY)
   const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
   long long c = d.at(in, jn0 + u0, kn0 + u0);
   const long long cb = ib - in;                 // offset of the black member
-  double qprev = in <= ni ? phi[c - sy] + phi[c - sz] : 0.0;
-  for (int u = u0; u < u1; u++, c += step) {
-    if (in <= ni) {
-      const double q = phi[c + sy] + phi[c + sz];
-      out[c] = fma(((phi[c + 1] + phi[c - 1]) + qprev) + q, c1, fs[c]) - phi[c];
-      qprev = q;
-    }
+  if (in > ni) {   // only the black member is interior
+    if (ib <= ni)
+      for (int u = u0; u < u1; u++, c += step) out[c + cb] = 0.0;
+    return;
+  }
+  double qprev = phi[c - sy] + phi[c - sz];
+  // raw operands one node ahead, summed one step later (as in k_sweep_diag)
+  double e = phi[c + 1], w = phi[c - 1], nn = phi[c + sy], up = phi[c + sz], f = fs[c], x = phi[c];
+  for (int u = u0; u < u1; u++) {
+    const long long cn = u + 1 < u1 ? c + step : c;
+    const double e2 = phi[cn + 1], w2 = phi[cn - 1], n2 = phi[cn + sy], u2 = phi[cn + sz], f2 = fs[cn], x2 = phi[cn];
+    const double q = nn + up;
+    out[c] = fma(((e + w) + qprev) + q, c1, f) - x;
+    qprev = q;
     if (ib <= ni) out[c + cb] = 0.0;
+    c += step;
+    e = e2;
+    w = w2;
+    nn = n2;
+    up = u2;
+    f = f2;
+    x = x2;
   }
 }
 
@@ -381,18 +432,37 @@ __global__ void __launch_bounds__(BX* BY)
     const bool hb = ia + 1 <= ni;
     const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
     long long c = d.at(ia, jn0 + u0, kn0 + u0);
+    const long long o = hb ? 1 : 0;   // the second member (or the first again, unused)
     double qa = phi[c - sy] + phi[c - sz];
-    double qb = hb ? phi[c + 1 - sy] + phi[c + 1 - sz] : 0.0;
-    for (int u = u0; u < u1; u++, c += step) {
-      const double na = phi[c + sy] + phi[c + sz];
-      take(c, fma(((phi[c + 1] + phi[c - 1]) + qa) + na, c1, fs[c]) - phi[c]);
-      qa = na;
+    double qb = phi[c + o - sy] + phi[c + o - sz];
+    // raw operands of both members one node ahead, summed one step later
+    double w = phi[c - 1], xa = phi[c], xb = phi[c + 1], e = phi[c + 2];
+    double na = phi[c + sy], ua = phi[c + sz], nb = phi[c + o + sy], ub = phi[c + o + sz];
+    double fa = fs[c], fb = fs[c + o];
+    for (int u = u0; u < u1; u++) {
+      const long long cn = u + 1 < u1 ? c + step : c;
+      const double w2 = phi[cn - 1], xa2 = phi[cn], xb2 = phi[cn + 1], e2 = phi[cn + 2];
+      const double na2 = phi[cn + sy], ua2 = phi[cn + sz], nb2 = phi[cn + o + sy], ub2 = phi[cn + o + sz];
+      const double fa2 = fs[cn], fb2 = fs[cn + o];
+      const double qa2 = na + ua;
+      take(c, fma(((xb + w) + qa) + qa2, c1, fa) - xa);
+      qa = qa2;
       if (hb) {
-        const long long cb = c + 1;
-        const double nb = phi[cb + sy] + phi[cb + sz];
-        take(cb, fma(((phi[cb + 1] + phi[cb - 1]) + qb) + nb, c1, fs[cb]) - phi[cb]);
-        qb = nb;
+        const double qb2 = nb + ub;
+        take(c + 1, fma(((e + xa) + qb) + qb2, c1, fb) - xb);
+        qb = qb2;
       }
+      c += step;
+      w = w2;
+      xa = xa2;
+      xb = xb2;
+      e = e2;
+      na = na2;
+      ua = ua2;
+      nb = nb2;
+      ub = ub2;
+      fa = fa2;
+      fb = fb2;
     }
   }
   if (STORE) block_sum_max_scaled(s2f, mxf, oscale, partials);
@@ -562,27 +632,28 @@ __global__ void __launch_bounds__(BX* BY)
   const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
   long long c = d.at(in, jn0 + u0, kn0 + u0);
   double qprev = phi[c - sy] + phi[c - sz];
-  // operands of the next node are loaded before this node's store (its
-  // neighbours have the other colour and are not written in this pass)
-  double ew = phi[c + 1] + phi[c - 1], q = phi[c + sy] + phi[c + sz], f = fs[c];
+  // the next node's operands are loaded as raw values before this node's
+  // arithmetic and store (its neighbours have the other colour and are not
+  // written in this pass); their sums are formed one step later, so no
+  // instruction of this step waits on them.  The last step reloads its own
+  // node instead of branching.
+  double e = phi[c + 1], w = phi[c - 1], nn = phi[c + sy], up = phi[c + sz], f = fs[c];
   double old = OM1 ? 0.0 : phi[c];
   for (int u = u0; u < u1; u++) {
-    const long long cn = c + step;
-    double ewn = 0.0, qn = 0.0, fn = 0.0, oldn = 0.0;
-    if (u + 1 < u1) {
-      ewn = phi[cn + 1] + phi[cn - 1];
-      qn = phi[cn + sy] + phi[cn + sz];
-      fn = fs[cn];
-      if (!OM1) oldn = phi[cn];
-    }
-    const double gs = fma((ew + qprev) + q, c1, f);
+    const long long cn = u + 1 < u1 ? c + step : c;
+    const double e2 = phi[cn + 1], w2 = phi[cn - 1], n2 = phi[cn + sy], u2 = phi[cn + sz], f2 = fs[cn];
+    const double old2 = OM1 ? 0.0 : phi[cn];
+    const double q = nn + up;
+    const double gs = fma(((e + w) + qprev) + q, c1, f);
     phi[c] = OM1 ? gs : fma(omega, gs - old, old);
     qprev = q;
-    c = cn;
-    ew = ewn;
-    q = qn;
-    f = fn;
-    old = oldn;
+    c += step;
+    e = e2;
+    w = w2;
+    nn = n2;
+    up = u2;
+    f = f2;
+    old = old2;
   }
 }
 

@@ -48,6 +48,13 @@ cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int
 cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,
                                  cudaStream_t s);
 
+// FP64 reference norm ||f - A phi0|| with every interior value of phi0 read
+// as zero (only the boundary data enter): partials {sum, max} per block of
+// point_grid(d) (cart_partials_count blocks), equal to launch_delta's with
+// zero_interior bit for bit.
+cudaError_t launch_ref_norm(const Dims& d, int order, const double h[3], const double* phi, const double* fs,
+                            double* partials, cudaStream_t s);
+
 // FP64 residual pass of the 7-point stencil on equal spacings along (j, k)
 // diagonals (every delta equal to launch_delta's / launch_delta_st's bit for
 // bit; the reductions run in another order).  out == NULL: partials {sum of

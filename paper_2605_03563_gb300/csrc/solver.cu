@@ -603,7 +603,7 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
   // the compact schemes form R_h f and their reference norm themselves
   if (own_rhs) return PS_OK;
   // reference norm ||f - A phi0||, phi0 = boundary data only
-  TRY((h->nlaunch += 1, launch_delta(h->d0, h->order, h->h0, DT_F64, h->phi0, h->fs64, DT_F64, nullptr, 1.0, true, h->partials, nullptr, s)));
+  TRY((h->nlaunch += 1, launch_ref_norm(h->d0, h->order, h->h0, h->phi0, h->fs64, h->partials, s)));
   TRY((h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), cf.d, 0, h->st, s)));
   return PS_OK;
 }

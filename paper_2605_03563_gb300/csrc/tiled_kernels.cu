@@ -1030,11 +1030,22 @@ __global__ void __launch_bounds__(256)
     const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
     long long c = d.at(in, jn0 + u0, kn0 + u0);
     double qprev = phi[c - sy] + phi[c - sz];
-    for (int u = u0; u < u1; u++, c += step) {
-      const double q = phi[c + sy] + phi[c + sz];
-      const double dl_ = fma(((phi[c + 1] + phi[c - 1]) + qprev) + q, c1, fs[c]) - phi[c];
+    // raw operands one node ahead, summed one step later (the last step reloads its own node)
+    double e = phi[c + 1], w = phi[c - 1], nn = phi[c + sy], up = phi[c + sz], f = fs[c], x = phi[c];
+    for (int u = u0; u < u1; u++) {
+      const long long cn = u + 1 < u1 ? c + step : c;
+      const double e2 = phi[cn + 1], w2 = phi[cn - 1], n2 = phi[cn + sy], u2 = phi[cn + sz], f2 = fs[cn], x2 = phi[cn];
+      const double q = nn + up;
+      const double dl_ = fma(((e + w) + qprev) + q, c1, f) - x;
       s2 = fma(dl_, dl_, s2);
       qprev = q;
+      c += step;
+      e = e2;
+      w = w2;
+      nn = n2;
+      up = u2;
+      f = f2;
+      x = x2;
     }
   }
   __shared__ double sh[8];
