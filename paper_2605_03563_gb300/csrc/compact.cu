@@ -289,8 +289,23 @@ __global__ void __launch_bounds__(CBX*(CBY / FRB))
     load(k0, v);
     sums(v, C, F, E, qc);
     load(k0 + 1, v);
+    // b (MODE 0) or the residual being updated (MODE 1) of the thread's rows on
+    // plane k, loaded one plane ahead like the stencil operands (the thread
+    // writes only plane k of its own rows before it reads plane k + 1)
+    auto load_b = [&](int k, double (&bb)[FRB]) {
+      const long long base = (long long)k * sz;
+#pragma unroll
+      for (int q = 0; q < FRB; q++) {
+        const long long o = base + roff[q + 1];
+        bb[q] = j0 + q <= d.nj() ? (MODE == 0 ? b[o] : (double)dst[o]) : 0.0;
+      }
+    };
+    double bc[FRB];
+    load_b(k0, bc);
     for (int k = k0; k < k1; k++) {
       if (k + 2 <= k1) load(k + 2, vn);   // plane k1 <= nk + 1 exists
+      double bn[FRB];
+      load_b(k + 1 < k1 ? k + 1 : k, bn);
       double nC[FRB], nF[FRB], nE[FRB], qn[FRB];
       sums(v, nC, nF, nE, qn);
       const long long base = (long long)k * sz;
@@ -298,7 +313,7 @@ __global__ void __launch_bounds__(CBX*(CBY / FRB))
       for (int q = 0; q < FRB; q++) {
         if (j0 + q <= d.nj()) {
           const long long o = base + roff[q + 1];
-          const double bv = MODE == 0 ? b[o] : (double)dst[o];
+          const double bv = bc[q];
           const double val = fma(nw.w[0], C[q], fma(nw.w[1], F[q], fma(nw.w[2], E[q], bv))) + (qm[q] + qn[q]);
           dst[o] = store_as<TR>(val);
           if (MODE == 0 && NORM) s2 = fma(val, val, s2);
@@ -319,6 +334,7 @@ __global__ void __launch_bounds__(CBX*(CBY / FRB))
         C[q] = nC[q];
         F[q] = nF[q];
         E[q] = nE[q];
+        bc[q] = bn[q];
       }
 #pragma unroll
       for (int s = 0; s < FRB + 2; s++)
