@@ -427,14 +427,16 @@ cudaError_t launch_c27_spai(const Dims& d, const W27& M, double omega, const dou
 // centres); one block barrier per plane returns a stage to the copy engine.
 // Traffic is 12 bytes per node instead of 24 for a residual pass followed by a
 // SPAI pass; the results equal that route's up to FP32 rounding.
-static constexpr int GW = 4, GR = 4;                  // warps per block, output rows per warp
-static constexpr int GTX = 30, GTY = GW * GR;         // output tile
-static constexpr int GRR = GR + 2, GUR = GR + 4;      // residual rows and u rows per warp
-static constexpr int GBW = 40, GUH = GTY + 4, GBH = GTY + 2;
-static constexpr int GNS = 6;                         // stages (planes of u and b)
-static constexpr int GUB = GBW * GUH * 4, GBB = GBW * GBH * 4;
-static constexpr int GUBA = (GUB + 127) / 128 * 128, GBBA = (GBB + 127) / 128 * 128;
-static constexpr int GSTAGE = GUBA + GBBA;
+static constexpr int GTX = 30, GBW = 40, GNS = 6;    // output columns, staged row width, stages
+// Tile of GW warps x GR output rows per warp: GTY = GW GR rows per block, GRR
+// residual rows and GUR u rows per warp, staged boxes of GUH u rows and GBH b rows.
+template <int GW, int GR>
+struct SmT {
+  static constexpr int GTY = GW * GR, GRR = GR + 2, GUR = GR + 4, GUH = GTY + 4, GBH = GTY + 2;
+  static constexpr int GUB = GBW * GUH * 4, GBB = GBW * GBH * 4;
+  static constexpr int GUBA = (GUB + 127) / 128 * 128, GBBA = (GBB + 127) / 128 * 128;
+  static constexpr int GSTAGE = GUBA + GBBA, SMEM = GNS * GSTAGE + GNS * 8;
+};
 
 // Per-plane split of a class stencil w on the in-plane sums (C, F, E) of one
 // plane: P = w0 C + w1 F + w2 E and Q = w1 C + w2 F + w3 E, so that
@@ -446,8 +448,10 @@ __device__ __forceinline__ void pq_split(const float (&w)[4], float c, float f, 
 
 // u of one staged plane on the residual rows: P and Q of its in-plane sums
 // (the pair sums u(x-1) + u(x+1) shared between rows)
-__device__ __forceinline__ void c27_upq(const float* __restrict__ U, const float (&w)[4], float (&P)[GRR],
-                                        float (&Q)[GRR]) {
+template <int GR>
+__device__ __forceinline__ void c27_upq(const float* __restrict__ U, const float (&w)[4], float (&P)[GR + 2],
+                                        float (&Q)[GR + 2]) {
+  constexpr int GRR = GR + 2, GUR = GR + 4;
   float c[GUR], a[GUR];
 #pragma unroll
   for (int s = 0; s < GUR; s++) {
@@ -460,7 +464,9 @@ __device__ __forceinline__ void c27_upq(const float* __restrict__ U, const float
 
 // the residual of one plane on the residual rows: P and Q (of -omega M) of its
 // in-plane sums on the output rows, x-neighbours by shuffles
-__device__ __forceinline__ void c27_rpq(const float (&r)[GRR], const float (&w)[4], float (&P)[GR], float (&Q)[GR]) {
+template <int GR>
+__device__ __forceinline__ void c27_rpq(const float (&r)[GR + 2], const float (&w)[4], float (&P)[GR], float (&Q)[GR]) {
+  constexpr int GRR = GR + 2;
   float ar[GRR];
 #pragma unroll
   for (int t = 0; t < GRR; t++) {
@@ -472,20 +478,24 @@ __device__ __forceinline__ void c27_rpq(const float (&r)[GRR], const float (&w)[
   for (int q = 0; q < GR; q++) pq_split(w, r[q + 1], ar[q + 1] + (r[q] + r[q + 2]), ar[q] + ar[q + 2], P[q], Q[q]);
 }
 
+template <int GR>
 struct SmoothMarch {
+  static constexpr int GRR = GR + 2;
   float up[3][GRR], uq[3][GRR];   // P and Q of u on the residual rows, three planes
   float mp[3][GR], mq[3][GR];     // P and Q of the residual under -omega M on the output rows
 };
 
 // RESID: the same march writes the residual r = b - A u of the output rows
 // instead (the residual before a restriction), with no M stencil.
-template <bool RESID>
-__global__ void __launch_bounds__(32 * GW, 5)
+template <bool RESID, int GW, int GR>
+__global__ void __launch_bounds__(32 * GW, GR <= 4 ? 5 : 3)
     k_c27_smooth(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mB, Dims d,
                  Wts<float> WA, Wts<float> WM, float om, float* __restrict__ dst, int zc,
                  const DevState* __restrict__ st, int* __restrict__ fault) {
-  __shared__ __align__(128) unsigned char smem[GNS * GSTAGE];
-  __shared__ __align__(8) unsigned long long bar[GNS];
+  using T = SmT<GW, GR>;
+  constexpr int GTY = T::GTY, GRR = T::GRR, GUB = T::GUB, GBB = T::GBB, GUBA = T::GUBA, GSTAGE = T::GSTAGE;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + GNS * GSTAGE);
   if (st != nullptr && st->done) return;   // uniform
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * GTX + 1, y0b = blockIdx.y * GTY + 1;   // first output node of the tile
@@ -546,29 +556,29 @@ __global__ void __launch_bounds__(32 * GW, 5)
   };
   const long long sy = d.sy(), sz = d.sz();
   float* ob = dst + d.at(min(max(x, 1), d.ni()), min(y0w, d.nj()), k0);   // output row y0w, plane k0
-  SmoothMarch m;
+  SmoothMarch<GR> m;
   // prologue: residual planes k0 - 1 and k0 (u planes k0 - 2 .. k0 + 1); u
   // plane z's split sits in slot (z - zl) mod 3, the residual's of plane z in
   // slot (z - k0 + 1) mod 3
   {
     float r[GRR];
     wait_next();
-    c27_upq(sU, WA.w, m.up[0], m.uq[0]);
+    c27_upq<GR>(sU, WA.w, m.up[0], m.uq[0]);
     wait_next();
-    c27_upq(sU + SE, WA.w, m.up[1], m.uq[1]);
+    c27_upq<GR>(sU + SE, WA.w, m.up[1], m.uq[1]);
     wait_next();
-    c27_upq(sU + 2 * SE, WA.w, m.up[2], m.uq[2]);
+    c27_upq<GR>(sU + 2 * SE, WA.w, m.up[2], m.uq[2]);
     resid(k0 - 1, 1, m.up[1], m.uq[0], m.uq[2], r);
-    c27_rpq(r, nm, m.mp[0], m.mq[0]);
+    c27_rpq<GR>(r, nm, m.mp[0], m.mq[0]);
     wait_next();
-    c27_upq(sU + 3 * SE, WA.w, m.up[0], m.uq[0]);
+    c27_upq<GR>(sU + 3 * SE, WA.w, m.up[0], m.uq[0]);
     resid(k0, 2, m.up[2], m.uq[1], m.uq[0], r);
     if (RESID) {
 #pragma unroll
       for (int q = 0; q < GR; q++)
         if (oin[q]) ob[q * sy] = r[q + 1];
     } else {
-      c27_rpq(r, nm, m.mp[1], m.mq[1]);
+      c27_rpq<GR>(r, nm, m.mp[1], m.mq[1]);
     }
   }
   __syncthreads();
@@ -586,7 +596,7 @@ __global__ void __launch_bounds__(32 * GW, 5)
     constexpr int UK = (P + 2) % 3, UK1 = P, UK2 = (P + 1) % 3;
     constexpr int RM = P, RC = (P + 1) % 3, RN = (P + 2) % 3;
     wait_next();   // plane k + 2
-    c27_upq(sU + s2 * SE, WA.w, m.up[UK2], m.uq[UK2]);
+    c27_upq<GR>(sU + s2 * SE, WA.w, m.up[UK2], m.uq[UK2]);
     float r[GRR];
     resid(k + 1, s1, m.up[UK1], m.uq[UK], m.uq[UK2], r);
     if (RESID) {
@@ -597,7 +607,7 @@ __global__ void __launch_bounds__(32 * GW, 5)
         for (int q = 0; q < GR; q++)
           if (oin[q]) ob[q * sy] = r[q + 1];
     } else {
-      c27_rpq(r, nm, m.mp[RN], m.mq[RN]);
+      c27_rpq<GR>(r, nm, m.mp[RN], m.mq[RN]);
       const float* U = sU + s0 * SE + 2 * GBW;   // u row y0w, plane k
 #pragma unroll
       for (int q = 0; q < GR; q++)
@@ -621,22 +631,42 @@ __global__ void __launch_bounds__(32 * GW, 5)
   if (!ok && fault != nullptr) atomicExch(fault, 1);
 }
 
+template <bool RESID, int GW, int GR>
+static cudaError_t launch_march_t(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
+                                  const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
+  using T = SmT<GW, GR>;
+  CUtensorMap mu, mb;
+  if (!encode_level_map(&mu, DT_F32, u, d, GBW, T::GUH)) return cudaErrorInvalidValue;
+  if (!encode_level_map(&mb, DT_F32, b, d, GBW, T::GBH)) return cudaErrorInvalidValue;
+  auto kern = k_c27_smooth<RESID, GW, GR>;
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 32 * GW, T::SMEM);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = std::max(1, blocks_per_sm);
+  }
+  const int sms = device_sm_count();
+  const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + T::GTY - 1) / T::GTY, nk = d.nk();
+  // about two to three waves, z-chunks of at least 16 planes (4 extra staged planes each)
+  const int want = std::max(1, 5 * sms * blocks_per_sm / (2 * gx * gy));
+  const int zc = std::max(16, (nk + want - 1) / want);
+  const dim3 grid(gx, gy, (nk + zc - 1) / zc);
+  kern<<<grid, 32 * GW, T::SMEM, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
+  return cudaGetLastError();
+}
+
+// Tiles: 4 warps x 4 rows (16 rows, 20 warps per SM) below 384 points per side,
+// 4 warps x 8 rows (32 rows, residual rows recomputed 1.25 times instead of
+// 1.5, 12 warps per SM) above; the same values bit for bit (measured: 255^3
+// 0.059 against 0.067 ms, 511^3 0.368 against 0.348 ms per smoothing step).
 template <bool RESID>
 static cudaError_t launch_march(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
                                 const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
   if (d.g != 1 || u == dst) return cudaErrorInvalidValue;
-  CUtensorMap mu, mb;
-  if (!encode_level_map(&mu, DT_F32, u, d, GBW, GUH)) return cudaErrorInvalidValue;
-  if (!encode_level_map(&mb, DT_F32, b, d, GBW, GBH)) return cudaErrorInvalidValue;
-  const int sms = device_sm_count();
-  const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + GTY - 1) / GTY, nk = d.nk();
-  // about two to three waves of 5 blocks per SM, z-chunks of at least 16 planes (4 extra staged planes each)
-  const int want = std::max(1, 12 * sms / (gx * gy));
-  const int zc = std::max(16, (nk + want - 1) / want);
-  const dim3 grid(gx, gy, (nk + zc - 1) / zc);
-  k_c27_smooth<RESID><<<grid, 32 * GW, 0, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st,
-                                               fault);
-  return cudaGetLastError();
+  if (d.ni() >= 384 && d.nj() >= 384) return launch_march_t<RESID, 4, 8>(d, A, M, omega, u, b, dst, st, fault, s);
+  return launch_march_t<RESID, 4, 4>(d, A, M, omega, u, b, dst, st, fault, s);
 }
 
 cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
