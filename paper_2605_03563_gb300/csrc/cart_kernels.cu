@@ -657,6 +657,62 @@ __global__ void __launch_bounds__(BX* BY)
   }
 }
 
+// FP64 13-point colour pass on equal spacings along (j, k) anti-diagonals: the
+// nodes (i, j+u, k-u) have one colour of the three, none of their neighbours
+// is written in the pass, and the pair sum N + D (distance 1) of one node is
+// the S + U of the next, the N + D at distance 2 the S + U of the node after
+// that.  So x_GS = c1 ((E + W) + (S + U) + (N + D)) + c2 (... at distance 2)
+// + fs costs 10 FP64 instructions instead of 12 (the order of gs_value).  A
+// thread owns an x triple and updates the member of the pass's colour along a
+// walk of dl nodes; walks tile (j, nk + 1 - k) as the 7-point walks tile
+// (j, k).  Raw operands of the next node are loaded a step ahead.
+template <bool OM1>
+__global__ void __launch_bounds__(BX* BY)
+    k_sweep_diag13(Dims d, double c1, double c2, double* __restrict__ phi, const double* __restrict__ fs,
+                   int colour, double omega, int dl, const DevState* __restrict__ st,
+                   const double* __restrict__ wtab, int wlen) {
+  if (st != nullptr && st->done) return;
+  if (!OM1 && wtab != nullptr && st != nullptr) omega = wtab[min(st->iter * 3 + colour, wlen - 1)];
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;   // walks start at jn0 = 2 - dl .. nj
+  const int kr0 = blockIdx.z * dl + 1;                       // k reflected: k = nk + 1 - kr
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kr0 + 1));
+  if (u0 >= u1) return;
+  const int jk = jn0 + nk + 1 - kr0;   // j + k, fixed along the walk
+  const int in = 1 + 3 * t + (((colour - jk - 1) % 3) + 3) % 3;
+  if (in > ni) return;
+  const long long sy = d.sy(), sz = d.sz(), step = sy - sz;
+  long long c = d.at(in + 1, jn0 + u0 + 1, nk + 1 - (kr0 + u0) + 1);   // array index = node + 1
+  // S + U of the first node (distance 1), and at distance 2 of the first two nodes
+  double su1 = phi[c - sy] + phi[c + sz];
+  const long long c2n = u0 + 1 < u1 ? c + step : c;
+  double su2 = phi[c - 2 * sy] + phi[c + 2 * sz];
+  double su2n = phi[c2n - 2 * sy] + phi[c2n + 2 * sz];
+  double e1 = phi[c + 1], w1 = phi[c - 1], n1 = phi[c + sy], d1 = phi[c - sz];
+  double e2 = phi[c + 2], w2 = phi[c - 2], n2 = phi[c + 2 * sy], d2 = phi[c - 2 * sz], f = fs[c];
+  double old = OM1 ? 0.0 : phi[c];
+  for (int u = u0; u < u1; u++) {
+    const long long cn = u + 1 < u1 ? c + step : c;
+    const double e1n = phi[cn + 1], w1n = phi[cn - 1], n1n = phi[cn + sy], d1n = phi[cn - sz];
+    const double e2n = phi[cn + 2], w2n = phi[cn - 2], n2n = phi[cn + 2 * sy], d2n = phi[cn - 2 * sz];
+    const double fn = fs[cn], oldn = OM1 ? 0.0 : phi[cn];
+    const double nd1 = n1 + d1, nd2 = n2 + d2;
+    const double v1 = fma(((e1 + w1) + su1) + nd1, c1, f);
+    const double gs = fma(((e2 + w2) + su2) + nd2, c2, v1);
+    phi[c] = OM1 ? gs : fma(omega, gs - old, old);
+    su1 = nd1;
+    su2 = su2n;
+    su2n = nd2;
+    c += step;
+    e1 = e1n; w1 = w1n; n1 = n1n; d1 = d1n;
+    e2 = e2n; w2 = w2n; n2 = n2n; d2 = d2n;
+    f = fn;
+    old = oldn;
+  }
+}
+
 template <int G, bool ISO, typename T>
 static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* phi, const void* fs,
                            int colour, double omega, const DevState* st, const double* wtab, int wlen,
@@ -675,6 +731,18 @@ static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* ph
     else
       k_sweep_diag<false><<<grid, dim3(BX, BY), 0, s>>>(d, (double)cf.c1[0], (double*)phi, (const double*)fs,
                                                          colour, omega, dl, st, wtab, wlen);
+    return cudaGetLastError();
+  }
+  if constexpr (G == 2 && ISO && sizeof(T) == sizeof(double)) {
+    const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+    const int triples = (d.ni() + 2) / 3;
+    const dim3 grid((triples + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
+    if (omega == 1.0 && wtab == nullptr)
+      k_sweep_diag13<true><<<grid, dim3(BX, BY), 0, s>>>(d, (double)cf.c1[0], (double)cf.c2[0], (double*)phi,
+                                                          (const double*)fs, colour, omega, dl, st, nullptr, 0);
+    else
+      k_sweep_diag13<false><<<grid, dim3(BX, BY), 0, s>>>(d, (double)cf.c1[0], (double)cf.c2[0], (double*)phi,
+                                                           (const double*)fs, colour, omega, dl, st, wtab, wlen);
     return cudaGetLastError();
   }
   int per_row = (d.ni() + NCOL - 1) / NCOL;

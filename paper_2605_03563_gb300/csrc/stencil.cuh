@@ -22,6 +22,18 @@ __device__ __forceinline__ C gs_value(const T* __restrict__ phi, long long p, lo
     const C nu = S::ld(phi + p + sy) + S::ld(phi + p + sz);
     return fma((ax + sd) + nu, cf.c1[0], fs);
   }
+  if constexpr (ISO && G == 2 && sizeof(C) == 8) {
+    // FP64 13-point on equal spacings: the order of the diagonal colour pass
+    // (k_sweep_diag13), (E + W) + (S + U) + (N + D) at distance 1, then the
+    // same at distance 2
+    const C su1 = S::ld(phi + p - sy) + S::ld(phi + p + sz);
+    const C nd1 = S::ld(phi + p + sy) + S::ld(phi + p - sz);
+    const C v1 = fma((ax + su1) + nd1, cf.c1[0], fs);
+    const C ew2 = S::ld(phi + p + 2) + S::ld(phi + p - 2);
+    const C su2 = S::ld(phi + p - 2 * sy) + S::ld(phi + p + 2 * sz);
+    const C nd2 = S::ld(phi + p + 2 * sy) + S::ld(phi + p - 2 * sz);
+    return fma((ew2 + su2) + nd2, cf.c2[0], v1);
+  }
   C ay = S::ld(phi + p + sy) + S::ld(phi + p - sy);
   C az = S::ld(phi + p + sz) + S::ld(phi + p - sz);
   if (ISO) {
