@@ -485,12 +485,196 @@ cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* ph
   return cudaGetLastError();
 }
 
+// FP64 13-point residual passes on equal spacings along the (j, k)
+// anti-diagonal walks of k_sweep_diag13 (every delta equals gs_value's bit for
+// bit; only reductions run in another order), on colours 0 and 1 after a
+// sweep whose last colour 2 has delta = 0.  A thread owns an x triple and walks
+// its two members of colours 0 and 1, each with its carried pair sums.  MODE 0:
+// sum of delta^2 (the norm after a sweep); 1: delta stored, zero stored on
+// colour 2 (the residual before a restriction).
+template <int MODE>
+__global__ void __launch_bounds__(BX* BY)
+    k_delta_diag13(Dims d, double c1, double c2, const double* __restrict__ phi, const double* __restrict__ fs,
+                   int dl, int dout, void* __restrict__ out, const DevState* __restrict__ st,
+                   double* __restrict__ partials) {
+  static_assert(MODE == 0 || MODE == 1, "every-node passes use k_delta_diag13_all");
+  constexpr int NM = 2;   // members evaluated: colours 0 and 1
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
+  const int kr0 = blockIdx.z * dl + 1;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kr0 + 1));
+  double s2 = 0.0;
+  if (u0 < u1 && 1 + 3 * t <= ni) {
+    const int jk = jn0 + nk + 1 - kr0;
+    const long long sy = d.sy(), sz = d.sz(), step = sy - sz;
+    const long long c0 = d.at(1, jn0 + u0 + 1, nk + 1 - (kr0 + u0) + 1);   // x node 0 of the first walk node
+    long long cm[3];
+    bool ok[3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+      const int x = 1 + 3 * t + (((m - jk - 1) % 3) + 3) % 3;   // the member of colour m
+      ok[m] = x <= ni;
+      cm[m] = c0 + (ok[m] ? x : 1 + 3 * t);
+    }
+    double su1[NM], su2[NM], su2n[NM], e1[NM], w1[NM], n1[NM], d1[NM], e2[NM], w2[NM], n2[NM], d2[NM], f[NM], xc[NM];
+#pragma unroll
+    for (int m = 0; m < NM; m++) {
+      const long long c = cm[m];
+      const long long c2n = u0 + 1 < u1 ? c + step : c;
+      su1[m] = phi[c - sy] + phi[c + sz];
+      su2[m] = phi[c - 2 * sy] + phi[c + 2 * sz];
+      su2n[m] = phi[c2n - 2 * sy] + phi[c2n + 2 * sz];
+      e1[m] = phi[c + 1]; w1[m] = phi[c - 1]; n1[m] = phi[c + sy]; d1[m] = phi[c - sz];
+      e2[m] = phi[c + 2]; w2[m] = phi[c - 2]; n2[m] = phi[c + 2 * sy]; d2[m] = phi[c - 2 * sz];
+      f[m] = fs[c]; xc[m] = phi[c];
+    }
+    for (int u = u0; u < u1; u++) {
+      const bool more = u + 1 < u1;
+#pragma unroll
+      for (int m = 0; m < NM; m++) {
+        const long long c = cm[m];
+        const long long cn = more ? c + step : c;
+        const double e1n = phi[cn + 1], w1n = phi[cn - 1], n1n = phi[cn + sy], d1n = phi[cn - sz];
+        const double e2n = phi[cn + 2], w2n = phi[cn - 2], n2n = phi[cn + 2 * sy], d2n = phi[cn - 2 * sz];
+        const double fn = fs[cn], xn = phi[cn];
+        const double nd1 = n1[m] + d1[m], nd2 = n2[m] + d2[m];
+        const double v1 = fma(((e1[m] + w1[m]) + su1[m]) + nd1, c1, f[m]);
+        const double dl_ = fma(((e2[m] + w2[m]) + su2[m]) + nd2, c2, v1) - xc[m];
+        if (ok[m]) {
+          if (MODE == 1) ((double*)out)[c] = dl_;
+          else s2 = fma(dl_, dl_, s2);
+        }
+        su1[m] = nd1;
+        su2[m] = su2n[m];
+        su2n[m] = nd2;
+        cm[m] = cn;
+        e1[m] = e1n; w1[m] = w1n; n1[m] = n1n; d1[m] = d1n;
+        e2[m] = e2n; w2[m] = w2n; n2[m] = n2n; d2[m] = d2n;
+        f[m] = fn; xc[m] = xn;
+      }
+      if (MODE == 1 && ok[2]) {   // the last colour: exactly zero after the sweep
+        ((double*)out)[cm[2]] = 0.0;
+        cm[2] += step;
+      }
+    }
+  }
+  if (MODE == 0) block_sum_max(s2, 0.0, partials);
+}
+
+// Every node (modes 2 and 3 of k_delta_diag13): one x per thread (consecutive
+// lanes, consecutive x), one walk with its own carried pair sums; no lane is
+// idle because every colour is evaluated.
+template <bool STORE>
+__global__ void __launch_bounds__(BX* BY)
+    k_delta_diag13_all(Dims d, double c1, double c2, const double* __restrict__ phi, const double* __restrict__ fs,
+                       int dl, int dout, void* __restrict__ out, const DevState* __restrict__ st,
+                       double* __restrict__ partials) {
+  const int x = blockIdx.x * BX + threadIdx.x + 1;
+  const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
+  const int kr0 = blockIdx.z * dl + 1;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kr0 + 1));
+  double s2 = 0.0;
+  float s2f = 0.0f, mxf = 0.0f;
+  const double oscale = STORE ? st->scale_next : 1.0;
+  const int oexp = pow2_exponent(oscale);
+  if (u0 < u1 && x <= ni) {
+    const long long sy = d.sy(), sz = d.sz(), step = sy - sz;
+    long long c = d.at(x + 1, jn0 + u0 + 1, nk + 1 - (kr0 + u0) + 1);
+    const long long c2n = u0 + 1 < u1 ? c + step : c;
+    double su1 = phi[c - sy] + phi[c + sz];
+    double su2 = phi[c - 2 * sy] + phi[c + 2 * sz];
+    double su2n = phi[c2n - 2 * sy] + phi[c2n + 2 * sz];
+    double e1 = phi[c + 1], w1 = phi[c - 1], n1 = phi[c + sy], d1 = phi[c - sz];
+    double e2 = phi[c + 2], w2 = phi[c - 2], n2 = phi[c + 2 * sy], d2 = phi[c - 2 * sz];
+    double f = fs[c], xc = phi[c];
+    for (int u = u0; u < u1; u++) {
+      const long long cn = u + 1 < u1 ? c + step : c;
+      const double e1n = phi[cn + 1], w1n = phi[cn - 1], n1n = phi[cn + sy], d1n = phi[cn - sz];
+      const double e2n = phi[cn + 2], w2n = phi[cn - 2], n2n = phi[cn + 2 * sy], d2n = phi[cn - 2 * sz];
+      const double fn = fs[cn], xn = phi[cn];
+      const double nd1 = n1 + d1, nd2 = n2 + d2;
+      const double v1 = fma(((e1 + w1) + su1) + nd1, c1, f);
+      const double dl_ = fma(((e2 + w2) + su2) + nd2, c2, v1) - xc;
+      if (STORE) {
+        const float v = oexp != INT_MIN ? f64_to_f32_pow2(dl_, oexp) : (float)(dl_ * oscale);
+        s2f = fmaf(v, v, s2f);
+        mxf = fmaxf(mxf, fabsf(v));
+        if (dout == DT_F32) ((float*)out)[c] = v;
+        else ((__nv_bfloat16*)out)[c] = __float2bfloat16_rn(v);
+      } else {
+        s2 = fma(dl_, dl_, s2);
+      }
+      su1 = nd1;
+      su2 = su2n;
+      su2n = nd2;
+      c = cn;
+      e1 = e1n; w1 = w1n; n1 = n1n; d1 = d1n;
+      e2 = e2n; w2 = w2n; n2 = n2n; d2 = d2n;
+      f = fn;
+      xc = xn;
+    }
+  }
+  if (STORE) block_sum_max_scaled(s2f, mxf, oscale, partials);
+  else block_sum_max(s2, 0.0, partials);
+}
+
+static dim3 diag13_grid(const Dims& d, int* dl_out) {
+  const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+  if (dl_out) *dl_out = dl;
+  const int triples = (d.ni() + 2) / 3;
+  return dim3((triples + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
+}
+
+static dim3 diag13_all_grid(const Dims& d) {
+  const dim3 g = diag13_grid(d, nullptr);
+  return dim3((d.ni() + BX - 1) / BX, g.y, g.z);
+}
+
+int delta_diag13_blocks(const Dims& d) {
+  const dim3 g = diag13_all_grid(d);   // the larger of the two grids
+  return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, const double* phi, const double* fs,
+                                int dout, void* out, const DevState* st, double* partials, int* nblocks,
+                                cudaStream_t s) {
+  if (!is_iso(h) || d.g != 2 || mode < 0 || mode > 3 || (mode == 1 && out == nullptr) ||
+      (mode == 3 && (out == nullptr || st == nullptr || (dout != DT_F32 && dout != DT_BF16))))
+    return cudaErrorInvalidValue;
+  const Coef<double> cf = make_coef<double>(d, h, 4);
+  int dl = 0;
+  const dim3 grid = diag13_grid(d, &dl), blk(BX, BY);
+  if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+  const double a = cf.c1[0], b = cf.c2[0];
+  switch (mode) {
+    case 0: k_delta_diag13<0><<<grid, blk, 0, s>>>(d, a, b, phi, fs, dl, DT_F64, nullptr, nullptr, partials); break;
+    case 1: k_delta_diag13<1><<<grid, blk, 0, s>>>(d, a, b, phi, fs, dl, DT_F64, out, nullptr, nullptr); break;
+    case 2:
+    case 3: {
+      const dim3 ga = diag13_all_grid(d);
+      if (nblocks) *nblocks = (int)(ga.x * ga.y * ga.z);
+      if (mode == 2)
+        k_delta_diag13_all<false><<<ga, blk, 0, s>>>(d, a, b, phi, fs, dl, DT_F64, nullptr, nullptr, partials);
+      else
+        k_delta_diag13_all<true><<<ga, blk, 0, s>>>(d, a, b, phi, fs, dl, dout, out, st, partials);
+      break;
+    }
+  }
+  return cudaGetLastError();
+}
+
 template <int G, bool ISO, typename T, typename TO>
 static cudaError_t delta_skip_t(const Dims& d, const double h[3], int order, const void* phi,
                                 const void* fs, void* out, cudaStream_t s) {
   using C = typename St<T>::C;
   constexpr int NCOL = G == 1 ? 2 : 3;
   Coef<C> cf = make_coef<C>(d, h, order);
+  if constexpr (G == 2 && ISO && sizeof(T) == 8 && sizeof(TO) == 8)
+    return launch_delta_diag13(d, h, 1, (const double*)phi, (const double*)fs, DT_F64, out, nullptr, nullptr, nullptr, s);
   if constexpr (G == 1 && ISO && sizeof(T) == 8 && sizeof(TO) == 8) {
     const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
     const int pairs = (d.ni() + 1) / 2;

@@ -48,6 +48,18 @@ cudaError_t launch_sweep_colour(const Dims& d, int order, const double h[3], int
 cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const void* f, void* fs,
                                  cudaStream_t s);
 
+// FP64 13-point residual passes on equal spacings along (j, k) anti-diagonals
+// (every delta equal to launch_delta's bit for bit; reductions in another
+// order).  mode 0: partials {sum of delta^2 over colours 0 and 1, 0} (the norm
+// after a sweep); 1: delta of colours 0 and 1 into out (FP64), zero on colour 2;
+// 2: partials {sum of delta^2 over every node, 0}; 3: the refinement pass of
+// launch_delta_st (out FP32 or BF16 scaled by st->scale_next, FP32 sum and max).
+// nblocks: the partials count, delta_diag13_blocks(d).
+int delta_diag13_blocks(const Dims& d);
+cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, const double* phi, const double* fs,
+                                int dout, void* out, const DevState* st, double* partials, int* nblocks,
+                                cudaStream_t s);
+
 // FP64 reference norm ||f - A phi0|| with every interior value of phi0 read
 // as zero (only the boundary data enter): partials {sum, max} per block of
 // point_grid(d) (cart_partials_count blocks), equal to launch_delta's with

@@ -390,10 +390,10 @@ cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState
   const int ncol = h->order == 2 ? 2 : 3;
   const Work w = work_of(L, h->order);
   cudaError_t e;
-  // FP64 7-point passes on equal spacings walk (j, k) diagonals: 5 FP64
-  // instructions per update instead of 6
-  const bool diag = h->order == 2 && L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
-  const double per_update = diag ? 5.0 : 6.0 * w.G;
+  // FP64 passes on equal spacings walk (j, k) diagonals: 5 FP64 instructions
+  // per update instead of 6 (13-point: 10 instead of 12)
+  const bool diag = L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
+  const double per_update = diag ? 5.0 * w.G : 6.0 * w.G;
   for (int c = 0; c < ncol; c++) {
     // one colour pass reads phi everywhere, fs and phi on its colour, writes phi on its colour
     prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, w.n * w.S * (1.0 + 2.0 / ncol),
@@ -469,8 +469,8 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
     // colour's residual is exactly zero and is not evaluated (not for BF16
     // storage, where it is the rounding error of the stored value)
     const double frac = h->order == 2 ? 0.5 : 2.0 / 3.0;
-    const bool diag = h->order == 2 && L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
-    if (l == 0) prof_begin(h, PC_DELTA0, w.n * (w.S * (1.0 + frac) + w.St), w.n * frac * ((diag ? 5.0 : 6.0 * w.G) + 1.0), w.fp64, s);
+    const bool diag = L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
+    if (l == 0) prof_begin(h, PC_DELTA0, w.n * (w.S * (1.0 + frac) + w.St), w.n * frac * ((diag ? 5.0 * w.G : 6.0 * w.G) + 1.0), w.fp64, s);
     e = (h->nlaunch += 1, launch_delta_after_sweep(L.d, h->order, L.h, L.dt, L.phi, L.fs, L.dt_tmp, L.tmp, s));
     if (l == 0) prof_end(h, s);
     if (e != cudaSuccess) return e;
@@ -513,20 +513,25 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
   const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
   if (after_sweep && out == nullptr) {
     const double frac = h->order == 2 ? 0.5 : 2.0 / 3.0;   // colours evaluated
-    const bool diag = h->order == 2 && h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2];   // diagonal walks
-    prof_begin(h, PC_NORM0, n * 8.0 * (1.0 + frac), n * frac * ((diag ? 5.0 : 6.0 * G) + 2.0), 1, s);
+    const bool diag = h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2];   // diagonal walks
+    prof_begin(h, PC_NORM0, n * 8.0 * (1.0 + frac), n * frac * ((diag ? 5.0 * G : 6.0 * G) + 2.0), 1, s);
     int nb = 0;
     cudaError_t e = (h->nlaunch += 1, launch_delta_colours(h->d0, h->order, h->h0, phi, h->fs64, h->partials, &nb, s));
     prof_end(h, s);
     if (e != cudaSuccess) return e;
     return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, mode, h->st, s, cond, chunk));
   }
-  if (h->order == 2 && h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2]) {
-    // (j, k) diagonal walks: 5 + 1 FP64 instructions per node, + 1 for the FP64 sum of squares
-    prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? 6.0 : 7.0), 1, s);
+  if (h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2]) {
+    // (j, k) diagonal walks: 5 + 1 FP64 instructions per node (13-point: 10 + 1),
+    // + 1 for the FP64 sum of squares
+    const double per = h->order == 2 ? 6.0 : 11.0;
+    prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? per : per + 1.0), 1, s);
     int nb = 0;
-    cudaError_t e = (h->nlaunch += 1, launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, out ? h->st : nullptr,
-                                                        h->partials, &nb, s));
+    cudaError_t e = (h->nlaunch += 1,
+                     h->order == 2 ? launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, out ? h->st : nullptr,
+                                                       h->partials, &nb, s)
+                                   : launch_delta_diag13(h->d0, h->h0, out ? 3 : 2, phi, h->fs64, dout, out,
+                                                         out ? h->st : nullptr, h->partials, &nb, s));
     prof_end(h, s);
     if (e != cudaSuccess) return e;
     return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, mode, h->st, s, cond, chunk));

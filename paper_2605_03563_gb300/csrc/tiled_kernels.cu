@@ -1075,7 +1075,7 @@ static dim3 delta_colours_grid(const Dims& d, int order) {
 
 int delta_colours_partials(const Dims& d, int order) {
   const dim3 g = delta_colours_grid(d, order), gd = diag_grid(d);
-  return (int)std::max(g.x * g.y * g.z, order == 2 ? gd.x * gd.y * gd.z : 0u);
+  return (int)std::max(g.x * g.y * g.z, order == 2 ? gd.x * gd.y * gd.z : (unsigned)delta_diag13_blocks(d));
 }
 
 cudaError_t launch_delta_colours(const Dims& d, int order, const double h[3], const double* phi,
@@ -1089,6 +1089,7 @@ cudaError_t launch_delta_colours(const Dims& d, int order, const double h[3], co
     k_delta_red_diag<<<gd, blk, 0, s>>>(d, cf.c1[0], phi, fs, diag_walk(d.nk()), partials);
     return cudaGetLastError();
   }
+  if (order == 4 && iso) return launch_delta_diag13(d, h, 0, phi, fs, DT_F64, nullptr, nullptr, partials, nblocks, s);
   const dim3 grid = delta_colours_grid(d, order);
   if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
   if (order == 2) {
