@@ -441,3 +441,23 @@ def test_prolongation_midpoints_bitwise(pkg):
     ref[fine.interior] = base[fine.interior] + ez[fine.interior]
     with np.errstate(invalid="ignore"):
         assert np.array_equal(got[fine.interior], ref[fine.interior])
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_mg_equal_spacing_noncubic(pkg, order, prec):
+    """Equal spacings on a non-cubic box: the FP64 passes walk (j, k) diagonals
+    (7-point) or anti-diagonals (13-point, three colours), clipped at the
+    unequal j and k extents; multipole boundary, the same V-cycle count as the
+    oracle and its potential (FP64), or the refinement tolerance (FP32 inner)."""
+    n = (64, 48, 32)
+    box = (1.0, 0.75, 0.5)   # h = 1/64 on every axis
+    rho = np.abs(W.rng(21).standard_normal(W.cart_shape(n, order)))
+    info, info_o, got, ref = _solve_pair(pkg, n, order, rho, np.zeros(W.cart_shape(n, order)), "mg", 1e-10,
+                                         bc="multipole", lmax=4, box=box, prec=prec)
+    assert info.converged and info_o.converged
+    if prec == "fp64":
+        assert info.iterations == info_o.iterations
+        assert rel_err(got, ref) <= FP64_TOL
+    else:
+        assert rel_err(got, ref) <= 1e-7
