@@ -1341,6 +1341,9 @@ static cudaError_t coarse_t(const Dims& d, const double h[3], int order, const v
   const int nint = d.ni() * d.nj() * d.nk();
   int ppt = 1;
   while (ppt < 16 && (nint + ppt - 1) / ppt > 128) ppt *= 2;
+  // up to 512 unknowns: 4 warps (one per SM sub-partition, each with its FP64
+  // unit) with up to 4 unknowns per thread
+  if (nint <= 512) ppt = (nint + 127) / 128;
   // very elongated coarsest levels (more than 16 x 256 unknowns): up to 1024 threads x 8
   const bool wide = (nint + ppt - 1) / ppt > 256;
   if (wide) ppt = 8;
@@ -1359,6 +1362,7 @@ static cudaError_t coarse_t(const Dims& d, const double h[3], int order, const v
   if (wide) PS_COARSE_LAUNCH(8, 1024)
   else if (ppt == 1) PS_COARSE_LAUNCH(1, 256)
   else if (ppt == 2) PS_COARSE_LAUNCH(2, 256)
+  else if (ppt == 3) PS_COARSE_LAUNCH(3, 256)
   else if (ppt == 4) PS_COARSE_LAUNCH(4, 256)
   else if (ppt == 8) PS_COARSE_LAUNCH(8, 256)
   else PS_COARSE_LAUNCH(16, 256)
