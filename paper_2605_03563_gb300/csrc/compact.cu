@@ -649,8 +649,9 @@ static cudaError_t launch_march_t(const Dims& d, const W27& A, const W27& M, dou
   }
   const int sms = device_sm_count();
   const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + T::GTY - 1) / T::GTY, nk = d.nk();
-  // about two to three waves, z-chunks of at least 16 planes (4 extra staged planes each)
-  const int want = std::max(1, 5 * sms * blocks_per_sm / (2 * gx * gy));
+  // z-chunks of at least 16 planes (4 extra staged planes each): about one wave
+  // with the small tile, two to three with the large one
+  const int want = std::max(1, (GR <= 4 ? 2 : 5) * sms * blocks_per_sm / (2 * gx * gy));
   const int zc = std::max(16, (nk + want - 1) / want);
   const dim3 grid(gx, gy, (nk + zc - 1) / zc);
   kern<<<grid, 32 * GW, T::SMEM, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
