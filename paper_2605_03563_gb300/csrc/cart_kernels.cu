@@ -100,20 +100,21 @@ __device__ __forceinline__ void store_dt(void* out, int dt, long long p, double 
   else ((__nv_bfloat16*)out)[p] = __float2bfloat16_rn((float)v);
 }
 
-// Block reduction of {sum, max} into partials[2*block], partials[2*block+1].
+// Block reduction of {sum, max} into partials[2*block], partials[2*block+1];
+// m >= 0 (a max of magnitudes), reduced by its bits on the integer pipe.
 __device__ __forceinline__ void block_sum_max(double s, double m, double* partials) {
   __shared__ double sh[64];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
   s = warp_sum(s);
-  m = warp_max(m);
+  m = warp_absmax(m);
   if (lane == 0) { sh[warp] = s; sh[32 + warp] = m; }
   __syncthreads();
   if (warp == 0) {
     double a = lane < nw ? sh[lane] : 0.0;
     double b = lane < nw ? sh[32 + lane] : 0.0;
     a = warp_sum(a);
-    b = warp_max(b);
+    b = warp_absmax(b);
     if (lane == 0) {
       int bid = block_linear_id();
       partials[2 * bid] = a;
@@ -170,9 +171,7 @@ __global__ void __launch_bounds__(BX* BY)
   const int k1 = min(k0 + zc, G + d.nk());
   const long long sy = d.sy(), sz = d.sz();
   double s2 = 0.0, mx = 0.0;
-  // max |delta| in FP64 as the largest bit pattern of |delta| (the order of
-  // non-negative doubles is that of their bits): no FP64 instruction
-  unsigned long long mxb = 0ull;
+  AbsMax mxb;   // max |delta| without FP64 instructions
   float s2f = 0.0f, mxf = 0.0f;
   double oscale = out_scale;
   if (st != nullptr) oscale = st->scale_next;
@@ -204,7 +203,7 @@ __global__ void __launch_bounds__(BX* BY)
         continue;
       }
       if (RED >= 1) s2 = fma(dd, dd, s2);
-      if (RED == 2) mxb = max(mxb, (unsigned long long)__double_as_longlong(dd) & 0x7fffffffffffffffull);
+      if (RED == 2) mxb.take(dd);
       if (out != nullptr) {
         if (sizeof(C) == sizeof(float)) {
           // FP32 arithmetic levels never touch the FP64 pipe on the store path
@@ -222,37 +221,118 @@ __global__ void __launch_bounds__(BX* BY)
     block_sum_max_scaled(s2f, mxf, oscale, partials);
     return;
   }
-  if (RED == 2) mx = __longlong_as_double((long long)mxb);
+  if (RED == 2) mx = mxb.value();
   if (RED >= 1) block_sum_max(s2, mx, partials);
 }
 
-// Reference norm ||f - A phi0|| of the boundary data (interior read as zero),
-// FP64: on a node whose neighbours are all interior the value is fs itself,
-// so away from the boundary the pass reads fs alone, one FP64 FMA per node,
-// max |value| on the integer pipe.  Threads, their order over z and the block
-// reduction are those of k_delta, so the result equals its bits.
+// Set-up copy of the caller's initial guess (dense rows) into the handle's
+// pitched array, one warp per row.  It records in st->guess_nonzero whether
+// any interior node of the guess is nonzero (+0 and -0 both count as zero):
+// from a zero guess the initial residual f - A phi0 is the reference vector,
+// and the initial residual pass takes the reference norm instead.
+__global__ void __launch_bounds__(256)
+    k_copy_guess(Dims dd, Dims sd, const double* __restrict__ src, double* __restrict__ dst,
+                 DevState* __restrict__ st) {
+  const long long rows = (long long)sd.ey * sd.ez;
+  const long long row = blockIdx.x * 8LL + (threadIdx.x >> 5);
+  int nz = 0;
+  if (row < rows) {
+    const int j = (int)(row % sd.ey), k = (int)(row / sd.ey), g = sd.g;
+    const bool inrow = j >= g && j < sd.ey - g && k >= g && k < sd.ez - g;
+    const double* a = src + row * sd.px;
+    double* b = dst + row * dd.px;
+#pragma unroll 4
+    for (int i = threadIdx.x & 31; i < sd.ex; i += 32) {
+      const double v = a[i];
+      b[i] = v;
+      if (inrow && i >= g && i < sd.ex - g && ((unsigned long long)__double_as_longlong(v) << 1) != 0ull) nz = 1;
+    }
+  }
+  if (__syncthreads_or(nz) && threadIdx.x == 0) st->guess_nonzero = 1;
+}
+
+cudaError_t launch_copy_guess(const Dims& dd, const Dims& sd, const double* src, double* dst, DevState* st,
+                              cudaStream_t s) {
+  if (dd.ex != sd.ex || dd.ey != sd.ey || dd.ez != sd.ez || dd.g != sd.g || dd.px < sd.px)
+    return cudaErrorInvalidValue;
+  const long long rows = (long long)sd.ey * sd.ez;
+  k_copy_guess<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(dd, sd, src, dst, st);
+  return cudaGetLastError();
+}
+
+// Set-up pass of FP64 solves: fs = factor * rho on interior nodes and, in the
+// same sweep, the partials of the reference norm ||f - A phi0||, phi0 = the
+// boundary data of phi with every interior value read as zero.  The value at
+// a node is fs plus c * phi over its boundary neighbours, added axis by axis
+// (x, then y, then z; per axis the offsets o = 1..G in turn, each term one FMA
+// of a selected ghost value): away from the boundary it is fs itself, and the
+// pass costs one FP64 multiply and one FMA per node.  The x terms run in the
+// warps that hold a lane next to an x boundary (all lanes of such a warp add
+// the term, zero where it does not apply, so no lane walks alone); the y and
+// z terms are uniform over a warp.  The max |value| runs on the integer pipe.
+template <int G>
+__device__ __forceinline__ double add_ghost_terms(double v, const double* __restrict__ phi, long long p,
+                                                  long long stride, int a, int n, const Coef<double>& cf,
+                                                  int axis) {
+  // a = array index along the axis; interior [G, G + n - 1]
+#pragma unroll
+  for (int o = 1; o <= G; o++) {
+    const bool lo = a - o < G, hi = a + o > G + n - 1;
+    const double c = o == 1 ? cf.c1[axis] : cf.c2[axis];
+    if (n >= 2 * o) {
+      // one side at most (the node would need n < 2o to see both ghosts)
+      const double b = lo ? phi[p - o * stride] : (hi ? phi[p + o * stride] : 0.0);
+      v = fma(b, c, v);
+    } else {
+      const double b = (lo ? phi[p - o * stride] : 0.0) + (hi ? phi[p + o * stride] : 0.0);
+      v = fma(b, c, v);
+    }
+  }
+  return v;
+}
+
 template <int G>
 __global__ void __launch_bounds__(BX* BY)
-    k_ref_norm(Dims d, Coef<double> cf, const double* __restrict__ phi, const double* __restrict__ fs,
-               double* __restrict__ partials) {
+    k_scale_rhs_ref(Dims d, Dims du, double factor, Coef<double> cf, const double* __restrict__ rho,
+                    const double* __restrict__ phi, double* __restrict__ fs, double* __restrict__ partials) {
   const int i = blockIdx.x * BX + threadIdx.x + G;
   const int j = blockIdx.y * BY + threadIdx.y + G;
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + G;
   const int k1 = min(k0 + zc, G + d.nk());
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const bool act = i < G + ni && j < G + nj;
+  // the warp holds a lane next to an x boundary (decided once, warp-uniform)
+  const bool wx = __any_sync(0xffffffffu, act && (i < 2 * G || i >= ni));
+  const bool yb = j < 2 * G || j >= nj;
   double s2 = 0.0;
-  unsigned long long mxb = 0ull;
-  if (i < G + d.ni() && j < G + d.nj()) {
-    const bool inxy = i >= 2 * G && i < d.ni() && j >= 2 * G && j < d.nj();
-#pragma unroll 2
+  AbsMax mx;
+  if (act) {
+    const long long syu = du.sy(), szu = du.sz();
     for (int k = k0; k < k1; k++) {
-      const long long p = d.at(i, j, k);
-      const double v = inxy && k >= 2 * G && k < d.nk() ? fs[p] : gs_value_zero_interior<G>(phi, d, i, j, k, cf, fs[p]);
+      const long long pu = du.at(i, j, k);
+      const double f = factor * rho[pu];
+      fs[d.at(i, j, k)] = f;
+      double v = f;
+      if (wx) v = add_ghost_terms<G>(v, phi, pu, 1, i, ni, cf, 0);
+      if (yb) v = add_ghost_terms<G>(v, phi, pu, syu, j, nj, cf, 1);
+      if (k < 2 * G || k >= nk) v = add_ghost_terms<G>(v, phi, pu, szu, k, nk, cf, 2);
       s2 = fma(v, v, s2);
-      mxb = max(mxb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull);
+      mx.take(v);
     }
   }
-  block_sum_max(s2, __longlong_as_double((long long)mxb), partials);
+  block_sum_max(s2, mx.value(), partials);
+}
+
+cudaError_t launch_scale_rhs_ref(const Dims& d, const Dims& du, int order, const double h[3], double factor,
+                                 const double* rho, const double* phi, double* fs, double* partials,
+                                 cudaStream_t s) {
+  if (du.ex != d.ex || du.ey != d.ey || du.ez != d.ez || du.g != d.g || d.g != order / 2)
+    return cudaErrorInvalidValue;
+  const Coef<double> cf = make_coef<double>(d, h, order);
+  if (order == 2) k_scale_rhs_ref<1><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, du, factor, cf, rho, phi, fs, partials);
+  else k_scale_rhs_ref<2><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, du, factor, cf, rho, phi, fs, partials);
+  return cudaGetLastError();
 }
 
 template <int G, bool ISO, typename TI>
@@ -271,14 +351,6 @@ static cudaError_t delta_t(const Dims& d, const double h[3], int order, const vo
   else
     k_delta<G, ISO, TI, 1><<<point_grid(d), dim3(BX, BY), 0, s>>>(
         d, cf, (const TI*)phi, (const TI*)fs, dout, out, out_scale, st, zi ? 1 : 0, partials);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ref_norm(const Dims& d, int order, const double h[3], const double* phi, const double* fs,
-                            double* partials, cudaStream_t s) {
-  const Coef<double> cf = make_coef<double>(d, h, order);
-  if (order == 2) k_ref_norm<1><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, cf, phi, fs, partials);
-  else k_ref_norm<2><<<point_grid(d), dim3(BX, BY), 0, s>>>(d, cf, phi, fs, partials);
   return cudaGetLastError();
 }
 
@@ -401,11 +473,14 @@ __global__ void __launch_bounds__(BX* BY)
 // equals k_delta's bit for bit and only the reductions run in another order).
 // STORE: the refinement pass of k_delta (the scaled FP32/BF16 inner right-hand
 // side, the FP32 sum of squares and max of the scaled values); otherwise the
-// FP64 sum of delta^2.  Partials {sum, max} per block.
+// FP64 sum of delta^2.  Partials {sum, max} per block.  !STORE with a state:
+// the initial residual pass, which returns at once when the set-up copy found
+// the guess's interior zero (its residual is then the reference vector).
 template <bool STORE>
 __global__ void __launch_bounds__(BX* BY)
     k_delta_diag(Dims d, double c1, const double* __restrict__ phi, const double* __restrict__ fs, int dl, int dout,
                  void* __restrict__ out, const DevState* __restrict__ st, double* __restrict__ partials) {
+  if (!STORE && st != nullptr && st->guess_nonzero == 0) return;
   const int t = blockIdx.x * BX + threadIdx.x;
   const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
   const int kn0 = blockIdx.z * dl + 1;
@@ -481,7 +556,7 @@ cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* ph
   if (out != nullptr)
     k_delta_diag<true><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, dout, out, st, partials);
   else
-    k_delta_diag<false><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, DT_F64, nullptr, nullptr, partials);
+    k_delta_diag<false><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, DT_F64, nullptr, st, partials);
   return cudaGetLastError();
 }
 
@@ -565,12 +640,14 @@ __global__ void __launch_bounds__(BX* BY)
 
 // Every node (modes 2 and 3 of k_delta_diag13): one x per thread (consecutive
 // lanes, consecutive x), one walk with its own carried pair sums; no lane is
-// idle because every colour is evaluated.
+// idle because every colour is evaluated.  !STORE with a state: the initial
+// residual pass, skipped on a zero guess as in k_delta_diag.
 template <bool STORE>
 __global__ void __launch_bounds__(BX* BY)
     k_delta_diag13_all(Dims d, double c1, double c2, const double* __restrict__ phi, const double* __restrict__ fs,
                        int dl, int dout, void* __restrict__ out, const DevState* __restrict__ st,
                        double* __restrict__ partials) {
+  if (!STORE && st != nullptr && st->guess_nonzero == 0) return;
   const int x = blockIdx.x * BX + threadIdx.x + 1;
   const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
   const int kr0 = blockIdx.z * dl + 1;
@@ -642,7 +719,7 @@ int delta_diag13_blocks(const Dims& d) {
 cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, const double* phi, const double* fs,
                                 int dout, void* out, const DevState* st, double* partials, int* nblocks,
                                 cudaStream_t s) {
-  if (!is_iso(h) || d.g != 2 || mode < 0 || mode > 3 || (mode == 1 && out == nullptr) ||
+  if (!is_iso(h) || d.g != 2 || mode < 0 || mode > 3 || (mode == 1 && out == nullptr) || (mode < 2 && st != nullptr) ||
       (mode == 3 && (out == nullptr || st == nullptr || (dout != DT_F32 && dout != DT_BF16))))
     return cudaErrorInvalidValue;
   const Coef<double> cf = make_coef<double>(d, h, 4);
@@ -658,7 +735,7 @@ cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, cons
       const dim3 ga = diag13_all_grid(d);
       if (nblocks) *nblocks = (int)(ga.x * ga.y * ga.z);
       if (mode == 2)
-        k_delta_diag13_all<false><<<ga, blk, 0, s>>>(d, a, b, phi, fs, dl, DT_F64, nullptr, nullptr, partials);
+        k_delta_diag13_all<false><<<ga, blk, 0, s>>>(d, a, b, phi, fs, dl, DT_F64, nullptr, st, partials);
       else
         k_delta_diag13_all<true><<<ga, blk, 0, s>>>(d, a, b, phi, fs, dl, dout, out, st, partials);
       break;

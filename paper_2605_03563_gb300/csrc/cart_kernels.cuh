@@ -52,25 +52,37 @@ cudaError_t launch_scale_rhs_any(const Dims& d, double factor, int dt, const voi
 // (every delta equal to launch_delta's bit for bit; reductions in another
 // order).  mode 0: partials {sum of delta^2 over colours 0 and 1, 0} (the norm
 // after a sweep); 1: delta of colours 0 and 1 into out (FP64), zero on colour 2;
-// 2: partials {sum of delta^2 over every node, 0}; 3: the refinement pass of
-// launch_delta_st (out FP32 or BF16 scaled by st->scale_next, FP32 sum and max).
-// nblocks: the partials count, delta_diag13_blocks(d).
+// 2: partials {sum of delta^2 over every node, 0}, and with st the initial
+// residual pass, which writes nothing when st->guess_nonzero == 0 (finisher
+// mode 4); 3: the refinement pass of launch_delta_st (out FP32 or BF16 scaled
+// by st->scale_next, FP32 sum and max).  nblocks: the partials count,
+// delta_diag13_blocks(d).
 int delta_diag13_blocks(const Dims& d);
 cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, const double* phi, const double* fs,
                                 int dout, void* out, const DevState* st, double* partials, int* nblocks,
                                 cudaStream_t s);
 
-// FP64 reference norm ||f - A phi0|| with every interior value of phi0 read
-// as zero (only the boundary data enter): partials {sum, max} per block of
-// point_grid(d) (cart_partials_count blocks), equal to launch_delta's with
-// zero_interior bit for bit.
-cudaError_t launch_ref_norm(const Dims& d, int order, const double h[3], const double* phi, const double* fs,
-                            double* partials, cudaStream_t s);
+// Set-up copy of the initial guess (same logical extents, dst pitch >= src
+// pitch) that sets st->guess_nonzero when an interior node is nonzero.
+cudaError_t launch_copy_guess(const Dims& dd, const Dims& sd, const double* src, double* dst, DevState* st,
+                              cudaStream_t s);
+
+// FP64 set-up pass: fs = factor * rho on interior nodes (rho in the layout du,
+// fs in d: same logical extents) and the partials {sum, max} of the reference
+// norm ||f - A phi0|| with every interior value of phi (layout du) read as
+// zero (only the boundary data enter), per block of point_grid(d)
+// (cart_partials_count blocks); the values equal launch_delta's with
+// zero_interior up to the order in which the boundary terms are added.
+cudaError_t launch_scale_rhs_ref(const Dims& d, const Dims& du, int order, const double h[3], double factor,
+                                 const double* rho, const double* phi, double* fs, double* partials,
+                                 cudaStream_t s);
 
 // FP64 residual pass of the 7-point stencil on equal spacings along (j, k)
 // diagonals (every delta equal to launch_delta's / launch_delta_st's bit for
 // bit; the reductions run in another order).  out == NULL: partials {sum of
-// delta^2, 0}; otherwise the refinement pass of launch_delta_st (out FP32 or
+// delta^2, 0} (with st: the initial residual pass, which writes nothing when
+// st->guess_nonzero == 0, finisher mode 4); otherwise the refinement pass of
+// launch_delta_st (out FP32 or
 // BF16, scaled by st->scale_next, FP32 sum and max of the scaled values).
 // Returns the block count in nblocks (at most delta_colours_partials(d, 2)).
 cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* phi, const double* fs, int dout,

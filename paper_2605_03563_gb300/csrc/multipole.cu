@@ -8,8 +8,14 @@
 // to q_lm with a fixed sparse table built on the host.  The per-node cost is
 // l_max+1 FP64 multiply-adds and one coalesced read of rho.
 //
-// Boundary values (Eq. outer_expansion): Phi = -G sum_lm q_lm R_lm(x) / r^(2l+1),
-// with R_lm evaluated per node from the recurrences
+// Boundary values (Eq. outer_expansion): Phi = -G sum_lm q_lm R_lm(x) / r^(2l+1).
+// P_l = sum_m q_lm R_lm is a homogeneous polynomial of degree l with
+// coefficients C_abc (a+b+c = l), formed once per solve from q and the table.
+// Since r^-(2l+1) x^a y^b z^c = (1/r) (x/r^2)^a (y/r^2)^b (z/r^2)^c, the sum
+// over l is one polynomial of total degree <= l_max in (x, y, z)/r^2:
+//   Phi = -G (1/r) F(x/r^2, y/r^2, z/r^2),  F(u, v, w) = sum C_abc u^a v^b w^c,
+// evaluated per node by nested Horner, one FMA per coefficient.  The table
+// of R_lm's monomials is built on the host from the recurrences
 //   (x + i y)^m = C_m + i S_m,
 //   T_mm = (2m-1)!!,  T_{m+1,m} = (2m+1) z T_mm,
 //   (l-m) T_lm = (2l-1) z T_{l-1,m} - (l+m-1) r^2 T_{l-2,m},
@@ -136,6 +142,20 @@ void build_multipole_tables(int L, MultipoleTables* t) {
     }
   }
   t->off[W * W] = (int)t->mono.size();
+  // transpose: for every monomial slot, its (lm, val) pairs in increasing lm
+  const int NS = W * W * W;
+  t->toff.assign(NS + 1, 0);
+  for (int e = 0; e < (int)t->mono.size(); e++) t->toff[t->mono[e] + 1]++;
+  for (int q = 0; q < NS; q++) t->toff[q + 1] += t->toff[q];
+  t->tlm.assign(t->mono.size(), 0);
+  t->tval.assign(t->mono.size(), 0.0);
+  std::vector<int> fill(t->toff.begin(), t->toff.end() - 1);
+  for (int lm = 0; lm < W * W; lm++)
+    for (int e = t->off[lm]; e < t->off[lm + 1]; e++) {
+      const int slot = fill[t->mono[e]]++;
+      t->tlm[slot] = lm;
+      t->tval[slot] = t->val[e];
+    }
 }
 
 // ------------------------------------------------------------------ moment kernels
@@ -238,36 +258,42 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Pass 3: x-moments M_abc = dV sum_i x_i^a Y_bc(i), Y summed over the y-chunks
-// (warp per monomial, lanes over x), then the sparse map from monomials to q_lm.
-__global__ void __launch_bounds__(1024)
-    k_mp_final(Dims d, double x0, double hx, double dV, int L, int njc, const double* __restrict__ ypart,
-               const int* __restrict__ off, const int* __restrict__ mono,
-               const double* __restrict__ val, double* __restrict__ q) {
-  extern __shared__ double M[];   // (L+1)^3
+// Pass 3: x-moments M_abc = dV sum_i x_i^a Y_bc(i), Y summed over the y-chunks:
+// one block per monomial slot (threads over x, then a block sum), so that the
+// FP64 work is spread over the SMs instead of one SM's narrow FP64 pipe.
+__global__ void __launch_bounds__(256)
+    k_mp_xmom(Dims d, double x0, double hx, double dV, int L, int njc, const double* __restrict__ ypart,
+              double* __restrict__ M) {
   const int W = L + 1;
   const int P2 = W * (W + 1) / 2;
   const int ni = d.ni();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < W * W * W; t += blockDim.x) M[t] = 0.0;
-  __syncthreads();
-  for (int t = warp; t < W * W * W; t += nw) {
-    const int c = t % W, b = (t / W) % W, a = t / (W * W);
-    if (a + b + c > L) continue;
-    const int pi = pair_index(b, c, L);
-    double acc = 0.0;
-    for (int i = lane; i < ni; i += 32) {
-      double y = 0.0;
-      for (int jc = 0; jc < njc; jc++) y += ypart[((long long)jc * P2 + pi) * ni + i];
-      const double x = fma((double)(i + 1), hx, x0);
-      double xa = 1.0;
-      for (int e = 0; e < a; e++) xa *= x;
-      acc = fma(y, xa, acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) M[t] = acc * dV;
+  const int t = blockIdx.x;
+  const int c = t % W, b = (t / W) % W, a = t / (W * W);
+  if (a + b + c > L) {
+    if (threadIdx.x == 0) M[t] = 0.0;
+    return;   // uniform over the block
   }
-  __syncthreads();
+  const int pi = pair_index(b, c, L);
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+    double y = 0.0;
+    for (int jc = 0; jc < njc; jc++) y += ypart[((long long)jc * P2 + pi) * ni + i];
+    const double x = fma((double)(i + 1), hx, x0);
+    double xa = 1.0;
+    for (int e = 0; e < a; e++) xa *= x;
+    acc = fma(y, xa, acc);
+  }
+  __shared__ double red[32];
+  double v[1] = {acc};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) M[t] = v[0] * dV;
+}
+
+// q_lm = sum over the monomials of R_lm's coefficient times M_abc (sparse table).
+__global__ void __launch_bounds__(256)
+    k_mp_q(int L, const double* __restrict__ M, const int* __restrict__ off, const int* __restrict__ mono,
+           const double* __restrict__ val, double* __restrict__ q) {
+  const int W = L + 1;
   for (int lm = threadIdx.x; lm < W * W; lm += blockDim.x) {
     double acc = 0.0;
     for (int t = off[lm]; t < off[lm + 1]; t++) acc = fma(val[t], M[mono[t]], acc);
@@ -276,48 +302,39 @@ __global__ void __launch_bounds__(1024)
 }
 
 // ------------------------------------------------------------------ boundary values
-__device__ double eval_expansion(double x, double y, double z, int L, const double* __restrict__ q,
-                                 const double* __restrict__ consts, double G) {
+// F(u, v, w) = sum_{a+b+c <= L} C_abc u^a v^b w^c by nested Horner (w, then v,
+// then u); C dense over (L+1)^3 slots.
+__device__ __forceinline__ double eval_boundary_poly(double u, double v, double w, int L,
+                                                     const double* __restrict__ C) {
   const int W = L + 1;
-  const double* rec_a = consts;
-  const double* rec_b = consts + W * W;
-  const double* nrm = consts + 2 * W * W;
-  const double* dfac = consts + 3 * W * W;
-  const double r2 = x * x + y * y + z * z;
-  double acc[MAXL + 1];
-  for (int l = 0; l <= L; l++) acc[l] = 0.0;
-  double Cm = 1.0, Sm = 0.0;
-  for (int m = 0; m <= L; m++) {
-    if (m > 0) {
-      const double c = x * Cm - y * Sm;
-      Sm = x * Sm + y * Cm;
-      Cm = c;
+  double F = 0.0;
+  for (int a = L; a >= 0; a--) {
+    double Gv = 0.0;
+    for (int b = L - a; b >= 0; b--) {
+      const double* cb = C + (a * W + b) * W;
+      double H = cb[L - a - b];
+      for (int c = L - a - b - 1; c >= 0; c--) H = fma(H, w, cb[c]);
+      Gv = b == L - a ? H : fma(Gv, v, H);
     }
-    double t2 = 0.0, t1 = dfac[m];   // T_{l-2,m}, T_{l-1,m}
-    for (int l = m; l <= L; l++) {
-      double T;
-      if (l == m) T = dfac[m];
-      else if (l == m + 1) T = (2.0 * m + 1.0) * z * t1;
-      else T = rec_a[l * W + m] * z * t1 - rec_b[l * W + m] * r2 * t2;
-      if (l > m) { t2 = t1; t1 = T; }
-      const double ang = m == 0 ? q[l * l + l] : fma(q[l * l + l + m], Cm, q[l * l + l - m] * Sm);
-      acc[l] = fma(nrm[l * W + m] * T, ang, acc[l]);
-    }
+    F = a == L ? Gv : fma(F, u, Gv);
   }
-  const double ir = 1.0 / sqrt(r2);
-  const double ir2 = ir * ir;
-  double f = ir, phi = 0.0;
-  for (int l = 0; l <= L; l++) {
-    phi = fma(acc[l], f, phi);
-    f *= ir2;
-  }
-  return -G * phi;
+  return F;
 }
 
 __global__ void __launch_bounds__(256)
     k_mp_faces(Dims d, double x0, double y0, double z0, double hx, double hy, double hz, int L,
-               double G, const double* __restrict__ q, const double* __restrict__ consts,
-               double* __restrict__ phi) {
+               double G, const double* __restrict__ q, const int* __restrict__ toff,
+               const int* __restrict__ tlm, const double* __restrict__ tval, double* __restrict__ phi) {
+  // the boundary polynomial C_abc = sum over lm of q_lm times R_lm's coefficient
+  // of x^a y^b z^c (transposed table; zero where a+b+c > L), per block
+  extern __shared__ double poly[];
+  const int W = L + 1;
+  for (int t = threadIdx.x; t < W * W * W; t += blockDim.x) {
+    double acc = 0.0;
+    for (int e = toff[t]; e < toff[t + 1]; e++) acc = fma(tval[e], q[tlm[e]], acc);
+    poly[t] = acc;
+  }
+  __syncthreads();
   const long long id0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int g = d.g, ni = d.ni(), nj = d.nj(), nk = d.nk();
   const long long nzs = (long long)g * d.ex * d.ey;     // one z slab
@@ -355,7 +372,9 @@ __global__ void __launch_bounds__(256)
   const double x = fma((double)(i - g + 1), hx, x0);
   const double y = fma((double)(j - g + 1), hy, y0);
   const double z = fma((double)(k - g + 1), hz, z0);
-  phi[d.at(i, j, k)] = eval_expansion(x, y, z, L, q, consts, G);
+  const double ir = rsqrt(fma(x, x, fma(y, y, z * z)));
+  const double t = ir * ir;
+  phi[d.at(i, j, k)] = -G * ir * eval_boundary_poly(x * t, y * t, z * t, L, poly);
 }
 
 // ------------------------------------------------------------------ host launchers
@@ -374,45 +393,52 @@ cudaError_t cart_multipole_alloc(const Dims& d, int lmax, const MultipoleTables&
   m->nchunk = mp_chunks(d);
   size_t ncol = (size_t)m->nchunk * W * d.ni() * d.nj();
   size_t ny = (size_t)((d.nj() + MP_JT - 1) / MP_JT) * d.ni() * W * (W + 1) / 2;
-  size_t ncons = 3 * (size_t)W * W + W;
   cudaError_t e;
   if ((e = cudaMalloc(&m->colmom, ncol * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->ymom, ny * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->mom, (size_t)W * W * W * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->q, (size_t)W * W * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->off, t.off.size() * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->mono, std::max<size_t>(1, t.mono.size()) * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&m->val, std::max<size_t>(1, t.val.size()) * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&m->consts, ncons * sizeof(double))) != cudaSuccess) return e;
-  m->bytes = (ncol + ny + W * W + ncons + t.val.size()) * sizeof(double) +
-             (t.off.size() + t.mono.size()) * sizeof(int);
-  std::vector<double> cons;
-  cons.insert(cons.end(), t.rec_a.begin(), t.rec_a.end());
-  cons.insert(cons.end(), t.rec_b.begin(), t.rec_b.end());
-  cons.insert(cons.end(), t.nrm.begin(), t.nrm.end());
-  cons.insert(cons.end(), t.dfac.begin(), t.dfac.end());
+  if ((e = cudaMalloc(&m->toff, t.toff.size() * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->tlm, std::max<size_t>(1, t.tlm.size()) * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&m->tval, std::max<size_t>(1, t.tval.size()) * sizeof(double))) != cudaSuccess) return e;
+  m->bytes = (ncol + ny + W * W * W + W * W + 2 * t.val.size()) * sizeof(double) +
+             (t.off.size() + t.toff.size() + 2 * t.mono.size()) * sizeof(int);
   if ((e = cudaMemcpy(m->off, t.off.data(), t.off.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(m->toff, t.toff.data(), t.toff.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if (!t.mono.empty()) {
     if ((e = cudaMemcpy(m->mono, t.mono.data(), t.mono.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(m->val, t.val.data(), t.val.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(m->tlm, t.tlm.data(), t.tlm.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(m->tval, t.tval.data(), t.tval.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   }
-  return cudaMemcpy(m->consts, cons.data(), cons.size() * sizeof(double), cudaMemcpyHostToDevice);
+  return cudaSuccess;
 }
 
 size_t cart_multipole_bytes(const Dims& d, int lmax) {
   const size_t W = lmax + 1;
+  // table entries: at most (l+1)(l+2)/2 monomials for each of the 2l+1 R_lm of degree l
+  size_t ent = 0;
+  for (size_t l = 0; l < W; l++) ent += (2 * l + 1) * (l + 1) * (l + 2) / 2;
   return ((size_t)mp_chunks(d) * W * d.ni() * d.nj() +
-          (size_t)((d.nj() + MP_JT - 1) / MP_JT) * d.ni() * W * (W + 1) / 2 + W * W * 4 + 4096) *
-         sizeof(double);
+          (size_t)((d.nj() + MP_JT - 1) / MP_JT) * d.ni() * W * (W + 1) / 2 + W * W * W + W * W + 4096) *
+             sizeof(double) +
+         ent * 2 * (sizeof(double) + sizeof(int)) + (W * W + W * W * W + 2) * sizeof(int);
 }
 
 void cart_multipole_free(CartMultipoleDev* m) {
   cudaFree(m->colmom);
   cudaFree(m->ymom);
+  cudaFree(m->mom);
   cudaFree(m->q);
   cudaFree(m->off);
   cudaFree(m->mono);
   cudaFree(m->val);
-  cudaFree(m->consts);
+  cudaFree(m->toff);
+  cudaFree(m->tlm);
+  cudaFree(m->tval);
   *m = CartMultipoleDev();
 }
 
@@ -428,8 +454,8 @@ static void passes12(const Dims& d, double y0, double hy, double z0, double hz, 
   k_mp_ycols<L><<<g2, 256, 0, s>>>(d, y0, hy, nchunk, colmom, ypart);
 }
 
-// Moments about the origin in three separable passes (z, then y, then x).
-// Launches: 3.
+// Moments about the origin in three separable passes (z, then y, then x),
+// then the map to q_lm.  Launches: 4.
 cudaError_t launch_cart_moments(const Dims& d, const double lo[3], const double h[3],
                                 const double origin[3], const double* rho, CartMultipoleDev* m,
                                 cudaStream_t s) {
@@ -448,10 +474,9 @@ cudaError_t launch_cart_moments(const Dims& d, const double lo[3], const double 
   }
 #undef PS_MP_CASE
   const int W = L + 1;
-  size_t smem = (size_t)W * W * W * sizeof(double);
   const int njc = (d.nj() + MP_JT - 1) / MP_JT;
-  k_mp_final<<<1, 1024, smem, s>>>(d, lo[0] - origin[0], h[0], dV, L, njc, m->ymom, m->off, m->mono,
-                                   m->val, m->q);
+  k_mp_xmom<<<W * W * W, 256, 0, s>>>(d, lo[0] - origin[0], h[0], dV, L, njc, m->ymom, m->mom);
+  k_mp_q<<<1, 256, 0, s>>>(L, m->mom, m->off, m->mono, m->val, m->q);
   return cudaGetLastError();
 }
 
@@ -462,9 +487,10 @@ cudaError_t launch_cart_faces(const Dims& d, const double lo[3], const double h[
                                        (long long)d.nj() * d.nk());
   const int thr = 256;
   const long long blocks = (total + thr - 1) / thr;
-  k_mp_faces<<<(unsigned)blocks, thr, 0, s>>>(d, lo[0] - origin[0], lo[1] - origin[1],
-                                              lo[2] - origin[2], h[0], h[1], h[2], m->lmax, G, q,
-                                              m->consts, phi);
+  const size_t W = m->lmax + 1;
+  k_mp_faces<<<(unsigned)blocks, thr, W * W * W * sizeof(double), s>>>(
+      d, lo[0] - origin[0], lo[1] - origin[1], lo[2] - origin[2], h[0], h[1], h[2], m->lmax, G, q, m->toff,
+      m->tlm, m->tval, phi);
   return cudaGetLastError();
 }
 

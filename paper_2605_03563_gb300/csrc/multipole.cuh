@@ -17,6 +17,10 @@ struct MultipoleTables {
   // mono[k] = (a*(L+1) + b)*(L+1) + c, terms of (l,m) in [off[lm], off[lm+1]).
   std::vector<int> off, mono;
   std::vector<double> val;
+  // the transpose: per monomial slot t = (a*(L+1) + b)*(L+1) + c, the pairs
+  // (lm, val) of the R_lm that contain x^a y^b z^c, in [toff[t], toff[t+1])
+  std::vector<int> toff, tlm;
+  std::vector<double> tval;
   // recurrence constants for direct evaluation: rec_a[l*(L+1)+m] = (2l-1)/(l-m),
   // rec_b = (l+m-1)/(l-m) for l >= m+2; nrm[l*(L+1)+m] = sqrt(2 (l-m)!/(l+m)!) (m>0), 1 (m=0);
   // dfac[m] = (2m-1)!!
@@ -30,11 +34,14 @@ struct CartMultipoleDev {
   int nchunk = 1;              // z-chunks of the column pass
   double* colmom = nullptr;    // [nchunk][L+1][nj][ni] column z-moments
   double* ymom = nullptr;      // [y-chunks][(L+1)(L+2)/2][ni] y-moments of the column sums
+  double* mom = nullptr;       // [(L+1)^3] monomial moments M_abc (zero where a+b+c > L)
   double* q = nullptr;         // [(L+1)^2]
   int* off = nullptr;
   int* mono = nullptr;
   double* val = nullptr;
-  double* consts = nullptr;    // rec_a | rec_b | nrm | dfac
+  int* toff = nullptr;         // transposed table (see MultipoleTables)
+  int* tlm = nullptr;
+  double* tval = nullptr;
   size_t bytes = 0;
 };
 

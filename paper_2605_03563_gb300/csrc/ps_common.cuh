@@ -109,6 +109,34 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Running max |x| of FP64 values without FP64 instructions: non-negative
+// doubles order like their bit patterns, compared here as (high word, low
+// word) pairs of 32-bit integers (a 64-bit integer max issues at about the
+// FP64 rate on this part; the 32-bit compares and selects do not).
+struct AbsMax {
+  unsigned hi = 0u, lo = 0u;
+  __device__ __forceinline__ void take(double v) {
+    const unsigned h = (unsigned)__double2hiint(v) & 0x7fffffffu, l = (unsigned)__double2loint(v);
+    take_bits(h, l);
+  }
+  __device__ __forceinline__ void take_bits(unsigned h, unsigned l) {
+    const bool gt = h > hi || (h == hi && l > lo);
+    hi = gt ? h : hi;
+    lo = gt ? l : lo;
+  }
+  __device__ __forceinline__ double value() const { return __hiloint2double((int)hi, (int)lo); }
+};
+
+// Max over the warp of |v| (the bit order of AbsMax, integer pipe only).
+__device__ __forceinline__ double warp_absmax(double v) {
+  AbsMax a;
+  a.take(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    a.take_bits(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+  return a.value();
+}
+
 // Block-wide sum of NV values per thread, result valid in thread 0.
 // `sh` must hold 32 * NV doubles.
 template <int NV>
@@ -206,7 +234,7 @@ struct DevState {
   int done;           // 1 converged, 2 not converged (max_iter), 3 diverged
   int coarse_iter_last;
   int chunk_end;      // a captured loop continues while iter < chunk_end (set per step)
-  int pad0_;
+  int guess_nonzero;  // set-up copy: some interior node of the initial guess is nonzero
   long long coarse_iter_total;
   long long inner_cycles;   // IR inner cycles; FP32 BiCGSTAB: residual replacements
   // BiCGSTAB: breakdown restart and residual replacement

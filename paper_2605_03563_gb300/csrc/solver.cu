@@ -506,8 +506,12 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
 // after_sweep: the last operation on phi was a complete omega = 1 colour sweep of
 // the finest level, so the last colour's residual is exactly zero and only the
 // other colours are evaluated.
+// initial: the solve's first residual pass straight after cart_prepare; on
+// equal spacings it is skipped on the device when the set-up copy found the
+// guess's interior zero (the residual is then the reference vector).
 cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cudaStream_t s,
-                      unsigned long long cond = 0, int chunk = 0, bool after_sweep = false) {
+                      unsigned long long cond = 0, int chunk = 0, bool after_sweep = false,
+                      bool initial = false) {
   const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
   const int G = h->order / 2;
   const double dd = make_coef<double>(h->d0, h->h0, h->order).d;
@@ -527,14 +531,15 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
     const double per = h->order == 2 ? 6.0 : 11.0;
     prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? per : per + 1.0), 1, s);
     int nb = 0;
+    const bool gate = initial && mode == 1 && out == nullptr;
+    DevState* st = out != nullptr || gate ? h->st : nullptr;
     cudaError_t e = (h->nlaunch += 1,
-                     h->order == 2 ? launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, out ? h->st : nullptr,
-                                                       h->partials, &nb, s)
-                                   : launch_delta_diag13(h->d0, h->h0, out ? 3 : 2, phi, h->fs64, dout, out,
-                                                         out ? h->st : nullptr, h->partials, &nb, s));
+                     h->order == 2 ? launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, st, h->partials, &nb, s)
+                                   : launch_delta_diag13(h->d0, h->h0, out ? 3 : 2, phi, h->fs64, dout, out, st,
+                                                         h->partials, &nb, s));
     prof_end(h, s);
     if (e != cudaSuccess) return e;
-    return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, mode, h->st, s, cond, chunk));
+    return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, gate ? 4 : mode, h->st, s, cond, chunk));
   }
   prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (6.0 * G + 3.0), 1, s);
   cudaError_t e = out ? launch_delta_st(h->d0, h->order, h->h0, DT_F64, phi, h->fs64, dout, out, h->st, h->partials, s)
@@ -590,7 +595,7 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
     const double nf = (double)h->du.size() - n;
     const double W = h->lmax + 1.0;
     prof_begin(h, PC_MOMENTS, n * 8.0, n * W, 1, s);
-    cudaError_t e = (h->nlaunch += 3, launch_cart_moments(h->du, h->grid.lo, h->h0, h->bc.origin, rho, &h->mp, s));
+    cudaError_t e = (h->nlaunch += 4, launch_cart_moments(h->du, h->grid.lo, h->h0, h->bc.origin, rho, &h->mp, s));
     prof_end(h, s);
     TRY(e);
     prof_begin(h, PC_FACES, nf * 8.0, nf * 4.0 * W * W, 1, s);
@@ -601,14 +606,15 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
   TRY(cudaEventRecord(h->ev[1], s));
   Coef<double> cf = make_coef<double>(h->d0, h->h0, h->order);
   const double fscale = -4.0 * M_PI * h->bc.G * cf.inv_d;
-  if (!own_rhs) TRY((h->nlaunch += 1, launch_scale_rhs(h->d0, h->du, fscale, rho, DT_F64, h->fs64, s)));
+  // fs and the partials of the reference norm ||f - A phi0||, phi0 = boundary
+  // data only (the compact schemes form R_h f and their reference norm themselves)
+  if (!own_rhs)
+    TRY((h->nlaunch += 1, launch_scale_rhs_ref(h->d0, h->du, h->order, h->h0, fscale, rho, phi, h->fs64,
+                                               h->partials, s)));
   TRY((h->nlaunch += 1, launch_init_state(h->st, tol, max_iter, s)));
   // iterate on the handle's own (pitched) copy of phi: captured loop graphs reference it
-  TRY(copy_rows(h->phi0, h->d0, phi, h->du, s));
-  // the compact schemes form R_h f and their reference norm themselves
+  TRY((h->nlaunch += 1, launch_copy_guess(h->d0, h->du, phi, h->phi0, h->st, s)));
   if (own_rhs) return PS_OK;
-  // reference norm ||f - A phi0||, phi0 = boundary data only
-  TRY((h->nlaunch += 1, launch_ref_norm(h->d0, h->order, h->h0, h->phi0, h->fs64, h->partials, s)));
   TRY((h->nlaunch += 1, launch_finish_norm(h->partials, cart_partials_count(h->d0), cf.d, 0, h->st, s)));
   return PS_OK;
 }
@@ -624,7 +630,7 @@ ps_status begin_mg64(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   Hier* H = &h->h64;
   double* phi = h->phi0;
   H->lv[0].phi = phi;
-  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
+  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s, 0, 0, false, true));
   const int nu1 = o->nu1, nu2 = o->nu2;
   h->act.body = [h, H, phi, nu1, nu2](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
     cudaError_t e = vcycle(h, *H, 0, nu1, nu2, q);
@@ -700,7 +706,7 @@ ps_status sor_chebyshev_table(ps_ctx* h, double rj) {
 
 ps_status begin_sor(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   double* phi = h->phi0;
-  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s));
+  TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s, 0, 0, false, true));
   Level L0;
   L0.d = h->d0;
   for (int a = 0; a < 3; a++) L0.h[a] = h->h0[a];
@@ -2026,7 +2032,7 @@ ps_status poisson_batch_add(ps_batch b, ps_handle h, const double* rho_dev, doub
   if ((r = build_hier(h, b->prec == PS_FP64 ? 0 : 1, H)) != PS_OK) return r;
   if (b->prec == PS_FP64) {
     H->lv[0].phi = h->phi0;
-    TRY(norm_pass(h, h->phi0, 1, DT_F64, nullptr, s));
+    TRY(norm_pass(h, h->phi0, 1, DT_F64, nullptr, s, 0, 0, false, true));
   } else {
     TRY(norm_pass(h, h->phi0, 1, H->lv[0].dt, H->lv[0].fs, s));
   }

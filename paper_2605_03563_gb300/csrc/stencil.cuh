@@ -69,11 +69,15 @@ __device__ __forceinline__ void set_loop(const DevState* st, unsigned long long 
 // mode: 0 = reference norm, 1 = initial residual, 2 = iteration check, 3 =
 // iteration check that calls only a non-finite norm divergence (SOR on graded
 // spherical grids: its non-normal iteration grows the residual a
-// hundred-to-thousandfold before it converges).
+// hundred-to-thousandfold before it converges), 4 = initial residual whose
+// pass returned early on a zero guess (st->guess_nonzero == 0): the residual
+// is then the reference vector, and its norm and max are those of mode 0.
 __device__ __forceinline__ void finish_norm_block(const double* __restrict__ partials, int nblocks,
                                                   double dscale, int mode, DevState* __restrict__ st,
                                                   unsigned long long cond, int chunk) {
   __shared__ double red[64];
+  const bool from_ref = mode == 4 && st->guess_nonzero == 0;
+  if (mode == 4) mode = 1;
   double s = 0.0, m = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
     s += partials[2 * b];
@@ -90,8 +94,10 @@ __device__ __forceinline__ void finish_norm_block(const double* __restrict__ par
   for (int w = 1; w < (int)(blockDim.x + 31) / 32; w++) m = fmax(m, mx[w]);
   m = fmax(m, mx[0]);
   const double S = a[0];
-  const double rr = dscale * dscale * S;
+  const double rr = from_ref ? st->rr : dscale * dscale * S;
+  if (from_ref) m = st->amax;
   if (mode == 0) {
+    st->rr = rr;
     double ref = sqrt(rr);
     st->ref = ref > 0.0 ? ref : 1.0;
     st->amax = m;

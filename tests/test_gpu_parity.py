@@ -461,3 +461,43 @@ def test_mg_equal_spacing_noncubic(pkg, order, prec):
         assert rel_err(got, ref) <= FP64_TOL
     else:
         assert rel_err(got, ref) <= 1e-7
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_initial_residual_zero_and_nonzero_guess(pkg, order):
+    """From a guess whose interior is zero the initial residual is the
+    reference vector, and the solve takes the reference norm for it instead
+    of evaluating the stencil.  Any nonzero interior node must disable that:
+    (a) a guess that is zero but for one node of 1e8 starts from a relative
+    residual far above one, and the V-cycle count and potential follow the
+    oracle started from the same guess (a skipped pass would take 1 for the
+    initial residual and call the first cycle a divergence); (b) the converged
+    potential as guess is accepted after zero cycles; (c) an interior of -0.0
+    counts as zero and reproduces the +0.0 solve."""
+    n = 32
+    rho = np.abs(W.rng(31).standard_normal(W.cart_shape(n, order)))
+    zero = np.zeros(W.cart_shape(n, order))
+    g = order // 2
+    spike = zero.copy()
+    spike[g + 7, g + 11, g + 5] = 1e8
+    info, info_o, got, ref = _solve_pair(pkg, n, order, rho, spike, "mg", 1e-10, bc="multipole", lmax=4)
+    assert info.converged and info_o.converged
+    assert info.iterations == info_o.iterations
+    assert rel_err(got, ref) <= FP64_TOL
+    info0, info0_o, got0, ref0 = _solve_pair(pkg, n, order, rho, zero, "mg", 1e-10, bc="multipole", lmax=4)
+    assert info0.converged and info0.iterations == info0_o.iterations
+    assert rel_err(got0, ref0) <= FP64_TOL
+    # (b) warm start from the converged potential
+    phi_t = dev(got0)
+    with pkg.CartesianSolver(n, order, bc="multipole", lmax=4) as s:
+        infow = s.solve(dev(rho), phi_t, tol=1e-10, method="mg")
+    assert infow.converged and infow.iterations == 0
+    assert np.array_equal(host(phi_t), got0)
+    # (c) -0.0 interior
+    negz = zero.copy()
+    negz[g:-g, g:-g, g:-g] = -0.0
+    phi_t = dev(negz)
+    with pkg.CartesianSolver(n, order, bc="multipole", lmax=4) as s:
+        infon = s.solve(dev(rho), phi_t, tol=1e-10, method="mg")
+    assert infon.converged and infon.iterations == info0.iterations
+    assert np.array_equal(host(phi_t) + 0.0, got0 + 0.0)
