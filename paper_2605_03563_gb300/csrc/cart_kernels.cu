@@ -918,6 +918,101 @@ __global__ void __launch_bounds__(BX* BY)
   }
 }
 
+// The first colour pass (colour 0, omega = 1) of a V-cycle on the finest FP64
+// level (7-point, equal spacings), walked as k_sweep_diag walks it, with two
+// additions for a convergence check that lags one pass behind the V-cycle it
+// checks: the pass keeps the old value of every node it updates in save, so
+// that the state before it can be put back, and with NORM it forms the block
+// partials {sum of delta^2, 0}, delta = x_GS - x_old.  When the previous
+// V-cycle ended with a complete sweep, colour 1's residual is exactly zero and
+// these deltas (the operand order of the norm pass, so equal to its deltas bit
+// for bit) are the whole residual of that V-cycle's result.  The variant
+// without NORM opens a step: a plain pass that marks st->lag_pending = 1 for
+// the restore (it saves nothing: a step runs at least one iteration, whose
+// pass with NORM saves what the restore puts back).
+template <bool NORM>
+__global__ void __launch_bounds__(BX* BY)
+    k_sweep_diag_lag(Dims d, double c1, double* __restrict__ phi, const double* __restrict__ fs,
+                     double* __restrict__ save, int dl, DevState* __restrict__ st, double* __restrict__ partials) {
+  if (st->done) return;   // uniform over the grid
+  if (!NORM && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    st->lag_pending = 1;
+  const int t = blockIdx.x * BX + threadIdx.x;
+  const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
+  const int kn0 = blockIdx.z * dl + 1;
+  const int ni = d.ni(), nj = d.nj(), nk = d.nk();
+  const int u0 = jn0 < 1 ? 1 - jn0 : 0;
+  const int u1 = min(dl, min(nj - jn0 + 1, nk - kn0 + 1));
+  const int pm = (1 + jn0 + kn0) & 1;   // the pair member of colour 0 on this diagonal
+  const int in = 1 + 2 * t + pm;
+  double s2 = 0.0;
+  if (u0 < u1 && in <= ni) {
+    const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
+    long long c = d.at(in, jn0 + u0, kn0 + u0);
+    double qprev = phi[c - sy] + phi[c - sz];
+    double e = phi[c + 1], w = phi[c - 1], nn = phi[c + sy], up = phi[c + sz], f = fs[c], old = phi[c];
+    for (int u = u0; u < u1; u++) {
+      const long long cn = u + 1 < u1 ? c + step : c;
+      const double e2 = phi[cn + 1], w2 = phi[cn - 1], n2 = phi[cn + sy], u2 = phi[cn + sz], f2 = fs[cn];
+      const double old2 = phi[cn];
+      const double q = nn + up;
+      const double gs = fma(((e + w) + qprev) + q, c1, f);
+      if (NORM) {
+        const double dd = gs - old;
+        s2 = fma(dd, dd, s2);
+        save[c] = old;
+      }
+      phi[c] = gs;
+      qprev = q;
+      c += step;
+      e = e2;
+      w = w2;
+      nn = n2;
+      up = u2;
+      f = f2;
+      old = old2;
+    }
+  }
+  if (NORM) block_sum_max(s2, 0.0, partials);
+}
+
+// Put back the colour-0 values that the last lagged first pass of this step
+// saved (a no-op when none ran): the state of the last V-cycle checked.
+__global__ void __launch_bounds__(BX* BY)
+    k_restore_colour0(Dims d, double* __restrict__ phi, const double* __restrict__ save,
+                      const DevState* __restrict__ st) {
+  if (!st->lag_pending) return;
+  const int i = blockIdx.x * BX + threadIdx.x + 1;
+  const int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > d.ni() || j > d.nj()) return;
+  const int zc = zchunk(d.nk());
+  const int k0 = blockIdx.z * zc + 1, k1 = min(k0 + zc, d.nk() + 1);
+  for (int k = k0 + ((i + j + k0) & 1); k < k1; k += 2) {
+    const long long p = d.at(i, j, k);
+    phi[p] = save[p];
+  }
+}
+
+cudaError_t launch_sweep_lag(const Dims& d, const double h[3], double* phi, const double* fs, double* save,
+                             bool norm, DevState* st, double* partials, int* nblocks, cudaStream_t s) {
+  if (!is_iso(h) || d.g != 1 || (norm && partials == nullptr)) return cudaErrorInvalidValue;
+  const Coef<double> cf = make_coef<double>(d, h, 2);
+  const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+  const int pairs = (d.ni() + 1) / 2;
+  const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
+  if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+  if (norm) k_sweep_diag_lag<true><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, save, dl, st, partials);
+  else k_sweep_diag_lag<false><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, save, dl, st, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore_colour0(const Dims& d, double* phi, const double* save, const DevState* st,
+                                   cudaStream_t s) {
+  if (d.g != 1) return cudaErrorInvalidValue;
+  k_restore_colour0<<<point_grid(d), dim3(BX, BY), 0, s>>>(d, phi, save, st);
+  return cudaGetLastError();
+}
+
 // FP64 13-point colour pass on equal spacings along (j, k) anti-diagonals: the
 // nodes (i, j+u, k-u) have one colour of the three, none of their neighbours
 // is written in the pass, and the pair sum N + D (distance 1) of one node is
@@ -1467,7 +1562,10 @@ cudaError_t launch_coarse_cg(const Dims& d, int order, const double h[3], int dt
 }
 
 // ------------------------------------------------------------------ norm finisher
-__global__ void k_set_budget(DevState* st, int k) { st->chunk_end = st->iter + k; }
+__global__ void k_set_budget(DevState* st, int k) {
+  st->chunk_end = st->iter + k;
+  st->lag_pending = 0;
+}
 
 __global__ void k_init_state(DevState* st, double tol, int max_iter) {
   DevState z;

@@ -62,6 +62,18 @@ cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, cons
                                 int dout, void* out, const DevState* st, double* partials, int* nblocks,
                                 cudaStream_t s);
 
+// Lagged convergence check of FP64 7-point V-cycles on equal spacings: the
+// first colour pass (colour 0, omega = 1) of the next V-cycle; with norm it
+// stores the old values of its nodes in save (same layout as phi) and writes
+// partials {sum of (x_GS - x_old)^2, 0} (nblocks blocks, at most
+// delta_colours_partials(d, 2)); without norm it is the plain pass and marks
+// st->lag_pending.  Skipped once st->done.
+cudaError_t launch_sweep_lag(const Dims& d, const double h[3], double* phi, const double* fs, double* save,
+                             bool norm, DevState* st, double* partials, int* nblocks, cudaStream_t s);
+// phi <- save on the colour-0 nodes when st->lag_pending (undoes the last lagged pass).
+cudaError_t launch_restore_colour0(const Dims& d, double* phi, const double* save, const DevState* st,
+                                   cudaStream_t s);
+
 // Set-up copy of the initial guess (same logical extents, dst pitch >= src
 // pitch) that sets st->guess_nonzero when an interior node is nonzero.
 cudaError_t launch_copy_guess(const Dims& dd, const Dims& sd, const double* src, double* dst, DevState* st,

@@ -248,6 +248,7 @@ struct DevState {
   int iter_repl;           // BiCGSTAB: iteration of the last replacement
   int discard;             // refinement form: the inner solve failed, drop its increments
   int inner_cap;           // refinement form: most iterations of the current inner solve
+  int lag_pending;         // lagged-norm V-cycles: a first colour pass with saved values ran this step
 };
 
 enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_MAXITER = 2, DONE_DIVERGED = 3, DONE_FAULT = 4 };

@@ -117,6 +117,8 @@ struct Active {
   int restrict_tile = 0;              // tile variant of the fused FP32/BF16 residual + restriction
   long long body_kernels = 0;
   int inner_per_iter = 0;
+  // enqueued by every step before the iterations / after them (may be empty)
+  std::function<cudaError_t(cudaStream_t)> prologue, epilogue;
 };
 
 // A captured iteration body inside a CUDA-graph while loop.
@@ -386,7 +388,7 @@ Work work_of(const Level& L, int order) {
 }
 
 cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState* st, cudaStream_t s,
-                        const double* wtab = nullptr, int wlen = 0) {
+                        const double* wtab = nullptr, int wlen = 0, int first_colour = 0) {
   const int ncol = h->order == 2 ? 2 : 3;
   const Work w = work_of(L, h->order);
   cudaError_t e;
@@ -394,7 +396,7 @@ cudaError_t sweep_level(ps_ctx* h, Level& L, int l, double omega, const DevState
   // per update instead of 6 (13-point: 10 instead of 12)
   const bool diag = L.dt == DT_F64 && L.h[0] == L.h[1] && L.h[1] == L.h[2];
   const double per_update = diag ? 5.0 * w.G : 6.0 * w.G;
-  for (int c = 0; c < ncol; c++) {
+  for (int c = first_colour; c < ncol; c++) {
     // one colour pass reads phi everywhere, fs and phi on its colour, writes phi on its colour
     prof_begin(h, l == 0 ? PC_SWEEP0 : PC_SWEEP_C, w.n * w.S * (1.0 + 2.0 / ncol),
                w.n / ncol * (per_update + (omega != 1.0 || wtab ? 2.0 : 0.0)), w.fp64, s);
@@ -422,11 +424,16 @@ bool use_tiles(const ps_ctx* h, const Level& L, int l) {
 
 // count GS sweeps (omega = 1) on level l, starting and ending in L.phi: pairs of
 // out-of-place fused sweeps phi -> phib -> phi on tiled 7-point levels, colour
-// passes otherwise (and for an odd last sweep).
-cudaError_t smooth(ps_ctx* h, Level& L, int l, int count, cudaStream_t s) {
+// passes otherwise (and for an odd last sweep).  skip_first: the first colour
+// pass of the first sweep has already run (colour-pass levels only).
+cudaError_t smooth(ps_ctx* h, Level& L, int l, int count, cudaStream_t s, bool skip_first = false) {
   cudaError_t e = cudaSuccess;
   int done = 0;
-  if (L.phib && h->order == 2 && use_tiles(h, L, l)) {
+  if (skip_first && count >= 1) {
+    if ((e = sweep_level(h, L, l, 1.0, nullptr, s, nullptr, 0, 1)) != cudaSuccess) return e;
+    done = 1;
+  }
+  if (!skip_first && L.phib && h->order == 2 && use_tiles(h, L, l)) {
     const Work w = work_of(L, h->order);
     for (; done + 2 <= count; done += 2) {
       for (int half = 0; half < 2; half++) {
@@ -445,7 +452,9 @@ cudaError_t smooth(ps_ctx* h, Level& L, int l, int count, cudaStream_t s) {
   return cudaSuccess;
 }
 
-cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) {
+// skip_first: the first colour pass of level l's pre-smoothing has already run
+// (the lagged-norm V-cycles run it at the end of the previous iteration).
+cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s, bool skip_first = false) {
   Level& L = H.lv[l];
   cudaError_t e;
   if (l == h->nlev - 1) {
@@ -456,7 +465,7 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s) 
     return e;
   }
   const Work w = work_of(L, h->order);
-  if ((e = smooth(h, L, l, nu1, s)) != cudaSuccess) return e;
+  if ((e = smooth(h, L, l, nu1, s, skip_first)) != cudaSuccess) return e;
   Level& Cl = H.lv[l + 1];
   if (use_tiles(h, L, l)) {
     const int rtile = h->order == 2 ? (h->act.restrict_tile != 0 ? h->act.restrict_tile : rr_default_tile(L.dt)) : 0;
@@ -632,14 +641,51 @@ ps_status begin_mg64(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   H->lv[0].phi = phi;
   TRY(norm_pass(h, phi, 1, DT_F64, nullptr, s, 0, 0, false, true));
   const int nu1 = o->nu1, nu2 = o->nu2;
-  h->act.body = [h, H, phi, nu1, nu2](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
-    cudaError_t e = vcycle(h, *H, 0, nu1, nu2, q);
-    if (e != cudaSuccess) return e;
-    return norm_pass(h, phi, 2, DT_F64, nullptr, q, cond, chunk, nu2 >= 1);
-  };
-  h->act.key = "mg64:" + std::to_string(nu1) + ":" + std::to_string(nu2) + ":" + std::to_string(o->tile_min_n);
+  // 7-point on equal spacings with nu1, nu2 >= 1: the convergence check of
+  // V-cycle n lags into the first colour pass of V-cycle n + 1 (that pass's
+  // x_GS - x_old on colour 0 is V-cycle n's whole residual, colour 1's being
+  // zero after the post-smoothing), so the iteration body is
+  //   [V-cycle n without its first colour pass] [first colour pass of n + 1,
+  //   saving the old colour-0 values and forming the norm of n] [check of n].
+  // Each step opens with that first pass (the prologue, skipped once done)
+  // and closes by putting back the saved values (the epilogue): the state a
+  // step leaves is that of the last V-cycle checked, as without the lag.
+  Level& L0 = H->lv[0];
+  const bool lag = h->order == 2 && h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2] && nu1 >= 1 && nu2 >= 1 &&
+                   h->nlev >= 2 && L0.tmp != nullptr && L0.dt_tmp == DT_F64;
+  if (lag) {
+    double* save = (double*)L0.tmp;
+    const double dd = make_coef<double>(h->d0, h->h0, 2).d;
+    h->act.body = [h, H, phi, save, nu1, nu2, dd](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+      cudaError_t e = vcycle(h, *H, 0, nu1, nu2, q, true);
+      if (e != cudaSuccess) return e;
+      const double n = (double)h->d0.ni() * h->d0.nj() * h->d0.nk();
+      int nb = 0;
+      prof_begin(h, PC_NORM0, n * 8.0 * 2.0, n * 0.5 * 7.0, 1, q);
+      e = (h->nlaunch += 1, launch_sweep_lag(h->d0, h->h0, phi, h->fs64, save, true, h->st, h->partials, &nb, q));
+      prof_end(h, q);
+      if (e != cudaSuccess) return e;
+      return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, 2, h->st, q, cond, chunk));
+    };
+    h->act.prologue = [h, phi, save](cudaStream_t q) -> cudaError_t {
+      return (h->nlaunch += 1, launch_sweep_lag(h->d0, h->h0, phi, h->fs64, save, false, h->st, nullptr, nullptr, q));
+    };
+    h->act.epilogue = [h, phi, save](cudaStream_t q) -> cudaError_t {
+      return (h->nlaunch += 1, launch_restore_colour0(h->d0, phi, save, h->st, q));
+    };
+  } else {
+    h->act.body = [h, H, phi, nu1, nu2](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
+      cudaError_t e = vcycle(h, *H, 0, nu1, nu2, q);
+      if (e != cudaSuccess) return e;
+      return norm_pass(h, phi, 2, DT_F64, nullptr, q, cond, chunk, nu2 >= 1);
+    };
+  }
+  h->act.key = std::string(lag ? "mg64lag:" : "mg64:") + std::to_string(nu1) + ":" + std::to_string(nu2) + ":" +
+               std::to_string(o->tile_min_n);
   h->act.chunk = MG_CHUNK;
-  h->act.plain_chunk = 1;
+  // lagged: profiling steps also run up to a chunk of iterations (the state is
+  // read after each), so that the prologue and the restore stay once per step
+  h->act.plain_chunk = lag ? MG_CHUNK : 1;
   return PS_OK;
 }
 
@@ -1228,6 +1274,7 @@ ps_status build_loop_graph(ps_ctx* h, LoopGraph* g) {
 ps_status step_active(ps_ctx* h, int k) {
   cudaStream_t s = h->stream;
   ps_status r;
+  if (k <= 0) return PS_OK;
   if (h->prof) {
     // Event records cannot sit inside conditional graph bodies, so profiling
     // replays one iteration per launch from a plain graph that carries event
@@ -1235,6 +1282,7 @@ ps_status step_active(ps_ctx* h, int k) {
     // iteration runs past convergence; the events are harvested after each
     // launch (no host gaps between the kernels being timed).
     if ((r = read_state(h, s)) != PS_OK) return r;
+    if (h->act.prologue) TRY(h->act.prologue(s));
     ProfGraph& pg = h->pgraphs[h->act.key];
     if (!pg.exec) {
       while (h->ev_pool.size() < 512) {
@@ -1278,7 +1326,9 @@ ps_status step_active(ps_ctx* h, int k) {
         a.fp64 = rec.fp64;
         a.variant = rec.variant;
       }
+      if (q + 1 < n && (r = read_state(h, s)) != PS_OK) return r;
     }
+    if (h->act.epilogue) TRY(h->act.epilogue(s));
     h->act.plain_steps = true;
     return PS_OK;
   }
@@ -1286,7 +1336,9 @@ ps_status step_active(ps_ctx* h, int k) {
   if (!g.exec && (r = build_loop_graph(h, &g)) != PS_OK) return r;
   h->act.body_kernels = g.body_kernels;
   TRY((h->nlaunch += 2, launch_set_budget(h->st, k, s)));
+  if (h->act.prologue) TRY(h->act.prologue(s));
   TRY(cudaGraphLaunch(g.exec, s));
+  if (h->act.epilogue) TRY(h->act.epilogue(s));
   return PS_OK;
 }
 

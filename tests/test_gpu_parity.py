@@ -501,3 +501,34 @@ def test_initial_residual_zero_and_nonzero_guess(pkg, order):
         infon = s.solve(dev(rho), phi_t, tol=1e-10, method="mg")
     assert infon.converged and infon.iterations == info0.iterations
     assert np.array_equal(host(phi_t) + 0.0, got0 + 0.0)
+
+
+def test_lagged_check_leaves_the_checked_iterate(pkg):
+    """The FP64 7-point V-cycles check V-cycle n inside the first colour pass of
+    V-cycle n + 1 and put that pass back when a step ends.  A solve stopped by
+    max_iter must hold the oracle's iterate after exactly that many V-cycles
+    (an extra colour pass left in place would differ by far more than
+    rounding), and stepping one V-cycle at a time must reproduce the one-shot
+    solve bit for bit."""
+    n = 32
+    rho = W.gaussian_blobs(n, seed=7)
+    zero = np.zeros(W.cart_shape(n, 2))
+    for it in (1, 3):
+        info, info_o, got, ref = _solve_pair(pkg, n, 2, rho, zero, "mg", 1e-14, bc="multipole", max_iter=it)
+        assert info.status == pkg.capi.PS_NOT_CONVERGED
+        assert info.iterations == it == info_o.iterations
+        assert rel_err(got, ref) <= 1e-12
+        assert abs(info.rel_residual - info_o.rel_residual) <= 1e-9 * info_o.rel_residual
+    with pkg.CartesianSolver(n, bc="multipole") as s:
+        r = dev(rho)
+        one = torch.zeros_like(r)
+        base = s.solve(r, one, tol=1e-10)
+        phi = torch.zeros_like(r)
+        s.begin(r, phi, tol=1e-10)
+        done, _ = s.poll()
+        while not done:
+            s.step(1)
+            done, _ = s.poll()
+        info = s.end()
+    assert info.iterations == base.iterations
+    assert torch.equal(phi, one)
