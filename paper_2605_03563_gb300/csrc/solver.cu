@@ -538,15 +538,16 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
     // (j, k) diagonal walks: 5 + 1 FP64 instructions per node (13-point: 10 + 1),
     // + 1 for the FP64 sum of squares
     const double per = h->order == 2 ? 6.0 : 11.0;
-    prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? per : per + 1.0), 1, s);
-    int nb = 0;
     const bool gate = initial && mode == 1 && out == nullptr;
+    // (the gated initial pass is not timed: it does no work from a zero guess)
+    if (!gate) prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? per : per + 1.0), 1, s);
+    int nb = 0;
     DevState* st = out != nullptr || gate ? h->st : nullptr;
     cudaError_t e = (h->nlaunch += 1,
                      h->order == 2 ? launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, st, h->partials, &nb, s)
                                    : launch_delta_diag13(h->d0, h->h0, out ? 3 : 2, phi, h->fs64, dout, out, st,
                                                          h->partials, &nb, s));
-    prof_end(h, s);
+    if (!gate) prof_end(h, s);
     if (e != cudaSuccess) return e;
     return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, gate ? 4 : mode, h->st, s, cond, chunk));
   }
@@ -607,7 +608,9 @@ ps_status cart_prepare(ps_ctx* h, const double* rho, double* phi, double tol, in
     cudaError_t e = (h->nlaunch += 4, launch_cart_moments(h->du, h->grid.lo, h->h0, h->bc.origin, rho, &h->mp, s));
     prof_end(h, s);
     TRY(e);
-    prof_begin(h, PC_FACES, nf * 8.0, nf * 4.0 * W * W, 1, s);
+    // one FMA per coefficient of the boundary polynomial (Horner) + about 15 for
+    // 1/r, the scaled coordinates and the final product
+    prof_begin(h, PC_FACES, nf * 8.0, nf * (W * (W + 1.0) * (W + 2.0) / 6.0 + 15.0), 1, s);
     e = (h->nlaunch += 1, launch_cart_faces(h->du, h->grid.lo, h->h0, h->bc.origin, h->bc.G, h->mp.q, &h->mp, phi, s));
     prof_end(h, s);
     TRY(e);
