@@ -473,14 +473,20 @@ __global__ void __launch_bounds__(BX* BY)
 // equals k_delta's bit for bit and only the reductions run in another order).
 // STORE: the refinement pass of k_delta (the scaled FP32/BF16 inner right-hand
 // side, the FP32 sum of squares and max of the scaled values); otherwise the
-// FP64 sum of delta^2.  Partials {sum, max} per block.  !STORE with a state:
-// the initial residual pass, which returns at once when the set-up copy found
-// the guess's interior zero (its residual is then the reference vector).
+// FP64 sum of delta^2.  Partials {sum, max} per block.  initial: the solve's
+// initial residual; when the set-up copy found the guess's interior zero, the
+// plain pass returns at once (its residual is the reference vector, whose norm
+// is known) and the STORE pass takes delta = fs on every node away from the
+// boundary, and one FMA of the ghost value on a face (the general formula on
+// the rows and planes next to a y or z boundary): with the interior of phi
+// zero these are the general path's deltas bit for bit (up to the sign of a
+// zero), without its FP64 work.
 template <bool STORE>
 __global__ void __launch_bounds__(BX* BY)
     k_delta_diag(Dims d, double c1, const double* __restrict__ phi, const double* __restrict__ fs, int dl, int dout,
-                 void* __restrict__ out, const DevState* __restrict__ st, double* __restrict__ partials) {
-  if (!STORE && st != nullptr && st->guess_nonzero == 0) return;
+                 void* __restrict__ out, const DevState* __restrict__ st, int initial, double* __restrict__ partials) {
+  const bool zero_guess = initial && st->guess_nonzero == 0;
+  if (!STORE && zero_guess) return;
   const int t = blockIdx.x * BX + threadIdx.x;
   const int jn0 = blockIdx.y * BY + threadIdx.y + 2 - dl;
   const int kn0 = blockIdx.z * dl + 1;
@@ -503,7 +509,35 @@ __global__ void __launch_bounds__(BX* BY)
       s2 = fma(dd, dd, s2);
     }
   };
-  if (u0 < u1 && ia <= ni) {
+  if (STORE && zero_guess) {
+    if (u0 < u1 && ia <= ni) {
+      const bool hb = ia + 1 <= ni;
+      const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
+      long long c = d.at(ia, jn0 + u0, kn0 + u0);
+      auto full = [&](long long p) {
+        return fma(((phi[p + 1] + phi[p - 1]) + (phi[p - sy] + phi[p - sz])) + (phi[p + sy] + phi[p + sz]), c1,
+                   fs[p]) - phi[p];
+      };
+      for (int u = u0; u < u1; u++, c += step) {
+        const int j = jn0 + u, k = kn0 + u;
+        if (j == 1 || j == nj || k == 1 || k == nk) {   // uniform over the warp
+          take(c, full(c));
+          if (hb) take(c + 1, full(c + 1));
+          continue;
+        }
+        // x faces: the one nonzero neighbour is the ghost
+        double va = fs[c];
+        if (ia == 1) va = fma(phi[c - 1], c1, va);
+        else if (ia == ni) va = fma(phi[c + 1], c1, va);
+        take(c, va);
+        if (hb) {
+          double vb = fs[c + 1];
+          if (ia + 1 == ni) vb = fma(phi[c + 2], c1, vb);
+          take(c + 1, vb);
+        }
+      }
+    }
+  } else if (u0 < u1 && ia <= ni) {
     const bool hb = ia + 1 <= ni;
     const long long sy = d.sy(), sz = d.sz(), step = sy + sz;
     long long c = d.at(ia, jn0 + u0, kn0 + u0);
@@ -545,8 +579,10 @@ __global__ void __launch_bounds__(BX* BY)
 }
 
 cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* phi, const double* fs, int dout,
-                              void* out, const DevState* st, double* partials, int* nblocks, cudaStream_t s) {
-  if (!is_iso(h) || d.g != 1 || (out != nullptr && (st == nullptr || (dout != DT_F32 && dout != DT_BF16))))
+                              void* out, const DevState* st, bool initial, double* partials, int* nblocks,
+                              cudaStream_t s) {
+  if (!is_iso(h) || d.g != 1 || (out != nullptr && (st == nullptr || (dout != DT_F32 && dout != DT_BF16))) ||
+      (initial && st == nullptr))
     return cudaErrorInvalidValue;
   const Coef<double> cf = make_coef<double>(d, h, 2);
   const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
@@ -554,9 +590,11 @@ cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* ph
   const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
   if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
   if (out != nullptr)
-    k_delta_diag<true><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, dout, out, st, partials);
+    k_delta_diag<true><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, dout, out, st, initial ? 1 : 0,
+                                                      partials);
   else
-    k_delta_diag<false><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, DT_F64, nullptr, st, partials);
+    k_delta_diag<false><<<grid, dim3(BX, BY), 0, s>>>(d, cf.c1[0], phi, fs, dl, DT_F64, nullptr, st,
+                                                       initial ? 1 : 0, partials);
   return cudaGetLastError();
 }
 

@@ -92,13 +92,15 @@ cudaError_t launch_scale_rhs_ref(const Dims& d, const Dims& du, int order, const
 // FP64 residual pass of the 7-point stencil on equal spacings along (j, k)
 // diagonals (every delta equal to launch_delta's / launch_delta_st's bit for
 // bit; the reductions run in another order).  out == NULL: partials {sum of
-// delta^2, 0} (with st: the initial residual pass, which writes nothing when
-// st->guess_nonzero == 0, finisher mode 4); otherwise the refinement pass of
-// launch_delta_st (out FP32 or
+// delta^2, 0}; otherwise the refinement pass of launch_delta_st (out FP32 or
 // BF16, scaled by st->scale_next, FP32 sum and max of the scaled values).
 // Returns the block count in nblocks (at most delta_colours_partials(d, 2)).
+// initial (st required): the solve's initial residual; when st->guess_nonzero
+// == 0 the plain pass writes nothing (finisher mode 4) and the refinement pass
+// takes its deltas from fs and the ghost values alone.
 cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* phi, const double* fs, int dout,
-                              void* out, const DevState* st, double* partials, int* nblocks, cudaStream_t s);
+                              void* out, const DevState* st, bool initial, double* partials, int* nblocks,
+                              cudaStream_t s);
 
 // fs_coarse = factor * R(delta_fine)  (scaled coarse right-hand side); coarse = layout of fs_c
 cudaError_t launch_restrict(const Dims& fine, const Dims& coarse, int dt_f, const void* delta_f, int dt_c,

@@ -516,8 +516,10 @@ cudaError_t vcycle(ps_ctx* h, Hier& H, int l, int nu1, int nu2, cudaStream_t s, 
 // the finest level, so the last colour's residual is exactly zero and only the
 // other colours are evaluated.
 // initial: the solve's first residual pass straight after cart_prepare; on
-// equal spacings it is skipped on the device when the set-up copy found the
-// guess's interior zero (the residual is then the reference vector).
+// equal spacings, when the set-up copy found the guess's interior zero, the
+// norm-only pass is skipped on the device (the residual is then the reference
+// vector) and the 7-point refinement pass reads its deltas off fs and the
+// ghost values.
 cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cudaStream_t s,
                       unsigned long long cond = 0, int chunk = 0, bool after_sweep = false,
                       bool initial = false) {
@@ -539,15 +541,18 @@ cudaError_t norm_pass(ps_ctx* h, double* phi, int mode, int dout, void* out, cud
     // + 1 for the FP64 sum of squares
     const double per = h->order == 2 ? 6.0 : 11.0;
     const bool gate = initial && mode == 1 && out == nullptr;
-    // (the gated initial pass is not timed: it does no work from a zero guess)
-    if (!gate) prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? per : per + 1.0), 1, s);
+    // 7-point initial pass with a store: from a zero guess its deltas come from
+    // fs and the ghost values alone
+    const bool zg = initial && mode == 1 && h->order == 2;
+    // (the initial passes are not timed: from a zero guess they do little or no work)
+    if (!initial) prof_begin(h, PC_NORM0, n * (16.0 + (out ? (double)dt_size(dout) : 0.0)), n * (out ? per : per + 1.0), 1, s);
     int nb = 0;
     DevState* st = out != nullptr || gate ? h->st : nullptr;
     cudaError_t e = (h->nlaunch += 1,
-                     h->order == 2 ? launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, st, h->partials, &nb, s)
+                     h->order == 2 ? launch_delta_diag(h->d0, h->h0, phi, h->fs64, dout, out, st, zg, h->partials, &nb, s)
                                    : launch_delta_diag13(h->d0, h->h0, out ? 3 : 2, phi, h->fs64, dout, out, st,
                                                          h->partials, &nb, s));
-    if (!gate) prof_end(h, s);
+    if (!initial) prof_end(h, s);
     if (e != cudaSuccess) return e;
     return (h->nlaunch += 1, launch_finish_norm(h->partials, nb, dd, gate ? 4 : mode, h->st, s, cond, chunk));
   }
@@ -700,7 +705,7 @@ ps_status begin_ir(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   Level* L0 = &H->lv[0];
   double* phi = h->phi0;
   const int inner = std::max(1, o->inner_cycles);
-  TRY(norm_pass(h, phi, 1, L0->dt, L0->fs, s));
+  TRY(norm_pass(h, phi, 1, L0->dt, L0->fs, s, 0, 0, false, true));
   const int nu1 = o->nu1, nu2 = o->nu2;
   h->act.body = [h, H, L0, phi, nu1, nu2, inner](unsigned long long cond, int chunk, cudaStream_t q) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(L0->phi, 0, (size_t)L0->d.size() * dt_size(L0->dt), q);
@@ -2089,7 +2094,7 @@ ps_status poisson_batch_add(ps_batch b, ps_handle h, const double* rho_dev, doub
     H->lv[0].phi = h->phi0;
     TRY(norm_pass(h, h->phi0, 1, DT_F64, nullptr, s, 0, 0, false, true));
   } else {
-    TRY(norm_pass(h, h->phi0, 1, H->lv[0].dt, H->lv[0].fs, s));
+    TRY(norm_pass(h, h->phi0, 1, H->lv[0].dt, H->lv[0].fs, s, 0, 0, false, true));
   }
   BSlot& sd = b->hslots[si];
   memset(&sd, 0, sizeof(sd));

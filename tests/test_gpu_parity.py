@@ -532,3 +532,33 @@ def test_lagged_check_leaves_the_checked_iterate(pkg):
         info = s.end()
     assert info.iterations == base.iterations
     assert torch.equal(phi, one)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32", "mixed_bf16"])
+def test_zero_guess_fast_paths_equal_general_path(pkg, prec):
+    """From a guess whose interior is zero the initial residual is read off fs
+    and the ghost values (the FP64 norm-only pass returns at once, the
+    refinement's pass stores fs and one FMA of a ghost value per face node).
+    A guess that is zero but for one node of 5e-324 runs the general path, and
+    adding 5e-324 to the O(1) values there changes nothing: the two solves
+    must agree bit for bit (up to the sign of zeros) in iterations and
+    potential.  A guess that is zero but for one node of 1e3 reaches the
+    oracle's potential within the tolerance of the precision."""
+    n = 32
+    rho = W.gaussian_blobs(n, seed=9)
+    zero = np.zeros(W.cart_shape(n, 2))
+    tiny = zero.copy()
+    tiny[1 + 9, 1 + 4, 1 + 13] = 5e-324
+    outs = []
+    for guess in (zero, tiny):
+        phi_t = dev(guess)
+        with pkg.CartesianSolver(n, bc="multipole") as s:
+            info = s.solve(dev(rho), phi_t, tol=1e-10, method="mg", prec=prec)
+        assert info.converged
+        outs.append((info.iterations, host(phi_t) + 0.0))
+    assert outs[0][0] == outs[1][0] and np.array_equal(outs[0][1], outs[1][1])
+    spike = zero.copy()
+    spike[1 + 9, 1 + 4, 1 + 13] = 1e3
+    info, info_o, got, ref = _solve_pair(pkg, n, 2, rho, spike, "mg", 1e-10, bc="multipole", prec=prec)
+    assert info.converged and info_o.converged
+    assert rel_err(got, ref) <= (FP64_TOL if prec == "fp64" else MIXED_TOL)
