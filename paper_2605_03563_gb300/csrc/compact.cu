@@ -631,9 +631,11 @@ __global__ void __launch_bounds__(32 * GW, GR <= 4 ? 5 : 3)
   if (!ok && fault != nullptr) atomicExch(fault, 1);
 }
 
+// half_waves: z-chunks enough for about half_waves / 2 waves of blocks
 template <bool RESID, int GW, int GR>
 static cudaError_t launch_march_t(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
-                                  const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
+                                  const float* b, float* dst, const DevState* st, int* fault, int half_waves,
+                                  cudaStream_t s) {
   using T = SmT<GW, GR>;
   CUtensorMap mu, mb;
   if (!encode_level_map(&mu, DT_F32, u, d, GBW, T::GUH)) return cudaErrorInvalidValue;
@@ -649,9 +651,8 @@ static cudaError_t launch_march_t(const Dims& d, const W27& A, const W27& M, dou
   }
   const int sms = device_sm_count();
   const int gx = (d.ni() + GTX - 1) / GTX, gy = (d.nj() + T::GTY - 1) / T::GTY, nk = d.nk();
-  // z-chunks of at least 16 planes (4 extra staged planes each): about one wave
-  // with the small tile, two to three with the large one
-  const int want = std::max(1, (GR <= 4 ? 2 : 5) * sms * blocks_per_sm / (2 * gx * gy));
+  // z-chunks of at least 16 planes (4 extra staged planes each)
+  const int want = std::max(1, half_waves * sms * blocks_per_sm / (2 * gx * gy));
   const int zc = std::max(16, (nk + want - 1) / want);
   const dim3 grid(gx, gy, (nk + zc - 1) / zc);
   kern<<<grid, 32 * GW, T::SMEM, s>>>(mu, mb, d, wts<float>(A), wts<float>(M), (float)omega, dst, zc, st, fault);
@@ -666,8 +667,13 @@ template <bool RESID>
 static cudaError_t launch_march(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
                                 const float* b, float* dst, const DevState* st, int* fault, cudaStream_t s) {
   if (d.g != 1 || u == dst) return cudaErrorInvalidValue;
-  if (d.ni() >= 384 && d.nj() >= 384) return launch_march_t<RESID, 4, 8>(d, A, M, omega, u, b, dst, st, fault, s);
-  return launch_march_t<RESID, 4, 4>(d, A, M, omega, u, b, dst, st, fault, s);
+  // measured at 255^3 and 511^3: 8 output rows per warp from 200 points per
+  // side (65 thread instructions per node against 90 with 4 rows), with one
+  // wave of z-chunks below 384 points and about 2.5 waves from 384 (one wave
+  // of 511^3 chunks leaves SMs idle)
+  if (d.ni() >= 384 && d.nj() >= 384) return launch_march_t<RESID, 4, 8>(d, A, M, omega, u, b, dst, st, fault, 5, s);
+  if (d.ni() >= 200 && d.nj() >= 200) return launch_march_t<RESID, 4, 8>(d, A, M, omega, u, b, dst, st, fault, 2, s);
+  return launch_march_t<RESID, 4, 4>(d, A, M, omega, u, b, dst, st, fault, 2, s);
 }
 
 cudaError_t launch_c27_smooth(const Dims& d, const W27& A, const W27& M, double omega, const float* u,
