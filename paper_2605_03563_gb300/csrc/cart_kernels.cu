@@ -585,7 +585,7 @@ cudaError_t launch_delta_diag(const Dims& d, const double h[3], const double* ph
       (initial && st == nullptr))
     return cudaErrorInvalidValue;
   const Coef<double> cf = make_coef<double>(d, h, 2);
-  const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+  const int dl = diag_walk_len(d.nk());
   const int pairs = (d.ni() + 1) / 2;
   const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
   if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(BX* BY)
 }
 
 static dim3 diag13_grid(const Dims& d, int* dl_out) {
-  const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+  const int dl = diag_walk_len(d.nk());
   if (dl_out) *dl_out = dl;
   const int triples = (d.ni() + 2) / 3;
   return dim3((triples + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
@@ -791,7 +791,7 @@ static cudaError_t delta_skip_t(const Dims& d, const double h[3], int order, con
   if constexpr (G == 2 && ISO && sizeof(T) == 8 && sizeof(TO) == 8)
     return launch_delta_diag13(d, h, 1, (const double*)phi, (const double*)fs, DT_F64, out, nullptr, nullptr, nullptr, s);
   if constexpr (G == 1 && ISO && sizeof(T) == 8 && sizeof(TO) == 8) {
-    const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+    const int dl = diag_walk_len(d.nk());
     const int pairs = (d.ni() + 1) / 2;
     const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
     k_delta_skip_diag<<<grid, dim3(BX, BY), 0, s>>>(d, (double)cf.c1[0], (const double*)phi, (const double*)fs,
@@ -1035,7 +1035,7 @@ cudaError_t launch_sweep_lag(const Dims& d, const double h[3], double* phi, cons
                              bool norm, DevState* st, double* partials, int* nblocks, cudaStream_t s) {
   if (!is_iso(h) || d.g != 1 || (norm && partials == nullptr)) return cudaErrorInvalidValue;
   const Coef<double> cf = make_coef<double>(d, h, 2);
-  const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+  const int dl = diag_walk_len(d.nk());
   const int pairs = (d.ni() + 1) / 2;
   const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
   if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
@@ -1116,7 +1116,7 @@ static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* ph
   Coef<C> cf = make_coef<C>(d, h, order);
   if constexpr (G == 1 && ISO && sizeof(T) == sizeof(double)) {
     // diagonal walks of dl nodes (any dl gives the same result)
-    const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+    const int dl = diag_walk_len(d.nk());
     const int pairs = (d.ni() + 1) / 2;
     const dim3 grid((pairs + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
     if (omega == 1.0 && wtab == nullptr)
@@ -1128,7 +1128,7 @@ static cudaError_t sweep_t(const Dims& d, const double h[3], int order, void* ph
     return cudaGetLastError();
   }
   if constexpr (G == 2 && ISO && sizeof(T) == sizeof(double)) {
-    const int dl = d.nk() >= 200 ? 16 : (d.nk() >= 64 ? 8 : 4);
+    const int dl = diag_walk_len(d.nk());
     const int triples = (d.ni() + 2) / 3;
     const dim3 grid((triples + BX - 1) / BX, (d.nj() + dl - 1 + BY - 1) / BY, (d.nk() + dl - 1) / dl);
     if (omega == 1.0 && wtab == nullptr)

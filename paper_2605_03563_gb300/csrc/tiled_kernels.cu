@@ -1008,9 +1008,8 @@ __global__ void __launch_bounds__(256)
 // with the pair sum (N + U) of one node carried as the (S + D) of the next, in
 // the order of the diagonal colour pass (5 + 1 FP64 instructions per node).
 // Layout of the walks as in k_sweep_diag (x pair per thread, dl nodes per walk).
-static int diag_walk(int nk) { return nk >= 200 ? 16 : (nk >= 64 ? 8 : 4); }
 static dim3 diag_grid(const Dims& d) {
-  const int dl = diag_walk(d.nk());
+  const int dl = diag_walk_len(d.nk());
   const int pairs = (d.ni() + 1) / 2;
   return dim3((pairs + 31) / 32, (d.nj() + dl - 1 + 7) / 8, (d.nk() + dl - 1) / dl);
 }
@@ -1086,7 +1085,7 @@ cudaError_t launch_delta_colours(const Dims& d, int order, const double h[3], co
   if (order == 2 && iso) {
     const dim3 gd = diag_grid(d);
     if (nblocks) *nblocks = (int)(gd.x * gd.y * gd.z);
-    k_delta_red_diag<<<gd, blk, 0, s>>>(d, cf.c1[0], phi, fs, diag_walk(d.nk()), partials);
+    k_delta_red_diag<<<gd, blk, 0, s>>>(d, cf.c1[0], phi, fs, diag_walk_len(d.nk()), partials);
     return cudaGetLastError();
   }
   if (order == 4 && iso) return launch_delta_diag13(d, h, 0, phi, fs, DT_F64, nullptr, nullptr, partials, nblocks, s);
