@@ -161,47 +161,77 @@ void build_multipole_tables(int L, MultipoleTables* t) {
 // ------------------------------------------------------------------ moment kernels
 // Pass 1: z-moments of every (i, j) column, S_c(i, j) = sum_k rho(i, j, k) z_k^c,
 // c <= L.  One thread per column and z-chunk: a warp reads 32 consecutive x
-// nodes of a plane (coalesced), and each node costs L+1 FP64 multiply-adds with
-// the powers z_k^c taken from a shared table of the block's z-chunk.  No
-// reduction is needed inside the pass; z-chunks (for parallelism on small
-// grids) leave separate partial sums that pass 2 adds up.
+// nodes of a plane (coalesced).  The chunk's planes are taken in pairs
+// symmetric about its centre z_m, z = z_m +- u: the pair adds
+// (rho_hi + rho_lo) u^c to the moment about z_m for even c and
+// (rho_hi - rho_lo) u^c for odd c, (L+3)/2 FP64 instructions per node instead
+// of L+1 (the middle plane of an odd chunk adds to c = 0 only); the moments
+// about z_m move to the origin once per column by the binomial expansion
+// sum_e C(c, e) z_m^(c-e) mu_e.  No reduction is needed inside the pass;
+// z-chunks (for parallelism on small grids) leave separate partial sums that
+// pass 2 adds up.
 constexpr int MP_KC_MAX = 256;   // planes per z-chunk
 
 template <int L>
 __global__ void __launch_bounds__(256)
     k_mp_cols(Dims d, double z0, double hz, int kc, const double* __restrict__ rho,
               double* __restrict__ colmom) {
-  __shared__ double Z[MP_KC_MAX * (L + 1)];
+  __shared__ double U[MP_KC_MAX / 2 * (L + 1)];   // u_t^c of the chunk's plane pairs
+  __shared__ double Wsh[(L + 1) * (L + 1)];        // C(c, e) z_m^(c-e)
   const int ni = d.ni(), nj = d.nj(), nk = d.nk(), g = d.g;
   const int kb = blockIdx.y * kc, ke = min(kb + kc, nk);
-  for (int t = threadIdx.x; t < (ke - kb); t += blockDim.x) {
-    const double z = fma((double)(kb + t + 1), hz, z0);
+  const int m = ke - kb, np = m / 2;
+  const double half_h = 0.5 * hz;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    const double u = (double)(m - 1 - 2 * t) * half_h;   // z of plane ke-1-t minus z_m
     double pw = 1.0;
 #pragma unroll
     for (int c = 0; c <= L; c++) {
-      Z[t * (L + 1) + c] = pw;
-      pw *= z;
+      U[t * (L + 1) + c] = pw;
+      pw *= u;
     }
+  }
+  for (int q0 = threadIdx.x; q0 < (L + 1) * (L + 1); q0 += blockDim.x) {
+    const int c = q0 / (L + 1), e = q0 % (L + 1);
+    double w = 0.0;
+    if (e <= c) {
+      const double zm = fma((double)(kb + 1 + ke), half_h, z0);   // planes kb..ke-1 sit at z0 + (k+1) hz
+      double binom = 1.0;
+      for (int q = 1; q <= e; q++) binom = binom * (double)(c - e + q) / (double)q;
+      double zp = 1.0;
+      for (int q = 0; q < c - e; q++) zp *= zm;
+      w = binom * zp;
+    }
+    Wsh[q0] = w;
   }
   __syncthreads();
   const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (col >= (long long)ni * nj) return;
   const int i = (int)(col % ni), j = (int)(col / ni);
-  double sacc[L + 1];
+  double mu[L + 1];
 #pragma unroll
-  for (int c = 0; c <= L; c++) sacc[c] = 0.0;
+  for (int c = 0; c <= L; c++) mu[c] = 0.0;
   const long long sz = d.sz();
-  const double* r = rho + d.at(i + g, j + g, kb + g);
-  for (int k = kb; k < ke; k++, r += sz) {
-    const double w = *r;
-    const double* zp = Z + (k - kb) * (L + 1);
+  const double* lo = rho + d.at(i + g, j + g, kb + g);
+  const double* hi = rho + d.at(i + g, j + g, ke - 1 + g);
+  for (int t = 0; t < np; t++, lo += sz, hi -= sz) {
+    const double rl = *lo, rh = *hi;
+    const double sum = rh + rl, dif = rh - rl;
+    const double* up = U + t * (L + 1);
+    mu[0] += sum;
 #pragma unroll
-    for (int c = 0; c <= L; c++) sacc[c] = fma(w, zp[c], sacc[c]);
+    for (int c = 1; c <= L; c++) mu[c] = fma((c & 1) ? dif : sum, up[c], mu[c]);
   }
+  if (m & 1) mu[0] += *lo;   // the middle plane (u = 0)
   const long long plane = (long long)ni * nj;
   double* out = colmom + (long long)blockIdx.y * (L + 1) * plane + col;
 #pragma unroll
-  for (int c = 0; c <= L; c++) out[c * plane] = sacc[c];
+  for (int c = 0; c <= L; c++) {
+    double v = 0.0;
+#pragma unroll
+    for (int e = 0; e <= c; e++) v = fma(Wsh[c * (L + 1) + e], mu[e], v);
+    out[c * plane] = v;
+  }
 }
 
 __device__ __forceinline__ int pair_index(int b, int c, int L) {

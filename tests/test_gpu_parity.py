@@ -562,3 +562,18 @@ def test_zero_guess_fast_paths_equal_general_path(pkg, prec):
     info, info_o, got, ref = _solve_pair(pkg, n, 2, rho, spike, "mg", 1e-10, bc="multipole", prec=prec)
     assert info.converged and info_o.converged
     assert rel_err(got, ref) <= (FP64_TOL if prec == "fp64" else MIXED_TOL)
+
+
+@pytest.mark.parametrize("nu", [(1, 1), (3, 1), (2, 0), (0, 2)])
+def test_mg_cycle_shapes_match_oracle(pkg, nu):
+    """V(nu1, nu2) cycles other than V(2,2): with nu1, nu2 >= 1 the convergence
+    check lags into the next V-cycle's first colour pass, with nu1 = 0 or
+    nu2 = 0 the solve keeps a separate norm pass (after a sweep when nu2 >= 1);
+    either way the V-cycle count and the potential are the oracle's."""
+    n = 32
+    rho = W.gaussian_blobs(n, seed=13)
+    info, info_o, got, ref = _solve_pair(pkg, n, 2, rho, np.zeros(W.cart_shape(n, 2)), "mg", 1e-10,
+                                         bc="multipole", lmax=4, nu=nu)
+    assert info.converged and info_o.converged
+    assert info.iterations == info_o.iterations, (nu, info.iterations, info_o.iterations)
+    assert rel_err(got, ref) <= FP64_TOL
