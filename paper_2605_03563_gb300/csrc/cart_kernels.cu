@@ -959,8 +959,10 @@ __global__ void __launch_bounds__(BX* BY)
 // The first colour pass (colour 0, omega = 1) of a V-cycle on the finest FP64
 // level (7-point, equal spacings), walked as k_sweep_diag walks it, with two
 // additions for a convergence check that lags one pass behind the V-cycle it
-// checks: the pass keeps the old value of every node it updates in save, so
-// that the state before it can be put back, and with NORM it forms the block
+// checks: the pass keeps the old value of every node it updates in save
+// (packed at index c / 2: rows start at even offsets, so the colour-0 nodes of
+// a row have distinct halves), so that the state before it can be put back,
+// and with NORM it forms the block
 // partials {sum of delta^2, 0}, delta = x_GS - x_old.  When the previous
 // V-cycle ended with a complete sweep, colour 1's residual is exactly zero and
 // these deltas (the operand order of the norm pass, so equal to its deltas bit
@@ -998,7 +1000,7 @@ __global__ void __launch_bounds__(BX* BY)
       if (NORM) {
         const double dd = gs - old;
         s2 = fma(dd, dd, s2);
-        save[c] = old;
+        save[c >> 1] = old;   // packed: consecutive lanes, consecutive doubles
       }
       phi[c] = gs;
       qprev = q;
@@ -1027,13 +1029,15 @@ __global__ void __launch_bounds__(BX* BY)
   const int k0 = blockIdx.z * zc + 1, k1 = min(k0 + zc, d.nk() + 1);
   for (int k = k0 + ((i + j + k0) & 1); k < k1; k += 2) {
     const long long p = d.at(i, j, k);
-    phi[p] = save[p];
+    phi[p] = save[p >> 1];
   }
 }
 
 cudaError_t launch_sweep_lag(const Dims& d, const double h[3], double* phi, const double* fs, double* save,
                              bool norm, DevState* st, double* partials, int* nblocks, cudaStream_t s) {
-  if (!is_iso(h) || d.g != 1 || (norm && partials == nullptr)) return cudaErrorInvalidValue;
+  // the packed save index needs rows and planes at even offsets
+  if (!is_iso(h) || d.g != 1 || (norm && partials == nullptr) || (d.sy() & 1) || (d.sz() & 1))
+    return cudaErrorInvalidValue;
   const Coef<double> cf = make_coef<double>(d, h, 2);
   const int dl = diag_walk_len(d.nk());
   const int pairs = (d.ni() + 1) / 2;
@@ -1046,7 +1050,7 @@ cudaError_t launch_sweep_lag(const Dims& d, const double h[3], double* phi, cons
 
 cudaError_t launch_restore_colour0(const Dims& d, double* phi, const double* save, const DevState* st,
                                    cudaStream_t s) {
-  if (d.g != 1) return cudaErrorInvalidValue;
+  if (d.g != 1 || (d.sy() & 1) || (d.sz() & 1)) return cudaErrorInvalidValue;
   k_restore_colour0<<<point_grid(d), dim3(BX, BY), 0, s>>>(d, phi, save, st);
   return cudaGetLastError();
 }

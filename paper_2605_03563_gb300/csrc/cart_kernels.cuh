@@ -64,7 +64,8 @@ cudaError_t launch_delta_diag13(const Dims& d, const double h[3], int mode, cons
 
 // Lagged convergence check of FP64 7-point V-cycles on equal spacings: the
 // first colour pass (colour 0, omega = 1) of the next V-cycle; with norm it
-// stores the old values of its nodes in save (same layout as phi) and writes
+// stores the old values of its nodes in save (node index p at save[p / 2]; the
+// row pitch and plane stride of d must be even) and writes
 // partials {sum of (x_GS - x_old)^2, 0} (nblocks blocks, at most
 // delta_colours_partials(d, 2)); without norm it is the plain pass and marks
 // st->lag_pending.  Skipped once st->done.

@@ -660,7 +660,8 @@ ps_status begin_mg64(ps_ctx* h, const ps_solve_opts* o, cudaStream_t s) {
   // step leaves is that of the last V-cycle checked, as without the lag.
   Level& L0 = H->lv[0];
   const bool lag = h->order == 2 && h->h0[0] == h->h0[1] && h->h0[1] == h->h0[2] && nu1 >= 1 && nu2 >= 1 &&
-                   h->nlev >= 2 && L0.tmp != nullptr && L0.dt_tmp == DT_F64;
+                   h->nlev >= 2 && L0.tmp != nullptr && L0.dt_tmp == DT_F64 && h->d0.sy() % 2 == 0 &&
+                   h->d0.sz() % 2 == 0;   // the saved values are packed at node index / 2
   if (lag) {
     double* save = (double*)L0.tmp;
     const double dd = make_coef<double>(h->d0, h->h0, 2).d;
