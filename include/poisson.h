@@ -437,6 +437,14 @@ ps_status ps_op_prolong(const ps_grid* fine_grid, int stencil_order, int dtype,
  * the caller. */
 ps_status ps_op_scale_to_fp32(const double* x_dev, int64_t n, int e, float* out_dev, void* stream);
 
+/* phi[i] += e[i] * 2^p for -100 <= p <= 100 (otherwise PS_ERR_INVALID_ARG): the
+ * correction step of the mixed-precision refinement (Sec. 2.1.3), which adds
+ * the FP32 inner solution, computed for a right-hand side scaled by 2^-p, to
+ * the FP64 potential.  e * 2^p is exact in FP64 and is built on the integer
+ * pipe; the sum rounds once, as fma((double)e, 2^p, phi) does.  e_dev (FP32)
+ * and phi_dev (FP64) are device arrays of n elements owned by the caller. */
+ps_status ps_op_add_scaled_fp32(const float* e_dev, int64_t n, int p, double* phi_dev, void* stream);
+
 /* Multipole moments q_lm (Eq. outer_multipole) of rho over the interior nodes
  * about `origin`, (l_max+1)^2 doubles into q_host (synchronises). */
 ps_status ps_op_multipole_moments(const ps_grid* grid, int stencil_order, const double* rho_dev,

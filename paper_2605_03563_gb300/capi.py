@@ -99,6 +99,7 @@ SIGNATURES = {
                                            C.c_void_p, C.c_void_p]),
     "ps_op_spherical_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ps_op_scale_to_fp32": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "ps_op_add_scaled_fp32": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "ps_probe_fp64": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double),
                                 C.c_void_p]),
     "ps_probe_bounded_wait": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),

@@ -383,7 +383,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_correct(BArgs a, int list) {
     if (sl.st->done) continue;
     const BLevel& lv = sl.lv[0];
     const Dims d = lv.d;
-    const double isc = 1.0 / sl.st->scale_cur;
+    const double isc = inverse_scale(sl.st->scale_cur);
+    const int ie = pow2_exponent(isc);
     const int g = d.g;
     const int i = item.bx * BBX + threadIdx.x + g;
     const int j = item.by * BBY + threadIdx.y + g;
@@ -393,7 +394,8 @@ __global__ void __launch_bounds__(BBX* BBY) kb_correct(BArgs a, int list) {
     double* phi = sl.phi64;
     for (int k = k0; k < k1; k++) {
       const long long q = d.at(i, j, k);
-      phi[q] = fma((double)e[q], isc, phi[q]);
+      if (ie != INT_MIN) phi[q] += f32_to_f64_pow2(e[q], ie);
+      else phi[q] = fma((double)e[q], isc, phi[q]);
     }
   }
 }

@@ -1471,16 +1471,22 @@ __global__ void __launch_bounds__(BX* BY)
               const DevState* __restrict__ st) {
   if (st != nullptr && st->done) return;
   double isc = inv_scale;
-  if (st != nullptr) isc = 1.0 / st->scale_cur;
+  if (st != nullptr) isc = inverse_scale(st->scale_cur);
   const int g = d.g;
   const int i = blockIdx.x * BX + threadIdx.x + g;
   const int j = blockIdx.y * BY + threadIdx.y + g;
   if (i >= g + d.ni() || j >= g + d.nj()) return;
   const int zc = zchunk(d.nk());
   const int k0 = blockIdx.z * zc + g, k1 = min(k0 + zc, g + d.nk());
+  // FP32/BF16 corrections scaled by a power of two: the scaled value is built
+  // on the integer pipe and one DADD remains (the same bits as the FMA)
+  const int ie = sizeof(TE) < sizeof(double) ? pow2_exponent(isc) : INT_MIN;
+  // unrolled: the loads of several planes in flight together
+#pragma unroll 4
   for (int k = k0; k < k1; k++) {
     const long long p = d.at(i, j, k);
-    phi[p] = fma((double)St<TE>::ld(e + p), isc, phi[p]);
+    if (ie != INT_MIN) phi[p] += f32_to_f64_pow2((float)St<TE>::ld(e + p), ie);
+    else phi[p] = fma((double)St<TE>::ld(e + p), isc, phi[p]);
   }
 }
 
@@ -1640,6 +1646,21 @@ cudaError_t launch_loop_gate(const DevState* st, unsigned long long cond, cudaSt
 __global__ void k_pow2_to_f32(const double* __restrict__ x, long long n, int e, float* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = f64_to_f32_pow2(x[i], e);
+}
+
+// phi[i] += e[i] * 2^p: the refinement's correction step, the scaled value
+// built on the integer pipe and one DADD
+__global__ void k_add_pow2_f32(const float* __restrict__ e, long long n, int p, double* __restrict__ phi) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    phi[i] += f32_to_f64_pow2(e[i], p);
+}
+
+cudaError_t launch_add_pow2_f32(const float* e, long long n, int p, double* phi, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  const int blocks = (int)std::min<long long>(want, 8LL * device_sm_count());
+  k_add_pow2_f32<<<blocks, 256, 0, s>>>(e, n, p, phi);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pow2_to_f32(const double* x, long long n, int e, float* out, cudaStream_t s) {

@@ -177,6 +177,8 @@ int cart_partials_count(const Dims& d);
 // st->chunk_end = st->iter + k: iteration budget of the next loop-graph launch
 cudaError_t launch_set_budget(DevState* st, int k, cudaStream_t s);
 // out[i] = x[i] * 2^e rounded to the nearest FP32 (ties to even), |e| <= 100
+// phi[i] += e[i] * 2^p (|p| <= 100) on n elements: the refinement's correction.
+cudaError_t launch_add_pow2_f32(const float* e, long long n, int p, double* phi, cudaStream_t s);
 cudaError_t launch_pow2_to_f32(const double* x, long long n, int e, float* out, cudaStream_t s);
 // reset a solve's state on the device (no host round trip)
 cudaError_t launch_init_state(DevState* st, double tol, int max_iter, cudaStream_t s);

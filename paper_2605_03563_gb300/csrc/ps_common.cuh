@@ -220,6 +220,34 @@ __device__ __forceinline__ float f64_to_f32_pow2(double x, int e) {
   return __uint_as_float(sign | q);
 }
 
+// v * 2^e as binary64 for a binary32 v and |e| <= 100, built from v's encoding
+// on the integer pipe: the product is exact in binary64 (its exponent range
+// covers 2^(-149-100) .. 2^(128+100)), so only the exponent moves; binary32
+// subnormals are normalised with a count of leading zeros; zeros, infinities
+// and NaNs keep their class.  It replaces the FP64 pipe's conversion and
+// multiply (a DADD of the result rounds exactly as an FMA of v, 2^e and the
+// addend would).
+__device__ __forceinline__ double f32_to_f64_pow2(float v, int e) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const int ex = (int)((b >> 23) & 0xffu);
+  unsigned frac = b & 0x7fffffu;
+  if (ex == 0xff)   // infinity or NaN
+    return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((unsigned long long)frac << 29)));
+  int E;
+  if (ex == 0) {
+    if (frac == 0u) return __longlong_as_double((long long)sign);
+    const int p = 31 - __clz(frac);   // leading bit: value = 1.f x 2^(p - 149)
+    E = p - 149;
+    frac = (frac << (23 - p)) & 0x7fffffu;
+  } else {
+    E = ex - 127;
+  }
+  const unsigned long long bits =
+      sign | ((unsigned long long)(E + e + 1023) << 52) | ((unsigned long long)frac << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ int block_linear_id() {
   return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }

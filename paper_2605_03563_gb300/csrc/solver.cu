@@ -2356,6 +2356,13 @@ ps_status ps_op_scale_to_fp32(const double* x, int64_t n, int e, float* out, voi
   return PS_OK;
 }
 
+ps_status ps_op_add_scaled_fp32(const float* e, int64_t n, int p, double* phi, void* stream) {
+  if (n < 0 || (n > 0 && (!e || !phi))) return fail(PS_ERR_INVALID_ARG, "NULL buffer or negative n");
+  if (p < -100 || p > 100) return fail(PS_ERR_INVALID_ARG, "p must be in -100..100 (got %d)", p);
+  TRY(launch_add_pow2_f32(e, (long long)n, p, phi, (cudaStream_t)stream));
+  return PS_OK;
+}
+
 ps_status ps_op_multipole_moments(const ps_grid* grid, int order, const double* rho, const double origin[3],
                                   int l_max, double* q_host, void* stream) {
   Dims d;

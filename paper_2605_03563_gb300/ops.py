@@ -93,6 +93,15 @@ def scale_to_fp32(x, e, out, stream=None):
     check(lib().ps_op_scale_to_fp32(_p(x), x.numel(), int(e), _p(out), _s(stream)), "ps_op_scale_to_fp32")
 
 
+def add_scaled_fp32(e, p, phi, stream=None):
+    """phi += e * 2^p (the refinement's correction step); e float32, phi
+    float64, both contiguous CUDA tensors of the same size."""
+    import torch
+    if e.dtype != torch.float32 or phi.dtype != torch.float64 or e.numel() != phi.numel():
+        raise ValueError("e must be float32 and phi float64 of the same size")
+    check(lib().ps_op_add_scaled_fp32(_p(e), e.numel(), int(p), _p(phi), _s(stream)), "ps_op_add_scaled_fp32")
+
+
 def compact_operators(order, h, nlevels):
     """Level operators of the compact-stencil multigrid (Sec. 2.1.3) as a compact
     solve builds them, computed on the host: per level l (spacing h 2^l) the

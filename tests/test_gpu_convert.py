@@ -64,3 +64,42 @@ def test_scale_to_fp32_rejects_large_exponent(ops):
     out = torch.empty(4, dtype=torch.float32, device="cuda")
     with pytest.raises(P.capi.PoissonError):
         ops.scale_to_fp32(x, 101, out)
+
+
+@pytest.mark.parametrize("p", [0, 3, -3, 64, -64, 100, -100])
+def test_add_scaled_fp32_matches_fma(ops, p):
+    """The refinement's correction phi += e * 2^p builds e * 2^p from e's FP32
+    encoding on the integer pipe and adds once: bit for bit what CUDA's
+    conversion and FMA give, for FP32 normals, subnormals, signed zeros and
+    infinities, against FP64 addends of every magnitude (cancellation, ties)."""
+    rng = np.random.default_rng(300 + p)
+    n = 40000
+    f = (rng.uniform(1.0, 2.0, n) * rng.choice([-1.0, 1.0], n) * np.ldexp(1.0, rng.integers(-149, 128, n)))
+    f = f.astype(np.float32)
+    sub = np.ldexp(rng.integers(1, 1 << 23, 2000).astype(np.float64), -149).astype(np.float32)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, 1.0, -1.0, np.finfo(np.float32).max,
+                        np.finfo(np.float32).tiny, 2.0 ** -149], dtype=np.float32)
+    e = np.concatenate([f, sub, -sub, special])
+    m = e.size
+    base = np.ldexp(rng.uniform(-2.0, 2.0, m), rng.integers(-300, 300, m))
+    # addends that cancel the correction to a few bits, and exact ties
+    close = -np.ldexp(e.astype(np.float64), p)
+    fin = np.isfinite(close)
+    base[: m // 4][fin[: m // 4]] = close[: m // 4][fin[: m // 4]] * (1 + 2.0 ** -30)
+    e_t = torch.from_numpy(e).cuda()
+    phi = torch.from_numpy(base).cuda()
+    ref = torch.addcmul(phi, e_t.double(), torch.full_like(phi, 2.0 ** p))
+    got = phi.clone()
+    ops.add_scaled_fp32(e_t, p, got)
+    torch.cuda.synchronize()
+    a, b = got.view(torch.int64).cpu().numpy(), ref.view(torch.int64).cpu().numpy()
+    bad = np.nonzero(a != b)[0]
+    assert bad.size == 0, [(float(e[i]), float(base[i]), int(a[i]), int(b[i])) for i in bad[:5]]
+
+
+def test_add_scaled_fp32_rejects_large_exponent(ops):
+    import paper_2605_03563_gb300 as P
+    e = torch.zeros(4, dtype=torch.float32, device="cuda")
+    phi = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.capi.PoissonError):
+        ops.add_scaled_fp32(e, -101, phi)
