@@ -1047,8 +1047,9 @@ def main():
                 "fp64_dadd_peak": fp64_rate["dadd"],
                 "peak_source": "measured in this run: ps_probe_fp64 (DFMA chains, CUDA events); hbm " + peak_src}
         if dom_name == "sweep_colour_finest":
-            # the survey's count: 3S per unknown per full red-black sweep, i.e. 12 B
-            # per unknown per colour pass (FP64)
+            # the minimal count: 3S per unknown per full red-black sweep (phi and
+            # fs read once, phi written once), i.e. 12 B per unknown per colour
+            # pass (FP64)
             sb = unknowns * 3 * 8 / 2
             roof["hbm_frac_3S"] = sb / avg_s / 1e9 / peaks["hbm_gbs"]
             roof["algorithmic_bytes_3S"] = sb
