@@ -669,8 +669,8 @@ static cudaError_t launch_march(const Dims& d, const W27& A, const W27& M, doubl
   if (d.g != 1 || u == dst) return cudaErrorInvalidValue;
   // measured at 255^3 and 511^3: 8 output rows per warp from 200 points per
   // side (65 thread instructions per node against 90 with 4 rows), with one
-  // wave of z-chunks below 384 points and about 2.5 waves from 384 (one wave
-  // of 511^3 chunks leaves SMs idle)
+  // wave of z-chunks below 384 points and up to 2.5 from 384 (511^3: 3 chunks
+  // of 171 planes, 864 blocks; one chunk leaves SMs idle)
   if (d.ni() >= 384 && d.nj() >= 384) return launch_march_t<RESID, 4, 8>(d, A, M, omega, u, b, dst, st, fault, 5, s);
   if (d.ni() >= 200 && d.nj() >= 200) return launch_march_t<RESID, 4, 8>(d, A, M, omega, u, b, dst, st, fault, 2, s);
   return launch_march_t<RESID, 4, 4>(d, A, M, omega, u, b, dst, st, fault, 2, s);
